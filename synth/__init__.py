@@ -1,0 +1,308 @@
+"""Seeded synthetic inputs shared by the oracle tests and the GPU path.
+
+This module only *generates inputs*: domains, per-box refinement requests,
+charge and density fields sampled at cell centres, and transport-coefficient
+tables sampled from closed forms.  It holds none of the method's arithmetic
+(no octree construction, no ghost cells, no multigrid, no fluxes); both the
+oracle under ``oracle/`` and the CUDA library receive exactly the arrays made
+here.
+
+Shapes follow the paper's workloads (Sec. 3.1: octree of 8^3-cell boxes, a
+positive streamer with a charged head in a background field between a
+grounded bottom plate and a top electrode, Neumann-zero side walls).  The
+nitrogen transport data of Sec. 3.1 are not available, so closed forms stand
+in for them (mobility 0.03 m^2/Vs, diffusion 0.1 m^2/s,
+alpha(E) = 4.3e5 exp(-2e7/E) 1/m).
+
+Cell order inside a box is x fastest, then y, then z (index i + 8 j + 64 k).
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import numpy as np
+
+BOX = 8
+CELLS = BOX ** 3
+SEED = 0x5EED
+
+# SI constants (exact elementary charge; CODATA 2018 vacuum permittivity)
+E_CHARGE = 1.602176634e-19
+EPS0 = 8.8541878128e-12
+
+# face order used everywhere: -x, +x, -y, +y, -z, +z
+NEUMANN, DIRICHLET = 0, 1
+
+
+# --------------------------------------------------------------------------
+# counter-based uniform generator (SplitMix64, Steele/Lea/Flood 2014)
+# --------------------------------------------------------------------------
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for each counter value (state = seed + (c+1)*golden)."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (c + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
+    """U[0,1) with 53 random bits from SplitMix64."""
+    return (splitmix64(seed, counters) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+# --------------------------------------------------------------------------
+# domains
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Domain:
+    """Cubic domain [origin, origin+length]^3 on a base grid of nb^3 boxes.
+
+    nb must be a power of two; the coarse multigrid levels below the base
+    grid are the uniform levels 0..log2(nb).  max_level counts refinement
+    levels above the base grid.  bc_type/bc_val are per face in the order
+    -x,+x,-y,+y,-z,+z (0 = Neumann zero, 1 = Dirichlet with the given value).
+    """
+    length: float
+    nb: int
+    max_level: int
+    bc_type: tuple = (NEUMANN, NEUMANN, NEUMANN, NEUMANN, DIRICHLET, DIRICHLET)
+    bc_val: tuple = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    origin: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def lbase(self) -> int:
+        lb = int(round(np.log2(self.nb)))
+        assert (1 << lb) == self.nb, "base boxes per side must be a power of two"
+        return lb
+
+    def h(self, level: int) -> float:
+        return self.length / (BOX * (1 << level))
+
+
+def domain_uniform_cube(n_cells: int = 64, top: float = 1.0) -> Domain:
+    """Unit cube, phi=0 at z=0, phi=top at z=1, Neumann-zero sides."""
+    return Domain(length=1.0, nb=n_cells // BOX, max_level=0,
+                  bc_val=(0.0, 0.0, 0.0, 0.0, 0.0, top))
+
+
+@dataclasses.dataclass
+class Streamer:
+    """Synthetic positive streamer hanging from the top electrode.
+
+    Channel of radius `radius` along z above z_head, hemispherical head
+    centred at z_head (tip at z_head - radius), electron and ion density
+    `n_channel` inside with a smoothstep edge of width `edge`, and extra
+    positive ions `n_head` in a shell of thickness `shell` inside the
+    hemisphere surface (the space-charge layer of the head).
+    """
+    length: float = 0.016
+    radius: float = 0.5e-3
+    z_head: float = 8.5e-3
+    n_channel: float = 1e19
+    n_head: float = 1e20
+    edge: float = 50e-6
+    shell: float = 20e-6
+    background: float = 0.0
+    voltage: float = 25e3
+    refine_c: float = 10.0      # refine where |dist to surface| < box half-diagonal + C*h
+    refine_tip: float = 4.2e-3  # ... and box within refine_tip/2^k of the tip (k = level above base)
+
+    def axis(self):
+        return 0.5 * self.length, 0.5 * self.length
+
+    def signed_distance(self, x, y, z):
+        xc, yc = self.axis()
+        da = np.hypot(x - xc, y - yc)
+        s_cyl = da - self.radius
+        s_sph = np.sqrt(da ** 2 + (z - self.z_head) ** 2) - self.radius
+        return np.where(z >= self.z_head, s_cyl, s_sph)
+
+    def tip_distance(self, x, y, z):
+        xc, yc = self.axis()
+        zt = self.z_head - self.radius
+        return np.sqrt((x - xc) ** 2 + (y - yc) ** 2 + (z - zt) ** 2)
+
+
+def domain_streamer(nb: int = 8, max_level: int = 6, st: Streamer | None = None) -> Domain:
+    st = st or Streamer()
+    return Domain(length=st.length, nb=nb, max_level=max_level,
+                  bc_val=(0.0, 0.0, 0.0, 0.0, 0.0, st.voltage))
+
+
+# named workloads (sizes of the paper-shaped configurations)
+def workload(name: str):
+    """Return (Domain, Streamer|None) for a named workload.
+
+    uniform64     : unit cube, 64^3 cells as 512 boxes, Gaussian charge + noise
+    streamer6     : 16 mm cube, base 64^3, 6 refinement levels, ~2.4e6 cells
+    streamer8     : 16 mm cube, base 64^3, 8 refinement levels, ~1.7e7 cells
+    streamer_small: 16 mm cube, base 16^3, 3 refinement levels (test size)
+    streamer_tiny : 16 mm cube, base 16^3, 1 refinement level (dense-solve size)
+    """
+    if name == "uniform64":
+        return domain_uniform_cube(64), None
+    if name == "uniform32":
+        return domain_uniform_cube(32), None
+    if name == "streamer6":
+        st = Streamer()
+        return domain_streamer(8, 6, st), st
+    if name == "streamer8":
+        st = Streamer(refine_c=16.0, refine_tip=12e-3)
+        return domain_streamer(8, 8, st), st
+    if name == "streamer_small":
+        st = Streamer(refine_c=2.0, refine_tip=6e-3)
+        return domain_streamer(2, 3, st), st
+    if name == "streamer_tiny":
+        st = Streamer(refine_c=0.0, refine_tip=1e-3)
+        return domain_streamer(2, 1, st), st
+    raise KeyError(name)
+
+
+# --------------------------------------------------------------------------
+# sampling at cell centres
+# --------------------------------------------------------------------------
+def cell_centres(dom: Domain, levels: np.ndarray, ijk: np.ndarray):
+    """x, y, z of every cell of the given boxes, shape [nbox, 512]."""
+    levels = np.asarray(levels)
+    ijk = np.asarray(ijk, dtype=np.float64).reshape(-1, 3)
+    h = dom.length / (BOX * np.exp2(levels.astype(np.float64)))
+    loc = np.arange(BOX, dtype=np.float64) + 0.5
+    ii = np.tile(loc, BOX * BOX)
+    jj = np.tile(np.repeat(loc, BOX), BOX)
+    kk = np.repeat(loc, BOX * BOX)
+    x = dom.origin[0] + (ijk[:, 0:1] * BOX + ii[None, :]) * h[:, None]
+    y = dom.origin[1] + (ijk[:, 1:2] * BOX + jj[None, :]) * h[:, None]
+    z = dom.origin[2] + (ijk[:, 2:3] * BOX + kk[None, :]) * h[:, None]
+    return x, y, z
+
+
+def gaussian_charge(dom: Domain, levels, ijk, box_rank, sigma=0.05, amp=1.0,
+                    noise=1e-3, seed=SEED):
+    """rho = amp*exp(-|x-c|^2/(2 sigma^2)) + noise*U per cell.
+
+    U comes from SplitMix64(seed) with counter box_rank*512 + cell, so the
+    same cell always draws the same number whatever the array layout.
+    """
+    x, y, z = cell_centres(dom, levels, ijk)
+    c = dom.origin[0] + 0.5 * dom.length
+    r2 = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2
+    rho = amp * np.exp(-r2 / (2.0 * sigma ** 2))
+    if noise:
+        ctr = np.asarray(box_rank, dtype=np.uint64)[:, None] * np.uint64(CELLS) + \
+            np.arange(CELLS, dtype=np.uint64)[None, :]
+        rho = rho + noise * uniform01(seed, ctr)
+    return rho
+
+
+def manufactured_gaussian(dom: Domain, levels, ijk, sigma=0.05):
+    """phi* = z + exp(-r^2/(2 sigma^2)) and rho = -lap(phi*) at cell centres."""
+    x, y, z = cell_centres(dom, levels, ijk)
+    c = dom.origin[0] + 0.5 * dom.length
+    r2 = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2
+    g = np.exp(-r2 / (2.0 * sigma ** 2))
+    phi = z + g
+    lap = (r2 / sigma ** 4 - 3.0 / sigma ** 2) * g
+    return phi, -lap
+
+
+def smoothstep_edge(s, width):
+    """1 well inside (s <= -width), 0 outside (s >= 0), 1-3x^2+2x^3 between."""
+    x = np.clip((s + width) / width, 0.0, 1.0)
+    return 1.0 - 3.0 * x ** 2 + 2.0 * x ** 3
+
+
+def streamer_densities(dom: Domain, st: Streamer, levels, ijk, noise=None, seed=SEED):
+    """Electron and ion densities of the synthetic streamer at cell centres."""
+    x, y, z = cell_centres(dom, levels, ijk)
+    s = st.signed_distance(x, y, z)
+    core = st.n_channel * smoothstep_edge(s, st.edge)
+    ne = core + st.background
+    ni = core + st.background
+    head = (z < st.z_head) & (s < 0.0) & (s >= -st.shell)
+    ni = ni + np.where(head, st.n_head, 0.0)
+    return ne, ni
+
+
+def streamer_refine_flags(dom: Domain, st: Streamer, level: int, ijk: np.ndarray) -> np.ndarray:
+    """Refinement request (+1/0) per box of `level` for the synthetic streamer.
+
+    A box is requested when its centre lies within (half box diagonal +
+    refine_c * h) of the streamer surface and within (half box diagonal +
+    refine_tip / 2^k) of the tip, k = level - lbase: the finest levels
+    gather at the head, where the field is enhanced.
+    """
+    ijk = np.asarray(ijk, dtype=np.float64).reshape(-1, 3)
+    hb = dom.length / (1 << level)
+    h = hb / BOX
+    c = dom.origin[0] + (ijk + 0.5) * hb
+    hd = np.sqrt(3.0) * hb / 2.0
+    s = np.abs(st.signed_distance(c[:, 0], c[:, 1], c[:, 2]))
+    k = level - dom.lbase
+    td = st.tip_distance(c[:, 0], c[:, 1], c[:, 2])
+    near = (s < hd + st.refine_c * h) & (td < hd + st.refine_tip * 2.0 ** (-k))
+    return near.astype(np.int8)
+
+
+def refine_all(dom: Domain, st: Streamer, get_level_ijk, refine_level):
+    """Drive level-by-level refinement for any implementation.
+
+    get_level_ijk(level) -> int array [n,3] of the boxes of that level;
+    refine_level(level, flags) refines it.  Pure control flow.
+    """
+    for level in range(dom.lbase, dom.lbase + dom.max_level):
+        ijk = get_level_ijk(level)
+        if len(ijk) == 0:
+            break
+        refine_level(level, streamer_refine_flags(dom, st, level, ijk))
+
+
+# --------------------------------------------------------------------------
+# transport coefficients (Sec. 2.3 lookup table; closed forms stand in for
+# the BOLSIG+ nitrogen data)
+# --------------------------------------------------------------------------
+MOBILITY = 0.03
+DIFFUSION = 0.1
+
+
+def alpha_closed(E):
+    E = np.asarray(E, dtype=np.float64)
+    out = np.zeros_like(E)
+    pos = E > 0
+    out[pos] = 4.3e5 * np.exp(-2e7 / E[pos])
+    return out
+
+
+def coefficient_table(n: int = 1000, e_max: float = 35e6):
+    """Samples of mu, D, alpha at E_k = k*e_max/(n-1), k = 0..n-1."""
+    E = np.arange(n, dtype=np.float64) * (e_max / (n - 1))
+    return {
+        "e_max": e_max,
+        "mu": np.full(n, MOBILITY),
+        "diff": np.full(n, DIFFUSION),
+        "alpha": alpha_closed(E),
+        "E": E,
+    }
+
+
+def morton3(i, j, k, bits=21):
+    """Morton key with x in bit 0, y in bit 1, z in bit 2 (reference helper for tests)."""
+    key = 0
+    for b in range(bits):
+        key |= ((i >> b) & 1) << (3 * b)
+        key |= ((j >> b) & 1) << (3 * b + 1)
+        key |= ((k >> b) & 1) << (3 * b + 2)
+    return key
+
+
+def uniform_level_ijk(level: int) -> np.ndarray:
+    """All box coordinates of a full uniform level (x fastest), test helper."""
+    n = 1 << level
+    return np.array([(i, j, k) for k, j, i in itertools.product(range(n), repeat=3)], dtype=np.int64)
