@@ -851,6 +851,15 @@ static void leaf_fluxes(orc *o, int var_n) {
   }
 }
 
+/* refined boxes of both densities := average of their children, finest
+ * level first */
+static void restrict_densities(orc *o, int ne, int ni) {
+  for (int l = o->nlev - 1; l >= 1; --l) {
+    restrict_level(o, l, ne, ne);
+    restrict_level(o, l, ni, ni);
+  }
+}
+
 /* One forward Euler step dst = src + dt F(src) (Eq. 2-3) on leaf cells,
  * using the stored potential and |E|; then refined boxes get the average of
  * their children. */
@@ -882,13 +891,13 @@ static void euler_stage(orc *o, int sne, int sni, int dne, int dni, double dt) {
           oni[IX(i, j, k)] = ni[IX(i, j, k)] + dt * src;
         }
   }
-  for (int l = o->nlev - 1; l >= 1; --l) {
-    restrict_level(o, l, dne, dne);
-    restrict_level(o, l, dni, dni);
-  }
+  restrict_densities(o, dne, dni);
 }
 
+/* one Euler stage on the current densities (refined boxes first get the
+ * average of their children, so only leaf values matter) */
 void orc_fluid_stage(orc *o, double dt) {
+  restrict_densities(o, V_NE, V_NI);
   euler_stage(o, V_NE, V_NI, V_NE1, V_NI1, dt);
   memcpy(o->v[V_NE], o->v[V_NE1], sizeof(double) * BS * (size_t)o->nbox);
   memcpy(o->v[V_NI], o->v[V_NI1], sizeof(double) * BS * (size_t)o->nbox);
@@ -931,6 +940,7 @@ double orc_dt_limit(orc *o, double q, double eps) {
 int orc_advance(orc *o, double dt, double q, double eps, double tol, int max_cycles,
                 int nu1, int nu2, double *dt_next, int *cycles1, int *cycles2) {
   size_t bytes = sizeof(double) * BS * (size_t)o->nbox;
+  restrict_densities(o, V_NE, V_NI);
   memcpy(o->v[V_NE0], o->v[V_NE], bytes);
   memcpy(o->v[V_NI0], o->v[V_NI], bytes);
   euler_stage(o, V_NE0, V_NI0, V_NE, V_NI, dt);
