@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-time-step path on the 6-level synthetic streamer.
+
+Workload (one "step"): the 16 mm cube on a 64^3 base grid refined 6 levels
+around a synthetic positive streamer (2.4e6 leaf cells), 25 kV between the
+z plates: reset the densities from a device-resident copy, Eq. 5 charge
+right-hand side, FMG Poisson solve to relative residual 1e-8, field, time
+step, one Heun fluid step with two more Poisson solves to 1e-8.  Three
+Poisson solves per step; the metric is solves per second (and leaf
+Mcells x V-cycles per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+N > 1 runs under torchrun as N independent replicas (one per GPU, no data
+exchange): the path has no exchange step between independent solves.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "streamer6"
+TOL = 1e-8
+MAX_CYCLES = 40
+SOLVES_PER_STEP = 3
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_gpu_case():
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    dom, st = synth.workload(WORKLOAD)
+    g = pkg.Solver(dom, max_boxes=8192)
+    g.build_octree()
+    synth.refine_all(dom, st, g.level_ijk, g.refine_level)
+    t = g.tables()
+    ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+    g.set_table(synth.coefficient_table())
+    return dom, st, g, t, ne, ni
+
+
+def run_gpu(args):
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    import __graft_entry__
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    Q, E0 = synth.E_CHARGE, synth.EPS0
+    dom, st, g, t, ne, ni = build_gpu_case()
+    n_boxes = g.n_boxes
+    leaf_cells = g.n_leaves * 512
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ne_d = torch.from_numpy(ne).to(dev)
+    ni_d = torch.from_numpy(ni).to(dev)
+    ne_h = torch.from_numpy(ne).pin_memory()
+    ni_h = torch.from_numpy(ni).pin_memory()
+    phi_out = torch.empty((n_boxes, 512), dtype=torch.float64).pin_memory()
+    ne_out = torch.empty((n_boxes, 512), dtype=torch.float64).pin_memory()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    stream = g.stream
+
+    def step(host_io=False):
+        if host_io:
+            g.upload(pkg.NE, ne_h)
+            g.upload(pkg.NI, ni_h)
+        else:
+            g.var(pkg.NE).copy_(ne_d)
+            g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        rc0, rel0, c0 = g.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+        dt = g.dt_limit(Q, E0)
+        rc1, dtn, c1, c2 = g.advance(dt, Q, E0, TOL, MAX_CYCLES)
+        if host_io:
+            g.download(pkg.PHI, phi_out)
+            g.download(pkg.NE, ne_out)
+        assert rc0 == 0 and rc1 == 0, (rc0, rc1)
+        return c0 + c1 + c2
+
+    def timed(n, host_io=False):
+        total_ms, cycles = 0.0, 0
+        l0 = g.launch_count()
+        for _ in range(n):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cycles += step(host_io)
+            b.record(stream)
+            torch.cuda.synchronize()
+            total_ms += a.elapsed_time(b)
+        return total_ms, cycles, g.launch_count() - l0
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    ms, cycles, launches = timed(args.steps)
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    # end to end through the C ABI with host buffers (H2D + D2H every step)
+    e2e_ms, _, _ = timed(args.steps, host_io=True)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    # roofline of the dominant kernel: event-timed red-black smoother
+    # launches over a second pass of the same steps
+    roof = None
+    if not args.no_profile:
+        g.profile(True)
+        timed(args.steps)
+        kms, kn, kbytes = g.kernel_time(pkg.K_SMOOTH)
+        g.profile(False)
+        peak, kind = measured_peaks()
+        ach = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "kernel": "k_rbgs",
+                "launches": kn, "avg_launch_us": round(1e3 * kms / max(kn, 1), 3),
+                "bytes_per_launch": round(kbytes / max(kn, 1)), "peak_kind": kind,
+                "note": "per-launch average over %d event-timed launches; small coarse-level "
+                        "launches included" % kn}
+    steps = args.steps
+    solves = SOLVES_PER_STEP * steps * world
+    value = solves / (ms * 1e-3)
+    e2e_value = solves / (e2e_ms * 1e-3)
+    mcell_vc = leaf_cells * cycles * world / (ms * 1e-3) / 1e6
+    res = {
+        "metric": "Poisson solves/s to rel residual 1e-8 (octree FMG + Heun step, 3 solves/step)",
+        "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "leaf_cells": leaf_cells, "boxes": n_boxes,
+                   "levels": g.n_levels, "tol": TOL, "nu": [2, 2],
+                   "l2": "flushed between steps (258 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "mcells_vcycles_per_s": round(mcell_vc, 2),
+        "vcycles_per_step": cycles / steps,
+        "e2e": {"value": round(e2e_value, 3), "unit": "solves/s",
+                "h2d_bytes_per_step": int(2 * ne_h.numel() * 8),
+                "d2h_bytes_per_step": int(2 * phi_out.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roof,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline()
+    g.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def oracle_case():
+    import oracle
+    import synth
+    dom, st = synth.workload(WORKLOAD)
+    o = oracle.build_mesh(dom, st)
+    t = o.tables()
+    ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+    o.set_table(synth.coefficient_table())
+    return o, ne, ni
+
+
+def oracle_solve(o, ne, ni):
+    import oracle
+    import synth
+    o.set(oracle.NE, ne)
+    o.set(oracle.NI, ni)
+    o.charge_rhs(synth.E_CHARGE, synth.EPS0)
+    t0 = time.perf_counter()
+    st, rel, cyc = o.fmg(TOL, MAX_CYCLES)
+    return time.perf_counter() - t0, cyc
+
+
+def cpu_baseline():
+    """The oracle as it stands, single-threaded, on one FMG solve of the
+    same workload (about 10-20 s of CPU work)."""
+    o, ne, ni = oracle_case()
+    sec, cyc = oracle_solve(o, ne, ni)
+    return {"value": round(1.0 / sec, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "one FMG solve to 1e-8 of the %s workload (%d top-level V-cycles), "
+                      "plain C oracle, 1 thread" % (WORKLOAD, cyc)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    o, ne, ni = oracle_case()
+    for _ in range(args.warmup):
+        oracle_solve(o, ne, ni)
+    total = 0.0
+    for _ in range(args.steps):
+        sec, _ = oracle_solve(o, ne, ni)
+        total += sec
+    value = args.steps / total
+    res = {
+        "metric": "Poisson solves/s to rel residual 1e-8 (octree FMG + Heun step, 3 solves/step)",
+        "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "tol": TOL, "nu": [2, 2]},
+        "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step = one FMG solve to 1e-8 of the workload, plain C oracle"},
+        "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

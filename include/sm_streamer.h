@@ -1,0 +1,247 @@
+/* sm_streamer.h -- C ABI of the GB300 (sm_103a) library for the per-time-step
+ * path of the streamer fluid model of arXiv:1708.08434 (Afivo-streamer):
+ *
+ *   - octree of fixed 8^3-cell boxes with proper nesting   (Sec. 2.1.1)
+ *   - geometric multigrid for Poisson's equation, FAS V-cycle and FMG with
+ *     red-black Gauss-Seidel smoothing                      (Sec. 2.1.2, Eq. 1, 5)
+ *   - cell-centred field from the potential                 (Sec. 2.3)
+ *   - drift-diffusion-reaction step with Koren-limited upwind fluxes,
+ *     transport-coefficient lookup table, refinement-boundary fluxes and
+ *     Heun time stepping with CFL/diffusion/relaxation limits
+ *                                                            (Sec. 2.2-2.4, Eq. 2-3, 6-7)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an sm_status; SM_OK is 0, errors are negative.  After
+ *   an error, sm_last_error() gives a one-line reason.
+ * - Work is ordered on the CUDA stream given to sm_create (a cudaStream_t
+ *   passed as void*; NULL = the legacy default stream).  Calls that return a
+ *   scalar to the host (residuals, counts, time steps) synchronise that
+ *   stream before returning; the others only enqueue work.
+ * - Device memory: the caller allocates one device buffer ("arena") of the
+ *   size reported by sm_arena_size and hands it over with sm_bind_arena.  The
+ *   library carves every table and field out of it, never frees it and
+ *   never allocates device memory itself.  The arena must outlive the
+ *   context.
+ * - Field layout in the arena: each variable is an array of
+ *   [max_boxes][512] doubles; box b is the b-th entry of the box tables
+ *   (boxes sorted by level, then Morton key); inside a box cell (i,j,k),
+ *   0 <= i,j,k < 8, sits at i + 8 j + 64 k.
+ * - Faces are numbered 0..5 = -x,+x,-y,+y,-z,+z everywhere.
+ * - There is no CPU fallback: without a usable CUDA device sm_create returns
+ *   SM_ECUDA.
+ */
+#ifndef SM_STREAMER_H
+#define SM_STREAMER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SM_BOX 8            /* cells per box side (Sec. 2.1.1, N = 8) */
+#define SM_MAX_LEVELS 24    /* levels 0 .. SM_MAX_LEVELS-1 */
+
+typedef struct sm_ctx sm_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+  SM_OK = 0,
+  SM_EINVAL = -1,     /* bad argument or unsupported domain */
+  SM_ENOMEM = -2,     /* arena too small / box capacity exceeded */
+  SM_ECUDA = -3,      /* a CUDA runtime call failed */
+  SM_ENOCONV = -4,    /* tolerance not reached within max_cycles */
+  SM_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+  SM_ESTATE = -6      /* call out of order (e.g. no arena, no table) or a
+                         device-side consistency check failed */
+} sm_status;
+
+typedef enum { SM_FP64 = 0, SM_MIXED = 1 } sm_precision;
+
+typedef enum {
+  SM_PHI = 0,   /* electric potential phi                       */
+  SM_RHS = 1,   /* right-hand side f of L phi = f (Eq. 5)       */
+  SM_RES = 2,   /* scratch: residual / correction               */
+  SM_NE = 3,    /* electron density n_e (current)               */
+  SM_NI = 4,    /* positive-ion density n_i (current)           */
+  SM_EMAG = 5,  /* cell-centred field strength |E| (leaf boxes) */
+  SM_RHO = 6    /* external charge density rho (optional)       */
+} sm_var;
+
+/* Domain [origin, origin + length]^3 on a base grid of nb^3 boxes (nb a
+ * power of two, so levels 0 .. log2(nb) are uniform multigrid levels with
+ * 2^l boxes per side), refined up to max_level levels above the base.
+ * bc_type: 0 = Neumann zero, 1 = Dirichlet with value bc_val (potential).
+ * Densities always use Neumann zero walls (Sec. 3.1).  At least one face
+ * must be Dirichlet. */
+typedef struct {
+  double length;
+  double origin[3];
+  int nb;
+  int max_level;
+  int bc_type[6];
+  double bc_val[6];
+} sm_domain;
+
+typedef struct {
+  int max_boxes;   /* capacity of box tables and fields */
+  int nu1, nu2;    /* pre/post smoothing sweeps per level (2, 2) */
+  int precision;   /* sm_precision */
+} sm_config;
+
+/* Box tables (device pointers, borrowed: valid until the next
+ * sm_refine_level).  -1 in child[] = no children; nbr[b*26+d] for
+ * d = (dx+1) + 3(dy+1) + 9(dz+1) with the centre skipped (d > 13 shifted
+ * down by one): box index, -1 = outside the domain, -2 = no box of this
+ * level there (the parent's neighbour covers it).  level_offset[l] ..
+ * level_offset[l+1]-1 are the boxes of level l (host array). */
+typedef struct {
+  int n_boxes;
+  int n_levels;
+  int n_leaves;
+  int level_offset[SM_MAX_LEVELS + 1];
+  const int32_t *level;    /* [n_boxes]    */
+  const int32_t *ijk;      /* [n_boxes][3] box coordinates at its level */
+  const uint64_t *morton;  /* [n_boxes]    x -> bit 0, y -> bit 1, z -> bit 2 */
+  const int32_t *parent;   /* [n_boxes]    -1 on level 0 */
+  const int32_t *child;    /* [n_boxes][8] child c = cx + 2 cy + 4 cz */
+  const int32_t *nbr;      /* [n_boxes][26] */
+  const int32_t *leaf;     /* [n_leaves]   leaf box indices, table order */
+} sm_tables;
+
+/* ---- lifetime and memory ------------------------------------------------ */
+
+/* Create a context on the current CUDA device.  cfg and dom are copied.
+ * stream: cudaStream_t (as void*) all work is ordered on.
+ * Errors: SM_EINVAL (nb not a power of two, too many levels, no Dirichlet
+ * face, nu < 1, max_boxes too small for the uniform levels), SM_ECUDA. */
+int sm_create(sm_ctx **out, const sm_config *cfg, const sm_domain *dom, void *stream);
+
+/* Destroy the context (does not free the arena). NULL is accepted. */
+int sm_destroy(sm_ctx *ctx);
+
+/* Bytes of device memory the context needs (depends on cfg.max_boxes). */
+int sm_arena_size(const sm_ctx *ctx, size_t *bytes);
+
+/* Hand over a device buffer of at least sm_arena_size bytes, 256-byte
+ * aligned.  Zero-fills it on the stream.  Errors: SM_EINVAL, SM_ENOMEM. */
+int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* ---- octree (Sec. 2.1.1) ------------------------------------------------ */
+
+/* Build the uniform levels 0 .. log2(nb) (the base grid and the coarse
+ * multigrid levels below it) and their tables on the device.
+ * Out: *n_boxes.  Errors: SM_ESTATE (no arena), SM_ENOMEM. */
+int sm_build_octree(sm_ctx *ctx, int *n_boxes);
+
+/* Refine boxes of `level`, which must be the finest existing level and
+ * below the domain's maximum.  flags: HOST array, one int8 per box of the
+ * level in table order; > 0 requests refinement.  Proper nesting: a request
+ * is dropped when one of the box's 26 neighbour positions at its level
+ * holds no box (inside the domain).  Children are appended as level+1 in
+ * Morton order and all tables (neighbours, leaf list) are rebuilt on the
+ * device.  Out: *n_new boxes created, *n_dropped requests dropped (either
+ * may be NULL).  Errors: SM_EINVAL, SM_ESTATE, SM_ENOMEM (capacity). */
+int sm_refine_level(sm_ctx *ctx, int level, const int8_t *flags, int *n_new, int *n_dropped);
+
+/* Borrowed device pointers to the tables (see sm_tables). */
+int sm_get_tables(const sm_ctx *ctx, sm_tables *out);
+
+/* ---- fields -------------------------------------------------------------- */
+
+/* Device pointer of a variable's [max_boxes][512] double array (borrowed;
+ * SM_NE/SM_NI move between buffers in sm_advance_fluid). */
+int sm_var_ptr(const sm_ctx *ctx, int var, void **dev_ptr);
+
+/* Copy boxes [0, n_boxes) of a variable from / to HOST memory (pinned
+ * memory gives asynchronous uploads; sm_download synchronises the stream).
+ * Errors: SM_EINVAL (var, n_boxes > current box count). */
+int sm_upload(sm_ctx *ctx, int var, const double *host, int n_boxes);
+int sm_download(sm_ctx *ctx, int var, double *host, int n_boxes);
+
+/* Transport-coefficient table (Sec. 2.3): HOST arrays of n samples of the
+ * mobility, diffusion coefficient and effective ionization coefficient at
+ * E_k = k e_max/(n-1); looked up by linear interpolation, clamped at the
+ * ends.  2 <= n <= 4096. */
+int sm_set_table(sm_ctx *ctx, int n, double e_max, const double *mu,
+                 const double *diff, const double *alpha);
+
+/* Right-hand side of Eq. 5 on every leaf cell:
+ * f = -q (n_i - n_e) / eps, or f = -rho / eps when use_rho != 0. */
+int sm_charge_rhs(sm_ctx *ctx, double q, double eps, int use_rho);
+
+/* Refined boxes of n_e and n_i get the average of their 8 children,
+ * finest level first. */
+int sm_restrict_densities(sm_ctx *ctx);
+
+/* Coarse-to-fine interpolation values at refinement boundaries of `level`
+ * for variable var (SM_PHI): for each ghost cell of a face with no box of
+ * the same level, phihat = c/2 + c_t1/4 + c_t2/4 from the coarse cell c
+ * containing the ghost and its two tangential neighbours on the ghost's
+ * side; the ghost value is then phi_f/3 + 2 phihat/3 (Sec. 2.1.1). */
+int sm_fill_ghosts(sm_ctx *ctx, int var, int level);
+
+/* ---- multigrid (Sec. 2.1.2) ---------------------------------------------- */
+
+/* n_cycles FAS V(nu1,nu2) cycles on the full hierarchy starting from the
+ * current potential.  Out: relative residual max_leaf|f - L phi| /
+ * max_leaf|f - L 0| after the last cycle (may be NULL). */
+int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res);
+
+/* V-cycles from the current potential (warm start, Sec. 2.1.2) until the
+ * relative residual is <= tol (at least one cycle).  Errors: SM_ENOCONV
+ * when max_cycles is reached (the potential is still updated). */
+int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res);
+
+/* Full multigrid from scratch (restrict f, exact level-0 solve, prolong
+ * and one V-cycle per level), then V-cycles to tol.  *cycles counts the
+ * top-level V-cycles including the last FMG one. */
+int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res);
+
+/* ---- field and fluid step (Sec. 2.3, 2.4) --------------------------------- */
+
+/* |E| on every leaf cell: face fields E = (phi_i - phi_{i+1})/dx, cell
+ * components = mean of the two faces, |E| = Euclidean norm. */
+int sm_compute_field(sm_ctx *ctx);
+
+/* Next time step from the current field and n_e: 0.9 x min of the CFL 0.5
+ * limit, the advection+diffusion limit and the dielectric relaxation time
+ * eps/(q mu n_e).  Synchronises. */
+int sm_dt_limit(sm_ctx *ctx, double q, double eps, double *dt);
+
+/* One forward-Euler stage n <- n + dt F(n) with the current field (for
+ * tests); densities of refined boxes are restricted afterwards. */
+int sm_fluid_stage(sm_ctx *ctx, double dt);
+
+/* One explicit trapezoidal (Heun) step over dt (Sec. 2.4): stage 1, charge
+ * rhs, V-cycles to tol, field; stage 2 averaged with the stored densities,
+ * charge rhs, V-cycles to tol, field.  Out: *dt_next from the limits
+ * evaluated at stage 2, cycles[0..1] V-cycles of the two solves (either may
+ * be NULL).  Errors: SM_ENOCONV (a solve did not reach tol), SM_ESTATE (no
+ * table). */
+int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
+                     int max_cycles, double *dt_next, int *cycles);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+
+/* Per-kernel-class timing with CUDA events on the context stream: enable
+ * (1) or disable (0) recording; while enabled each launch of the selected
+ * classes is bracketed by events (this serialises nothing but adds a few
+ * microseconds per launch).  sm_kernel_time returns the summed device time
+ * in ms, launch count and algorithmic bytes moved for one class since the
+ * last enable.  Classes: 0 = red-black smoother. */
+int sm_profile_enable(sm_ctx *ctx, int enable);
+int sm_kernel_time(sm_ctx *ctx, int kclass, double *ms, long long *launches, double *bytes);
+
+/* Number of kernels this context has launched since it was created
+ * (diagnostics: lets a caller count device launches inside a region). */
+int sm_launch_count(const sm_ctx *ctx, long long *n);
+
+/* Human-readable reason of the last error on this context. */
+const char *sm_last_error(const sm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SM_STREAMER_H */

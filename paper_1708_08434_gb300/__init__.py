@@ -1,0 +1,325 @@
+"""Python binding of the GB300 library for the per-time-step path of the
+streamer fluid model of arXiv:1708.08434 (octree multigrid Poisson solve
+and drift-diffusion-reaction step).
+
+Argument marshalling only: every step runs in the CUDA kernels of
+``libsm_streamer.so`` (C ABI in ``include/sm_streamer.h``).  PyTorch
+provides the device memory (one arena tensor per solver) and the stream.
+There is no CPU fallback: without the compiled library or a CUDA device,
+constructing a ``Solver`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ENOCONV, SM_ETIMEOUT, SM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PHI, RHS, RES, NE, NI, EMAG, RHO = range(7)
+FP64, MIXED = 0, 1
+MAX_LEVELS = 24
+K_SMOOTH = 0
+
+_NAMES = {SM_EINVAL: "SM_EINVAL", SM_ENOMEM: "SM_ENOMEM", SM_ECUDA: "SM_ECUDA",
+          SM_ENOCONV: "SM_ENOCONV", SM_ETIMEOUT: "SM_ETIMEOUT", SM_ESTATE: "SM_ESTATE"}
+
+
+class SmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class _Domain(C.Structure):
+    _fields_ = [("length", C.c_double), ("origin", C.c_double * 3), ("nb", C.c_int),
+                ("max_level", C.c_int), ("bc_type", C.c_int * 6), ("bc_val", C.c_double * 6)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("max_boxes", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int)]
+
+
+class _Tables(C.Structure):
+    _fields_ = [("n_boxes", C.c_int), ("n_levels", C.c_int), ("n_leaves", C.c_int),
+                ("level_offset", C.c_int * (MAX_LEVELS + 1)),
+                ("level", C.c_void_p), ("ijk", C.c_void_p), ("morton", C.c_void_p),
+                ("parent", C.c_void_p), ("child", C.c_void_p), ("nbr", C.c_void_p),
+                ("leaf", C.c_void_p)]
+
+
+_lib = None
+
+EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_build_octree",
+           "sm_refine_level", "sm_get_tables", "sm_var_ptr", "sm_upload", "sm_download",
+           "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
+           "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
+           "sm_fluid_stage", "sm_advance_fluid", "sm_profile_enable", "sm_kernel_time",
+           "sm_launch_count", "sm_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libsm_streamer.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("CUDA library %s is not built (run __graft_entry__.build())" % path)
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    pI, pD = C.POINTER(C.c_int), C.POINTER(C.c_double)
+    sig = {
+        "sm_create": [C.POINTER(P), P, P, P],
+        "sm_destroy": [P],
+        "sm_arena_size": [P, C.POINTER(C.c_size_t)],
+        "sm_bind_arena": [P, P, C.c_size_t],
+        "sm_build_octree": [P, pI],
+        "sm_refine_level": [P, I, P, pI, pI],
+        "sm_get_tables": [P, P],
+        "sm_var_ptr": [P, I, C.POINTER(P)],
+        "sm_upload": [P, I, P, I],
+        "sm_download": [P, I, P, I],
+        "sm_set_table": [P, I, D, P, P, P],
+        "sm_charge_rhs": [P, D, D, I],
+        "sm_restrict_densities": [P],
+        "sm_fill_ghosts": [P, I, I],
+        "sm_mg_vcycle": [P, I, pD],
+        "sm_mg_solve": [P, D, I, pI, pD],
+        "sm_mg_fmg": [P, D, I, pI, pD],
+        "sm_compute_field": [P],
+        "sm_dt_limit": [P, D, D, pD],
+        "sm_fluid_stage": [P, D],
+        "sm_advance_fluid": [P, D, D, D, D, I, pD, pI],
+        "sm_profile_enable": [P, I],
+        "sm_kernel_time": [P, I, pD, C.POINTER(C.c_longlong), pD],
+        "sm_launch_count": [P, C.POINTER(C.c_longlong)],
+        "sm_last_error": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name == "sm_last_error" else C.c_int
+    _lib = lib
+    return lib
+
+
+def _hp(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """One octree with its fields on the current CUDA device."""
+
+    def __init__(self, dom, max_boxes: int, nu1: int = 2, nu2: int = 2, precision: int = FP64,
+                 stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise SmError(SM_ECUDA, "no CUDA device")
+        self._lib = lib
+        self.torch = torch
+        self.dom = dom
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d = _Domain(dom.length, (C.c_double * 3)(*dom.origin), dom.nb, dom.max_level,
+                    (C.c_int * 6)(*dom.bc_type), (C.c_double * 6)(*dom.bc_val))
+        cfg = _Config(max_boxes, nu1, nu2, precision)
+        h = C.c_void_p()
+        rc = lib.sm_create(C.byref(h), C.byref(cfg), C.byref(d), C.c_void_p(self.stream.cuda_stream))
+        if rc != SM_OK:
+            raise SmError(rc, "sm_create failed")
+        self._h = h
+        size = C.c_size_t()
+        self._ck(lib.sm_arena_size(h, C.byref(size)))
+        self.arena = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+        self._ck(lib.sm_bind_arena(h, C.c_void_p(self.arena.data_ptr()), size.value))
+        self.max_boxes = max_boxes
+
+    # -- plumbing --
+    def _ck(self, rc):
+        if rc != SM_OK:
+            raise SmError(rc, self._lib.sm_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.sm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _view(self, ptr: int, count: int, dtype):
+        """Zero-copy torch view of `count` elements at device pointer `ptr`."""
+        off = ptr - self.arena.data_ptr()
+        nbytes = count * dtype.itemsize
+        assert 0 <= off and off + nbytes <= self.arena.numel()
+        return self.arena[off:off + nbytes].view(dtype)
+
+    # -- octree --
+    def build_octree(self) -> int:
+        n = C.c_int()
+        self._ck(self._lib.sm_build_octree(self._h, C.byref(n)))
+        return n.value
+
+    def refine_level(self, level: int, flags) -> int:
+        f = np.ascontiguousarray(flags, dtype=np.int8)
+        new, dropped = C.c_int(), C.c_int()
+        self._ck(self._lib.sm_refine_level(self._h, level, _hp(f), C.byref(new), C.byref(dropped)))
+        self.dropped = dropped.value
+        return new.value
+
+    def _tables_raw(self) -> _Tables:
+        t = _Tables()
+        self._ck(self._lib.sm_get_tables(self._h, C.byref(t)))
+        return t
+
+    @property
+    def n_boxes(self) -> int:
+        return self._tables_raw().n_boxes
+
+    @property
+    def n_levels(self) -> int:
+        return self._tables_raw().n_levels
+
+    @property
+    def n_leaves(self) -> int:
+        return self._tables_raw().n_leaves
+
+    def tables(self) -> dict:
+        """Device tables copied to numpy (tests and input generation)."""
+        torch = self.torch
+        t = self._tables_raw()
+        n = t.n_boxes
+        self.stream.synchronize()
+        i32 = torch.int32
+        out = {
+            "level": self._view(t.level, n, i32).cpu().numpy().copy(),
+            "ijk": self._view(t.ijk, 3 * n, i32).cpu().numpy().reshape(n, 3).copy(),
+            "morton": self._view(t.morton, 2 * n, i32).cpu().numpy().view(np.uint64).copy(),
+            "parent": self._view(t.parent, n, i32).cpu().numpy().copy(),
+            "child": self._view(t.child, 8 * n, i32).cpu().numpy().reshape(n, 8).copy(),
+            "nbr": self._view(t.nbr, 26 * n, i32).cpu().numpy().reshape(n, 26).copy(),
+            "leaf": self._view(t.leaf, t.n_leaves, i32).cpu().numpy().copy(),
+            "level_offset": np.array(t.level_offset[:t.n_levels + 1], np.int32),
+        }
+        return out
+
+    def level_ijk(self, level: int) -> np.ndarray:
+        t = self._tables_raw()
+        if level >= t.n_levels:
+            return np.zeros((0, 3), np.int32)
+        lo, hi = t.level_offset[level], t.level_offset[level + 1]
+        self.stream.synchronize()
+        v = self._view(t.ijk, 3 * t.n_boxes, self.torch.int32)
+        return v[3 * lo:3 * hi].cpu().numpy().reshape(-1, 3)
+
+    def level_range(self, level: int):
+        t = self._tables_raw()
+        return t.level_offset[level], t.level_offset[level + 1]
+
+    # -- fields --
+    def var(self, var: int):
+        """Zero-copy [n_boxes, 512] float64 torch view of a variable."""
+        p = C.c_void_p()
+        self._ck(self._lib.sm_var_ptr(self._h, var, C.byref(p)))
+        n = self.n_boxes
+        return self._view(p.value, n * 512, self.torch.float64).view(n, 512)
+
+    def upload(self, var: int, arr):
+        """Host -> device for boxes [0, n); arr: numpy array or pinned torch CPU tensor."""
+        if isinstance(arr, np.ndarray):
+            a = np.ascontiguousarray(arr, dtype=np.float64).reshape(-1, 512)
+            self._keep = a
+            self._ck(self._lib.sm_upload(self._h, var, _hp(a), a.shape[0]))
+            self.stream.synchronize()
+        else:
+            self._ck(self._lib.sm_upload(self._h, var, C.c_void_p(arr.data_ptr()), arr.numel() // 512))
+
+    def download(self, var: int, out=None):
+        n = self.n_boxes
+        if out is None:
+            out = np.empty((n, 512), np.float64)
+        if isinstance(out, np.ndarray):
+            self._ck(self._lib.sm_download(self._h, var, _hp(out), out.shape[0]))
+        else:
+            self._ck(self._lib.sm_download(self._h, var, C.c_void_p(out.data_ptr()), out.numel() // 512))
+        return out
+
+    def set_table(self, tab: dict):
+        mu = np.ascontiguousarray(tab["mu"], np.float64)
+        dc = np.ascontiguousarray(tab["diff"], np.float64)
+        al = np.ascontiguousarray(tab["alpha"], np.float64)
+        self._ck(self._lib.sm_set_table(self._h, len(mu), float(tab["e_max"]), _hp(mu), _hp(dc), _hp(al)))
+
+    # -- method steps --
+    def charge_rhs(self, q=1.0, eps=1.0, use_rho=False):
+        self._ck(self._lib.sm_charge_rhs(self._h, q, eps, int(use_rho)))
+
+    def restrict_densities(self):
+        self._ck(self._lib.sm_restrict_densities(self._h))
+
+    def fill_ghosts(self, level: int, var: int = PHI):
+        self._ck(self._lib.sm_fill_ghosts(self._h, var, level))
+
+    def vcycles(self, n: int) -> float:
+        rel = C.c_double()
+        self._ck(self._lib.sm_mg_vcycle(self._h, n, C.byref(rel)))
+        return rel.value
+
+    def _solve(self, fn, tol, max_cycles, allow_noconv):
+        rel, cyc = C.c_double(), C.c_int()
+        rc = fn(self._h, tol, max_cycles, C.byref(cyc), C.byref(rel))
+        if rc != SM_OK and not (allow_noconv and rc == SM_ENOCONV):
+            self._ck(rc)
+        return rc, rel.value, cyc.value
+
+    def solve(self, tol=1e-8, max_cycles=50, allow_noconv=True):
+        return self._solve(self._lib.sm_mg_solve, tol, max_cycles, allow_noconv)
+
+    def fmg(self, tol=1e-8, max_cycles=50, allow_noconv=True):
+        return self._solve(self._lib.sm_mg_fmg, tol, max_cycles, allow_noconv)
+
+    def compute_field(self):
+        self._ck(self._lib.sm_compute_field(self._h))
+
+    def dt_limit(self, q, eps) -> float:
+        dt = C.c_double()
+        self._ck(self._lib.sm_dt_limit(self._h, q, eps, C.byref(dt)))
+        return dt.value
+
+    def fluid_stage(self, dt):
+        self._ck(self._lib.sm_fluid_stage(self._h, dt))
+
+    def advance(self, dt, q, eps, tol=1e-8, max_cycles=50, allow_noconv=True):
+        dtn = C.c_double()
+        cyc = (C.c_int * 2)()
+        rc = self._lib.sm_advance_fluid(self._h, dt, q, eps, tol, max_cycles, C.byref(dtn), cyc)
+        if rc != SM_OK and not (allow_noconv and rc == SM_ENOCONV):
+            self._ck(rc)
+        return rc, dtn.value, cyc[0], cyc[1]
+
+    # -- diagnostics --
+    def profile(self, enable: bool):
+        self._ck(self._lib.sm_profile_enable(self._h, int(enable)))
+
+    def launch_count(self) -> int:
+        n = C.c_longlong()
+        self._ck(self._lib.sm_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def kernel_time(self, kclass: int = K_SMOOTH):
+        ms, n, by = C.c_double(), C.c_longlong(), C.c_double()
+        self._ck(self._lib.sm_kernel_time(self._h, kclass, C.byref(ms), C.byref(n), C.byref(by)))
+        return ms.value, n.value, by.value
+

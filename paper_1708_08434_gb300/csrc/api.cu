@@ -1,0 +1,577 @@
+// api.cu -- context, arena, octree tables (Sec. 2.1.1), field transfer and
+// diagnostics of the C ABI declared in sm_streamer.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "sm_internal.cuh"
+
+using namespace sm;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+int sm_fail(sm_ctx *ctx, int code, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int sm_cuda_check(sm_ctx *ctx, cudaError_t e, const char *what) {
+  return sm_fail(ctx, SM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" int sm_launch_count(const sm_ctx *ctx, long long *n) {
+  if (!ctx || !n) return SM_EINVAL;
+  *n = ctx->n_launch;
+  return SM_OK;
+}
+
+extern "C" const char *sm_last_error(const sm_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+// ---------------------------------------------------------------------------
+// event timing of selected kernel classes
+// ---------------------------------------------------------------------------
+int sm_prof_begin(sm_ctx *ctx, int kclass, cudaEvent_t *ev) {
+  (void)kclass;
+  if (!ctx->prof) return SM_OK;
+  SM_CK(cudaEventCreate(ev));
+  SM_CK(cudaEventRecord(*ev, ctx->stream));
+  return SM_OK;
+}
+
+int sm_prof_end(sm_ctx *ctx, int kclass, cudaEvent_t *ev, double bytes) {
+  if (!ctx->prof) return SM_OK;
+  cudaEvent_t e2;
+  SM_CK(cudaEventCreate(&e2));
+  SM_CK(cudaEventRecord(e2, ctx->stream));
+  ctx->prof_recs.push_back({*ev, e2, kclass, bytes});
+  return SM_OK;
+}
+
+static int prof_collect(sm_ctx *ctx) {
+  auto &recs = ctx->prof_recs;
+  for (auto &r : recs) {
+    SM_CK(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    SM_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->prof_ms[r.kclass] += ms;
+    ctx->prof_n[r.kclass] += 1;
+    ctx->prof_bytes[r.kclass] += r.bytes;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  recs.clear();
+  return SM_OK;
+}
+
+extern "C" int sm_profile_enable(sm_ctx *ctx, int enable) {
+  if (!ctx) return SM_EINVAL;
+  int st = prof_collect(ctx);
+  if (st) return st;
+  ctx->prof = enable != 0;
+  if (enable)
+    for (int c = 0; c < K_NCLASS; ++c) ctx->prof_ms[c] = 0, ctx->prof_n[c] = 0, ctx->prof_bytes[c] = 0;
+  return SM_OK;
+}
+
+extern "C" int sm_kernel_time(sm_ctx *ctx, int kclass, double *ms, long long *launches, double *bytes) {
+  if (!ctx || kclass < 0 || kclass >= K_NCLASS) return SM_EINVAL;
+  int st = prof_collect(ctx);
+  if (st) return st;
+  if (ms) *ms = ctx->prof_ms[kclass];
+  if (launches) *launches = ctx->prof_n[kclass];
+  if (bytes) *bytes = ctx->prof_bytes[kclass];
+  return SM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// lifetime and arena
+// ---------------------------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct ArenaPlan {
+  size_t total = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    size_t at = total;
+    total = align256(total + count * sizeof(T));
+    return at;
+  }
+};
+
+// layout shared by sm_arena_size and sm_bind_arena
+struct Layout {
+  size_t level, ijk, parent, child, nbr, nbr6, leaf, morton, scan_a, scan_b, count, flags;
+  size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, total;
+};
+
+static Layout plan(int cap) {
+  ArenaPlan p;
+  Layout L;
+  size_t nc = (size_t)cap * CELLS;
+  L.level = p.take<int32_t>(cap);
+  L.ijk = p.take<int32_t>((size_t)cap * 3);
+  L.parent = p.take<int32_t>(cap);
+  L.child = p.take<int32_t>((size_t)cap * 8);
+  L.nbr = p.take<int32_t>((size_t)cap * 26);
+  L.nbr6 = p.take<int32_t>((size_t)cap * 6);
+  L.leaf = p.take<int32_t>(cap);
+  L.morton = p.take<uint64_t>(cap);
+  L.scan_a = p.take<int32_t>(cap + 1);
+  L.scan_b = p.take<int32_t>(cap + 1);
+  L.count = p.take<int32_t>(64);
+  L.flags = p.take<int8_t>(cap);
+  L.phi = p.take<double>(nc);
+  L.rhs = p.take<double>(nc);
+  L.res = p.take<double>(nc);
+  L.old = p.take<double>(nc);
+  L.rho = p.take<double>(nc);
+  L.emag = p.take<double>(nc);
+  for (int i = 0; i < 3; ++i) L.nb[i] = p.take<double>(nc);
+  for (int i = 0; i < 3; ++i) L.ib[i] = p.take<double>(nc);
+  L.gh = p.take<double>((size_t)cap * 6 * FACE);
+  L.cflux = p.take<double>((size_t)cap * 6 * FACE);
+  L.basis = p.take<double>(3 * 64 + 3 * 8);
+  L.tab = p.take<double>(3 * 4096);
+  L.dscal = p.take<unsigned long long>(SC_N);
+  L.total = p.total;
+  return L;
+}
+
+static int uniform_boxes(int lbase) {
+  int n = 0;
+  for (int l = 0; l <= lbase; ++l) n += 1 << (3 * l);
+  return n;
+}
+
+extern "C" int sm_create(sm_ctx **out, const sm_config *cfg, const sm_domain *dom, void *stream) {
+  if (!out || !cfg || !dom) return SM_EINVAL;
+  *out = nullptr;
+  int lb = 0;
+  while ((1 << lb) < dom->nb) ++lb;
+  if (dom->nb < 1 || (1 << lb) != dom->nb) return SM_EINVAL;
+  if (dom->max_level < 0 || lb + dom->max_level >= SM_MAX_LEVELS) return SM_EINVAL;
+  if (cfg->nu1 < 1 || cfg->nu2 < 1 || cfg->max_boxes < uniform_boxes(lb)) return SM_EINVAL;
+  if (!(dom->length > 0.0)) return SM_EINVAL;
+  bool any_dirichlet = false;
+  for (int f = 0; f < 6; ++f) {
+    if (dom->bc_type[f] != 0 && dom->bc_type[f] != 1) return SM_EINVAL;
+    any_dirichlet |= dom->bc_type[f] == 1;
+  }
+  if (!any_dirichlet) return SM_EINVAL;
+  if (cfg->precision != SM_FP64 && cfg->precision != SM_MIXED) return SM_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return SM_ECUDA;
+  }
+  sm_ctx *ctx = new sm_ctx();
+  ctx->cfg = *cfg;
+  ctx->dom = *dom;
+  ctx->lbase = lb;
+  ctx->lmax = lb + dom->max_level;
+  ctx->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    delete ctx;
+    return SM_ECUDA;
+  }
+  for (int f = 0; f < 6; ++f) {
+    ctx->bc.type[f] = dom->bc_type[f];
+    ctx->bc.val[f] = dom->bc_val[f];
+  }
+  for (int l = 0; l < MAXL; ++l) {
+    double h = dom->length / (NC * (double)(1 << l));
+    ctx->lh.h[l] = h;
+    ctx->lh.inv_h[l] = 1.0 / h;
+    ctx->lh.h2[l] = h * h;
+    ctx->lh.inv_h2[l] = 1.0 / (h * h);
+  }
+  if (cudaMallocHost((void **)&ctx->hscal, sizeof(double) * SC_N) != cudaSuccess) {
+    delete ctx;
+    return SM_ECUDA;
+  }
+  *out = ctx;
+  return SM_OK;
+}
+
+extern "C" int sm_destroy(sm_ctx *ctx) {
+  if (!ctx) return SM_OK;
+  prof_collect(ctx);
+  if (ctx->hscal) cudaFreeHost(ctx->hscal);
+  delete ctx;
+  return SM_OK;
+}
+
+extern "C" int sm_arena_size(const sm_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return SM_EINVAL;
+  *bytes = plan(ctx->cfg.max_boxes).total;
+  return SM_OK;
+}
+
+extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
+  if (!ctx || !dev_ptr) return SM_EINVAL;
+  Layout L = plan(ctx->cfg.max_boxes);
+  if (bytes < L.total) return sm_fail(ctx, SM_ENOMEM, "arena %zu bytes < needed %zu", bytes, L.total);
+  if (((uintptr_t)dev_ptr & 255) != 0) return sm_fail(ctx, SM_EINVAL, "arena not 256-byte aligned");
+  char *a = (char *)dev_ptr;
+  ctx->arena = a;
+  ctx->arena_bytes = bytes;
+  ctx->level = (int32_t *)(a + L.level);
+  ctx->ijk = (int32_t *)(a + L.ijk);
+  ctx->parent = (int32_t *)(a + L.parent);
+  ctx->child = (int32_t *)(a + L.child);
+  ctx->nbr = (int32_t *)(a + L.nbr);
+  ctx->nbr6 = (int32_t *)(a + L.nbr6);
+  ctx->leaf = (int32_t *)(a + L.leaf);
+  ctx->morton = (uint64_t *)(a + L.morton);
+  ctx->scan_a = (int32_t *)(a + L.scan_a);
+  ctx->scan_b = (int32_t *)(a + L.scan_b);
+  ctx->dev_count = (int32_t *)(a + L.count);
+  ctx->dev_flags = (int8_t *)(a + L.flags);
+  ctx->phi = (double *)(a + L.phi);
+  ctx->rhs = (double *)(a + L.rhs);
+  ctx->res = (double *)(a + L.res);
+  ctx->old = (double *)(a + L.old);
+  ctx->rho = (double *)(a + L.rho);
+  ctx->emag = (double *)(a + L.emag);
+  for (int i = 0; i < 3; ++i) {
+    ctx->nbuf[i] = (double *)(a + L.nb[i]);
+    ctx->ibuf[i] = (double *)(a + L.ib[i]);
+  }
+  ctx->gh = (double *)(a + L.gh);
+  ctx->cflux = (double *)(a + L.cflux);
+  ctx->basis = (double *)(a + L.basis);
+  ctx->tab = (double *)(a + L.tab);
+  ctx->dscal = (unsigned long long *)(a + L.dscal);
+  SM_CK(cudaMemsetAsync(a, 0, L.total, ctx->stream));
+  ctx->n_boxes = ctx->n_levels = ctx->n_leaves = 0;
+  ctx->basis_ready = false;
+  return SM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// octree kernels (Sec. 2.1.1): Morton-sorted levels, parent/child links,
+// 26-neighbour table by binary search in the sorted keys of a level
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t d_morton(int i, int j, int k) {
+  uint64_t key = 0;
+  for (int b = 0; b < 21; ++b) {
+    key |= (uint64_t)((i >> b) & 1) << (3 * b);
+    key |= (uint64_t)((j >> b) & 1) << (3 * b + 1);
+    key |= (uint64_t)((k >> b) & 1) << (3 * b + 2);
+  }
+  return key;
+}
+
+struct LevelOffsets {
+  int off[SM_MAX_LEVELS + 1];
+};
+
+// all boxes of the uniform levels 0..lbase (level l: key = index - off[l])
+__global__ void k_build_uniform(int total, int lbase, LevelOffsets lo, int32_t *level, int32_t *ijk,
+                                uint64_t *morton, int32_t *parent, int32_t *child) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= total) return;
+  int l = 0;
+  while (b >= lo.off[l + 1]) ++l;
+  uint64_t key = (uint64_t)(b - lo.off[l]);
+  int c[3] = {0, 0, 0};
+  for (int bit = 0; bit < 21; ++bit)
+    for (int d = 0; d < 3; ++d) c[d] |= (int)((key >> (3 * bit + d)) & 1) << bit;
+  level[b] = l;
+  ijk[3 * b] = c[0];
+  ijk[3 * b + 1] = c[1];
+  ijk[3 * b + 2] = c[2];
+  morton[b] = key;
+  parent[b] = l ? lo.off[l - 1] + (int)(key >> 3) : -1;
+  for (int q = 0; q < 8; ++q) child[8 * b + q] = l < lbase ? lo.off[l + 1] + (int)((key << 3) | q) : -1;
+}
+
+// neighbour tables of the boxes [lo, hi) of level l
+__global__ void k_neighbours(int lo, int hi, int l, const int32_t *__restrict__ ijk,
+                             const uint64_t *__restrict__ morton, int32_t *nbr, int32_t *nbr6) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = lo + t / 26, d = t % 26;
+  if (b >= hi) return;
+  int dd = d < 13 ? d : d + 1;
+  int dx = dd % 3 - 1, dy = (dd / 3) % 3 - 1, dz = dd / 9 - 1;
+  int q[3] = {ijk[3 * b] + dx, ijk[3 * b + 1] + dy, ijk[3 * b + 2] + dz};
+  int side = 1 << l;
+  int res;
+  if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= side || q[1] >= side || q[2] >= side) {
+    res = -1;
+  } else {
+    uint64_t key = d_morton(q[0], q[1], q[2]);
+    int a = lo, z = hi - 1;
+    res = -2;
+    while (a <= z) {
+      int m = (a + z) >> 1;
+      uint64_t km = morton[m];
+      if (km == key) { res = m; break; }
+      if (km < key) a = m + 1; else z = m - 1;
+    }
+  }
+  nbr[26 * b + d] = res;
+  // faces -x,+x,-y,+y,-z,+z sit at 26-list positions 12,13,10,15,4,21
+  int f = -1;
+  if (d == 12) f = 0; else if (d == 13) f = 1; else if (d == 10) f = 2;
+  else if (d == 15) f = 3; else if (d == 4) f = 4; else if (d == 21) f = 5;
+  if (f >= 0) nbr6[6 * b + f] = res;
+}
+
+// refinement request of box lo+t accepted when flagged and all 26
+// neighbour positions of its level hold a box or lie outside the domain
+__global__ void k_refine_accept(int lo, int n, const int8_t *__restrict__ flags,
+                                const int32_t *__restrict__ nbr, int32_t *accept, int32_t *count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int ok = 0;
+  if (flags[t] > 0) {
+    ok = 1;
+    for (int d = 0; d < 26; ++d)
+      if (nbr[26 * (lo + t) + d] == -2) ok = 0;
+    if (!ok) atomicAdd(count + 1, 1);
+  }
+  accept[t] = ok;
+}
+
+// exclusive prefix sum of n ints in one block (sizes here are <= ~1e6),
+// total written to out[n]
+__global__ void k_scan(const int32_t *__restrict__ in, int32_t *out, int n) {
+  __shared__ int32_t s[1024];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int x = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+// append 8 children per accepted box of level l (boxes [lo, lo+n)), in
+// parent order then child order: Morton order of the new level
+__global__ void k_make_children(int lo, int n, int new_lo, int l, const int32_t *__restrict__ accept,
+                                const int32_t *__restrict__ pos, int32_t *level, int32_t *ijk,
+                                uint64_t *morton, int32_t *parent, int32_t *child) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int p = t >> 3, c = t & 7;
+  if (p >= n || !accept[p]) return;
+  int pb = lo + p;
+  int b = new_lo + 8 * pos[p] + c;
+  int q[3] = {2 * ijk[3 * pb] + (c & 1), 2 * ijk[3 * pb + 1] + ((c >> 1) & 1), 2 * ijk[3 * pb + 2] + (c >> 2)};
+  level[b] = l + 1;
+  ijk[3 * b] = q[0];
+  ijk[3 * b + 1] = q[1];
+  ijk[3 * b + 2] = q[2];
+  morton[b] = (morton[pb] << 3) | (uint64_t)c;
+  parent[b] = pb;
+  child[8 * pb + c] = b;
+  for (int r = 0; r < 8; ++r) child[8 * b + r] = -1;
+}
+
+__global__ void k_mark_leaves(int n, const int32_t *__restrict__ child, int32_t *is_leaf) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n) is_leaf[b] = child[8 * b] < 0 ? 1 : 0;
+}
+
+__global__ void k_compact(int n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                          int32_t *out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n && flag[b]) out[pos[b]] = b;
+}
+
+static int rebuild_leaves(sm_ctx *ctx) {
+  int n = ctx->n_boxes;
+  k_mark_leaves<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->child, ctx->scan_a);
+  ++ctx->n_launch;
+  k_scan<<<1, 1024, 0, ctx->stream>>>(ctx->scan_a, ctx->scan_b, n);
+  ++ctx->n_launch;
+  k_compact<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->scan_a, ctx->scan_b, ctx->leaf);
+  ++ctx->n_launch;
+  SM_CKL("leaf list");
+  // leaf count and per-level leaf offsets from the prefix sums at level offsets
+  std::vector<int32_t> h(ctx->n_levels + 1);
+  for (int l = 0; l <= ctx->n_levels; ++l) {
+    SM_CK(cudaMemcpyAsync(&h[l], ctx->scan_b + ctx->level_off[l], sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  for (int l = 0; l <= ctx->n_levels; ++l) ctx->leaf_level_off[l] = h[l];
+  ctx->n_leaves = h[ctx->n_levels];
+  return SM_OK;
+}
+
+extern "C" int sm_build_octree(sm_ctx *ctx, int *n_boxes) {
+  if (!ctx) return SM_EINVAL;
+  if (!ctx->arena) return sm_fail(ctx, SM_ESTATE, "no arena bound");
+  LevelOffsets lo;
+  int n = 0;
+  for (int l = 0; l <= ctx->lbase; ++l) {
+    lo.off[l] = n;
+    n += 1 << (3 * l);
+  }
+  lo.off[ctx->lbase + 1] = n;
+  for (int l = ctx->lbase + 2; l <= SM_MAX_LEVELS; ++l) lo.off[l] = n;
+  if (n > ctx->cfg.max_boxes) return sm_fail(ctx, SM_ENOMEM, "max_boxes %d < %d", ctx->cfg.max_boxes, n);
+  k_build_uniform<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->lbase, lo, ctx->level, ctx->ijk,
+                                                            ctx->morton, ctx->parent, ctx->child);
+  ++ctx->n_launch;
+  SM_CKL("build_uniform");
+  for (int l = 0; l <= ctx->lbase; ++l) {
+    int cnt = (lo.off[l + 1] - lo.off[l]) * 26;
+    k_neighbours<<<(cnt + 255) / 256, 256, 0, ctx->stream>>>(lo.off[l], lo.off[l + 1], l, ctx->ijk,
+                                                             ctx->morton, ctx->nbr, ctx->nbr6);
+    ++ctx->n_launch;
+  }
+  SM_CKL("neighbours");
+  ctx->n_boxes = n;
+  ctx->n_levels = ctx->lbase + 1;
+  for (int l = 0; l <= SM_MAX_LEVELS; ++l) ctx->level_off[l] = lo.off[l];
+  int st = rebuild_leaves(ctx);
+  if (st) return st;
+  if (n_boxes) *n_boxes = n;
+  return SM_OK;
+}
+
+extern "C" int sm_refine_level(sm_ctx *ctx, int level, const int8_t *flags, int *n_new, int *n_dropped) {
+  if (!ctx || !flags) return SM_EINVAL;
+  if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
+  if (level != ctx->n_levels - 1 || level >= ctx->lmax)
+    return sm_fail(ctx, SM_EINVAL, "refine_level(%d): only the finest level %d below %d", level,
+                   ctx->n_levels - 1, ctx->lmax);
+  int lo = ctx->level_off[level], n = ctx->level_off[level + 1] - lo;
+  SM_CK(cudaMemcpyAsync(ctx->dev_flags, flags, n, cudaMemcpyHostToDevice, ctx->stream));
+  SM_CK(cudaMemsetAsync(ctx->dev_count, 0, 4 * sizeof(int32_t), ctx->stream));
+  k_refine_accept<<<(n + 255) / 256, 256, 0, ctx->stream>>>(lo, n, ctx->dev_flags, ctx->nbr, ctx->scan_a,
+                                                            ctx->dev_count);
+  ++ctx->n_launch;
+  k_scan<<<1, 1024, 0, ctx->stream>>>(ctx->scan_a, ctx->scan_b, n);
+  ++ctx->n_launch;
+  SM_CKL("refine accept");
+  int32_t h[2];
+  SM_CK(cudaMemcpyAsync(&h[0], ctx->scan_b + n, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SM_CK(cudaMemcpyAsync(&h[1], ctx->dev_count + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  int accepted = h[0];
+  if (n_dropped) *n_dropped = h[1];
+  if (n_new) *n_new = 8 * accepted;
+  if (accepted == 0) return SM_OK;
+  int new_lo = ctx->n_boxes;
+  if (new_lo + 8 * accepted > ctx->cfg.max_boxes)
+    return sm_fail(ctx, SM_ENOMEM, "max_boxes %d exceeded (%d needed)", ctx->cfg.max_boxes,
+                   new_lo + 8 * accepted);
+  k_make_children<<<(8 * n + 255) / 256, 256, 0, ctx->stream>>>(lo, n, new_lo, level, ctx->scan_a, ctx->scan_b,
+                                                                ctx->level, ctx->ijk, ctx->morton, ctx->parent,
+                                                                ctx->child);
+  ++ctx->n_launch;
+  int hi = new_lo + 8 * accepted;
+  int cnt = (hi - new_lo) * 26;
+  k_neighbours<<<(cnt + 255) / 256, 256, 0, ctx->stream>>>(new_lo, hi, level + 1, ctx->ijk, ctx->morton,
+                                                           ctx->nbr, ctx->nbr6);
+  ++ctx->n_launch;
+  SM_CKL("make children");
+  ctx->n_boxes = hi;
+  ctx->n_levels = level + 2;
+  for (int l = level + 2; l <= SM_MAX_LEVELS; ++l) ctx->level_off[l] = hi;
+  return rebuild_leaves(ctx);
+}
+
+extern "C" int sm_get_tables(const sm_ctx *ctx, sm_tables *out) {
+  if (!ctx || !out) return SM_EINVAL;
+  out->n_boxes = ctx->n_boxes;
+  out->n_levels = ctx->n_levels;
+  out->n_leaves = ctx->n_leaves;
+  for (int l = 0; l <= SM_MAX_LEVELS; ++l) out->level_offset[l] = ctx->level_off[l];
+  out->level = ctx->level;
+  out->ijk = ctx->ijk;
+  out->morton = ctx->morton;
+  out->parent = ctx->parent;
+  out->child = ctx->child;
+  out->nbr = ctx->nbr;
+  out->leaf = ctx->leaf;
+  return SM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fields
+// ---------------------------------------------------------------------------
+static double *var_ptr(const sm_ctx *ctx, int var) {
+  switch (var) {
+    case SM_PHI: return ctx->phi;
+    case SM_RHS: return ctx->rhs;
+    case SM_RES: return ctx->res;
+    case SM_NE: return ctx->nbuf[ctx->ncur];
+    case SM_NI: return ctx->ibuf[ctx->ncur];
+    case SM_EMAG: return ctx->emag;
+    case SM_RHO: return ctx->rho;
+    default: return nullptr;
+  }
+}
+
+extern "C" int sm_var_ptr(const sm_ctx *ctx, int var, void **dev_ptr) {
+  if (!ctx || !dev_ptr || !ctx->arena) return SM_EINVAL;
+  double *p = var_ptr(ctx, var);
+  if (!p) return SM_EINVAL;
+  *dev_ptr = p;
+  return SM_OK;
+}
+
+extern "C" int sm_upload(sm_ctx *ctx, int var, const double *host, int n_boxes) {
+  if (!ctx || !host || !ctx->arena) return SM_EINVAL;
+  double *p = var_ptr(ctx, var);
+  if (!p || n_boxes < 0 || n_boxes > ctx->n_boxes)
+    return sm_fail(ctx, SM_EINVAL, "upload: bad var %d or n_boxes %d", var, n_boxes);
+  SM_CK(cudaMemcpyAsync(p, host, sizeof(double) * CELLS * (size_t)n_boxes, cudaMemcpyHostToDevice,
+                        ctx->stream));
+  return SM_OK;
+}
+
+extern "C" int sm_download(sm_ctx *ctx, int var, double *host, int n_boxes) {
+  if (!ctx || !host || !ctx->arena) return SM_EINVAL;
+  double *p = var_ptr(ctx, var);
+  if (!p || n_boxes < 0 || n_boxes > ctx->n_boxes)
+    return sm_fail(ctx, SM_EINVAL, "download: bad var %d or n_boxes %d", var, n_boxes);
+  SM_CK(cudaMemcpyAsync(host, p, sizeof(double) * CELLS * (size_t)n_boxes, cudaMemcpyDeviceToHost,
+                        ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  return SM_OK;
+}
+
+extern "C" int sm_set_table(sm_ctx *ctx, int n, double e_max, const double *mu, const double *diff,
+                            const double *alpha) {
+  if (!ctx || !mu || !diff || !alpha || n < 2 || n > 4096 || !(e_max > 0.0)) return SM_EINVAL;
+  if (!ctx->arena) return sm_fail(ctx, SM_ESTATE, "no arena bound");
+  SM_CK(cudaMemcpyAsync(ctx->tab, mu, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  SM_CK(cudaMemcpyAsync(ctx->tab + 4096, diff, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  SM_CK(cudaMemcpyAsync(ctx->tab + 8192, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  // the host arrays may be released right after the call
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->tab_n = n;
+  ctx->tab_emax = e_max;
+  return SM_OK;
+}

@@ -1,0 +1,526 @@
+// fluid.cu -- field and drift-diffusion-reaction step (Sec. 2.2-2.4):
+// cell |E| from the potential, Eq. 5 right-hand side, Koren-limited upwind
+// advective flux (Eq. 6-7) plus central diffusive flux with coefficients
+// from a lookup table, refinement-boundary ghosts and flux averaging,
+// forward-Euler stages combined into the explicit trapezoidal (Heun) step,
+// and the time-step limits reduced by block/atomic maxima.
+#include <math.h>
+#include <string.h>
+
+#include "sm_internal.cuh"
+
+using namespace sm;
+
+int sm_mg_solve_internal(sm_ctx *ctx, double tol, int max_cycles, int *cycles);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+// linear interpolation in a table sampled at E_k = k e_max/(n-1), clamped
+__device__ __forceinline__ double lookup(const double *__restrict__ t, int n, double inv_de, double e) {
+  double x = e * inv_de;
+  if (x <= 0.0) return __ldg(t);
+  if (x >= (double)(n - 1)) return __ldg(t + n - 1);
+  int i = (int)x;
+  double w = x - (double)i;
+  double t0 = __ldg(t + i), t1 = __ldg(t + i + 1);
+  return t0 + w * (t1 - t0);
+}
+
+// psi(a/b)*b for the Koren limiter psi(x) = max(0, min(1, (2+x)/6, x)),
+// without the division: 0 when a*b <= 0, else sign(b) min(|b|, (2|b|+|a|)/6, |a|)
+__device__ __forceinline__ double koren(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  double ab = fabs(b), aa = fabs(a);
+  double m = fmin(fmin(ab, (2.0 * ab + aa) * (1.0 / 6.0)), aa);
+  return b > 0.0 ? m : -m;
+}
+
+// Flux through the face between cells L and R (positive toward R):
+// v = -mu(E*) E_face, E* = (|E|_L + |E|_R)/2; advective part by Eq. 7 when
+// v >= 0 and Eq. 6 when v < 0; diffusive part -D(E*) (n_R - n_L)/dx.
+__device__ __forceinline__ double face_flux(double nL2, double nL, double nR, double nR2, double pL, double pR,
+                                            double eL, double eR, double inv_h, const Table &tb) {
+  double e_face = (pL - pR) * inv_h;
+  double e_star = 0.5 * (eL + eR);
+  double mu = lookup(tb.mu, tb.n, tb.inv_de, e_star);
+  double dc = lookup(tb.diff, tb.n, tb.inv_de, e_star);
+  double v = -mu * e_face;
+  double nf = v < 0.0 ? nR - koren(nR2 - nR, nR - nL) : nL + koren(nL - nL2, nR - nL);
+  return v * nf - dc * (nR - nL) * inv_h;
+}
+
+// Density ghost (depth t = 1 or 2) across refinement face f of fine box b
+// at face cell (u,w): linear prolongation (c + c_sx + c_sy + c_sz)/4 of the
+// coarse cell c that contains the ghost, limited to 2c (Sec. 2.3).
+__device__ double density_cf_ghost(const double *__restrict__ n, const int32_t *__restrict__ nbr6,
+                                   const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk, int b,
+                                   int f, int t, int u, int w, unsigned long long *err) {
+  int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  int G[3];
+  G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC - 1 + t : -t);
+  G[t1] = NC * ijk[3 * b + t1] + u;
+  G[t2] = NC * ijk[3 * b + t2] + w;
+  int P = parent[b];
+  int Q = nbr6[6 * P + f];
+  if (Q < 0) {
+    atomicOr(err, 4ull);
+    return 0.0;
+  }
+  int lc[3];
+  for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
+  double c = n[(size_t)Q * CELLS + cidx(lc[0], lc[1], lc[2])];
+  double sum = c;
+  for (int d = 0; d < 3; ++d) {
+    int s = (G[d] & 1) ? 1 : -1;
+    int q[3] = {lc[0], lc[1], lc[2]};
+    q[d] += s;
+    double v;
+    if (q[d] >= 0 && q[d] < NC) {
+      v = n[(size_t)Q * CELLS + cidx(q[0], q[1], q[2])];
+    } else {
+      int Qn = nbr6[6 * Q + 2 * d + (s > 0)];
+      if (Qn >= 0) {
+        q[d] = s > 0 ? 0 : NC - 1;
+        v = n[(size_t)Qn * CELLS + cidx(q[0], q[1], q[2])];
+      } else {
+        if (Qn == -2) atomicOr(err, 8ull);
+        v = c;  // Neumann wall: mirror of c
+      }
+    }
+    sum += v;
+  }
+  double g = 0.25 * sum;
+  return g > 2.0 * c ? 2.0 * c : g;
+}
+
+// |E| ghost at a refinement face: the coarse cell containing the ghost
+__device__ double emag_cf_ghost(const double *__restrict__ em, const int32_t *__restrict__ nbr6,
+                                const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk, int b, int f,
+                                int u, int w) {
+  int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  int G[3];
+  G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
+  G[t1] = NC * ijk[3 * b + t1] + u;
+  G[t2] = NC * ijk[3 * b + t2] + w;
+  int Q = nbr6[6 * parent[b] + f];
+  if (Q < 0) return 0.0;
+  int lc[3];
+  for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
+  return em[(size_t)Q * CELLS + cidx(lc[0], lc[1], lc[2])];
+}
+
+// local cell (i,j,k) of face f at depth dep (0 = next to the face)
+__device__ __forceinline__ void face_loc(int f, int dep, int u, int w, int c[3]) {
+  int a = f >> 1;
+  c[a] = (f & 1) ? NC - 1 - dep : dep;
+  c[(a + 1) % 3] = u;
+  c[(a + 2) % 3] = w;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// |E| on leaf cells: cell component = mean of the two face fields
+// (phi_{i-1} - phi_i)/dx and (phi_i - phi_{i+1})/dx
+__global__ void __launch_bounds__(512) k_field(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
+                                               const double *__restrict__ phi, const double *__restrict__ gh,
+                                               const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
+                                               double *__restrict__ emag) {
+  int b = leaf[blockIdx.x];
+  int t = threadIdx.x;
+  int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
+  double ih = lh.inv_h[level[b]];
+  const double *p = phi + (size_t)b * CELLS;
+  double pc = p[t];
+  double e2 = 0.0;
+  const int stride[3] = {1, NC, FACE};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double pm = c[a] > 0 ? p[t - stride[a]] : pot_ghost(phi, nbr6, gh, b, 2 * a, c[0], c[1], c[2], pc, bc, 0);
+    double pp = c[a] < NC - 1 ? p[t + stride[a]]
+                              : pot_ghost(phi, nbr6, gh, b, 2 * a + 1, c[0], c[1], c[2], pc, bc, 0);
+    double e = 0.5 * ((pm - pc) * ih + (pc - pp) * ih);
+    e2 += e * e;
+  }
+  emag[(size_t)b * CELLS + t] = sqrt(e2);
+}
+
+// Eq. 5 right-hand side on leaf cells
+__global__ void __launch_bounds__(512) k_charge(const int32_t *__restrict__ leaf, const double *__restrict__ ne,
+                                                const double *__restrict__ ni, const double *__restrict__ rho,
+                                                double q, double inv_eps, int use_rho, double *__restrict__ rhs) {
+  size_t x = (size_t)leaf[blockIdx.x] * CELLS + threadIdx.x;
+  rhs[x] = use_rho ? -rho[x] * inv_eps : -q * (ni[x] - ne[x]) * inv_eps;
+}
+
+// per-cell time-step quantities: sum_d mu |E_d|/dx, plus 2*3*D/dx^2, mu n_e
+__device__ __forceinline__ void dt_terms(const double *__restrict__ phi, const double *__restrict__ gh,
+                                         const int32_t *__restrict__ nbr6, const Bc &bc, int b, int t, double ih,
+                                         double em, double ne, const Table &tb, double &adv, double &ad,
+                                         double &drt) {
+  int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
+  const double *p = phi + (size_t)b * CELLS;
+  double pc = p[t];
+  const int stride[3] = {1, NC, FACE};
+  double mu = lookup(tb.mu, tb.n, tb.inv_de, em), dc = lookup(tb.diff, tb.n, tb.inv_de, em);
+  double s = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double pm = c[a] > 0 ? p[t - stride[a]] : pot_ghost(phi, nbr6, gh, b, 2 * a, c[0], c[1], c[2], pc, bc, 0);
+    double pp = c[a] < NC - 1 ? p[t + stride[a]]
+                              : pot_ghost(phi, nbr6, gh, b, 2 * a + 1, c[0], c[1], c[2], pc, bc, 0);
+    double e = 0.5 * ((pm - pc) * ih + (pc - pp) * ih);
+    s += fabs(mu * e);
+  }
+  adv = s * ih;
+  ad = adv + 6.0 * dc * ih * ih;
+  drt = mu * ne;
+}
+
+__global__ void __launch_bounds__(512) k_dt(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
+                                            const double *__restrict__ phi, const double *__restrict__ gh,
+                                            const double *__restrict__ emag, const double *__restrict__ ne,
+                                            const int32_t *__restrict__ nbr6, Bc bc, LevelH lh, Table tb,
+                                            unsigned long long *slots) {
+  __shared__ double red[16];
+  int b = leaf[blockIdx.x];
+  int t = threadIdx.x;
+  size_t x = (size_t)b * CELLS + t;
+  double adv, ad, drt;
+  dt_terms(phi, gh, nbr6, bc, b, t, lh.inv_h[level[b]], emag[x], ne[x], tb, adv, ad, drt);
+  block_max_to(slots + SC_ADV, adv, red);
+  __syncthreads();
+  block_max_to(slots + SC_AD, ad, red);
+  __syncthreads();
+  block_max_to(slots + SC_DRT, drt, red);
+}
+
+// Fine-side fluxes through the refinement faces of leaf boxes (64 threads
+// per leaf box, one per face cell); read by the box itself and averaged by
+// its coarse neighbour, so both sides use the same numbers.
+__global__ void __launch_bounds__(64) k_cf_flux(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
+                                                const double *__restrict__ n, const double *__restrict__ phi,
+                                                const double *__restrict__ gh, const double *__restrict__ emag,
+                                                const int32_t *__restrict__ nbr6,
+                                                const int32_t *__restrict__ parent,
+                                                const int32_t *__restrict__ ijk, LevelH lh, Table tb,
+                                                double *__restrict__ cflux, unsigned long long *err) {
+  int b = leaf[blockIdx.x];
+  int u = threadIdx.x & 7, w = threadIdx.x >> 3;
+  double ih = lh.inv_h[level[b]];
+  size_t base = (size_t)b * CELLS;
+  for (int f = 0; f < 6; ++f) {
+    if (__ldg(nbr6 + 6 * b + f) != -2) continue;
+    int c0[3], c1[3];
+    face_loc(f, 0, u, w, c0);
+    face_loc(f, 1, u, w, c1);
+    int a = f >> 1;
+    double n0 = n[base + cidx(c0[0], c0[1], c0[2])], n1 = n[base + cidx(c1[0], c1[1], c1[2])];
+    double g1 = density_cf_ghost(n, nbr6, parent, ijk, b, f, 1, u, w, err);
+    double g2 = density_cf_ghost(n, nbr6, parent, ijk, b, f, 2, u, w, err);
+    double p0 = phi[base + cidx(c0[0], c0[1], c0[2])];
+    double pg = p0 * (1.0 / 3.0) + (2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + fcell(a, c0[0], c0[1], c0[2])];
+    double e0 = emag[base + cidx(c0[0], c0[1], c0[2])];
+    double eg = emag_cf_ghost(emag, nbr6, parent, ijk, b, f, u, w);
+    double F;
+    if (f & 1) F = face_flux(n1, n0, g1, g2, p0, pg, e0, eg, ih, tb);
+    else F = face_flux(g2, g1, n0, n1, pg, p0, eg, e0, ih, tb);
+    cflux[(size_t)(6 * b + f) * FACE + u + NC * w] = F;
+  }
+}
+
+// Smem layout of one box for the update kernel
+struct UpdSmem {
+  double n[12 * 12 * 12];   // density with 2 ghost layers on faces
+  double p[10 * 10 * 10];   // potential with 1 ghost layer
+  double e[10 * 10 * 10];   // |E| with 1 ghost layer
+  double F[3 * 9 * 64];     // face fluxes [a][m][w][u]
+  double red[16];
+};
+__device__ __forceinline__ int I12(int i, int j, int k) { return (i + 2) + 12 * ((j + 2) + 12 * (k + 2)); }
+__device__ __forceinline__ int I10(int i, int j, int k) { return (i + 1) + 10 * ((j + 1) + 10 * (k + 1)); }
+
+// One forward-Euler stage on a leaf box: dst = src + dt F(src), with
+// F = -div(flux) + alpha mu |E| n_e for electrons and the same source for
+// ions.  heun != 0: dst = (n0 + src + dt F(src))/2.  Also writes the Eq. 5
+// right-hand side from dst, and with want_dt the time-step maxima of src.
+__global__ void __launch_bounds__(512) k_update(
+    const int32_t *__restrict__ leaf, const int32_t *__restrict__ level, const double *__restrict__ ne_src,
+    const double *__restrict__ ni_src, const double *__restrict__ ne0, const double *__restrict__ ni0,
+    double *__restrict__ ne_dst, double *__restrict__ ni_dst, const double *__restrict__ phi,
+    const double *__restrict__ gh, const double *__restrict__ emag, const double *__restrict__ cflux,
+    const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child, const int32_t *__restrict__ parent,
+    const int32_t *__restrict__ ijk, Bc bc, LevelH lh, Table tb, double dt, int heun, double q, double inv_eps,
+    double *__restrict__ rhs, int want_dt, unsigned long long *slots) {
+  extern __shared__ double smraw[];
+  UpdSmem &S = *reinterpret_cast<UpdSmem *>(smraw);
+  int b = leaf[blockIdx.x];
+  int t = threadIdx.x;
+  int l = level[b];
+  double ih = lh.inv_h[l];
+  size_t base = (size_t)b * CELLS;
+  int ci = t & 7, cj = (t >> 3) & 7, ck = t >> 6;
+  S.n[I12(ci, cj, ck)] = ne_src[base + t];
+  S.p[I10(ci, cj, ck)] = phi[base + t];
+  S.e[I10(ci, cj, ck)] = emag[base + t];
+  __syncthreads();
+  // face halos: thread -> (face, face cell)
+  if (t < 6 * FACE) {
+    int f = t >> 6, fc = t & 63;
+    int u = fc & 7, w = fc >> 3;
+    int nb = nbr6[6 * b + f];
+    int c0[3], c1[3], g1[3], g2[3];
+    face_loc(f, 0, u, w, c0);
+    face_loc(f, 1, u, w, c1);
+    face_loc(f, -1, u, w, g1);
+    face_loc(f, -2, u, w, g2);
+    double n0 = S.n[I12(c0[0], c0[1], c0[2])], n1 = S.n[I12(c1[0], c1[1], c1[2])];
+    double p0 = S.p[I10(c0[0], c0[1], c0[2])], e0 = S.e[I10(c0[0], c0[1], c0[2])];
+    double vg1, vg2, pg, eg;
+    if (nb >= 0) {
+      int m0[3], m1[3];
+      face_loc(f ^ 1, 0, u, w, m0);
+      face_loc(f ^ 1, 1, u, w, m1);
+      size_t nbase = (size_t)nb * CELLS;
+      vg1 = ne_src[nbase + cidx(m0[0], m0[1], m0[2])];
+      vg2 = ne_src[nbase + cidx(m1[0], m1[1], m1[2])];
+      pg = phi[nbase + cidx(m0[0], m0[1], m0[2])];
+      eg = child[8 * nb] < 0 ? emag[nbase + cidx(m0[0], m0[1], m0[2])] : 0.0;
+    } else if (nb == -1) {
+      vg1 = n0;
+      vg2 = n1;
+      pg = bc.type[f] ? 2.0 * bc.val[f] - p0 : p0;
+      eg = e0;
+    } else {
+      vg1 = density_cf_ghost(ne_src, nbr6, parent, ijk, b, f, 1, u, w, slots + SC_ERR);
+      vg2 = density_cf_ghost(ne_src, nbr6, parent, ijk, b, f, 2, u, w, slots + SC_ERR);
+      pg = p0 * (1.0 / 3.0) + (2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + fcell(f >> 1, c0[0], c0[1], c0[2])];
+      eg = emag_cf_ghost(emag, nbr6, parent, ijk, b, f, u, w);
+    }
+    S.n[I12(g1[0], g1[1], g1[2])] = vg1;
+    S.n[I12(g2[0], g2[1], g2[2])] = vg2;
+    S.p[I10(g1[0], g1[1], g1[2])] = pg;
+    S.e[I10(g1[0], g1[1], g1[2])] = eg;
+  }
+  __syncthreads();
+  // fluxes: 3 axes x 9 faces x 64
+  for (int x = t; x < 3 * 9 * FACE; x += blockDim.x) {
+    int a = x / (9 * FACE), rem = x % (9 * FACE);
+    int m = rem >> 6, u = rem & 7, w = (rem >> 3) & 7;
+    int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    double F;
+    bool done = false;
+    if (m == 0 || m == NC) {
+      int f = 2 * a + (m == NC);
+      int nb = nbr6[6 * b + f];
+      if (nb == -2) {
+        F = cflux[(size_t)(6 * b + f) * FACE + u + NC * w];
+        done = true;
+      } else if (nb >= 0 && child[8 * nb] >= 0) {
+        // coarse side of a refinement face: mean of the 4 fine fluxes
+        int cidx3[3];
+        cidx3[a] = (f & 1) ? 0 : 1;
+        cidx3[t1] = u >> 2;
+        cidx3[t2] = w >> 2;
+        int ch = child[8 * nb + cidx3[0] + 2 * cidx3[1] + 4 * cidx3[2]];
+        const double *cf = cflux + (size_t)(6 * ch + (f ^ 1)) * FACE;
+        int uf = 2 * (u & 3), wf = 2 * (w & 3);
+        double s = 0.0;
+        s += cf[uf + NC * wf];
+        s += cf[uf + 1 + NC * wf];
+        s += cf[uf + NC * (wf + 1)];
+        s += cf[uf + 1 + NC * (wf + 1)];
+        F = s * 0.25;
+        done = true;
+      }
+    }
+    if (!done) {
+      int c[4][3];
+      for (int s = 0; s < 4; ++s) {
+        c[s][a] = m - 2 + s;
+        c[s][t1] = u;
+        c[s][t2] = w;
+      }
+      F = face_flux(S.n[I12(c[0][0], c[0][1], c[0][2])], S.n[I12(c[1][0], c[1][1], c[1][2])],
+                    S.n[I12(c[2][0], c[2][1], c[2][2])], S.n[I12(c[3][0], c[3][1], c[3][2])],
+                    S.p[I10(c[1][0], c[1][1], c[1][2])], S.p[I10(c[2][0], c[2][1], c[2][2])],
+                    S.e[I10(c[1][0], c[1][1], c[1][2])], S.e[I10(c[2][0], c[2][1], c[2][2])], ih, tb);
+    }
+    S.F[(a * 9 + m) * FACE + u + NC * w] = F;
+  }
+  __syncthreads();
+  // update
+  int c[3] = {ci, cj, ck};
+  double div = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int u = c[(a + 1) % 3], w = c[(a + 2) % 3], m = c[a];
+    div += (S.F[(a * 9 + m + 1) * FACE + u + NC * w] - S.F[(a * 9 + m) * FACE + u + NC * w]) * ih;
+  }
+  double e = S.e[I10(ci, cj, ck)];
+  double nes = S.n[I12(ci, cj, ck)];
+  double src = lookup(tb.alpha, tb.n, tb.inv_de, e) * lookup(tb.mu, tb.n, tb.inv_de, e) * e * nes;
+  double ne_new = nes - dt * div + dt * src;
+  double ni_new = ni_src[base + t] + dt * src;
+  if (heun) {
+    ne_new = 0.5 * (ne0[base + t] + ne_new);
+    ni_new = 0.5 * (ni0[base + t] + ni_new);
+  }
+  ne_dst[base + t] = ne_new;
+  ni_dst[base + t] = ni_new;
+  rhs[base + t] = -q * (ni_new - ne_new) * inv_eps;
+  if (want_dt) {
+    double adv, ad, drt;
+    dt_terms(phi, gh, nbr6, bc, b, t, ih, e, nes, tb, adv, ad, drt);
+    block_max_to(slots + SC_ADV, adv, S.red);
+    __syncthreads();
+    block_max_to(slots + SC_AD, ad, S.red);
+    __syncthreads();
+    block_max_to(slots + SC_DRT, drt, S.red);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+static Table table_of(const sm_ctx *ctx) {
+  Table tb;
+  tb.mu = ctx->tab;
+  tb.diff = ctx->tab + 4096;
+  tb.alpha = ctx->tab + 8192;
+  tb.n = ctx->tab_n;
+  tb.inv_de = (ctx->tab_n - 1) / ctx->tab_emax;
+  return tb;
+}
+
+static int ready(sm_ctx *ctx) {
+  if (!ctx) return SM_EINVAL;
+  if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
+  return SM_OK;
+}
+
+extern "C" int sm_compute_field(sm_ctx *ctx) {
+  int st = ready(ctx);
+  if (st) return st;
+  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+  k_field<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->level, ctx->phi, ctx->gh, ctx->nbr6, ctx->bc,
+                                                  ctx->lh, ctx->emag);
+  ++ctx->n_launch;
+  SM_CKL("field");
+  return SM_OK;
+}
+
+extern "C" int sm_charge_rhs(sm_ctx *ctx, double q, double eps, int use_rho) {
+  int st = ready(ctx);
+  if (st) return st;
+  if (!(eps != 0.0)) return SM_EINVAL;
+  k_charge<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->nbuf[ctx->ncur], ctx->ibuf[ctx->ncur], ctx->rho,
+                                                   q, 1.0 / eps, use_rho, ctx->rhs);
+  ++ctx->n_launch;
+  SM_CKL("charge");
+  return SM_OK;
+}
+
+extern "C" int sm_restrict_densities(sm_ctx *ctx) {
+  int st = ready(ctx);
+  if (st) return st;
+  return sm_restrict_pair(ctx, ctx->nbuf[ctx->ncur], ctx->ibuf[ctx->ncur]);
+}
+
+static int dt_from_slots(sm_ctx *ctx, double q, double eps, double *dt) {
+  SM_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long e;
+  memcpy(&e, &ctx->hscal[SC_ERR], sizeof e);
+  if (e) return sm_fail(ctx, SM_ESTATE, "device consistency check failed (flags 0x%llx)", e);
+  double m_adv = ctx->hscal[SC_ADV], m_ad = ctx->hscal[SC_AD], m_drt = ctx->hscal[SC_DRT];
+  double d = 1e300;
+  if (m_adv > 0.0 && 0.5 / m_adv < d) d = 0.5 / m_adv;
+  if (m_ad > 0.0 && 1.0 / m_ad < d) d = 1.0 / m_ad;
+  if (m_drt > 0.0 && eps / (q * m_drt) < d) d = eps / (q * m_drt);
+  *dt = 0.9 * d;
+  return SM_OK;
+}
+
+extern "C" int sm_dt_limit(sm_ctx *ctx, double q, double eps, double *dt) {
+  int st = ready(ctx);
+  if (st) return st;
+  if (!dt || ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");
+  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_ADV, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  k_dt<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->level, ctx->phi, ctx->gh, ctx->emag,
+                                               ctx->nbuf[ctx->ncur], ctx->nbr6, ctx->bc, ctx->lh, table_of(ctx),
+                                               ctx->dscal);
+  ++ctx->n_launch;
+  SM_CKL("dt");
+  return dt_from_slots(ctx, q, eps, dt);
+}
+
+// one stage from buffer s into buffer d (heun: averaged with buffer h0)
+static int stage(sm_ctx *ctx, int s, int d, int h0, double dt, double q, double eps, int want_dt) {
+  int st;
+  Table tb = table_of(ctx);
+  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+  k_cf_flux<<<ctx->n_leaves, 64, 0, ctx->stream>>>(ctx->leaf, ctx->level, ctx->nbuf[s], ctx->phi, ctx->gh,
+                                                   ctx->emag, ctx->nbr6, ctx->parent, ctx->ijk, ctx->lh, tb,
+                                                   ctx->cflux, ctx->dscal + SC_ERR);
+  ++ctx->n_launch;
+  SM_CKL("cf_flux");
+  size_t smem = sizeof(UpdSmem);
+  k_update<<<ctx->n_leaves, 512, smem, ctx->stream>>>(
+      ctx->leaf, ctx->level, ctx->nbuf[s], ctx->ibuf[s], h0 >= 0 ? ctx->nbuf[h0] : nullptr,
+      h0 >= 0 ? ctx->ibuf[h0] : nullptr, ctx->nbuf[d], ctx->ibuf[d], ctx->phi, ctx->gh, ctx->emag, ctx->cflux,
+      ctx->nbr6, ctx->child, ctx->parent, ctx->ijk, ctx->bc, ctx->lh, tb, dt, h0 >= 0, q, 1.0 / eps, ctx->rhs,
+      want_dt, ctx->dscal);
+  ++ctx->n_launch;
+  SM_CKL("update");
+  return sm_restrict_pair(ctx, ctx->nbuf[d], ctx->ibuf[d]);
+}
+
+extern "C" int sm_fluid_stage(sm_ctx *ctx, double dt) {
+  int st = ready(ctx);
+  if (st) return st;
+  if (ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");
+  int a = ctx->ncur, b = (a + 1) % 3;
+  if ((st = sm_restrict_pair(ctx, ctx->nbuf[a], ctx->ibuf[a]))) return st;
+  // q/eps only feed the right-hand side written alongside; a stage alone
+  // uses SI values
+  if ((st = stage(ctx, a, b, -1, dt, 1.602176634e-19, 8.8541878128e-12, 0))) return st;
+  ctx->ncur = b;
+  return SM_OK;
+}
+
+extern "C" int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol, int max_cycles,
+                                double *dt_next, int *cycles) {
+  int st = ready(ctx);
+  if (st) return st;
+  if (ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");
+  if (!(eps != 0.0) || max_cycles < 1) return SM_EINVAL;
+  int A = ctx->ncur, B = (A + 1) % 3, C = (A + 2) % 3;
+  if ((st = sm_restrict_pair(ctx, ctx->nbuf[A], ctx->ibuf[A]))) return st;
+  // stage 1: n1 = n0 + dt F(n0); new field
+  if ((st = stage(ctx, A, B, -1, dt, q, eps, 0))) return st;
+  int c1 = 0, c2 = 0, st1, st2;
+  st1 = sm_mg_solve(ctx, tol, max_cycles, &c1, nullptr);
+  if (st1 && st1 != SM_ENOCONV) return st1;
+  if ((st = sm_compute_field(ctx))) return st;
+  // stage 2: n = (n0 + n1 + dt F(n1))/2 with the time-step limits at n1
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_ADV, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  if ((st = stage(ctx, B, C, A, dt, q, eps, 1))) return st;
+  ctx->ncur = C;
+  double dtn = 0.0;
+  if ((st = dt_from_slots(ctx, q, eps, &dtn))) return st;
+  st2 = sm_mg_solve(ctx, tol, max_cycles, &c2, nullptr);
+  if (st2 && st2 != SM_ENOCONV) return st2;
+  if ((st = sm_compute_field(ctx))) return st;
+  if (dt_next) *dt_next = dtn;
+  if (cycles) {
+    cycles[0] = c1;
+    cycles[1] = c2;
+  }
+  if (st1 || st2) return sm_fail(ctx, SM_ENOCONV, "a Poisson solve did not reach tol %.3e", tol);
+  return SM_OK;
+}

@@ -1,0 +1,522 @@
+// multigrid.cu -- geometric multigrid for Poisson's equation on the octree
+// (Sec. 2.1.2, Eq. 1 and 5): full approximation scheme V-cycle and full
+// multigrid, red-black Gauss-Seidel smoothing of the 7-point cell-centred
+// Laplacian, 8-child averaging restriction, 4-point linear prolongation,
+// coarse-to-fine ghost interpolation and an exact solve on level 0.
+#include <math.h>
+#include <string.h>
+
+#include "sm_internal.cuh"
+
+using namespace sm;
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// One colour of a Gauss-Seidel red-black sweep over the boxes [lo, lo+grid)
+// of one level: phi = (sum of 6 neighbours - h^2 f)/6 on cells with
+// (i+j+k) % 2 == color (level-global parity; box origins are multiples of
+// 8).  One block of 256 threads per box, one thread per cell of the colour.
+__global__ void __launch_bounds__(256) k_rbgs(int lo, int color, double *__restrict__ phi,
+                                              const double *__restrict__ rhs, const double *__restrict__ gh,
+                                              const int32_t *__restrict__ nbr6, Bc bc, double h2) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int k = t >> 5, j = (t >> 2) & 7;
+  int i = ((t & 3) << 1) | ((j + k + color) & 1);
+  int c = cidx(i, j, k);
+  size_t base = (size_t)b * CELLS;
+  double ctr = phi[base + c];
+  double s = nb_sum(phi, nbr6, gh, b, i, j, k, ctr, bc, 0);
+  phi[base + c] = (s - h2 * rhs[base + c]) * (1.0 / 6.0);
+}
+
+// r = f - L phi on every cell of the boxes [lo, lo+grid)
+__global__ void __launch_bounds__(512) k_residual(int lo, const double *__restrict__ phi,
+                                                  const double *__restrict__ rhs, const double *__restrict__ gh,
+                                                  const int32_t *__restrict__ nbr6, Bc bc, double inv_h2,
+                                                  double *__restrict__ res) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+  size_t base = (size_t)b * CELLS;
+  double p = phi[base + t];
+  double s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, 0);
+  res[base + t] = rhs[base + t] - (s - 6.0 * p) * inv_h2;
+}
+
+// Restriction from the boxes [lo, lo+grid) of level l to their parents:
+// each child box fills its 4^3 block of parent cells with the average of
+// the 8 fine cells, for phi (into phi) and for the residual (into rhs,
+// completed to the FAS right-hand side by k_fas).  64 threads per child.
+__global__ void __launch_bounds__(64) k_restrict_fas(int lo, const int32_t *__restrict__ parent,
+                                                     const int32_t *__restrict__ ijk, double *__restrict__ phi,
+                                                     const double *__restrict__ res, double *__restrict__ rhs) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
+  int P = parent[b];
+  int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
+  size_t fb = (size_t)b * CELLS;
+  double sp = 0.0, sr = 0.0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        sp += phi[fb + c];
+        sr += res[fb + c];
+      }
+  size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
+  phi[cc] = sp * 0.125;
+  rhs[cc] = sr * 0.125;
+}
+
+// plain 8-child average of one variable (FMG right-hand side, densities)
+__global__ void __launch_bounds__(64) k_restrict1(int lo, const int32_t *__restrict__ parent,
+                                                  const int32_t *__restrict__ ijk, double *__restrict__ a,
+                                                  double *__restrict__ a2) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
+  int P = parent[b];
+  int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
+  size_t fb = (size_t)b * CELLS;
+  double s = 0.0, s2 = 0.0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        s += a[fb + c];
+        if (a2) s2 += a2[fb + c];
+      }
+  size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
+  a[cc] = s * 0.125;
+  if (a2) a2[cc] = s2 * 0.125;
+}
+
+// After restriction into level l-1 (boxes [lo, lo+grid)): keep a copy of
+// phi, and on refined boxes complete the FAS right-hand side
+// f = avg(r_fine) + L phi_restricted.
+__global__ void __launch_bounds__(512) k_fas(int lo, double *__restrict__ phi, double *__restrict__ old,
+                                             double *__restrict__ rhs, const double *__restrict__ gh,
+                                             const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child,
+                                             Bc bc, double inv_h2) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  size_t base = (size_t)b * CELLS;
+  double p = phi[base + t];
+  old[base + t] = p;
+  if (child[8 * b] < 0) return;
+  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+  double s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, 0);
+  rhs[base + t] += (s - 6.0 * p) * inv_h2;
+}
+
+// value of a coarse-level quantity at local cell q of box Q, where q may
+// leave the box by one step along axis e (sign s): the neighbour box of the
+// same level, or the physical-boundary ghost of the cell `ctr` it left.
+template <typename F>
+__device__ __forceinline__ double coarse_at(F val, const int32_t *__restrict__ nbr6, int Q, int q[3], int e,
+                                            int s, double ctr, const Bc &bc, int homog,
+                                            unsigned long long *err) {
+  if (q[e] >= 0 && q[e] < NC) return val(Q, cidx(q[0], q[1], q[2]));
+  int f = 2 * e + (s > 0);
+  int Qn = __ldg(nbr6 + 6 * Q + f);
+  if (Qn >= 0) {
+    q[e] = s > 0 ? 0 : NC - 1;
+    return val(Qn, cidx(q[0], q[1], q[2]));
+  }
+  if (Qn == -1) {
+    if (bc.type[f]) return (homog ? 0.0 : 2.0 * bc.val[f]) - ctr;
+    return ctr;
+  }
+  atomicOr(err, 1ull);  // nesting violated: no coarse box where one must be
+  return ctr;
+}
+
+// Coarse interpolation values for the refinement-boundary faces of the
+// boxes [lo, lo+grid): phihat = c/2 + c_t1/4 + c_t2/4 (c the level l-1 cell
+// containing the ghost, t1/t2 its tangential neighbours on the ghost's
+// side).  64 threads per box, one per face cell.
+__global__ void __launch_bounds__(64) k_fill_cf(int lo, const double *__restrict__ v, double *__restrict__ gh,
+                                                const int32_t *__restrict__ nbr6,
+                                                const int32_t *__restrict__ parent,
+                                                const int32_t *__restrict__ ijk, Bc bc, int homog,
+                                                unsigned long long *err) {
+  int b = lo + blockIdx.x;
+  int u = threadIdx.x & 7, w = threadIdx.x >> 3;
+  auto val = [&](int Q, int c) { return v[(size_t)Q * CELLS + c]; };
+  for (int f = 0; f < 6; ++f) {
+    if (__ldg(nbr6 + 6 * b + f) != -2) continue;
+    int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    int G[3];
+    G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
+    G[t1] = NC * ijk[3 * b + t1] + u;
+    G[t2] = NC * ijk[3 * b + t2] + w;
+    int P = parent[b];
+    int Q = nbr6[6 * P + f];
+    if (Q < 0) {
+      atomicOr(err, 2ull);
+      continue;
+    }
+    int lc[3];
+    for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
+    double c = val(Q, cidx(lc[0], lc[1], lc[2]));
+    double ph = 0.5 * c;
+    int ts[2] = {t1, t2};
+    for (int e2 = 0; e2 < 2; ++e2) {
+      int e = ts[e2];
+      int s = (G[e] & 1) ? 1 : -1;
+      int q[3] = {lc[0], lc[1], lc[2]};
+      q[e] += s;
+      ph += 0.25 * coarse_at(val, nbr6, Q, q, e, s, c, bc, homog, err);
+    }
+    gh[(size_t)(6 * b + f) * FACE + u + NC * w] = ph;
+  }
+}
+
+// Prolongation into the boxes [lo, lo+grid) of level l: per fine cell
+// (c + c_sx + c_sy + c_sz)/4 of the parent cell c and its neighbours toward
+// the fine cell.  mode 0: add the correction (phi - old) of level l-1 with
+// homogeneous boundary ghosts; mode 1: overwrite with the prolonged
+// solution (FMG).
+__global__ void __launch_bounds__(512) k_prolong(int lo, int mode, double *__restrict__ phi,
+                                                 const double *__restrict__ old,
+                                                 const int32_t *__restrict__ nbr6,
+                                                 const int32_t *__restrict__ parent,
+                                                 const int32_t *__restrict__ ijk, Bc bc,
+                                                 unsigned long long *err) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int loc[3] = {t & 7, (t >> 3) & 7, t >> 6};
+  int P = parent[b];
+  int G[3], lc[3];
+  for (int d = 0; d < 3; ++d) {
+    G[d] = NC * ijk[3 * b + d] + loc[d];
+    lc[d] = (G[d] >> 1) - NC * ijk[3 * P + d];
+  }
+  auto val = [&](int Q, int c) {
+    size_t x = (size_t)Q * CELLS + c;
+    return mode ? phi[x] : phi[x] - old[x];
+  };
+  double c0 = val(P, cidx(lc[0], lc[1], lc[2]));
+  double sum = c0;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    int s = (G[e] & 1) ? 1 : -1;
+    int q[3] = {lc[0], lc[1], lc[2]};
+    q[e] += s;
+    sum += coarse_at(val, nbr6, P, q, e, s, c0, bc, mode ? 0 : 1, err);
+  }
+  size_t x = (size_t)b * CELLS + t;
+  if (mode) phi[x] = 0.25 * sum;
+  else phi[x] += 0.25 * sum;
+}
+
+// Orthonormal eigenvectors and (h^2-scaled) eigenvalues of the 1-D
+// cell-centred 3-point operator on n cells with Neumann (ghost = inner) or
+// Dirichlet (ghost = -inner) ends: cosine (NN), sine (DD) and quarter-wave
+// sine (DN, ND) families.  basis[a*64 + i*8 + m] = component i of vector m.
+__global__ void k_coarse_basis(double *basis, Bc bc, int n) {
+  int t = threadIdx.x;
+  if (t >= 3 * n) return;
+  int a = t / n, m = t % n;
+  int lo = bc.type[2 * a], hi = bc.type[2 * a + 1];
+  double v[NC], nrm = 0.0, mu;
+  for (int i = 0; i < n; ++i) {
+    double x = (i + 0.5) / n;
+    if (!lo && !hi) v[i] = cospi(m * x);
+    else if (lo && hi) v[i] = sinpi((m + 1) * x);
+    else if (lo) v[i] = sinpi((m + 0.5) * x);
+    else v[i] = sinpi((m + 0.5) * (n - i - 0.5) / n);
+    nrm += v[i] * v[i];
+  }
+  double th = (!lo && !hi) ? m : ((lo && hi) ? m + 1 : m + 0.5);
+  double sn = sinpi(th / (2.0 * n));
+  mu = -4.0 * sn * sn;
+  nrm = rsqrt(nrm);
+  for (int i = 0; i < n; ++i) basis[a * 64 + i * 8 + m] = v[i] * nrm;
+  basis[192 + a * 8 + m] = mu;
+}
+
+// Exact solve on level 0 (one 8^3 box): fold the Dirichlet boundary values
+// into the right-hand side, transform to the separable eigenbasis, divide
+// by the eigenvalues of the 7-point operator, transform back.
+__global__ void __launch_bounds__(512) k_coarse_solve(double *__restrict__ phi, const double *__restrict__ rhs,
+                                                      const double *__restrict__ basis, Bc bc, double h2,
+                                                      double inv_h2) {
+  __shared__ double x[CELLS], y[CELLS], V[3][64], lam[3][8];
+  int t = threadIdx.x;
+  if (t < 192) V[t / 64][t % 64] = basis[t];
+  if (t < 24) lam[t / 8][t % 8] = basis[192 + t];
+  int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
+  double r = rhs[t];
+  for (int f = 0; f < 6; ++f) {
+    int q = c[f >> 1] + ((f & 1) ? 1 : -1);
+    if ((q < 0 || q >= NC) && bc.type[f]) r -= 2.0 * bc.val[f] * inv_h2;
+  }
+  x[t] = r;
+  __syncthreads();
+  // forward: coefficients along x, then y, then z
+  double acc = 0.0;
+  for (int m = 0; m < NC; ++m) acc += V[0][m * 8 + c[0]] * x[cidx(m, c[1], c[2])];
+  y[t] = acc;
+  __syncthreads();
+  acc = 0.0;
+  for (int m = 0; m < NC; ++m) acc += V[1][m * 8 + c[1]] * y[cidx(c[0], m, c[2])];
+  x[t] = acc;
+  __syncthreads();
+  acc = 0.0;
+  for (int m = 0; m < NC; ++m) acc += V[2][m * 8 + c[2]] * x[cidx(c[0], c[1], m)];
+  y[t] = acc * h2 / (lam[0][c[0]] + lam[1][c[1]] + lam[2][c[2]]);
+  __syncthreads();
+  // backward
+  acc = 0.0;
+  for (int m = 0; m < NC; ++m) acc += V[0][c[0] * 8 + m] * y[cidx(m, c[1], c[2])];
+  x[t] = acc;
+  __syncthreads();
+  acc = 0.0;
+  for (int m = 0; m < NC; ++m) acc += V[1][c[1] * 8 + m] * x[cidx(c[0], m, c[2])];
+  y[t] = acc;
+  __syncthreads();
+  acc = 0.0;
+  for (int m = 0; m < NC; ++m) acc += V[2][c[2] * 8 + m] * y[cidx(c[0], c[1], m)];
+  phi[t] = acc;
+}
+
+// max over leaf cells of |f - L v| into *slot (one block per leaf box)
+__global__ void __launch_bounds__(512) k_resnorm(const int32_t *__restrict__ leaf,
+                                                 const int32_t *__restrict__ level,
+                                                 const double *__restrict__ v, const double *__restrict__ rhs,
+                                                 const double *__restrict__ gh,
+                                                 const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
+                                                 unsigned long long *slot) {
+  __shared__ double red[16];
+  int b = leaf[blockIdx.x];
+  int t = threadIdx.x;
+  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+  size_t base = (size_t)b * CELLS;
+  double p = v[base + t];
+  double s = nb_sum(v, nbr6, gh, b, i, j, k, p, bc, 0);
+  double r = rhs[base + t] - (s - 6.0 * p) * lh.inv_h2[level[b]];
+  block_max_to(slot, fabs(r), red);
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+static int lvl_n(const sm_ctx *ctx, int l) { return ctx->level_off[l + 1] - ctx->level_off[l]; }
+
+int sm_mg_fill_cf(sm_ctx *ctx, double *var, int l, int homog) {
+  if (l <= ctx->lbase || l >= ctx->n_levels) return SM_OK;  // uniform levels: no refinement faces
+  int n = lvl_n(ctx, l);
+  if (n == 0) return SM_OK;
+  k_fill_cf<<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], var, ctx->gh, ctx->nbr6, ctx->parent, ctx->ijk,
+                                       ctx->bc, homog, ctx->dscal + SC_ERR);
+  ++ctx->n_launch;
+  SM_CKL("fill_cf");
+  return SM_OK;
+}
+
+int sm_fill_all_cf(sm_ctx *ctx, double *var) {
+  for (int l = ctx->lbase + 1; l < ctx->n_levels; ++l) {
+    int st = sm_mg_fill_cf(ctx, var, l, 0);
+    if (st) return st;
+  }
+  return SM_OK;
+}
+
+// a = avg8 of children (and a2 likewise), finest level first
+int sm_restrict_pair(sm_ctx *ctx, double *a, double *a2) {
+  for (int l = ctx->n_levels - 1; l >= 1; --l) {
+    int n = lvl_n(ctx, l);
+    if (!n) continue;
+    k_restrict1<<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], ctx->parent, ctx->ijk, a, a2);
+    ++ctx->n_launch;
+  }
+  SM_CKL("restrict");
+  return SM_OK;
+}
+
+static int smooth(sm_ctx *ctx, int l, int nu) {
+  int n = lvl_n(ctx, l);
+  if (!n) return SM_OK;
+  for (int s = 0; s < nu; ++s)
+    for (int color = 0; color < 2; ++color) {
+      cudaEvent_t ev;
+      int st = sm_prof_begin(ctx, K_SMOOTH, &ev);
+      if (st) return st;
+      k_rbgs<<<n, 256, 0, ctx->stream>>>(ctx->level_off[l], color, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6,
+                                         ctx->bc, ctx->lh.h2[l]);
+      ++ctx->n_launch;
+      // algorithmic bytes of one colour pass: read phi of all cells (the
+      // neighbours), f of the colour, write phi of the colour
+      st = sm_prof_end(ctx, K_SMOOTH, &ev, (double)n * CELLS * (8.0 + 4.0 + 4.0));
+      if (st) return st;
+    }
+  SM_CKL("rbgs");
+  return SM_OK;
+}
+
+static int coarse_solve(sm_ctx *ctx) {
+  if (!ctx->basis_ready) {
+    k_coarse_basis<<<1, 32, 0, ctx->stream>>>(ctx->basis, ctx->bc, NC);
+    ++ctx->n_launch;
+    ctx->basis_ready = true;
+  }
+  k_coarse_solve<<<1, 512, 0, ctx->stream>>>(ctx->phi, ctx->rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
+                                             ctx->lh.inv_h2[0]);
+  ++ctx->n_launch;
+  SM_CKL("coarse solve");
+  return SM_OK;
+}
+
+// FAS V-cycle with `top` as finest level
+static int vcycle(sm_ctx *ctx, int top) {
+  int st;
+  const int nu1 = ctx->cfg.nu1, nu2 = ctx->cfg.nu2;
+  for (int l = top; l >= 1; --l) {
+    int n = lvl_n(ctx, l);
+    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l, 0))) return st;
+    if ((st = smooth(ctx, l, nu1))) return st;
+    k_residual<<<n, 512, 0, ctx->stream>>>(ctx->level_off[l], ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6, ctx->bc,
+                                           ctx->lh.inv_h2[l], ctx->res);
+    ++ctx->n_launch;
+    k_restrict_fas<<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], ctx->parent, ctx->ijk, ctx->phi, ctx->res,
+                                              ctx->rhs);
+    ++ctx->n_launch;
+    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l - 1, 0))) return st;
+    k_fas<<<lvl_n(ctx, l - 1), 512, 0, ctx->stream>>>(ctx->level_off[l - 1], ctx->phi, ctx->old, ctx->rhs,
+                                                      ctx->gh, ctx->nbr6, ctx->child, ctx->bc,
+                                                      ctx->lh.inv_h2[l - 1]);
+    ++ctx->n_launch;
+    SM_CKL("vcycle down");
+  }
+  if ((st = coarse_solve(ctx))) return st;
+  for (int l = 1; l <= top; ++l) {
+    int n = lvl_n(ctx, l);
+    k_prolong<<<n, 512, 0, ctx->stream>>>(ctx->level_off[l], 0, ctx->phi, ctx->old, ctx->nbr6, ctx->parent,
+                                          ctx->ijk, ctx->bc, ctx->dscal + SC_ERR);
+    ++ctx->n_launch;
+    SM_CKL("prolong");
+    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l, 0))) return st;
+    if ((st = smooth(ctx, l, nu2))) return st;
+  }
+  return SM_OK;
+}
+
+// max_leaf |f - L v| into slot (v's refinement ghosts must be current)
+static int leaf_norm(sm_ctx *ctx, double *v, int slot) {
+  SM_CK(cudaMemsetAsync(ctx->dscal + slot, 0, sizeof(unsigned long long), ctx->stream));
+  k_resnorm<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->level, v, ctx->rhs, ctx->gh, ctx->nbr6,
+                                                    ctx->bc, ctx->lh, ctx->dscal + slot);
+  ++ctx->n_launch;
+  SM_CKL("resnorm");
+  return SM_OK;
+}
+
+static int read_scalars(sm_ctx *ctx) {
+  SM_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long e;
+  memcpy(&e, &ctx->hscal[SC_ERR], sizeof e);
+  if (e) return sm_fail(ctx, SM_ESTATE, "device consistency check failed (flags 0x%llx)", e);
+  return SM_OK;
+}
+
+// denominator of the relative residual: max_leaf |f - L 0| (uses old as 0)
+static int residual_denominator(sm_ctx *ctx) {
+  int st;
+  SM_CK(cudaMemsetAsync(ctx->old, 0, sizeof(double) * CELLS * (size_t)ctx->n_boxes, ctx->stream));
+  if ((st = sm_fill_all_cf(ctx, ctx->old))) return st;
+  if ((st = leaf_norm(ctx, ctx->old, SC_DEN))) return st;
+  return SM_OK;
+}
+
+static int rel_residual(sm_ctx *ctx, double *rel) {
+  int st;
+  if ((st = leaf_norm(ctx, ctx->phi, SC_NORM))) return st;
+  if ((st = read_scalars(ctx))) return st;
+  double num = ctx->hscal[SC_NORM], den = ctx->hscal[SC_DEN];
+  *rel = den > 0.0 ? num / den : num;
+  return SM_OK;
+}
+
+static int check_ready(sm_ctx *ctx) {
+  if (!ctx) return SM_EINVAL;
+  if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
+  return SM_OK;
+}
+
+extern "C" int sm_fill_ghosts(sm_ctx *ctx, int var, int level) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (var != SM_PHI || level < 0 || level >= ctx->n_levels) return SM_EINVAL;
+  return sm_mg_fill_cf(ctx, ctx->phi, level, 0);
+}
+
+extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (n_cycles < 0) return SM_EINVAL;
+  if ((st = residual_denominator(ctx))) return st;
+  for (int c = 0; c < n_cycles; ++c)
+    if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
+  double rel = 0.0;
+  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+  if ((st = rel_residual(ctx, &rel))) return st;
+  if (rel_res) *rel_res = rel;
+  return SM_OK;
+}
+
+extern "C" int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (max_cycles < 1) return SM_EINVAL;
+  if ((st = residual_denominator(ctx))) return st;
+  int c = 0;
+  double rel = 0.0;
+  do {
+    if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
+    ++c;
+    if ((st = rel_residual(ctx, &rel))) return st;
+  } while (rel > tol && c < max_cycles);
+  if (cycles) *cycles = c;
+  if (rel_res) *rel_res = rel;
+  return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
+}
+
+extern "C" int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (max_cycles < 1) return SM_EINVAL;
+  if ((st = residual_denominator(ctx))) return st;
+  int top = ctx->n_levels - 1;
+  if ((st = sm_restrict_pair(ctx, ctx->rhs, nullptr))) return st;
+  if ((st = coarse_solve(ctx))) return st;
+  for (int l = 1; l <= top; ++l) {
+    k_prolong<<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], 1, ctx->phi, ctx->old, ctx->nbr6,
+                                                      ctx->parent, ctx->ijk, ctx->bc, ctx->dscal + SC_ERR);
+    ++ctx->n_launch;
+    SM_CKL("fmg prolong");
+    if ((st = vcycle(ctx, l))) return st;
+  }
+  int c = 1;
+  double rel = 0.0;
+  if ((st = rel_residual(ctx, &rel))) return st;
+  while (rel > tol && c < max_cycles) {
+    if ((st = vcycle(ctx, top))) return st;
+    ++c;
+    if ((st = rel_residual(ctx, &rel))) return st;
+  }
+  if (cycles) *cycles = c;
+  if (rel_res) *rel_res = rel;
+  return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
+}

@@ -1,0 +1,218 @@
+// sm_internal.cuh -- context layout and device helpers shared by the CUDA
+// translation units of the library (octree, multigrid, fluid).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sm_streamer.h"
+
+namespace sm {
+
+constexpr int NC = SM_BOX;         // cells per box side (Sec. 2.1.1)
+constexpr int CELLS = NC * NC * NC;
+constexpr int FACE = NC * NC;
+constexpr int MAXL = SM_MAX_LEVELS;
+
+// physical boundary description, passed by value to kernels
+struct Bc {
+  int type[6];      // 0 Neumann zero, 1 Dirichlet
+  double val[6];
+};
+
+// per-level grid spacing tables, passed by value to kernels
+struct LevelH {
+  double h[MAXL], inv_h[MAXL], h2[MAXL], inv_h2[MAXL];
+};
+
+// transport-coefficient lookup table (device arrays)
+struct Table {
+  const double *mu, *diff, *alpha;
+  int n;
+  double inv_de;    // (n-1)/e_max
+};
+
+// kernel classes for event timing
+enum KClass { K_SMOOTH = 0, K_NCLASS = 1 };
+
+// one timed launch: events around it, its class and algorithmic bytes
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kclass;
+  double bytes;
+};
+
+}  // namespace sm
+
+struct sm_ctx {
+  sm_config cfg;
+  sm_domain dom;
+  int lbase = 0, lmax = 0;       // base level, finest allowed level
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  sm::Bc bc;
+  sm::LevelH lh;
+
+  // arena
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+
+  // tables (device)
+  int32_t *level = nullptr, *ijk = nullptr, *parent = nullptr, *child = nullptr,
+          *nbr = nullptr, *nbr6 = nullptr, *leaf = nullptr;
+  uint64_t *morton = nullptr;
+  int32_t *scan_a = nullptr, *scan_b = nullptr;  // [max_boxes] build scratch
+  int32_t *dev_count = nullptr;                   // small device counters
+  int8_t *dev_flags = nullptr;
+
+  // fields (device) [max_boxes][512]
+  double *phi = nullptr, *rhs = nullptr, *res = nullptr, *old = nullptr,
+         *rho = nullptr, *emag = nullptr;
+  double *nbuf[3] = {nullptr, nullptr, nullptr};  // electron density buffers
+  double *ibuf[3] = {nullptr, nullptr, nullptr};  // ion density buffers
+  int ncur = 0;                                   // current density buffer
+  double *gh = nullptr;      // [max_boxes][6][64] coarse interpolation values
+  double *cflux = nullptr;   // [max_boxes][6][64] fine-side refinement fluxes
+  double *basis = nullptr;   // level-0 eigenbasis: [3][64] vectors, [3][8] eigenvalues
+  double *tab = nullptr;     // [3][4096] coefficient table
+  unsigned long long *dscal = nullptr;  // device scalars (max reductions, flags)
+  int tab_n = 0;
+  double tab_emax = 0.0;
+
+  // host mirrors
+  int n_boxes = 0, n_levels = 0, n_leaves = 0;
+  int level_off[SM_MAX_LEVELS + 1] = {0};
+  int leaf_level_off[SM_MAX_LEVELS + 1] = {0};
+  double *hscal = nullptr;   // pinned host scalars
+  bool basis_ready = false;
+  double den = 0.0;          // residual norm of phi == 0 (current rhs)
+
+  // kernels launched so far (diagnostics)
+  long long n_launch = 0;
+
+  // profiling
+  bool prof = false;
+  double prof_ms[sm::K_NCLASS] = {0};
+  long long prof_n[sm::K_NCLASS] = {0};
+  double prof_bytes[sm::K_NCLASS] = {0};
+  std::vector<sm::ProfRec> prof_recs;
+
+  std::string err;
+};
+
+// ----------------------------------------------------------------------
+// host helpers
+// ----------------------------------------------------------------------
+int sm_fail(sm_ctx *ctx, int code, const char *fmt, ...);
+int sm_cuda_check(sm_ctx *ctx, cudaError_t e, const char *what);
+#define SM_CK(call)                                                   \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return sm_cuda_check(ctx, e_, #call);      \
+  } while (0)
+#define SM_CKL(what)                                                  \
+  do {                                                                \
+    cudaError_t e_ = cudaGetLastError();                              \
+    if (e_ != cudaSuccess) return sm_cuda_check(ctx, e_, what);       \
+  } while (0)
+
+// device scalar slots (unsigned long long each)
+enum {
+  SC_NORM = 0,      // residual max (double bits)
+  SC_DEN = 1,       // residual max of phi == 0
+  SC_ADV = 2,       // dt: max sum |v|/dx
+  SC_AD = 3,        // dt: max adv + 6 D/dx^2
+  SC_DRT = 4,       // dt: max mu n_e
+  SC_ERR = 5,       // consistency error flag
+  SC_COUNT = 6,     // generic counter
+  SC_N = 16
+};
+
+namespace sm {
+
+// ----------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------
+__device__ __forceinline__ int cidx(int i, int j, int k) { return i + NC * j + FACE * k; }
+
+// index of a cell within a face of axis a: tangential coordinates
+// u along (a+1)%3 and w along (a+2)%3
+__device__ __forceinline__ int fcell(int a, int i, int j, int k) {
+  return a == 0 ? (j + NC * k) : (a == 1 ? (k + NC * i) : (i + NC * j));
+}
+
+// atomic max of a non-negative double through its bit pattern
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *slot, double v) {
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// block-wide max (blockDim.x multiple of 32, <= 1024) pushed to a slot
+__device__ __forceinline__ void block_max_to(unsigned long long *slot, double v, double *red) {
+  v = warp_max(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    double x = lane < nw ? red[lane] : 0.0;
+    x = warp_max(x);
+    if (lane == 0) atomic_max_pos(slot, x);
+  }
+}
+
+// Ghost value of a potential-type variable across face f of box b next to
+// interior cell (i,j,k) holding `inner`: same-level neighbour cell, physical
+// boundary (Dirichlet 2g - inner or -inner when homogeneous; Neumann
+// inner), or refinement boundary inner/3 + 2 phihat/3 with the stored
+// coarse interpolation phihat.
+template <typename T>
+__device__ __forceinline__ T pot_ghost(const T *__restrict__ v, const int32_t *__restrict__ nbr6,
+                                       const T *__restrict__ gh, int b, int f, int i, int j, int k,
+                                       T inner, const Bc &bc, int homog) {
+  int nb = __ldg(nbr6 + 6 * b + f);
+  int a = f >> 1;
+  if (nb >= 0) {
+    int c[3] = {i, j, k};
+    c[a] = (f & 1) ? 0 : NC - 1;
+    return v[(size_t)nb * CELLS + cidx(c[0], c[1], c[2])];
+  }
+  if (nb == -1) {
+    if (bc.type[f]) return (homog ? T(0) : T(2.0 * bc.val[f])) - inner;
+    return inner;
+  }
+  return inner * T(1.0 / 3.0) + T(2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + fcell(a, i, j, k)];
+}
+
+// sum of the six neighbours of cell (i,j,k) of box b (ghosts as above)
+template <typename T>
+__device__ __forceinline__ T nb_sum(const T *__restrict__ v, const int32_t *__restrict__ nbr6,
+                                    const T *__restrict__ gh, int b, int i, int j, int k, T ctr,
+                                    const Bc &bc, int homog) {
+  const T *p = v + (size_t)b * CELLS;
+  int c = cidx(i, j, k);
+  T s = (i > 0) ? p[c - 1] : pot_ghost(v, nbr6, gh, b, 0, i, j, k, ctr, bc, homog);
+  s += (i < NC - 1) ? p[c + 1] : pot_ghost(v, nbr6, gh, b, 1, i, j, k, ctr, bc, homog);
+  s += (j > 0) ? p[c - NC] : pot_ghost(v, nbr6, gh, b, 2, i, j, k, ctr, bc, homog);
+  s += (j < NC - 1) ? p[c + NC] : pot_ghost(v, nbr6, gh, b, 3, i, j, k, ctr, bc, homog);
+  s += (k > 0) ? p[c - FACE] : pot_ghost(v, nbr6, gh, b, 4, i, j, k, ctr, bc, homog);
+  s += (k < NC - 1) ? p[c + FACE] : pot_ghost(v, nbr6, gh, b, 5, i, j, k, ctr, bc, homog);
+  return s;
+}
+
+}  // namespace sm
+
+// entry points implemented in the other translation units
+int sm_mg_fill_cf(sm_ctx *ctx, double *var, int level, int homog);
+int sm_fill_all_cf(sm_ctx *ctx, double *var);
+int sm_restrict_pair(sm_ctx *ctx, double *a, double *b);
+int sm_prof_begin(sm_ctx *ctx, int kclass, cudaEvent_t *ev);
+int sm_prof_end(sm_ctx *ctx, int kclass, cudaEvent_t *ev, double bytes);

@@ -1,0 +1,237 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+Tables: bit-exact.  FP64 potential and field: max |gpu - oracle| <= 1e-12 x
+max |oracle| (the FP64 tolerance of the method's solve).  Densities after a
+fluid stage or Heun step: same 1e-12 relative bound (FP64 throughout; the
+two sides differ only in rounding order and fused multiply-adds).
+Cycle counts to a tolerance must agree exactly (max-norm residuals).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import EPS0, Q, gpu_mesh, load_inputs, pair, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def pkg():
+    import paper_1708_08434_gb300 as p
+    return p
+
+
+TABLE_KEYS = ("level", "ijk", "morton", "parent", "child", "nbr")
+
+
+def assert_tables_equal(o, g):
+    to, tg = o.tables(), g.tables()
+    for k in TABLE_KEYS:
+        assert to[k].shape == tg[k].shape, k
+        assert np.array_equal(to[k], tg[k]), k
+    assert np.array_equal(to["level_offset"], tg["level_offset"])
+    leaf = np.where(to["child"][:, 0] < 0)[0]
+    assert np.array_equal(leaf, tg["leaf"])
+    return to
+
+
+@pytest.mark.parametrize("name", ["uniform64", "streamer_small", "streamer6"])
+def test_tables_bit_exact(name):
+    dom, st, o, g = pair(name)
+    assert_tables_equal(o, g)
+    if st is not None:
+        assert o.dropped == g.dropped
+
+
+def test_tables_nesting_drop_and_empty_refinement():
+    dom = synth.Domain(length=1.0, nb=2, max_level=3)
+    o = oracle.Oracle(dom)
+    g = gpu_mesh(dom)
+    f1 = np.zeros(8, np.int8)
+    f1[0] = 1
+    assert o.refine_level(1, f1) == g.refine_level(1, f1) == 8
+    lo, hi = o.level_range(2)
+    f2 = np.zeros(hi - lo, np.int8)
+    ijk2 = o.level_ijk(2)
+    for b, q in enumerate(map(tuple, ijk2)):
+        if q in ((1, 1, 1), (0, 0, 0)):
+            f2[b] = 1
+    o.refine_level(2, f2)
+    g.refine_level(2, f2)
+    assert o.dropped == g.dropped == 1
+    assert_tables_equal(o, g)
+    # a request list with nothing to refine leaves the octree unchanged
+    lo, hi = o.level_range(3)
+    z = np.zeros(hi - lo, np.int8)
+    assert o.refine_level(3, z) == 0 and g.refine_level(3, z) == 0
+    assert_tables_equal(o, g)
+
+
+@pytest.mark.parametrize("name", ["uniform64", "streamer_small"])
+def test_fmg_fixed_cycles_and_tolerance(name):
+    dom, st, o, g = pair(name)
+    t = assert_tables_equal(o, g)
+    load_inputs(dom, st, o, g, t)
+    # identical work: FMG plus 2 more cycles regardless of tolerance
+    so = o.fmg(0.0, 3)
+    sg = g.fmg(0.0, 3)
+    assert so[2] == sg[2] == 3
+    p = pkg()
+    po, pg = o.get(oracle.PHI), g.download(p.PHI)
+    assert rel_err(pg, po) <= TOL
+    assert abs(so[1] - sg[1]) <= 1e-6 * so[1]
+    # same stopping decision to a tolerance from a warm start
+    ro = o.solve(1e-10, 30)
+    rg = g.solve(1e-10, 30)
+    assert ro[0] == rg[0] == 0 and ro[2] == rg[2]
+    assert rel_err(g.download(p.PHI), o.get(oracle.PHI)) <= TOL
+
+
+def test_vcycle_residual_history_matches():
+    dom, st, o, g = pair("streamer_small")
+    load_inputs(dom, st, o, g)
+    for _ in range(4):
+        ro = o.vcycles(1)
+        rg = g.vcycles(1)
+        assert rg == pytest.approx(ro, rel=1e-6)
+
+
+def test_field_parity():
+    dom, st, o, g = pair("streamer_small")
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    o.fmg(1e-10, 30)
+    g.fmg(1e-10, 30)
+    o.compute_field()
+    g.compute_field()
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    assert rel_err(g.download(p.EMAG)[leaf], o.get(oracle.EMAG)[leaf]) <= TOL
+    assert g.dt_limit(Q, EPS0) == pytest.approx(o.dt_limit(Q, EPS0), rel=TOL)
+
+
+def test_fluid_stage_parity():
+    dom, st, o, g = pair("streamer_small")
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    o.fmg(1e-10, 30)
+    g.fmg(1e-10, 30)
+    o.compute_field()
+    g.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+    o.fluid_stage(dt)
+    g.fluid_stage(dt)
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    assert rel_err(g.download(p.NE)[leaf], o.get(oracle.NE)[leaf]) <= TOL
+    assert rel_err(g.download(p.NI)[leaf], o.get(oracle.NI)[leaf]) <= TOL
+    # refined boxes hold the average of their children on both sides
+    assert rel_err(g.download(p.NE), o.get(oracle.NE)) <= TOL
+
+
+def check_advance(name, tol_solve=1e-8):
+    dom, st, o, g = pair(name)
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    so = o.fmg(tol_solve, 40)
+    sg = g.fmg(tol_solve, 40)
+    assert so[2] == sg[2]
+    o.compute_field()
+    g.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+    assert g.dt_limit(Q, EPS0) == pytest.approx(dt, rel=TOL)
+    ro = o.advance(dt, Q, EPS0, tol_solve, 40)
+    rg = g.advance(dt, Q, EPS0, tol_solve, 40)
+    assert ro[0] == rg[0] == 0
+    assert ro[2:] == rg[2:], (ro, rg)
+    assert rg[1] == pytest.approx(ro[1], rel=TOL)
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    for vo, vg in ((oracle.NE, p.NE), (oracle.NI, p.NI), (oracle.PHI, p.PHI), (oracle.EMAG, p.EMAG)):
+        e = rel_err(g.download(vg)[leaf], o.get(vo)[leaf])
+        assert e <= TOL, (vo, e)
+    return g
+
+
+def test_heun_step_parity_small():
+    check_advance("streamer_small")
+
+
+@pytest.mark.slow
+def test_full_size_streamer6_parity():
+    """The benchmark workload (16 mm cube, base 64^3 + 6 levels, 2.4e6 leaf
+    cells): FMG to 1e-8, field, one Heun step, element-wise parity."""
+    g = check_advance("streamer6")
+    assert g.n_leaves * 512 > 2.0e6
+
+
+def test_single_box_domain():
+    """nb = 1: the whole solve is the exact level-0 solve."""
+    dom = synth.Domain(length=2.0, nb=1, max_level=0, bc_type=(1, 0, 0, 1, 1, 0),
+                       bc_val=(1.0, 0.0, 0.0, -2.0, 0.5, 0.0))
+    o = oracle.Oracle(dom)
+    g = gpu_mesh(dom)
+    t = assert_tables_equal(o, g)
+    rho = synth.gaussian_charge(dom, t["level"], t["ijk"], np.arange(1), sigma=0.3)
+    p = pkg()
+    o.set(oracle.RHO, rho); g.upload(p.RHO, rho)
+    o.charge_rhs(1.0, 1.0, True); g.charge_rhs(1.0, 1.0, True)
+    so = o.fmg(1e-12, 3)
+    sg = g.fmg(1e-12, 3)
+    assert so[2] == sg[2] == 1 and so[1] < 1e-13 and sg[1] < 1e-13
+    assert rel_err(g.download(p.PHI), o.get(oracle.PHI)) <= TOL
+
+
+@pytest.mark.parametrize("bct", [(1, 1, 1, 1, 1, 1), (0, 1, 1, 0, 0, 1)])
+def test_boundary_condition_mixes(bct):
+    dom = synth.Domain(length=1.0, nb=4, max_level=2, bc_type=bct,
+                       bc_val=(0.3, -0.2, 0.0, 1.0, 0.0, 2.0))
+    st = synth.Streamer(length=1.0, radius=0.1, z_head=0.45, refine_c=2.0, refine_tip=0.4)
+    o = oracle.build_mesh(dom, st)
+    g = gpu_mesh(dom, st)
+    t = assert_tables_equal(o, g)
+    assert o.n_levels == 5
+    rho = synth.gaussian_charge(dom, t["level"], t["ijk"], np.arange(len(t["level"])))
+    p = pkg()
+    o.set(oracle.RHO, rho); g.upload(p.RHO, rho)
+    o.charge_rhs(1.0, 1.0, True); g.charge_rhs(1.0, 1.0, True)
+    so = o.fmg(1e-11, 30)
+    sg = g.fmg(1e-11, 30)
+    assert so[2] == sg[2]
+    assert rel_err(g.download(p.PHI), o.get(oracle.PHI)) <= TOL
+
+
+def test_error_paths():
+    p = pkg()
+    dom = synth.domain_uniform_cube(64)
+    g = p.Solver(dom, 600)
+    with pytest.raises(p.SmError) as e:
+        g.solve(1e-8, 5)
+    assert e.value.code == p.SM_ESTATE
+    g.build_octree()
+    dom2, st = synth.workload("streamer_small")
+    g2 = p.Solver(dom2, 80)
+    g2.build_octree()
+    with pytest.raises(p.SmError) as e:
+        synth.refine_all(dom2, st, g2.level_ijk, g2.refine_level)
+    assert e.value.code == p.SM_ENOMEM
+    with pytest.raises(p.SmError) as e:
+        g.refine_level(1, np.ones(8, np.int8))    # not the finest level
+    assert e.value.code == p.SM_EINVAL
+    # max_cycles reached: SM_ENOCONV reported, potential still updated
+    rho = np.ones((g.n_boxes, 512))
+    g.upload(p.RHO, rho)
+    g.charge_rhs(1.0, 1.0, True)
+    rc, rel, cyc = g.fmg(1e-30, 2)
+    assert rc == p.SM_ENOCONV and cyc == 2 and rel < 1e-2
