@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "vcycle"],
+                    help="vcycle: build the workload, then only run --steps V-cycles "
+                         "(small, fixed launch sequence for ncu captures)")
     return ap.parse_args()
 
 
@@ -61,6 +64,14 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+# FP64 arithmetic peak of GB300 (nominal 1.25 TFLOP/s; a DFMA loop measured
+# 1.19-1.20 TFLOP/s at 1.9-2.07 GHz, about 2 DFMA per clock per SM)
+FP64_PEAK_GFLOPS = 1250.0
+# one colour pass of the red-black smoother, per cell of the level:
+# 16 bytes (phi read, f and phi of the colour) and 4 flops (8 per updated cell)
+RBGS_FLOP_PER_BYTE = 4.0 / 16.0
 
 
 class Clocks:
@@ -188,6 +199,16 @@ def run_gpu(args):
             total_ms += a.elapsed_time(b)
         return total_ms, cycles, g.launch_count() - l0
 
+    if args.mode == "vcycle":
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        rel = g.vcycles(args.steps)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"mode": "vcycle", "cycles": args.steps, "rel": rel}), flush=True)
+        g.close()
+        return
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -217,13 +238,19 @@ def run_gpu(args):
         kms, kn, kbytes = g.kernel_time(pkg.K_SMOOTH)
         g.profile(False)
         peak, kind = measured_peaks()
-        ach = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None, "kernel": "k_rbgs",
-                "launches": kn, "avg_launch_us": round(1e3 * kms / max(kn, 1), 3),
-                "bytes_per_launch": round(kbytes / max(kn, 1)), "peak_kind": kind,
-                "note": "per-launch average over %d event-timed launches; small coarse-level "
-                        "launches included" % kn}
+        gbs = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+        gflops = gbs * RBGS_FLOP_PER_BYTE
+        # FP64 at 1/64 rate makes the smoother ALU-bound: 4 flop per 16 B
+        # needs 1.7 TFLOP/s to keep up with HBM, above the FP64 peak
+        roof = {"bound": "alu", "achieved": round(gflops, 2), "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s (fp64)", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
+                "traffic": None, "kernel": "k_rbgs", "launches": kn,
+                "avg_launch_us": round(1e3 * kms / max(kn, 1), 3),
+                "bytes_per_launch": round(kbytes / max(kn, 1)),
+                "hbm": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "peak_kind": kind},
+                "note": "per-launch average over %d event-timed launches of every level in a "
+                        "second pass of the same steps" % kn}
     steps = args.steps
     solves = SOLVES_PER_STEP * steps * world
     value = solves / (ms * 1e-3)
