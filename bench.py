@@ -229,28 +229,25 @@ def run_gpu(args):
         tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
-    # roofline of the dominant kernel: event-timed red-black smoother
-    # launches over a second pass of the same steps
+    # roofline of the dominant kernel: the red-black smoother, timed with
+    # CUDA events around a graph of its launches in the V-cycle mix (every
+    # level, both colours) on the state left by the timed steps
     roof = None
     if not args.no_profile:
-        g.profile(True)
-        timed(args.steps)
-        kms, kn, kbytes = g.kernel_time(pkg.K_SMOOTH)
-        g.profile(False)
+        us, kn, kbytes = g.kernel_bench(pkg.K_SMOOTH, 20)
         peak, kind = measured_peaks()
-        gbs = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+        gbs = kbytes / (us * 1e-6) / 1e9
         gflops = gbs * RBGS_FLOP_PER_BYTE
         # FP64 at 1/64 rate makes the smoother ALU-bound: 4 flop per 16 B
         # needs 1.7 TFLOP/s to keep up with HBM, above the FP64 peak
         roof = {"bound": "alu", "achieved": round(gflops, 2), "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s (fp64)", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
                 "traffic": None, "kernel": "k_rbgs", "launches": kn,
-                "avg_launch_us": round(1e3 * kms / max(kn, 1), 3),
-                "bytes_per_launch": round(kbytes / max(kn, 1)),
+                "avg_launch_us": round(us, 3), "bytes_per_launch": round(kbytes),
                 "hbm": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 4), "peak_kind": kind},
-                "note": "per-launch average over %d event-timed launches of every level in a "
-                        "second pass of the same steps" % kn}
+                "note": "mean over %d graph-launched colour passes of every level "
+                        "(the V-cycle mix), CUDA events on the launching stream" % kn}
     steps = args.steps
     solves = SOLVES_PER_STEP * steps * world
     value = solves / (ms * 1e-3)

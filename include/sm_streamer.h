@@ -225,14 +225,22 @@ int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
 
 /* ---- diagnostics ----------------------------------------------------------- */
 
-/* Per-kernel-class timing with CUDA events on the context stream: enable
- * (1) or disable (0) recording; while enabled each launch of the selected
- * classes is bracketed by events (this serialises nothing but adds a few
- * microseconds per launch).  sm_kernel_time returns the summed device time
- * in ms, launch count and algorithmic bytes moved for one class since the
- * last enable.  Classes: 0 = red-black smoother. */
-int sm_profile_enable(sm_ctx *ctx, int enable);
-int sm_kernel_time(sm_ctx *ctx, int kclass, double *ms, long long *launches, double *bytes);
+/* Average device time of one launch of a kernel class in the launch mix of
+ * a V-cycle: one CUDA graph of `reps` repetitions of that class's launches
+ * over every level 1..top (both colours of the red-black smoother for class
+ * 0) is launched once to warm up and once between two CUDA events on the
+ * context stream.  Out: microseconds per launch, launches timed, algorithmic
+ * bytes per launch (16 per cell of the level: phi read, f and phi of the
+ * colour).  Side effect: the potential receives 2 x reps extra sweeps.
+ * Classes: 0 = red-black smoother. */
+int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, long long *launches,
+                    double *bytes_per_launch);
+
+/* Solves run as CUDA graphs (captured on first use per octree, with the
+ * cycle loop and its stopping test on the device) when enabled (default),
+ * or as individually launched kernels with a host loop when disabled.
+ * Both paths launch the same kernels in the same order. */
+int sm_set_graphs(sm_ctx *ctx, int enable);
 
 /* Number of kernels this context has launched since it was created
  * (diagnostics: lets a caller count device launches inside a region). */

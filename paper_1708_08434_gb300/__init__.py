@@ -56,7 +56,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_refine_level", "sm_get_tables", "sm_var_ptr", "sm_upload", "sm_download",
            "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
-           "sm_fluid_stage", "sm_advance_fluid", "sm_profile_enable", "sm_kernel_time",
+           "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs",
            "sm_launch_count", "sm_last_error"]
 
 
@@ -97,8 +97,8 @@ def load():
         "sm_dt_limit": [P, D, D, pD],
         "sm_fluid_stage": [P, D],
         "sm_advance_fluid": [P, D, D, D, D, I, pD, pI],
-        "sm_profile_enable": [P, I],
-        "sm_kernel_time": [P, I, pD, C.POINTER(C.c_longlong), pD],
+        "sm_kernel_bench": [P, I, I, pD, C.POINTER(C.c_longlong), pD],
+        "sm_set_graphs": [P, I],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_last_error": [P],
     }
@@ -310,16 +310,15 @@ class Solver:
         return rc, dtn.value, cyc[0], cyc[1]
 
     # -- diagnostics --
-    def profile(self, enable: bool):
-        self._ck(self._lib.sm_profile_enable(self._h, int(enable)))
+    def set_graphs(self, enable: bool):
+        self._ck(self._lib.sm_set_graphs(self._h, int(enable)))
+
+    def kernel_bench(self, kclass: int = K_SMOOTH, reps: int = 10):
+        us, n, by = C.c_double(), C.c_longlong(), C.c_double()
+        self._ck(self._lib.sm_kernel_bench(self._h, kclass, reps, C.byref(us), C.byref(n), C.byref(by)))
+        return us.value, n.value, by.value
 
     def launch_count(self) -> int:
         n = C.c_longlong()
         self._ck(self._lib.sm_launch_count(self._h, C.byref(n)))
         return n.value
-
-    def kernel_time(self, kclass: int = K_SMOOTH):
-        ms, n, by = C.c_double(), C.c_longlong(), C.c_double()
-        self._ck(self._lib.sm_kernel_time(self._h, kclass, C.byref(ms), C.byref(n), C.byref(by)))
-        return ms.value, n.value, by.value
-

@@ -41,62 +41,6 @@ extern "C" const char *sm_last_error(const sm_ctx *ctx) {
 }
 
 // ---------------------------------------------------------------------------
-// event timing of selected kernel classes
-// ---------------------------------------------------------------------------
-int sm_prof_begin(sm_ctx *ctx, int kclass, cudaEvent_t *ev) {
-  (void)kclass;
-  if (!ctx->prof) return SM_OK;
-  SM_CK(cudaEventCreate(ev));
-  SM_CK(cudaEventRecord(*ev, ctx->stream));
-  return SM_OK;
-}
-
-int sm_prof_end(sm_ctx *ctx, int kclass, cudaEvent_t *ev, double bytes) {
-  if (!ctx->prof) return SM_OK;
-  cudaEvent_t e2;
-  SM_CK(cudaEventCreate(&e2));
-  SM_CK(cudaEventRecord(e2, ctx->stream));
-  ctx->prof_recs.push_back({*ev, e2, kclass, bytes});
-  return SM_OK;
-}
-
-static int prof_collect(sm_ctx *ctx) {
-  auto &recs = ctx->prof_recs;
-  for (auto &r : recs) {
-    SM_CK(cudaEventSynchronize(r.b));
-    float ms = 0.f;
-    SM_CK(cudaEventElapsedTime(&ms, r.a, r.b));
-    ctx->prof_ms[r.kclass] += ms;
-    ctx->prof_n[r.kclass] += 1;
-    ctx->prof_bytes[r.kclass] += r.bytes;
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
-  }
-  recs.clear();
-  return SM_OK;
-}
-
-extern "C" int sm_profile_enable(sm_ctx *ctx, int enable) {
-  if (!ctx) return SM_EINVAL;
-  int st = prof_collect(ctx);
-  if (st) return st;
-  ctx->prof = enable != 0;
-  if (enable)
-    for (int c = 0; c < K_NCLASS; ++c) ctx->prof_ms[c] = 0, ctx->prof_n[c] = 0, ctx->prof_bytes[c] = 0;
-  return SM_OK;
-}
-
-extern "C" int sm_kernel_time(sm_ctx *ctx, int kclass, double *ms, long long *launches, double *bytes) {
-  if (!ctx || kclass < 0 || kclass >= K_NCLASS) return SM_EINVAL;
-  int st = prof_collect(ctx);
-  if (st) return st;
-  if (ms) *ms = ctx->prof_ms[kclass];
-  if (launches) *launches = ctx->prof_n[kclass];
-  if (bytes) *bytes = ctx->prof_bytes[kclass];
-  return SM_OK;
-}
-
-// ---------------------------------------------------------------------------
 // lifetime and arena
 // ---------------------------------------------------------------------------
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -208,7 +152,9 @@ extern "C" int sm_create(sm_ctx **out, const sm_config *cfg, const sm_domain *do
 
 extern "C" int sm_destroy(sm_ctx *ctx) {
   if (!ctx) return SM_OK;
-  prof_collect(ctx);
+  sm_drop_graphs(ctx);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
   if (ctx->hscal) cudaFreeHost(ctx->hscal);
   delete ctx;
   return SM_OK;
@@ -256,6 +202,7 @@ extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   ctx->tab = (double *)(a + L.tab);
   ctx->dscal = (unsigned long long *)(a + L.dscal);
   SM_CK(cudaMemsetAsync(a, 0, L.total, ctx->stream));
+  sm_drop_graphs(ctx);
   ctx->n_boxes = ctx->n_levels = ctx->n_leaves = 0;
   ctx->basis_ready = false;
   return SM_OK;
@@ -438,6 +385,7 @@ extern "C" int sm_build_octree(sm_ctx *ctx, int *n_boxes) {
   lo.off[ctx->lbase + 1] = n;
   for (int l = ctx->lbase + 2; l <= SM_MAX_LEVELS; ++l) lo.off[l] = n;
   if (n > ctx->cfg.max_boxes) return sm_fail(ctx, SM_ENOMEM, "max_boxes %d < %d", ctx->cfg.max_boxes, n);
+  sm_drop_graphs(ctx);
   k_build_uniform<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->lbase, lo, ctx->level, ctx->ijk,
                                                             ctx->morton, ctx->parent, ctx->child);
   ++ctx->n_launch;
@@ -482,6 +430,7 @@ extern "C" int sm_refine_level(sm_ctx *ctx, int level, const int8_t *flags, int 
   if (n_new) *n_new = 8 * accepted;
   if (accepted == 0) return SM_OK;
   int new_lo = ctx->n_boxes;
+  sm_drop_graphs(ctx);
   if (new_lo + 8 * accepted > ctx->cfg.max_boxes)
     return sm_fail(ctx, SM_ENOMEM, "max_boxes %d exceeded (%d needed)", ctx->cfg.max_boxes,
                    new_lo + 8 * accepted);

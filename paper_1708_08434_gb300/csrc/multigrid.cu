@@ -309,6 +309,124 @@ __global__ void __launch_bounds__(512) k_resnorm(const int32_t *__restrict__ lea
   block_max_to(slot, fabs(r), red);
 }
 
+// Residual and restriction fused: one block per fine box of level l
+// computes r = f - L phi for its 512 cells, then its 64 parent cells get
+// the 8-child averages of phi (into phi) and of r (into rhs, completed to
+// the FAS right-hand side by k_fas).
+__global__ void __launch_bounds__(512) k_resid_restrict(int lo, double *__restrict__ phi,
+                                                        double *__restrict__ rhs, const double *__restrict__ gh,
+                                                        const int32_t *__restrict__ nbr6,
+                                                        const int32_t *__restrict__ parent,
+                                                        const int32_t *__restrict__ ijk, Bc bc, double inv_h2) {
+  __shared__ double sp[CELLS], sr[CELLS];
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+  size_t base = (size_t)b * CELLS;
+  double p = phi[base + t];
+  double s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, 0);
+  sp[t] = p;
+  sr[t] = rhs[base + t] - (s - 6.0 * p) * inv_h2;
+  __syncthreads();
+  if (t >= 64) return;
+  int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
+  int P = parent[b];
+  int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
+  double ap = 0.0, ar = 0.0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        ap += sp[c];
+        ar += sr[c];
+      }
+  size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
+  phi[cc] = ap * 0.125;
+  rhs[cc] = ar * 0.125;
+}
+
+// Prolongation into the boxes of level l fused with the coarse
+// interpolation values of their refinement faces (both read only level
+// l-1): mode 0 adds the correction (phi - old), mode 1 overwrites with the
+// prolonged solution (FMG); gh always interpolates phi itself.
+__global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, double *__restrict__ phi,
+                                                    const double *__restrict__ old, double *__restrict__ gh,
+                                                    const int32_t *__restrict__ nbr6,
+                                                    const int32_t *__restrict__ parent,
+                                                    const int32_t *__restrict__ ijk, Bc bc,
+                                                    unsigned long long *err) {
+  int b = lo + blockIdx.x;
+  int t = threadIdx.x;
+  int P = parent[b];
+  {
+    int loc[3] = {t & 7, (t >> 3) & 7, t >> 6};
+    int G[3], lc[3];
+    for (int d = 0; d < 3; ++d) {
+      G[d] = NC * ijk[3 * b + d] + loc[d];
+      lc[d] = (G[d] >> 1) - NC * ijk[3 * P + d];
+    }
+    auto val = [&](int Q, int c) {
+      size_t x = (size_t)Q * CELLS + c;
+      return mode ? phi[x] : phi[x] - old[x];
+    };
+    double c0 = val(P, cidx(lc[0], lc[1], lc[2]));
+    double sum = c0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      int s = (G[e] & 1) ? 1 : -1;
+      int q[3] = {lc[0], lc[1], lc[2]};
+      q[e] += s;
+      sum += coarse_at(val, nbr6, P, q, e, s, c0, bc, mode ? 0 : 1, err);
+    }
+    size_t x = (size_t)b * CELLS + t;
+    if (mode) phi[x] = 0.25 * sum;
+    else phi[x] += 0.25 * sum;
+  }
+  if (t >= 6 * FACE) return;
+  int f = t >> 6, u = t & 7, w = (t >> 3) & 7;
+  if (__ldg(nbr6 + 6 * b + f) != -2) return;
+  auto pv = [&](int Q, int c) { return phi[(size_t)Q * CELLS + c]; };
+  int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  int G[3];
+  G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
+  G[t1] = NC * ijk[3 * b + t1] + u;
+  G[t2] = NC * ijk[3 * b + t2] + w;
+  int Q = nbr6[6 * P + f];
+  if (Q < 0) {
+    atomicOr(err, 2ull);
+    return;
+  }
+  int lc[3];
+  for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
+  double c = pv(Q, cidx(lc[0], lc[1], lc[2]));
+  double ph = 0.5 * c;
+  int ts[2] = {t1, t2};
+  for (int e2 = 0; e2 < 2; ++e2) {
+    int e = ts[e2];
+    int s = (G[e] & 1) ? 1 : -1;
+    int q[3] = {lc[0], lc[1], lc[2]};
+    q[e] += s;
+    ph += 0.25 * coarse_at(pv, nbr6, Q, q, e, s, c, bc, 0, err);
+  }
+  gh[(size_t)(6 * b + f) * FACE + u + NC * w] = ph;
+}
+
+// Stopping test of the device-side cycle loop: relative residual of the
+// last norm, cycle count, and the loop condition rel > tol && cycles < max.
+__global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *sc) {
+  double num = __longlong_as_double((long long)sc[SC_NORM]);
+  double den = __longlong_as_double((long long)sc[SC_DEN]);
+  double rel = den > 0.0 ? num / den : num;
+  unsigned long long c = sc[SC_CYC] + 1;
+  sc[SC_CYC] = c;
+  sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
+  double tol = __longlong_as_double((long long)sc[SC_TOL]);
+  cudaGraphSetConditional(h, (rel > tol && c < sc[SC_MAXC]) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
@@ -345,32 +463,34 @@ int sm_restrict_pair(sm_ctx *ctx, double *a, double *a2) {
   return SM_OK;
 }
 
+static int rbgs_pass(sm_ctx *ctx, int l, int color) {
+  k_rbgs<<<lvl_n(ctx, l), 256, 0, ctx->stream>>>(ctx->level_off[l], color, ctx->phi, ctx->rhs, ctx->gh,
+                                                 ctx->nbr6, ctx->bc, ctx->lh.h2[l]);
+  ++ctx->n_launch;
+  return SM_OK;
+}
+
 static int smooth(sm_ctx *ctx, int l, int nu) {
-  int n = lvl_n(ctx, l);
-  if (!n) return SM_OK;
+  if (!lvl_n(ctx, l)) return SM_OK;
   for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color) {
-      cudaEvent_t ev;
-      int st = sm_prof_begin(ctx, K_SMOOTH, &ev);
-      if (st) return st;
-      k_rbgs<<<n, 256, 0, ctx->stream>>>(ctx->level_off[l], color, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6,
-                                         ctx->bc, ctx->lh.h2[l]);
-      ++ctx->n_launch;
-      // algorithmic bytes of one colour pass: read phi of all cells (the
-      // neighbours), f of the colour, write phi of the colour
-      st = sm_prof_end(ctx, K_SMOOTH, &ev, (double)n * CELLS * (8.0 + 4.0 + 4.0));
-      if (st) return st;
-    }
+    for (int color = 0; color < 2; ++color) rbgs_pass(ctx, l, color);
   SM_CKL("rbgs");
   return SM_OK;
 }
 
-static int coarse_solve(sm_ctx *ctx) {
+static int ensure_basis(sm_ctx *ctx) {
   if (!ctx->basis_ready) {
     k_coarse_basis<<<1, 32, 0, ctx->stream>>>(ctx->basis, ctx->bc, NC);
     ++ctx->n_launch;
+    SM_CKL("coarse basis");
     ctx->basis_ready = true;
   }
+  return SM_OK;
+}
+
+static int coarse_solve(sm_ctx *ctx) {
+  int st = ensure_basis(ctx);
+  if (st) return st;
   k_coarse_solve<<<1, 512, 0, ctx->stream>>>(ctx->phi, ctx->rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
                                              ctx->lh.inv_h2[0]);
   ++ctx->n_launch;
@@ -378,21 +498,28 @@ static int coarse_solve(sm_ctx *ctx) {
   return SM_OK;
 }
 
-// FAS V-cycle with `top` as finest level
+static int prolong_cf(sm_ctx *ctx, int l, int mode) {
+  k_prolong_cf<<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], mode, ctx->phi, ctx->old, ctx->gh,
+                                                       ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
+                                                       ctx->dscal + SC_ERR);
+  ++ctx->n_launch;
+  SM_CKL("prolong");
+  return SM_OK;
+}
+
+// FAS V-cycle with `top` as finest level.  On entry the coarse
+// interpolation values gh of every level <= top must match the current
+// potential of the level below (the solve prologue and every up-sweep
+// leave them so); the down-sweep changes no level below the one it smooths
+// before that level is visited again, so it needs no refill.
 static int vcycle(sm_ctx *ctx, int top) {
   int st;
-  const int nu1 = ctx->cfg.nu1, nu2 = ctx->cfg.nu2;
   for (int l = top; l >= 1; --l) {
-    int n = lvl_n(ctx, l);
-    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l, 0))) return st;
-    if ((st = smooth(ctx, l, nu1))) return st;
-    k_residual<<<n, 512, 0, ctx->stream>>>(ctx->level_off[l], ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6, ctx->bc,
-                                           ctx->lh.inv_h2[l], ctx->res);
+    if ((st = smooth(ctx, l, ctx->cfg.nu1))) return st;
+    k_resid_restrict<<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], ctx->phi, ctx->rhs, ctx->gh,
+                                                             ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
+                                                             ctx->lh.inv_h2[l]);
     ++ctx->n_launch;
-    k_restrict_fas<<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], ctx->parent, ctx->ijk, ctx->phi, ctx->res,
-                                              ctx->rhs);
-    ++ctx->n_launch;
-    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l - 1, 0))) return st;
     k_fas<<<lvl_n(ctx, l - 1), 512, 0, ctx->stream>>>(ctx->level_off[l - 1], ctx->phi, ctx->old, ctx->rhs,
                                                       ctx->gh, ctx->nbr6, ctx->child, ctx->bc,
                                                       ctx->lh.inv_h2[l - 1]);
@@ -401,13 +528,8 @@ static int vcycle(sm_ctx *ctx, int top) {
   }
   if ((st = coarse_solve(ctx))) return st;
   for (int l = 1; l <= top; ++l) {
-    int n = lvl_n(ctx, l);
-    k_prolong<<<n, 512, 0, ctx->stream>>>(ctx->level_off[l], 0, ctx->phi, ctx->old, ctx->nbr6, ctx->parent,
-                                          ctx->ijk, ctx->bc, ctx->dscal + SC_ERR);
-    ++ctx->n_launch;
-    SM_CKL("prolong");
-    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l, 0))) return st;
-    if ((st = smooth(ctx, l, nu2))) return st;
+    if ((st = prolong_cf(ctx, l, 0))) return st;
+    if ((st = smooth(ctx, l, ctx->cfg.nu2))) return st;
   }
   return SM_OK;
 }
@@ -431,12 +553,15 @@ static int read_scalars(sm_ctx *ctx) {
   return SM_OK;
 }
 
-// denominator of the relative residual: max_leaf |f - L 0| (uses old as 0)
-static int residual_denominator(sm_ctx *ctx) {
+// denominator of the relative residual, max_leaf |f - L 0| (old serves as
+// the zero field), then the coarse interpolation values of phi restored
+static int solve_prologue(sm_ctx *ctx) {
   int st;
   SM_CK(cudaMemsetAsync(ctx->old, 0, sizeof(double) * CELLS * (size_t)ctx->n_boxes, ctx->stream));
   if ((st = sm_fill_all_cf(ctx, ctx->old))) return st;
   if ((st = leaf_norm(ctx, ctx->old, SC_DEN))) return st;
+  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_CYC, 0, sizeof(unsigned long long), ctx->stream));
   return SM_OK;
 }
 
@@ -455,6 +580,162 @@ static int check_ready(sm_ctx *ctx) {
   return SM_OK;
 }
 
+// FMG part before the cycle loop: restrict f, exact level-0 solve, then for
+// each finer level prolong the solution (and its interpolation values) and
+// run one V-cycle with that level on top
+static int fmg_ladder(sm_ctx *ctx) {
+  int st;
+  if ((st = sm_restrict_pair(ctx, ctx->rhs, nullptr))) return st;
+  if ((st = coarse_solve(ctx))) return st;
+  for (int l = 1; l < ctx->n_levels; ++l) {
+    if ((st = prolong_cf(ctx, l, 1))) return st;
+    if ((st = vcycle(ctx, l))) return st;
+  }
+  return SM_OK;
+}
+
+// ---- graph-captured solves with a device-side cycle loop ------------------
+
+void sm_drop_graphs(sm_ctx *ctx) {
+  for (auto *g : {&ctx->g_solve, &ctx->g_fmg}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+}
+
+static bool use_graphs(const sm_ctx *ctx) { return ctx->graphs; }
+
+static int end_captures(sm_ctx *ctx, cudaStream_t saved, int st) {
+  cudaGraph_t tmp = nullptr;
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(ctx->cap2, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    cudaStreamEndCapture(ctx->cap2, &tmp);
+    if (tmp) cudaGraphDestroy(tmp);
+  }
+  tmp = nullptr;
+  if (cudaStreamIsCapturing(ctx->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    cudaStreamEndCapture(ctx->cap, &tmp);
+    if (tmp) cudaGraphDestroy(tmp);
+  }
+  ctx->stream = saved;
+  cudaGetLastError();
+  return st;
+}
+
+// Capture [prologue] + WHILE(cond){ V-cycle; norm; check } into an
+// executable graph.  fmg: the prologue is the FMG ladder followed by a norm
+// and a check (which sets the first loop condition); otherwise the loop
+// body runs at least once.
+static int capture_solve(sm_ctx *ctx, int fmg, sm_graph *out) {
+  cudaStream_t saved = ctx->stream;
+  if (!ctx->cap) SM_CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+  if (!ctx->cap2) SM_CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
+  {
+    int st = ensure_basis(ctx);  // once per context, outside any graph
+    if (st) return st;
+  }
+  SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+  ctx->stream = ctx->cap;
+  int st = SM_OK;
+  cudaGraph_t g = nullptr, body = nullptr, whole = nullptr;
+  cudaStreamCaptureStatus cs;
+  cudaGraphConditionalHandle h;
+  cudaGraphNode_t node;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  // the node-parameter union has no default constructor: zeroed raw storage
+  alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+  memset(pbuf, 0, sizeof pbuf);
+  cudaGraphNodeParams &p = *reinterpret_cast<cudaGraphNodeParams *>(pbuf);
+  long long n0;
+  if (cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "capture info"));
+  if (cudaGraphConditionalHandleCreate(&h, g, fmg ? 0u : 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "conditional handle"));
+  n0 = ctx->n_launch;
+  if ((st = solve_prologue(ctx))) return end_captures(ctx, saved, st);
+  if (fmg) {
+    if ((st = fmg_ladder(ctx))) return end_captures(ctx, saved, st);
+    if ((st = leaf_norm(ctx, ctx->phi, SC_NORM))) return end_captures(ctx, saved, st);
+    k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal);
+    ++ctx->n_launch;
+  }
+  out->prefix_launches = ctx->n_launch - n0;
+  if (cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "capture deps"));
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &p) != cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "while node"));
+  body = p.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(ctx->cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+      cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "capture deps update"));
+  if (cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "body capture"));
+  ctx->stream = ctx->cap2;
+  n0 = ctx->n_launch;
+  if ((st = vcycle(ctx, ctx->n_levels - 1))) return end_captures(ctx, saved, st);
+  if ((st = leaf_norm(ctx, ctx->phi, SC_NORM))) return end_captures(ctx, saved, st);
+  k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal);
+  ++ctx->n_launch;
+  out->body_launches = ctx->n_launch - n0;
+  if (cudaStreamEndCapture(ctx->cap2, &body) != cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end body capture"));
+  ctx->stream = ctx->cap;
+  if (cudaStreamEndCapture(ctx->cap, &whole) != cudaSuccess)
+    return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end capture"));
+  ctx->stream = saved;
+  cudaError_t e = cudaGraphInstantiate(&out->exec, whole, 0);
+  cudaGraphDestroy(whole);
+  if (e != cudaSuccess) return sm_cuda_check(ctx, e, "graph instantiate");
+  // captured launches are counted when the graph runs
+  ctx->n_launch -= out->prefix_launches + out->body_launches;
+  return SM_OK;
+}
+
+static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycles, double *rel_res) {
+  int st;
+  int c = 0;
+  double rel = 0.0;
+  if (use_graphs(ctx)) {
+    sm_graph *g = fmg ? &ctx->g_fmg : &ctx->g_solve;
+    if (!g->exec && (st = capture_solve(ctx, fmg, g))) return st;
+    ctx->hscal[SC_TOL] = tol;
+    unsigned long long mc = (unsigned long long)max_cycles;
+    memcpy(&ctx->hscal[SC_MAXC], &mc, sizeof mc);
+    SM_CK(cudaMemcpyAsync(ctx->dscal + SC_TOL, ctx->hscal + SC_TOL, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                          ctx->stream));
+    SM_CK(cudaGraphLaunch(g->exec, ctx->stream));
+    if ((st = read_scalars(ctx))) return st;
+    unsigned long long cc;
+    memcpy(&cc, &ctx->hscal[SC_CYC], sizeof cc);
+    c = (int)cc;
+    rel = ctx->hscal[SC_REL];
+    ctx->n_launch += g->prefix_launches + g->body_launches * (long long)(fmg ? c - 1 : c);
+  } else {
+    if ((st = solve_prologue(ctx))) return st;
+    if (fmg) {
+      if ((st = fmg_ladder(ctx))) return st;
+      c = 1;
+      if ((st = rel_residual(ctx, &rel))) return st;
+    }
+    if (!fmg || (rel > tol && c < max_cycles)) {
+      do {
+        if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
+        ++c;
+        if ((st = rel_residual(ctx, &rel))) return st;
+      } while (rel > tol && c < max_cycles);
+    }
+  }
+  if (cycles) *cycles = c;
+  if (rel_res) *rel_res = rel;
+  return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
+}
+
 extern "C" int sm_fill_ghosts(sm_ctx *ctx, int var, int level) {
   int st = check_ready(ctx);
   if (st) return st;
@@ -466,11 +747,10 @@ extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
   int st = check_ready(ctx);
   if (st) return st;
   if (n_cycles < 0) return SM_EINVAL;
-  if ((st = residual_denominator(ctx))) return st;
+  if ((st = solve_prologue(ctx))) return st;
   for (int c = 0; c < n_cycles; ++c)
     if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
   double rel = 0.0;
-  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
   if ((st = rel_residual(ctx, &rel))) return st;
   if (rel_res) *rel_res = rel;
   return SM_OK;
@@ -480,43 +760,69 @@ extern "C" int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles,
   int st = check_ready(ctx);
   if (st) return st;
   if (max_cycles < 1) return SM_EINVAL;
-  if ((st = residual_denominator(ctx))) return st;
-  int c = 0;
-  double rel = 0.0;
-  do {
-    if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
-    ++c;
-    if ((st = rel_residual(ctx, &rel))) return st;
-  } while (rel > tol && c < max_cycles);
-  if (cycles) *cycles = c;
-  if (rel_res) *rel_res = rel;
-  return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
+  return run_solve(ctx, 0, tol, max_cycles, cycles, rel_res);
 }
 
 extern "C" int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res) {
   int st = check_ready(ctx);
   if (st) return st;
   if (max_cycles < 1) return SM_EINVAL;
-  if ((st = residual_denominator(ctx))) return st;
+  return run_solve(ctx, 1, tol, max_cycles, cycles, rel_res);
+}
+
+extern "C" int sm_set_graphs(sm_ctx *ctx, int enable) {
+  if (!ctx) return SM_EINVAL;
+  ctx->graphs = enable != 0;
+  return SM_OK;
+}
+
+// Average launch duration of a kernel class in the launch mix of a V-cycle,
+// timed with CUDA events around one graph of `reps` repetitions.
+extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, long long *launches,
+                               double *bytes_per_launch) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (kclass != K_SMOOTH || reps < 1) return SM_EINVAL;
   int top = ctx->n_levels - 1;
-  if ((st = sm_restrict_pair(ctx, ctx->rhs, nullptr))) return st;
-  if ((st = coarse_solve(ctx))) return st;
-  for (int l = 1; l <= top; ++l) {
-    k_prolong<<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], 1, ctx->phi, ctx->old, ctx->nbr6,
-                                                      ctx->parent, ctx->ijk, ctx->bc, ctx->dscal + SC_ERR);
-    ++ctx->n_launch;
-    SM_CKL("fmg prolong");
-    if ((st = vcycle(ctx, l))) return st;
-  }
-  int c = 1;
-  double rel = 0.0;
-  if ((st = rel_residual(ctx, &rel))) return st;
-  while (rel > tol && c < max_cycles) {
-    if ((st = vcycle(ctx, top))) return st;
-    ++c;
-    if ((st = rel_residual(ctx, &rel))) return st;
-  }
-  if (cycles) *cycles = c;
-  if (rel_res) *rel_res = rel;
-  return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
+  if (top < 1) return SM_EINVAL;
+  cudaStream_t saved = ctx->stream;
+  if (!ctx->cap) SM_CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+  SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+  ctx->stream = ctx->cap;
+  long long n = 0;
+  double bytes = 0.0;
+  for (int r = 0; r < reps; ++r)
+    for (int l = top; l >= 1; --l)
+      for (int color = 0; color < 2; ++color) {
+        rbgs_pass(ctx, l, color);
+        ++n;
+        bytes += (double)lvl_n(ctx, l) * CELLS * 16.0;
+      }
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+  ctx->stream = saved;
+  ctx->n_launch -= n;
+  if (e != cudaSuccess) return sm_cuda_check(ctx, e, "bench capture");
+  cudaGraphExec_t x;
+  e = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return sm_cuda_check(ctx, e, "bench instantiate");
+  cudaEvent_t a, b;
+  SM_CK(cudaEventCreate(&a));
+  SM_CK(cudaEventCreate(&b));
+  SM_CK(cudaGraphLaunch(x, ctx->stream));  // warm
+  SM_CK(cudaEventRecord(a, ctx->stream));
+  SM_CK(cudaGraphLaunch(x, ctx->stream));
+  SM_CK(cudaEventRecord(b, ctx->stream));
+  SM_CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  SM_CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaGraphExecDestroy(x);
+  ctx->n_launch += 2 * n;
+  if (us_per_launch) *us_per_launch = 1e3 * ms / n;
+  if (launches) *launches = n;
+  if (bytes_per_launch) *bytes_per_launch = bytes / n;
+  return SM_OK;
 }

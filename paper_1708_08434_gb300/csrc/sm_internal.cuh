@@ -35,15 +35,18 @@ struct Table {
   double inv_de;    // (n-1)/e_max
 };
 
-// kernel classes for event timing
+// kernel classes for sm_kernel_bench
 enum KClass { K_SMOOTH = 0, K_NCLASS = 1 };
 
-// one timed launch: events around it, its class and algorithmic bytes
-struct ProfRec {
-  cudaEvent_t a, b;
-  int kclass;
-  double bytes;
+}  // namespace sm
+
+// an instantiated solve graph and the kernel launches it contains
+struct sm_graph {
+  cudaGraphExec_t exec = nullptr;
+  long long prefix_launches = 0, body_launches = 0;
 };
+
+namespace sm {
 
 }  // namespace sm
 
@@ -93,12 +96,10 @@ struct sm_ctx {
   // kernels launched so far (diagnostics)
   long long n_launch = 0;
 
-  // profiling
-  bool prof = false;
-  double prof_ms[sm::K_NCLASS] = {0};
-  long long prof_n[sm::K_NCLASS] = {0};
-  double prof_bytes[sm::K_NCLASS] = {0};
-  std::vector<sm::ProfRec> prof_recs;
+  // captured solves (invalidated when the octree changes)
+  bool graphs = true;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  sm_graph g_solve, g_fmg;
 
   std::string err;
 };
@@ -127,7 +128,10 @@ enum {
   SC_AD = 3,        // dt: max adv + 6 D/dx^2
   SC_DRT = 4,       // dt: max mu n_e
   SC_ERR = 5,       // consistency error flag
-  SC_COUNT = 6,     // generic counter
+  SC_CYC = 6,       // V-cycles done by the device-side loop
+  SC_REL = 7,       // relative residual after the last cycle (double bits)
+  SC_TOL = 8,       // loop tolerance (double bits), set before a launch
+  SC_MAXC = 9,      // loop cycle limit, set before a launch
   SC_N = 16
 };
 
@@ -214,5 +218,4 @@ __device__ __forceinline__ T nb_sum(const T *__restrict__ v, const int32_t *__re
 int sm_mg_fill_cf(sm_ctx *ctx, double *var, int level, int homog);
 int sm_fill_all_cf(sm_ctx *ctx, double *var);
 int sm_restrict_pair(sm_ctx *ctx, double *a, double *b);
-int sm_prof_begin(sm_ctx *ctx, int kclass, cudaEvent_t *ev);
-int sm_prof_end(sm_ctx *ctx, int kclass, cudaEvent_t *ev, double bytes);
+void sm_drop_graphs(sm_ctx *ctx);

@@ -235,3 +235,40 @@ def test_error_paths():
     g.charge_rhs(1.0, 1.0, True)
     rc, rel, cyc = g.fmg(1e-30, 2)
     assert rc == p.SM_ENOCONV and cyc == 2 and rel < 1e-2
+
+
+def test_graph_and_direct_paths_identical():
+    """Captured solves (device-side cycle loop) launch the same kernels in
+    the same order as the host-driven path: results are bit-identical."""
+    dom, st = synth.workload("streamer_small")
+    p = pkg()
+    out = []
+    for graphs in (True, False):
+        g = gpu_mesh(dom, st)
+        g.set_graphs(graphs)
+        t = g.tables()
+        ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+        g.upload(p.NE, ne); g.upload(p.NI, ni)
+        g.charge_rhs(Q, EPS0)
+        r1 = g.fmg(1e-9, 30)
+        r2 = g.solve(1e-11, 30)
+        out.append((r1, r2, g.download(p.PHI)))
+        g.close()
+    (a1, a2, pa), (b1, b2, pb) = out
+    assert a1[2] == b1[2] and a2[2] == b2[2]
+    assert a1[1] == b1[1] and a2[1] == b2[1]
+    assert np.array_equal(pa, pb)
+
+
+def test_repeated_graph_launch_and_launch_count():
+    dom, st, o, g = pair("streamer_small")
+    load_inputs(dom, st, o, g)
+    n0 = g.launch_count()
+    r1 = g.fmg(1e-8, 30)
+    n1 = g.launch_count()
+    r2 = g.fmg(1e-8, 30)       # second launch of the cached graph
+    n2 = g.launch_count()
+    assert r1[:3] == r2[:3]
+    assert n2 - n1 == n1 - n0 - 1  # first call also built the level-0 basis
+    us, n, by = g.kernel_bench(0, 3)
+    assert us > 0 and n == 3 * 2 * (g.n_levels - 1) and by > 0
