@@ -246,6 +246,41 @@ int sm_set_graphs(sm_ctx *ctx, int enable);
  * (diagnostics: lets a caller count device launches inside a region). */
 int sm_launch_count(const sm_ctx *ctx, long long *n);
 
+/* ---- allocation-free entry point ---------------------------------------- */
+
+/* No counterpart in the paper: a service for callers that cannot allocate
+ * device memory -- code running while another component owns all device
+ * memory (a caching allocator or pool it must not bypass), code in regions
+ * where an allocation is forbidden or would synchronise the device, and
+ * embedders that only hand over their own input and output buffers.
+ *
+ * Solves n_problems independent Poisson problems L phi = f, each on one box
+ * of 8^3 cells and side `length`, with the 7-point operator and boundary
+ * rules of the multigrid solve (Dirichlet ghost 2g - phi, Neumann ghost
+ * phi); this is the same eigenbasis solve as level 0 of sm_mg_fmg.
+ *   bc_type: DEVICE int32 [n_problems][6] (faces -x,+x,-y,+y,-z,+z;
+ *            0 Neumann zero, 1 Dirichlet); a problem without a Dirichlet
+ *            face gets its constant mode set to zero
+ *   bc_val:  DEVICE double [n_problems][6] Dirichlet values
+ *   f:       DEVICE double [n_problems][512] right-hand side (cell i+8j+64k)
+ *   phi:     DEVICE double [n_problems][512] solution (written)
+ *   stream:  cudaStream_t as void*; the call only enqueues work.
+ * The library allocates nothing: its only scratch (one eigenbasis per
+ * problem) is a fixed device array of SM_NOALLOC_MAX_PROBLEMS x 1728 bytes
+ * (1.77 MB) that every GPU loading the library holds until exit.  The first
+ * call on a device looks up that array's device address (set-up, once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls share the array and each call overwrites the slots of
+ * its problems before reading them, so nothing needs clearing, but calls
+ * that overlap on the GPU (different streams, or devices sharing nothing
+ * else) race on it: order them.
+ * Errors: SM_ENOMEM if n_problems > SM_NOALLOC_MAX_PROBLEMS (the fixed
+ * scratch is too small), SM_EINVAL (n_problems < 0, length <= 0, null
+ * pointer), SM_ECUDA (no device, address lookup or launch failed). */
+#define SM_NOALLOC_MAX_PROBLEMS 1024
+int sm_box_solve_noalloc(double length, int n_problems, const int32_t *bc_type, const double *bc_val,
+                         const double *f, double *phi, void *stream);
+
 /* Human-readable reason of the last error on this context. */
 const char *sm_last_error(const sm_ctx *ctx);
 

@@ -57,7 +57,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs",
-           "sm_launch_count", "sm_last_error"]
+           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc"]
 
 
 def library_path() -> str:
@@ -100,6 +100,7 @@ def load():
         "sm_kernel_bench": [P, I, I, pD, C.POINTER(C.c_longlong), pD],
         "sm_set_graphs": [P, I],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
+        "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
         "sm_last_error": [P],
     }
     for name, args in sig.items():
