@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "vcycle"],
                     help="vcycle: build the workload, then only run --steps V-cycles "
                          "(small, fixed launch sequence for ncu captures)")
@@ -121,12 +122,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_gpu_case():
+def build_gpu_case(precision=0):
     import torch
     import synth
     import paper_1708_08434_gb300 as pkg
     dom, st = synth.workload(WORKLOAD)
-    g = pkg.Solver(dom, max_boxes=8192)
+    g = pkg.Solver(dom, max_boxes=8192, precision=precision)
     g.build_octree()
     synth.refine_all(dom, st, g.level_ijk, g.refine_level)
     t = g.tables()
@@ -166,38 +167,42 @@ def run_gpu(args):
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     stream = g.stream
 
-    def step(host_io=False):
-        if host_io:
-            g.upload(pkg.NE, ne_h)
-            g.upload(pkg.NI, ni_h)
-        else:
-            g.var(pkg.NE).copy_(ne_d)
-            g.var(pkg.NI).copy_(ni_d)
-        g.charge_rhs(Q, E0)
-        rc0, rel0, c0 = g.fmg(TOL, MAX_CYCLES)
-        g.compute_field()
-        dt = g.dt_limit(Q, E0)
-        rc1, dtn, c1, c2 = g.advance(dt, Q, E0, TOL, MAX_CYCLES)
-        if host_io:
-            g.download(pkg.PHI, phi_out)
-            g.download(pkg.NE, ne_out)
-        assert rc0 == 0 and rc1 == 0, (rc0, rc1)
-        return c0 + c1 + c2
+    def make_step(g):
+        def step(host_io=False):
+            if host_io:
+                g.upload(pkg.NE, ne_h)
+                g.upload(pkg.NI, ni_h)
+            else:
+                g.var(pkg.NE).copy_(ne_d)
+                g.var(pkg.NI).copy_(ni_d)
+            g.charge_rhs(Q, E0)
+            rc0, rel0, c0 = g.fmg(TOL, MAX_CYCLES)
+            g.compute_field()
+            dt = g.dt_limit(Q, E0)
+            rc1, dtn, c1, c2 = g.advance(dt, Q, E0, TOL, MAX_CYCLES)
+            if host_io:
+                g.download(pkg.PHI, phi_out)
+                g.download(pkg.NE, ne_out)
+            assert rc0 == 0 and rc1 == 0, (rc0, rc1)
+            return c0 + c1 + c2
 
-    def timed(n, host_io=False):
-        total_ms, cycles = 0.0, 0
-        l0 = g.launch_count()
-        for _ in range(n):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            cycles += step(host_io)
-            b.record(stream)
-            torch.cuda.synchronize()
-            total_ms += a.elapsed_time(b)
-        return total_ms, cycles, g.launch_count() - l0
+        def timed(n, host_io=False):
+            total_ms, cycles = 0.0, 0
+            l0 = g.launch_count()
+            for _ in range(n):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cycles += step(host_io)
+                b.record(stream)
+                torch.cuda.synchronize()
+                total_ms += a.elapsed_time(b)
+            return total_ms, cycles, g.launch_count() - l0
+        return step, timed
+
+    step, timed = make_step(g)
 
     if args.mode == "vcycle":
         g.var(pkg.NE).copy_(ne_d)
@@ -248,6 +253,26 @@ def run_gpu(args):
                         "frac": round(gbs / peak, 4), "peak_kind": kind},
                 "note": "mean over %d graph-launched colour passes of every level "
                         "(the V-cycle mix), CUDA events on the launching stream" % kn}
+    # the same step with the mixed-precision solve (FP32 error equation in an
+    # FP64 defect-correction loop) on a second solver of the same workload
+    mixed = None
+    if not args.no_mixed:
+        gm = build_gpu_case(precision=pkg.MIXED)[2]
+        step_m, timed_m = make_step(gm)
+        for _ in range(args.warmup):
+            step_m()
+        torch.cuda.synchronize()
+        mms, mcyc, mlaunch = timed_m(args.steps)
+        if world > 1:
+            tt = torch.tensor([mms], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            mms = float(tt.item())
+        mixed = {"value": round(SOLVES_PER_STEP * args.steps * world / (mms * 1e-3), 3),
+                 "unit": "solves/s", "ms_per_step": round(mms / args.steps, 4),
+                 "corrections_per_step": mcyc / args.steps, "gpu_launches": mlaunch,
+                 "speedup_vs_fp64": round(ms / mms, 3),
+                 "dtype": "f32 error equation, f64 residual/accumulation/level-0 solve"}
+        gm.close()
     steps = args.steps
     solves = SOLVES_PER_STEP * steps * world
     value = solves / (ms * 1e-3)
@@ -270,6 +295,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roof,
+        "mixed_precision": mixed,
     }
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline()

@@ -58,10 +58,11 @@ struct ArenaPlan {
 // layout shared by sm_arena_size and sm_bind_arena
 struct Layout {
   size_t level, ijk, parent, child, nbr, nbr6, leaf, morton, scan_a, scan_b, count, flags;
-  size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, total;
+  size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, e32, f32, old32, gh32,
+      total;
 };
 
-static Layout plan(int cap) {
+static Layout plan(int cap, bool mixed) {
   ArenaPlan p;
   Layout L;
   size_t nc = (size_t)cap * CELLS;
@@ -90,6 +91,14 @@ static Layout plan(int cap) {
   L.basis = p.take<double>(3 * 64 + 3 * 8);
   L.tab = p.take<double>(3 * 4096);
   L.dscal = p.take<unsigned long long>(SC_N);
+  if (mixed) {
+    L.e32 = p.take<float>(nc);
+    L.f32 = p.take<float>(nc);
+    L.old32 = p.take<float>(nc);
+    L.gh32 = p.take<float>((size_t)cap * 6 * FACE);
+  } else {
+    L.e32 = L.f32 = L.old32 = L.gh32 = 0;
+  }
   L.total = p.total;
   return L;
 }
@@ -162,13 +171,13 @@ extern "C" int sm_destroy(sm_ctx *ctx) {
 
 extern "C" int sm_arena_size(const sm_ctx *ctx, size_t *bytes) {
   if (!ctx || !bytes) return SM_EINVAL;
-  *bytes = plan(ctx->cfg.max_boxes).total;
+  *bytes = plan(ctx->cfg.max_boxes, ctx->cfg.precision == SM_MIXED).total;
   return SM_OK;
 }
 
 extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   if (!ctx || !dev_ptr) return SM_EINVAL;
-  Layout L = plan(ctx->cfg.max_boxes);
+  Layout L = plan(ctx->cfg.max_boxes, ctx->cfg.precision == SM_MIXED);
   if (bytes < L.total) return sm_fail(ctx, SM_ENOMEM, "arena %zu bytes < needed %zu", bytes, L.total);
   if (((uintptr_t)dev_ptr & 255) != 0) return sm_fail(ctx, SM_EINVAL, "arena not 256-byte aligned");
   char *a = (char *)dev_ptr;
@@ -201,6 +210,12 @@ extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   ctx->basis = (double *)(a + L.basis);
   ctx->tab = (double *)(a + L.tab);
   ctx->dscal = (unsigned long long *)(a + L.dscal);
+  if (ctx->cfg.precision == SM_MIXED) {
+    ctx->e32 = (float *)(a + L.e32);
+    ctx->f32 = (float *)(a + L.f32);
+    ctx->old32 = (float *)(a + L.old32);
+    ctx->gh32 = (float *)(a + L.gh32);
+  }
   SM_CK(cudaMemsetAsync(a, 0, L.total, ctx->stream));
   sm_drop_graphs(ctx);
   ctx->n_boxes = ctx->n_levels = ctx->n_leaves = 0;

@@ -3,6 +3,11 @@
 // multigrid, red-black Gauss-Seidel smoothing of the 7-point cell-centred
 // Laplacian, 8-child averaging restriction, 4-point linear prolongation,
 // coarse-to-fine ghost interpolation and an exact solve on level 0.
+//
+// The level kernels are templates on the value type: FP64 for the plain
+// solve, FP32 for the error equation of the mixed-precision form, whose
+// outer defect-correction loop (residual, accumulation, level-0 solve)
+// stays in FP64.
 #include <math.h>
 #include <string.h>
 
@@ -18,74 +23,34 @@ using namespace sm;
 // of one level: phi = (sum of 6 neighbours - h^2 f)/6 on cells with
 // (i+j+k) % 2 == color (level-global parity; box origins are multiples of
 // 8).  One block of 256 threads per box, one thread per cell of the colour.
-__global__ void __launch_bounds__(256) k_rbgs(int lo, int color, double *__restrict__ phi,
-                                              const double *__restrict__ rhs, const double *__restrict__ gh,
-                                              const int32_t *__restrict__ nbr6, Bc bc, double h2) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_rbgs(int lo, int color, T *__restrict__ phi, const T *__restrict__ rhs,
+                                              const T *__restrict__ gh, const int32_t *__restrict__ nbr6, Bc bc,
+                                              T h2, int homog) {
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   int k = t >> 5, j = (t >> 2) & 7;
   int i = ((t & 3) << 1) | ((j + k + color) & 1);
   int c = cidx(i, j, k);
   size_t base = (size_t)b * CELLS;
-  double ctr = phi[base + c];
-  double s = nb_sum(phi, nbr6, gh, b, i, j, k, ctr, bc, 0);
-  phi[base + c] = (s - h2 * rhs[base + c]) * (1.0 / 6.0);
+  T ctr = phi[base + c];
+  T s = nb_sum(phi, nbr6, gh, b, i, j, k, ctr, bc, homog);
+  phi[base + c] = (s - h2 * rhs[base + c]) * T(1.0 / 6.0);
 }
 
-// r = f - L phi on every cell of the boxes [lo, lo+grid)
-__global__ void __launch_bounds__(512) k_residual(int lo, const double *__restrict__ phi,
-                                                  const double *__restrict__ rhs, const double *__restrict__ gh,
-                                                  const int32_t *__restrict__ nbr6, Bc bc, double inv_h2,
-                                                  double *__restrict__ res) {
-  int b = lo + blockIdx.x;
-  int t = threadIdx.x;
-  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-  size_t base = (size_t)b * CELLS;
-  double p = phi[base + t];
-  double s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, 0);
-  res[base + t] = rhs[base + t] - (s - 6.0 * p) * inv_h2;
-}
-
-// Restriction from the boxes [lo, lo+grid) of level l to their parents:
-// each child box fills its 4^3 block of parent cells with the average of
-// the 8 fine cells, for phi (into phi) and for the residual (into rhs,
-// completed to the FAS right-hand side by k_fas).  64 threads per child.
-__global__ void __launch_bounds__(64) k_restrict_fas(int lo, const int32_t *__restrict__ parent,
-                                                     const int32_t *__restrict__ ijk, double *__restrict__ phi,
-                                                     const double *__restrict__ res, double *__restrict__ rhs) {
-  int b = lo + blockIdx.x;
-  int t = threadIdx.x;
-  int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
-  int P = parent[b];
-  int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
-  size_t fb = (size_t)b * CELLS;
-  double sp = 0.0, sr = 0.0;
-#pragma unroll
-  for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
-        sp += phi[fb + c];
-        sr += res[fb + c];
-      }
-  size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
-  phi[cc] = sp * 0.125;
-  rhs[cc] = sr * 0.125;
-}
-
-// plain 8-child average of one variable (FMG right-hand side, densities)
+// plain 8-child average of one or two variables (FMG right-hand side,
+// densities, potential after a mixed-precision correction)
+template <typename T>
 __global__ void __launch_bounds__(64) k_restrict1(int lo, const int32_t *__restrict__ parent,
-                                                  const int32_t *__restrict__ ijk, double *__restrict__ a,
-                                                  double *__restrict__ a2) {
+                                                  const int32_t *__restrict__ ijk, T *__restrict__ a,
+                                                  T *__restrict__ a2) {
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
   int P = parent[b];
   int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
   size_t fb = (size_t)b * CELLS;
-  double s = 0.0, s2 = 0.0;
+  T s = 0, s2 = 0;
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
@@ -97,35 +62,34 @@ __global__ void __launch_bounds__(64) k_restrict1(int lo, const int32_t *__restr
         if (a2) s2 += a2[fb + c];
       }
   size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
-  a[cc] = s * 0.125;
-  if (a2) a2[cc] = s2 * 0.125;
+  a[cc] = s * T(0.125);
+  if (a2) a2[cc] = s2 * T(0.125);
 }
 
 // After restriction into level l-1 (boxes [lo, lo+grid)): keep a copy of
 // phi, and on refined boxes complete the FAS right-hand side
 // f = avg(r_fine) + L phi_restricted.
-__global__ void __launch_bounds__(512) k_fas(int lo, double *__restrict__ phi, double *__restrict__ old,
-                                             double *__restrict__ rhs, const double *__restrict__ gh,
-                                             const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child,
-                                             Bc bc, double inv_h2) {
+template <typename T>
+__global__ void __launch_bounds__(512) k_fas(int lo, T *__restrict__ phi, T *__restrict__ old, T *__restrict__ rhs,
+                                             const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
+                                             const int32_t *__restrict__ child, Bc bc, T inv_h2, int homog) {
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   size_t base = (size_t)b * CELLS;
-  double p = phi[base + t];
+  T p = phi[base + t];
   old[base + t] = p;
   if (child[8 * b] < 0) return;
   int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-  double s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, 0);
-  rhs[base + t] += (s - 6.0 * p) * inv_h2;
+  T s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, homog);
+  rhs[base + t] += (s - T(6) * p) * inv_h2;
 }
 
 // value of a coarse-level quantity at local cell q of box Q, where q may
 // leave the box by one step along axis e (sign s): the neighbour box of the
 // same level, or the physical-boundary ghost of the cell `ctr` it left.
-template <typename F>
-__device__ __forceinline__ double coarse_at(F val, const int32_t *__restrict__ nbr6, int Q, int q[3], int e,
-                                            int s, double ctr, const Bc &bc, int homog,
-                                            unsigned long long *err) {
+template <typename T, typename F>
+__device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, int Q, int q[3], int e, int s,
+                                       T ctr, const Bc &bc, int homog, unsigned long long *err) {
   if (q[e] >= 0 && q[e] < NC) return val(Q, cidx(q[0], q[1], q[2]));
   int f = 2 * e + (s > 0);
   int Qn = __ldg(nbr6 + 6 * Q + f);
@@ -134,90 +98,61 @@ __device__ __forceinline__ double coarse_at(F val, const int32_t *__restrict__ n
     return val(Qn, cidx(q[0], q[1], q[2]));
   }
   if (Qn == -1) {
-    if (bc.type[f]) return (homog ? 0.0 : 2.0 * bc.val[f]) - ctr;
+    if (bc.type[f]) return (homog ? T(0) : T(2.0 * bc.val[f])) - ctr;
     return ctr;
   }
   atomicOr(err, 1ull);  // nesting violated: no coarse box where one must be
   return ctr;
 }
 
+// phihat = c/2 + c_t1/4 + c_t2/4 for ghost cell (u,w) of refinement face f
+// of box b (level l), from the level l-1 values of v
+template <typename T>
+__device__ __forceinline__ void cf_value(const T *__restrict__ v, T *__restrict__ gh,
+                                         const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
+                                         const int32_t *__restrict__ ijk, const Bc &bc, int homog, int b, int f,
+                                         int u, int w, unsigned long long *err) {
+  auto val = [&](int Q, int c) { return v[(size_t)Q * CELLS + c]; };
+  int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  int G[3];
+  G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
+  G[t1] = NC * ijk[3 * b + t1] + u;
+  G[t2] = NC * ijk[3 * b + t2] + w;
+  int P = parent[b];
+  int Q = nbr6[6 * P + f];
+  if (Q < 0) {
+    atomicOr(err, 2ull);
+    return;
+  }
+  int lc[3];
+  for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
+  T c = val(Q, cidx(lc[0], lc[1], lc[2]));
+  T ph = T(0.5) * c;
+  int ts[2] = {t1, t2};
+  for (int e2 = 0; e2 < 2; ++e2) {
+    int e = ts[e2];
+    int s = (G[e] & 1) ? 1 : -1;
+    int q[3] = {lc[0], lc[1], lc[2]};
+    q[e] += s;
+    ph += T(0.25) * coarse_at<T>(val, nbr6, Q, q, e, s, c, bc, homog, err);
+  }
+  gh[(size_t)(6 * b + f) * FACE + u + NC * w] = ph;
+}
+
 // Coarse interpolation values for the refinement-boundary faces of the
-// boxes [lo, lo+grid): phihat = c/2 + c_t1/4 + c_t2/4 (c the level l-1 cell
-// containing the ghost, t1/t2 its tangential neighbours on the ghost's
-// side).  64 threads per box, one per face cell.
-__global__ void __launch_bounds__(64) k_fill_cf(int lo, const double *__restrict__ v, double *__restrict__ gh,
+// boxes [lo, lo+grid), 64 threads per box, one per face cell.
+template <typename T>
+__global__ void __launch_bounds__(64) k_fill_cf(int lo, const T *__restrict__ v, T *__restrict__ gh,
                                                 const int32_t *__restrict__ nbr6,
                                                 const int32_t *__restrict__ parent,
                                                 const int32_t *__restrict__ ijk, Bc bc, int homog,
                                                 unsigned long long *err) {
   int b = lo + blockIdx.x;
   int u = threadIdx.x & 7, w = threadIdx.x >> 3;
-  auto val = [&](int Q, int c) { return v[(size_t)Q * CELLS + c]; };
   for (int f = 0; f < 6; ++f) {
     if (__ldg(nbr6 + 6 * b + f) != -2) continue;
-    int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
-    int G[3];
-    G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
-    G[t1] = NC * ijk[3 * b + t1] + u;
-    G[t2] = NC * ijk[3 * b + t2] + w;
-    int P = parent[b];
-    int Q = nbr6[6 * P + f];
-    if (Q < 0) {
-      atomicOr(err, 2ull);
-      continue;
-    }
-    int lc[3];
-    for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
-    double c = val(Q, cidx(lc[0], lc[1], lc[2]));
-    double ph = 0.5 * c;
-    int ts[2] = {t1, t2};
-    for (int e2 = 0; e2 < 2; ++e2) {
-      int e = ts[e2];
-      int s = (G[e] & 1) ? 1 : -1;
-      int q[3] = {lc[0], lc[1], lc[2]};
-      q[e] += s;
-      ph += 0.25 * coarse_at(val, nbr6, Q, q, e, s, c, bc, homog, err);
-    }
-    gh[(size_t)(6 * b + f) * FACE + u + NC * w] = ph;
+    cf_value(v, gh, nbr6, parent, ijk, bc, homog, b, f, u, w, err);
   }
-}
-
-// Prolongation into the boxes [lo, lo+grid) of level l: per fine cell
-// (c + c_sx + c_sy + c_sz)/4 of the parent cell c and its neighbours toward
-// the fine cell.  mode 0: add the correction (phi - old) of level l-1 with
-// homogeneous boundary ghosts; mode 1: overwrite with the prolonged
-// solution (FMG).
-__global__ void __launch_bounds__(512) k_prolong(int lo, int mode, double *__restrict__ phi,
-                                                 const double *__restrict__ old,
-                                                 const int32_t *__restrict__ nbr6,
-                                                 const int32_t *__restrict__ parent,
-                                                 const int32_t *__restrict__ ijk, Bc bc,
-                                                 unsigned long long *err) {
-  int b = lo + blockIdx.x;
-  int t = threadIdx.x;
-  int loc[3] = {t & 7, (t >> 3) & 7, t >> 6};
-  int P = parent[b];
-  int G[3], lc[3];
-  for (int d = 0; d < 3; ++d) {
-    G[d] = NC * ijk[3 * b + d] + loc[d];
-    lc[d] = (G[d] >> 1) - NC * ijk[3 * P + d];
-  }
-  auto val = [&](int Q, int c) {
-    size_t x = (size_t)Q * CELLS + c;
-    return mode ? phi[x] : phi[x] - old[x];
-  };
-  double c0 = val(P, cidx(lc[0], lc[1], lc[2]));
-  double sum = c0;
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    int s = (G[e] & 1) ? 1 : -1;
-    int q[3] = {lc[0], lc[1], lc[2]};
-    q[e] += s;
-    sum += coarse_at(val, nbr6, P, q, e, s, c0, bc, mode ? 0 : 1, err);
-  }
-  size_t x = (size_t)b * CELLS + t;
-  if (mode) phi[x] = 0.25 * sum;
-  else phi[x] += 0.25 * sum;
 }
 
 // Orthonormal eigenvectors and (h^2-scaled) eigenvalues of the 1-D
@@ -246,22 +181,25 @@ __global__ void k_coarse_basis(double *basis, Bc bc, int n) {
   basis[192 + a * 8 + m] = mu;
 }
 
-// Exact solve on level 0 (one 8^3 box): fold the Dirichlet boundary values
-// into the right-hand side, transform to the separable eigenbasis, divide
-// by the eigenvalues of the 7-point operator, transform back.
-__global__ void __launch_bounds__(512) k_coarse_solve(double *__restrict__ phi, const double *__restrict__ rhs,
+// Exact solve on level 0 (one 8^3 box), always in FP64: fold the Dirichlet
+// boundary values into the right-hand side (not for the homogeneous error
+// equation), transform to the separable eigenbasis, divide by the
+// eigenvalues of the 7-point operator, transform back.
+template <typename T>
+__global__ void __launch_bounds__(512) k_coarse_solve(T *__restrict__ phi, const T *__restrict__ rhs,
                                                       const double *__restrict__ basis, Bc bc, double h2,
-                                                      double inv_h2) {
+                                                      double inv_h2, int homog) {
   __shared__ double x[CELLS], y[CELLS], V[3][64], lam[3][8];
   int t = threadIdx.x;
   if (t < 192) V[t / 64][t % 64] = basis[t];
   if (t < 24) lam[t / 8][t % 8] = basis[192 + t];
   int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
-  double r = rhs[t];
-  for (int f = 0; f < 6; ++f) {
-    int q = c[f >> 1] + ((f & 1) ? 1 : -1);
-    if ((q < 0 || q >= NC) && bc.type[f]) r -= 2.0 * bc.val[f] * inv_h2;
-  }
+  double r = (double)rhs[t];
+  if (!homog)
+    for (int f = 0; f < 6; ++f) {
+      int q = c[f >> 1] + ((f & 1) ? 1 : -1);
+      if ((q < 0 || q >= NC) && bc.type[f]) r -= 2.0 * bc.val[f] * inv_h2;
+    }
   x[t] = r;
   __syncthreads();
   // forward: coefficients along x, then y, then z
@@ -288,7 +226,7 @@ __global__ void __launch_bounds__(512) k_coarse_solve(double *__restrict__ phi, 
   __syncthreads();
   acc = 0.0;
   for (int m = 0; m < NC; ++m) acc += V[2][c[2] * 8 + m] * y[cidx(c[0], c[1], m)];
-  phi[t] = acc;
+  phi[t] = (T)acc;
 }
 
 // max over leaf cells of |f - L v| into *slot (one block per leaf box)
@@ -309,30 +247,60 @@ __global__ void __launch_bounds__(512) k_resnorm(const int32_t *__restrict__ lea
   block_max_to(slot, fabs(r), red);
 }
 
+// Outer FP64 residual of the mixed-precision solve on leaf cells: the max
+// norm into *slot and the residual rounded to FP32 as the right-hand side
+// of the error equation.
+__global__ void __launch_bounds__(512) k_resid_to32(const int32_t *__restrict__ leaf,
+                                                    const int32_t *__restrict__ level,
+                                                    const double *__restrict__ v, const double *__restrict__ rhs,
+                                                    const double *__restrict__ gh,
+                                                    const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
+                                                    float *__restrict__ f32, unsigned long long *slot) {
+  __shared__ double red[16];
+  int b = leaf[blockIdx.x];
+  int t = threadIdx.x;
+  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+  size_t base = (size_t)b * CELLS;
+  double p = v[base + t];
+  double s = nb_sum(v, nbr6, gh, b, i, j, k, p, bc, 0);
+  double r = rhs[base + t] - (s - 6.0 * p) * lh.inv_h2[level[b]];
+  f32[base + t] = (float)r;
+  block_max_to(slot, fabs(r), red);
+}
+
+// FP64 accumulation of the FP32 correction on leaf cells
+__global__ void __launch_bounds__(512) k_add_corr(const int32_t *__restrict__ leaf, double *__restrict__ phi,
+                                                  const float *__restrict__ e32) {
+  size_t x = (size_t)leaf[blockIdx.x] * CELLS + threadIdx.x;
+  phi[x] += (double)e32[x];
+}
+
 // Residual and restriction fused: one block per fine box of level l
 // computes r = f - L phi for its 512 cells, then its 64 parent cells get
 // the 8-child averages of phi (into phi) and of r (into rhs, completed to
 // the FAS right-hand side by k_fas).
-__global__ void __launch_bounds__(512) k_resid_restrict(int lo, double *__restrict__ phi,
-                                                        double *__restrict__ rhs, const double *__restrict__ gh,
+template <typename T>
+__global__ void __launch_bounds__(512) k_resid_restrict(int lo, T *__restrict__ phi, T *__restrict__ rhs,
+                                                        const T *__restrict__ gh,
                                                         const int32_t *__restrict__ nbr6,
                                                         const int32_t *__restrict__ parent,
-                                                        const int32_t *__restrict__ ijk, Bc bc, double inv_h2) {
-  __shared__ double sp[CELLS], sr[CELLS];
+                                                        const int32_t *__restrict__ ijk, Bc bc, T inv_h2,
+                                                        int homog) {
+  __shared__ T sp[CELLS], sr[CELLS];
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
   size_t base = (size_t)b * CELLS;
-  double p = phi[base + t];
-  double s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, 0);
+  T p = phi[base + t];
+  T s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, homog);
   sp[t] = p;
-  sr[t] = rhs[base + t] - (s - 6.0 * p) * inv_h2;
+  sr[t] = rhs[base + t] - (s - T(6) * p) * inv_h2;
   __syncthreads();
   if (t >= 64) return;
   int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
   int P = parent[b];
   int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
-  double ap = 0.0, ar = 0.0;
+  T ap = 0, ar = 0;
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
@@ -344,19 +312,22 @@ __global__ void __launch_bounds__(512) k_resid_restrict(int lo, double *__restri
         ar += sr[c];
       }
   size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
-  phi[cc] = ap * 0.125;
-  rhs[cc] = ar * 0.125;
+  phi[cc] = ap * T(0.125);
+  rhs[cc] = ar * T(0.125);
 }
 
 // Prolongation into the boxes of level l fused with the coarse
 // interpolation values of their refinement faces (both read only level
-// l-1): mode 0 adds the correction (phi - old), mode 1 overwrites with the
-// prolonged solution (FMG); gh always interpolates phi itself.
-__global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, double *__restrict__ phi,
-                                                    const double *__restrict__ old, double *__restrict__ gh,
+// l-1): mode 0 adds the correction (phi - old) with homogeneous wall
+// ghosts, mode 1 overwrites with the prolonged solution (FMG); gh
+// interpolates phi itself.  homog: the variable is an error (homogeneous
+// wall ghosts everywhere).
+template <typename T>
+__global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, T *__restrict__ phi,
+                                                    const T *__restrict__ old, T *__restrict__ gh,
                                                     const int32_t *__restrict__ nbr6,
                                                     const int32_t *__restrict__ parent,
-                                                    const int32_t *__restrict__ ijk, Bc bc,
+                                                    const int32_t *__restrict__ ijk, Bc bc, int homog,
                                                     unsigned long long *err) {
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
@@ -372,55 +343,33 @@ __global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, double *__
       size_t x = (size_t)Q * CELLS + c;
       return mode ? phi[x] : phi[x] - old[x];
     };
-    double c0 = val(P, cidx(lc[0], lc[1], lc[2]));
-    double sum = c0;
+    T c0 = val(P, cidx(lc[0], lc[1], lc[2]));
+    T sum = c0;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       int s = (G[e] & 1) ? 1 : -1;
       int q[3] = {lc[0], lc[1], lc[2]};
       q[e] += s;
-      sum += coarse_at(val, nbr6, P, q, e, s, c0, bc, mode ? 0 : 1, err);
+      sum += coarse_at<T>(val, nbr6, P, q, e, s, c0, bc, (mode && !homog) ? 0 : 1, err);
     }
     size_t x = (size_t)b * CELLS + t;
-    if (mode) phi[x] = 0.25 * sum;
-    else phi[x] += 0.25 * sum;
+    if (mode) phi[x] = T(0.25) * sum;
+    else phi[x] += T(0.25) * sum;
   }
   if (t >= 6 * FACE) return;
   int f = t >> 6, u = t & 7, w = (t >> 3) & 7;
   if (__ldg(nbr6 + 6 * b + f) != -2) return;
-  auto pv = [&](int Q, int c) { return phi[(size_t)Q * CELLS + c]; };
-  int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
-  int G[3];
-  G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
-  G[t1] = NC * ijk[3 * b + t1] + u;
-  G[t2] = NC * ijk[3 * b + t2] + w;
-  int Q = nbr6[6 * P + f];
-  if (Q < 0) {
-    atomicOr(err, 2ull);
-    return;
-  }
-  int lc[3];
-  for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
-  double c = pv(Q, cidx(lc[0], lc[1], lc[2]));
-  double ph = 0.5 * c;
-  int ts[2] = {t1, t2};
-  for (int e2 = 0; e2 < 2; ++e2) {
-    int e = ts[e2];
-    int s = (G[e] & 1) ? 1 : -1;
-    int q[3] = {lc[0], lc[1], lc[2]};
-    q[e] += s;
-    ph += 0.25 * coarse_at(pv, nbr6, Q, q, e, s, c, bc, 0, err);
-  }
-  gh[(size_t)(6 * b + f) * FACE + u + NC * w] = ph;
+  cf_value(phi, gh, nbr6, parent, ijk, bc, homog, b, f, u, w, err);
 }
 
 // Stopping test of the device-side cycle loop: relative residual of the
-// last norm, cycle count, and the loop condition rel > tol && cycles < max.
-__global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *sc) {
+// last norm, cycle count (+inc), and the loop condition
+// rel > tol && cycles < max.
+__global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *sc, int inc) {
   double num = __longlong_as_double((long long)sc[SC_NORM]);
   double den = __longlong_as_double((long long)sc[SC_DEN]);
   double rel = den > 0.0 ? num / den : num;
-  unsigned long long c = sc[SC_CYC] + 1;
+  unsigned long long c = sc[SC_CYC] + (unsigned long long)inc;
   sc[SC_CYC] = c;
   sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
   double tol = __longlong_as_double((long long)sc[SC_TOL]);
@@ -432,12 +381,22 @@ __global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *s
 // ---------------------------------------------------------------------------
 static int lvl_n(const sm_ctx *ctx, int l) { return ctx->level_off[l + 1] - ctx->level_off[l]; }
 
+// the arrays one multigrid cycle works on
+template <typename T>
+struct MG {
+  T *phi, *rhs, *old, *gh;
+  int homog;  // error equation: homogeneous physical ghosts
+};
+
+static MG<double> mg64(sm_ctx *ctx) { return {ctx->phi, ctx->rhs, ctx->old, ctx->gh, 0}; }
+static MG<float> mg32(sm_ctx *ctx) { return {ctx->e32, ctx->f32, ctx->old32, ctx->gh32, 1}; }
+
 int sm_mg_fill_cf(sm_ctx *ctx, double *var, int l, int homog) {
   if (l <= ctx->lbase || l >= ctx->n_levels) return SM_OK;  // uniform levels: no refinement faces
   int n = lvl_n(ctx, l);
   if (n == 0) return SM_OK;
-  k_fill_cf<<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], var, ctx->gh, ctx->nbr6, ctx->parent, ctx->ijk,
-                                       ctx->bc, homog, ctx->dscal + SC_ERR);
+  k_fill_cf<double><<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], var, ctx->gh, ctx->nbr6, ctx->parent,
+                                               ctx->ijk, ctx->bc, homog, ctx->dscal + SC_ERR);
   ++ctx->n_launch;
   SM_CKL("fill_cf");
   return SM_OK;
@@ -451,29 +410,34 @@ int sm_fill_all_cf(sm_ctx *ctx, double *var) {
   return SM_OK;
 }
 
-// a = avg8 of children (and a2 likewise), finest level first
-int sm_restrict_pair(sm_ctx *ctx, double *a, double *a2) {
+template <typename T>
+static int restrict_chain(sm_ctx *ctx, T *a, T *a2) {
   for (int l = ctx->n_levels - 1; l >= 1; --l) {
     int n = lvl_n(ctx, l);
     if (!n) continue;
-    k_restrict1<<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], ctx->parent, ctx->ijk, a, a2);
+    k_restrict1<T><<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], ctx->parent, ctx->ijk, a, a2);
     ++ctx->n_launch;
   }
   SM_CKL("restrict");
   return SM_OK;
 }
 
-static int rbgs_pass(sm_ctx *ctx, int l, int color) {
-  k_rbgs<<<lvl_n(ctx, l), 256, 0, ctx->stream>>>(ctx->level_off[l], color, ctx->phi, ctx->rhs, ctx->gh,
-                                                 ctx->nbr6, ctx->bc, ctx->lh.h2[l]);
+// a = avg8 of children (and a2 likewise), finest level first
+int sm_restrict_pair(sm_ctx *ctx, double *a, double *a2) { return restrict_chain(ctx, a, a2); }
+
+template <typename T>
+static int rbgs_pass(sm_ctx *ctx, const MG<T> &m, int l, int color) {
+  k_rbgs<T><<<lvl_n(ctx, l), 256, 0, ctx->stream>>>(ctx->level_off[l], color, m.phi, m.rhs, m.gh, ctx->nbr6,
+                                                    ctx->bc, (T)ctx->lh.h2[l], m.homog);
   ++ctx->n_launch;
   return SM_OK;
 }
 
-static int smooth(sm_ctx *ctx, int l, int nu) {
+template <typename T>
+static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu) {
   if (!lvl_n(ctx, l)) return SM_OK;
   for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color) rbgs_pass(ctx, l, color);
+    for (int color = 0; color < 2; ++color) rbgs_pass(ctx, m, l, color);
   SM_CKL("rbgs");
   return SM_OK;
 }
@@ -488,20 +452,22 @@ static int ensure_basis(sm_ctx *ctx) {
   return SM_OK;
 }
 
-static int coarse_solve(sm_ctx *ctx) {
+template <typename T>
+static int coarse_solve(sm_ctx *ctx, const MG<T> &m) {
   int st = ensure_basis(ctx);
   if (st) return st;
-  k_coarse_solve<<<1, 512, 0, ctx->stream>>>(ctx->phi, ctx->rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
-                                             ctx->lh.inv_h2[0]);
+  k_coarse_solve<T><<<1, 512, 0, ctx->stream>>>(m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
+                                                ctx->lh.inv_h2[0], m.homog);
   ++ctx->n_launch;
   SM_CKL("coarse solve");
   return SM_OK;
 }
 
-static int prolong_cf(sm_ctx *ctx, int l, int mode) {
-  k_prolong_cf<<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], mode, ctx->phi, ctx->old, ctx->gh,
-                                                       ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
-                                                       ctx->dscal + SC_ERR);
+template <typename T>
+static int prolong_cf(sm_ctx *ctx, const MG<T> &m, int l, int mode) {
+  k_prolong_cf<T><<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], mode, m.phi, m.old, m.gh,
+                                                          ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, m.homog,
+                                                          ctx->dscal + SC_ERR);
   ++ctx->n_launch;
   SM_CKL("prolong");
   return SM_OK;
@@ -509,27 +475,43 @@ static int prolong_cf(sm_ctx *ctx, int l, int mode) {
 
 // FAS V-cycle with `top` as finest level.  On entry the coarse
 // interpolation values gh of every level <= top must match the current
-// potential of the level below (the solve prologue and every up-sweep
-// leave them so); the down-sweep changes no level below the one it smooths
+// values of the level below (the solve prologue and every up-sweep leave
+// them so); the down-sweep changes no level below the one it smooths
 // before that level is visited again, so it needs no refill.
-static int vcycle(sm_ctx *ctx, int top) {
+template <typename T>
+static int vcycle(sm_ctx *ctx, const MG<T> &m, int top) {
   int st;
   for (int l = top; l >= 1; --l) {
-    if ((st = smooth(ctx, l, ctx->cfg.nu1))) return st;
-    k_resid_restrict<<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], ctx->phi, ctx->rhs, ctx->gh,
-                                                             ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
-                                                             ctx->lh.inv_h2[l]);
+    if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
+    k_resid_restrict<T><<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], m.phi, m.rhs, m.gh,
+                                                                ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
+                                                                (T)ctx->lh.inv_h2[l], m.homog);
     ++ctx->n_launch;
-    k_fas<<<lvl_n(ctx, l - 1), 512, 0, ctx->stream>>>(ctx->level_off[l - 1], ctx->phi, ctx->old, ctx->rhs,
-                                                      ctx->gh, ctx->nbr6, ctx->child, ctx->bc,
-                                                      ctx->lh.inv_h2[l - 1]);
+    k_fas<T><<<lvl_n(ctx, l - 1), 512, 0, ctx->stream>>>(ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+                                                         ctx->nbr6, ctx->child, ctx->bc,
+                                                         (T)ctx->lh.inv_h2[l - 1], m.homog);
     ++ctx->n_launch;
     SM_CKL("vcycle down");
   }
-  if ((st = coarse_solve(ctx))) return st;
+  if ((st = coarse_solve(ctx, m))) return st;
   for (int l = 1; l <= top; ++l) {
-    if ((st = prolong_cf(ctx, l, 0))) return st;
-    if ((st = smooth(ctx, l, ctx->cfg.nu2))) return st;
+    if ((st = prolong_cf(ctx, m, l, 0))) return st;
+    if ((st = smooth(ctx, m, l, ctx->cfg.nu2))) return st;
+  }
+  return SM_OK;
+}
+
+// FMG ladder: restrict f, exact level-0 solve, then for each finer level
+// prolong the solution (and its interpolation values) and run one V-cycle
+// with that level on top
+template <typename T>
+static int fmg_ladder(sm_ctx *ctx, const MG<T> &m) {
+  int st;
+  if ((st = restrict_chain<T>(ctx, m.rhs, nullptr))) return st;
+  if ((st = coarse_solve(ctx, m))) return st;
+  for (int l = 1; l < ctx->n_levels; ++l) {
+    if ((st = prolong_cf(ctx, m, l, 1))) return st;
+    if ((st = vcycle(ctx, m, l))) return st;
   }
   return SM_OK;
 }
@@ -542,6 +524,39 @@ static int leaf_norm(sm_ctx *ctx, double *v, int slot) {
   ++ctx->n_launch;
   SM_CKL("resnorm");
   return SM_OK;
+}
+
+// outer FP64 residual of the mixed form: norm into SC_NORM, f32 = (float) r
+static int leaf_resid32(sm_ctx *ctx) {
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_NORM, 0, sizeof(unsigned long long), ctx->stream));
+  k_resid_to32<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->level, ctx->phi, ctx->rhs, ctx->gh,
+                                                       ctx->nbr6, ctx->bc, ctx->lh, ctx->f32,
+                                                       ctx->dscal + SC_NORM);
+  ++ctx->n_launch;
+  SM_CKL("resid32");
+  return SM_OK;
+}
+
+// One defect-correction step of the mixed form, after leaf_resid32: solve
+// the error equation A e = r in FP32 from e = 0 (one V-cycle, or the FMG
+// ladder for the first step of an FMG solve), add e to phi in FP64 on leaf
+// cells, re-average refined boxes, refresh the coarse interpolation values
+// and the outer residual.
+static int mixed_correction(sm_ctx *ctx, int ladder) {
+  int st;
+  size_t nc = (size_t)CELLS * ctx->n_boxes;
+  SM_CK(cudaMemsetAsync(ctx->e32, 0, sizeof(float) * nc, ctx->stream));
+  SM_CK(cudaMemsetAsync(ctx->gh32, 0, sizeof(float) * 6 * FACE * (size_t)ctx->n_boxes, ctx->stream));
+  MG<float> m = mg32(ctx);
+  if (ladder) st = fmg_ladder(ctx, m);
+  else st = vcycle(ctx, m, ctx->n_levels - 1);
+  if (st) return st;
+  k_add_corr<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->phi, ctx->e32);
+  ++ctx->n_launch;
+  SM_CKL("add correction");
+  if ((st = restrict_chain<double>(ctx, ctx->phi, nullptr))) return st;
+  if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+  return leaf_resid32(ctx);
 }
 
 static int read_scalars(sm_ctx *ctx) {
@@ -580,30 +595,61 @@ static int check_ready(sm_ctx *ctx) {
   return SM_OK;
 }
 
-// FMG part before the cycle loop: restrict f, exact level-0 solve, then for
-// each finer level prolong the solution (and its interpolation values) and
-// run one V-cycle with that level on top
-static int fmg_ladder(sm_ctx *ctx) {
+// ---- solve bodies shared by the graph and the direct paths ----------------
+//
+// kind 0: FP64 solve (warm start), 1: FP64 FMG, 2: mixed solve, 3: mixed FMG.
+// prefix(): work before the cycle loop; for kinds 1 and 3 it ends with the
+// residual of the FMG result.  body(): one loop iteration up to and
+// including the residual it leaves in SC_NORM.
+
+static int solve_prefix(sm_ctx *ctx, int kind) {
   int st;
-  if ((st = sm_restrict_pair(ctx, ctx->rhs, nullptr))) return st;
-  if ((st = coarse_solve(ctx))) return st;
-  for (int l = 1; l < ctx->n_levels; ++l) {
-    if ((st = prolong_cf(ctx, l, 1))) return st;
-    if ((st = vcycle(ctx, l))) return st;
+  switch (kind) {
+    case 0:
+      return solve_prologue(ctx);
+    case 1:
+      if ((st = solve_prologue(ctx))) return st;
+      if ((st = fmg_ladder(ctx, mg64(ctx)))) return st;
+      return leaf_norm(ctx, ctx->phi, SC_NORM);
+    case 2:
+      if ((st = solve_prologue(ctx))) return st;
+      return leaf_resid32(ctx);
+    default:
+      // phi = 0: its outer residual is the denominator itself
+      SM_CK(cudaMemsetAsync(ctx->phi, 0, sizeof(double) * CELLS * (size_t)ctx->n_boxes, ctx->stream));
+      if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+      SM_CK(cudaMemsetAsync(ctx->dscal + SC_CYC, 0, sizeof(unsigned long long), ctx->stream));
+      if ((st = leaf_resid32(ctx))) return st;
+      SM_CK(cudaMemcpyAsync(ctx->dscal + SC_DEN, ctx->dscal + SC_NORM, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+      return mixed_correction(ctx, 1);
   }
-  return SM_OK;
+}
+
+static int solve_body(sm_ctx *ctx, int kind) {
+  int st;
+  if (kind >= 2) return mixed_correction(ctx, 0);
+  if ((st = vcycle(ctx, mg64(ctx), ctx->n_levels - 1))) return st;
+  return leaf_norm(ctx, ctx->phi, SC_NORM);
 }
 
 // ---- graph-captured solves with a device-side cycle loop ------------------
 
+static sm_graph *graph_of(sm_ctx *ctx, int kind) {
+  switch (kind) {
+    case 0: return &ctx->g_solve;
+    case 1: return &ctx->g_fmg;
+    case 2: return &ctx->g_solve32;
+    default: return &ctx->g_fmg32;
+  }
+}
+
 void sm_drop_graphs(sm_ctx *ctx) {
-  for (auto *g : {&ctx->g_solve, &ctx->g_fmg}) {
+  for (auto *g : {&ctx->g_solve, &ctx->g_fmg, &ctx->g_solve32, &ctx->g_fmg32}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     g->exec = nullptr;
   }
 }
-
-static bool use_graphs(const sm_ctx *ctx) { return ctx->graphs; }
 
 static int end_captures(sm_ctx *ctx, cudaStream_t saved, int st) {
   cudaGraph_t tmp = nullptr;
@@ -622,11 +668,10 @@ static int end_captures(sm_ctx *ctx, cudaStream_t saved, int st) {
   return st;
 }
 
-// Capture [prologue] + WHILE(cond){ V-cycle; norm; check } into an
-// executable graph.  fmg: the prologue is the FMG ladder followed by a norm
-// and a check (which sets the first loop condition); otherwise the loop
-// body runs at least once.
-static int capture_solve(sm_ctx *ctx, int fmg, sm_graph *out) {
+// Capture prefix + WHILE(cond){ body; check } into an executable graph.
+// FMG kinds check once after the prefix (the FMG result counts as cycle
+// 1); the others run the body at least once.
+static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   cudaStream_t saved = ctx->stream;
   if (!ctx->cap) SM_CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
   if (!ctx->cap2) SM_CK(cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking));
@@ -634,6 +679,7 @@ static int capture_solve(sm_ctx *ctx, int fmg, sm_graph *out) {
     int st = ensure_basis(ctx);  // once per context, outside any graph
     if (st) return st;
   }
+  const int fmg = kind == 1 || kind == 3;
   SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
   ctx->stream = ctx->cap;
   int st = SM_OK;
@@ -653,11 +699,9 @@ static int capture_solve(sm_ctx *ctx, int fmg, sm_graph *out) {
   if (cudaGraphConditionalHandleCreate(&h, g, fmg ? 0u : 1u, cudaGraphCondAssignDefault) != cudaSuccess)
     return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "conditional handle"));
   n0 = ctx->n_launch;
-  if ((st = solve_prologue(ctx))) return end_captures(ctx, saved, st);
+  if ((st = solve_prefix(ctx, kind))) return end_captures(ctx, saved, st);
   if (fmg) {
-    if ((st = fmg_ladder(ctx))) return end_captures(ctx, saved, st);
-    if ((st = leaf_norm(ctx, ctx->phi, SC_NORM))) return end_captures(ctx, saved, st);
-    k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal);
+    k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal, 1);
     ++ctx->n_launch;
   }
   out->prefix_launches = ctx->n_launch - n0;
@@ -678,9 +722,8 @@ static int capture_solve(sm_ctx *ctx, int fmg, sm_graph *out) {
     return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "body capture"));
   ctx->stream = ctx->cap2;
   n0 = ctx->n_launch;
-  if ((st = vcycle(ctx, ctx->n_levels - 1))) return end_captures(ctx, saved, st);
-  if ((st = leaf_norm(ctx, ctx->phi, SC_NORM))) return end_captures(ctx, saved, st);
-  k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal);
+  if ((st = solve_body(ctx, kind))) return end_captures(ctx, saved, st);
+  k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal, 1);
   ++ctx->n_launch;
   out->body_launches = ctx->n_launch - n0;
   if (cudaStreamEndCapture(ctx->cap2, &body) != cudaSuccess)
@@ -701,9 +744,10 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
   int st;
   int c = 0;
   double rel = 0.0;
-  if (use_graphs(ctx)) {
-    sm_graph *g = fmg ? &ctx->g_fmg : &ctx->g_solve;
-    if (!g->exec && (st = capture_solve(ctx, fmg, g))) return st;
+  const int kind = (ctx->cfg.precision == SM_MIXED ? 2 : 0) + (fmg ? 1 : 0);
+  if (ctx->graphs) {
+    sm_graph *g = graph_of(ctx, kind);
+    if (!g->exec && (st = capture_solve(ctx, kind, g))) return st;
     ctx->hscal[SC_TOL] = tol;
     unsigned long long mc = (unsigned long long)max_cycles;
     memcpy(&ctx->hscal[SC_MAXC], &mc, sizeof mc);
@@ -717,18 +761,23 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
     rel = ctx->hscal[SC_REL];
     ctx->n_launch += g->prefix_launches + g->body_launches * (long long)(fmg ? c - 1 : c);
   } else {
-    if ((st = solve_prologue(ctx))) return st;
+    if ((st = ensure_basis(ctx))) return st;
+    if ((st = solve_prefix(ctx, kind))) return st;
+    bool go = true;
     if (fmg) {
-      if ((st = fmg_ladder(ctx))) return st;
       c = 1;
-      if ((st = rel_residual(ctx, &rel))) return st;
+      if ((st = read_scalars(ctx))) return st;
+      double num = ctx->hscal[SC_NORM], den = ctx->hscal[SC_DEN];
+      rel = den > 0.0 ? num / den : num;
+      go = rel > tol && c < max_cycles;
     }
-    if (!fmg || (rel > tol && c < max_cycles)) {
-      do {
-        if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
-        ++c;
-        if ((st = rel_residual(ctx, &rel))) return st;
-      } while (rel > tol && c < max_cycles);
+    while (go) {
+      if ((st = solve_body(ctx, kind))) return st;
+      ++c;
+      if ((st = read_scalars(ctx))) return st;
+      double num = ctx->hscal[SC_NORM], den = ctx->hscal[SC_DEN];
+      rel = den > 0.0 ? num / den : num;
+      go = rel > tol && c < max_cycles;
     }
   }
   if (cycles) *cycles = c;
@@ -747,9 +796,10 @@ extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
   int st = check_ready(ctx);
   if (st) return st;
   if (n_cycles < 0) return SM_EINVAL;
+  if ((st = ensure_basis(ctx))) return st;
   if ((st = solve_prologue(ctx))) return st;
   for (int c = 0; c < n_cycles; ++c)
-    if ((st = vcycle(ctx, ctx->n_levels - 1))) return st;
+    if ((st = vcycle(ctx, mg64(ctx), ctx->n_levels - 1))) return st;
   double rel = 0.0;
   if ((st = rel_residual(ctx, &rel))) return st;
   if (rel_res) *rel_res = rel;
@@ -791,10 +841,11 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   ctx->stream = ctx->cap;
   long long n = 0;
   double bytes = 0.0;
+  MG<double> m = mg64(ctx);
   for (int r = 0; r < reps; ++r)
     for (int l = top; l >= 1; --l)
       for (int color = 0; color < 2; ++color) {
-        rbgs_pass(ctx, l, color);
+        rbgs_pass(ctx, m, l, color);
         ++n;
         bytes += (double)lvl_n(ctx, l) * CELLS * 16.0;
       }

@@ -78,6 +78,9 @@ struct sm_ctx {
   double *ibuf[3] = {nullptr, nullptr, nullptr};  // ion density buffers
   int ncur = 0;                                   // current density buffer
   double *gh = nullptr;      // [max_boxes][6][64] coarse interpolation values
+  // FP32 error-equation arrays of the mixed-precision solve
+  float *e32 = nullptr, *f32 = nullptr, *old32 = nullptr;  // [max_boxes][512]
+  float *gh32 = nullptr;                                    // [max_boxes][6][64]
   double *cflux = nullptr;   // [max_boxes][6][64] fine-side refinement fluxes
   double *basis = nullptr;   // level-0 eigenbasis: [3][64] vectors, [3][8] eigenvalues
   double *tab = nullptr;     // [3][4096] coefficient table
@@ -99,7 +102,7 @@ struct sm_ctx {
   // captured solves (invalidated when the octree changes)
   bool graphs = true;
   cudaStream_t cap = nullptr, cap2 = nullptr;
-  sm_graph g_solve, g_fmg;
+  sm_graph g_solve, g_fmg, g_solve32, g_fmg32;
 
   std::string err;
 };

@@ -1,0 +1,124 @@
+"""Mixed-precision form: FP32 smoothing, restriction and prolongation of the
+error equation inside an FP64 defect-correction loop (FP64 residual,
+accumulation and level-0 solve).  The reference is the FP64 oracle
+converged to 1e-12, so only the algebraic error of the form is measured;
+the bound is 1e-6 relative on the potential at a converged residual of
+1e-8 (the error of |E| is reported beside it)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import EPS0, Q, gpu_mesh, load_inputs, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def pkg():
+    import paper_1708_08434_gb300 as p
+    return p
+
+
+def mixed_pair(name):
+    dom, st = synth.workload(name)
+    o = oracle.build_mesh(dom, st)
+    g = gpu_mesh(dom, st, precision=pkg().MIXED)
+    return dom, st, o, g
+
+
+@pytest.mark.parametrize("name", ["uniform64", "streamer_small"])
+def test_mixed_fmg_error_against_fp64_oracle(name):
+    dom, st, o, g = mixed_pair(name)
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    o.fmg(1e-12, 60)
+    rc, rel, cyc = g.fmg(1e-8, 40)
+    assert rc == 0 and rel <= 1e-8
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    e_phi = rel_err(g.download(p.PHI)[leaf], o.get(oracle.PHI)[leaf])
+    o.compute_field()
+    g.compute_field()
+    e_field = rel_err(g.download(p.EMAG)[leaf], o.get(oracle.EMAG)[leaf])
+    print("%s mixed: cycles %d rel %.2e  |dphi| %.2e  |d|E|| %.2e" % (name, cyc, rel, e_phi, e_field))
+    assert e_phi <= TOL_MIXED
+    assert e_field <= 1e-4
+
+
+def test_mixed_residual_is_the_fp64_residual():
+    """The tolerance is met by the FP64 composite residual: the oracle,
+    handed the mixed solution, computes the same relative residual."""
+    dom, st, o, g = mixed_pair("streamer_small")
+    load_inputs(dom, st, o, g)
+    rc, rel, cyc = g.fmg(1e-9, 40)
+    assert rc == 0
+    p = pkg()
+    o.set(oracle.PHI, g.download(p.PHI))
+    assert o.rel_residual() == pytest.approx(rel, rel=1e-6)
+
+
+def test_mixed_warm_solve_and_heun_step():
+    dom, st, o, g = mixed_pair("streamer_small")
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    o.fmg(1e-12, 60)
+    g.fmg(1e-8, 40)
+    o.compute_field()
+    g.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+    ro = o.advance(dt, Q, EPS0, 1e-12, 60)
+    rg = g.advance(dt, Q, EPS0, 1e-8, 40)
+    assert rg[0] == 0
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    for vo, vg in ((oracle.PHI, p.PHI), (oracle.NE, p.NE), (oracle.NI, p.NI)):
+        e = rel_err(g.download(vg)[leaf], o.get(vo)[leaf])
+        assert e <= TOL_MIXED, (vo, e)
+    assert rg[1] == pytest.approx(ro[1], rel=1e-5)
+
+
+def test_mixed_graph_and_direct_identical():
+    dom, st = synth.workload("streamer_small")
+    p = pkg()
+    out = []
+    for graphs in (True, False):
+        g = gpu_mesh(dom, st, precision=p.MIXED)
+        g.set_graphs(graphs)
+        t = g.tables()
+        ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+        g.upload(p.NE, ne); g.upload(p.NI, ni)
+        g.charge_rhs(Q, EPS0)
+        r1 = g.fmg(1e-8, 30)
+        r2 = g.solve(1e-10, 30)
+        out.append((r1, r2, g.download(p.PHI)))
+        g.close()
+    (a1, a2, pa), (b1, b2, pb) = out
+    assert a1 == b1 and a2 == b2
+    assert np.array_equal(pa, pb)
+
+
+@pytest.mark.slow
+def test_mixed_full_size_streamer8_residual():
+    """The 8-level workload (1.7e7 leaf cells): mixed FMG to 1e-8; the oracle
+    evaluates the FP64 composite residual of the GPU potential."""
+    dom, st = synth.workload("streamer8")
+    g = gpu_mesh(dom, st, max_boxes=1 << 16, precision=pkg().MIXED)
+    o = oracle.build_mesh(dom, st)
+    t = o.tables()
+    assert g.n_leaves * 512 > 1.5e7
+    load_inputs(dom, st, o, g, t)
+    rc, rel, cyc = g.fmg(1e-8, 40)
+    assert rc == 0
+    o.set(oracle.PHI, g.download(pkg().PHI))
+    assert o.rel_residual() <= 1.01e-8
