@@ -34,6 +34,7 @@ TOL = 1e-8
 MAX_CYCLES = 40
 SOLVES_PER_STEP = 3
 L2_BYTES = 129 * 2 ** 20
+NO_GRAPHS = False
 
 
 def parse():
@@ -45,9 +46,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "vcycle"],
-                    help="vcycle: build the workload, then only run --steps V-cycles "
-                         "(small, fixed launch sequence for ncu captures)")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the same kernels from the host instead of CUDA graphs "
+                         "(profilers cannot see kernels inside conditional graph nodes)")
+    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch"],
+                    help="vcycle: build the workload, then only run --steps V-cycles; "
+                         "batch: only the batched solves, --steps solves with the default "
+                         "schedule (small, fixed launch sequences for ncu captures)")
     return ap.parse_args()
 
 
@@ -128,12 +134,30 @@ def build_gpu_case(precision=0):
     import paper_1708_08434_gb300 as pkg
     dom, st = synth.workload(WORKLOAD)
     g = pkg.Solver(dom, max_boxes=8192, precision=precision)
+    if NO_GRAPHS:
+        g.set_graphs(False)
     g.build_octree()
     synth.refine_all(dom, st, g.level_ijk, g.refine_level)
     t = g.tables()
     ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
     g.set_table(synth.coefficient_table())
     return dom, st, g, t, ne, ni
+
+
+def run_batch_only(args):
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    b, _ = make_batch_workload()
+    if args.no_graphs:
+        b.set_graphs(False)
+    for _ in range(args.steps):
+        b.phi.zero_()
+        rc, cyc, rel = b.solve(TOL, MAX_CYCLES)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "batch", "solves": args.steps, "max_corrections": int(cyc.max())}), flush=True)
+    b.close()
 
 
 def run_gpu(args):
@@ -273,6 +297,7 @@ def run_gpu(args):
                  "speedup_vs_fp64": round(ms / mms, 3),
                  "dtype": "f32 error equation, f64 residual/accumulation/level-0 solve"}
         gm.close()
+    batched = None if args.no_batch else bench_batch(args, dev, world)
     steps = args.steps
     solves = SOLVES_PER_STEP * steps * world
     value = solves / (ms * 1e-3)
@@ -296,6 +321,7 @@ def run_gpu(args):
         "clocks": clocks,
         "roofline": roof,
         "mixed_precision": mixed,
+        "batched": batched,
     }
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline()
@@ -305,6 +331,64 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def make_batch_workload():
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    sides = synth.batch_sizes(256)
+    b = pkg.Batch(sides, 1.0, (0, 0, 0, 0, 1, 1), (0, 0, 0, 0, 0, 1.0))
+    blobs = synth.batch_blobs(len(sides))
+    for s, n in enumerate(sides):
+        b.grid(b.rhs, s).copy_(torch.from_numpy(-synth.blob_rho(int(n), blobs[s])))
+    return b, sides
+
+
+def bench_batch(args, dev, world):
+    """The batched form: 256 independent unit-cube solves of 32^3..128^3
+    cells (log-uniform sizes, 1-8 Gaussian charge blobs each), autotuned,
+    solved from phi = 0 to 1e-8; value = solves per second."""
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    if world > 1:
+        import torch.distributed as dist
+    b, sides = make_batch_workload()
+    if NO_GRAPHS:
+        b.set_graphs(False)
+    shape, gmult, tune_ms = b.tune(2)
+    for _ in range(args.warmup):
+        b.phi.zero_()
+        b.solve(TOL, MAX_CYCLES)
+    total, cycles = 0.0, 0
+    l0 = b.info()[2]
+    for _ in range(args.steps):
+        b.phi.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        rc, cyc, rel = b.solve(TOL, MAX_CYCLES)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+        assert rc == 0, rc
+        total += e0.elapsed_time(e1)
+        cycles += int(cyc.max())
+    if world > 1:
+        tt = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    cells, levels, launches = b.info()
+    res = {"value": round(256 * args.steps * world / (total * 1e-3), 2), "unit": "solves/s",
+           "ms_per_batch": round(total / args.steps, 3), "solves_per_batch": 256, "cells": cells,
+           "max_corrections": cycles / args.steps,
+           "gcells_corrections_per_s": round(cells * cycles * world / (total * 1e-3) / 1e9, 3),
+           "schedule": {"tile": pkg.Batch.SHAPES[shape], "blocks_per_sm": gmult, "tuned_ms": round(tune_ms, 3)},
+           "gpu_launches": launches - l0, "dtype": "f32 cycles, f64 residual/accumulation/coarsest solve",
+           "workload": "256 unit-cube solves, sides 8*round(32*4^u/8), phi=0/1 on z plates"}
+    b.close()
+    return res
 
 
 def oracle_case():
@@ -367,9 +451,13 @@ def run_reference(args):
 
 
 def main():
+    global NO_GRAPHS
     args = parse()
+    NO_GRAPHS = args.no_graphs
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batch":
+        run_batch_only(args)
     else:
         run_gpu(args)
 

@@ -246,6 +246,51 @@ int sm_set_graphs(sm_ctx *ctx, int enable);
  * (diagnostics: lets a caller count device launches inside a region). */
 int sm_launch_count(const sm_ctx *ctx, long long *n);
 
+/* ---- batched form: many independent uniform solves ------------------------ */
+
+/* Build form (not in the paper): n_solves independent Poisson problems
+ * L phi = f with the 7-point operator and ghost rules of the octree solve,
+ * each on a uniform grid of cells_per_side[s]^3 cells covering a cube of
+ * side `length`, all with the same boundary types/values (bc_type, bc_val
+ * as in sm_domain).  Each grid is coarsened by halving its side while it is
+ * even and larger than 8; the coarsest side must be <= 16 (SM_EINVAL
+ * otherwise); it is solved exactly in FP64.  Cycles are FP32
+ * correction-scheme V(nu1,nu2) cycles on the error equation inside a
+ * per-solve FP64 defect-correction loop; every level of all solves is one
+ * grid-stride launch over a tile work list; a batched solve is one CUDA
+ * graph whose loop runs on the device; converged solves are masked out.
+ * Memory: sm_batch_arena_size / sm_batch_bind_arena as for sm_ctx.
+ * Arrays (device, through sm_batch_ptrs): phi and rhs, FP64, the grids of
+ * all solves one after another at the returned offsets, cell (x,y,z) of
+ * solve s at offsets[s] + x + N (y + N z). */
+typedef struct sm_batch sm_batch;
+int sm_batch_create(sm_batch **out, int n_solves, const int *cells_per_side, double length, const int *bc_type,
+                    const double *bc_val, int nu1, int nu2, void *stream);
+int sm_batch_destroy(sm_batch *b);
+int sm_batch_arena_size(const sm_batch *b, size_t *bytes);
+int sm_batch_bind_arena(sm_batch *b, void *dev_ptr, size_t bytes);
+/* device pointers of phi and rhs and the per-solve offsets (host array of
+ * n_solves, may be NULL) */
+int sm_batch_ptrs(const sm_batch *b, double **phi, double **rhs, long long *offsets);
+/* Solve every problem from its current phi until its relative residual
+ * max|f - L phi| / max|f - L 0| <= tol or max_cycles corrections.  Out
+ * (host arrays of n_solves, may be NULL): corrections and final relative
+ * residual per solve.  SM_ENOCONV if a solve missed tol. Synchronises. */
+int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycles, double *rel_res);
+/* Autotuner: times `iters` corrections from phi = 0 for every candidate
+ * tile shape (8x8x8, 16x8x4, 32x4x4, 32x8x2 cells) and grid size
+ * (2, 4, 8 blocks per SM), keeps the fastest; leaves phi = 0.  Out: the
+ * chosen shape index, blocks per SM and its time in ms. */
+int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult, double *best_ms);
+int sm_batch_set_schedule(sm_batch *b, int shape, int grid_mult);
+/* Solves as one CUDA graph with the loop on the device (default) or as the
+ * same launches driven from the host (for profilers that cannot see into
+ * conditional graph nodes). */
+int sm_batch_set_graphs(sm_batch *b, int enable);
+/* total cells (finest grids), deepest level count, kernels launched so far */
+int sm_batch_info(const sm_batch *b, long long *cells, int *levels_max, long long *launches);
+const char *sm_batch_last_error(const sm_batch *b);
+
 /* ---- allocation-free entry point ---------------------------------------- */
 
 /* No counterpart in the paper: a service for callers that cannot allocate

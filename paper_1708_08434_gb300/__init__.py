@@ -57,7 +57,11 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs",
-           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc"]
+           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc",
+           "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
+           "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
+           "sm_batch_set_graphs",
+           "sm_batch_last_error"]
 
 
 def library_path() -> str:
@@ -101,12 +105,23 @@ def load():
         "sm_set_graphs": [P, I],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
+        "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
+        "sm_batch_destroy": [P],
+        "sm_batch_arena_size": [P, C.POINTER(C.c_size_t)],
+        "sm_batch_bind_arena": [P, P, C.c_size_t],
+        "sm_batch_ptrs": [P, C.POINTER(P), C.POINTER(P), P],
+        "sm_batch_solve": [P, D, I, P, P],
+        "sm_batch_tune": [P, I, pI, pI, pD],
+        "sm_batch_set_schedule": [P, I, I],
+        "sm_batch_set_graphs": [P, I],
+        "sm_batch_info": [P, C.POINTER(C.c_longlong), pI, C.POINTER(C.c_longlong)],
+        "sm_batch_last_error": [P],
         "sm_last_error": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = C.c_char_p if name == "sm_last_error" else C.c_int
+        fn.restype = C.c_char_p if name.endswith("last_error") else C.c_int
     _lib = lib
     return lib
 
@@ -323,3 +338,89 @@ class Solver:
         n = C.c_longlong()
         self._ck(self._lib.sm_launch_count(self._h, C.byref(n)))
         return n.value
+
+
+class Batch:
+    """Many independent uniform-grid Poisson solves advanced together."""
+
+    SHAPES = ((8, 8, 8), (16, 8, 4), (32, 4, 4), (32, 8, 2))
+
+    def __init__(self, sides, length=1.0, bc_type=(0, 0, 0, 0, 1, 1), bc_val=(0, 0, 0, 0, 0, 1.0),
+                 nu1=2, nu2=2, stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise SmError(SM_ECUDA, "no CUDA device")
+        self._lib, self.torch = lib, torch
+        self.sides = np.ascontiguousarray(sides, dtype=np.int32)
+        self.n = len(self.sides)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = lib.sm_batch_create(C.byref(h), self.n, _hp(self.sides), float(length),
+                                 (C.c_int * 6)(*bc_type), (C.c_double * 6)(*bc_val), nu1, nu2,
+                                 C.c_void_p(self.stream.cuda_stream))
+        if rc != SM_OK:
+            raise SmError(rc, "sm_batch_create failed")
+        self._h = h
+        size = C.c_size_t()
+        self._ck(lib.sm_batch_arena_size(h, C.byref(size)))
+        self.arena = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+        self._ck(lib.sm_batch_bind_arena(h, C.c_void_p(self.arena.data_ptr()), size.value))
+        phi, rhs = C.c_void_p(), C.c_void_p()
+        self.offsets = np.zeros(self.n, np.int64)
+        self._ck(lib.sm_batch_ptrs(h, C.byref(phi), C.byref(rhs), _hp(self.offsets)))
+        total = int(np.sum(self.sides.astype(np.int64) ** 3))
+        self.cells = total
+        self.phi = self._view(phi.value, total)
+        self.rhs = self._view(rhs.value, total)
+
+    def _ck(self, rc):
+        if rc != SM_OK:
+            raise SmError(rc, self._lib.sm_batch_last_error(self._h).decode())
+        return rc
+
+    def _view(self, ptr, count):
+        off = ptr - self.arena.data_ptr()
+        return self.arena[off:off + 8 * count].view(self.torch.float64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.sm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def grid(self, t, s):
+        """Solve s's grid [z][y][x] as a view of flat device array t."""
+        n = int(self.sides[s])
+        o = int(self.offsets[s])
+        return t[o:o + n ** 3].view(n, n, n)
+
+    def solve(self, tol=1e-8, max_cycles=50, allow_noconv=True):
+        cyc = np.zeros(self.n, np.int32)
+        rel = np.zeros(self.n, np.float64)
+        rc = self._lib.sm_batch_solve(self._h, tol, max_cycles, _hp(cyc), _hp(rel))
+        if rc != SM_OK and not (allow_noconv and rc == SM_ENOCONV):
+            self._ck(rc)
+        return rc, cyc, rel
+
+    def tune(self, iters=3):
+        s, g, ms = C.c_int(), C.c_int(), C.c_double()
+        self._ck(self._lib.sm_batch_tune(self._h, iters, C.byref(s), C.byref(g), C.byref(ms)))
+        return s.value, g.value, ms.value
+
+    def set_schedule(self, shape, grid_mult):
+        self._ck(self._lib.sm_batch_set_schedule(self._h, shape, grid_mult))
+
+    def set_graphs(self, enable: bool):
+        self._ck(self._lib.sm_batch_set_graphs(self._h, int(enable)))
+
+    def info(self):
+        c, lv, nl = C.c_longlong(), C.c_int(), C.c_longlong()
+        self._ck(self._lib.sm_batch_info(self._h, C.byref(c), C.byref(lv), C.byref(nl)))
+        return c.value, lv.value, nl.value

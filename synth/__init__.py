@@ -306,3 +306,41 @@ def uniform_level_ijk(level: int) -> np.ndarray:
     """All box coordinates of a full uniform level (x fastest), test helper."""
     n = 1 << level
     return np.array([(i, j, k) for k, j, i in itertools.product(range(n), repeat=3)], dtype=np.int64)
+
+
+# --------------------------------------------------------------------------
+# batched independent uniform solves (unit cube, phi = 0 at z = 0 and 1 at
+# z = 1, Neumann sides; rho = sum of Gaussian blobs)
+# --------------------------------------------------------------------------
+def batch_sizes(n_solves: int, seed: int = SEED, lo: int = 32, ratio: float = 4.0):
+    """Cells per side of each solve: 8*round(lo * ratio^u / 8), u ~ U[0,1)
+    from SplitMix64 (log-uniform between lo and lo*ratio)."""
+    u = uniform01(seed ^ 0xB47C, np.arange(n_solves))
+    return (8 * np.rint(lo * ratio ** u / 8.0)).astype(np.int64)
+
+
+def batch_blobs(n_solves: int, seed: int = SEED):
+    """Per solve: K in [1,8] blobs with centre ~ U[0.2,0.8]^3, sigma ~
+    U[0.03,0.1], amplitude ~ U[0.5,1] (counter-based draws per solve)."""
+    out = []
+    for s in range(n_solves):
+        base = np.uint64(s) * np.uint64(64)
+        u = uniform01(seed ^ 0xB10B, base + np.arange(64, dtype=np.uint64))
+        k = 1 + int(u[0] * 8)
+        blobs = []
+        for b in range(k):
+            v = u[1 + 6 * b: 7 + 6 * b]
+            blobs.append((0.2 + 0.6 * v[0], 0.2 + 0.6 * v[1], 0.2 + 0.6 * v[2],
+                          0.03 + 0.07 * v[3], 0.5 + 0.5 * v[4]))
+        out.append(blobs)
+    return out
+
+
+def blob_rho(n: int, blobs) -> np.ndarray:
+    """rho on the n^3 cell centres of the unit cube, array [z][y][x]."""
+    c = (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rho = np.zeros((n, n, n))
+    for cx, cy, cz, sg, a in blobs:
+        rho += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) / (2 * sg * sg))
+    return rho

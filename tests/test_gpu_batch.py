@@ -1,0 +1,111 @@
+"""Batched form: many independent uniform solves of uneven sizes in one
+set of launches per level.  Reference: the exact discrete solution by
+separable transforms (oracle/spectral.py).  Bound: 1e-6 relative on each
+potential at a converged residual of 1e-8 (the mixed-precision bound)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import spectral
+
+pytestmark = pytest.mark.gpu
+BCT = (0, 0, 0, 0, 1, 1)
+BCV = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def make_batch(sides, seed_blobs=0, keep=None):
+    """Batch with the seeded blob charges; returns the charges of the solves
+    in `keep` (all when None)."""
+    import torch
+    import paper_1708_08434_gb300 as pkg
+    b = pkg.Batch(sides, 1.0, BCT, BCV)
+    blobs = synth.batch_blobs(len(sides) + seed_blobs)[seed_blobs:]
+    rhos = {}
+    for s, n in enumerate(sides):
+        rho = synth.blob_rho(int(n), blobs[s])
+        if keep is None or s in keep:
+            rhos[s] = rho
+        b.grid(b.rhs, s).copy_(torch.from_numpy(-rho))
+    b.phi.zero_()
+    return b, rhos
+
+
+def check(b, rhos, sel, bound):
+    for s in sel:
+        ref = spectral.solve(-rhos[s], 1.0, BCT, BCV)
+        got = b.grid(b.phi, s).cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= bound, (s, b.sides[s], err)
+
+
+def test_batch_uneven_sizes_against_spectral():
+    sides = [32, 40, 48, 56, 24, 16, 8, 72, 88, 64]
+    b, rhos = make_batch(sides)
+    rc, cyc, rel = b.solve(1e-8, 40)
+    assert rc == 0 and np.all(rel <= 1e-8)
+    assert len(set(cyc.tolist())) > 1            # solves stop at different cycles
+    check(b, rhos, range(len(sides)), 1e-6)
+    # tighter tolerance from the converged state: error follows
+    rc, cyc2, rel2 = b.solve(1e-11, 40)
+    assert rc == 0
+    check(b, rhos, range(len(sides)), 1e-9)
+
+
+def test_batch_autotune_keeps_results():
+    sides = [40, 48, 32, 56]
+    b, rhos = make_batch(sides, seed_blobs=3)
+    shape, gmult, ms = b.tune(2)
+    assert 0 <= shape < 4 and gmult in (2, 4, 8) and ms > 0
+    rc, cyc, rel = b.solve(1e-9, 40)
+    assert rc == 0
+    check(b, rhos, range(len(sides)), 1e-7)
+    # every schedule gives the same potential to roundoff of FP32 cycles
+    ref = b.phi.clone()
+    for sh in range(4):
+        b.set_schedule(sh, 2)
+        b.phi.zero_()
+        b.solve(1e-9, 40)
+        d = (b.phi - ref).abs().max().item() / ref.abs().max().item()
+        assert d <= 1e-7
+
+
+def test_batch_rejects_too_large_coarsest():
+    import paper_1708_08434_gb300 as pkg
+    with pytest.raises(pkg.SmError):
+        pkg.Batch([136], 1.0, BCT, BCV)   # 136 -> 68 -> 34 -> 17 > 16
+
+
+@pytest.mark.slow
+def test_batch_full_size_sampled():
+    """256 solves of 32^3..128^3 (1.3e8 cells): every solve reaches 1e-8;
+    sampled solves (including the largest) against the spectral reference."""
+    sides = synth.batch_sizes(256)
+    big = int(np.argmax(sides))
+    sample = sorted({0, 17, 99, 200, big})
+    b, rhos = make_batch(sides, keep=set(sample))
+    rc, cyc, rel = b.solve(1e-8, 40)
+    assert rc == 0 and np.all(rel <= 1e-8)
+    check(b, rhos, sample, 1e-6)
+
+
+def test_batch_graph_and_host_paths_identical():
+    sides = [40, 32, 8, 56]
+    out = []
+    for graphs in (True, False):
+        b, rhos = make_batch(sides, seed_blobs=5)
+        b.set_graphs(graphs)
+        rc, cyc, rel = b.solve(1e-9, 40)
+        out.append((cyc.copy(), rel.copy(), b.phi.cpu().numpy()))
+        b.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
