@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels from the host instead of CUDA graphs "
                          "(profilers cannot see kernels inside conditional graph nodes)")
@@ -298,6 +299,7 @@ def run_gpu(args):
                  "dtype": "f32 error equation, f64 residual/accumulation/level-0 solve"}
         gm.close()
     batched = None if args.no_batch else bench_batch(args, dev, world)
+    learned = None if args.no_learned else bench_learned(args, dev, world)
     steps = args.steps
     solves = SOLVES_PER_STEP * steps * world
     value = solves / (ms * 1e-3)
@@ -322,6 +324,7 @@ def run_gpu(args):
         "roofline": roof,
         "mixed_precision": mixed,
         "batched": batched,
+        "learned_warm_start": learned,
     }
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline()
@@ -331,6 +334,70 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def bench_learned(args, dev, world):
+    """The learned warm start on the benchmark workload: record the
+    (input, solved change) pairs of the first 6 Heun steps, train the
+    network on the GPU, then time 4 more steps with predictions (judged by
+    the multigrid residual) and the same 4 steps without."""
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    Q, E0 = synth.E_CHARGE, synth.EPS0
+    n_train, n_eval = 6, 4
+
+    def start():
+        dom, st, g, t, ne, ni = build_gpu_case()
+        g.upload(pkg.NE, ne)
+        g.upload(pkg.NI, ni)
+        g.charge_rhs(Q, E0)
+        g.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+        return g, g.dt_limit(Q, E0)
+
+    def steps(g, dt, n):
+        ms, cyc = 0.0, []
+        for _ in range(n):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(g.stream)
+            rc, dt, c1, c2 = g.advance(dt, Q, E0, TOL, MAX_CYCLES)
+            e1.record(g.stream)
+            torch.cuda.synchronize()
+            assert rc == 0, rc
+            ms += e0.elapsed_time(e1)
+            cyc += [c1, c2]
+        return ms, cyc, dt
+
+    net = pkg.Network(16384, 4096)
+    net.set_params(synth.cnn_initial_params())
+    g, dt = start()
+    net.attach(g, 1, per_solve=4096)
+    steps(g, dt, n_train)
+    samples = net.stats()["samples"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = net.train(30, 64, 1e-3)
+    train_s = time.perf_counter() - t0
+    g.close()
+    res = {"train_samples": samples, "train_epochs": 30, "train_s": round(train_s, 3),
+           "final_loss": round(loss, 6)}
+    for mode in ("plain", "learned"):
+        g, dt = start()
+        _, _, dt = steps(g, dt, n_train)
+        if mode == "learned":
+            net.attach(g, 2, per_solve=4096, taper=True)
+        ms, cyc, _ = steps(g, dt, n_eval)
+        res[mode] = {"solves_per_s": round(2 * n_eval / (ms * 1e-3), 2), "vcycles": cyc,
+                     "mean_vcycles": sum(cyc) / len(cyc)}
+        g.close()
+    s = net.stats()
+    res["predictions_kept"] = "%d/%d" % (s["kept"], s["predictions"])
+    res["vcycles_saved_per_solve"] = res["plain"]["mean_vcycles"] - res["learned"]["mean_vcycles"]
+    res["workload"] = "streamer6; train on Heun steps 1-6 (12 solves), evaluate steps 7-10"
+    return res
 
 
 def make_batch_workload():

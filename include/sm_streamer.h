@@ -291,6 +291,65 @@ int sm_batch_set_graphs(sm_batch *b, int enable);
 int sm_batch_info(const sm_batch *b, long long *cells, int *levels_max, long long *launches);
 const char *sm_batch_last_error(const sm_batch *b);
 
+/* ---- learned warm start ---------------------------------------------------- */
+
+/* Build form (not in the paper): a per-box 3D convolutional network
+ * predicts the change of the potential of an 8^3 box from its right-hand
+ * side and previous potential; it warm-starts the two warm-started solves
+ * of sm_advance_fluid, and the multigrid residual judges each prediction.
+ *   input: 2 channels on the box and its ghost layer (10^3; positions
+ *          outside the box repeat the nearest interior cell): the FP64
+ *          residual h^2 (f - L phi) of the plain warm start divided by the
+ *          box scale s = max |h^2 (f - L phi)|, and h^2 f divided by its box
+ *          maximum; output delta on 8^3; phi += s * delta.  Training target:
+ *          (phi_solved - phi_prev)/s clipped to [-8, 8].
+ *   layers: conv 3^3 valid 2->16 + ReLU, conv 3^3 same 16->16 + ReLU (BF16
+ *          tensor-core GEMM), conv 3^3 same 16->1.  Weights BF16, operands
+ *          rounded to BF16, FP32 accumulation, biases FP32.
+ *   parameters (FP32, SM_CNN_PARAMS): W1[16][2][27], b1[16], W2[16][16][27],
+ *          b2[16], W3[16][27], b3 with tap t = (dx+1) + 3(dy+1) + 9(dz+1).
+ * Samples and inputs are kept in the network's own arena
+ * (sm_cnn_arena_size / sm_cnn_bind_arena); max_samples >= 16 training
+ * pairs, max_boxes boxes per prediction. */
+#define SM_CNN_PARAMS 8241
+typedef struct sm_cnn sm_cnn;
+int sm_cnn_create(sm_cnn **out, int max_samples, int max_boxes, void *stream);
+int sm_cnn_destroy(sm_cnn *c);
+int sm_cnn_arena_size(const sm_cnn *c, size_t *bytes);
+int sm_cnn_bind_arena(sm_cnn *c, void *dev_ptr, size_t bytes);
+/* FP32 parameters from / to HOST memory (n = SM_CNN_PARAMS); setting them
+ * resets the Adam moments. */
+int sm_cnn_set_params(sm_cnn *c, const float *host, int n);
+int sm_cnn_get_params(sm_cnn *c, float *host, int n);
+/* Forward pass of n explicit inputs (HOST [n][1000][2] floats, position
+ * index x + 10 y + 100 z, rounded to BF16): out HOST [n][512]; acts (HOST,
+ * may be NULL) [min(n,16)][4][16][512] = z1, relu'd BF16 a1, z2, a2. */
+int sm_cnn_forward(sm_cnn *c, const float *x_host, int n, float *out_host, float *acts_host);
+/* Gradient of the mean squared error over n explicit (input, target)
+ * pairs (HOST [n][1000][2], [n][512]); grad HOST [SM_CNN_PARAMS].
+ * Overwrites recorded samples. */
+int sm_cnn_gradient(sm_cnn *c, const float *x_host, const float *t_host, int n, float *grad_host, float *loss);
+/* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) with an explicit
+ * gradient (HOST [SM_CNN_PARAMS]). */
+int sm_cnn_adam_step(sm_cnn *c, const float *grad_host, float lr);
+/* `epochs` passes over the recorded samples in minibatches of `batch`, an
+ * Adam step after each; sample order shuffled per epoch from `seed`.  Out:
+ * mean loss of the last epoch.  Synchronises. */
+int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned long long seed, float *loss);
+/* Couple the network to a solver's sm_advance_fluid: mode 1 records
+ * (input, solved change) pairs of up to per_solve leaf boxes of the two
+ * finest levels (every stride-th) per solve; mode 2 predicts a warm start
+ * for those boxes before each solve (taper != 0: the prediction is
+ * weighted 1/4, 3/4 on the two outer cell layers of each axis) and keeps
+ * it only if the relative residual of the predicted start is below judge
+ * times that of the plain warm start (else the plain warm start); the
+ * solve then iterates to its tolerance either way.  mode 0 detaches. */
+int sm_cnn_attach(sm_ctx *ctx, sm_cnn *c, int mode, int per_solve, int stride, int taper, double judge);
+/* recorded samples, predictions made and kept, last residuals
+ * (last_rel[0] plain start, last_rel[1] predicted start) */
+int sm_cnn_stats(const sm_cnn *c, int *n_samples, long long *predictions, long long *kept, double *last_rel);
+const char *sm_cnn_last_error(const sm_cnn *c);
+
 /* ---- allocation-free entry point ---------------------------------------- */
 
 /* No counterpart in the paper: a service for callers that cannot allocate

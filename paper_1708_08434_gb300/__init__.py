@@ -60,7 +60,10 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
-           "sm_batch_set_graphs",
+           "sm_batch_set_graphs", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
+           "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
+           "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
+           "sm_cnn_last_error",
            "sm_batch_last_error"]
 
 
@@ -116,6 +119,19 @@ def load():
         "sm_batch_set_graphs": [P, I],
         "sm_batch_info": [P, C.POINTER(C.c_longlong), pI, C.POINTER(C.c_longlong)],
         "sm_batch_last_error": [P],
+        "sm_cnn_create": [C.POINTER(P), I, I, P],
+        "sm_cnn_destroy": [P],
+        "sm_cnn_arena_size": [P, C.POINTER(C.c_size_t)],
+        "sm_cnn_bind_arena": [P, P, C.c_size_t],
+        "sm_cnn_set_params": [P, P, I],
+        "sm_cnn_get_params": [P, P, I],
+        "sm_cnn_forward": [P, P, I, P, P],
+        "sm_cnn_gradient": [P, P, P, I, P, C.POINTER(C.c_float)],
+        "sm_cnn_adam_step": [P, P, C.c_float],
+        "sm_cnn_train": [P, I, I, C.c_float, C.c_ulonglong, C.POINTER(C.c_float)],
+        "sm_cnn_attach": [P, P, I, I, I, I, D],
+        "sm_cnn_stats": [P, pI, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), pD],
+        "sm_cnn_last_error": [P],
         "sm_last_error": [P],
     }
     for name, args in sig.items():
@@ -424,3 +440,89 @@ class Batch:
         c, lv, nl = C.c_longlong(), C.c_int(), C.c_longlong()
         self._ck(self._lib.sm_batch_info(self._h, C.byref(c), C.byref(lv), C.byref(nl)))
         return c.value, lv.value, nl.value
+
+
+CNN_PARAMS = 8241
+
+
+class Network:
+    """The learned warm-start network (weights, samples, training)."""
+
+    def __init__(self, max_samples=4096, max_boxes=4096, stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise SmError(SM_ECUDA, "no CUDA device")
+        self._lib, self.torch = lib, torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = lib.sm_cnn_create(C.byref(h), max_samples, max_boxes, C.c_void_p(self.stream.cuda_stream))
+        if rc != SM_OK:
+            raise SmError(rc, "sm_cnn_create failed")
+        self._h = h
+        size = C.c_size_t()
+        self._ck(lib.sm_cnn_arena_size(h, C.byref(size)))
+        self.arena = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+        self._ck(lib.sm_cnn_bind_arena(h, C.c_void_p(self.arena.data_ptr()), size.value))
+
+    def _ck(self, rc):
+        if rc != SM_OK:
+            raise SmError(rc, self._lib.sm_cnn_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.sm_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        self._ck(self._lib.sm_cnn_set_params(self._h, _hp(a), a.size))
+
+    def get_params(self):
+        a = np.zeros(CNN_PARAMS, np.float32)
+        self._ck(self._lib.sm_cnn_get_params(self._h, _hp(a), a.size))
+        return a
+
+    def forward(self, x, acts=False):
+        """x: [n][1000][2] float32 (position-major); returns out [n][512]
+        and, with acts, [min(n,16)][4][16][512] = z1, a1, z2, a2."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n = x.shape[0]
+        out = np.zeros((n, 512), np.float32)
+        ac = np.zeros((min(n, 16), 4, 16, 512), np.float32) if acts else None
+        self._ck(self._lib.sm_cnn_forward(self._h, _hp(x), n, _hp(out), _hp(ac) if acts else None))
+        return (out, ac) if acts else out
+
+    def gradient(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(CNN_PARAMS, np.float32)
+        loss = C.c_float()
+        self._ck(self._lib.sm_cnn_gradient(self._h, _hp(x), _hp(t), x.shape[0], _hp(g), C.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, g, lr):
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        self._ck(self._lib.sm_cnn_adam_step(self._h, _hp(g), lr))
+
+    def train(self, epochs, batch, lr, seed=0x5EED):
+        loss = C.c_float()
+        self._ck(self._lib.sm_cnn_train(self._h, epochs, batch, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def attach(self, solver, mode, per_solve=512, stride=1, taper=False, judge=1.0):
+        self._ck(self._lib.sm_cnn_attach(solver._h, self._h, mode, per_solve, stride, int(taper), judge))
+
+    def stats(self):
+        n, p, k = C.c_int(), C.c_longlong(), C.c_longlong()
+        rel = (C.c_double * 2)()
+        self._ck(self._lib.sm_cnn_stats(self._h, C.byref(n), C.byref(p), C.byref(k), rel))
+        return {"samples": n.value, "predictions": p.value, "kept": k.value, "last_rel": (rel[0], rel[1])}

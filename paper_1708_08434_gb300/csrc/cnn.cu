@@ -1,0 +1,834 @@
+// cnn.cu -- learned warm start for the warm-started Poisson solves of the
+// time step (build form, not in the paper): a small per-box 3D
+// convolutional network predicts the change of the potential of a box from
+// its right-hand side and its previous potential.  It is trained on the GPU
+// by the kernels below on pairs the solver itself produces during a run;
+// the multigrid solve stays the judge (a prediction is kept only if it
+// lowers the relative residual) and iterates to the same tolerance.
+//
+// Network per 8^3 box (weights BF16, activations rounded to BF16 as the
+// next layer's operands, FP32 accumulation, biases FP32):
+//   input  X: 2 channels on the 10^3 box-with-ghosts region, the FP64
+//          residual h^2 (f - L phi_prev) divided by the box scale s and the
+//          normalised right-hand side h^2 f
+//   conv 3^3 valid 2->16, ReLU;  conv 3^3 same 16->16, ReLU (tensor cores);
+//   conv 3^3 same 16->1 -> delta on 8^3;  prediction phi += s * delta.
+// Training: mean squared error against (phi_solved - phi_prev)/s (clipped),
+// Adam on
+// FP32 master weights, gradients reduced in a fixed order (deterministic).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sm_internal.cuh"
+
+using namespace sm;
+
+int sm_rel_residual_now(sm_ctx *ctx, double *rel);
+
+namespace {
+
+constexpr int NW1 = 16 * 2 * 27, NW2 = 16 * 16 * 27, NW3 = 16 * 27;
+constexpr int O_W1 = 0, O_B1 = NW1, O_W2 = O_B1 + 16, O_B2 = O_W2 + NW2, O_W3 = O_B2 + 16, O_B3 = O_W3 + NW3;
+constexpr int NP = O_B3 + 1;  // 8241 parameters
+constexpr int NPOS = 1000;    // 10^3 positions of a box with one ghost layer
+constexpr int CT = 256;       // threads per CTA
+constexpr int MAX_DEBUG = 16;
+
+typedef __nv_bfloat16 bf16;
+
+// voxel v = x + 8y + 64z of the box -> position in the 10^3 region
+__device__ __forceinline__ int Pos(int v) { return ((v & 7) + 1) + 10 * (((v >> 3) & 7) + 1) + 100 * ((v >> 6) + 1); }
+// tap t = (dx+1) + 3(dy+1) + 9(dz+1) -> position offset
+__device__ __forceinline__ int Off(int t) { return (t % 3 - 1) + 10 * ((t / 3) % 3 - 1) + 100 * (t / 9 - 1); }
+__device__ __forceinline__ float bf(bf16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float rbf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// D += A B for one m16n8k16 tile, BF16 operands, FP32 accumulation
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// weights as one CTA uses them
+struct NetS {
+  float w1[NW1];      // [co][ci][t], BF16 values
+  float b1[16];
+  bf16 w2[27 * 256];  // [t][co][ci] (mma B operand)
+  float b2[16];
+  float w3[NW3];      // [ci][t], BF16 values
+  float b3;
+};
+
+struct FwdS {
+  bf16 x[NPOS * 2];    // [pos][ci]
+  bf16 a1[NPOS * 16];  // [pos][c], zero outside the box interior
+  bf16 a2[NPOS * 16];
+  float out[512];
+};
+
+__device__ void load_net(NetS &N, const float *__restrict__ w) {
+  for (int i = threadIdx.x; i < NW1; i += blockDim.x) N.w1[i] = rbf(w[O_W1 + i]);
+  for (int i = threadIdx.x; i < NW3; i += blockDim.x) N.w3[i] = rbf(w[O_W3 + i]);
+  for (int i = threadIdx.x; i < 27 * 256; i += blockDim.x) {
+    int t = i / 256, co = (i / 16) % 16, ci = i % 16;
+    N.w2[i] = __float2bfloat16_rn(w[O_W2 + (co * 16 + ci) * 27 + t]);
+  }
+  if (threadIdx.x < 16) {
+    N.b1[threadIdx.x] = w[O_B1 + threadIdx.x];
+    N.b2[threadIdx.x] = w[O_B2 + threadIdx.x];
+  }
+  if (threadIdx.x == 0) N.b3 = w[O_B3];
+}
+
+__device__ void zero_acts(FwdS &F) {
+  uint32_t *p = reinterpret_cast<uint32_t *>(F.a1);
+  for (int i = threadIdx.x; i < NPOS * 16; i += blockDim.x) p[i] = 0u;  // a1 and a2
+}
+
+// Forward pass of one box whose input is already in F.x.  Debug pointers
+// (per box [16][512] / [512], may be null) receive z1, a1, z2, a2.
+__device__ void forward_box(const NetS &N, FwdS &F, float *z1d, float *a1d, float *z2d, float *a2d) {
+  const int t = threadIdx.x;
+  // layer 1: valid 3^3 conv 2 -> 16 on CUDA cores
+  for (int r = 0; r < 2; ++r) {
+    int v = t + r * CT, p = Pos(v);
+    float acc[16];
+#pragma unroll
+    for (int co = 0; co < 16; ++co) acc[co] = N.b1[co];
+    for (int tp = 0; tp < 27; ++tp) {
+      int q = p + Off(tp);
+      float x0 = bf(F.x[2 * q]), x1 = bf(F.x[2 * q + 1]);
+#pragma unroll
+      for (int co = 0; co < 16; ++co) acc[co] += N.w1[(co * 2) * 27 + tp] * x0 + N.w1[(co * 2 + 1) * 27 + tp] * x1;
+    }
+#pragma unroll
+    for (int co = 0; co < 16; ++co) {
+      bf16 a = __float2bfloat16_rn(fmaxf(acc[co], 0.0f));
+      F.a1[p * 16 + co] = a;
+      if (z1d) {
+        z1d[co * 512 + v] = acc[co];
+        a1d[co * 512 + v] = bf(a);
+      }
+    }
+  }
+  __syncthreads();
+  // layer 2: same 3^3 conv 16 -> 16 as an implicit GEMM on tensor cores,
+  // M = 512 voxels, N = 16 channels, K = 27 taps x 16 channels
+  {
+    int warp = t >> 5, lane = t & 31, g = lane >> 2, c = lane & 3;
+    float acc[4][2][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[m][j][e] = 0.0f;
+    for (int tp = 0; tp < 27; ++tp) {
+      int off = Off(tp);
+      uint32_t bfr[2][2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const bf16 *wr = N.w2 + (tp * 16 + 8 * j + g) * 16;
+        bfr[j][0] = *reinterpret_cast<const uint32_t *>(wr + 2 * c);
+        bfr[j][1] = *reinterpret_cast<const uint32_t *>(wr + 2 * c + 8);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int v0 = (warp * 4 + m) * 16 + g;
+        const bf16 *r0 = F.a1 + (Pos(v0) + off) * 16, *r1 = F.a1 + (Pos(v0 + 8) + off) * 16;
+        uint32_t afr[4] = {*reinterpret_cast<const uint32_t *>(r0 + 2 * c),
+                           *reinterpret_cast<const uint32_t *>(r1 + 2 * c),
+                           *reinterpret_cast<const uint32_t *>(r0 + 2 * c + 8),
+                           *reinterpret_cast<const uint32_t *>(r1 + 2 * c + 8)};
+        mma16816(acc[m][0], afr, bfr[0]);
+        mma16816(acc[m][1], afr, bfr[1]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int v = (warp * 4 + m) * 16 + g + 8 * h, co = 8 * j + 2 * c;
+          float z0 = acc[m][j][2 * h] + N.b2[co], z1 = acc[m][j][2 * h + 1] + N.b2[co + 1];
+          __nv_bfloat162 a2 = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+          *reinterpret_cast<__nv_bfloat162 *>(F.a2 + Pos(v) * 16 + co) = a2;
+          if (z2d) {
+            z2d[co * 512 + v] = z0;
+            z2d[(co + 1) * 512 + v] = z1;
+            a2d[co * 512 + v] = __low2float(a2);
+            a2d[(co + 1) * 512 + v] = __high2float(a2);
+          }
+        }
+  }
+  __syncthreads();
+  // layer 3: same 3^3 conv 16 -> 1 on CUDA cores
+  for (int r = 0; r < 2; ++r) {
+    int v = t + r * CT, p = Pos(v);
+    float acc = N.b3;
+    for (int tp = 0; tp < 27; ++tp) {
+      const bf16 *row = F.a2 + (p + Off(tp)) * 16;
+#pragma unroll
+      for (int ci = 0; ci < 16; ++ci) acc += N.w3[ci * 27 + tp] * bf(row[ci]);
+    }
+    F.out[v] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ void load_input(FwdS &F, const bf16 *__restrict__ X) {
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(X);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(F.x);
+  for (int i = threadIdx.x; i < NPOS; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// inference / debug forward over boxes [0, n) of X; out [n][512]
+__global__ void __launch_bounds__(CT) k_cnn_forward(const bf16 *__restrict__ X, int n, const float *__restrict__ w,
+                                                    float *__restrict__ out, float *__restrict__ dbg) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  NetS &N = *reinterpret_cast<NetS *>(smraw);
+  FwdS &F = *reinterpret_cast<FwdS *>(smraw + ((sizeof(NetS) + 15) & ~(size_t)15));
+  load_net(N, w);
+  zero_acts(F);
+  __syncthreads();
+  for (int b = blockIdx.x; b < n; b += gridDim.x) {
+    load_input(F, X + (size_t)b * NPOS * 2);
+    float *d = (dbg && b < MAX_DEBUG) ? dbg + (size_t)b * 4 * 16 * 512 : nullptr;
+    forward_box(N, F, d, d ? d + 8192 : nullptr, d ? d + 16384 : nullptr, d ? d + 24576 : nullptr);
+    for (int v = threadIdx.x; v < 512; v += blockDim.x) out[(size_t)b * 512 + v] = F.out[v];
+    __syncthreads();
+  }
+}
+
+// ---- training: forward + backward per box, per-CTA partial gradients ----
+struct BwdS {
+  float g3[512];        // dL/d out
+  float d2[512 * 16];   // dL/dz2 [v][c]
+  float d1[512 * 16];   // dL/dz1 [v][c]
+  float grad[NP];       // this CTA's gradient accumulator
+  float red[CT / 32];
+};
+
+__global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, const float *__restrict__ target,
+                                                  const int *__restrict__ ids, int n, float inv_count,
+                                                  const float *__restrict__ w, float *__restrict__ partial,
+                                                  float *__restrict__ loss_partial) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  size_t o1 = (sizeof(NetS) + 15) & ~(size_t)15, o2 = o1 + ((sizeof(FwdS) + 15) & ~(size_t)15);
+  NetS &N = *reinterpret_cast<NetS *>(smraw);
+  FwdS &F = *reinterpret_cast<FwdS *>(smraw + o1);
+  BwdS &B = *reinterpret_cast<BwdS *>(smraw + o2);
+  const int t = threadIdx.x;
+  load_net(N, w);
+  zero_acts(F);
+  for (int i = t; i < NP; i += CT) B.grad[i] = 0.0f;
+  float my_loss = 0.0f;
+  __syncthreads();
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    int s = ids[it];
+    load_input(F, X + (size_t)s * NPOS * 2);
+    forward_box(N, F, nullptr, nullptr, nullptr, nullptr);
+    const float *tg = target + (size_t)s * 512;
+    for (int v = t; v < 512; v += CT) {
+      float e = F.out[v] - tg[v];
+      my_loss += e * e * inv_count;
+      B.g3[v] = 2.0f * inv_count * e;
+    }
+    __syncthreads();
+    // layer 3 weights and bias
+    for (int e = t; e < NW3; e += CT) {
+      int ci = e / 27, tp = e % 27, off = Off(tp);
+      float acc = 0.0f;
+      for (int v = 0; v < 512; ++v) acc += bf(F.a2[(Pos(v) + off) * 16 + ci]) * B.g3[v];
+      B.grad[O_W3 + e] += acc;
+    }
+    if (t == 0) {
+      float acc = 0.0f;
+      for (int v = 0; v < 512; ++v) acc += B.g3[v];
+      B.grad[O_B3] += acc;
+    }
+    // dL/dz2[u][c] = relu'(a2[u][c]) * sum_t W3[c][t] g3[u - d_t]
+    for (int e = t; e < 512 * 16; e += CT) {
+      int u = e >> 4, c = e & 15;
+      float acc = 0.0f;
+      if (bf(F.a2[Pos(u) * 16 + c]) > 0.0f) {
+        int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
+        for (int tp = 0; tp < 27; ++tp) {
+          int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
+          if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
+          acc += N.w3[c * 27 + tp] * B.g3[vx + 8 * vy + 64 * vz];
+        }
+      }
+      B.d2[e] = acc;
+    }
+    __syncthreads();
+    // layer 2 weights: thread (co, ci) accumulates its 27 taps
+    {
+      int co = t >> 4, ci = t & 15;
+      for (int tp = 0; tp < 27; ++tp) {
+        int off = Off(tp);
+        float acc = 0.0f;
+        for (int v = 0; v < 512; ++v) acc += bf(F.a1[(Pos(v) + off) * 16 + ci]) * B.d2[v * 16 + co];
+        B.grad[O_W2 + (co * 16 + ci) * 27 + tp] += acc;
+      }
+      if (t < 16) {
+        float acc = 0.0f;
+        for (int v = 0; v < 512; ++v) acc += B.d2[v * 16 + t];
+        B.grad[O_B2 + t] += acc;
+      }
+    }
+    // dL/dz1[u][ci] = relu'(a1) * sum_t sum_co W2[co][ci][t] d2[u - d_t][co]
+    for (int e = t; e < 512 * 16; e += CT) {
+      int u = e >> 4, ci = e & 15;
+      float acc = 0.0f;
+      if (bf(F.a1[Pos(u) * 16 + ci]) > 0.0f) {
+        int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
+        for (int tp = 0; tp < 27; ++tp) {
+          int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
+          if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
+          const float *dv = B.d2 + (vx + 8 * vy + 64 * vz) * 16;
+          const bf16 *wr = N.w2 + tp * 256 + ci;  // [t][co][ci]
+#pragma unroll
+          for (int co = 0; co < 16; ++co) acc += bf(wr[co * 16]) * dv[co];
+        }
+      }
+      B.d1[e] = acc;
+    }
+    __syncthreads();
+    // layer 1 weights and bias (valid conv on the 10^3 input)
+    for (int e = t; e < NW1; e += CT) {
+      int co = e / 54, ci = (e / 27) % 2, tp = e % 27, off = Off(tp);
+      float acc = 0.0f;
+      for (int v = 0; v < 512; ++v) acc += bf(F.x[2 * (Pos(v) + off) + ci]) * B.d1[v * 16 + co];
+      B.grad[O_W1 + e] += acc;
+    }
+    if (t < 16) {
+      float acc = 0.0f;
+      for (int v = 0; v < 512; ++v) acc += B.d1[v * 16 + t];
+      B.grad[O_B1 + t] += acc;
+    }
+    __syncthreads();
+  }
+  float* dst = partial + (size_t)blockIdx.x * NP;
+  for (int i = t; i < NP; i += CT) dst[i] = B.grad[i];
+  // this CTA's loss
+  float v = my_loss;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((t & 31) == 0) B.red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    float s = 0.0f;
+    for (int i = 0; i < CT / 32; ++i) s += B.red[i];
+    loss_partial[blockIdx.x] = s;
+  }
+}
+
+// gradient = sum of the CTA partials in CTA order (deterministic)
+__global__ void k_cnn_reduce(const float *__restrict__ partial, int nblk, float *__restrict__ grad,
+                             const float *__restrict__ loss_partial, float *__restrict__ loss) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NP) {
+    float s = 0.0f;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * NP + i];
+    grad[i] = s;
+  }
+  if (i == 0) {
+    float s = 0.0f;
+    for (int b = 0; b < nblk; ++b) s += loss_partial[b];
+    *loss = s;
+  }
+}
+
+// Adam on the FP32 master weights (bias-corrected moments)
+__global__ void k_cnn_adam(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                           const float *__restrict__ g, float lr, float c1, float c2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NP) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.0f - b1) * gi;
+  float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Inputs of the listed boxes from the solver state, on the 10^3 box-with-
+// ghosts positions (positions outside the box repeat the nearest interior
+// cell): channel 0 = h^2 r with r = f - L phi the FP64 residual of the
+// plain warm start, divided by the box scale s = max |h^2 r|; channel 1 =
+// h^2 f divided by its own box maximum (where the charge is).  The residual
+// is formed in FP64 before any rounding: it is ~1e-3 of f, below BF16
+// resolution, so the network could not form it from rounded inputs.
+__global__ void __launch_bounds__(CT) k_cnn_gather(const int *__restrict__ boxes, int n,
+                                                   const double *__restrict__ phi, const double *__restrict__ rhs,
+                                                   const double *__restrict__ gh, const int32_t *__restrict__ nbr6,
+                                                   const int32_t *__restrict__ level,
+                                                   const int32_t *__restrict__ child, Bc bc, LevelH lh,
+                                                   bf16 *__restrict__ X, float *__restrict__ scale,
+                                                   double *__restrict__ phi_prev, int slot0) {
+  __shared__ double vr[CELLS], vf[CELLS], red[2][CT / 32];
+  int b = boxes[blockIdx.x], slot = slot0 + blockIdx.x;
+  int l = level[b];
+  double h2 = lh.h2[l], inv_h2 = lh.inv_h2[l];
+  const double *pb = phi + (size_t)b * CELLS, *fb = rhs + (size_t)b * CELLS;
+  double mr = 0.0, mf = 0.0;
+  for (int v = threadIdx.x; v < CELLS; v += CT) {
+    double p = pb[v];
+    double sum = nb_sum(phi, nbr6, gh, b, v & 7, (v >> 3) & 7, v >> 6, p, bc, 0);
+    double r = fb[v] - (sum - 6.0 * p) * inv_h2;
+    vr[v] = h2 * r;
+    vf[v] = h2 * fb[v];
+    mr = fmax(mr, fabs(vr[v]));
+    mf = fmax(mf, fabs(vf[v]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = mr;
+    red[1][threadIdx.x >> 5] = mf;
+  }
+  __syncthreads();
+  double sr = 0.0, sf = 0.0;
+  for (int i = 0; i < CT / 32; ++i) {
+    sr = fmax(sr, red[0][i]);
+    sf = fmax(sf, red[1][i]);
+  }
+  double ir = sr > 0.0 ? 1.0 / sr : 0.0, iff = sf > 0.0 ? 1.0 / sf : 0.0;
+  bf16 *xo = X + (size_t)slot * NPOS * 2;
+  for (int q = threadIdx.x; q < NPOS; q += CT) {
+    int cx = min(max(q % 10 - 1, 0), NC - 1), cy = min(max((q / 10) % 10 - 1, 0), NC - 1),
+        cz = min(max(q / 100 - 1, 0), NC - 1);
+    int v = cidx(cx, cy, cz);
+    xo[2 * q] = __float2bfloat16_rn((float)(vr[v] * ir));
+    xo[2 * q + 1] = __float2bfloat16_rn((float)(vf[v] * iff));
+  }
+  if (threadIdx.x == 0) scale[slot] = (float)sr;
+  if (phi_prev)  // indexed by position in the box list
+    for (int v = threadIdx.x; v < CELLS; v += CT) phi_prev[(size_t)blockIdx.x * CELLS + v] = pb[v];
+}
+
+// training target (phi_new - phi_prev) / s of recorded boxes, clipped to
+// +-8: a box whose change is mostly driven by charge elsewhere cannot be
+// predicted from its own residual and is taught a bounded correction
+__global__ void k_cnn_target(const int *__restrict__ boxes, int n, const double *__restrict__ phi,
+                             const double *__restrict__ phi_prev, const float *__restrict__ scale,
+                             float *__restrict__ target, int slot0) {
+  int i = blockIdx.x, slot = slot0 + i, b = boxes[i];
+  double s = (double)scale[slot];
+  for (int v = threadIdx.x; v < CELLS; v += blockDim.x) {
+    double d = phi[(size_t)b * CELLS + v] - phi_prev[(size_t)i * CELLS + v];
+    double t = s > 0.0 ? d / s : 0.0;
+    target[(size_t)slot * CELLS + v] = (float)fmin(8.0, fmax(-8.0, t));
+  }
+}
+
+// phi += s * w * prediction on the listed boxes; with taper, w falls from
+// 1 in the 4^3 core to 3/4 and 1/4 on the two outer cell layers per axis
+// (so neighbouring boxes' independent predictions do not meet in jumps)
+__device__ __forceinline__ double taper1(int i) { return i == 0 || i == 7 ? 0.25 : (i == 1 || i == 6 ? 0.75 : 1.0); }
+
+__global__ void k_cnn_apply(const int *__restrict__ boxes, int n, const float *__restrict__ out,
+                            const float *__restrict__ scale, double *__restrict__ phi, int taper) {
+  int i = blockIdx.x, b = boxes[i];
+  for (int v = threadIdx.x; v < CELLS; v += blockDim.x) {
+    double w = taper ? taper1(v & 7) * taper1((v >> 3) & 7) * taper1(v >> 6) : 1.0;
+    phi[(size_t)b * CELLS + v] += w * (double)scale[i] * (double)out[(size_t)i * CELLS + v];
+  }
+}
+
+size_t fwd_smem() { return ((sizeof(NetS) + 15) & ~(size_t)15) + ((sizeof(FwdS) + 15) & ~(size_t)15); }
+size_t train_smem() { return fwd_smem() + sizeof(BwdS); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct sm_cnn {
+  cudaStream_t stream = nullptr;
+  int max_samples = 0, max_boxes = 0, sms = 148;
+  int n_samples = 0;
+  char *arena = nullptr;
+  float *w = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *partial = nullptr, *lossp = nullptr,
+        *loss = nullptr;
+  bf16 *X = nullptr;            // samples [max_samples][1000][2]
+  float *target = nullptr;      // [max_samples][512]
+  float *scale = nullptr;       // [max_samples]
+  double *phi_prev = nullptr;   // [max_boxes][512] boxes of the pending record
+  bf16 *Xp = nullptr;           // prediction inputs [max_boxes][1000][2]
+  float *out = nullptr, *sc_p = nullptr;  // prediction outputs and scales
+  float *dbg = nullptr;         // [MAX_DEBUG][4][16][512]
+  int *ids = nullptr, *boxes = nullptr;
+  int adam_step = 0;
+  // attached solver
+  int mode = 0, stride = 1, per_solve = 0, taper = 0;
+  double judge = 1.0;  // keep a prediction when rel_cnn < judge * rel_plain
+  std::vector<int> pending;     // boxes recorded by the last pre-solve hook
+  int pending_slot = 0;
+  long long predictions = 0, kept = 0;
+  double last_rel_plain = 0.0, last_rel_cnn = 0.0;
+  std::string err;
+};
+
+static int cfail(sm_cnn *c, int code, const char *msg) {
+  if (c) c->err = msg;
+  return code;
+}
+#define CCK(call)                                                          \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return SM_ECUDA;                                                     \
+    }                                                                      \
+  } while (0)
+
+struct CLayout {
+  size_t w, m, v, grad, partial, lossp, loss, X, target, scale, phi_prev, Xp, out, sc_p, dbg, ids, boxes, total;
+};
+
+static CLayout clayout(int max_samples, int max_boxes, int sms) {
+  CLayout L;
+  size_t t = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = t;
+    t = (t + bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  L.w = take(4 * NP);
+  L.m = take(4 * NP);
+  L.v = take(4 * NP);
+  L.grad = take(4 * NP);
+  L.partial = take(4 * (size_t)NP * sms);
+  L.lossp = take(4 * (size_t)sms);
+  L.loss = take(4);
+  L.X = take(2 * (size_t)NPOS * 2 * max_samples);
+  L.target = take(4 * (size_t)512 * max_samples);
+  L.scale = take(4 * (size_t)max_samples);
+  L.phi_prev = take(8 * (size_t)512 * max_boxes);
+  L.Xp = take(2 * (size_t)NPOS * 2 * max_boxes);
+  L.out = take(4 * (size_t)512 * max_boxes);
+  L.sc_p = take(4 * (size_t)max_boxes);
+  L.dbg = take(4 * (size_t)MAX_DEBUG * 4 * 16 * 512);
+  L.ids = take(4 * (size_t)max_samples);
+  L.boxes = take(4 * (size_t)max_boxes);
+  L.total = t;
+  return L;
+}
+
+extern "C" int sm_cnn_create(sm_cnn **out, int max_samples, int max_boxes, void *stream) {
+  if (!out || max_samples < MAX_DEBUG || max_boxes < 1) return SM_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return SM_ECUDA;
+  }
+  sm_cnn *c = new sm_cnn();
+  c->stream = (cudaStream_t)stream;
+  c->max_samples = max_samples;
+  c->max_boxes = max_boxes;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  *out = c;
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_destroy(sm_cnn *c) {
+  delete c;
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_arena_size(const sm_cnn *c, size_t *bytes) {
+  if (!c || !bytes) return SM_EINVAL;
+  *bytes = clayout(c->max_samples, c->max_boxes, c->sms).total;
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_bind_arena(sm_cnn *c, void *dev_ptr, size_t bytes) {
+  if (!c || !dev_ptr) return SM_EINVAL;
+  CLayout L = clayout(c->max_samples, c->max_boxes, c->sms);
+  if (bytes < L.total) return cfail(c, SM_ENOMEM, "arena too small");
+  if (((uintptr_t)dev_ptr & 255) != 0) return cfail(c, SM_EINVAL, "arena not 256-byte aligned");
+  char *a = (char *)dev_ptr;
+  c->arena = a;
+  c->w = (float *)(a + L.w);
+  c->m = (float *)(a + L.m);
+  c->v = (float *)(a + L.v);
+  c->grad = (float *)(a + L.grad);
+  c->partial = (float *)(a + L.partial);
+  c->lossp = (float *)(a + L.lossp);
+  c->loss = (float *)(a + L.loss);
+  c->X = (bf16 *)(a + L.X);
+  c->target = (float *)(a + L.target);
+  c->scale = (float *)(a + L.scale);
+  c->phi_prev = (double *)(a + L.phi_prev);
+  c->Xp = (bf16 *)(a + L.Xp);
+  c->out = (float *)(a + L.out);
+  c->sc_p = (float *)(a + L.sc_p);
+  c->dbg = (float *)(a + L.dbg);
+  c->ids = (int *)(a + L.ids);
+  c->boxes = (int *)(a + L.boxes);
+  CCK(cudaMemsetAsync(a, 0, L.total, c->stream));
+  CCK(cudaFuncSetAttribute(k_cnn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem()));
+  CCK(cudaFuncSetAttribute(k_cnn_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem()));
+  c->n_samples = 0;
+  c->adam_step = 0;
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_set_params(sm_cnn *c, const float *host, int n) {
+  if (!c || !host || n != NP || !c->arena) return SM_EINVAL;
+  CCK(cudaMemcpyAsync(c->w, host, 4 * NP, cudaMemcpyHostToDevice, c->stream));
+  CCK(cudaMemsetAsync(c->m, 0, 4 * NP, c->stream));
+  CCK(cudaMemsetAsync(c->v, 0, 4 * NP, c->stream));
+  CCK(cudaStreamSynchronize(c->stream));
+  c->adam_step = 0;
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_get_params(sm_cnn *c, float *host, int n) {
+  if (!c || !host || n != NP || !c->arena) return SM_EINVAL;
+  CCK(cudaMemcpyAsync(host, c->w, 4 * NP, cudaMemcpyDeviceToHost, c->stream));
+  CCK(cudaStreamSynchronize(c->stream));
+  return SM_OK;
+}
+
+// forward of n explicit inputs (host [n][1000][2] floats, rounded to BF16
+// on upload); out [n][512] and optional per-layer activations of the first
+// min(n, 16) boxes ([n][4][16][512]: z1, a1, z2, a2)
+extern "C" int sm_cnn_forward(sm_cnn *c, const float *x_host, int n, float *out_host, float *acts_host) {
+  if (!c || !x_host || !out_host || n < 1 || n > c->max_boxes || !c->arena) return SM_EINVAL;
+  std::vector<bf16> xb((size_t)n * NPOS * 2);
+  for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(x_host[i]);
+  CCK(cudaMemcpyAsync(c->Xp, xb.data(), 2 * xb.size(), cudaMemcpyHostToDevice, c->stream));
+  int grid = std::min(n, 4 * c->sms);
+  k_cnn_forward<<<grid, CT, fwd_smem(), c->stream>>>(c->Xp, n, c->w, c->out, acts_host ? c->dbg : nullptr);
+  CCK(cudaGetLastError());
+  CCK(cudaMemcpyAsync(out_host, c->out, 4 * (size_t)512 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (acts_host)
+    CCK(cudaMemcpyAsync(acts_host, c->dbg, 4 * (size_t)std::min(n, MAX_DEBUG) * 4 * 16 * 512,
+                        cudaMemcpyDeviceToHost, c->stream));
+  CCK(cudaStreamSynchronize(c->stream));
+  return SM_OK;
+}
+
+static int grad_step(sm_cnn *c, int n, const int *ids_host) {
+  CCK(cudaMemcpyAsync(c->ids, ids_host, 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+  int nblk = std::min(n, c->sms);
+  k_cnn_train<<<nblk, CT, train_smem(), c->stream>>>(c->X, c->target, c->ids, n, 1.0f / (512.0f * n), c->w,
+                                                     c->partial, c->lossp);
+  k_cnn_reduce<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->partial, nblk, c->grad, c->lossp, c->loss);
+  CCK(cudaGetLastError());
+  return SM_OK;
+}
+
+static int adam(sm_cnn *c, float lr) {
+  ++c->adam_step;
+  float c1 = 1.0f - powf(0.9f, (float)c->adam_step), c2 = 1.0f - powf(0.999f, (float)c->adam_step);
+  k_cnn_adam<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->w, c->m, c->v, c->grad, lr, c1, c2);
+  CCK(cudaGetLastError());
+  return SM_OK;
+}
+
+// gradient of the mean squared error over n explicit (input, target)
+// pairs (host [n][1000][2] and [n][512]); overwrites sample slots 0..n-1
+extern "C" int sm_cnn_gradient(sm_cnn *c, const float *x_host, const float *t_host, int n, float *grad_host,
+                               float *loss) {
+  if (!c || !x_host || !t_host || !grad_host || n < 1 || n > c->max_samples || !c->arena) return SM_EINVAL;
+  std::vector<bf16> xb((size_t)n * NPOS * 2);
+  for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(x_host[i]);
+  CCK(cudaMemcpyAsync(c->X, xb.data(), 2 * xb.size(), cudaMemcpyHostToDevice, c->stream));
+  CCK(cudaMemcpyAsync(c->target, t_host, 4 * (size_t)512 * n, cudaMemcpyHostToDevice, c->stream));
+  std::vector<int> ids(n);
+  for (int i = 0; i < n; ++i) ids[i] = i;
+  int st = grad_step(c, n, ids.data());
+  if (st) return st;
+  CCK(cudaMemcpyAsync(grad_host, c->grad, 4 * NP, cudaMemcpyDeviceToHost, c->stream));
+  float l = 0.0f;
+  CCK(cudaMemcpyAsync(&l, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
+  CCK(cudaStreamSynchronize(c->stream));
+  if (loss) *loss = l;
+  c->n_samples = 0;
+  return SM_OK;
+}
+
+// one Adam step with an explicit gradient (host [NP])
+extern "C" int sm_cnn_adam_step(sm_cnn *c, const float *grad_host, float lr) {
+  if (!c || !grad_host || !c->arena) return SM_EINVAL;
+  CCK(cudaMemcpyAsync(c->grad, grad_host, 4 * NP, cudaMemcpyHostToDevice, c->stream));
+  int st = adam(c, lr);
+  if (st) return st;
+  CCK(cudaStreamSynchronize(c->stream));
+  return SM_OK;
+}
+
+static uint64_t splitmix(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// epochs over the recorded samples in minibatches, Adam after each; the
+// sample order of each epoch is a seeded shuffle (SplitMix64 keys).
+// Out: mean loss of the last epoch.
+extern "C" int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned long long seed, float *loss) {
+  if (!c || epochs < 1 || batch < 1 || !c->arena) return SM_EINVAL;
+  if (c->n_samples < 1) return cfail(c, SM_ESTATE, "no recorded samples");
+  int n = c->n_samples;
+  std::vector<int> order(n);
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::vector<std::pair<uint64_t, int>> key(n);
+    for (int i = 0; i < n; ++i) key[i] = {splitmix(seed ^ ((uint64_t)ep << 32) ^ (uint64_t)i), i};
+    std::sort(key.begin(), key.end());
+    for (int i = 0; i < n; ++i) order[i] = key[i].second;
+    double acc = 0.0;
+    int nb = 0;
+    for (int s = 0; s < n; s += batch) {
+      int k = std::min(batch, n - s);
+      int st = grad_step(c, k, order.data() + s);
+      if (st) return st;
+      if ((st = adam(c, lr))) return st;
+      float l = 0.0f;
+      CCK(cudaMemcpyAsync(&l, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
+      CCK(cudaStreamSynchronize(c->stream));
+      acc += l;
+      ++nb;
+    }
+    last = acc / nb;
+  }
+  if (loss) *loss = (float)last;
+  return SM_OK;
+}
+
+// ---- coupling to a solver ---------------------------------------------------
+
+// leaf boxes of the two finest levels, every stride-th, at most per_solve
+static int sample_boxes(sm_cnn *c, sm_ctx *ctx, std::vector<int> &boxes) {
+  boxes.clear();
+  int lo = ctx->n_levels >= 2 ? ctx->leaf_level_off[ctx->n_levels - 2] : 0;
+  int hi = ctx->n_leaves;
+  std::vector<int32_t> leaf(hi - lo);
+  if (hi > lo)
+    CCK(cudaMemcpyAsync(leaf.data(), ctx->leaf + lo, 4 * (size_t)(hi - lo), cudaMemcpyDeviceToHost, ctx->stream));
+  CCK(cudaStreamSynchronize(ctx->stream));
+  for (size_t i = 0; i < leaf.size() && (int)boxes.size() < c->per_solve; i += c->stride) boxes.push_back(leaf[i]);
+  return SM_OK;
+}
+
+static int cnn_pre_solve(void *obj, sm_ctx *ctx) {
+  sm_cnn *c = (sm_cnn *)obj;
+  int st = sm_fill_all_cf(ctx, ctx->phi);
+  if (st) return st;
+  if (c->mode == 1) {  // record inputs and the previous potential
+    std::vector<int> boxes;
+    if ((st = sample_boxes(c, ctx, boxes))) return st;
+    int k = std::min((int)boxes.size(), c->max_samples - c->n_samples);
+    c->pending.assign(boxes.begin(), boxes.begin() + std::max(k, 0));
+    c->pending_slot = c->n_samples;
+    if (k <= 0) return SM_OK;
+    CCK(cudaMemcpyAsync(c->boxes, boxes.data(), 4 * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
+    k_cnn_gather<<<k, CT, 0, ctx->stream>>>(c->boxes, k, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6, ctx->level,
+                                            ctx->child, ctx->bc, ctx->lh, c->X, c->scale, c->phi_prev,
+                                            c->pending_slot);
+    ++ctx->n_launch;
+    CCK(cudaGetLastError());
+    return SM_OK;
+  }
+  if (c->mode == 2) {  // predict, keep the prediction only if it helps
+    std::vector<int> boxes;
+    if ((st = sample_boxes(c, ctx, boxes))) return st;
+    int k = std::min((int)boxes.size(), c->max_boxes);
+    if (k <= 0) return SM_OK;
+    double rel_plain = 0.0, rel_cnn = 0.0;
+    if ((st = sm_rel_residual_now(ctx, &rel_plain))) return st;
+    CCK(cudaMemcpyAsync(ctx->res, ctx->phi, sizeof(double) * CELLS * (size_t)ctx->n_boxes,
+                        cudaMemcpyDeviceToDevice, ctx->stream));
+    CCK(cudaMemcpyAsync(c->boxes, boxes.data(), 4 * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
+    k_cnn_gather<<<k, CT, 0, ctx->stream>>>(c->boxes, k, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6, ctx->level,
+                                            ctx->child, ctx->bc, ctx->lh, c->Xp, c->sc_p, nullptr, 0);
+    k_cnn_forward<<<std::min(k, 4 * c->sms), CT, fwd_smem(), ctx->stream>>>(c->Xp, k, c->w, c->out, nullptr);
+    k_cnn_apply<<<k, CT, 0, ctx->stream>>>(c->boxes, k, c->out, c->sc_p, ctx->phi, c->taper);
+    ctx->n_launch += 3;
+    CCK(cudaGetLastError());
+    if ((st = sm_restrict_pair(ctx, ctx->phi, nullptr))) return st;
+    if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+    if ((st = sm_rel_residual_now(ctx, &rel_cnn))) return st;
+    ++c->predictions;
+    c->last_rel_plain = rel_plain;
+    c->last_rel_cnn = rel_cnn;
+    if (rel_cnn < c->judge * rel_plain) {
+      ++c->kept;
+    } else {  // the judge rejects the prediction: plain warm start
+      CCK(cudaMemcpyAsync(ctx->phi, ctx->res, sizeof(double) * CELLS * (size_t)ctx->n_boxes,
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+      if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
+    }
+  }
+  return SM_OK;
+}
+
+static int cnn_post_solve(void *obj, sm_ctx *ctx) {
+  sm_cnn *c = (sm_cnn *)obj;
+  if (c->mode != 1 || c->pending.empty()) return SM_OK;
+  int k = (int)c->pending.size();
+  CCK(cudaMemcpyAsync(c->boxes, c->pending.data(), 4 * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
+  k_cnn_target<<<k, CT, 0, ctx->stream>>>(c->boxes, k, ctx->phi, c->phi_prev, c->scale, c->target,
+                                          c->pending_slot);
+  ++ctx->n_launch;
+  CCK(cudaGetLastError());
+  c->n_samples += k;
+  c->pending.clear();
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_attach(sm_ctx *ctx, sm_cnn *c, int mode, int per_solve, int stride, int taper,
+                             double judge) {
+  if (!ctx) return SM_EINVAL;
+  if (mode == 0 || !c) {
+    ctx->hook_obj = nullptr;
+    ctx->pre_solve = nullptr;
+    ctx->post_solve = nullptr;
+    return SM_OK;
+  }
+  if ((mode != 1 && mode != 2) || per_solve < 1 || stride < 1 || !c->arena || !(judge > 0.0)) return SM_EINVAL;
+  if (per_solve > c->max_boxes) return SM_EINVAL;
+  c->mode = mode;
+  c->per_solve = per_solve;
+  c->stride = stride;
+  c->taper = taper != 0;
+  c->judge = judge;
+  ctx->hook_obj = c;
+  ctx->pre_solve = cnn_pre_solve;
+  ctx->post_solve = cnn_post_solve;
+  return SM_OK;
+}
+
+extern "C" int sm_cnn_stats(const sm_cnn *c, int *n_samples, long long *predictions, long long *kept,
+                            double *last_rel) {
+  if (!c) return SM_EINVAL;
+  if (n_samples) *n_samples = c->n_samples;
+  if (predictions) *predictions = c->predictions;
+  if (kept) *kept = c->kept;
+  if (last_rel) {
+    last_rel[0] = c->last_rel_plain;
+    last_rel[1] = c->last_rel_cnn;
+  }
+  return SM_OK;
+}
+
+extern "C" const char *sm_cnn_last_error(const sm_cnn *c) { return c ? c->err.c_str() : "null network"; }

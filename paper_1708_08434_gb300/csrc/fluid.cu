@@ -504,8 +504,10 @@ extern "C" int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, do
   // stage 1: n1 = n0 + dt F(n0); new field
   if ((st = stage(ctx, A, B, -1, dt, q, eps, 0))) return st;
   int c1 = 0, c2 = 0, st1, st2;
+  if (ctx->pre_solve && (st = ctx->pre_solve(ctx->hook_obj, ctx))) return st;
   st1 = sm_mg_solve(ctx, tol, max_cycles, &c1, nullptr);
   if (st1 && st1 != SM_ENOCONV) return st1;
+  if (ctx->post_solve && (st = ctx->post_solve(ctx->hook_obj, ctx))) return st;
   if ((st = sm_compute_field(ctx))) return st;
   // stage 2: n = (n0 + n1 + dt F(n1))/2 with the time-step limits at n1
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_ADV, 0, 3 * sizeof(unsigned long long), ctx->stream));
@@ -513,8 +515,10 @@ extern "C" int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, do
   ctx->ncur = C;
   double dtn = 0.0;
   if ((st = dt_from_slots(ctx, q, eps, &dtn))) return st;
+  if (ctx->pre_solve && (st = ctx->pre_solve(ctx->hook_obj, ctx))) return st;
   st2 = sm_mg_solve(ctx, tol, max_cycles, &c2, nullptr);
   if (st2 && st2 != SM_ENOCONV) return st2;
+  if (ctx->post_solve && (st = ctx->post_solve(ctx->hook_obj, ctx))) return st;
   if ((st = sm_compute_field(ctx))) return st;
   if (dt_next) *dt_next = dtn;
   if (cycles) {

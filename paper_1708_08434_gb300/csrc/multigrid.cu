@@ -785,6 +785,14 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
   return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
 }
 
+// relative residual of the current potential (denominator recomputed);
+// leaves the coarse interpolation values of phi current
+int sm_rel_residual_now(sm_ctx *ctx, double *rel) {
+  int st = solve_prologue(ctx);
+  if (st) return st;
+  return rel_residual(ctx, rel);
+}
+
 extern "C" int sm_fill_ghosts(sm_ctx *ctx, int var, int level) {
   int st = check_ready(ctx);
   if (st) return st;

@@ -99,6 +99,11 @@ struct sm_ctx {
   // kernels launched so far (diagnostics)
   long long n_launch = 0;
 
+  // optional hooks around the solves of sm_advance_fluid (learned warm start)
+  void *hook_obj = nullptr;
+  int (*pre_solve)(void *, sm_ctx *) = nullptr;
+  int (*post_solve)(void *, sm_ctx *) = nullptr;
+
   // captured solves (invalidated when the octree changes)
   bool graphs = true;
   cudaStream_t cap = nullptr, cap2 = nullptr;

@@ -344,3 +344,23 @@ def blob_rho(n: int, blobs) -> np.ndarray:
     for cx, cy, cz, sg, a in blobs:
         rho += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) / (2 * sg * sg))
     return rho
+
+
+# --------------------------------------------------------------------------
+# initial weights of the learned warm-start network (He-normal from
+# SplitMix64 through Box-Muller; biases zero)
+# --------------------------------------------------------------------------
+CNN_LAYERS = ((16, 2), (16, 16), (1, 16))   # (out, in) channels, 3^3 taps
+
+
+def cnn_initial_params(seed: int = SEED, gain: float = 1.0) -> np.ndarray:
+    parts = []
+    ctr = 0
+    for co, ci in CNN_LAYERS:
+        n = co * ci * 27
+        u = uniform01(seed ^ 0xC0117, np.arange(ctr, ctr + 2 * n, dtype=np.uint64))
+        ctr += 2 * n
+        z = np.sqrt(-2.0 * np.log(1.0 - u[:n])) * np.cos(2.0 * np.pi * u[n:])
+        parts.append(gain * z * np.sqrt(2.0 / (ci * 27)))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
