@@ -35,6 +35,7 @@ MAX_CYCLES = 40
 SOLVES_PER_STEP = 3
 L2_BYTES = 129 * 2 ** 20
 NO_GRAPHS = False
+NO_PDL = False
 
 
 def parse():
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels from the host instead of CUDA graphs "
                          "(profilers cannot see kernels inside conditional graph nodes)")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="launch the solver kernels without programmatic dependent launch")
     ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch"],
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
@@ -137,6 +140,8 @@ def build_gpu_case(precision=0):
     g = pkg.Solver(dom, max_boxes=8192, precision=precision)
     if NO_GRAPHS:
         g.set_graphs(False)
+    if NO_PDL:
+        g.set_pdl(False)
     g.build_octree()
     synth.refine_all(dom, st, g.level_ijk, g.refine_level)
     t = g.tables()
@@ -518,9 +523,10 @@ def run_reference(args):
 
 
 def main():
-    global NO_GRAPHS
+    global NO_GRAPHS, NO_PDL
     args = parse()
     NO_GRAPHS = args.no_graphs
+    NO_PDL = args.no_pdl
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":

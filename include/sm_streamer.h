@@ -242,6 +242,13 @@ int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, lo
  * Both paths launch the same kernels in the same order. */
 int sm_set_graphs(sm_ctx *ctx, int enable);
 
+/* Kernels of the multigrid solve are launched with programmatic dependent
+ * launch when enabled (default): a kernel may be scheduled while its
+ * predecessor on the stream drains, and waits for that predecessor's
+ * completion and memory before its first access, so results are identical
+ * with the switch on or off.  Captured graphs are dropped on a change. */
+int sm_set_pdl(sm_ctx *ctx, int enable);
+
 /* Number of kernels this context has launched since it was created
  * (diagnostics: lets a caller count device launches inside a region). */
 int sm_launch_count(const sm_ctx *ctx, long long *n);

@@ -56,7 +56,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_refine_level", "sm_get_tables", "sm_var_ptr", "sm_upload", "sm_download",
            "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
-           "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs",
+           "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs", "sm_set_pdl",
            "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
@@ -106,6 +106,7 @@ def load():
         "sm_advance_fluid": [P, D, D, D, D, I, pD, pI],
         "sm_kernel_bench": [P, I, I, pD, C.POINTER(C.c_longlong), pD],
         "sm_set_graphs": [P, I],
+        "sm_set_pdl": [P, I],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
         "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
@@ -344,6 +345,10 @@ class Solver:
     # -- diagnostics --
     def set_graphs(self, enable: bool):
         self._ck(self._lib.sm_set_graphs(self._h, int(enable)))
+
+    def set_pdl(self, enable: bool):
+        """Programmatic dependent launch of the solver kernels on or off."""
+        self._ck(self._lib.sm_set_pdl(self._h, int(enable)))
 
     def kernel_bench(self, kclass: int = K_SMOOTH, reps: int = 10):
         us, n, by = C.c_double(), C.c_longlong(), C.c_double()

@@ -19,23 +19,61 @@ using namespace sm;
 // kernels
 // ---------------------------------------------------------------------------
 
+// position of interior cell c (i + 8j + 64k) in a 10^3 staging array
+__device__ __forceinline__ int s10(int c) { return ((c & 7) + 1) + 10 * (((c >> 3) & 7) + 1) + 100 * ((c >> 6) + 1); }
+
+// Stage box b of variable v and its six face halos (ghost values by the
+// rules of pot_ghost, evaluated from the staged interior) in s[1000].
+// Blocks of NT threads (a multiple of 64); face f is filled by the 64-thread
+// group f mod (NT/64), the face loop unrolled so that f is a constant.
+template <int NT, typename T>
+__device__ __forceinline__ void stage_box(T *s, const T *__restrict__ v, const int32_t *__restrict__ nbr6,
+                                          const T *__restrict__ gh, int b, const Bc &bc, int homog) {
+  const T *p = v + (size_t)b * CELLS;
+#pragma unroll
+  for (int c = threadIdx.x; c < CELLS; c += NT) s[s10(c)] = p[c];
+  __syncthreads();
+  const int grp = threadIdx.x >> 6, u = threadIdx.x & 7, w = (threadIdx.x >> 3) & 7;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (grp != f % (NT / 64)) continue;
+    const int a = f >> 1;
+    const int i = a == 0 ? ((f & 1) ? NC - 1 : 0) : (a == 1 ? w : u);
+    const int j = a == 1 ? ((f & 1) ? NC - 1 : 0) : (a == 2 ? w : u);
+    const int k = a == 2 ? ((f & 1) ? NC - 1 : 0) : (a == 0 ? w : u);
+    const int q = s10(cidx(i, j, k));
+    const int stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
+    s[q + ((f & 1) ? stride : -stride)] = pot_ghost(v, nbr6, gh, b, f, i, j, k, s[q], bc, homog);
+  }
+  __syncthreads();
+}
+
+// sum of the six neighbours from a staged box (order -x,+x,-y,+y,-z,+z)
+template <typename T>
+__device__ __forceinline__ T staged_sum(const T *s, int q) {
+  return s[q - 1] + s[q + 1] + s[q - 10] + s[q + 10] + s[q - 100] + s[q + 100];
+}
+
 // One colour of a Gauss-Seidel red-black sweep over the boxes [lo, lo+grid)
 // of one level: phi = (sum of 6 neighbours - h^2 f)/6 on cells with
 // (i+j+k) % 2 == color (level-global parity; box origins are multiples of
-// 8).  One block of 256 threads per box, one thread per cell of the colour.
+// 8).  One block of 256 threads per box: the box and its face halos are
+// staged in shared memory, then one thread per cell of the colour.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rbgs(int lo, int color, T *__restrict__ phi, const T *__restrict__ rhs,
                                               const T *__restrict__ gh, const int32_t *__restrict__ nbr6, Bc bc,
                                               T h2, int homog) {
+  __shared__ T s[1000];
+  pdl_wait();
   int b = lo + blockIdx.x;
+  stage_box<256>(s, phi, nbr6, gh, b, bc, homog);
   int t = threadIdx.x;
   int k = t >> 5, j = (t >> 2) & 7;
   int i = ((t & 3) << 1) | ((j + k + color) & 1);
   int c = cidx(i, j, k);
   size_t base = (size_t)b * CELLS;
-  T ctr = phi[base + c];
-  T s = nb_sum(phi, nbr6, gh, b, i, j, k, ctr, bc, homog);
-  phi[base + c] = (s - h2 * rhs[base + c]) * T(1.0 / 6.0);
+  T sum = staged_sum(s, s10(c));
+  phi[base + c] = (sum - h2 * rhs[base + c]) * T(1.0 / 6.0);
 }
 
 // plain 8-child average of one or two variables (FMG right-hand side,
@@ -44,6 +82,7 @@ template <typename T>
 __global__ void __launch_bounds__(64) k_restrict1(int lo, const int32_t *__restrict__ parent,
                                                   const int32_t *__restrict__ ijk, T *__restrict__ a,
                                                   T *__restrict__ a2) {
+  pdl_wait();
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
@@ -73,6 +112,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_fas(int lo, T *__restrict__ phi, T *__restrict__ old, T *__restrict__ rhs,
                                              const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
                                              const int32_t *__restrict__ child, Bc bc, T inv_h2, int homog) {
+  pdl_wait();
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   size_t base = (size_t)b * CELLS;
@@ -147,6 +187,7 @@ __global__ void __launch_bounds__(64) k_fill_cf(int lo, const T *__restrict__ v,
                                                 const int32_t *__restrict__ parent,
                                                 const int32_t *__restrict__ ijk, Bc bc, int homog,
                                                 unsigned long long *err) {
+  pdl_wait();
   int b = lo + blockIdx.x;
   int u = threadIdx.x & 7, w = threadIdx.x >> 3;
   for (int f = 0; f < 6; ++f) {
@@ -160,6 +201,7 @@ __global__ void __launch_bounds__(64) k_fill_cf(int lo, const T *__restrict__ v,
 // Dirichlet (ghost = -inner) ends: cosine (NN), sine (DD) and quarter-wave
 // sine (DN, ND) families.  basis[a*64 + i*8 + m] = component i of vector m.
 __global__ void k_coarse_basis(double *basis, Bc bc, int n) {
+  pdl_wait();
   int t = threadIdx.x;
   if (t >= 3 * n) return;
   int a = t / n, m = t % n;
@@ -189,6 +231,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_coarse_solve(T *__restrict__ phi, const T *__restrict__ rhs,
                                                       const double *__restrict__ basis, Bc bc, double h2,
                                                       double inv_h2, int homog) {
+  pdl_wait();
   __shared__ double x[CELLS], y[CELLS], V[3][64], lam[3][8];
   int t = threadIdx.x;
   if (t < 192) V[t / 64][t % 64] = basis[t];
@@ -236,6 +279,7 @@ __global__ void __launch_bounds__(512) k_resnorm(const int32_t *__restrict__ lea
                                                  const double *__restrict__ gh,
                                                  const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
                                                  unsigned long long *slot) {
+  pdl_wait();
   __shared__ double red[16];
   int b = leaf[blockIdx.x];
   int t = threadIdx.x;
@@ -256,6 +300,7 @@ __global__ void __launch_bounds__(512) k_resid_to32(const int32_t *__restrict__ 
                                                     const double *__restrict__ gh,
                                                     const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
                                                     float *__restrict__ f32, unsigned long long *slot) {
+  pdl_wait();
   __shared__ double red[16];
   int b = leaf[blockIdx.x];
   int t = threadIdx.x;
@@ -271,14 +316,15 @@ __global__ void __launch_bounds__(512) k_resid_to32(const int32_t *__restrict__ 
 // FP64 accumulation of the FP32 correction on leaf cells
 __global__ void __launch_bounds__(512) k_add_corr(const int32_t *__restrict__ leaf, double *__restrict__ phi,
                                                   const float *__restrict__ e32) {
+  pdl_wait();
   size_t x = (size_t)leaf[blockIdx.x] * CELLS + threadIdx.x;
   phi[x] += (double)e32[x];
 }
 
 // Residual and restriction fused: one block per fine box of level l
-// computes r = f - L phi for its 512 cells, then its 64 parent cells get
-// the 8-child averages of phi (into phi) and of r (into rhs, completed to
-// the FAS right-hand side by k_fas).
+// computes r = f - L phi for its 512 cells (box staged with its face
+// halos), then its 64 parent cells get the 8-child averages of phi (into
+// phi) and of r (into rhs, completed to the FAS right-hand side by k_fas).
 template <typename T>
 __global__ void __launch_bounds__(512) k_resid_restrict(int lo, T *__restrict__ phi, T *__restrict__ rhs,
                                                         const T *__restrict__ gh,
@@ -286,15 +332,15 @@ __global__ void __launch_bounds__(512) k_resid_restrict(int lo, T *__restrict__ 
                                                         const int32_t *__restrict__ parent,
                                                         const int32_t *__restrict__ ijk, Bc bc, T inv_h2,
                                                         int homog) {
-  __shared__ T sp[CELLS], sr[CELLS];
+  __shared__ T s[1000], sr[CELLS];
+  pdl_wait();
   int b = lo + blockIdx.x;
+  stage_box<512>(s, phi, nbr6, gh, b, bc, homog);
   int t = threadIdx.x;
-  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
   size_t base = (size_t)b * CELLS;
-  T p = phi[base + t];
-  T s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, homog);
-  sp[t] = p;
-  sr[t] = rhs[base + t] - (s - T(6) * p) * inv_h2;
+  int q = s10(t);
+  T p = s[q];
+  sr[t] = rhs[base + t] - (staged_sum(s, q) - T(6) * p) * inv_h2;
   __syncthreads();
   if (t >= 64) return;
   int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
@@ -308,7 +354,7 @@ __global__ void __launch_bounds__(512) k_resid_restrict(int lo, T *__restrict__ 
 #pragma unroll
       for (int di = 0; di < 2; ++di) {
         int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
-        ap += sp[c];
+        ap += s[s10(c)];
         ar += sr[c];
       }
   size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
@@ -329,6 +375,7 @@ __global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, T *__restr
                                                     const int32_t *__restrict__ parent,
                                                     const int32_t *__restrict__ ijk, Bc bc, int homog,
                                                     unsigned long long *err) {
+  pdl_wait();
   int b = lo + blockIdx.x;
   int t = threadIdx.x;
   int P = parent[b];
@@ -366,6 +413,7 @@ __global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, T *__restr
 // last norm, cycle count (+inc), and the loop condition
 // rel > tol && cycles < max.
 __global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *sc, int inc) {
+  pdl_wait();
   double num = __longlong_as_double((long long)sc[SC_NORM]);
   double den = __longlong_as_double((long long)sc[SC_DEN]);
   double rel = den > 0.0 ? num / den : num;
@@ -395,9 +443,8 @@ int sm_mg_fill_cf(sm_ctx *ctx, double *var, int l, int homog) {
   if (l <= ctx->lbase || l >= ctx->n_levels) return SM_OK;  // uniform levels: no refinement faces
   int n = lvl_n(ctx, l);
   if (n == 0) return SM_OK;
-  k_fill_cf<double><<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], var, ctx->gh, ctx->nbr6, ctx->parent,
-                                               ctx->ijk, ctx->bc, homog, ctx->dscal + SC_ERR);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_fill_cf<double>, n, 64, 0, ctx->level_off[l], var, ctx->gh, ctx->nbr6, ctx->parent,
+            ctx->ijk, ctx->bc, homog, ctx->dscal + SC_ERR);
   SM_CKL("fill_cf");
   return SM_OK;
 }
@@ -415,8 +462,7 @@ static int restrict_chain(sm_ctx *ctx, T *a, T *a2) {
   for (int l = ctx->n_levels - 1; l >= 1; --l) {
     int n = lvl_n(ctx, l);
     if (!n) continue;
-    k_restrict1<T><<<n, 64, 0, ctx->stream>>>(ctx->level_off[l], ctx->parent, ctx->ijk, a, a2);
-    ++ctx->n_launch;
+    sm_launch(ctx, k_restrict1<T>, n, 64, 0, ctx->level_off[l], ctx->parent, ctx->ijk, a, a2);
   }
   SM_CKL("restrict");
   return SM_OK;
@@ -427,9 +473,8 @@ int sm_restrict_pair(sm_ctx *ctx, double *a, double *a2) { return restrict_chain
 
 template <typename T>
 static int rbgs_pass(sm_ctx *ctx, const MG<T> &m, int l, int color) {
-  k_rbgs<T><<<lvl_n(ctx, l), 256, 0, ctx->stream>>>(ctx->level_off[l], color, m.phi, m.rhs, m.gh, ctx->nbr6,
-                                                    ctx->bc, (T)ctx->lh.h2[l], m.homog);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_rbgs<T>, lvl_n(ctx, l), 256, 0, ctx->level_off[l], color, m.phi, m.rhs, m.gh, ctx->nbr6,
+            ctx->bc, (T)ctx->lh.h2[l], m.homog);
   return SM_OK;
 }
 
@@ -444,8 +489,7 @@ static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu) {
 
 static int ensure_basis(sm_ctx *ctx) {
   if (!ctx->basis_ready) {
-    k_coarse_basis<<<1, 32, 0, ctx->stream>>>(ctx->basis, ctx->bc, NC);
-    ++ctx->n_launch;
+    sm_launch(ctx, k_coarse_basis, 1, 32, 0, ctx->basis, ctx->bc, NC);
     SM_CKL("coarse basis");
     ctx->basis_ready = true;
   }
@@ -456,19 +500,17 @@ template <typename T>
 static int coarse_solve(sm_ctx *ctx, const MG<T> &m) {
   int st = ensure_basis(ctx);
   if (st) return st;
-  k_coarse_solve<T><<<1, 512, 0, ctx->stream>>>(m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
-                                                ctx->lh.inv_h2[0], m.homog);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_coarse_solve<T>, 1, 512, 0, m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
+            ctx->lh.inv_h2[0], m.homog);
   SM_CKL("coarse solve");
   return SM_OK;
 }
 
 template <typename T>
 static int prolong_cf(sm_ctx *ctx, const MG<T> &m, int l, int mode) {
-  k_prolong_cf<T><<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], mode, m.phi, m.old, m.gh,
-                                                          ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, m.homog,
-                                                          ctx->dscal + SC_ERR);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_prolong_cf<T>, lvl_n(ctx, l), 512, 0, ctx->level_off[l], mode, m.phi, m.old, m.gh,
+            ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, m.homog,
+            ctx->dscal + SC_ERR);
   SM_CKL("prolong");
   return SM_OK;
 }
@@ -483,14 +525,12 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top) {
   int st;
   for (int l = top; l >= 1; --l) {
     if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
-    k_resid_restrict<T><<<lvl_n(ctx, l), 512, 0, ctx->stream>>>(ctx->level_off[l], m.phi, m.rhs, m.gh,
-                                                                ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
-                                                                (T)ctx->lh.inv_h2[l], m.homog);
-    ++ctx->n_launch;
-    k_fas<T><<<lvl_n(ctx, l - 1), 512, 0, ctx->stream>>>(ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
-                                                         ctx->nbr6, ctx->child, ctx->bc,
-                                                         (T)ctx->lh.inv_h2[l - 1], m.homog);
-    ++ctx->n_launch;
+    sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), 512, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
+              ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
+              (T)ctx->lh.inv_h2[l], m.homog);
+    sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), 512, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+              ctx->nbr6, ctx->child, ctx->bc,
+              (T)ctx->lh.inv_h2[l - 1], m.homog);
     SM_CKL("vcycle down");
   }
   if ((st = coarse_solve(ctx, m))) return st;
@@ -519,9 +559,8 @@ static int fmg_ladder(sm_ctx *ctx, const MG<T> &m) {
 // max_leaf |f - L v| into slot (v's refinement ghosts must be current)
 static int leaf_norm(sm_ctx *ctx, double *v, int slot) {
   SM_CK(cudaMemsetAsync(ctx->dscal + slot, 0, sizeof(unsigned long long), ctx->stream));
-  k_resnorm<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->level, v, ctx->rhs, ctx->gh, ctx->nbr6,
-                                                    ctx->bc, ctx->lh, ctx->dscal + slot);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_resnorm, ctx->n_leaves, 512, 0, ctx->leaf, ctx->level, v, ctx->rhs, ctx->gh, ctx->nbr6,
+            ctx->bc, ctx->lh, ctx->dscal + slot);
   SM_CKL("resnorm");
   return SM_OK;
 }
@@ -529,10 +568,9 @@ static int leaf_norm(sm_ctx *ctx, double *v, int slot) {
 // outer FP64 residual of the mixed form: norm into SC_NORM, f32 = (float) r
 static int leaf_resid32(sm_ctx *ctx) {
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_NORM, 0, sizeof(unsigned long long), ctx->stream));
-  k_resid_to32<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->level, ctx->phi, ctx->rhs, ctx->gh,
-                                                       ctx->nbr6, ctx->bc, ctx->lh, ctx->f32,
-                                                       ctx->dscal + SC_NORM);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_resid_to32, ctx->n_leaves, 512, 0, ctx->leaf, ctx->level, ctx->phi, ctx->rhs, ctx->gh,
+            ctx->nbr6, ctx->bc, ctx->lh, ctx->f32,
+            ctx->dscal + SC_NORM);
   SM_CKL("resid32");
   return SM_OK;
 }
@@ -551,8 +589,7 @@ static int mixed_correction(sm_ctx *ctx, int ladder) {
   if (ladder) st = fmg_ladder(ctx, m);
   else st = vcycle(ctx, m, ctx->n_levels - 1);
   if (st) return st;
-  k_add_corr<<<ctx->n_leaves, 512, 0, ctx->stream>>>(ctx->leaf, ctx->phi, ctx->e32);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_add_corr, ctx->n_leaves, 512, 0, ctx->leaf, ctx->phi, ctx->e32);
   SM_CKL("add correction");
   if ((st = restrict_chain<double>(ctx, ctx->phi, nullptr))) return st;
   if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
@@ -701,8 +738,7 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   n0 = ctx->n_launch;
   if ((st = solve_prefix(ctx, kind))) return end_captures(ctx, saved, st);
   if (fmg) {
-    k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal, 1);
-    ++ctx->n_launch;
+    sm_launch(ctx, k_loop_check, 1, 1, 0, h, ctx->dscal, 1);
   }
   out->prefix_launches = ctx->n_launch - n0;
   if (cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess)
@@ -723,8 +759,7 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   ctx->stream = ctx->cap2;
   n0 = ctx->n_launch;
   if ((st = solve_body(ctx, kind))) return end_captures(ctx, saved, st);
-  k_loop_check<<<1, 1, 0, ctx->stream>>>(h, ctx->dscal, 1);
-  ++ctx->n_launch;
+  sm_launch(ctx, k_loop_check, 1, 1, 0, h, ctx->dscal, 1);
   out->body_launches = ctx->n_launch - n0;
   if (cudaStreamEndCapture(ctx->cap2, &body) != cudaSuccess)
     return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end body capture"));
@@ -831,6 +866,13 @@ extern "C" int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, d
 extern "C" int sm_set_graphs(sm_ctx *ctx, int enable) {
   if (!ctx) return SM_EINVAL;
   ctx->graphs = enable != 0;
+  return SM_OK;
+}
+
+extern "C" int sm_set_pdl(sm_ctx *ctx, int enable) {
+  if (!ctx) return SM_EINVAL;
+  if (ctx->pdl != (enable != 0)) sm_drop_graphs(ctx);
+  ctx->pdl = enable != 0;
   return SM_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sm_streamer.h"
@@ -106,6 +107,7 @@ struct sm_ctx {
 
   // captured solves (invalidated when the octree changes)
   bool graphs = true;
+  bool pdl = true;  // programmatic dependent launch between level kernels
   cudaStream_t cap = nullptr, cap2 = nullptr;
   sm_graph g_solve, g_fmg, g_solve32, g_fmg32;
 
@@ -155,6 +157,10 @@ __device__ __forceinline__ int cidx(int i, int j, int k) { return i + NC * j + F
 __device__ __forceinline__ int fcell(int a, int i, int j, int k) {
   return a == 0 ? (j + NC * k) : (a == 1 ? (k + NC * i) : (i + NC * j));
 }
+
+// wait for the predecessor grid of a programmatic dependent launch (a
+// no-op for a normal launch)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // atomic max of a non-negative double through its bit pattern
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *slot, double v) {
@@ -221,6 +227,27 @@ __device__ __forceinline__ T nb_sum(const T *__restrict__ v, const int32_t *__re
 }
 
 }  // namespace sm
+
+// Launch with programmatic dependent launch when enabled: the kernel may
+// be scheduled while its predecessor drains; every kernel launched this way
+// starts with sm::pdl_wait(), so it still reads nothing before the
+// predecessor has finished and its writes are visible.
+template <typename... KArgs, typename... Args>
+inline cudaError_t sm_launch(sm_ctx *ctx, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = ctx->pdl ? 1 : 0;
+  ++ctx->n_launch;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 // entry points implemented in the other translation units
 int sm_mg_fill_cf(sm_ctx *ctx, double *var, int level, int homog);

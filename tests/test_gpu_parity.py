@@ -237,27 +237,32 @@ def test_error_paths():
     assert rc == p.SM_ENOCONV and cyc == 2 and rel < 1e-2
 
 
-def test_graph_and_direct_paths_identical():
+def test_graph_direct_and_pdl_paths_identical():
     """Captured solves (device-side cycle loop) launch the same kernels in
-    the same order as the host-driven path: results are bit-identical."""
+    the same order as the host-driven path, and programmatic dependent
+    launch only lets a kernel start waiting early: all four combinations
+    give bit-identical results."""
     dom, st = synth.workload("streamer_small")
     p = pkg()
     out = []
     for graphs in (True, False):
-        g = gpu_mesh(dom, st)
-        g.set_graphs(graphs)
-        t = g.tables()
-        ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
-        g.upload(p.NE, ne); g.upload(p.NI, ni)
-        g.charge_rhs(Q, EPS0)
-        r1 = g.fmg(1e-9, 30)
-        r2 = g.solve(1e-11, 30)
-        out.append((r1, r2, g.download(p.PHI)))
-        g.close()
-    (a1, a2, pa), (b1, b2, pb) = out
-    assert a1[2] == b1[2] and a2[2] == b2[2]
-    assert a1[1] == b1[1] and a2[1] == b2[1]
-    assert np.array_equal(pa, pb)
+        for pdl in (True, False):
+            g = gpu_mesh(dom, st)
+            g.set_graphs(graphs)
+            g.set_pdl(pdl)
+            t = g.tables()
+            ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+            g.upload(p.NE, ne); g.upload(p.NI, ni)
+            g.charge_rhs(Q, EPS0)
+            r1 = g.fmg(1e-9, 30)
+            r2 = g.solve(1e-11, 30)
+            out.append((r1, r2, g.download(p.PHI)))
+            g.close()
+    a1, a2, pa = out[0]
+    for b1, b2, pb in out[1:]:
+        assert a1[2] == b1[2] and a2[2] == b2[2]
+        assert a1[1] == b1[1] and a2[1] == b2[1]
+        assert np.array_equal(pa, pb)
 
 
 def test_repeated_graph_launch_and_launch_count():
