@@ -36,6 +36,7 @@ SOLVES_PER_STEP = 3
 L2_BYTES = 129 * 2 ** 20
 NO_GRAPHS = False
 NO_PDL = False
+PERSIST = False
 
 
 def parse():
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels from the host instead of CUDA graphs "
                          "(profilers cannot see kernels inside conditional graph nodes)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="run V-cycles as one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the solver kernels without programmatic dependent launch")
     ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch"],
@@ -77,12 +80,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 arithmetic peak of GB300 (nominal 1.25 TFLOP/s; a DFMA loop measured
-# 1.19-1.20 TFLOP/s at 1.9-2.07 GHz, about 2 DFMA per clock per SM)
-FP64_PEAK_GFLOPS = 1250.0
-# one colour pass of the red-black smoother, per cell of the level:
-# 16 bytes (phi read, f and phi of the colour) and 4 flops (8 per updated cell)
-RBGS_FLOP_PER_BYTE = 4.0 / 16.0
+# FP64 pipe of GB300: 2 instructions per clock per SM (nominal 1.25 TFLOP/s
+# counting a fused multiply-add as 2; a DFMA loop measured 1.19-1.20 TFLOP/s
+# at 1.9-2.07 GHz), 152 SMs x 2.07 GHz x 2 = 629 G FP64 instructions/s
+FP64_PEAK_GINSTR = 629.0
 
 
 class Clocks:
@@ -142,6 +143,8 @@ def build_gpu_case(precision=0):
         g.set_graphs(False)
     if NO_PDL:
         g.set_pdl(False)
+    if PERSIST:
+        g.set_persistent(True)
     g.build_octree()
     synth.refine_all(dom, st, g.level_ijk, g.refine_level)
     t = g.tables()
@@ -266,23 +269,39 @@ def run_gpu(args):
         e2e_ms = float(tt.item())
     # roofline of the dominant kernel: the red-black smoother, timed with
     # CUDA events around a graph of its launches in the V-cycle mix (every
-    # level, both colours) on the state left by the timed steps
+    # level, both colours), or with --persistent the persistent V-cycle
+    # kernel (one cooperative launch per V-cycle, 20 launches); beside it the
+    # whole FP64 V-cycle of the per-level path (graph of 10 V-cycles)
     roof = None
     if not args.no_profile:
-        us, kn, kbytes = g.kernel_bench(pkg.K_SMOOTH, 20)
+        kclass = pkg.K_PERSIST if PERSIST else pkg.K_SMOOTH
+        us, kn, kbytes, kflops = g.kernel_bench(kclass, 20)
         peak, kind = measured_peaks()
         gbs = kbytes / (us * 1e-6) / 1e9
-        gflops = gbs * RBGS_FLOP_PER_BYTE
-        # FP64 at 1/64 rate makes the smoother ALU-bound: 4 flop per 16 B
-        # needs 1.7 TFLOP/s to keep up with HBM, above the FP64 peak
-        roof = {"bound": "alu", "achieved": round(gflops, 2), "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s (fp64)", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
-                "traffic": None, "kernel": "k_rbgs", "launches": kn,
+        ginstr = kflops / (us * 1e-6) / 1e9
+        # FP64 at 1/64 rate makes the level operations ALU-bound: a smoothing
+        # pass at 6780 GB/s moves 424 G cells/s and would need 3.5 x 424 =
+        # 1480 G FP64 instructions/s, above the 629 G/s of the FP64 pipe
+        roof = {"bound": "alu", "achieved": round(ginstr, 2), "peak": FP64_PEAK_GINSTR,
+                "unit": "G FP64 instructions/s", "frac": round(ginstr / FP64_PEAK_GINSTR, 4),
+                "traffic": None, "kernel": "k_persist" if PERSIST else "k_rbgs", "launches": kn,
                 "avg_launch_us": round(us, 3), "bytes_per_launch": round(kbytes),
+                "fp64_instr_per_launch": round(kflops),
                 "hbm": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 4), "peak_kind": kind},
-                "note": "mean over %d graph-launched colour passes of every level "
-                        "(the V-cycle mix), CUDA events on the launching stream" % kn}
+                "note": ("mean over %d graph-launched colour passes of every level "
+                         "(the V-cycle mix), CUDA events on the launching stream" % kn) if not PERSIST else
+                        ("mean over %d launches, each one whole FP64 V-cycle, CUDA events on the "
+                         "launching stream; bytes and FP64 instructions from the per-level model" % kn)}
+        if not PERSIST:
+            vus, vn, vbytes, vinstr = g.kernel_bench(pkg.K_VCYCLE, 10)
+            roof["vcycle"] = {"us": round(vus, 2), "cycles": vn, "bytes": round(vbytes),
+                              "fp64_instr": round(vinstr),
+                              "achieved": round(vinstr / (vus * 1e-6) / 1e9, 2),
+                              "frac": round(vinstr / (vus * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4),
+                              "hbm_frac": round(vbytes / (vus * 1e-6) / 1e9 / peak, 4),
+                              "note": "whole FP64 V-cycle, per-level launches in a CUDA graph, "
+                                      "model bytes and FP64 instructions"}
     # the same step with the mixed-precision solve (FP32 error equation in an
     # FP64 defect-correction loop) on a second solver of the same workload
     mixed = None
@@ -523,10 +542,11 @@ def run_reference(args):
 
 
 def main():
-    global NO_GRAPHS, NO_PDL
+    global NO_GRAPHS, NO_PDL, PERSIST
     args = parse()
     NO_GRAPHS = args.no_graphs
     NO_PDL = args.no_pdl
+    PERSIST = args.persistent
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":

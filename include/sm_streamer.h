@@ -225,22 +225,48 @@ int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
 
 /* ---- diagnostics ----------------------------------------------------------- */
 
-/* Average device time of one launch of a kernel class in the launch mix of
- * a V-cycle: one CUDA graph of `reps` repetitions of that class's launches
- * over every level 1..top (both colours of the red-black smoother for class
- * 0) is launched once to warm up and once between two CUDA events on the
- * context stream.  Out: microseconds per launch, launches timed, algorithmic
- * bytes per launch (16 per cell of the level: phi read, f and phi of the
- * colour).  Side effect: the potential receives 2 x reps extra sweeps.
- * Classes: 0 = red-black smoother. */
+/* Average device time of one launch of a kernel class, timed on the context
+ * stream between two CUDA events after one untimed warm-up.
+ *   class 0 (red-black smoother): one CUDA graph of `reps` repetitions of
+ *     both colour passes over every level 1..top, the launch mix of a
+ *     V-cycle; algorithmic bytes 16 per cell of the level (phi read, f and
+ *     phi of the colour), FP64 instructions 3.5 per cell (5 adds, 1 fused
+ *     multiply-add and 1 multiply per updated cell).
+ *   class 1 (persistent V-cycle, Sec. 2.1.2): `reps` cooperative launches of
+ *     the persistent kernel, each one whole FP64 FAS V-cycle; algorithmic
+ *     bytes and FP64 instructions per V-cycle from the per-level model:
+ *     smoothing 16 B and 3.5 per cell and colour pass; residual with
+ *     restriction 18 B and 9 per fine cell; FAS completion 16 B per cell of
+ *     the level below plus 16 B and 7 per cell of its refined boxes;
+ *     prolongation 18 B and 8 per fine cell; level-0 solve 16 B and 60 per
+ *     cell.  Ghost-value arithmetic is not counted.
+ *   class 2 (V-cycle as per-level launches): one CUDA graph of `reps` FP64
+ *     V-cycles launched level by level; the unit is one V-cycle, bytes and
+ *     instructions as for class 1.
+ * Out (each may be NULL): microseconds per launch, launches timed,
+ * algorithmic bytes and FP64 instructions per launch.  Side effect: the
+ * potential receives the extra sweeps or cycles.  Errors: SM_EINVAL for an
+ * unknown class, reps < 1 or a single-level octree. */
 int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, long long *launches,
-                    double *bytes_per_launch);
+                    double *bytes_per_launch, double *fp64_per_launch);
 
 /* Solves run as CUDA graphs (captured on first use per octree, with the
  * cycle loop and its stopping test on the device) when enabled (default),
  * or as individually launched kernels with a host loop when disabled.
  * Both paths launch the same kernels in the same order. */
 int sm_set_graphs(sm_ctx *ctx, int enable);
+
+/* V-cycles run as one persistent cooperative launch when enabled (default
+ * off: on GB300 a software grid barrier between phases costs more than a
+ * kernel boundary inside a CUDA graph):
+ * every block stays resident, each level operation is one phase over all
+ * boxes of the level with a grid barrier after it, and the FP64 solves keep
+ * their residual test and cycle loop inside the same launch.  Disabled, the
+ * same per-box operations run as one launch per level and phase.  Both give
+ * bit-identical results.  A barrier wait that runs out (about a second)
+ * ends the launch and the solve returns SM_ETIMEOUT.  Captured graphs are
+ * dropped on a change. */
+int sm_set_persistent(sm_ctx *ctx, int enable);
 
 /* Kernels of the multigrid solve are launched with programmatic dependent
  * launch when enabled (default): a kernel may be scheduled while its

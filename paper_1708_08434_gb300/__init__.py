@@ -22,6 +22,8 @@ PHI, RHS, RES, NE, NI, EMAG, RHO = range(7)
 FP64, MIXED = 0, 1
 MAX_LEVELS = 24
 K_SMOOTH = 0
+K_PERSIST = 1
+K_VCYCLE = 2
 
 _NAMES = {SM_EINVAL: "SM_EINVAL", SM_ENOMEM: "SM_ENOMEM", SM_ECUDA: "SM_ECUDA",
           SM_ENOCONV: "SM_ENOCONV", SM_ETIMEOUT: "SM_ETIMEOUT", SM_ESTATE: "SM_ESTATE"}
@@ -57,6 +59,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs", "sm_set_pdl",
+           "sm_set_persistent",
            "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
@@ -104,9 +107,10 @@ def load():
         "sm_dt_limit": [P, D, D, pD],
         "sm_fluid_stage": [P, D],
         "sm_advance_fluid": [P, D, D, D, D, I, pD, pI],
-        "sm_kernel_bench": [P, I, I, pD, C.POINTER(C.c_longlong), pD],
+        "sm_kernel_bench": [P, I, I, pD, C.POINTER(C.c_longlong), pD, pD],
         "sm_set_graphs": [P, I],
         "sm_set_pdl": [P, I],
+        "sm_set_persistent": [P, I],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
         "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
@@ -351,9 +355,17 @@ class Solver:
         self._ck(self._lib.sm_set_pdl(self._h, int(enable)))
 
     def kernel_bench(self, kclass: int = K_SMOOTH, reps: int = 10):
-        us, n, by = C.c_double(), C.c_longlong(), C.c_double()
-        self._ck(self._lib.sm_kernel_bench(self._h, kclass, reps, C.byref(us), C.byref(n), C.byref(by)))
-        return us.value, n.value, by.value
+        """(microseconds per launch, launches, algorithmic bytes and FP64
+        operations per launch) of a kernel class."""
+        us, n, by, fl = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        self._ck(self._lib.sm_kernel_bench(self._h, kclass, reps, C.byref(us), C.byref(n), C.byref(by),
+                                           C.byref(fl)))
+        return us.value, n.value, by.value, fl.value
+
+    def set_persistent(self, enable: bool):
+        """V-cycles as one persistent cooperative launch, or as per-level
+        launches (default)."""
+        self._ck(self._lib.sm_set_persistent(self._h, int(enable)))
 
     def launch_count(self) -> int:
         n = C.c_longlong()

@@ -385,6 +385,7 @@ static int rebuild_leaves(sm_ctx *ctx) {
   SM_CK(cudaStreamSynchronize(ctx->stream));
   for (int l = 0; l <= ctx->n_levels; ++l) ctx->leaf_level_off[l] = h[l];
   ctx->n_leaves = h[ctx->n_levels];
+  ctx->pdl_fence = true;  // level kernels read the new tables before their PDL wait
   return SM_OK;
 }
 

@@ -16,36 +16,97 @@
 using namespace sm;
 
 // ---------------------------------------------------------------------------
-// kernels
+// per-box work of the level operations
 // ---------------------------------------------------------------------------
+//
+// Every level operation processes one 8^3 box with a group of GT threads.
+// In the per-level kernels the group is the whole block (barrier 0); in the
+// persistent kernel it is one of the PGROUPS groups of a block (named
+// barriers 1..PGROUPS), each taking boxes in turn.
+
+constexpr int GT = 128;             // threads of a box group
+constexpr int CPT = CELLS / GT;     // cells per thread
+constexpr int RPT = CELLS / 2 / GT; // cells of one colour per thread
+constexpr int NSL = GT / 64;        // 64-thread slices of a group (one face cell each)
+constexpr int FPS = 6 / NSL;        // faces per slice
+constexpr int PGROUPS = 8;          // box groups per block of the persistent kernel
+static_assert(CELLS % GT == 0 && 6 % NSL == 0, "group size");
+
+struct Grp {
+  int t;    // thread within the group
+  int bar;  // hardware barrier of the group
+  __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(GT) : "memory"); }
+};
 
 // position of interior cell c (i + 8j + 64k) in a 10^3 staging array
 __device__ __forceinline__ int s10(int c) { return ((c & 7) + 1) + 10 * (((c >> 3) & 7) + 1) + 100 * ((c >> 6) + 1); }
 
-// Stage box b of variable v and its six face halos (ghost values by the
-// rules of pot_ghost, evaluated from the staged interior) in s[1000].
-// Blocks of NT threads (a multiple of 64); face f is filled by the 64-thread
-// group f mod (NT/64), the face loop unrolled so that f is a constant.
-template <int NT, typename T>
-__device__ __forceinline__ void stage_box(T *s, const T *__restrict__ v, const int32_t *__restrict__ nbr6,
-                                          const T *__restrict__ gh, int b, const Bc &bc, int homog) {
-  const T *p = v + (size_t)b * CELLS;
+// interior cell next to face f at face coordinates (u, w): u runs along
+// axis (a+1)%3 and w along (a+2)%3 of the face axis a
+__device__ __forceinline__ int face_cell(int f, int u, int w) {
+  const int a = f >> 1, e = (f & 1) ? NC - 1 : 0;
+  return a == 0 ? cidx(e, u, w) : (a == 1 ? cidx(w, e, u) : cidx(u, w, e));
+}
+
+// neighbour-table entries of the faces a thread fills while staging box b
+// (face f belongs to the 64-thread slice f mod NSL); the tables do not
+// change during a solve, so kernels read them before waiting on their
+// predecessor
+struct Nb {
+  int v[FPS];
+};
+
+__device__ __forceinline__ Nb load_nb(const Grp &g, const int32_t *__restrict__ nbr6, int b) {
+  Nb nb;
+  const int slice = g.t >> 6;
 #pragma unroll
-  for (int c = threadIdx.x; c < CELLS; c += NT) s[s10(c)] = p[c];
-  __syncthreads();
-  const int grp = threadIdx.x >> 6, u = threadIdx.x & 7, w = (threadIdx.x >> 3) & 7;
+  for (int f = 0; f < 6; ++f)
+    if (f % NSL == slice) nb.v[f / NSL] = __ldg(nbr6 + 6 * b + f);
+  return nb;
+}
+
+// Stage box b of variable v and its six face halos in s[1000] (10^3, one
+// ghost layer).  Ghost values follow pot_ghost: the same-level neighbour
+// cell, the physical-boundary ghost (Dirichlet 2g - inner, -inner when
+// homogeneous, Neumann inner) or inner/3 + 2 phihat/3 at a refinement face.
+// The neighbour-table, neighbour-cell and phihat loads are issued together
+// with the interior loads; face f is filled by the 64-thread slice f mod NSL.
+template <typename T>
+__device__ __forceinline__ void stage_box(const Grp &g, T *s, const T *v, const Nb &nbv, const T *gh, int b,
+                                          const Bc &bc, int homog) {
+  const T *p = v + (size_t)b * CELLS;
+  T x[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) x[h] = p[g.t + h * GT];
+  const int slice = g.t >> 6, u = g.t & 7, w = (g.t >> 3) & 7;
+  T hv[FPS];
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
-    if (grp != f % (NT / 64)) continue;
-    const int a = f >> 1;
-    const int i = a == 0 ? ((f & 1) ? NC - 1 : 0) : (a == 1 ? w : u);
-    const int j = a == 1 ? ((f & 1) ? NC - 1 : 0) : (a == 2 ? w : u);
-    const int k = a == 2 ? ((f & 1) ? NC - 1 : 0) : (a == 0 ? w : u);
-    const int q = s10(cidx(i, j, k));
-    const int stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
-    s[q + ((f & 1) ? stride : -stride)] = pot_ghost(v, nbr6, gh, b, f, i, j, k, s[q], bc, homog);
+    if (f % NSL != slice) continue;
+    const int r = f / NSL;
+    const int nb = nbv.v[r];
+    if (nb >= 0) hv[r] = v[(size_t)nb * CELLS + face_cell(f ^ 1, u, w)];
+    else if (nb == -2) hv[r] = gh[(size_t)(6 * b + f) * FACE + u + NC * w];
+    else hv[r] = T(0);
   }
-  __syncthreads();
+  g.sync();  // earlier users of s are done
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) s[s10(g.t + h * GT)] = x[h];
+  g.sync();
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f % NSL != slice) continue;
+    const int r = f / NSL, a = f >> 1;
+    const int q = s10(face_cell(f, u, w));
+    const int stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
+    const T inner = s[q];
+    T gv;
+    if (nbv.v[r] >= 0) gv = hv[r];
+    else if (nbv.v[r] == -1) gv = bc.type[f] ? (homog ? T(0) : T(2.0 * bc.val[f])) - inner : inner;
+    else gv = inner * T(1.0 / 3.0) + T(2.0 / 3.0) * hv[r];
+    s[q + ((f & 1) ? stride : -stride)] = gv;
+  }
+  g.sync();
 }
 
 // sum of the six neighbours from a staged box (order -x,+x,-y,+y,-z,+z)
@@ -54,41 +115,100 @@ __device__ __forceinline__ T staged_sum(const T *s, int q) {
   return s[q - 1] + s[q + 1] + s[q - 10] + s[q + 10] + s[q - 100] + s[q + 100];
 }
 
-// One colour of a Gauss-Seidel red-black sweep over the boxes [lo, lo+grid)
-// of one level: phi = (sum of 6 neighbours - h^2 f)/6 on cells with
-// (i+j+k) % 2 == color (level-global parity; box origins are multiples of
-// 8).  One block of 256 threads per box: the box and its face halos are
-// staged in shared memory, then one thread per cell of the colour.
+// One colour of a red-black Gauss-Seidel sweep on box b: phi = (sum of 6
+// neighbours - h^2 f)/6 on the cells with (i+j+k) % 2 == color (level-global
+// parity; box origins are multiples of 8).
 template <typename T>
-__global__ void __launch_bounds__(256) k_rbgs(int lo, int color, T *__restrict__ phi, const T *__restrict__ rhs,
-                                              const T *__restrict__ gh, const int32_t *__restrict__ nbr6, Bc bc,
-                                              T h2, int homog) {
-  __shared__ T s[1000];
-  pdl_wait();
-  int b = lo + blockIdx.x;
-  stage_box<256>(s, phi, nbr6, gh, b, bc, homog);
-  int t = threadIdx.x;
-  int k = t >> 5, j = (t >> 2) & 7;
-  int i = ((t & 3) << 1) | ((j + k + color) & 1);
-  int c = cidx(i, j, k);
-  size_t base = (size_t)b * CELLS;
-  T sum = staged_sum(s, s10(c));
-  phi[base + c] = (sum - h2 * rhs[base + c]) * T(1.0 / 6.0);
+__device__ __forceinline__ void rbgs_box(const Grp &g, T *s, int b, int color, T *phi, const T *rhs, const T *gh,
+                                         const Nb &nb, const Bc &bc, T h2, int homog) {
+  const size_t base = (size_t)b * CELLS;
+  int c[RPT];
+  T f[RPT];
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    const int n = g.t + h * GT;  // n-th cell of the colour
+    const int k = n >> 5, j = (n >> 2) & 7;
+    c[h] = cidx(((n & 3) << 1) | ((j + k + color) & 1), j, k);
+    f[h] = rhs[base + c[h]];
+  }
+  stage_box(g, s, phi, nb, gh, b, bc, homog);
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) phi[base + c[h]] = (staged_sum(s, s10(c[h])) - h2 * f[h]) * T(1.0 / 6.0);
 }
 
-// plain 8-child average of one or two variables (FMG right-hand side,
-// densities, potential after a mixed-precision correction)
+// parent of box b and the octant of the parent that b covers
+struct Place {
+  int P, ox, oy, oz;
+};
+
+__device__ __forceinline__ Place load_place(const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk,
+                                            int b) {
+  return Place{__ldg(parent + b), __ldg(ijk + 3 * b) & 1, __ldg(ijk + 3 * b + 1) & 1, __ldg(ijk + 3 * b + 2) & 1};
+}
+
+// Residual r = f - L phi of box b (level l) and restriction: the 64 cells
+// of the parent region get the 8-child averages of phi (into phi) and of r
+// (into rhs, completed to the FAS right-hand side by fas_box).
 template <typename T>
-__global__ void __launch_bounds__(64) k_restrict1(int lo, const int32_t *__restrict__ parent,
-                                                  const int32_t *__restrict__ ijk, T *__restrict__ a,
-                                                  T *__restrict__ a2) {
-  pdl_wait();
-  int b = lo + blockIdx.x;
-  int t = threadIdx.x;
-  int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
-  int P = parent[b];
-  int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
-  size_t fb = (size_t)b * CELLS;
+__device__ __forceinline__ void resid_restrict_box(const Grp &g, T *s, T *sr, int b, T *phi, T *rhs, const T *gh,
+                                                   const Nb &nb, const Place &pl, const Bc &bc, T inv_h2,
+                                                   int homog) {
+  const size_t base = (size_t)b * CELLS;
+  T f[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) f[h] = rhs[base + g.t + h * GT];
+  stage_box(g, s, phi, nb, gh, b, bc, homog);
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int q = s10(g.t + h * GT);
+    sr[g.t + h * GT] = f[h] - (staged_sum(s, q) - T(6) * s[q]) * inv_h2;
+  }
+  g.sync();
+  if (g.t >= 64) return;
+  const int ci = g.t & 3, cj = (g.t >> 2) & 3, ck = g.t >> 4;
+  T ap = 0, ar = 0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        ap += s[s10(c)];
+        ar += sr[c];
+      }
+  const size_t cc = (size_t)pl.P * CELLS + cidx(4 * pl.ox + ci, 4 * pl.oy + cj, 4 * pl.oz + ck);
+  phi[cc] = ap * T(0.125);
+  rhs[cc] = ar * T(0.125);
+}
+
+// After restriction into box b (level l-1): keep a copy of phi, and on a
+// refined box complete the FAS right-hand side f = avg(r_fine) + L phi.
+template <typename T>
+__device__ __forceinline__ void fas_box(const Grp &g, T *s, int b, T *phi, T *old, T *rhs, const T *gh,
+                                        const Nb &nb, bool refined, const Bc &bc, T inv_h2, int homog) {
+  const size_t base = (size_t)b * CELLS;
+  if (!refined) {
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) old[base + g.t + h * GT] = phi[base + g.t + h * GT];
+    return;
+  }
+  stage_box(g, s, phi, nb, gh, b, bc, homog);
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int c = g.t + h * GT, q = s10(c);
+    const T p = s[q];
+    old[base + c] = p;
+    rhs[base + c] += (staged_sum(s, q) - T(6) * p) * inv_h2;
+  }
+}
+
+// plain 8-child average of one or two variables from box b into its parent
+template <typename T>
+__device__ __forceinline__ void restrict1_box(const Grp &g, int b, const Place &pl, T *a, T *a2) {
+  if (g.t >= 64) return;
+  const int ci = g.t & 3, cj = (g.t >> 2) & 3, ck = g.t >> 4;
+  const size_t fb = (size_t)b * CELLS;
   T s = 0, s2 = 0;
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk)
@@ -96,46 +216,30 @@ __global__ void __launch_bounds__(64) k_restrict1(int lo, const int32_t *__restr
     for (int dj = 0; dj < 2; ++dj)
 #pragma unroll
       for (int di = 0; di < 2; ++di) {
-        int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        const int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
         s += a[fb + c];
         if (a2) s2 += a2[fb + c];
       }
-  size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
+  const size_t cc = (size_t)pl.P * CELLS + cidx(4 * pl.ox + ci, 4 * pl.oy + cj, 4 * pl.oz + ck);
   a[cc] = s * T(0.125);
   if (a2) a2[cc] = s2 * T(0.125);
 }
 
-// After restriction into level l-1 (boxes [lo, lo+grid)): keep a copy of
-// phi, and on refined boxes complete the FAS right-hand side
-// f = avg(r_fine) + L phi_restricted.
-template <typename T>
-__global__ void __launch_bounds__(512) k_fas(int lo, T *__restrict__ phi, T *__restrict__ old, T *__restrict__ rhs,
-                                             const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
-                                             const int32_t *__restrict__ child, Bc bc, T inv_h2, int homog) {
-  pdl_wait();
-  int b = lo + blockIdx.x;
-  int t = threadIdx.x;
-  size_t base = (size_t)b * CELLS;
-  T p = phi[base + t];
-  old[base + t] = p;
-  if (child[8 * b] < 0) return;
-  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-  T s = nb_sum(phi, nbr6, gh, b, i, j, k, p, bc, homog);
-  rhs[base + t] += (s - T(6) * p) * inv_h2;
-}
-
-// value of a coarse-level quantity at local cell q of box Q, where q may
-// leave the box by one step along axis e (sign s): the neighbour box of the
-// same level, or the physical-boundary ghost of the cell `ctr` it left.
-template <typename T, typename F>
-__device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, int Q, int q[3], int e, int s,
-                                       T ctr, const Bc &bc, int homog, unsigned long long *err) {
-  if (q[e] >= 0 && q[e] < NC) return val(Q, cidx(q[0], q[1], q[2]));
-  int f = 2 * e + (s > 0);
-  int Qn = __ldg(nbr6 + 6 * Q + f);
+// Value of a coarse-level quantity at local cell (q0,q1,q2) of box Q where
+// the cell may lie one step outside the box along axis E (direction S):
+// the neighbour box of the same level, or the physical-boundary ghost of
+// the cell `ctr` it left.  E and S are compile-time so that the boundary
+// table is indexed by constants.
+template <int E, int S, typename T, typename F>
+__device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, int Q, int q0, int q1, int q2, T ctr,
+                                       const Bc &bc, int homog, unsigned long long *err) {
+  const int qe = E == 0 ? q0 : (E == 1 ? q1 : q2);
+  if (qe >= 0 && qe < NC) return val(Q, cidx(q0, q1, q2));
+  constexpr int f = 2 * E + (S > 0);
+  const int Qn = __ldg(nbr6 + 6 * Q + f);
   if (Qn >= 0) {
-    q[e] = s > 0 ? 0 : NC - 1;
-    return val(Qn, cidx(q[0], q[1], q[2]));
+    const int w = S > 0 ? 0 : NC - 1;
+    return val(Qn, cidx(E == 0 ? w : q0, E == 1 ? w : q1, E == 2 ? w : q2));
   }
   if (Qn == -1) {
     if (bc.type[f]) return (homog ? T(0) : T(2.0 * bc.val[f])) - ctr;
@@ -145,42 +249,291 @@ __device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, 
   return ctr;
 }
 
-// phihat = c/2 + c_t1/4 + c_t2/4 for ghost cell (u,w) of refinement face f
+// coarse_at with a run-time direction s along compile-time axis E
+template <int E, typename T, typename F>
+__device__ __forceinline__ T coarse_step(F val, const int32_t *__restrict__ nbr6, int Q, int q0, int q1, int q2,
+                                         int s, T ctr, const Bc &bc, int homog, unsigned long long *err) {
+  if (s > 0)
+    return coarse_at<E, 1, T>(val, nbr6, Q, q0 + (E == 0), q1 + (E == 1), q2 + (E == 2), ctr, bc, homog, err);
+  return coarse_at<E, -1, T>(val, nbr6, Q, q0 - (E == 0), q1 - (E == 1), q2 - (E == 2), ctr, bc, homog, err);
+}
+
+// phihat = c/2 + c_t1/4 + c_t2/4 for ghost cell (u,w) of refinement face F
 // of box b (level l), from the level l-1 values of v
-template <typename T>
-__device__ __forceinline__ void cf_value(const T *__restrict__ v, T *__restrict__ gh,
-                                         const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
-                                         const int32_t *__restrict__ ijk, const Bc &bc, int homog, int b, int f,
-                                         int u, int w, unsigned long long *err) {
+template <int F, typename T>
+__device__ __forceinline__ void cf_value(const T *v, T *gh, const int32_t *__restrict__ nbr6,
+                                         const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk,
+                                         const Bc &bc, int homog, int b, int u, int w, unsigned long long *err) {
   auto val = [&](int Q, int c) { return v[(size_t)Q * CELLS + c]; };
-  int a = f >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  constexpr int a = F >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
   int G[3];
-  G[a] = NC * ijk[3 * b + a] + ((f & 1) ? NC : -1);
-  G[t1] = NC * ijk[3 * b + t1] + u;
-  G[t2] = NC * ijk[3 * b + t2] + w;
-  int P = parent[b];
-  int Q = nbr6[6 * P + f];
+  G[a] = NC * __ldg(ijk + 3 * b + a) + ((F & 1) ? NC : -1);
+  G[t1] = NC * __ldg(ijk + 3 * b + t1) + u;
+  G[t2] = NC * __ldg(ijk + 3 * b + t2) + w;
+  const int P = __ldg(parent + b);
+  const int Q = __ldg(nbr6 + 6 * P + F);
   if (Q < 0) {
     atomicOr(err, 2ull);
     return;
   }
-  int lc[3];
-  for (int d = 0; d < 3; ++d) lc[d] = (G[d] >> 1) - NC * ijk[3 * Q + d];
-  T c = val(Q, cidx(lc[0], lc[1], lc[2]));
+  const int l0 = (G[0] >> 1) - NC * __ldg(ijk + 3 * Q), l1 = (G[1] >> 1) - NC * __ldg(ijk + 3 * Q + 1),
+            l2 = (G[2] >> 1) - NC * __ldg(ijk + 3 * Q + 2);
+  const T c = val(Q, cidx(l0, l1, l2));
   T ph = T(0.5) * c;
-  int ts[2] = {t1, t2};
-  for (int e2 = 0; e2 < 2; ++e2) {
-    int e = ts[e2];
-    int s = (G[e] & 1) ? 1 : -1;
-    int q[3] = {lc[0], lc[1], lc[2]};
-    q[e] += s;
-    ph += T(0.25) * coarse_at<T>(val, nbr6, Q, q, e, s, c, bc, homog, err);
-  }
-  gh[(size_t)(6 * b + f) * FACE + u + NC * w] = ph;
+  ph += T(0.25) * coarse_step<t1, T>(val, nbr6, Q, l0, l1, l2, (G[t1] & 1) ? 1 : -1, c, bc, homog, err);
+  ph += T(0.25) * coarse_step<t2, T>(val, nbr6, Q, l0, l1, l2, (G[t2] & 1) ? 1 : -1, c, bc, homog, err);
+  gh[(size_t)(6 * b + F) * FACE + u + NC * w] = ph;
 }
 
-// Coarse interpolation values for the refinement-boundary faces of the
-// boxes [lo, lo+grid), 64 threads per box, one per face cell.
+// coarse interpolation values of the refinement faces of box b, cells
+// (u,w) = (e & 7, e >> 3) for the face-cell index e of this thread
+template <typename T>
+__device__ __forceinline__ void cf_faces_box(int e, int nthreads, const T *v, T *gh, const int32_t *__restrict__ nbr6,
+                                             const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk,
+                                             const Bc &bc, int homog, int b, unsigned long long *err) {
+  // thread e handles face cells e, e + nthreads, ... of the 6 x 64 list
+  const int u = e & 7, w = (e >> 3) & 7, first = e >> 6, step = nthreads >> 6;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f < first || (f - first) % step) continue;
+    if (__ldg(nbr6 + 6 * b + f) != -2) continue;
+    switch (f) {
+      case 0: cf_value<0>(v, gh, nbr6, parent, ijk, bc, homog, b, u, w, err); break;
+      case 1: cf_value<1>(v, gh, nbr6, parent, ijk, bc, homog, b, u, w, err); break;
+      case 2: cf_value<2>(v, gh, nbr6, parent, ijk, bc, homog, b, u, w, err); break;
+      case 3: cf_value<3>(v, gh, nbr6, parent, ijk, bc, homog, b, u, w, err); break;
+      case 4: cf_value<4>(v, gh, nbr6, parent, ijk, bc, homog, b, u, w, err); break;
+      default: cf_value<5>(v, gh, nbr6, parent, ijk, bc, homog, b, u, w, err); break;
+    }
+  }
+}
+
+// Prolongation into box b (level l) and the coarse interpolation values of
+// its refinement faces (both read only level l-1): mode 0 adds the
+// correction (phi - old) with homogeneous wall ghosts, mode 1 overwrites
+// with the prolonged solution (FMG); gh interpolates phi itself.  homog:
+// the variable is an error (homogeneous wall ghosts everywhere).
+template <typename T>
+__device__ __forceinline__ void prolong_box(const Grp &g, int b, int mode, T *phi, const T *old, T *gh,
+                                            const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
+                                            const int32_t *__restrict__ ijk, const Bc &bc, int homog,
+                                            unsigned long long *err) {
+  const int P = __ldg(parent + b);
+  const int bx = __ldg(ijk + 3 * b), by = __ldg(ijk + 3 * b + 1), bz = __ldg(ijk + 3 * b + 2);
+  const int px = __ldg(ijk + 3 * P), py = __ldg(ijk + 3 * P + 1), pz = __ldg(ijk + 3 * P + 2);
+  auto val = [&](int Q, int c) {
+    const size_t x = (size_t)Q * CELLS + c;
+    return mode ? phi[x] : phi[x] - old[x];
+  };
+  const int hom = (mode && !homog) ? 0 : 1;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = g.t + h * GT;
+    const int G0 = NC * bx + (t & 7), G1 = NC * by + ((t >> 3) & 7), G2 = NC * bz + (t >> 6);
+    const int l0 = (G0 >> 1) - NC * px, l1 = (G1 >> 1) - NC * py, l2 = (G2 >> 1) - NC * pz;
+    const T c0 = val(P, cidx(l0, l1, l2));
+    T sum = c0;
+    sum += coarse_step<0, T>(val, nbr6, P, l0, l1, l2, (G0 & 1) ? 1 : -1, c0, bc, hom, err);
+    sum += coarse_step<1, T>(val, nbr6, P, l0, l1, l2, (G1 & 1) ? 1 : -1, c0, bc, hom, err);
+    sum += coarse_step<2, T>(val, nbr6, P, l0, l1, l2, (G2 & 1) ? 1 : -1, c0, bc, hom, err);
+    const size_t x = (size_t)b * CELLS + t;
+    if (mode) phi[x] = T(0.25) * sum;
+    else phi[x] += T(0.25) * sum;
+  }
+  cf_faces_box(g.t, GT, phi, gh, nbr6, parent, ijk, bc, homog, b, err);
+}
+
+// Exact solve on level 0 (one 8^3 box), always in FP64: fold the Dirichlet
+// boundary values into the right-hand side (not for the homogeneous error
+// equation), transform to the separable eigenbasis, divide by the
+// eigenvalues of the 7-point operator, transform back.  sm: 2 x 512 + 216
+// doubles of shared memory.
+template <typename T>
+__device__ __forceinline__ void coarse_box(const Grp &g, double *sm, T *phi, const T *rhs,
+                                           const double *__restrict__ basis, const Bc &bc, double h2,
+                                           double inv_h2, int homog) {
+  double *x = sm, *y = sm + CELLS, *V = sm + 2 * CELLS, *lam = V + 192;
+  const int t0 = g.t;
+  for (int i = t0; i < 216; i += GT) {
+    if (i < 192) V[i] = __ldg(basis + i);
+    else lam[i - 192] = __ldg(basis + i);
+  }
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT;
+    const int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
+    double r = (double)rhs[t];
+    if (!homog) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const int q = c[f >> 1] + ((f & 1) ? 1 : -1);
+        if ((q < 0 || q >= NC) && bc.type[f]) r -= 2.0 * bc.val[f] * inv_h2;
+      }
+    }
+    x[t] = r;
+  }
+  g.sync();
+  // forward: coefficients along x, then y, then z
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[0 * 64 + m * 8 + c0] * x[cidx(m, c1, c2)];
+    y[t] = acc;
+  }
+  g.sync();
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[1 * 64 + m * 8 + c1] * y[cidx(c0, m, c2)];
+    x[t] = acc;
+  }
+  g.sync();
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[2 * 64 + m * 8 + c2] * x[cidx(c0, c1, m)];
+    y[t] = acc * h2 / (lam[c0] + lam[8 + c1] + lam[16 + c2]);
+  }
+  g.sync();
+  // backward
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[0 * 64 + c0 * 8 + m] * y[cidx(m, c1, c2)];
+    x[t] = acc;
+  }
+  g.sync();
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[1 * 64 + c1 * 8 + m] * x[cidx(c0, m, c2)];
+    y[t] = acc;
+  }
+  g.sync();
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[2 * 64 + c2 * 8 + m] * y[cidx(c0, c1, m)];
+    phi[t] = (T)acc;
+  }
+  g.sync();  // sm is free again
+}
+
+// FP64 residual f - L v of the cells of this thread in leaf box b; the
+// largest magnitude is returned, r is stored to r32 when given
+__device__ __forceinline__ double resid_box(const Grp &g, double *s, int b, const double *v, const double *rhs,
+                                            const double *gh, const Nb &nb, const Bc &bc, double inv_h2,
+                                            float *r32) {
+  const size_t base = (size_t)b * CELLS;
+  double f[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) f[h] = rhs[base + g.t + h * GT];
+  stage_box(g, s, v, nb, gh, b, bc, 0);
+  double m = 0.0;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int q = s10(g.t + h * GT);
+    const double r = f[h] - (staged_sum(s, q) - 6.0 * s[q]) * inv_h2;
+    if (r32) r32[base + g.t + h * GT] = (float)r;
+    m = fmax(m, fabs(r));
+  }
+  return m;
+}
+
+// max over a box group, pushed to *slot by thread 0 (red: GT/32 doubles
+// of shared memory of the group)
+__device__ __forceinline__ void group_max_to(const Grp &g, unsigned long long *slot, double v, double *red) {
+  v = warp_max(v);
+  if ((g.t & 31) == 0) red[g.t >> 5] = v;
+  g.sync();
+  if (g.t == 0) {
+    double x = red[0];
+#pragma unroll
+    for (int i = 1; i < GT / 32; ++i) x = fmax(x, red[i]);
+    atomic_max_pos(slot, x);
+  }
+  g.sync();
+}
+
+// ---------------------------------------------------------------------------
+// per-level kernels: one box per block of GT threads
+// ---------------------------------------------------------------------------
+//
+// Each kernel reads its table entries (neighbours, parent, children: fixed
+// during a solve) before waiting on its predecessor.  None of them triggers
+// its dependent early: dependent blocks scheduled while a level kernel still
+// runs slowed the V-cycle down by a third.
+
+__device__ __forceinline__ Grp block_grp() { return Grp{(int)threadIdx.x, 0}; }
+
+template <typename T>
+__global__ void __launch_bounds__(GT) k_rbgs(int lo, int color, T *__restrict__ phi, const T *__restrict__ rhs,
+                                             const T *__restrict__ gh, const int32_t *__restrict__ nbr6, Bc bc, T h2,
+                                             int homog) {
+  __shared__ T s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  pdl_wait();
+  rbgs_box(g, s, b, color, phi, rhs, gh, nb, bc, h2, homog);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GT) k_restrict1(int lo, const int32_t *__restrict__ parent,
+                                                  const int32_t *__restrict__ ijk, T *__restrict__ a,
+                                                  T *__restrict__ a2) {
+  const int b = lo + blockIdx.x;
+  const Place pl = load_place(parent, ijk, b);
+  pdl_wait();
+  restrict1_box(block_grp(), b, pl, a, a2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GT) k_fas(int lo, T *__restrict__ phi, T *__restrict__ old, T *__restrict__ rhs,
+                                            const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
+                                            const int32_t *__restrict__ child, Bc bc, T inv_h2, int homog) {
+  __shared__ T s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const bool refined = __ldg(child + 8 * b) >= 0;
+  pdl_wait();
+  fas_box(g, s, b, phi, old, rhs, gh, nb, refined, bc, inv_h2, homog);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GT) k_resid_restrict(int lo, T *__restrict__ phi, T *__restrict__ rhs,
+                                                       const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
+                                                       const int32_t *__restrict__ parent,
+                                                       const int32_t *__restrict__ ijk, Bc bc, T inv_h2,
+                                                       int homog) {
+  __shared__ T s[1000], sr[CELLS];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const Place pl = load_place(parent, ijk, b);
+  pdl_wait();
+  resid_restrict_box(g, s, sr, b, phi, rhs, gh, nb, pl, bc, inv_h2, homog);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GT) k_prolong_cf(int lo, int mode, T *__restrict__ phi, const T *__restrict__ old,
+                                                   T *__restrict__ gh, const int32_t *__restrict__ nbr6,
+                                                   const int32_t *__restrict__ parent,
+                                                   const int32_t *__restrict__ ijk, Bc bc, int homog,
+                                                   unsigned long long *err) {
+  pdl_wait();
+  prolong_box(block_grp(), lo + blockIdx.x, mode, phi, old, gh, nbr6, parent, ijk, bc, homog, err);
+}
+
+// coarse interpolation values of the refinement faces of the boxes
+// [lo, lo+grid), 64 threads per box
 template <typename T>
 __global__ void __launch_bounds__(64) k_fill_cf(int lo, const T *__restrict__ v, T *__restrict__ gh,
                                                 const int32_t *__restrict__ nbr6,
@@ -188,12 +541,16 @@ __global__ void __launch_bounds__(64) k_fill_cf(int lo, const T *__restrict__ v,
                                                 const int32_t *__restrict__ ijk, Bc bc, int homog,
                                                 unsigned long long *err) {
   pdl_wait();
-  int b = lo + blockIdx.x;
-  int u = threadIdx.x & 7, w = threadIdx.x >> 3;
-  for (int f = 0; f < 6; ++f) {
-    if (__ldg(nbr6 + 6 * b + f) != -2) continue;
-    cf_value(v, gh, nbr6, parent, ijk, bc, homog, b, f, u, w, err);
-  }
+  cf_faces_box((int)threadIdx.x, 64, v, gh, nbr6, parent, ijk, bc, homog, lo + blockIdx.x, err);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GT) k_coarse_solve(T *__restrict__ phi, const T *__restrict__ rhs,
+                                                     const double *__restrict__ basis, Bc bc, double h2,
+                                                     double inv_h2, int homog) {
+  __shared__ double sm[2 * CELLS + 216];
+  pdl_wait();
+  coarse_box(block_grp(), sm, phi, rhs, basis, bc, h2, inv_h2, homog);
 }
 
 // Orthonormal eigenvectors and (h^2-scaled) eigenvalues of the 1-D
@@ -223,190 +580,29 @@ __global__ void k_coarse_basis(double *basis, Bc bc, int n) {
   basis[192 + a * 8 + m] = mu;
 }
 
-// Exact solve on level 0 (one 8^3 box), always in FP64: fold the Dirichlet
-// boundary values into the right-hand side (not for the homogeneous error
-// equation), transform to the separable eigenbasis, divide by the
-// eigenvalues of the 7-point operator, transform back.
-template <typename T>
-__global__ void __launch_bounds__(512) k_coarse_solve(T *__restrict__ phi, const T *__restrict__ rhs,
-                                                      const double *__restrict__ basis, Bc bc, double h2,
-                                                      double inv_h2, int homog) {
+// max over leaf cells of |f - L v| into *slot (one leaf box per block); with
+// f32 given, also the residual rounded to FP32 (right-hand side of the
+// error equation of the mixed-precision solve)
+__global__ void __launch_bounds__(GT) k_resnorm(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
+                                                const double *__restrict__ v, const double *__restrict__ rhs,
+                                                const double *__restrict__ gh, const int32_t *__restrict__ nbr6,
+                                                Bc bc, LevelH lh, float *__restrict__ f32,
+                                                unsigned long long *slot) {
+  __shared__ double s[1000], red[GT / 32];
   pdl_wait();
-  __shared__ double x[CELLS], y[CELLS], V[3][64], lam[3][8];
-  int t = threadIdx.x;
-  if (t < 192) V[t / 64][t % 64] = basis[t];
-  if (t < 24) lam[t / 8][t % 8] = basis[192 + t];
-  int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
-  double r = (double)rhs[t];
-  if (!homog)
-    for (int f = 0; f < 6; ++f) {
-      int q = c[f >> 1] + ((f & 1) ? 1 : -1);
-      if ((q < 0 || q >= NC) && bc.type[f]) r -= 2.0 * bc.val[f] * inv_h2;
-    }
-  x[t] = r;
-  __syncthreads();
-  // forward: coefficients along x, then y, then z
-  double acc = 0.0;
-  for (int m = 0; m < NC; ++m) acc += V[0][m * 8 + c[0]] * x[cidx(m, c[1], c[2])];
-  y[t] = acc;
-  __syncthreads();
-  acc = 0.0;
-  for (int m = 0; m < NC; ++m) acc += V[1][m * 8 + c[1]] * y[cidx(c[0], m, c[2])];
-  x[t] = acc;
-  __syncthreads();
-  acc = 0.0;
-  for (int m = 0; m < NC; ++m) acc += V[2][m * 8 + c[2]] * x[cidx(c[0], c[1], m)];
-  y[t] = acc * h2 / (lam[0][c[0]] + lam[1][c[1]] + lam[2][c[2]]);
-  __syncthreads();
-  // backward
-  acc = 0.0;
-  for (int m = 0; m < NC; ++m) acc += V[0][c[0] * 8 + m] * y[cidx(m, c[1], c[2])];
-  x[t] = acc;
-  __syncthreads();
-  acc = 0.0;
-  for (int m = 0; m < NC; ++m) acc += V[1][c[1] * 8 + m] * x[cidx(c[0], m, c[2])];
-  y[t] = acc;
-  __syncthreads();
-  acc = 0.0;
-  for (int m = 0; m < NC; ++m) acc += V[2][c[2] * 8 + m] * y[cidx(c[0], c[1], m)];
-  phi[t] = (T)acc;
-}
-
-// max over leaf cells of |f - L v| into *slot (one block per leaf box)
-__global__ void __launch_bounds__(512) k_resnorm(const int32_t *__restrict__ leaf,
-                                                 const int32_t *__restrict__ level,
-                                                 const double *__restrict__ v, const double *__restrict__ rhs,
-                                                 const double *__restrict__ gh,
-                                                 const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
-                                                 unsigned long long *slot) {
-  pdl_wait();
-  __shared__ double red[16];
-  int b = leaf[blockIdx.x];
-  int t = threadIdx.x;
-  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-  size_t base = (size_t)b * CELLS;
-  double p = v[base + t];
-  double s = nb_sum(v, nbr6, gh, b, i, j, k, p, bc, 0);
-  double r = rhs[base + t] - (s - 6.0 * p) * lh.inv_h2[level[b]];
-  block_max_to(slot, fabs(r), red);
-}
-
-// Outer FP64 residual of the mixed-precision solve on leaf cells: the max
-// norm into *slot and the residual rounded to FP32 as the right-hand side
-// of the error equation.
-__global__ void __launch_bounds__(512) k_resid_to32(const int32_t *__restrict__ leaf,
-                                                    const int32_t *__restrict__ level,
-                                                    const double *__restrict__ v, const double *__restrict__ rhs,
-                                                    const double *__restrict__ gh,
-                                                    const int32_t *__restrict__ nbr6, Bc bc, LevelH lh,
-                                                    float *__restrict__ f32, unsigned long long *slot) {
-  pdl_wait();
-  __shared__ double red[16];
-  int b = leaf[blockIdx.x];
-  int t = threadIdx.x;
-  int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-  size_t base = (size_t)b * CELLS;
-  double p = v[base + t];
-  double s = nb_sum(v, nbr6, gh, b, i, j, k, p, bc, 0);
-  double r = rhs[base + t] - (s - 6.0 * p) * lh.inv_h2[level[b]];
-  f32[base + t] = (float)r;
-  block_max_to(slot, fabs(r), red);
+  const Grp g = block_grp();
+  const int b = __ldg(leaf + blockIdx.x);
+  const double m = resid_box(g, s, b, v, rhs, gh, load_nb(g, nbr6, b), bc, lh.inv_h2[__ldg(level + b)], f32);
+  group_max_to(g, slot, m, red);
 }
 
 // FP64 accumulation of the FP32 correction on leaf cells
-__global__ void __launch_bounds__(512) k_add_corr(const int32_t *__restrict__ leaf, double *__restrict__ phi,
-                                                  const float *__restrict__ e32) {
+__global__ void __launch_bounds__(GT) k_add_corr(const int32_t *__restrict__ leaf, double *__restrict__ phi,
+                                                 const float *__restrict__ e32) {
   pdl_wait();
-  size_t x = (size_t)leaf[blockIdx.x] * CELLS + threadIdx.x;
-  phi[x] += (double)e32[x];
-}
-
-// Residual and restriction fused: one block per fine box of level l
-// computes r = f - L phi for its 512 cells (box staged with its face
-// halos), then its 64 parent cells get the 8-child averages of phi (into
-// phi) and of r (into rhs, completed to the FAS right-hand side by k_fas).
-template <typename T>
-__global__ void __launch_bounds__(512) k_resid_restrict(int lo, T *__restrict__ phi, T *__restrict__ rhs,
-                                                        const T *__restrict__ gh,
-                                                        const int32_t *__restrict__ nbr6,
-                                                        const int32_t *__restrict__ parent,
-                                                        const int32_t *__restrict__ ijk, Bc bc, T inv_h2,
-                                                        int homog) {
-  __shared__ T s[1000], sr[CELLS];
-  pdl_wait();
-  int b = lo + blockIdx.x;
-  stage_box<512>(s, phi, nbr6, gh, b, bc, homog);
-  int t = threadIdx.x;
-  size_t base = (size_t)b * CELLS;
-  int q = s10(t);
-  T p = s[q];
-  sr[t] = rhs[base + t] - (staged_sum(s, q) - T(6) * p) * inv_h2;
-  __syncthreads();
-  if (t >= 64) return;
-  int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
-  int P = parent[b];
-  int o[3] = {ijk[3 * b] & 1, ijk[3 * b + 1] & 1, ijk[3 * b + 2] & 1};
-  T ap = 0, ar = 0;
+  const size_t x = (size_t)__ldg(leaf + blockIdx.x) * CELLS + threadIdx.x;
 #pragma unroll
-  for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
-        ap += s[s10(c)];
-        ar += sr[c];
-      }
-  size_t cc = (size_t)P * CELLS + cidx(4 * o[0] + ci, 4 * o[1] + cj, 4 * o[2] + ck);
-  phi[cc] = ap * T(0.125);
-  rhs[cc] = ar * T(0.125);
-}
-
-// Prolongation into the boxes of level l fused with the coarse
-// interpolation values of their refinement faces (both read only level
-// l-1): mode 0 adds the correction (phi - old) with homogeneous wall
-// ghosts, mode 1 overwrites with the prolonged solution (FMG); gh
-// interpolates phi itself.  homog: the variable is an error (homogeneous
-// wall ghosts everywhere).
-template <typename T>
-__global__ void __launch_bounds__(512) k_prolong_cf(int lo, int mode, T *__restrict__ phi,
-                                                    const T *__restrict__ old, T *__restrict__ gh,
-                                                    const int32_t *__restrict__ nbr6,
-                                                    const int32_t *__restrict__ parent,
-                                                    const int32_t *__restrict__ ijk, Bc bc, int homog,
-                                                    unsigned long long *err) {
-  pdl_wait();
-  int b = lo + blockIdx.x;
-  int t = threadIdx.x;
-  int P = parent[b];
-  {
-    int loc[3] = {t & 7, (t >> 3) & 7, t >> 6};
-    int G[3], lc[3];
-    for (int d = 0; d < 3; ++d) {
-      G[d] = NC * ijk[3 * b + d] + loc[d];
-      lc[d] = (G[d] >> 1) - NC * ijk[3 * P + d];
-    }
-    auto val = [&](int Q, int c) {
-      size_t x = (size_t)Q * CELLS + c;
-      return mode ? phi[x] : phi[x] - old[x];
-    };
-    T c0 = val(P, cidx(lc[0], lc[1], lc[2]));
-    T sum = c0;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      int s = (G[e] & 1) ? 1 : -1;
-      int q[3] = {lc[0], lc[1], lc[2]};
-      q[e] += s;
-      sum += coarse_at<T>(val, nbr6, P, q, e, s, c0, bc, (mode && !homog) ? 0 : 1, err);
-    }
-    size_t x = (size_t)b * CELLS + t;
-    if (mode) phi[x] = T(0.25) * sum;
-    else phi[x] += T(0.25) * sum;
-  }
-  if (t >= 6 * FACE) return;
-  int f = t >> 6, u = t & 7, w = (t >> 3) & 7;
-  if (__ldg(nbr6 + 6 * b + f) != -2) return;
-  cf_value(phi, gh, nbr6, parent, ijk, bc, homog, b, f, u, w, err);
+  for (int h = 0; h < CPT; ++h) phi[x + h * GT] += (double)e32[x + h * GT];
 }
 
 // Stopping test of the device-side cycle loop: relative residual of the
@@ -422,6 +618,230 @@ __global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *s
   sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
   double tol = __longlong_as_double((long long)sc[SC_TOL]);
   cudaGraphSetConditional(h, (rel > tol && c < sc[SC_MAXC]) ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// persistent V-cycle kernel
+// ---------------------------------------------------------------------------
+//
+// One cooperative launch (every block resident) runs the phases of one or
+// more V-cycles: each phase is one level operation over all boxes of a
+// level, spread over the box groups of all blocks, and ends with a grid
+// barrier.  The barrier waits are bounded: after PERSIST_SPIN polls a block
+// sets error bit 4 and returns, and so do the others at their next wait.
+
+constexpr unsigned long long ERR_BARRIER = 4ull;
+constexpr long long PERSIST_SPIN = 1ll << 22;
+
+template <typename T>
+struct PArgs {
+  T *phi, *rhs, *old, *gh;
+  const int32_t *nbr6, *parent, *ijk, *child, *leaf, *level;
+  const double *basis;
+  double *phi64, *rhs64, *gh64;  // FP64 potential, rhs, interpolation values (residual test)
+  unsigned long long *sc;
+  Bc bc;
+  LevelH lh;
+  int level_off[MAXL + 1];
+  int n_levels, n_leaves, top, nu1, nu2, homog;
+  int fmg;   // run the FMG ladder first (restricted rhs, level-0 solve, one V-cycle per finer level)
+  int loop;  // after that (or from the start): V-cycles with the residual test until converged
+};
+
+// shared memory of one box group of the persistent kernel (bytes)
+template <typename T>
+__host__ __device__ constexpr size_t persist_group_smem() {
+  return 1512 * sizeof(T) > (2 * CELLS + 216) * sizeof(double) ? 1512 * sizeof(T)
+                                                                 : (2 * CELLS + 216) * sizeof(double);
+}
+static_assert(1000 + GT / 32 <= 2 * CELLS + 216, "residual staging fits the FP64 scratch");
+
+struct GridBar {
+  unsigned int *cnt;
+  unsigned int epoch;
+  int *flag;  // shared: barrier outcome for the block
+  unsigned long long *err;
+  // all blocks arrive; false when the wait ran out (the caller returns)
+  __device__ __forceinline__ bool sync() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int target = ++epoch * gridDim.x;
+      __threadfence();
+      atomicAdd(cnt, 1u);
+      int ok = 1;
+      long long it = 0;
+      unsigned int v;
+      while (true) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+        if (v >= target) break;
+        if (++it > PERSIST_SPIN) {
+          atomicOr(err, ERR_BARRIER);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+      *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+  }
+};
+
+template <typename T>
+struct Persist {
+  const PArgs<T> &a;
+  Grp g;
+  int gi, ng;  // group index over the grid, number of groups
+  T *s, *sr;
+  double *sd;  // FP64 scratch of the group (coarse solve, residual staging)
+  GridBar bar;
+
+  __device__ int lo(int l) const { return a.level_off[l]; }
+  __device__ int hi(int l) const { return a.level_off[l + 1]; }
+  __device__ bool empty(int l) const { return hi(l) == lo(l); }
+
+  __device__ bool smooth(int l, int nu) {
+    if (empty(l)) return true;
+    const T h2 = (T)a.lh.h2[l];
+    for (int it = 0; it < nu; ++it)
+      for (int color = 0; color < 2; ++color) {
+        for (int b = lo(l) + gi; b < hi(l); b += ng)
+          rbgs_box(g, s, b, color, a.phi, a.rhs, a.gh, load_nb(g, a.nbr6, b), a.bc, h2, a.homog);
+        if (!bar.sync()) return false;
+      }
+    return true;
+  }
+
+  __device__ bool coarse() {
+    if (gi == 0) coarse_box(g, sd, a.phi, a.rhs, a.basis, a.bc, a.lh.h2[0], a.lh.inv_h2[0], a.homog);
+    return bar.sync();
+  }
+
+  __device__ bool prolong(int l, int mode) {
+    if (empty(l)) return true;
+    for (int b = lo(l) + gi; b < hi(l); b += ng)
+      prolong_box(g, b, mode, a.phi, a.old, a.gh, a.nbr6, a.parent, a.ijk, a.bc, a.homog, a.sc + SC_ERR);
+    return bar.sync();
+  }
+
+  __device__ bool vcycle(int top) {
+    for (int l = top; l >= 1; --l) {
+      if (!smooth(l, a.nu1)) return false;
+      if (!empty(l)) {
+        const T ih2 = (T)a.lh.inv_h2[l];
+        for (int b = lo(l) + gi; b < hi(l); b += ng)
+          resid_restrict_box(g, s, sr, b, a.phi, a.rhs, a.gh, load_nb(g, a.nbr6, b), load_place(a.parent, a.ijk, b),
+                             a.bc, ih2, a.homog);
+        if (!bar.sync()) return false;
+      }
+      const T ih2c = (T)a.lh.inv_h2[l - 1];
+      for (int b = lo(l - 1) + gi; b < hi(l - 1); b += ng)
+        fas_box(g, s, b, a.phi, a.old, a.rhs, a.gh, load_nb(g, a.nbr6, b), __ldg(a.child + 8 * b) >= 0, a.bc, ih2c,
+                a.homog);
+      if (!bar.sync()) return false;
+    }
+    if (!coarse()) return false;
+    for (int l = 1; l <= top; ++l) {
+      if (!prolong(l, 0)) return false;
+      if (!smooth(l, a.nu2)) return false;
+    }
+    return true;
+  }
+
+  __device__ bool ladder() {
+    for (int l = a.n_levels - 1; l >= 1; --l) {
+      for (int b = lo(l) + gi; b < hi(l); b += ng)
+        restrict1_box<T>(g, b, load_place(a.parent, a.ijk, b), a.rhs, nullptr);
+      if (!bar.sync()) return false;
+    }
+    if (!coarse()) return false;
+    for (int l = 1; l < a.n_levels; ++l) {
+      if (!prolong(l, 1)) return false;
+      if (!vcycle(l)) return false;
+    }
+    return true;
+  }
+
+  // max_leaf |f - L phi| (FP64) into slot; true when the wait succeeded
+  __device__ bool resnorm(unsigned long long *slot) {
+    double m = 0.0;
+    for (int i = gi; i < a.n_leaves; i += ng) {
+      const int b = __ldg(a.leaf + i);
+      m = fmax(m, resid_box(g, sd, b, a.phi64, a.rhs64, a.gh64, load_nb(g, a.nbr6, b), a.bc,
+                            a.lh.inv_h2[__ldg(a.level + b)], nullptr));
+    }
+    group_max_to(g, slot, m, sd + 1000);
+    return bar.sync();
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(PGROUPS *GT, 1) k_persist(const __grid_constant__ PArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int flag;
+  const int q = threadIdx.x / GT;
+  // one region per group, used by one phase at a time: T staging s[1000]
+  // and sr[512], or FP64 scratch (level-0 solve 2 x 512 + 216 doubles,
+  // residual staging 1000 + GT/32 doubles)
+  unsigned char *base = smem + (size_t)q * persist_group_smem<T>();
+  Persist<T> p{a, Grp{(int)threadIdx.x % GT, 1 + q}, q * (int)gridDim.x + (int)blockIdx.x,
+               PGROUPS * (int)gridDim.x, nullptr, nullptr, nullptr,
+               GridBar{(unsigned int *)(a.sc + SC_BAR), 0u, &flag, a.sc + SC_ERR}};
+  p.sd = (double *)base;
+  p.s = (T *)base;
+  p.sr = p.s + 1000;
+  int cyc = 0;
+  double rel = 0.0, num = 0.0;
+  const double den = __longlong_as_double((long long)a.sc[SC_DEN]);
+  const double tol = __longlong_as_double((long long)a.sc[SC_TOL]);
+  const unsigned long long maxc = a.sc[SC_MAXC];
+  int pass = 0;  // residual passes: slot SC_PN0 + (pass & 1)
+  auto test = [&]() -> int {  // 1 = go on, 0 = converged or limit, -1 = barrier wait ran out
+    unsigned long long *slot = a.sc + SC_PN0 + (pass & 1);
+    if (!p.resnorm(slot)) return -1;
+    unsigned long long bits;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(slot) : "memory");
+    num = __longlong_as_double((long long)bits);
+    rel = den > 0.0 ? num / den : num;
+    ++cyc;
+    ++pass;
+    return (rel > tol && (unsigned long long)cyc < maxc) ? 1 : 0;
+  };
+  // each residual slot is cleared one full cycle before its next use
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sc[SC_PN0] = 0ull;
+    a.sc[SC_PN1] = 0ull;
+  }
+  if (!p.bar.sync()) return;
+  int go = 1;
+  if (a.fmg) {
+    if (!p.ladder()) return;
+    if (a.loop) {
+      go = test();
+      if (go < 0) return;
+    } else {
+      go = 0;
+    }
+  }
+  while (go) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && pass > 0) a.sc[SC_PN0 + (pass & 1)] = 0ull;
+    if (!p.vcycle(a.top)) return;
+    if (!a.loop) break;
+    go = test();
+    if (go < 0) return;
+  }
+  if (a.loop && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sc[SC_NORM] = (unsigned long long)__double_as_longlong(num);
+    a.sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
+    a.sc[SC_CYC] = (unsigned long long)cyc;
+  }
+}
+
+template <typename T>
+constexpr size_t persist_smem() {
+  return (size_t)PGROUPS * persist_group_smem<T>();
 }
 
 // ---------------------------------------------------------------------------
@@ -473,7 +893,7 @@ int sm_restrict_pair(sm_ctx *ctx, double *a, double *a2) { return restrict_chain
 
 template <typename T>
 static int rbgs_pass(sm_ctx *ctx, const MG<T> &m, int l, int color) {
-  sm_launch(ctx, k_rbgs<T>, lvl_n(ctx, l), 256, 0, ctx->level_off[l], color, m.phi, m.rhs, m.gh, ctx->nbr6,
+  sm_launch(ctx, k_rbgs<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], color, m.phi, m.rhs, m.gh, ctx->nbr6,
             ctx->bc, (T)ctx->lh.h2[l], m.homog);
   return SM_OK;
 }
@@ -500,7 +920,7 @@ template <typename T>
 static int coarse_solve(sm_ctx *ctx, const MG<T> &m) {
   int st = ensure_basis(ctx);
   if (st) return st;
-  sm_launch(ctx, k_coarse_solve<T>, 1, 512, 0, m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
+  sm_launch(ctx, k_coarse_solve<T>, 1, GT, 0, m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
             ctx->lh.inv_h2[0], m.homog);
   SM_CKL("coarse solve");
   return SM_OK;
@@ -508,7 +928,7 @@ static int coarse_solve(sm_ctx *ctx, const MG<T> &m) {
 
 template <typename T>
 static int prolong_cf(sm_ctx *ctx, const MG<T> &m, int l, int mode) {
-  sm_launch(ctx, k_prolong_cf<T>, lvl_n(ctx, l), 512, 0, ctx->level_off[l], mode, m.phi, m.old, m.gh,
+  sm_launch(ctx, k_prolong_cf<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], mode, m.phi, m.old, m.gh,
             ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, m.homog,
             ctx->dscal + SC_ERR);
   SM_CKL("prolong");
@@ -525,10 +945,10 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top) {
   int st;
   for (int l = top; l >= 1; --l) {
     if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
-    sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), 512, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
+    sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
               ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
               (T)ctx->lh.inv_h2[l], m.homog);
-    sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), 512, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+    sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
               ctx->nbr6, ctx->child, ctx->bc,
               (T)ctx->lh.inv_h2[l - 1], m.homog);
     SM_CKL("vcycle down");
@@ -539,6 +959,84 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top) {
     if ((st = smooth(ctx, m, l, ctx->cfg.nu2))) return st;
   }
   return SM_OK;
+}
+
+// Blocks of the persistent kernel that fit on the device at once (its
+// launches are cooperative, so all of them are resident together).
+template <typename T>
+static int persist_prepare(sm_ctx *ctx) {
+  const int idx = sizeof(T) == sizeof(double) ? 0 : 1;
+  if (ctx->persist_grid[idx]) return SM_OK;
+  const size_t smem = persist_smem<T>();
+  SM_CK(cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0, coop = 0;
+  SM_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+  if (!coop) return sm_fail(ctx, SM_ECUDA, "device has no cooperative launch");
+  SM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<T>, PGROUPS * GT, smem));
+  SM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  if (per_sm < 1) return sm_fail(ctx, SM_ECUDA, "persistent kernel does not fit on one SM");
+  ctx->persist_grid[idx] = per_sm * sms;
+  return SM_OK;
+}
+
+// One cooperative launch of the persistent kernel on the arrays of m:
+// the FMG ladder (fmg), V-cycles with `top` as finest level, and with
+// loop set the FP64 residual test after each cycle until SC_TOL or SC_MAXC
+// is reached (SC_NORM, SC_REL, SC_CYC written at the end).  Without loop
+// one V-cycle runs (or only the ladder when fmg is set).
+template <typename T>
+static int persist_launch(sm_ctx *ctx, const MG<T> &m, int top, int fmg, int loop) {
+  int st = persist_prepare<T>(ctx);
+  if (st) return st;
+  PArgs<T> a;
+  memset(&a, 0, sizeof a);
+  a.phi = m.phi;
+  a.rhs = m.rhs;
+  a.old = m.old;
+  a.gh = m.gh;
+  a.nbr6 = ctx->nbr6;
+  a.parent = ctx->parent;
+  a.ijk = ctx->ijk;
+  a.child = ctx->child;
+  a.leaf = ctx->leaf;
+  a.level = ctx->level;
+  a.basis = ctx->basis;
+  a.phi64 = ctx->phi;
+  a.rhs64 = ctx->rhs;
+  a.gh64 = ctx->gh;
+  a.sc = ctx->dscal;
+  a.bc = ctx->bc;
+  a.lh = ctx->lh;
+  for (int l = 0; l <= MAXL; ++l) a.level_off[l] = ctx->level_off[l];
+  a.n_levels = ctx->n_levels;
+  a.n_leaves = ctx->n_leaves;
+  a.top = top;
+  a.nu1 = ctx->cfg.nu1;
+  a.nu2 = ctx->cfg.nu2;
+  a.homog = m.homog;
+  a.fmg = fmg;
+  a.loop = loop;
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_BAR, 0, sizeof(unsigned long long), ctx->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctx->persist_grid[sizeof(T) == sizeof(double) ? 0 : 1]);
+  cfg.blockDim = dim3(PGROUPS * GT);
+  cfg.dynamicSmemBytes = persist_smem<T>();
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++ctx->n_launch;
+  SM_CK(cudaLaunchKernelEx(&cfg, k_persist<T>, a));
+  return SM_OK;
+}
+
+// one V-cycle from `top` on the arrays of m: persistent or per-level launches
+template <typename T>
+static int cycle(sm_ctx *ctx, const MG<T> &m, int top) {
+  if (ctx->persist) return persist_launch(ctx, m, top, 0, 0);
+  return vcycle(ctx, m, top);
 }
 
 // FMG ladder: restrict f, exact level-0 solve, then for each finer level
@@ -559,8 +1057,8 @@ static int fmg_ladder(sm_ctx *ctx, const MG<T> &m) {
 // max_leaf |f - L v| into slot (v's refinement ghosts must be current)
 static int leaf_norm(sm_ctx *ctx, double *v, int slot) {
   SM_CK(cudaMemsetAsync(ctx->dscal + slot, 0, sizeof(unsigned long long), ctx->stream));
-  sm_launch(ctx, k_resnorm, ctx->n_leaves, 512, 0, ctx->leaf, ctx->level, v, ctx->rhs, ctx->gh, ctx->nbr6,
-            ctx->bc, ctx->lh, ctx->dscal + slot);
+  sm_launch(ctx, k_resnorm, ctx->n_leaves, GT, 0, ctx->leaf, ctx->level, v, ctx->rhs, ctx->gh, ctx->nbr6, ctx->bc,
+            ctx->lh, (float *)nullptr, ctx->dscal + slot);
   SM_CKL("resnorm");
   return SM_OK;
 }
@@ -568,9 +1066,8 @@ static int leaf_norm(sm_ctx *ctx, double *v, int slot) {
 // outer FP64 residual of the mixed form: norm into SC_NORM, f32 = (float) r
 static int leaf_resid32(sm_ctx *ctx) {
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_NORM, 0, sizeof(unsigned long long), ctx->stream));
-  sm_launch(ctx, k_resid_to32, ctx->n_leaves, 512, 0, ctx->leaf, ctx->level, ctx->phi, ctx->rhs, ctx->gh,
-            ctx->nbr6, ctx->bc, ctx->lh, ctx->f32,
-            ctx->dscal + SC_NORM);
+  sm_launch(ctx, k_resnorm, ctx->n_leaves, GT, 0, ctx->leaf, ctx->level, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6,
+            ctx->bc, ctx->lh, ctx->f32, ctx->dscal + SC_NORM);
   SM_CKL("resid32");
   return SM_OK;
 }
@@ -586,10 +1083,11 @@ static int mixed_correction(sm_ctx *ctx, int ladder) {
   SM_CK(cudaMemsetAsync(ctx->e32, 0, sizeof(float) * nc, ctx->stream));
   SM_CK(cudaMemsetAsync(ctx->gh32, 0, sizeof(float) * 6 * FACE * (size_t)ctx->n_boxes, ctx->stream));
   MG<float> m = mg32(ctx);
-  if (ladder) st = fmg_ladder(ctx, m);
+  if (ctx->persist) st = persist_launch(ctx, m, ctx->n_levels - 1, ladder, 0);
+  else if (ladder) st = fmg_ladder(ctx, m);
   else st = vcycle(ctx, m, ctx->n_levels - 1);
   if (st) return st;
-  sm_launch(ctx, k_add_corr, ctx->n_leaves, 512, 0, ctx->leaf, ctx->phi, ctx->e32);
+  sm_launch(ctx, k_add_corr, ctx->n_leaves, GT, 0, ctx->leaf, ctx->phi, ctx->e32);
   SM_CKL("add correction");
   if ((st = restrict_chain<double>(ctx, ctx->phi, nullptr))) return st;
   if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
@@ -601,6 +1099,7 @@ static int read_scalars(sm_ctx *ctx) {
   SM_CK(cudaStreamSynchronize(ctx->stream));
   unsigned long long e;
   memcpy(&e, &ctx->hscal[SC_ERR], sizeof e);
+  if (e & ERR_BARRIER) return sm_fail(ctx, SM_ETIMEOUT, "grid barrier of the persistent kernel timed out");
   if (e) return sm_fail(ctx, SM_ESTATE, "device consistency check failed (flags 0x%llx)", e);
   return SM_OK;
 }
@@ -717,6 +1216,30 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
     if (st) return st;
   }
   const int fmg = kind == 1 || kind == 3;
+  if (ctx->persist) {
+    int st = kind < 2 ? persist_prepare<double>(ctx) : persist_prepare<float>(ctx);
+    if (st) return st;
+  }
+  if (ctx->persist && kind < 2) {
+    // prologue + one persistent launch holding the cycle loop
+    SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->cap;
+    long long n0 = ctx->n_launch;
+    int st = solve_prologue(ctx);
+    if (!st) st = persist_launch(ctx, mg64(ctx), ctx->n_levels - 1, fmg, 1);
+    if (st) return end_captures(ctx, saved, st);
+    out->prefix_launches = ctx->n_launch - n0;
+    out->body_launches = 0;
+    cudaGraph_t whole = nullptr;
+    if (cudaStreamEndCapture(ctx->cap, &whole) != cudaSuccess)
+      return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end capture"));
+    ctx->stream = saved;
+    cudaError_t e = cudaGraphInstantiate(&out->exec, whole, 0);
+    cudaGraphDestroy(whole);
+    if (e != cudaSuccess) return sm_cuda_check(ctx, e, "graph instantiate");
+    ctx->n_launch -= out->prefix_launches;
+    return SM_OK;
+  }
   SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
   ctx->stream = ctx->cap;
   int st = SM_OK;
@@ -780,14 +1303,15 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
   int c = 0;
   double rel = 0.0;
   const int kind = (ctx->cfg.precision == SM_MIXED ? 2 : 0) + (fmg ? 1 : 0);
+  // stopping parameters of the device-side loops
+  ctx->hscal[SC_TOL] = tol;
+  unsigned long long mc = (unsigned long long)max_cycles;
+  memcpy(&ctx->hscal[SC_MAXC], &mc, sizeof mc);
+  SM_CK(cudaMemcpyAsync(ctx->dscal + SC_TOL, ctx->hscal + SC_TOL, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                        ctx->stream));
   if (ctx->graphs) {
     sm_graph *g = graph_of(ctx, kind);
     if (!g->exec && (st = capture_solve(ctx, kind, g))) return st;
-    ctx->hscal[SC_TOL] = tol;
-    unsigned long long mc = (unsigned long long)max_cycles;
-    memcpy(&ctx->hscal[SC_MAXC], &mc, sizeof mc);
-    SM_CK(cudaMemcpyAsync(ctx->dscal + SC_TOL, ctx->hscal + SC_TOL, 2 * sizeof(double), cudaMemcpyHostToDevice,
-                          ctx->stream));
     SM_CK(cudaGraphLaunch(g->exec, ctx->stream));
     if ((st = read_scalars(ctx))) return st;
     unsigned long long cc;
@@ -795,6 +1319,15 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
     c = (int)cc;
     rel = ctx->hscal[SC_REL];
     ctx->n_launch += g->prefix_launches + g->body_launches * (long long)(fmg ? c - 1 : c);
+  } else if (ctx->persist && kind < 2) {
+    if ((st = ensure_basis(ctx))) return st;
+    if ((st = solve_prologue(ctx))) return st;
+    if ((st = persist_launch(ctx, mg64(ctx), ctx->n_levels - 1, fmg, 1))) return st;
+    if ((st = read_scalars(ctx))) return st;
+    unsigned long long cc;
+    memcpy(&cc, &ctx->hscal[SC_CYC], sizeof cc);
+    c = (int)cc;
+    rel = ctx->hscal[SC_REL];
   } else {
     if ((st = ensure_basis(ctx))) return st;
     if ((st = solve_prefix(ctx, kind))) return st;
@@ -842,7 +1375,7 @@ extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
   if ((st = ensure_basis(ctx))) return st;
   if ((st = solve_prologue(ctx))) return st;
   for (int c = 0; c < n_cycles; ++c)
-    if ((st = vcycle(ctx, mg64(ctx), ctx->n_levels - 1))) return st;
+    if ((st = cycle(ctx, mg64(ctx), ctx->n_levels - 1))) return st;
   double rel = 0.0;
   if ((st = rel_residual(ctx, &rel))) return st;
   if (rel_res) *rel_res = rel;
@@ -869,6 +1402,13 @@ extern "C" int sm_set_graphs(sm_ctx *ctx, int enable) {
   return SM_OK;
 }
 
+extern "C" int sm_set_persistent(sm_ctx *ctx, int enable) {
+  if (!ctx) return SM_EINVAL;
+  if (ctx->persist != (enable != 0)) sm_drop_graphs(ctx);
+  ctx->persist = enable != 0;
+  return SM_OK;
+}
+
 extern "C" int sm_set_pdl(sm_ctx *ctx, int enable) {
   if (!ctx) return SM_EINVAL;
   if (ctx->pdl != (enable != 0)) sm_drop_graphs(ctx);
@@ -876,33 +1416,87 @@ extern "C" int sm_set_pdl(sm_ctx *ctx, int enable) {
   return SM_OK;
 }
 
-// Average launch duration of a kernel class in the launch mix of a V-cycle,
-// timed with CUDA events around one graph of `reps` repetitions.
+// Algorithmic bytes and FP64 instructions of one FP64 V-cycle from `top`
+// (the per-level model stated with sm_kernel_bench).
+static void vcycle_model(const sm_ctx *ctx, int top, double *bytes, double *ops) {
+  double by = 16.0 * CELLS, op = 60.0 * CELLS;  // level-0 solve
+  const double sweeps = ctx->cfg.nu1 + ctx->cfg.nu2;
+  for (int l = 1; l <= top; ++l) {
+    const double n = (double)CELLS * lvl_n(ctx, l), nc = (double)CELLS * lvl_n(ctx, l - 1);
+    const double refined = n / 8.0;  // cells of the refined boxes of level l-1
+    by += sweeps * 2.0 * 16.0 * n + 18.0 * n + 16.0 * nc + 16.0 * refined + 18.0 * n;
+    op += sweeps * 7.0 * n + 9.0 * n + 7.0 * refined + 8.0 * n;
+  }
+  *bytes = by;
+  *ops = op;
+}
+
+// Average launch duration of a kernel class (see the header for the
+// classes and their algorithmic bytes and operations).
 extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, long long *launches,
-                               double *bytes_per_launch) {
+                               double *bytes_per_launch, double *flops_per_launch) {
   int st = check_ready(ctx);
   if (st) return st;
-  if (kclass != K_SMOOTH || reps < 1) return SM_EINVAL;
+  if (kclass < 0 || kclass >= K_NCLASS || reps < 1) return SM_EINVAL;
   int top = ctx->n_levels - 1;
   if (top < 1) return SM_EINVAL;
+  if (kclass == K_PERSIST) {
+    if ((st = ensure_basis(ctx))) return st;
+    if ((st = solve_prologue(ctx))) return st;
+    MG<double> m = mg64(ctx);
+    if ((st = persist_launch(ctx, m, top, 0, 0))) return st;  // warm
+    cudaEvent_t a, b;
+    SM_CK(cudaEventCreate(&a));
+    SM_CK(cudaEventCreate(&b));
+    SM_CK(cudaEventRecord(a, ctx->stream));
+    for (int r = 0; r < reps && !st; ++r) st = persist_launch(ctx, m, top, 0, 0);
+    SM_CK(cudaEventRecord(b, ctx->stream));
+    SM_CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    SM_CK(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    if ((st = read_scalars(ctx))) return st;
+    double by, fl;
+    vcycle_model(ctx, top, &by, &fl);
+    if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
+    if (launches) *launches = reps;
+    if (bytes_per_launch) *bytes_per_launch = by;
+    if (flops_per_launch) *flops_per_launch = fl;
+    return SM_OK;
+  }
+  if (kclass == K_VCYCLE && (st = ensure_basis(ctx))) return st;
+  if (kclass == K_VCYCLE && (st = solve_prologue(ctx))) return st;
   cudaStream_t saved = ctx->stream;
   if (!ctx->cap) SM_CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
   SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
   ctx->stream = ctx->cap;
-  long long n = 0;
+  long long n = 0, n0 = ctx->n_launch;
   double bytes = 0.0;
   MG<double> m = mg64(ctx);
-  for (int r = 0; r < reps; ++r)
+  for (int r = 0; r < reps; ++r) {
+    if (kclass == K_VCYCLE) {
+      if ((st = vcycle(ctx, m, top))) break;
+      ++n;
+      continue;
+    }
     for (int l = top; l >= 1; --l)
       for (int color = 0; color < 2; ++color) {
         rbgs_pass(ctx, m, l, color);
         ++n;
         bytes += (double)lvl_n(ctx, l) * CELLS * 16.0;
       }
-  cudaGraph_t g;
+  }
+  const long long kernels = ctx->n_launch - n0;
+  cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
   ctx->stream = saved;
-  ctx->n_launch -= n;
+  ctx->n_launch -= kernels;
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
   if (e != cudaSuccess) return sm_cuda_check(ctx, e, "bench capture");
   cudaGraphExec_t x;
   e = cudaGraphInstantiate(&x, g, 0);
@@ -921,9 +1515,17 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaGraphExecDestroy(x);
-  ctx->n_launch += 2 * n;
+  ctx->n_launch += 2 * kernels;
   if (us_per_launch) *us_per_launch = 1e3 * ms / n;
   if (launches) *launches = n;
+  if (kclass == K_VCYCLE) {
+    double by, fl;
+    vcycle_model(ctx, top, &by, &fl);
+    if (bytes_per_launch) *bytes_per_launch = by;
+    if (flops_per_launch) *flops_per_launch = fl;
+    return SM_OK;
+  }
   if (bytes_per_launch) *bytes_per_launch = bytes / n;
+  if (flops_per_launch) *flops_per_launch = 3.5 * bytes / 16.0 / n;  // 7 per updated cell
   return SM_OK;
 }

@@ -37,7 +37,7 @@ struct Table {
 };
 
 // kernel classes for sm_kernel_bench
-enum KClass { K_SMOOTH = 0, K_NCLASS = 1 };
+enum KClass { K_SMOOTH = 0, K_PERSIST = 1, K_VCYCLE = 2, K_NCLASS = 3 };
 
 }  // namespace sm
 
@@ -108,6 +108,11 @@ struct sm_ctx {
   // captured solves (invalidated when the octree changes)
   bool graphs = true;
   bool pdl = true;  // programmatic dependent launch between level kernels
+  // the next launch waits for full completion of its predecessor: set after
+  // kernels that write the tables, which dependents read before their wait
+  bool pdl_fence = false;
+  bool persist = false;      // V-cycles as one persistent cooperative launch
+  int persist_grid[2] = {0, 0};  // co-resident blocks of the FP64 / FP32 kernel
   cudaStream_t cap = nullptr, cap2 = nullptr;
   sm_graph g_solve, g_fmg, g_solve32, g_fmg32;
 
@@ -142,6 +147,9 @@ enum {
   SC_REL = 7,       // relative residual after the last cycle (double bits)
   SC_TOL = 8,       // loop tolerance (double bits), set before a launch
   SC_MAXC = 9,      // loop cycle limit, set before a launch
+  SC_PN0 = 10,      // residual max of the persistent loop, even passes
+  SC_PN1 = 11,      // residual max of the persistent loop, odd passes
+  SC_BAR = 12,      // grid barrier arrival counter of the persistent kernel
   SC_N = 16
 };
 
@@ -193,9 +201,8 @@ __device__ __forceinline__ void block_max_to(unsigned long long *slot, double v,
 // inner), or refinement boundary inner/3 + 2 phihat/3 with the stored
 // coarse interpolation phihat.
 template <typename T>
-__device__ __forceinline__ T pot_ghost(const T *__restrict__ v, const int32_t *__restrict__ nbr6,
-                                       const T *__restrict__ gh, int b, int f, int i, int j, int k,
-                                       T inner, const Bc &bc, int homog) {
+__device__ __forceinline__ T pot_ghost(const T *v, const int32_t *__restrict__ nbr6, const T *gh, int b, int f,
+                                       int i, int j, int k, T inner, const Bc &bc, int homog) {
   int nb = __ldg(nbr6 + 6 * b + f);
   int a = f >> 1;
   if (nb >= 0) {
@@ -212,9 +219,8 @@ __device__ __forceinline__ T pot_ghost(const T *__restrict__ v, const int32_t *_
 
 // sum of the six neighbours of cell (i,j,k) of box b (ghosts as above)
 template <typename T>
-__device__ __forceinline__ T nb_sum(const T *__restrict__ v, const int32_t *__restrict__ nbr6,
-                                    const T *__restrict__ gh, int b, int i, int j, int k, T ctr,
-                                    const Bc &bc, int homog) {
+__device__ __forceinline__ T nb_sum(const T *v, const int32_t *__restrict__ nbr6, const T *gh, int b, int i,
+                                    int j, int k, T ctr, const Bc &bc, int homog) {
   const T *p = v + (size_t)b * CELLS;
   int c = cidx(i, j, k);
   T s = (i > 0) ? p[c - 1] : pot_ghost(v, nbr6, gh, b, 0, i, j, k, ctr, bc, homog);
@@ -244,7 +250,8 @@ inline cudaError_t sm_launch(sm_ctx *ctx, void (*k)(KArgs...), dim3 grid, dim3 b
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = ctx->pdl ? 1 : 0;
+  cfg.numAttrs = (ctx->pdl && !ctx->pdl_fence) ? 1 : 0;
+  ctx->pdl_fence = false;
   ++ctx->n_launch;
   return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }

@@ -88,13 +88,16 @@ def test_mixed_warm_solve_and_heun_step():
     assert rg[1] == pytest.approx(ro[1], rel=1e-5)
 
 
-def test_mixed_graph_and_direct_identical():
+def test_mixed_graph_direct_and_persistent_identical():
+    """Graph and host-driven paths, with the FP32 V-cycle as one persistent
+    launch or as per-level launches: bit-identical results."""
     dom, st = synth.workload("streamer_small")
     p = pkg()
     out = []
-    for graphs in (True, False):
+    for graphs, persist in ((True, True), (False, True), (True, False), (False, False)):
         g = gpu_mesh(dom, st, precision=p.MIXED)
         g.set_graphs(graphs)
+        g.set_persistent(persist)
         t = g.tables()
         ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
         g.upload(p.NE, ne); g.upload(p.NI, ni)
@@ -103,9 +106,10 @@ def test_mixed_graph_and_direct_identical():
         r2 = g.solve(1e-10, 30)
         out.append((r1, r2, g.download(p.PHI)))
         g.close()
-    (a1, a2, pa), (b1, b2, pb) = out
-    assert a1 == b1 and a2 == b2
-    assert np.array_equal(pa, pb)
+    a1, a2, pa = out[0]
+    for b1, b2, pb in out[1:]:
+        assert a1 == b1 and a2 == b2
+        assert np.array_equal(pa, pb)
 
 
 @pytest.mark.slow

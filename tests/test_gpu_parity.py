@@ -237,31 +237,34 @@ def test_error_paths():
     assert rc == p.SM_ENOCONV and cyc == 2 and rel < 1e-2
 
 
-def test_graph_direct_and_pdl_paths_identical():
-    """Captured solves (device-side cycle loop) launch the same kernels in
-    the same order as the host-driven path, and programmatic dependent
-    launch only lets a kernel start waiting early: all four combinations
-    give bit-identical results."""
+def test_graph_direct_pdl_and_persistent_paths_identical():
+    """Captured solves (device-side cycle loop) launch the same work in the
+    same order as the host-driven path; programmatic dependent launch only
+    lets a kernel start waiting early; the persistent kernel runs the same
+    per-box operations between grid barriers: every combination gives
+    bit-identical results."""
     dom, st = synth.workload("streamer_small")
     p = pkg()
     out = []
-    for graphs in (True, False):
-        for pdl in (True, False):
-            g = gpu_mesh(dom, st)
-            g.set_graphs(graphs)
-            g.set_pdl(pdl)
-            t = g.tables()
-            ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
-            g.upload(p.NE, ne); g.upload(p.NI, ni)
-            g.charge_rhs(Q, EPS0)
-            r1 = g.fmg(1e-9, 30)
-            r2 = g.solve(1e-11, 30)
-            out.append((r1, r2, g.download(p.PHI)))
-            g.close()
-    a1, a2, pa = out[0]
-    for b1, b2, pb in out[1:]:
+    for graphs, pdl, persist in ((True, True, True), (False, True, True), (True, True, False),
+                                 (False, True, False), (True, False, False), (False, False, False)):
+        g = gpu_mesh(dom, st)
+        g.set_graphs(graphs)
+        g.set_pdl(pdl)
+        g.set_persistent(persist)
+        t = g.tables()
+        ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+        g.upload(p.NE, ne); g.upload(p.NI, ni)
+        g.charge_rhs(Q, EPS0)
+        r1 = g.fmg(1e-9, 30)
+        r2 = g.solve(1e-11, 30)
+        r3 = g.vcycles(2)
+        out.append((r1, r2, r3, g.download(p.PHI)))
+        g.close()
+    a1, a2, a3, pa = out[0]
+    for b1, b2, b3, pb in out[1:]:
         assert a1[2] == b1[2] and a2[2] == b2[2]
-        assert a1[1] == b1[1] and a2[1] == b2[1]
+        assert a1[1] == b1[1] and a2[1] == b2[1] and a3 == b3
         assert np.array_equal(pa, pb)
 
 
@@ -275,5 +278,9 @@ def test_repeated_graph_launch_and_launch_count():
     n2 = g.launch_count()
     assert r1[:3] == r2[:3]
     assert n2 - n1 == n1 - n0 - 1  # first call also built the level-0 basis
-    us, n, by = g.kernel_bench(0, 3)
-    assert us > 0 and n == 3 * 2 * (g.n_levels - 1) and by > 0
+    us, n, by, fl = g.kernel_bench(0, 3)
+    assert us > 0 and n == 3 * 2 * (g.n_levels - 1) and by > 0 and fl == pytest.approx(3.5 * by / 16)
+    us, n, by, fl = g.kernel_bench(1, 3)
+    assert us > 0 and n == 3 and by > 0 and fl > 0
+    us2, n2, by2, fl2 = g.kernel_bench(2, 3)
+    assert us2 > 0 and n2 == 3 and by2 == by and fl2 == fl
