@@ -238,7 +238,7 @@ int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
  *     smoothing 16 B and 3.5 per cell and colour pass; residual with
  *     restriction 18 B and 9 per fine cell; FAS completion 16 B per cell of
  *     the level below plus 16 B and 7 per cell of its refined boxes;
- *     prolongation 18 B and 8 per fine cell; level-0 solve 16 B and 60 per
+ *     prolongation 18 B and 3 per fine cell; level-0 solve 16 B and 60 per
  *     cell.  Ghost-value arithmetic is not counted.
  *   class 2 (V-cycle as per-level launches): one CUDA graph of `reps` FP64
  *     V-cycles launched level by level; the unit is one V-cycle, bytes and

@@ -313,54 +313,105 @@ __device__ __forceinline__ void cf_faces_box(int e, int nthreads, const T *v, T 
 // correction (phi - old) with homogeneous wall ghosts, mode 1 overwrites
 // with the prolonged solution (FMG); gh interpolates phi itself.  homog:
 // the variable is an error (homogeneous wall ghosts everywhere).
+//
+// The coarse values of the 4^3 cells under b and of their face neighbours
+// (6^3 region without edges and corners) are staged once in sp[216]; each
+// thread then forms four of the eight fine values of one coarse cell from
+// the shared partial sums (c + c_x) and (c + c_x + c_y), which keeps the
+// summation order ((c + c_x) + c_y) + c_z of the 4-point stencil.
 template <typename T>
-__device__ __forceinline__ void prolong_box(const Grp &g, int b, int mode, T *phi, const T *old, T *gh,
+__device__ __forceinline__ void prolong_box(const Grp &g, T *sp, int b, int mode, T *phi, const T *old, T *gh,
                                             const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
                                             const int32_t *__restrict__ ijk, const Bc &bc, int homog,
                                             unsigned long long *err) {
   const int P = __ldg(parent + b);
-  const int bx = __ldg(ijk + 3 * b), by = __ldg(ijk + 3 * b + 1), bz = __ldg(ijk + 3 * b + 2);
-  const int px = __ldg(ijk + 3 * P), py = __ldg(ijk + 3 * P + 1), pz = __ldg(ijk + 3 * P + 2);
+  const int o[3] = {__ldg(ijk + 3 * b) & 1, __ldg(ijk + 3 * b + 1) & 1, __ldg(ijk + 3 * b + 2) & 1};
   auto val = [&](int Q, int c) {
     const size_t x = (size_t)Q * CELLS + c;
     return mode ? phi[x] : phi[x] - old[x];
   };
   const int hom = (mode && !homog) ? 0 : 1;
+  auto reg = [](int x, int y, int z) { return x + 6 * y + 36 * z; };
+  // interior of the region: the 64 coarse cells under b
+  if (g.t < 64) {
+    const int x = g.t & 3, y = (g.t >> 2) & 3, z = g.t >> 4;
+    sp[reg(x + 1, y + 1, z + 1)] = val(P, cidx(4 * o[0] + x, 4 * o[1] + y, 4 * o[2] + z));
+  }
+  // face layers: 16 cells per face, face F by threads [slot, slot + 16)
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = g.t + h * GT;
-    const int G0 = NC * bx + (t & 7), G1 = NC * by + ((t >> 3) & 7), G2 = NC * bz + (t >> 6);
-    const int l0 = (G0 >> 1) - NC * px, l1 = (G1 >> 1) - NC * py, l2 = (G2 >> 1) - NC * pz;
-    const T c0 = val(P, cidx(l0, l1, l2));
-    T sum = c0;
-    sum += coarse_step<0, T>(val, nbr6, P, l0, l1, l2, (G0 & 1) ? 1 : -1, c0, bc, hom, err);
-    sum += coarse_step<1, T>(val, nbr6, P, l0, l1, l2, (G1 & 1) ? 1 : -1, c0, bc, hom, err);
-    sum += coarse_step<2, T>(val, nbr6, P, l0, l1, l2, (G2 & 1) ? 1 : -1, c0, bc, hom, err);
-    const size_t x = (size_t)b * CELLS + t;
-    if (mode) phi[x] = T(0.25) * sum;
-    else phi[x] += T(0.25) * sum;
+  for (int F = 0; F < 6; ++F) {
+    const int slot = F < 4 ? 64 + 16 * F : 16 * (F - 4);
+    if (g.t < slot || g.t >= slot + 16) continue;
+    const int E = F >> 1, S = (F & 1) ? 1 : -1;
+    const int u = (g.t - slot) & 3, w = (g.t - slot) >> 2;
+    // region coordinates: the layer along E, (u, w) along the other axes
+    int rc[3], lc[3];
+    rc[E] = S > 0 ? 5 : 0;
+    rc[(E + 1) % 3] = u + 1;
+    rc[(E + 2) % 3] = w + 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lc[d] = 4 * o[d] - 1 + rc[d];
+    T v;
+    if (lc[E] >= 0 && lc[E] < NC) {
+      v = val(P, cidx(lc[0], lc[1], lc[2]));
+    } else {
+      const int Qn = __ldg(nbr6 + 6 * P + F);
+      if (Qn >= 0) {
+        lc[E] = S > 0 ? 0 : NC - 1;
+        v = val(Qn, cidx(lc[0], lc[1], lc[2]));
+      } else {
+        lc[E] -= S;  // the coarse cell inside P next to the boundary
+        const T ctr = val(P, cidx(lc[0], lc[1], lc[2]));
+        if (Qn == -1) {
+          v = bc.type[F] ? (hom ? T(0) : T(2.0 * bc.val[F])) - ctr : ctr;
+        } else {
+          atomicOr(err, 1ull);  // nesting violated: no coarse box where one must be
+          v = ctr;
+        }
+      }
+    }
+    sp[reg(rc[0], rc[1], rc[2])] = v;
+  }
+  g.sync();
+  {
+    const int cc = g.t >> 1, dx = g.t & 1;
+    const int ci = cc & 3, cj = (cc >> 2) & 3, ck = cc >> 4;
+    const int q = reg(ci + 1, cj + 1, ck + 1);
+    const T A = sp[q] + sp[q + (dx ? 1 : -1)];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const T B = A + sp[q + (dy ? 6 : -6)];
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const T sum = B + sp[q + (dz ? 36 : -36)];
+        const size_t x = (size_t)b * CELLS + cidx(2 * ci + dx, 2 * cj + dy, 2 * ck + dz);
+        if (mode) phi[x] = T(0.25) * sum;
+        else phi[x] += T(0.25) * sum;
+      }
+    }
   }
   cf_faces_box(g.t, GT, phi, gh, nbr6, parent, ijk, bc, homog, b, err);
+  g.sync();  // sp is free again
 }
 
 // Exact solve on level 0 (one 8^3 box), always in FP64: fold the Dirichlet
 // boundary values into the right-hand side (not for the homogeneous error
 // equation), transform to the separable eigenbasis, divide by the
-// eigenvalues of the 7-point operator, transform back.  sm: 2 x 512 + 216
-// doubles of shared memory.
-template <typename T>
-__device__ __forceinline__ void coarse_box(const Grp &g, double *sm, T *phi, const T *rhs,
+// eigenvalues of the 7-point operator, transform back.  NT threads (t0 the
+// thread's index, sync their barrier); sm: 2 x 512 + 216 doubles of shared
+// memory.
+template <int NT, typename T, typename Sync>
+__device__ __forceinline__ void coarse_box(int t0, Sync sync, double *sm, T *phi, const T *rhs,
                                            const double *__restrict__ basis, const Bc &bc, double h2,
                                            double inv_h2, int homog) {
   double *x = sm, *y = sm + CELLS, *V = sm + 2 * CELLS, *lam = V + 192;
-  const int t0 = g.t;
-  for (int i = t0; i < 216; i += GT) {
+  for (int i = t0; i < 216; i += NT) {
     if (i < 192) V[i] = __ldg(basis + i);
     else lam[i - 192] = __ldg(basis + i);
   }
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT;
     const int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
     double r = (double)rhs[t];
     if (!homog) {
@@ -372,57 +423,57 @@ __device__ __forceinline__ void coarse_box(const Grp &g, double *sm, T *phi, con
     }
     x[t] = r;
   }
-  g.sync();
+  sync();
   // forward: coefficients along x, then y, then z
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[0 * 64 + m * 8 + c0] * x[cidx(m, c1, c2)];
     y[t] = acc;
   }
-  g.sync();
+  sync();
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[1 * 64 + m * 8 + c1] * y[cidx(c0, m, c2)];
     x[t] = acc;
   }
-  g.sync();
+  sync();
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[2 * 64 + m * 8 + c2] * x[cidx(c0, c1, m)];
     y[t] = acc * h2 / (lam[c0] + lam[8 + c1] + lam[16 + c2]);
   }
-  g.sync();
+  sync();
   // backward
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[0 * 64 + c0 * 8 + m] * y[cidx(m, c1, c2)];
     x[t] = acc;
   }
-  g.sync();
+  sync();
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[1 * 64 + c1 * 8 + m] * x[cidx(c0, m, c2)];
     y[t] = acc;
   }
-  g.sync();
+  sync();
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int t = t0 + h * GT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
+  for (int h = 0; h < CELLS / NT; ++h) {
+    const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[2 * 64 + c2 * 8 + m] * y[cidx(c0, c1, m)];
     phi[t] = (T)acc;
   }
-  g.sync();  // sm is free again
+  sync();  // sm is free again
 }
 
 // FP64 residual f - L v of the cells of this thread in leaf box b; the
@@ -528,8 +579,9 @@ __global__ void __launch_bounds__(GT) k_prolong_cf(int lo, int mode, T *__restri
                                                    const int32_t *__restrict__ parent,
                                                    const int32_t *__restrict__ ijk, Bc bc, int homog,
                                                    unsigned long long *err) {
+  __shared__ T sp[216];
   pdl_wait();
-  prolong_box(block_grp(), lo + blockIdx.x, mode, phi, old, gh, nbr6, parent, ijk, bc, homog, err);
+  prolong_box(block_grp(), sp, lo + blockIdx.x, mode, phi, old, gh, nbr6, parent, ijk, bc, homog, err);
 }
 
 // coarse interpolation values of the refinement faces of the boxes
@@ -545,12 +597,12 @@ __global__ void __launch_bounds__(64) k_fill_cf(int lo, const T *__restrict__ v,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(GT) k_coarse_solve(T *__restrict__ phi, const T *__restrict__ rhs,
-                                                     const double *__restrict__ basis, Bc bc, double h2,
-                                                     double inv_h2, int homog) {
+__global__ void __launch_bounds__(CELLS) k_coarse_solve(T *__restrict__ phi, const T *__restrict__ rhs,
+                                                        const double *__restrict__ basis, Bc bc, double h2,
+                                                        double inv_h2, int homog) {
   __shared__ double sm[2 * CELLS + 216];
   pdl_wait();
-  coarse_box(block_grp(), sm, phi, rhs, basis, bc, h2, inv_h2, homog);
+  coarse_box<CELLS>((int)threadIdx.x, [] { __syncthreads(); }, sm, phi, rhs, basis, bc, h2, inv_h2, homog);
 }
 
 // Orthonormal eigenvectors and (h^2-scaled) eigenvalues of the 1-D
@@ -715,14 +767,15 @@ struct Persist {
   }
 
   __device__ bool coarse() {
-    if (gi == 0) coarse_box(g, sd, a.phi, a.rhs, a.basis, a.bc, a.lh.h2[0], a.lh.inv_h2[0], a.homog);
+    if (gi == 0)
+      coarse_box<GT>(g.t, [&] { g.sync(); }, sd, a.phi, a.rhs, a.basis, a.bc, a.lh.h2[0], a.lh.inv_h2[0], a.homog);
     return bar.sync();
   }
 
   __device__ bool prolong(int l, int mode) {
     if (empty(l)) return true;
     for (int b = lo(l) + gi; b < hi(l); b += ng)
-      prolong_box(g, b, mode, a.phi, a.old, a.gh, a.nbr6, a.parent, a.ijk, a.bc, a.homog, a.sc + SC_ERR);
+      prolong_box(g, s, b, mode, a.phi, a.old, a.gh, a.nbr6, a.parent, a.ijk, a.bc, a.homog, a.sc + SC_ERR);
     return bar.sync();
   }
 
@@ -920,7 +973,7 @@ template <typename T>
 static int coarse_solve(sm_ctx *ctx, const MG<T> &m) {
   int st = ensure_basis(ctx);
   if (st) return st;
-  sm_launch(ctx, k_coarse_solve<T>, 1, GT, 0, m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
+  sm_launch(ctx, k_coarse_solve<T>, 1, CELLS, 0, m.phi, m.rhs, ctx->basis, ctx->bc, ctx->lh.h2[0],
             ctx->lh.inv_h2[0], m.homog);
   SM_CKL("coarse solve");
   return SM_OK;
@@ -1425,7 +1478,7 @@ static void vcycle_model(const sm_ctx *ctx, int top, double *bytes, double *ops)
     const double n = (double)CELLS * lvl_n(ctx, l), nc = (double)CELLS * lvl_n(ctx, l - 1);
     const double refined = n / 8.0;  // cells of the refined boxes of level l-1
     by += sweeps * 2.0 * 16.0 * n + 18.0 * n + 16.0 * nc + 16.0 * refined + 18.0 * n;
-    op += sweeps * 7.0 * n + 9.0 * n + 7.0 * refined + 8.0 * n;
+    op += sweeps * 7.0 * n + 9.0 * n + 7.0 * refined + 3.0 * n;
   }
   *bytes = by;
   *ops = op;
