@@ -71,18 +71,23 @@ __device__ __forceinline__ Nb load_nb(const Grp &g, const int32_t *__restrict__ 
 // homogeneous, Neumann inner) or inner/3 + 2 phihat/3 at a refinement face.
 // The neighbour-table, neighbour-cell and phihat loads are issued together
 // with the interior loads; face f is filled by the 64-thread slice f mod NSL.
+// With color >= 0 only the halo cells next to interior cells of that colour
+// ((i+j+k) % 2 == color) are filled: a colour pass reads no others.
 template <typename T>
 __device__ __forceinline__ void stage_box(const Grp &g, T *s, const T *v, const Nb &nbv, const T *gh, int b,
-                                          const Bc &bc, int homog) {
+                                          const Bc &bc, int homog, int color = -1) {
   const T *p = v + (size_t)b * CELLS;
   T x[CPT];
 #pragma unroll
   for (int h = 0; h < CPT; ++h) x[h] = p[g.t + h * GT];
   const int slice = g.t >> 6, u = g.t & 7, w = (g.t >> 3) & 7;
   T hv[FPS];
+  // colour of the interior face cell (u, w) of face f: u + w + (0 or 7)
+  const int cw = (u + w) & 1;
+  auto used = [&](int f) { return color < 0 || ((cw + ((f & 1) ? 1 : 0)) & 1) == color; };
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
-    if (f % NSL != slice) continue;
+    if (f % NSL != slice || !used(f)) continue;
     const int r = f / NSL;
     const int nb = nbv.v[r];
     if (nb >= 0) hv[r] = v[(size_t)nb * CELLS + face_cell(f ^ 1, u, w)];
@@ -95,7 +100,7 @@ __device__ __forceinline__ void stage_box(const Grp &g, T *s, const T *v, const 
   g.sync();
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
-    if (f % NSL != slice) continue;
+    if (f % NSL != slice || !used(f)) continue;
     const int r = f / NSL, a = f >> 1;
     const int q = s10(face_cell(f, u, w));
     const int stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
@@ -131,7 +136,7 @@ __device__ __forceinline__ void rbgs_box(const Grp &g, T *s, int b, int color, T
     c[h] = cidx(((n & 3) << 1) | ((j + k + color) & 1), j, k);
     f[h] = rhs[base + c[h]];
   }
-  stage_box(g, s, phi, nb, gh, b, bc, homog);
+  stage_box(g, s, phi, nb, gh, b, bc, homog, color);
 #pragma unroll
   for (int h = 0; h < RPT; ++h) phi[base + c[h]] = (staged_sum(s, s10(c[h])) - h2 * f[h]) * T(1.0 / 6.0);
 }
@@ -573,15 +578,39 @@ __global__ void __launch_bounds__(GT) k_resid_restrict(int lo, T *__restrict__ p
   resid_restrict_box(g, s, sr, b, phi, rhs, gh, nb, pl, bc, inv_h2, homog);
 }
 
+// leaf boxes of one level whose FP64 residual norm a prolongation launch
+// computes in extra blocks (n = 0: none)
+struct LeafNorm {
+  const int32_t *leaf;  // leaf list segment of the level
+  int n;
+  const double *v, *rhs, *gh;
+  double inv_h2;
+  unsigned long long *slot;
+};
+
+// Blocks [0, n) prolong into the boxes [lo, lo + n) of level l; blocks
+// beyond add the residual max of the leaf boxes of level l-1, which no
+// later operation of the V-cycle changes, to ln.slot.
 template <typename T>
-__global__ void __launch_bounds__(GT) k_prolong_cf(int lo, int mode, T *__restrict__ phi, const T *__restrict__ old,
-                                                   T *__restrict__ gh, const int32_t *__restrict__ nbr6,
+__global__ void __launch_bounds__(GT) k_prolong_cf(int lo, int n, int mode, T *__restrict__ phi,
+                                                   const T *__restrict__ old, T *__restrict__ gh,
+                                                   const int32_t *__restrict__ nbr6,
                                                    const int32_t *__restrict__ parent,
                                                    const int32_t *__restrict__ ijk, Bc bc, int homog,
-                                                   unsigned long long *err) {
+                                                   unsigned long long *err, LeafNorm ln) {
   __shared__ T sp[216];
+  __shared__ double rs[1000 + GT / 32];
+  const Grp g = block_grp();
+  if ((int)blockIdx.x >= n) {
+    const int b = __ldg(ln.leaf + blockIdx.x - n);
+    const Nb nb = load_nb(g, nbr6, b);
+    pdl_wait();
+    const double m = resid_box(g, rs, b, ln.v, ln.rhs, ln.gh, nb, bc, ln.inv_h2, nullptr);
+    group_max_to(g, ln.slot, m, rs + 1000);
+    return;
+  }
   pdl_wait();
-  prolong_box(block_grp(), sp, lo + blockIdx.x, mode, phi, old, gh, nbr6, parent, ijk, bc, homog, err);
+  prolong_box(g, sp, lo + blockIdx.x, mode, phi, old, gh, nbr6, parent, ijk, bc, homog, err);
 }
 
 // coarse interpolation values of the refinement faces of the boxes
@@ -922,11 +951,14 @@ int sm_mg_fill_cf(sm_ctx *ctx, double *var, int l, int homog) {
   return SM_OK;
 }
 
+// every level at once: each level's values come from the level below only
 int sm_fill_all_cf(sm_ctx *ctx, double *var) {
-  for (int l = ctx->lbase + 1; l < ctx->n_levels; ++l) {
-    int st = sm_mg_fill_cf(ctx, var, l, 0);
-    if (st) return st;
-  }
+  if (ctx->lbase + 1 >= ctx->n_levels) return SM_OK;
+  const int lo = ctx->level_off[ctx->lbase + 1], n = ctx->n_boxes - lo;
+  if (n <= 0) return SM_OK;
+  sm_launch(ctx, k_fill_cf<double>, n, 64, 0, lo, var, ctx->gh, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, 0,
+            ctx->dscal + SC_ERR);
+  SM_CKL("fill_cf");
   return SM_OK;
 }
 
@@ -979,11 +1011,24 @@ static int coarse_solve(sm_ctx *ctx, const MG<T> &m) {
   return SM_OK;
 }
 
+// leaf segment of level l for a residual-norm role (none when slot < 0)
+static LeafNorm leaf_norm_of(sm_ctx *ctx, int l, int slot) {
+  LeafNorm ln = {};
+  if (slot < 0 || l < 0) return ln;
+  ln.leaf = ctx->leaf + ctx->leaf_level_off[l];
+  ln.n = ctx->leaf_level_off[l + 1] - ctx->leaf_level_off[l];
+  ln.v = ctx->phi;
+  ln.rhs = ctx->rhs;
+  ln.gh = ctx->gh;
+  ln.inv_h2 = ctx->lh.inv_h2[l];
+  ln.slot = ctx->dscal + slot;
+  return ln;
+}
+
 template <typename T>
-static int prolong_cf(sm_ctx *ctx, const MG<T> &m, int l, int mode) {
-  sm_launch(ctx, k_prolong_cf<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], mode, m.phi, m.old, m.gh,
-            ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, m.homog,
-            ctx->dscal + SC_ERR);
+static int prolong_cf(sm_ctx *ctx, const MG<T> &m, int l, int mode, LeafNorm ln = LeafNorm{}) {
+  sm_launch(ctx, k_prolong_cf<T>, lvl_n(ctx, l) + ln.n, GT, 0, ctx->level_off[l], lvl_n(ctx, l), mode, m.phi, m.old,
+            m.gh, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, m.homog, ctx->dscal + SC_ERR, ln);
   SM_CKL("prolong");
   return SM_OK;
 }
@@ -993,9 +1038,15 @@ static int prolong_cf(sm_ctx *ctx, const MG<T> &m, int l, int mode) {
 // values of the level below (the solve prologue and every up-sweep leave
 // them so); the down-sweep changes no level below the one it smooths
 // before that level is visited again, so it needs no refill.
+// With norm_slot >= 0 (FP64 arrays, top the finest level) the cycle also
+// leaves max_leaf |f - L phi| in that slot: the leaves of level l-1 are
+// measured by extra blocks of the prolongation into level l, those of the
+// top level after its post-smoothing.
 template <typename T>
-static int vcycle(sm_ctx *ctx, const MG<T> &m, int top) {
+static int vcycle(sm_ctx *ctx, const MG<T> &m, int top, int norm_slot = -1) {
   int st;
+  if (norm_slot >= 0)
+    SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
   for (int l = top; l >= 1; --l) {
     if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
     sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
@@ -1008,8 +1059,15 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top) {
   }
   if ((st = coarse_solve(ctx, m))) return st;
   for (int l = 1; l <= top; ++l) {
-    if ((st = prolong_cf(ctx, m, l, 0))) return st;
+    if ((st = prolong_cf(ctx, m, l, 0, leaf_norm_of(ctx, norm_slot >= 0 ? l - 1 : -1, norm_slot)))) return st;
     if ((st = smooth(ctx, m, l, ctx->cfg.nu2))) return st;
+  }
+  if (norm_slot >= 0) {
+    const LeafNorm ln = leaf_norm_of(ctx, top, norm_slot);
+    if (ln.n > 0)
+      sm_launch(ctx, k_resnorm, ln.n, GT, 0, ln.leaf, ctx->level, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6, ctx->bc,
+                ctx->lh, (float *)nullptr, ln.slot);
+    SM_CKL("resnorm");
   }
   return SM_OK;
 }
@@ -1092,18 +1150,22 @@ static int cycle(sm_ctx *ctx, const MG<T> &m, int top) {
   return vcycle(ctx, m, top);
 }
 
+static int leaf_norm(sm_ctx *ctx, double *v, int slot);
+
 // FMG ladder: restrict f, exact level-0 solve, then for each finer level
 // prolong the solution (and its interpolation values) and run one V-cycle
-// with that level on top
+// with that level on top; with norm_slot >= 0 (FP64) the residual max of
+// the result is left in that slot
 template <typename T>
-static int fmg_ladder(sm_ctx *ctx, const MG<T> &m) {
+static int fmg_ladder(sm_ctx *ctx, const MG<T> &m, int norm_slot = -1) {
   int st;
   if ((st = restrict_chain<T>(ctx, m.rhs, nullptr))) return st;
   if ((st = coarse_solve(ctx, m))) return st;
   for (int l = 1; l < ctx->n_levels; ++l) {
     if ((st = prolong_cf(ctx, m, l, 1))) return st;
-    if ((st = vcycle(ctx, m, l))) return st;
+    if ((st = vcycle(ctx, m, l, l == ctx->n_levels - 1 ? norm_slot : -1))) return st;
   }
+  if (norm_slot >= 0 && ctx->n_levels == 1) return leaf_norm(ctx, ctx->phi, norm_slot);
   return SM_OK;
 }
 
@@ -1198,8 +1260,7 @@ static int solve_prefix(sm_ctx *ctx, int kind) {
       return solve_prologue(ctx);
     case 1:
       if ((st = solve_prologue(ctx))) return st;
-      if ((st = fmg_ladder(ctx, mg64(ctx)))) return st;
-      return leaf_norm(ctx, ctx->phi, SC_NORM);
+      return fmg_ladder(ctx, mg64(ctx), SC_NORM);
     case 2:
       if ((st = solve_prologue(ctx))) return st;
       return leaf_resid32(ctx);
@@ -1216,10 +1277,8 @@ static int solve_prefix(sm_ctx *ctx, int kind) {
 }
 
 static int solve_body(sm_ctx *ctx, int kind) {
-  int st;
   if (kind >= 2) return mixed_correction(ctx, 0);
-  if ((st = vcycle(ctx, mg64(ctx), ctx->n_levels - 1))) return st;
-  return leaf_norm(ctx, ctx->phi, SC_NORM);
+  return vcycle(ctx, mg64(ctx), ctx->n_levels - 1, SC_NORM);
 }
 
 // ---- graph-captured solves with a device-side cycle loop ------------------
