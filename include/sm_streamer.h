@@ -268,6 +268,15 @@ int sm_set_graphs(sm_ctx *ctx, int enable);
  * dropped on a change. */
 int sm_set_persistent(sm_ctx *ctx, int enable);
 
+/* Self-test of the bounded grid-barrier wait of the persistent kernel: one
+ * launch whose barriers wait for one block more than the grid holds, so
+ * every block's wait runs out (about a second), sets the error flag and
+ * returns.  Expected result SM_ETIMEOUT; the flag is cleared afterwards and
+ * the context stays usable (the potential may have received part of a
+ * V-cycle).  Errors: SM_ESTATE (no octree or a pending device error),
+ * SM_EINVAL (single-level octree). */
+int sm_persist_barrier_selftest(sm_ctx *ctx);
+
 /* Kernels of the multigrid solve are launched with programmatic dependent
  * launch when enabled (default): a kernel may be scheduled while its
  * predecessor on the stream drains, and waits for that predecessor's

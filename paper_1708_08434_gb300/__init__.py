@@ -59,7 +59,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_set_table", "sm_charge_rhs", "sm_restrict_densities", "sm_fill_ghosts",
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs", "sm_set_pdl",
-           "sm_set_persistent",
+           "sm_set_persistent", "sm_persist_barrier_selftest",
            "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
@@ -111,6 +111,7 @@ def load():
         "sm_set_graphs": [P, I],
         "sm_set_pdl": [P, I],
         "sm_set_persistent": [P, I],
+        "sm_persist_barrier_selftest": [P],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
         "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
@@ -349,6 +350,11 @@ class Solver:
     # -- diagnostics --
     def set_graphs(self, enable: bool):
         self._ck(self._lib.sm_set_graphs(self._h, int(enable)))
+
+    def persist_barrier_selftest(self) -> int:
+        """Status of a persistent launch whose grid barriers cannot complete
+        (SM_ETIMEOUT expected); the context stays usable."""
+        return int(self._lib.sm_persist_barrier_selftest(self._h))
 
     def set_pdl(self, enable: bool):
         """Programmatic dependent launch of the solver kernels on or off."""

@@ -712,7 +712,7 @@ __global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *s
 // sets error bit 4 and returns, and so do the others at their next wait.
 
 constexpr unsigned long long ERR_BARRIER = 4ull;
-constexpr long long PERSIST_SPIN = 1ll << 22;
+constexpr long long PERSIST_SPIN = 1ll << 21;  // about a second of polling
 
 template <typename T>
 struct PArgs {
@@ -727,6 +727,7 @@ struct PArgs {
   int n_levels, n_leaves, top, nu1, nu2, homog;
   int fmg;   // run the FMG ladder first (restricted rhs, level-0 solve, one V-cycle per finer level)
   int loop;  // after that (or from the start): V-cycles with the residual test until converged
+  int bar_extra;  // arrivals a barrier waits for beyond the grid (0; 1 only in the timeout self-test)
 };
 
 // shared memory of one box group of the persistent kernel (bytes)
@@ -740,13 +741,14 @@ static_assert(1000 + GT / 32 <= 2 * CELLS + 216, "residual staging fits the FP64
 struct GridBar {
   unsigned int *cnt;
   unsigned int epoch;
+  unsigned int extra;  // see PArgs::bar_extra
   int *flag;  // shared: barrier outcome for the block
   unsigned long long *err;
   // all blocks arrive; false when the wait ran out (the caller returns)
   __device__ __forceinline__ bool sync() {
     __syncthreads();
     if (threadIdx.x == 0) {
-      const unsigned int target = ++epoch * gridDim.x;
+      const unsigned int target = ++epoch * (gridDim.x + extra);
       __threadfence();
       atomicAdd(cnt, 1u);
       int ok = 1;
@@ -870,7 +872,7 @@ __global__ void __launch_bounds__(PGROUPS *GT, 1) k_persist(const __grid_constan
   unsigned char *base = smem + (size_t)q * persist_group_smem<T>();
   Persist<T> p{a, Grp{(int)threadIdx.x % GT, 1 + q}, q * (int)gridDim.x + (int)blockIdx.x,
                PGROUPS * (int)gridDim.x, nullptr, nullptr, nullptr,
-               GridBar{(unsigned int *)(a.sc + SC_BAR), 0u, &flag, a.sc + SC_ERR}};
+               GridBar{(unsigned int *)(a.sc + SC_BAR), 0u, (unsigned int)a.bar_extra, &flag, a.sc + SC_ERR}};
   p.sd = (double *)base;
   p.s = (T *)base;
   p.sr = p.s + 1000;
@@ -1096,7 +1098,7 @@ static int persist_prepare(sm_ctx *ctx) {
 // is reached (SC_NORM, SC_REL, SC_CYC written at the end).  Without loop
 // one V-cycle runs (or only the ladder when fmg is set).
 template <typename T>
-static int persist_launch(sm_ctx *ctx, const MG<T> &m, int top, int fmg, int loop) {
+static int persist_launch(sm_ctx *ctx, const MG<T> &m, int top, int fmg, int loop, int bar_extra = 0) {
   int st = persist_prepare<T>(ctx);
   if (st) return st;
   PArgs<T> a;
@@ -1127,6 +1129,7 @@ static int persist_launch(sm_ctx *ctx, const MG<T> &m, int top, int fmg, int loo
   a.homog = m.homog;
   a.fmg = fmg;
   a.loop = loop;
+  a.bar_extra = bar_extra;
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_BAR, 0, sizeof(unsigned long long), ctx->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctx->persist_grid[sizeof(T) == sizeof(double) ? 0 : 1]);
@@ -1512,6 +1515,21 @@ extern "C" int sm_set_graphs(sm_ctx *ctx, int enable) {
   if (!ctx) return SM_EINVAL;
   ctx->graphs = enable != 0;
   return SM_OK;
+}
+
+extern "C" int sm_persist_barrier_selftest(sm_ctx *ctx) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->n_levels < 2) return SM_EINVAL;
+  if ((st = ensure_basis(ctx))) return st;
+  if ((st = read_scalars(ctx))) return st;  // no earlier error may be pending
+  // every barrier waits for one block more than the grid holds
+  if ((st = persist_launch(ctx, mg64(ctx), ctx->n_levels - 1, 0, 0, 1))) return st;
+  st = read_scalars(ctx);
+  // the launch ended by itself: clear its flag so the context stays usable
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_ERR, 0, sizeof(unsigned long long), ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  return st;
 }
 
 extern "C" int sm_set_persistent(sm_ctx *ctx, int enable) {

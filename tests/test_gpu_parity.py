@@ -268,6 +268,30 @@ def test_graph_direct_pdl_and_persistent_paths_identical():
         assert np.array_equal(pa, pb)
 
 
+def test_persistent_barrier_wait_is_bounded():
+    """A persistent launch whose grid barriers cannot complete (every wait
+    expects one block more than the grid) ends by itself within seconds with
+    SM_ETIMEOUT; afterwards the same context solves normally."""
+    import time
+    dom, st = synth.workload("streamer_small")
+    p = pkg()
+    g = gpu_mesh(dom, st)
+    t = g.tables()
+    ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+    g.upload(p.NE, ne); g.upload(p.NI, ni)
+    g.charge_rhs(Q, EPS0)
+    t0 = time.perf_counter()
+    rc = g.persist_barrier_selftest()
+    waited = time.perf_counter() - t0
+    print("barrier self-test: status %d after %.2f s" % (rc, waited))
+    assert rc == p.SM_ETIMEOUT and waited < 30.0
+    for persist in (True, False):
+        g.set_persistent(persist)
+        rc, rel, cyc = g.fmg(1e-9, 30)
+        assert rc == 0 and rel <= 1e-9
+    g.close()
+
+
 def test_repeated_graph_launch_and_launch_count():
     dom, st, o, g = pair("streamer_small")
     load_inputs(dom, st, o, g)
