@@ -321,6 +321,9 @@ def run_gpu(args):
                  "corrections_per_step": mcyc / args.steps, "gpu_launches": mlaunch,
                  "speedup_vs_fp64": round(ms / mms, 3),
                  "dtype": "f32 error equation, f64 residual/accumulation/level-0 solve"}
+        if not args.no_profile:
+            vus32, _, vby32, _ = gm.kernel_bench(pkg.K_VCYCLE32, 10)
+            mixed["fp32_vcycle_us"] = round(vus32, 2)
         gm.close()
     batched = None if args.no_batch else bench_batch(args, dev, world)
     learned = None if args.no_learned else bench_learned(args, dev, world)

@@ -243,6 +243,9 @@ int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
  *   class 2 (V-cycle as per-level launches): one CUDA graph of `reps` FP64
  *     V-cycles launched level by level; the unit is one V-cycle, bytes and
  *     instructions as for class 1.
+ *   class 3 (FP32 V-cycle of the mixed-precision form, mixed contexts only):
+ *     one CUDA graph of `reps` FP32 V-cycles on the error equation; bytes
+ *     half those of class 1, no FP64 instructions.
  * Out (each may be NULL): microseconds per launch, launches timed,
  * algorithmic bytes and FP64 instructions per launch.  Side effect: the
  * potential receives the extra sweeps or cycles.  Errors: SM_EINVAL for an

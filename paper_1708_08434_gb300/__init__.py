@@ -24,6 +24,7 @@ MAX_LEVELS = 24
 K_SMOOTH = 0
 K_PERSIST = 1
 K_VCYCLE = 2
+K_VCYCLE32 = 3
 
 _NAMES = {SM_EINVAL: "SM_EINVAL", SM_ENOMEM: "SM_ENOMEM", SM_ECUDA: "SM_ECUDA",
           SM_ENOCONV: "SM_ENOCONV", SM_ETIMEOUT: "SM_ETIMEOUT", SM_ESTATE: "SM_ESTATE"}

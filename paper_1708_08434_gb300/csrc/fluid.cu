@@ -17,15 +17,27 @@ int sm_mg_solve_internal(sm_ctx *ctx, double tol, int max_cycles, int *cycles);
 // device helpers
 // ---------------------------------------------------------------------------
 
-// linear interpolation in a table sampled at E_k = k e_max/(n-1), clamped
-__device__ __forceinline__ double lookup(const double *__restrict__ t, int n, double inv_de, double e) {
+// Linear interpolation in two tables sampled at E_k = k e_max/(n-1),
+// clamped at both ends, at the same e: the index and weight are computed
+// once (the same arithmetic as two separate lookups).
+__device__ __forceinline__ void lookup2(const double *__restrict__ ta, const double *__restrict__ tb, int n,
+                                        double inv_de, double e, double &va, double &vb) {
   double x = e * inv_de;
-  if (x <= 0.0) return __ldg(t);
-  if (x >= (double)(n - 1)) return __ldg(t + n - 1);
+  if (x <= 0.0) {
+    va = __ldg(ta);
+    vb = __ldg(tb);
+    return;
+  }
+  if (x >= (double)(n - 1)) {
+    va = __ldg(ta + n - 1);
+    vb = __ldg(tb + n - 1);
+    return;
+  }
   int i = (int)x;
   double w = x - (double)i;
-  double t0 = __ldg(t + i), t1 = __ldg(t + i + 1);
-  return t0 + w * (t1 - t0);
+  double a0 = __ldg(ta + i), a1 = __ldg(ta + i + 1), b0 = __ldg(tb + i), b1 = __ldg(tb + i + 1);
+  va = a0 + w * (a1 - a0);
+  vb = b0 + w * (b1 - b0);
 }
 
 // psi(a/b)*b for the Koren limiter psi(x) = max(0, min(1, (2+x)/6, x)),
@@ -44,8 +56,8 @@ __device__ __forceinline__ double face_flux(double nL2, double nL, double nR, do
                                             double eL, double eR, double inv_h, const Table &tb) {
   double e_face = (pL - pR) * inv_h;
   double e_star = 0.5 * (eL + eR);
-  double mu = lookup(tb.mu, tb.n, tb.inv_de, e_star);
-  double dc = lookup(tb.diff, tb.n, tb.inv_de, e_star);
+  double mu, dc;
+  lookup2(tb.mu, tb.diff, tb.n, tb.inv_de, e_star, mu, dc);
   double v = -mu * e_face;
   double nf = v < 0.0 ? nR - koren(nR2 - nR, nR - nL) : nL + koren(nL - nL2, nR - nL);
   return v * nf - dc * (nR - nL) * inv_h;
@@ -165,7 +177,8 @@ __device__ __forceinline__ void dt_terms(const double *__restrict__ phi, const d
   const double *p = phi + (size_t)b * CELLS;
   double pc = p[t];
   const int stride[3] = {1, NC, FACE};
-  double mu = lookup(tb.mu, tb.n, tb.inv_de, em), dc = lookup(tb.diff, tb.n, tb.inv_de, em);
+  double mu, dc;
+  lookup2(tb.mu, tb.diff, tb.n, tb.inv_de, em, mu, dc);
   double s = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -362,7 +375,9 @@ __global__ void __launch_bounds__(512) k_update(
   }
   double e = S.e[I10(ci, cj, ck)];
   double nes = S.n[I12(ci, cj, ck)];
-  double src = lookup(tb.alpha, tb.n, tb.inv_de, e) * lookup(tb.mu, tb.n, tb.inv_de, e) * e * nes;
+  double alpha, mu;
+  lookup2(tb.alpha, tb.mu, tb.n, tb.inv_de, e, alpha, mu);
+  double src = alpha * mu * e * nes;
   double ne_new = nes - dt * div + dt * src;
   double ni_new = ni_src[base + t] + dt * src;
   if (heun) {

@@ -1596,8 +1596,12 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
     if (flops_per_launch) *flops_per_launch = fl;
     return SM_OK;
   }
-  if (kclass == K_VCYCLE && (st = ensure_basis(ctx))) return st;
-  if (kclass == K_VCYCLE && (st = solve_prologue(ctx))) return st;
+  const bool whole = kclass == K_VCYCLE || kclass == K_VCYCLE32;
+  if (kclass == K_VCYCLE32 && ctx->cfg.precision != SM_MIXED)
+    return sm_fail(ctx, SM_EINVAL, "class 3 needs a mixed-precision context");
+  if (whole && (st = ensure_basis(ctx))) return st;
+  if (whole && (st = solve_prologue(ctx))) return st;
+  if (kclass == K_VCYCLE32 && (st = leaf_resid32(ctx))) return st;
   cudaStream_t saved = ctx->stream;
   if (!ctx->cap) SM_CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
   SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
@@ -1608,6 +1612,11 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   for (int r = 0; r < reps; ++r) {
     if (kclass == K_VCYCLE) {
       if ((st = vcycle(ctx, m, top))) break;
+      ++n;
+      continue;
+    }
+    if (kclass == K_VCYCLE32) {
+      if ((st = vcycle(ctx, mg32(ctx), top))) break;
       ++n;
       continue;
     }
@@ -1648,9 +1657,13 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   ctx->n_launch += 2 * kernels;
   if (us_per_launch) *us_per_launch = 1e3 * ms / n;
   if (launches) *launches = n;
-  if (kclass == K_VCYCLE) {
+  if (whole) {
     double by, fl;
     vcycle_model(ctx, top, &by, &fl);
+    if (kclass == K_VCYCLE32) {  // same cells, 4-byte values, no FP64 work
+      by *= 0.5;
+      fl = 0.0;
+    }
     if (bytes_per_launch) *bytes_per_launch = by;
     if (flops_per_launch) *flops_per_launch = fl;
     return SM_OK;

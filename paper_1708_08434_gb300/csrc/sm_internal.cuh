@@ -37,7 +37,7 @@ struct Table {
 };
 
 // kernel classes for sm_kernel_bench
-enum KClass { K_SMOOTH = 0, K_PERSIST = 1, K_VCYCLE = 2, K_NCLASS = 3 };
+enum KClass { K_SMOOTH = 0, K_PERSIST = 1, K_VCYCLE = 2, K_VCYCLE32 = 3, K_NCLASS = 4 };
 
 }  // namespace sm
 
