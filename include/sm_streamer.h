@@ -302,12 +302,15 @@ int sm_launch_count(const sm_ctx *ctx, long long *n);
  * otherwise); it is solved exactly in FP64.  Cycles are FP32
  * correction-scheme V(nu1,nu2) cycles on the error equation inside a
  * per-solve FP64 defect-correction loop; every level of all solves is one
- * grid-stride launch over a tile work list; a batched solve is one CUDA
+ * grid-stride launch per phase over a work list (32x16-cell z-marching
+ * columns for a whole red-black sweep, the prolongation and the FP64
+ * residual, small 3-D tiles for the restriction); a batched solve is one CUDA
  * graph whose loop runs on the device; converged solves are masked out.
  * Memory: sm_batch_arena_size / sm_batch_bind_arena as for sm_ctx.
  * Arrays (device, through sm_batch_ptrs): phi and rhs, FP64, the grids of
- * all solves one after another at the returned offsets, cell (x,y,z) of
- * solve s at offsets[s] + x + N (y + N z). */
+ * all solves one after another at the returned offsets (each a multiple of
+ * 32 elements; the arrays end at offsets[n-1] + N^3 of the last solve),
+ * cell (x,y,z) of solve s at offsets[s] + x + N (y + N z). */
 typedef struct sm_batch sm_batch;
 int sm_batch_create(sm_batch **out, int n_solves, const int *cells_per_side, double length, const int *bc_type,
                     const double *bc_val, int nu1, int nu2, void *stream);
@@ -323,7 +326,8 @@ int sm_batch_ptrs(const sm_batch *b, double **phi, double **rhs, long long *offs
  * residual per solve.  SM_ENOCONV if a solve missed tol. Synchronises. */
 int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycles, double *rel_res);
 /* Autotuner: times `iters` corrections from phi = 0 for every candidate
- * tile shape (8x8x8, 16x8x4, 32x4x4, 32x8x2 cells) and grid size
+ * restriction tile shape (8x8x8, 16x8x4, 32x4x4, 32x8x2
+ * cells) and grid size
  * (2, 4, 8 blocks per SM), keeps the fastest; leaves phi = 0.  Out: the
  * chosen shape index, blocks per SM and its time in ms. */
 int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult, double *best_ms);
@@ -429,6 +433,20 @@ const char *sm_cnn_last_error(const sm_cnn *c);
 #define SM_NOALLOC_MAX_PROBLEMS 1024
 int sm_box_solve_noalloc(double length, int n_problems, const int32_t *bc_type, const double *bc_val,
                          const double *f, double *phi, void *stream);
+
+/* Check of the library's own FP64 <-> FP32 conversions (not in the paper).
+ * The FP64 kernels convert on the 32-bit integer pipe instead of with the
+ * hardware conversion instructions, which share the narrow FP64 pipe; this
+ * entry point compares both ways against the hardware on n seeded bit
+ * patterns (SplitMix64 of seed + i; three quarters of them with exponents
+ * at the edges of the FP32 range and fractions at the rounding boundary).
+ *   d_scratch:  DEVICE uint64 [2], overwritten.
+ *   mismatches: HOST uint64 [2] out: FP64->FP32 and FP32->FP64 patterns
+ *               whose bits differ from the hardware result (NaN = NaN).
+ * Synchronises the stream.  Errors: SM_EINVAL (n < 0, null pointer),
+ * SM_ECUDA. */
+int sm_check_conversions(long long n, unsigned long long seed, unsigned long long *d_scratch,
+                         unsigned long long *mismatches, void *stream);
 
 /* Human-readable reason of the last error on this context. */
 const char *sm_last_error(const sm_ctx *ctx);

@@ -61,7 +61,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs", "sm_set_pdl",
            "sm_set_persistent", "sm_persist_barrier_selftest",
-           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc",
+           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc", "sm_check_conversions",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
            "sm_batch_set_graphs", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
@@ -115,6 +115,7 @@ def load():
         "sm_persist_barrier_selftest": [P],
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
+        "sm_check_conversions": [C.c_longlong, C.c_ulonglong, P, P, P],
         "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
         "sm_batch_destroy": [P],
         "sm_batch_arena_size": [P, C.POINTER(C.c_size_t)],
@@ -151,6 +152,21 @@ def load():
 
 def _hp(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def check_conversions(n: int, seed: int = 0x5EED):
+    """Mismatches (FP64->FP32, FP32->FP64) of the library's integer-pipe
+    conversions against the hardware ones on n seeded bit patterns."""
+    import torch
+    lib = load()
+    scratch = torch.zeros(2, dtype=torch.int64, device="cuda")
+    out = np.zeros(2, np.uint64)
+    stream = torch.cuda.current_stream()
+    rc = lib.sm_check_conversions(int(n), int(seed), C.c_void_p(scratch.data_ptr()), _hp(out),
+                                  C.c_void_p(stream.cuda_stream))
+    if rc != SM_OK:
+        raise SmError(rc, "sm_check_conversions failed")
+    return int(out[0]), int(out[1])
 
 
 class Solver:
@@ -409,10 +425,11 @@ class Batch:
         phi, rhs = C.c_void_p(), C.c_void_p()
         self.offsets = np.zeros(self.n, np.int64)
         self._ck(lib.sm_batch_ptrs(h, C.byref(phi), C.byref(rhs), _hp(self.offsets)))
-        total = int(np.sum(self.sides.astype(np.int64) ** 3))
-        self.cells = total
-        self.phi = self._view(phi.value, total)
-        self.rhs = self._view(rhs.value, total)
+        self.cells = int(np.sum(self.sides.astype(np.int64) ** 3))
+        # grids start on aligned offsets: the arrays span the last grid's end
+        length = int(self.offsets[-1] + int(self.sides[-1]) ** 3)
+        self.phi = self._view(phi.value, length)
+        self.rhs = self._view(rhs.value, length)
 
     def _ck(self, rc):
         if rc != SM_OK:

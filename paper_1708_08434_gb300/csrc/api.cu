@@ -144,6 +144,7 @@ extern "C" int sm_create(sm_ctx **out, const sm_config *cfg, const sm_domain *do
     ctx->bc.type[f] = dom->bc_type[f];
     ctx->bc.val[f] = dom->bc_val[f];
   }
+  bc_finish(ctx->bc);
   for (int l = 0; l < MAXL; ++l) {
     double h = dom->length / (NC * (double)(1 << l));
     ctx->lh.h[l] = h;
@@ -540,3 +541,59 @@ extern "C" int sm_set_table(sm_ctx *ctx, int n, double e_max, const double *mu, 
   ctx->tab_emax = e_max;
   return SM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// check of the integer-pipe FP64 <-> FP32 conversions against the hardware
+// ---------------------------------------------------------------------------
+namespace {
+
+// SplitMix64 output function of counter x (Steele, Lea, Flood 2014)
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_check_cvt(long long n, unsigned long long seed, unsigned long long *__restrict__ count) {
+  unsigned long long bad_d = 0, bad_f = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long x = splitmix64(seed + (unsigned long long)i);
+    const int mode = (int)(i & 3);
+    if (mode) {  // exponent near the binary32 range, then fraction tails at the rounding boundary
+      const unsigned long long ex = 1023ull - 130ull + (x >> 55) % 261ull;
+      x = (x & 0x800fffffffffffffull) | (ex << 52);
+      if (mode == 2) x = (x & ~0x1fffffffull) | 0x10000000ull;
+      if (mode == 3) {
+        const unsigned long long tails[6] = {0x0fffffffull, 0x10000001ull, 0x1fffffffull, 0ull, 1ull, 0x10000000ull};
+        x = (x & ~0x1fffffffull) | tails[(x >> 40) % 6];
+        if ((x >> 45) & 1) x |= 0x000fffffe0000000ull;  // all kept fraction bits set: carry into the exponent
+      }
+    }
+    const double d = __longlong_as_double((long long)x);
+    const float a = cvt_f64_f32_rn(d), b = __double2float_rn(d);
+    if (__float_as_uint(a) != __float_as_uint(b) && !(isnan(a) && isnan(b))) ++bad_d;
+    const float f = __uint_as_float((unsigned)(x >> 32) ^ (unsigned)x);
+    const double c = cvt_f32_f64(f), e = (double)f;
+    if (__double_as_longlong(c) != __double_as_longlong(e) && !(isnan(c) && isnan(e))) ++bad_f;
+  }
+  if (bad_d) atomicAdd(count, bad_d);
+  if (bad_f) atomicAdd(count + 1, bad_f);
+}
+
+}  // namespace
+
+extern "C" int sm_check_conversions(long long n, unsigned long long seed, unsigned long long *d_scratch,
+                                    unsigned long long *mismatches, void *stream) {
+  if (n < 0 || !d_scratch || !mismatches) return SM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_scratch, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return SM_ECUDA;
+  if (n > 0) k_check_cvt<<<1216, 256, 0, st>>>(n, seed, d_scratch);
+  if (cudaGetLastError() != cudaSuccess) return SM_ECUDA;
+  if (cudaMemcpyAsync(mismatches, d_scratch, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SM_ECUDA;
+  return SM_OK;
+}
+

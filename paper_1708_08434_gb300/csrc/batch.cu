@@ -4,12 +4,14 @@
 //
 // Every solve s has levels k = 0 (finest, N_s cells per side) .. K_s, with
 // N halved while it is even and larger than 8; the coarsest grid (at most
-// 16 per side) is solved exactly in FP64 by separable eigenbases.  All
-// solves' tiles of one level index are one work list, processed by one
-// grid-stride ("persistent") launch per level and phase.  The cycle is a
-// correction-scheme V(nu1,nu2) in FP32 on the error equation inside a
-// per-solve FP64 defect-correction loop (residual and accumulation in
-// FP64); converged solves are masked out.  A whole batched solve is one
+// 16 per side) is solved exactly in FP64 by separable eigenbases.  The work
+// of all solves at one level index is one work list, processed by one
+// grid-stride ("persistent") launch per level and phase: z-marching columns
+// for the smoother (a whole red-black sweep per launch), the prolongation
+// and the FP64 outer residual, small 3-D tiles for the restriction.  The
+// cycle is a correction-scheme V(nu1,nu2) in FP32 on the error equation
+// inside a per-solve FP64 defect-correction loop (residual and
+// accumulation in FP64); converged solves are masked out.  A whole batched solve is one
 // CUDA graph with a device-side loop; tile shape and grid size are chosen
 // by timing candidate configurations (sm_batch_tune).
 #include <math.h>
@@ -52,7 +54,7 @@ __device__ __forceinline__ long long gidx(int N, int x, int y, int z) {
 // physical-boundary ghost of `in` across face f (homogeneous for errors)
 template <typename T>
 __device__ __forceinline__ T wall(const Bc &bc, int f, T in, int homog) {
-  if (bc.type[f]) return (homog ? T(0) : T(2.0 * bc.val[f])) - in;
+  if (bc.type[f]) return (homog ? T(0) : bc_g2<T>(bc, f)) - in;
   return in;
 }
 
@@ -79,23 +81,213 @@ __device__ __forceinline__ bool tile_cell(const int4 &T, TileShape sh, int N, in
   return x < N && y < N && z < N;
 }
 
-// red-black Gauss-Seidel colour pass of level k on the error e
-__global__ void __launch_bounds__(TILE_CELLS) k_bt_smooth(const int4 *__restrict__ tiles, int ntiles, int k,
-                                                          int color, const BSolve *__restrict__ tab,
-                                                          const unsigned char *__restrict__ active,
-                                                          float *__restrict__ e, const float *__restrict__ f,
-                                                          Bc bc, TileShape sh) {
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    int4 T = tiles[it];
-    if (!active[T.x]) continue;
-    int N = tab[T.x].N[k];
-    int x, y, z;
-    if (!tile_cell(T, sh, N, x, y, z) || ((x + y + z) & 1) != color) continue;
-    float *ev = e + tab[T.x].off[k];
-    long long i = gidx(N, x, y, z);
-    float c = ev[i];
-    float s = sum6(ev, N, x, y, z, c, bc, 1);
-    ev[i] = (s - tab[T.x].h2f[k] * f[tab[T.x].off[k] + i]) * (1.0f / 6.0f);
+// ---- z-marching columns -------------------------------------------------
+//
+// The smoother and the outer residual walk columns of CX x CY cells in x, y
+// through the whole grid in z: one block of CT threads per column, thread t
+// owning x = x0 + t % 32 and the two rows y = y0 + 2 (t / 32) + {0, 1}.
+// Planes of the column, with an x/y halo, are staged in a ring of RING
+// shared-memory slots by asynchronous copies (cp.async) issued several
+// planes ahead.  Staged rows start 16 bytes before x0 so that rows of grids
+// with N % 4 == 0 (FP32) or N even (FP64) are copied in aligned 16-byte
+// chunks; other grids are copied element by element.  Halo cells outside
+// the grid are zero-filled by the copy (source size 0), so in-plane
+// neighbour sums need no tests; the wall ghosts enter through one
+// coefficient per cell: the homogeneous ghost is +c (Neumann) or -c
+// (Dirichlet), the inhomogeneous one c or 2g - c.
+
+constexpr int CX = 32, CY = 16, CT = 256;
+constexpr int RW = CX + 8;                    // FP32 staged row: x0-4 .. x0+35
+constexpr int ER = CY + 4, FR = CY + 2;       // staged rows: error halo 2, rhs halo 1
+constexpr int EPL = RW * ER, FPL = RW * FR;   // floats per staged plane
+constexpr int RWD = CX + 4;                   // FP64 staged row: x0-2 .. x0+33
+constexpr int DPL = RWD * FR;                 // doubles per staged potential plane
+constexpr int RING = 8;                       // staged planes per block (power of 2)
+constexpr int NRING = 2 * (CX + 2) + 2 * CY;  // cells of the one-cell ring around a column
+constexpr size_t SWEEP_SMEM = sizeof(float) * RING * (EPL + FPL);
+constexpr size_t SWEEP_SMEM_PHI = SWEEP_SMEM + sizeof(double) * RING * CX * CY;
+constexpr size_t OUTER_SMEM = sizeof(double) * RING * DPL;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// asynchronous copy of B bytes global -> shared; zero fill when !valid
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool valid) {
+  if (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B),
+                 "r"(valid ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// coefficient of c in the sum of the homogeneous wall ghosts of cell
+// coordinate v along axis a (faces 2a, 2a+1)
+__device__ __forceinline__ float wall_w(const Bc &bc, int a, int v, int N) {
+  float w = 0.f;
+  if (v == 0) w += bc.type[2 * a] ? -1.f : 1.f;
+  if (v == N - 1) w += bc.type[2 * a + 1] ? -1.f : 1.f;
+  return w;
+}
+
+// One full red-black Gauss-Seidel sweep (colour 0, then colour 1) of level
+// k on the error, column by column, from e_in into e_out (two buffers, so
+// that every column reads the sweep's starting values: a column's halo is
+// never a value another column has already swept).  Step p updates colour 0
+// on plane p over the column and the one-cell ring around it (the ring
+// repeats what the neighbouring columns compute, from the same values),
+// then colour 1 on plane p-1 over the column, which by then has all its
+// colour-0 neighbours, and stores plane p-1.  The updates use the values of
+// two separate colour passes over the level.  With phi != nullptr (level 0,
+// last sweep of a cycle) the swept error is not stored but added to the
+// FP64 potential: phi += (double)e.
+// Ring use at step p: planes p-2 .. p+1 are read, p+2 .. p+4 are in flight,
+// and plane p+5 is issued into the slot of plane p-3 (last read at step p-1).
+__global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, int ncols, int k,
+                                                 const BSolve *__restrict__ tab,
+                                                 const unsigned char *__restrict__ active,
+                                                 const float *__restrict__ e_in, float *__restrict__ e_out,
+                                                 const float *__restrict__ f, Bc bc, double *__restrict__ phi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float(*se)[EPL] = reinterpret_cast<float(*)[EPL]>(smem_raw);
+  float(*sf)[FPL] = reinterpret_cast<float(*)[FPL]>(smem_raw + sizeof(float) * RING * EPL);
+  double(*sph)[CX * CY] = reinterpret_cast<double(*)[CX * CY]>(smem_raw + SWEEP_SMEM);
+  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    const int4 C = cols[it];
+    if (!active[C.x]) continue;  // uniform per block
+    const int N = tab[C.x].N[k];
+    const long long off = tab[C.x].off[k], NN = (long long)N * N;
+    const float h2 = tab[C.x].h2f[k];
+    const int x0 = C.y * CX, y0 = C.z * CY;
+    const float *ev = e_in + off, *fv = f + off;
+    float *eo = e_out + off;
+    double *pv = phi ? phi + tab[C.x].off64 : nullptr;
+    const bool vec = (N & 3) == 0;
+    // copies of plane z (if it exists) as one commit group
+    auto issue = [&](int z) {
+      if (z < N) {
+        const int sl = z & (RING - 1);
+        const float *ez = ev + z * NN, *fz = fv + z * NN;
+        if (vec) {
+          for (int i = t; i < (ER + FR) * (RW / 4); i += CT) {
+            const bool ise = i < ER * (RW / 4);
+            const int j = ise ? i : i - ER * (RW / 4);
+            const int r = j / (RW / 4), c4 = 4 * (j % (RW / 4));
+            const int y = y0 - (ise ? 2 : 1) + r, x = x0 - 4 + c4;
+            const bool ok = y >= 0 && y < N && x >= 0 && x < N;
+            const float *src = ise ? ez : fz;
+            float *dst = ise ? &se[sl][r * RW + c4] : &sf[sl][r * RW + c4];
+            cp_async<16>(dst, ok ? src + y * N + x : src, ok);
+          }
+        } else {
+          for (int i = t; i < (ER + FR) * RW; i += CT) {
+            const bool ise = i < ER * RW;
+            const int j = ise ? i : i - ER * RW;
+            const int r = j / RW, c = j % RW;
+            const int y = y0 - (ise ? 2 : 1) + r, x = x0 - 4 + c;
+            const bool ok = y >= 0 && y < N && x >= 0 && x < N;
+            const float *src = ise ? ez : fz;
+            float *dst = ise ? &se[sl][j] : &sf[sl][j];
+            cp_async<4>(dst, ok ? src + y * N + x : src, ok);
+          }
+        }
+        if (pv) {  // level 0: N even, rows of the column in 16-byte pairs
+          const int r = t / (CX / 2), x = x0 + 2 * (t % (CX / 2)), y = y0 + r;
+          const bool ok = x < N && y < N;
+          cp_async<16>(&sph[sl][r * CX + 2 * (t % (CX / 2))], ok ? pv + z * NN + y * N + x : pv, ok);
+        }
+      }
+      cp_commit();
+    };
+    // Gauss-Seidel update of the staged cell at e-plane index q (rhs index
+    // qf) of plane z, wall coefficient w (in-plane part)
+    auto update = [&](int z, int q, int qf, float w) {
+      float *pz = se[z & (RING - 1)];
+      const float c = pz[q];
+      float s = pz[q - 1] + pz[q + 1];
+      s += pz[q - RW];
+      s += pz[q + RW];
+      if (z > 0) s += se[(z - 1) & (RING - 1)][q];
+      if (z < N - 1) s += se[(z + 1) & (RING - 1)][q];
+      s = fmaf(w + wall_w(bc, 2, z, N), c, s);
+      pz[q] = (s - h2 * sf[z & (RING - 1)][qf]) * (1.0f / 6.0f);
+    };
+    // this thread's two column cells (rows ya, ya+1) and its ring cell
+    const int x = x0 + tx, ya = y0 + ty2;
+    const bool in = x < N && ya < N;  // N even, ya even: both rows or neither
+    const int q0 = (ty2 + 2) * RW + tx + 4, qf0 = (ty2 + 1) * RW + tx + 4;
+    const float wx = wall_w(bc, 0, x, N);
+    const float w0 = wx + wall_w(bc, 1, ya, N), w1 = wx + wall_w(bc, 1, ya + 1, N);
+    int rx = -1, ry = -1;
+    if (t < NRING) {
+      if (t < CX + 2) rx = x0 - 1 + t, ry = y0 - 1;
+      else if (t < 2 * (CX + 2)) rx = x0 - 1 + t - (CX + 2), ry = y0 + CY;
+      else if (t < 2 * (CX + 2) + CY) rx = x0 - 1, ry = y0 + t - 2 * (CX + 2);
+      else rx = x0 + CX, ry = y0 + t - 2 * (CX + 2) - CY;
+    }
+    const bool rin = rx >= 0 && rx < N && ry >= 0 && ry < N;
+    const int rq = (ry - y0 + 2) * RW + (rx - x0 + 4), rqf = (ry - y0 + 1) * RW + (rx - x0 + 4);
+    const float rw = rin ? wall_w(bc, 0, rx, N) + wall_w(bc, 1, ry, N) : 0.f;
+    __syncthreads();  // the previous column's planes are no longer read
+#pragma unroll
+    for (int z = 0; z < RING - 3; ++z) issue(z);  // planes 0 .. RING-4
+    for (int p = 0; p <= N; ++p) {
+      cp_wait<RING - 5>();  // this thread's copies of planes <= p+1 have landed
+      __syncthreads();      // everyone's have; step p-1's reads of plane p-3 are done
+      issue(p + RING - 3);
+      if (p < N) {  // colour 0 on plane p: one column cell per thread, and the ring
+        if (in) {
+          const int o = (x + ya + p) & 1;  // row offset of the colour-0 cell
+          update(p, q0 + o * RW, qf0 + o * RW, o ? w1 : w0);
+        }
+        if (rin && !((rx + ry + p) & 1)) update(p, rq, rqf, rw);
+      }
+      __syncthreads();
+      if (p >= 1 && in) {  // colour 1 on plane p-1, then store both cells
+        const int z = p - 1, o = ((x + ya + z) & 1) ^ 1;
+        update(z, q0 + o * RW, qf0 + o * RW, o ? w1 : w0);
+        const float v0 = se[z & (RING - 1)][q0], v1 = se[z & (RING - 1)][q0 + RW];
+        const long long g = z * NN + (long long)ya * N + x;
+        if (pv) {
+          const double *ph = sph[z & (RING - 1)];
+          pv[g] = ph[ty2 * CX + tx] + cvt_f32_f64(v0);
+          pv[g + N] = ph[(ty2 + 1) * CX + tx] + cvt_f32_f64(v1);
+        } else {
+          eo[g] = v0;
+          eo[g + N] = v1;
+        }
+      }
+    }
+    cp_wait<0>();
+  }
+}
+
+// e_out = e_in on the listed columns of level k (odd sweep counts)
+__global__ void __launch_bounds__(CT) k_bt_copy(const int4 *__restrict__ cols, int ncols, int k,
+                                                const BSolve *__restrict__ tab,
+                                                const unsigned char *__restrict__ active,
+                                                const float *__restrict__ e_in, float *__restrict__ e_out) {
+  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    const int4 C = cols[it];
+    if (!active[C.x]) continue;
+    const int N = tab[C.x].N[k];
+    const long long off = tab[C.x].off[k];
+    const int x = C.y * CX + tx;
+    for (int r = 0; r < 2; ++r) {
+      const int y = C.z * CY + ty2 + r;
+      if (x >= N || y >= N) continue;
+      for (int z = 0; z < N; ++z) e_out[off + gidx(N, x, y, z)] = e_in[off + gidx(N, x, y, z)];
+    }
   }
 }
 
@@ -129,39 +321,99 @@ __global__ void __launch_bounds__(TILE_CELLS) k_bt_restrict(const int4 *__restri
   }
 }
 
-// e_k += (c + c_sx + c_sy + c_sz)/4 from level k+1 (homogeneous walls)
-__global__ void __launch_bounds__(TILE_CELLS) k_bt_prolong(const int4 *__restrict__ tiles, int ntiles, int k,
-                                                           const BSolve *__restrict__ tab,
-                                                           const unsigned char *__restrict__ active,
-                                                           float *__restrict__ e, Bc bc, TileShape sh) {
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    int4 T = tiles[it];
-    if (!active[T.x]) continue;
-    const BSolve &S = tab[T.x];
-    int Nf = S.N[k], Nc = S.N[k + 1];
-    int x, y, z;
-    if (!tile_cell(T, sh, Nf, x, y, z)) continue;
+// e_k += (c + c_sx + c_sy + c_sz)/4 from level k+1 (homogeneous walls), on
+// the sweep columns of level k: one coarse plane Z (fine planes 2Z, 2Z+1)
+// per step.  The coarse planes Z-1 .. Z+1 of the column's coarse footprint
+// (with a one-cell halo, zero outside the grid) sit in a ring of four
+// shared-memory slots, plane Z+2 is loaded into registers during step Z;
+// the fine values of the next step are loaded one step ahead.  A coarse
+// neighbour outside the grid is the homogeneous wall ghost +c (Neumann) or
+// -c (Dirichlet), added through one coefficient per fine cell.
+constexpr int PX = CX / 2 + 2, PY = CY / 2 + 2, PPL = PX * PY;  // staged coarse plane
+__global__ void __launch_bounds__(CT) k_bt_prolong(const int4 *__restrict__ cols, int ncols, int k,
+                                                   const BSolve *__restrict__ tab,
+                                                   const unsigned char *__restrict__ active,
+                                                   float *__restrict__ e, Bc bc) {
+  __shared__ float sc[4][PPL];
+  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    const int4 C = cols[it];
+    if (!active[C.x]) continue;  // uniform per block
+    const BSolve &S = tab[C.x];
+    const int N = S.N[k], Nc = S.N[k + 1];  // N = 2 Nc
+    const long long NN = (long long)N * N, NNc = (long long)Nc * Nc;
+    float *ef = e + S.off[k];
     const float *ec = e + S.off[k + 1];
-    int C[3] = {x >> 1, y >> 1, z >> 1}, g[3] = {x, y, z};
-    float c = ec[gidx(Nc, C[0], C[1], C[2])];
-    float sum = c;
-    for (int a = 0; a < 3; ++a) {
-      int s = (g[a] & 1) ? 1 : -1;
-      int q[3] = {C[0], C[1], C[2]};
-      q[a] += s;
-      if (q[a] < 0 || q[a] >= Nc) sum += wall(bc, 2 * a + (s > 0), c, 1);
-      else sum += ec[gidx(Nc, q[0], q[1], q[2])];
+    const int x0 = C.y * CX, y0 = C.z * CY, X0 = x0 / 2 - 1, Y0 = y0 / 2 - 1;
+    const int x = x0 + tx, ya = y0 + ty2;
+    const bool in = x < N && ya < N;  // N even, ya even: both rows or neither
+    // this thread's coarse cell (both rows share it) and neighbour offsets
+    const int Xi = x / 2 - X0, Yi = ya / 2 - Y0, sx = (x & 1) ? 1 : -1;
+    const int qc = Yi * PX + Xi;
+    // wall coefficients: a neighbour outside the coarse grid on the fine cell's side
+    auto ww = [&](int face) { return bc.type[face] ? -1.f : 1.f; };
+    float wxy0 = 0.f, wxy1 = 0.f;  // row ya looks to Y-1, row ya+1 to Y+1
+    if (sx < 0 && x / 2 == 0) wxy0 += ww(0), wxy1 += ww(0);
+    if (sx > 0 && x / 2 == Nc - 1) wxy0 += ww(1), wxy1 += ww(1);
+    if (ya / 2 == 0) wxy0 += ww(2);
+    if (ya / 2 == Nc - 1) wxy1 += ww(3);
+    // coarse plane Z of the footprint (zero outside the grid): one value per thread
+    auto load_c = [&](int Z) {
+      float v = 0.f;
+      if (t < PPL && Z < Nc) {
+        const int X = X0 + t % PX, Y = Y0 + t / PX;
+        if (X >= 0 && X < Nc && Y >= 0 && Y < Nc) v = ec[Z * NNc + (long long)Y * Nc + X];
+      }
+      return v;
+    };
+    const long long row0 = (long long)ya * N + x;
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;  // fine values of planes 2Z, 2Z+1 (rows ya, ya+1)
+    if (in) f0 = ef[row0], f1 = ef[row0 + N], f2 = ef[NN + row0], f3 = ef[NN + row0 + N];
+    __syncthreads();  // the previous column's coarse planes are no longer read
+    if (t < PPL) {
+      sc[0][t] = load_c(0);
+      sc[1][t] = load_c(1);
     }
-    e[S.off[k] + gidx(Nf, x, y, z)] += 0.25f * sum;
+    float nxt = load_c(2);
+    __syncthreads();
+    for (int Z = 0; Z < Nc; ++Z) {
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;  // the next step's fine values
+      if (in && Z + 1 < Nc) {
+        const long long b = (long long)(2 * Z + 2) * NN + row0;
+        g0 = ef[b], g1 = ef[b + N], g2 = ef[b + NN], g3 = ef[b + NN + N];
+      }
+      if (in) {
+        const float *cz = sc[Z & 3];
+        const float c = cz[qc], cxn = cz[qc + sx];
+        const float c_lo = (Z > 0) ? sc[(Z - 1) & 3][qc] : 0.f;  // fine plane 2Z looks to Z-1
+        const float c_hi = (Z + 1 < Nc) ? sc[(Z + 1) & 3][qc] : 0.f;
+        const float wz_lo = (Z == 0) ? ww(4) : 0.f, wz_hi = (Z == Nc - 1) ? ww(5) : 0.f;
+        const float cym = cz[qc - PX], cyp = cz[qc + PX];
+        const long long b = (long long)(2 * Z) * NN + row0;
+        // (c + c_x + c_y + c_z) with the wall ghosts, for the four fine cells
+        ef[b] = f0 + 0.25f * fmaf(wxy0 + wz_lo, c, ((c + cxn) + cym) + c_lo);
+        ef[b + N] = f1 + 0.25f * fmaf(wxy1 + wz_lo, c, ((c + cxn) + cyp) + c_lo);
+        ef[b + NN] = f2 + 0.25f * fmaf(wxy0 + wz_hi, c, ((c + cxn) + cym) + c_hi);
+        ef[b + NN + N] = f3 + 0.25f * fmaf(wxy1 + wz_hi, c, ((c + cxn) + cyp) + c_hi);
+      }
+      __syncthreads();  // plane Z-2's slot is free
+      if (t < PPL) sc[(Z + 2) & 3][t] = nxt;
+      nxt = load_c(Z + 3);
+      __syncthreads();
+      f0 = g0, f1 = g1, f2 = g2, f3 = g3;
+    }
   }
 }
 
 // exact FP64 solve of the error equation on the coarsest grid of each
-// listed solve (one block per solve): separable eigenbases per axis
+// listed solve (one block per solve): separable eigenbases per axis.  When
+// the coarsest grid is the finest (k = 0) the correction, rounded to FP32
+// like every other correction, is added to the FP64 potential directly.
 __global__ void __launch_bounds__(512) k_bt_coarse(const int *__restrict__ solves, int k,
                                                    const BSolve *__restrict__ tab,
                                                    const unsigned char *__restrict__ active,
-                                                   float *__restrict__ e, const float *__restrict__ f, Bc bc) {
+                                                   float *__restrict__ e, const float *__restrict__ f, Bc bc,
+                                                   double *__restrict__ phi) {
   extern __shared__ double sm[];
   int s = solves[blockIdx.x];
   if (!active[s]) return;
@@ -213,66 +465,137 @@ __global__ void __launch_bounds__(512) k_bt_coarse(const int *__restrict__ solve
     __syncthreads();
   }
   // passes alternate x -> y -> x ...: the sixth ends in x
-  float *ev = e + S.off[k];
-  for (int c = t; c < n3; c += blockDim.x) ev[c] = (float)x[c];
-}
-
-// FP64 outer residual on the finest grids: r = f - L phi (or of phi = 0
-// when zero_phi), its max norm per solve, FP32 copy as the error
-// equation's rhs and a zero initial error
-__global__ void __launch_bounds__(TILE_CELLS) k_bt_outer(const int4 *__restrict__ tiles, int ntiles,
-                                                         const BSolve *__restrict__ tab,
-                                                         const unsigned char *__restrict__ active,
-                                                         const double *__restrict__ phi,
-                                                         const double *__restrict__ f64, float *__restrict__ f32,
-                                                         float *__restrict__ e32, Bc bc, TileShape sh,
-                                                         int zero_phi, unsigned long long *__restrict__ num) {
-  __shared__ double red[16];
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    int4 T = tiles[it];
-    if (!active[T.x]) continue;  // uniform per block
-    const BSolve &S = tab[T.x];
-    int N = S.N[0];
-    int x, y, z;
-    double r = 0.0;
-    if (tile_cell(T, sh, N, x, y, z)) {
-      long long i = gidx(N, x, y, z);
-      const double *p = phi + S.off64;
-      double c = zero_phi ? 0.0 : p[i];
-      double s;
-      if (zero_phi) {
-        s = 0.0;
-        int g[3] = {x, y, z};
-        for (int fc = 0; fc < 6; ++fc) {
-          int q = g[fc >> 1] + ((fc & 1) ? 1 : -1);
-          if (q < 0 || q >= N) s += wall(bc, fc, 0.0, 0);
-        }
-      } else {
-        s = sum6(p, N, x, y, z, c, bc, 0);
-      }
-      r = f64[S.off64 + i] - (s - 6.0 * c) * S.inv_h2;
-      f32[S.off[0] + i] = (float)r;
-      e32[S.off[0] + i] = 0.0f;
-    }
-    block_max_to(num + T.x, fabs(r), red);
-    __syncthreads();
+  if (k == 0) {
+    double *pv = phi + S.off64;
+    for (int c = t; c < n3; c += blockDim.x) pv[c] += (double)(float)x[c];
+  } else {
+    float *ev = e + S.off[k];
+    for (int c = t; c < n3; c += blockDim.x) ev[c] = (float)x[c];
   }
 }
 
-// phi += e on the finest grids (FP64 accumulation of the FP32 correction)
-__global__ void __launch_bounds__(TILE_CELLS) k_bt_add(const int4 *__restrict__ tiles, int ntiles,
-                                                       const BSolve *__restrict__ tab,
-                                                       const unsigned char *__restrict__ active,
-                                                       double *__restrict__ phi, const float *__restrict__ e32,
-                                                       TileShape sh) {
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    int4 T = tiles[it];
-    if (!active[T.x]) continue;
-    const BSolve &S = tab[T.x];
-    int x, y, z;
-    if (!tile_cell(T, sh, S.N[0], x, y, z)) continue;
-    long long i = gidx(S.N[0], x, y, z);
-    phi[S.off64 + i] += (double)e32[S.off[0] + i];
+// FP64 outer residual on the finest grids, column by column:
+// r = f - L phi (or of phi = 0 when zero_phi), its max norm per solve, the
+// FP32 copy of r as the error equation's rhs and a zero initial error.
+// Planes of phi (one-cell halo) are staged by asynchronous copies: at step
+// p planes p-1 .. p+1 are read, p+2 .. p+4 are in flight and plane p+5 is
+// issued into the slot of plane p-3; f of plane p+1 is loaded into
+// registers during step p.  phi is only read here.  Per cell: the six
+// neighbours summed pairwise (zero-filled halo outside the grid), the wall
+// ghosts (boundary cells only), two fused multiply-adds; the max norm is
+// taken on the bit patterns of |r|.
+__global__ void __launch_bounds__(CT) k_bt_outer(const int4 *__restrict__ cols, int ncols,
+                                                 const BSolve *__restrict__ tab,
+                                                 const unsigned char *__restrict__ active,
+                                                 const double *__restrict__ phi, const double *__restrict__ f64,
+                                                 float *__restrict__ f32, float *__restrict__ e32, Bc bc,
+                                                 int zero_phi, unsigned long long *__restrict__ num) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double(*sp)[DPL] = reinterpret_cast<double(*)[DPL]>(smem_raw);
+  __shared__ unsigned long long red[CT / 32];
+  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    const int4 C = cols[it];
+    if (!active[C.x]) continue;  // uniform per block
+    const BSolve &S = tab[C.x];
+    const int N = S.N[0];
+    const long long o64 = S.off64, o32 = S.off[0], NN = (long long)N * N;
+    const double inv_h2 = S.inv_h2;
+    const int x0 = C.y * CX, y0 = C.z * CY;
+    const double *pv = phi + o64, *fv = f64 + o64;
+    const bool vec = (N & 1) == 0;
+    const int x = x0 + tx, ya = y0 + ty2;
+    const bool in0 = x < N && ya < N, in1 = x < N && ya + 1 < N;
+    auto issue = [&](int z) {
+      if (z < N && !zero_phi) {
+        const int sl = z & (RING - 1);
+        const double *pz = pv + z * NN;
+        if (vec) {
+          for (int i = t; i < FR * (RWD / 2); i += CT) {
+            const int r = i / (RWD / 2), c2 = 2 * (i % (RWD / 2)), y = y0 - 1 + r, xx = x0 - 2 + c2;
+            const bool ok = y >= 0 && y < N && xx >= 0 && xx < N;
+            cp_async<16>(&sp[sl][r * RWD + c2], ok ? pz + y * N + xx : pz, ok);
+          }
+        } else {
+          for (int i = t; i < FR * RWD; i += CT) {
+            const int y = y0 - 1 + i / RWD, xx = x0 - 2 + i % RWD;
+            const bool ok = y >= 0 && y < N && xx >= 0 && xx < N;
+            cp_async<8>(&sp[sl][i], ok ? pz + y * N + xx : pz, ok);
+          }
+        }
+      }
+      cp_commit();
+    };
+    // wall terms per cell: sum of ghosts = wd * c + G (Dirichlet: 2g - c; Neumann: c)
+    auto wall_terms = [&](int a, int v, double &wd, double &G) {
+      if (v == 0) {
+        if (bc.type[2 * a]) wd -= 1.0, G += bc.g2[2 * a];
+        else wd += 1.0;
+      }
+      if (v == N - 1) {
+        if (bc.type[2 * a + 1]) wd -= 1.0, G += bc.g2[2 * a + 1];
+        else wd += 1.0;
+      }
+    };
+    const long long row0 = (long long)ya * N + x;
+    double fc0 = in0 ? fv[row0] : 0.0, fc1 = in1 ? fv[row0 + N] : 0.0;  // f of plane p
+    unsigned long long m = 0;  // bit pattern of max |r|
+    __syncthreads();           // the previous column's planes are no longer read
+#pragma unroll
+    for (int z = 0; z < RING - 3; ++z) issue(z);
+    for (int p = 0; p < N; ++p) {
+      cp_wait<RING - 5>();
+      __syncthreads();
+      issue(p + RING - 3);
+      double fn0 = 0.0, fn1 = 0.0;  // f of plane p+1, in flight during this step
+      if (p + 1 < N) {
+        if (in0) fn0 = fv[(p + 1) * NN + row0];
+        if (in1) fn1 = fv[(p + 1) * NN + row0 + N];
+      }
+      const double *pz = sp[p & (RING - 1)];
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        const int y = ya + o;
+        if (!(o ? in1 : in0)) continue;
+        const int q = (ty2 + o + 1) * RWD + tx + 2;
+        double s = 0.0, c = 0.0;
+        if (!zero_phi) {
+          c = pz[q];
+          const double zm = p > 0 ? sp[(p - 1) & (RING - 1)][q] : 0.0;
+          const double zp = p < N - 1 ? sp[(p + 1) & (RING - 1)][q] : 0.0;
+          s = ((pz[q - 1] + pz[q + 1]) + (pz[q - RWD] + pz[q + RWD])) + (zm + zp);
+        }
+        if (x == 0 || x == N - 1 || y == 0 || y == N - 1 || p == 0 || p == N - 1) {
+          double wd = 0.0, G = 0.0;
+          wall_terms(0, x, wd, G);
+          wall_terms(1, y, wd, G);
+          wall_terms(2, p, wd, G);
+          s += fma(wd, c, G);
+        }
+        const double r = fma(-fma(-6.0, c, s), inv_h2, o ? fc1 : fc0);
+        const long long g = p * NN + row0 + o * N;
+        f32[o32 + g] = cvt_f64_f32_rn(r);
+        e32[o32 + g] = 0.0f;
+        const unsigned long long a = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+        m = a > m ? a : m;
+      }
+      fc0 = fn0;
+      fc1 = fn1;
+    }
+    cp_wait<0>();
+    // one max per column and solve
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if ((t & 31) == 0) red[t >> 5] = m;
+    __syncthreads();
+    if (t == 0) {
+      unsigned long long x2 = red[0];
+      for (int i = 1; i < CT / 32; ++i) x2 = red[i] > x2 ? red[i] : x2;
+      atomicMax(num + C.x, x2);
+    }
   }
 }
 
@@ -334,13 +657,14 @@ struct sm_batch {
   int nu1 = 2, nu2 = 2;
   std::vector<BSolve> solves;
   int kmax = 0;                     // deepest level index over all solves
-  long long pool = 0, cells64 = 0;  // FP32 pool cells, finest cells
-  size_t max_tiles = 0;             // capacity of the tile area (all lists)
+  long long pool = 0, cells64 = 0;  // FP32 pool length, finest cells
+  long long len64 = 0;              // FP64 array length (grids padded, see GRID_ALIGN)
+  size_t max_tiles = 0;             // capacity of the tile area (all lists, tiles and columns)
   // arena
   char *arena = nullptr;
   BSolve *d_tab = nullptr;
   double *phi = nullptr, *f64 = nullptr;
-  float *e32 = nullptr, *f32 = nullptr;
+  float *e32 = nullptr, *e32b = nullptr, *f32 = nullptr;  // error (two buffers), error-equation rhs
   int4 *d_tiles = nullptr;
   int *d_coarse = nullptr;
   unsigned long long *d_num = nullptr, *d_den = nullptr;
@@ -350,9 +674,10 @@ struct sm_batch {
   double *h_tolmax = nullptr;
   // current schedule
   int shape = 0, gmult = 4, sms = 148;
-  std::vector<size_t> smooth_off, smooth_cnt, restr_off, restr_cnt;  // per level index
+  std::vector<size_t> restr_off, restr_cnt;  // per level index: restriction tiles
   std::vector<size_t> coarse_off, coarse_cnt;
-  size_t fine_off = 0, fine_cnt = 0;  // level 0 of every solve (outer loop)
+  std::vector<size_t> scol_off, scol_cnt;  // per level index: sweep columns
+  size_t fine_off = 0, fine_cnt = 0;       // columns of level 0 of every solve (outer loop)
   cudaGraphExec_t exec = nullptr;
   bool graphs = true;
   long long launches_prefix = 0, launches_body = 0, n_launch = 0;
@@ -377,6 +702,15 @@ static size_t tiles_of(int N, int s) {
   return (size_t)((N + sh[0] - 1) / sh[0]) * ((N + sh[1] - 1) / sh[1]) * ((N + sh[2] - 1) / sh[2]);
 }
 
+// Every grid starts at a multiple of GRID_ALIGN elements in its pool (FP32
+// and FP64), whatever the sizes of the grids before it (coarsest grids can
+// have odd sides), so that rows of grids with N % 4 == 0 (FP32) or N even
+// (FP64) start on 16-byte boundaries for the 16-byte staging copies.
+constexpr long long GRID_ALIGN = 32;
+static long long pad_grid(long long n) { return (n + GRID_ALIGN - 1) / GRID_ALIGN * GRID_ALIGN; }
+
+static size_t cols_of(int N) { return (size_t)((N + CX - 1) / CX) * ((N + CY - 1) / CY); }
+
 extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_per_side, double length,
                                const int *bc_type, const double *bc_val, int nu1, int nu2, void *stream) {
   if (!out || !cells_per_side || !bc_type || !bc_val || n_solves < 1 || !(length > 0.0) || nu1 < 1 || nu2 < 1)
@@ -389,7 +723,7 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
   }
   if (!dir) return SM_EINVAL;
   std::vector<BSolve> S(n_solves);
-  long long pool = 0, c64 = 0;
+  long long pool = 0, c64 = 0, len64 = 0;
   int kmax = 0;
   for (int s = 0; s < n_solves; ++s) {
     int N = cells_per_side[s];
@@ -411,8 +745,9 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
     double h = length / N;
     q.h2 = h * h;
     q.inv_h2 = 1.0 / (h * h);
-    q.off64 = c64;
+    q.off64 = len64;
     c64 += (long long)N * N * N;
+    len64 += pad_grid((long long)N * N * N);
     kmax = std::max(kmax, k - 1);
   }
   // FP32 pool ordered by level index, then solve
@@ -420,7 +755,7 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
     for (int s = 0; s < n_solves; ++s)
       if (k < S[s].nlev) {
         S[s].off[k] = pool;
-        pool += (long long)S[s].N[k] * S[s].N[k] * S[s].N[k];
+        pool += pad_grid((long long)S[s].N[k] * S[s].N[k] * S[s].N[k]);
       }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -434,6 +769,7 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
     b->bc.type[f] = bc_type[f];
     b->bc.val[f] = bc_val[f];
   }
+  bc_finish(b->bc);
   b->nu1 = nu1;
   b->nu2 = nu2;
   b->stream = (cudaStream_t)stream;
@@ -441,13 +777,16 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
   b->kmax = kmax;
   b->pool = pool;
   b->cells64 = c64;
+  b->len64 = len64;
   size_t mt = 0;
   for (int sh = 0; sh < NSHAPES; ++sh) {
     size_t t = 0;
     for (auto &q : S)
-      for (int k = 0; k < q.nlev; ++k) t += (k == 0 ? 3 : 2) * tiles_of(q.N[k], sh);  // smooth, restrict, fine
+      for (int k = 0; k < q.nlev; ++k) t += tiles_of(q.N[k], sh);  // restriction
     mt = std::max(mt, t);
   }
+  for (auto &q : S)
+    for (int k = 0; k < q.nlev; ++k) mt += cols_of(q.N[k]) * (k == 0 ? 2 : 1);  // sweep, outer
   b->max_tiles = mt;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -461,7 +800,7 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
 }
 
 struct BLayout {
-  size_t tab, phi, f64, e32, f32, tiles, coarse, num, den, rel, tolmax, cycles, any, active, total;
+  size_t tab, phi, f64, e32, e32b, f32, tiles, coarse, num, den, rel, tolmax, cycles, any, active, total;
 };
 
 static BLayout blayout(const sm_batch *b) {
@@ -473,9 +812,10 @@ static BLayout blayout(const sm_batch *b) {
     return at;
   };
   L.tab = take(sizeof(BSolve) * b->n);
-  L.phi = take(sizeof(double) * b->cells64);
-  L.f64 = take(sizeof(double) * b->cells64);
+  L.phi = take(sizeof(double) * b->len64);
+  L.f64 = take(sizeof(double) * b->len64);
   L.e32 = take(sizeof(float) * b->pool);
+  L.e32b = take(sizeof(float) * b->pool);
   L.f32 = take(sizeof(float) * b->pool);
   L.tiles = take(sizeof(int4) * (b->max_tiles + 2 * (size_t)(b->kmax + 1)));
   L.coarse = take(sizeof(int) * b->n);
@@ -496,22 +836,24 @@ extern "C" int sm_batch_arena_size(const sm_batch *b, size_t *bytes) {
   return SM_OK;
 }
 
-// tile lists of one shape: per level index the smoothing/prolongation list
-// (solves for which the level is not the coarsest) and the restriction
-// target list (levels 1..coarsest); the coarse-solve list per level index
+// Work lists.  Tiles of one shape: per level index the restriction target
+// list (levels 1..coarsest).  Columns (shape-independent): per level index
+// the sweep and prolongation list (solves for which the level is not the
+// coarsest) and the finest grids of all solves (outer residual); longest
+// columns first, so that the grid-stride loops end together.  The
+// coarse-solve list per level index.
 static int build_lists(sm_batch *b, int shape) {
   const int *sh = SHAPES[shape];
   std::vector<int4> all;
-  b->smooth_off.assign(b->kmax + 1, 0);
-  b->smooth_cnt.assign(b->kmax + 1, 0);
   b->restr_off.assign(b->kmax + 1, 0);
   b->restr_cnt.assign(b->kmax + 1, 0);
-  auto push_level = [&](int k, bool restrict_list) {
+  b->scol_off.assign(b->kmax + 1, 0);
+  b->scol_cnt.assign(b->kmax + 1, 0);
+  auto push_level = [&](int k) {
     size_t start = all.size();
     for (int s = 0; s < b->n; ++s) {
       const BSolve &q = b->solves[s];
-      bool take = restrict_list ? (k >= 1 && k < q.nlev) : (k < q.nlev - 1);
-      if (!take) continue;
+      if (!(k >= 1 && k < q.nlev)) continue;
       int N = q.N[k];
       int nx = (N + sh[0] - 1) / sh[0], ny = (N + sh[1] - 1) / sh[1], nz = (N + sh[2] - 1) / sh[2];
       for (int tz = 0; tz < nz; ++tz)
@@ -520,24 +862,31 @@ static int build_lists(sm_batch *b, int shape) {
     }
     return std::make_pair(start, all.size() - start);
   };
+  auto push_cols = [&](int k, bool fine) {
+    size_t start = all.size();
+    std::vector<int> order;
+    for (int s = 0; s < b->n; ++s)
+      if (fine || k < b->solves[s].nlev - 1) order.push_back(s);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int u, int v) { return b->solves[u].N[k] > b->solves[v].N[k]; });
+    for (int s : order) {
+      int N = b->solves[s].N[k];
+      for (int cy = 0; cy < (N + CY - 1) / CY; ++cy)
+        for (int cx = 0; cx < (N + CX - 1) / CX; ++cx) all.push_back(make_int4(s, cx, cy, 0));
+    }
+    return std::make_pair(start, all.size() - start);
+  };
   for (int k = 0; k <= b->kmax; ++k) {
-    auto a = push_level(k, false);
-    b->smooth_off[k] = a.first;
-    b->smooth_cnt[k] = a.second;
-    auto r = push_level(k, true);
+    auto r = push_level(k);
     b->restr_off[k] = r.first;
     b->restr_cnt[k] = r.second;
+    auto c = push_cols(k, false);
+    b->scol_off[k] = c.first;
+    b->scol_cnt[k] = c.second;
   }
-  // finest grids of all solves, including those whose finest is the coarsest
-  b->fine_off = all.size();
-  for (int s = 0; s < b->n; ++s) {
-    int N = b->solves[s].N[0];
-    int nx = (N + sh[0] - 1) / sh[0], ny = (N + sh[1] - 1) / sh[1], nz = (N + sh[2] - 1) / sh[2];
-    for (int tz = 0; tz < nz; ++tz)
-      for (int ty = 0; ty < ny; ++ty)
-        for (int tx = 0; tx < nx; ++tx) all.push_back(make_int4(s, tx, ty, tz));
-  }
-  b->fine_cnt = all.size() - b->fine_off;
+  auto f = push_cols(0, true);
+  b->fine_off = f.first;
+  b->fine_cnt = f.second;
   if (all.size() > b->max_tiles) return bfail(b, SM_ESTATE, "tile list capacity");
   std::vector<int> coarse;
   b->coarse_off.assign(b->kmax + 1, 0);
@@ -571,6 +920,7 @@ extern "C" int sm_batch_bind_arena(sm_batch *b, void *dev_ptr, size_t bytes) {
   b->phi = (double *)(a + L.phi);
   b->f64 = (double *)(a + L.f64);
   b->e32 = (float *)(a + L.e32);
+  b->e32b = (float *)(a + L.e32b);
   b->f32 = (float *)(a + L.f32);
   b->d_tiles = (int4 *)(a + L.tiles);
   b->d_coarse = (int *)(a + L.coarse);
@@ -623,23 +973,31 @@ static BState bstate(sm_batch *b) {
 
 static int outer(sm_batch *b, int zero_phi) {
   size_t n0 = b->fine_cnt;
-  k_bt_outer<<<grid_for(b, n0), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab,
-                                                            b->d_active, b->phi, b->f64, b->f32, b->e32, b->bc,
-                                                            shape_of(b), zero_phi, b->d_num);
+  k_bt_outer<<<grid_for(b, n0), CT, OUTER_SMEM, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, b->d_active,
+                                                    b->phi, b->f64, b->f32, b->e32, b->bc, zero_phi, b->d_num);
   ++b->n_launch;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "outer residual launch");
 }
 
-static int smooth_level(sm_batch *b, int k, int nu) {
-  size_t n = b->smooth_cnt[k];
+// nu sweeps of level k, alternating between the two error buffers; the
+// result is left in e32.  With add_phi (level 0 after the V-cycle) the last
+// sweep adds the error to the FP64 potential instead of storing it.
+static int smooth_level(sm_batch *b, int k, int nu, bool add_phi) {
+  size_t n = b->scol_cnt[k];
   if (!n) return SM_OK;
-  for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color) {
-      k_bt_smooth<<<grid_for(b, n), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->smooth_off[k], (int)n, k, color,
-                                                                b->d_tab, b->d_active, b->e32, b->f32, b->bc,
-                                                                shape_of(b));
-      ++b->n_launch;
-    }
+  const int4 *cols = b->d_tiles + b->scol_off[k];
+  for (int s = 0; s < nu; ++s) {
+    const float *in = (s & 1) ? b->e32b : b->e32;
+    float *out = (s & 1) ? b->e32 : b->e32b;
+    double *phi = (add_phi && s == nu - 1) ? b->phi : nullptr;
+    k_bt_sweep<<<grid_for(b, n), CT, phi ? SWEEP_SMEM_PHI : SWEEP_SMEM, b->stream>>>(cols, (int)n, k, b->d_tab, b->d_active, in, out, b->f32,
+                                                     b->bc, phi);
+    ++b->n_launch;
+  }
+  if ((nu & 1) && !add_phi) {
+    k_bt_copy<<<grid_for(b, n), CT, 0, b->stream>>>(cols, (int)n, k, b->d_tab, b->d_active, b->e32b, b->e32);
+    ++b->n_launch;
+  }
   return SM_OK;
 }
 
@@ -647,21 +1005,30 @@ static size_t coarse_smem(int n) {
   return sizeof(double) * (2 * (size_t)n * n * n + 3 * BMAXC * BMAXC + 3 * BMAXC);
 }
 
+// dynamic shared memory of the kernels that stage more than 48 KB
+static int set_attrs(sm_batch *b) {
+  BCK(cudaFuncSetAttribute(k_bt_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem(BMAXC)));
+  BCK(cudaFuncSetAttribute(k_bt_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_PHI));
+  BCK(cudaFuncSetAttribute(k_bt_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUTER_SMEM));
+  return SM_OK;
+}
+
 static int coarse_at_level(sm_batch *b, int k) {
   size_t nc = b->coarse_cnt[k];
   if (nc) {
     k_bt_coarse<<<(int)nc, 512, coarse_smem(BMAXC), b->stream>>>(b->d_coarse + b->coarse_off[k], k, b->d_tab,
-                                                                b->d_active, b->e32, b->f32, b->bc);
+                                                                b->d_active, b->e32, b->f32, b->bc, b->phi);
     ++b->n_launch;
   }
   return SM_OK;
 }
 
-// correction-scheme V-cycle on the error equation of every active solve
+// correction-scheme V-cycle on the error equation of every active solve,
+// ending with phi += e on the finest grids
 static int bvcycle(sm_batch *b) {
-  coarse_at_level(b, 0);  // solves whose finest grid is already the coarsest
+  coarse_at_level(b, 0);  // solves whose finest grid is already the coarsest (adds to phi)
   for (int k = 0; k < b->kmax; ++k) {
-    smooth_level(b, k, b->nu1);
+    smooth_level(b, k, b->nu1, false);
     size_t nr = b->restr_cnt[k + 1];
     if (nr) {
       k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[k + 1], (int)nr, k,
@@ -672,14 +1039,13 @@ static int bvcycle(sm_batch *b) {
     coarse_at_level(b, k + 1);
   }
   for (int k = b->kmax - 1; k >= 0; --k) {
-    size_t n = b->smooth_cnt[k];
+    size_t n = b->scol_cnt[k];
     if (n) {
-      k_bt_prolong<<<grid_for(b, n), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->smooth_off[k], (int)n, k,
-                                                                 b->d_tab, b->d_active, b->e32, b->bc,
-                                                                 shape_of(b));
+      k_bt_prolong<<<grid_for(b, n), CT, 0, b->stream>>>(b->d_tiles + b->scol_off[k], (int)n, k, b->d_tab,
+                                                         b->d_active, b->e32, b->bc);
       ++b->n_launch;
     }
-    smooth_level(b, k, b->nu2);
+    smooth_level(b, k, b->nu2, k == 0);
   }
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "V-cycle launch");
 }
@@ -717,14 +1083,10 @@ static int prefix(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "prefix launch");
 }
 
-// one correction of every active solve: V-cycle, phi += e, residual, check
+// one correction of every active solve: V-cycle with phi += e, residual, check
 static int body_step(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
   int st;
   if ((st = bvcycle(b))) return st;
-  size_t n0t = b->fine_cnt;
-  k_bt_add<<<grid_for(b, n0t), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->fine_off, (int)n0t, b->d_tab,
-                                                           b->d_active, b->phi, b->e32, shape_of(b));
-  ++b->n_launch;
   if ((st = outer(b, 0))) return st;
   k_bt_check<<<1, 256, 0, b->stream>>>(h, in_graph, b->n, bstate(b), 1, 1, b->d_tolmax);
   ++b->n_launch;
@@ -737,7 +1099,7 @@ static int body_step(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
 static int capture(sm_batch *b) {
   if (!b->cap) BCK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   if (!b->cap2) BCK(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
-  BCK(cudaFuncSetAttribute(k_bt_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem(BMAXC)));
+  if (int st = set_attrs(b)) return st;
   cudaStream_t saved = b->stream;
   BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   b->stream = b->cap;
@@ -791,7 +1153,7 @@ static int capture(sm_batch *b) {
 static int run(sm_batch *b, double tol, int max_cycles, int *iterations) {
   if (!b->graphs) {
     // the same launches driven from the host, one flag read per correction
-    BCK(cudaFuncSetAttribute(k_bt_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem(BMAXC)));
+    if (int st = set_attrs(b)) return st;
     b->h_tolmax[0] = tol;
     b->h_tolmax[1] = (double)max_cycles;
     BCK(cudaMemcpyAsync(b->d_tolmax, b->h_tolmax, 2 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
@@ -864,9 +1226,9 @@ extern "C" int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult,
       int st = build_lists(b, s);
       if (st) return st;
       b->gmult = gm;
-      BCK(cudaMemsetAsync(b->phi, 0, sizeof(double) * b->cells64, b->stream));
+      BCK(cudaMemsetAsync(b->phi, 0, sizeof(double) * b->len64, b->stream));
       if ((st = run(b, 0.0, iters, nullptr))) return st;  // capture + warm-up
-      BCK(cudaMemsetAsync(b->phi, 0, sizeof(double) * b->cells64, b->stream));
+      BCK(cudaMemsetAsync(b->phi, 0, sizeof(double) * b->len64, b->stream));
       BCK(cudaEventRecord(e0, b->stream));
       if ((st = run(b, 0.0, iters, nullptr))) return st;
       BCK(cudaEventRecord(e1, b->stream));
@@ -884,7 +1246,7 @@ extern "C" int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult,
   int st = build_lists(b, bs);
   if (st) return st;
   b->gmult = bg;
-  BCK(cudaMemsetAsync(b->phi, 0, sizeof(double) * b->cells64, b->stream));
+  BCK(cudaMemsetAsync(b->phi, 0, sizeof(double) * b->len64, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   if (shape) *shape = bs;
   if (grid_mult) *grid_mult = bg;

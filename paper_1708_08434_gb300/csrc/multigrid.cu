@@ -107,7 +107,7 @@ __device__ __forceinline__ void stage_box(const Grp &g, T *s, const T *v, const 
     const T inner = s[q];
     T gv;
     if (nbv.v[r] >= 0) gv = hv[r];
-    else if (nbv.v[r] == -1) gv = bc.type[f] ? (homog ? T(0) : T(2.0 * bc.val[f])) - inner : inner;
+    else if (nbv.v[r] == -1) gv = bc.type[f] ? (homog ? T(0) : bc_g2<T>(bc, f)) - inner : inner;
     else gv = inner * T(1.0 / 3.0) + T(2.0 / 3.0) * hv[r];
     s[q + ((f & 1) ? stride : -stride)] = gv;
   }
@@ -247,7 +247,7 @@ __device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, 
     return val(Qn, cidx(E == 0 ? w : q0, E == 1 ? w : q1, E == 2 ? w : q2));
   }
   if (Qn == -1) {
-    if (bc.type[f]) return (homog ? T(0) : T(2.0 * bc.val[f])) - ctr;
+    if (bc.type[f]) return (homog ? T(0) : bc_g2<T>(bc, f)) - ctr;
     return ctr;
   }
   atomicOr(err, 1ull);  // nesting violated: no coarse box where one must be
@@ -368,7 +368,7 @@ __device__ __forceinline__ void prolong_box(const Grp &g, T *sp, int b, int mode
         lc[E] -= S;  // the coarse cell inside P next to the boundary
         const T ctr = val(P, cidx(lc[0], lc[1], lc[2]));
         if (Qn == -1) {
-          v = bc.type[F] ? (hom ? T(0) : T(2.0 * bc.val[F])) - ctr : ctr;
+          v = bc.type[F] ? (hom ? T(0) : bc_g2<T>(bc, F)) - ctr : ctr;
         } else {
           atomicOr(err, 1ull);  // nesting violated: no coarse box where one must be
           v = ctr;
@@ -496,7 +496,7 @@ __device__ __forceinline__ double resid_box(const Grp &g, double *s, int b, cons
   for (int h = 0; h < CPT; ++h) {
     const int q = s10(g.t + h * GT);
     const double r = f[h] - (staged_sum(s, q) - 6.0 * s[q]) * inv_h2;
-    if (r32) r32[base + g.t + h * GT] = (float)r;
+    if (r32) r32[base + g.t + h * GT] = cvt_f64_f32_rn(r);
     m = fmax(m, fabs(r));
   }
   return m;
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(GT) k_add_corr(const int32_t *__restrict__ lea
   pdl_wait();
   const size_t x = (size_t)__ldg(leaf + blockIdx.x) * CELLS + threadIdx.x;
 #pragma unroll
-  for (int h = 0; h < CPT; ++h) phi[x + h * GT] += (double)e32[x + h * GT];
+  for (int h = 0; h < CPT; ++h) phi[x + h * GT] += cvt_f32_f64(e32[x + h * GT]);
 }
 
 // Stopping test of the device-side cycle loop: relative residual of the

@@ -22,7 +22,29 @@ constexpr int MAXL = SM_MAX_LEVELS;
 struct Bc {
   int type[6];      // 0 Neumann zero, 1 Dirichlet
   double val[6];
+  double g2[6];     // 2 val, the Dirichlet ghost's constant part (filled by bc_finish)
+  float g2f[6];     // the same rounded to FP32
 };
+
+// fill the derived constants of a boundary description (host side)
+inline void bc_finish(Bc &bc) {
+  for (int f = 0; f < 6; ++f) {
+    bc.g2[f] = 2.0 * bc.val[f];
+    bc.g2f[f] = (float)bc.g2[f];
+  }
+}
+
+// 2 g of face f in the arithmetic type of a kernel (no FP64 work in FP32 kernels)
+template <typename T>
+__host__ __device__ __forceinline__ T bc_g2(const Bc &bc, int f);
+template <>
+__host__ __device__ __forceinline__ double bc_g2<double>(const Bc &bc, int f) {
+  return bc.g2[f];
+}
+template <>
+__host__ __device__ __forceinline__ float bc_g2<float>(const Bc &bc, int f) {
+  return bc.g2f[f];
+}
 
 // per-level grid spacing tables, passed by value to kernels
 struct LevelH {
@@ -170,6 +192,44 @@ __device__ __forceinline__ int fcell(int a, int i, int j, int k) {
 // no-op for a normal launch)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Conversions between IEEE-754 binary64 and binary32 done with 32-bit
+// integer operations on the bit fields.  On this GPU the hardware
+// conversion instructions share the narrow FP64 pipe (at a fraction of the
+// fused multiply-add rate), so FP64 kernels that convert every cell lose
+// most of their FP64 throughput to them.  Normal results take the integer
+// path; zeros, subnormals, infinities and NaNs fall back to the hardware
+// conversion.  Both agree bit for bit with the hardware (checked by
+// sm_check_conversions).
+//
+// binary64 -> binary32, round to nearest, ties to even: keep the top 23 of
+// the 52 fraction bits, round on the 29 dropped bits; a carry out of the
+// fraction increments the exponent field (and reaches the infinity
+// encoding on overflow), which is the correctly rounded result.
+__device__ __forceinline__ float cvt_f64_f32_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e >= 1 && e <= 254) {
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    unsigned r = ((unsigned)e << 23) | m;
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(r | (hi & 0x80000000u));
+  }
+  return __double2float_rn(d);
+}
+
+// binary32 -> binary64 (exact): re-bias the exponent, widen the fraction
+__device__ __forceinline__ double cvt_f32_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e != 0u && e != 255u) {
+    const unsigned hi = (u & 0x80000000u) | ((e + 1023u - 127u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  return (double)f;
+}
+
 // atomic max of a non-negative double through its bit pattern
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *slot, double v) {
   atomicMax(slot, (unsigned long long)__double_as_longlong(v));
@@ -211,7 +271,7 @@ __device__ __forceinline__ T pot_ghost(const T *v, const int32_t *__restrict__ n
     return v[(size_t)nb * CELLS + cidx(c[0], c[1], c[2])];
   }
   if (nb == -1) {
-    if (bc.type[f]) return (homog ? T(0) : T(2.0 * bc.val[f])) - inner;
+    if (bc.type[f]) return (homog ? T(0) : bc_g2<T>(bc, f)) - inner;
     return inner;
   }
   return inner * T(1.0 / 3.0) + T(2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + fcell(a, i, j, k)];

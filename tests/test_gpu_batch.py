@@ -61,6 +61,32 @@ def test_batch_uneven_sizes_against_spectral():
     check(b, rhos, range(len(sides)), 1e-9)
 
 
+def test_batch_odd_and_unaligned_sizes():
+    """Sides that are odd (finest grid = coarsest, exact solve only) or
+    2 mod 4 (rows not 16-byte aligned: element-wise staging), mixed with
+    aligned ones placed right after odd-sized grids (their starts must be
+    padded to stay aligned); Dirichlet on four faces."""
+    import torch
+    import paper_1708_08434_gb300 as pkg
+    sides = [15, 32, 9, 18, 20, 12, 26, 44]
+    bct, bcv = (1, 0, 0, 1, 1, 1), (0.5, 0.0, 0.0, -0.25, 0.0, 1.0)
+    b = pkg.Batch(sides, 1.0, bct, bcv)
+    blobs = synth.batch_blobs(len(sides) + 7)[7:]
+    rhos = {}
+    for s, n in enumerate(sides):
+        rhos[s] = synth.blob_rho(int(n), blobs[s])
+        b.grid(b.rhs, s).copy_(torch.from_numpy(-rhos[s]))
+    b.phi.zero_()
+    rc, cyc, rel = b.solve(1e-9, 40)
+    assert rc == 0 and np.all(rel <= 1e-9)
+    for s in range(len(sides)):
+        ref = spectral.solve(-rhos[s], 1.0, bct, bcv)
+        got = b.grid(b.phi, s).cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= 1e-7, (s, sides[s], err)
+    b.close()
+
+
 def test_batch_autotune_keeps_results():
     sides = [40, 48, 32, 56]
     b, rhos = make_batch(sides, seed_blobs=3)
