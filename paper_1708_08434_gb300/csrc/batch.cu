@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "sm_internal.cuh"
@@ -146,7 +147,9 @@ __device__ __forceinline__ float wall_w(const Bc &bc, int a, int v, int N) {
 // repeats what the neighbouring columns compute, from the same values),
 // then colour 1 on plane p-1 over the column, which by then has all its
 // colour-0 neighbours, and stores plane p-1.  The updates use the values of
-// two separate colour passes over the level.  With phi != nullptr (level 0,
+// two separate colour passes over the level.  With zero_in the sweep starts
+// from e = 0 (the first sweep of a level in a V-cycle): e_in is not read,
+// the staged error planes are zero-filled.  With phi != nullptr (level 0,
 // last sweep of a cycle) the swept error is not stored but added to the
 // FP64 potential: phi += (double)e.
 // Ring use at step p: planes p-2 .. p+1 are read, p+2 .. p+4 are in flight,
@@ -155,12 +158,14 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
                                                  const BSolve *__restrict__ tab,
                                                  const unsigned char *__restrict__ active,
                                                  const float *__restrict__ e_in, float *__restrict__ e_out,
-                                                 const float *__restrict__ f, Bc bc, double *__restrict__ phi) {
+                                                 const float *__restrict__ f, Bc bc, double *__restrict__ phi,
+                                                 int zero_in) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float(*se)[EPL] = reinterpret_cast<float(*)[EPL]>(smem_raw);
   float(*sf)[FPL] = reinterpret_cast<float(*)[FPL]>(smem_raw + sizeof(float) * RING * EPL);
   double(*sph)[CX * CY] = reinterpret_cast<double(*)[CX * CY]>(smem_raw + SWEEP_SMEM);
   const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  constexpr int NCH = (ER + FR) * (RW / 4);  // 16-byte chunks of one staged plane pair (e, f)
   for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
     const int4 C = cols[it];
     if (!active[C.x]) continue;  // uniform per block
@@ -172,29 +177,48 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
     float *eo = e_out + off;
     double *pv = phi ? phi + tab[C.x].off64 : nullptr;
     const bool vec = (N & 3) == 0;
+    // this thread's 16-byte chunks (at most two): shared address in slot 0,
+    // source plane (e or f), in-plane element offset, inside the grid
+    unsigned cdst[2] = {0u, 0u};
+    int coff[2] = {0, 0};
+    bool cise[2] = {false, false}, cok[2] = {false, false}, chas[2] = {false, false};
+    if (vec) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = t + u * CT;
+        if (i >= NCH) continue;
+        const bool ise = i < ER * (RW / 4);
+        const int j = ise ? i : i - ER * (RW / 4);
+        const int r = j / (RW / 4), c4 = 4 * (j % (RW / 4));
+        const int y = y0 - (ise ? 2 : 1) + r, x = x0 - 4 + c4;
+        chas[u] = true;
+        cise[u] = ise;
+        cok[u] = y >= 0 && y < N && x >= 0 && x < N && !(ise && zero_in);
+        coff[u] = cok[u] ? y * N + x : 0;
+        cdst[u] = ise ? smem_u32(&se[0][r * RW + c4]) : smem_u32(&sf[0][r * RW + c4]);
+      }
+    }
     // copies of plane z (if it exists) as one commit group
     auto issue = [&](int z) {
       if (z < N) {
         const int sl = z & (RING - 1);
         const float *ez = ev + z * NN, *fz = fv + z * NN;
         if (vec) {
-          for (int i = t; i < (ER + FR) * (RW / 4); i += CT) {
-            const bool ise = i < ER * (RW / 4);
-            const int j = ise ? i : i - ER * (RW / 4);
-            const int r = j / (RW / 4), c4 = 4 * (j % (RW / 4));
-            const int y = y0 - (ise ? 2 : 1) + r, x = x0 - 4 + c4;
-            const bool ok = y >= 0 && y < N && x >= 0 && x < N;
-            const float *src = ise ? ez : fz;
-            float *dst = ise ? &se[sl][r * RW + c4] : &sf[sl][r * RW + c4];
-            cp_async<16>(dst, ok ? src + y * N + x : src, ok);
-          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (chas[u]) {
+              const unsigned d = cdst[u] + (unsigned)sl * (cise[u] ? EPL * 4u : FPL * 4u);
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d),
+                           "l"((cise[u] ? ez : fz) + coff[u]), "r"(cok[u] ? 16 : 0)
+                           : "memory");
+            }
         } else {
           for (int i = t; i < (ER + FR) * RW; i += CT) {
             const bool ise = i < ER * RW;
             const int j = ise ? i : i - ER * RW;
             const int r = j / RW, c = j % RW;
             const int y = y0 - (ise ? 2 : 1) + r, x = x0 - 4 + c;
-            const bool ok = y >= 0 && y < N && x >= 0 && x < N;
+            const bool ok = y >= 0 && y < N && x >= 0 && x < N && !(ise && zero_in);
             const float *src = ise ? ez : fz;
             float *dst = ise ? &se[sl][j] : &sf[sl][j];
             cp_async<4>(dst, ok ? src + y * N + x : src, ok);
@@ -209,16 +233,17 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
       cp_commit();
     };
     // Gauss-Seidel update of the staged cell at e-plane index q (rhs index
-    // qf) of plane z, wall coefficient w (in-plane part)
-    auto update = [&](int z, int q, int qf, float w) {
+    // qf) of plane z: lo/hi tell whether planes z-1/z+1 exist, w is the
+    // cell's wall coefficient
+    auto update = [&](int z, int q, int qf, float w, bool lo, bool hi) {
       float *pz = se[z & (RING - 1)];
       const float c = pz[q];
       float s = pz[q - 1] + pz[q + 1];
       s += pz[q - RW];
       s += pz[q + RW];
-      if (z > 0) s += se[(z - 1) & (RING - 1)][q];
-      if (z < N - 1) s += se[(z + 1) & (RING - 1)][q];
-      s = fmaf(w + wall_w(bc, 2, z, N), c, s);
+      if (lo) s += se[(z - 1) & (RING - 1)][q];
+      if (hi) s += se[(z + 1) & (RING - 1)][q];
+      s = fmaf(w, c, s);
       pz[q] = (s - h2 * sf[z & (RING - 1)][qf]) * (1.0f / 6.0f);
     };
     // this thread's two column cells (rows ya, ya+1) and its ring cell
@@ -237,6 +262,7 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
     const bool rin = rx >= 0 && rx < N && ry >= 0 && ry < N;
     const int rq = (ry - y0 + 2) * RW + (rx - x0 + 4), rqf = (ry - y0 + 1) * RW + (rx - x0 + 4);
     const float rw = rin ? wall_w(bc, 0, rx, N) + wall_w(bc, 1, ry, N) : 0.f;
+    const long long row0 = (long long)ya * N + x;
     __syncthreads();  // the previous column's planes are no longer read
 #pragma unroll
     for (int z = 0; z < RING - 3; ++z) issue(z);  // planes 0 .. RING-4
@@ -245,18 +271,20 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
       __syncthreads();      // everyone's have; step p-1's reads of plane p-3 are done
       issue(p + RING - 3);
       if (p < N) {  // colour 0 on plane p: one column cell per thread, and the ring
+        const bool lo = p > 0, hi = p < N - 1;
+        const float wz = wall_w(bc, 2, p, N);
         if (in) {
           const int o = (x + ya + p) & 1;  // row offset of the colour-0 cell
-          update(p, q0 + o * RW, qf0 + o * RW, o ? w1 : w0);
+          update(p, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wz, lo, hi);
         }
-        if (rin && !((rx + ry + p) & 1)) update(p, rq, rqf, rw);
+        if (rin && !((rx + ry + p) & 1)) update(p, rq, rqf, rw + wz, lo, hi);
       }
       __syncthreads();
       if (p >= 1 && in) {  // colour 1 on plane p-1, then store both cells
         const int z = p - 1, o = ((x + ya + z) & 1) ^ 1;
-        update(z, q0 + o * RW, qf0 + o * RW, o ? w1 : w0);
+        update(z, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wall_w(bc, 2, z, N), z > 0, z < N - 1);
         const float v0 = se[z & (RING - 1)][q0], v1 = se[z & (RING - 1)][q0 + RW];
-        const long long g = z * NN + (long long)ya * N + x;
+        const long long g = z * NN + row0;
         if (pv) {
           const double *ph = sph[z & (RING - 1)];
           pv[g] = ph[ty2 * CX + tx] + cvt_f32_f64(v0);
@@ -291,12 +319,13 @@ __global__ void __launch_bounds__(CT) k_bt_copy(const int4 *__restrict__ cols, i
   }
 }
 
-// coarse rhs of level k+1 = mean of the 8 fine residuals; coarse error = 0
+// coarse rhs of level k+1 = mean of the 8 fine residuals (the coarse
+// error starts at zero: the level's first sweep does not read it)
 __global__ void __launch_bounds__(TILE_CELLS) k_bt_restrict(const int4 *__restrict__ tiles, int ntiles, int k,
                                                             const BSolve *__restrict__ tab,
                                                             const unsigned char *__restrict__ active,
-                                                            float *__restrict__ e, float *__restrict__ f, Bc bc,
-                                                            TileShape sh) {
+                                                            const float *__restrict__ e, float *__restrict__ f,
+                                                            Bc bc, TileShape sh) {
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
     int4 T = tiles[it];
     if (!active[T.x]) continue;
@@ -317,7 +346,6 @@ __global__ void __launch_bounds__(TILE_CELLS) k_bt_restrict(const int4 *__restri
         }
     long long ic = gidx(Nc, X, Y, Z);
     f[S.off[k + 1] + ic] = acc * 0.125f;
-    e[S.off[k + 1] + ic] = 0.0f;
   }
 }
 
@@ -475,21 +503,21 @@ __global__ void __launch_bounds__(512) k_bt_coarse(const int *__restrict__ solve
 }
 
 // FP64 outer residual on the finest grids, column by column:
-// r = f - L phi (or of phi = 0 when zero_phi), its max norm per solve, the
-// FP32 copy of r as the error equation's rhs and a zero initial error.
+// r = f - L phi (or of phi = 0 when zero_phi), its max norm per solve and
+// the FP32 copy of r as the error equation's rhs (the error itself starts
+// at zero: the first sweep does not read it).
 // Planes of phi (one-cell halo) are staged by asynchronous copies: at step
 // p planes p-1 .. p+1 are read, p+2 .. p+4 are in flight and plane p+5 is
-// issued into the slot of plane p-3; f of plane p+1 is loaded into
-// registers during step p.  phi is only read here.  Per cell: the six
-// neighbours summed pairwise (zero-filled halo outside the grid), the wall
-// ghosts (boundary cells only), two fused multiply-adds; the max norm is
-// taken on the bit patterns of |r|.
-__global__ void __launch_bounds__(CT) k_bt_outer(const int4 *__restrict__ cols, int ncols,
+// issued into the slot of plane p-3; f is loaded into registers two
+// planes ahead.  phi is only read here.  Per cell: the six
+// neighbours (wall ghosts selected in place) summed pairwise, two fused
+// multiply-adds; the max norm is taken on the bit patterns of |r|.
+__global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ cols, int ncols,
                                                  const BSolve *__restrict__ tab,
                                                  const unsigned char *__restrict__ active,
                                                  const double *__restrict__ phi, const double *__restrict__ f64,
-                                                 float *__restrict__ f32, float *__restrict__ e32, Bc bc,
-                                                 int zero_phi, unsigned long long *__restrict__ num) {
+                                                 float *__restrict__ f32, Bc bc, int zero_phi,
+                                                 unsigned long long *__restrict__ num) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double(*sp)[DPL] = reinterpret_cast<double(*)[DPL]>(smem_raw);
   __shared__ unsigned long long red[CT / 32];
@@ -526,61 +554,82 @@ __global__ void __launch_bounds__(CT) k_bt_outer(const int4 *__restrict__ cols, 
       }
       cp_commit();
     };
-    // wall terms per cell: sum of ghosts = wd * c + G (Dirichlet: 2g - c; Neumann: c)
-    auto wall_terms = [&](int a, int v, double &wd, double &G) {
-      if (v == 0) {
-        if (bc.type[2 * a]) wd -= 1.0, G += bc.g2[2 * a];
-        else wd += 1.0;
-      }
-      if (v == N - 1) {
-        if (bc.type[2 * a + 1]) wd -= 1.0, G += bc.g2[2 * a + 1];
-        else wd += 1.0;
-      }
+    // Neighbour value across face f of a cell holding c: the staged value v,
+    // or at the wall the ghost c (Neumann) or 2g - c (Dirichlet).  The face
+    // type is uniform over the kernel, so the Neumann case is a select with
+    // no FP64 work (a per-cell branch would run for every warp holding one
+    // boundary lane).
+    auto nbv = [&](int f, bool at_wall, double v, double c) {
+      if (bc.type[f]) return at_wall ? bc.g2[f] - c : v;
+      return at_wall ? c : v;
     };
     const long long row0 = (long long)ya * N + x;
-    double fc0 = in0 ? fv[row0] : 0.0, fc1 = in1 ? fv[row0 + N] : 0.0;  // f of plane p
+    // f of planes p (set A for even p, B for odd p): loaded two steps ahead
+    double fa0 = 0.0, fa1 = 0.0, fb0 = 0.0, fb1 = 0.0;
+    if (in0) fa0 = fv[row0];
+    if (in1) fa1 = fv[row0 + N];
+    if (N > 1 && in0) fb0 = fv[NN + row0];
+    if (N > 1 && in1) fb1 = fv[NN + row0 + N];
     unsigned long long m = 0;  // bit pattern of max |r|
     __syncthreads();           // the previous column's planes are no longer read
 #pragma unroll
     for (int z = 0; z < RING - 3; ++z) issue(z);
-    for (int p = 0; p < N; ++p) {
+    // NEU: all four in-plane faces are Neumann (a compile-time path: the
+    // ghosts are then selects of c, with no FP64 work for Dirichlet ghosts
+    // the compiler would otherwise compute on every cell)
+    auto step = [&](auto neu_tag, int p, double &f0, double &f1) {
+      constexpr bool NEU = decltype(neu_tag)::value;
       cp_wait<RING - 5>();
       __syncthreads();
       issue(p + RING - 3);
-      double fn0 = 0.0, fn1 = 0.0;  // f of plane p+1, in flight during this step
-      if (p + 1 < N) {
-        if (in0) fn0 = fv[(p + 1) * NN + row0];
-        if (in1) fn1 = fv[(p + 1) * NN + row0 + N];
-      }
       const double *pz = sp[p & (RING - 1)];
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
-        const int y = ya + o;
         if (!(o ? in1 : in0)) continue;
-        const int q = (ty2 + o + 1) * RWD + tx + 2;
-        double s = 0.0, c = 0.0;
-        if (!zero_phi) {
-          c = pz[q];
-          const double zm = p > 0 ? sp[(p - 1) & (RING - 1)][q] : 0.0;
-          const double zp = p < N - 1 ? sp[(p + 1) & (RING - 1)][q] : 0.0;
-          s = ((pz[q - 1] + pz[q + 1]) + (pz[q - RWD] + pz[q + RWD])) + (zm + zp);
+        const int q = (ty2 + o + 1) * RWD + tx + 2, y = ya + o;
+        // phi = 0 (zero_phi): the staged planes are not loaded; every value is 0
+        const double c = zero_phi ? 0.0 : pz[q];
+        double xm, xp, ym, yp;
+        if constexpr (NEU) {
+          xm = x == 0 ? c : (zero_phi ? 0.0 : pz[q - 1]);
+          xp = x == N - 1 ? c : (zero_phi ? 0.0 : pz[q + 1]);
+          ym = y == 0 ? c : (zero_phi ? 0.0 : pz[q - RWD]);
+          yp = y == N - 1 ? c : (zero_phi ? 0.0 : pz[q + RWD]);
+        } else {
+          xm = nbv(0, x == 0, zero_phi ? 0.0 : pz[q - 1], c);
+          xp = nbv(1, x == N - 1, zero_phi ? 0.0 : pz[q + 1], c);
+          ym = nbv(2, y == 0, zero_phi ? 0.0 : pz[q - RWD], c);
+          yp = nbv(3, y == N - 1, zero_phi ? 0.0 : pz[q + RWD], c);
         }
-        if (x == 0 || x == N - 1 || y == 0 || y == N - 1 || p == 0 || p == N - 1) {
-          double wd = 0.0, G = 0.0;
-          wall_terms(0, x, wd, G);
-          wall_terms(1, y, wd, G);
-          wall_terms(2, p, wd, G);
-          s += fma(wd, c, G);
+        double zm, zp;
+        if (p == 0 || p == N - 1) {  // uniform: the wall planes
+          zm = nbv(4, p == 0, (zero_phi || p == 0) ? 0.0 : sp[(p - 1) & (RING - 1)][q], c);
+          zp = nbv(5, p == N - 1, (zero_phi || p == N - 1) ? 0.0 : sp[(p + 1) & (RING - 1)][q], c);
+        } else {
+          zm = zero_phi ? 0.0 : sp[(p - 1) & (RING - 1)][q];
+          zp = zero_phi ? 0.0 : sp[(p + 1) & (RING - 1)][q];
         }
-        const double r = fma(-fma(-6.0, c, s), inv_h2, o ? fc1 : fc0);
-        const long long g = p * NN + row0 + o * N;
-        f32[o32 + g] = cvt_f64_f32_rn(r);
-        e32[o32 + g] = 0.0f;
+        const double s = ((xm + xp) + (ym + yp)) + (zm + zp);
+        const double r = fma(-fma(-6.0, c, s), inv_h2, o ? f1 : f0);
+        f32[o32 + p * NN + row0 + o * N] = cvt_f64_f32_rn(r);
         const unsigned long long a = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
         m = a > m ? a : m;
       }
-      fc0 = fn0;
-      fc1 = fn1;
+      if (p + 2 < N) {  // this set's next plane
+        if (in0) f0 = fv[(p + 2) * NN + row0];
+        if (in1) f1 = fv[(p + 2) * NN + row0 + N];
+      }
+    };
+    if (!(bc.type[0] | bc.type[1] | bc.type[2] | bc.type[3])) {
+      for (int p = 0; p < N; p += 2) {
+        step(std::true_type{}, p, fa0, fa1);
+        if (p + 1 < N) step(std::true_type{}, p + 1, fb0, fb1);
+      }
+    } else {
+      for (int p = 0; p < N; p += 2) {
+        step(std::false_type{}, p, fa0, fa1);
+        if (p + 1 < N) step(std::false_type{}, p + 1, fb0, fb1);
+      }
     }
     cp_wait<0>();
     // one max per column and solve
@@ -974,15 +1023,17 @@ static BState bstate(sm_batch *b) {
 static int outer(sm_batch *b, int zero_phi) {
   size_t n0 = b->fine_cnt;
   k_bt_outer<<<grid_for(b, n0), CT, OUTER_SMEM, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, b->d_active,
-                                                    b->phi, b->f64, b->f32, b->e32, b->bc, zero_phi, b->d_num);
+                                                    b->phi, b->f64, b->f32, b->bc, zero_phi, b->d_num);
   ++b->n_launch;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "outer residual launch");
 }
 
 // nu sweeps of level k, alternating between the two error buffers; the
-// result is left in e32.  With add_phi (level 0 after the V-cycle) the last
-// sweep adds the error to the FP64 potential instead of storing it.
-static int smooth_level(sm_batch *b, int k, int nu, bool add_phi) {
+// result is left in e32.  With from_zero (pre-smoothing) the first sweep
+// starts from e = 0 without reading it; with add_phi (level 0 after the
+// V-cycle) the last sweep adds the error to the FP64 potential instead of
+// storing it.
+static int smooth_level(sm_batch *b, int k, int nu, bool from_zero, bool add_phi) {
   size_t n = b->scol_cnt[k];
   if (!n) return SM_OK;
   const int4 *cols = b->d_tiles + b->scol_off[k];
@@ -990,8 +1041,8 @@ static int smooth_level(sm_batch *b, int k, int nu, bool add_phi) {
     const float *in = (s & 1) ? b->e32b : b->e32;
     float *out = (s & 1) ? b->e32 : b->e32b;
     double *phi = (add_phi && s == nu - 1) ? b->phi : nullptr;
-    k_bt_sweep<<<grid_for(b, n), CT, phi ? SWEEP_SMEM_PHI : SWEEP_SMEM, b->stream>>>(cols, (int)n, k, b->d_tab, b->d_active, in, out, b->f32,
-                                                     b->bc, phi);
+    k_bt_sweep<<<grid_for(b, n), CT, phi ? SWEEP_SMEM_PHI : SWEEP_SMEM, b->stream>>>(
+        cols, (int)n, k, b->d_tab, b->d_active, in, out, b->f32, b->bc, phi, (from_zero && s == 0) ? 1 : 0);
     ++b->n_launch;
   }
   if ((nu & 1) && !add_phi) {
@@ -1028,7 +1079,7 @@ static int coarse_at_level(sm_batch *b, int k) {
 static int bvcycle(sm_batch *b) {
   coarse_at_level(b, 0);  // solves whose finest grid is already the coarsest (adds to phi)
   for (int k = 0; k < b->kmax; ++k) {
-    smooth_level(b, k, b->nu1, false);
+    smooth_level(b, k, b->nu1, true, false);
     size_t nr = b->restr_cnt[k + 1];
     if (nr) {
       k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[k + 1], (int)nr, k,
@@ -1045,7 +1096,7 @@ static int bvcycle(sm_batch *b) {
                                                          b->d_active, b->e32, b->bc);
       ++b->n_launch;
     }
-    smooth_level(b, k, b->nu2, k == 0);
+    smooth_level(b, k, b->nu2, false, k == 0);
   }
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "V-cycle launch");
 }
