@@ -61,6 +61,8 @@ def parse():
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
                          "schedule (small, fixed launch sequences for ncu captures)")
+    ap.add_argument("--batch-solves", type=int, default=256,
+                    help="--mode batch only: solve the first N of the 256 batched problems (small ncu captures)")
     return ap.parse_args()
 
 
@@ -158,7 +160,7 @@ def run_batch_only(args):
     import __graft_entry__
     torch.cuda.set_device(0)
     __graft_entry__.build()
-    b, _ = make_batch_workload()
+    b, _ = make_batch_workload(args.batch_solves)
     if args.no_graphs:
         b.set_graphs(False)
     for _ in range(args.steps):
@@ -427,11 +429,12 @@ def bench_learned(args, dev, world):
     return res
 
 
-def make_batch_workload():
+def make_batch_workload(n=256):
+    """The first n solves of the seeded 256-solve workload."""
     import torch
     import synth
     import paper_1708_08434_gb300 as pkg
-    sides = synth.batch_sizes(256)
+    sides = synth.batch_sizes(256)[:n]
     b = pkg.Batch(sides, 1.0, (0, 0, 0, 0, 1, 1), (0, 0, 0, 0, 0, 1.0))
     blobs = synth.batch_blobs(len(sides))
     for s, n in enumerate(sides):
@@ -474,13 +477,31 @@ def bench_batch(args, dev, world):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total = float(tt.item())
     cells, levels, launches = b.info()
+    # per-kernel rooflines of the cycle (after the timed solves: the bench
+    # launches overwrite the error arrays)
+    hbm = measured_peaks()[0]
+    kern = {}
+    for kc, name in ((0, "k_bt_sweep level 0"), (1, "k_bt_outer (FP64 residual)"),
+                     (2, "k_bt_prolong level 0"), (3, "k_bt_restrict level 0->1")):
+        us, by, fl = b.kernel_bench(kc, 10)
+        e = {"us": round(us, 2), "bytes": int(by), "gbs": round(by / (us * 1e-6) / 1e9, 1),
+             "hbm_frac": round(by / (us * 1e-6) / 1e9 / hbm, 4)}
+        if fl:
+            e["fp64_ginstr"] = round(fl / (us * 1e-6) / 1e9, 1)
+            e["fp64_frac"] = round(fl / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4)
+        kern[name] = e
     res = {"value": round(256 * args.steps * world / (total * 1e-3), 2), "unit": "solves/s",
            "ms_per_batch": round(total / args.steps, 3), "solves_per_batch": 256, "cells": cells,
            "max_corrections": cycles / args.steps,
            "gcells_corrections_per_s": round(cells * cycles * world / (total * 1e-3) / 1e9, 3),
            "schedule": {"tile": pkg.Batch.SHAPES[shape], "blocks_per_sm": gmult, "tuned_ms": round(tune_ms, 3)},
            "gpu_launches": launches - l0, "dtype": "f32 cycles, f64 residual/accumulation/coarsest solve",
-           "workload": "256 unit-cube solves, sides 8*round(32*4^u/8), phi=0/1 on z plates"}
+           "workload": "256 unit-cube solves, sides 8*round(32*4^u/8), phi=0/1 on z plates",
+           "kernels": kern,
+           "kernels_note": "CUDA events around 10 back-to-back launches over all 256 solves; bytes = "
+                           "compulsory traffic (sweep 12 B, outer 20 B + 7 FP64 instr, prolong/restrict "
+                           "8.5 B per fine cell); hbm peak %.1f GB/s measured, FP64 peak %.0f G instr/s"
+                           % (hbm, FP64_PEAK_GINSTR)}
     b.close()
     return res
 

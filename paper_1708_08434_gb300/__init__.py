@@ -64,7 +64,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc", "sm_check_conversions",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
-           "sm_batch_set_graphs", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
+           "sm_batch_set_graphs", "sm_batch_kernel_bench", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
            "sm_cnn_last_error",
@@ -125,6 +125,7 @@ def load():
         "sm_batch_tune": [P, I, pI, pI, pD],
         "sm_batch_set_schedule": [P, I, I],
         "sm_batch_set_graphs": [P, I],
+        "sm_batch_kernel_bench": [P, I, I, pD, pD, pD],
         "sm_batch_info": [P, C.POINTER(C.c_longlong), pI, C.POINTER(C.c_longlong)],
         "sm_batch_last_error": [P],
         "sm_cnn_create": [C.POINTER(P), I, I, P],
@@ -476,6 +477,14 @@ class Batch:
 
     def set_graphs(self, enable: bool):
         self._ck(self._lib.sm_batch_set_graphs(self._h, int(enable)))
+
+    def kernel_bench(self, kclass: int, reps: int = 10):
+        """(microseconds per launch, algorithmic bytes, FP64 operations per
+        launch) of a kernel class of the batched cycle (0 level-0 sweep,
+        1 FP64 outer residual, 2 level-0 prolongation, 3 restriction)."""
+        us, by, fl = C.c_double(), C.c_double(), C.c_double()
+        self._ck(self._lib.sm_batch_kernel_bench(self._h, kclass, reps, C.byref(us), C.byref(by), C.byref(fl)))
+        return us.value, by.value, fl.value
 
     def info(self):
         c, lv, nl = C.c_longlong(), C.c_int(), C.c_longlong()

@@ -1305,6 +1305,71 @@ extern "C" int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult,
   return SM_OK;
 }
 
+// Time one kernel class over all solves (every solve active), CUDA events
+// on the batch stream around `reps` back-to-back launches.  Classes:
+// 0 level-0 sweep (e read, f read, e written: 12 B per cell), 1 FP64 outer
+// residual (phi and f read, FP32 rhs written: 20 B and 7 FP64 operations
+// per cell), 2 level-0 prolongation (fine e read and written, coarse e
+// read: 8.5 B per fine cell), 3 level-0 -> 1 restriction (fine e and f
+// read, coarse f written: 8.5 B per fine cell).  Leaves the potential and
+// the error arrays changed; a following solve starts from whatever phi
+// holds.  Algorithmic bytes and FP64 operations count compulsory work
+// only (no halo re-reads).
+extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *us_per_launch,
+                                     double *bytes_per_launch, double *fp64_per_launch) {
+  if (!b || reps < 1 || kclass < 0 || kclass > 3) return SM_EINVAL;
+  if (!b->arena) return bfail(b, SM_ESTATE, "no arena bound");
+  if (int st = set_attrs(b)) return st;
+  long long fine = 0;  // level-0 cells of solves whose level 0 is smoothed
+  for (auto &q : b->solves)
+    if (q.nlev > 1) fine += (long long)q.N[0] * q.N[0] * q.N[0];
+  const size_t nsw = b->scol_cnt.empty() ? 0 : b->scol_cnt[0];
+  const size_t nr = b->kmax >= 1 ? b->restr_cnt[1] : 0;
+  if ((kclass != 1 && fine == 0) || (kclass == 3 && nr == 0)) return bfail(b, SM_ESTATE, "no level below 0");
+  BCK(cudaMemsetAsync(b->d_active, 1, b->n, b->stream));
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  auto launch = [&]() {
+    switch (kclass) {
+      case 0:
+        k_bt_sweep<<<grid_for(b, nsw), CT, SWEEP_SMEM, b->stream>>>(b->d_tiles + b->scol_off[0], (int)nsw, 0,
+                                                                     b->d_tab, b->d_active, b->e32, b->e32b,
+                                                                     b->f32, b->bc, nullptr, 0);
+        break;
+      case 1:
+        k_bt_outer<<<grid_for(b, b->fine_cnt), CT, OUTER_SMEM, b->stream>>>(
+            b->d_tiles + b->fine_off, (int)b->fine_cnt, b->d_tab, b->d_active, b->phi, b->f64, b->f32, b->bc, 0,
+            b->d_num);
+        break;
+      case 2:
+        k_bt_prolong<<<grid_for(b, nsw), CT, 0, b->stream>>>(b->d_tiles + b->scol_off[0], (int)nsw, 0, b->d_tab,
+                                                             b->d_active, b->e32, b->bc);
+        break;
+      default:
+        k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[1], (int)nr, 0,
+                                                                     b->d_tab, b->d_active, b->e32, b->f32, b->bc,
+                                                                     shape_of(b));
+    }
+  };
+  launch();  // warm-up
+  BCK(cudaEventRecord(e0, b->stream));
+  for (int r = 0; r < reps; ++r) launch();
+  BCK(cudaEventRecord(e1, b->stream));
+  BCK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  BCK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double cells = kclass == 1 ? (double)b->cells64 : (double)fine;
+  const double per_cell[4] = {12.0, 20.0, 8.5, 8.5};
+  if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
+  if (bytes_per_launch) *bytes_per_launch = per_cell[kclass] * cells;
+  if (fp64_per_launch) *fp64_per_launch = kclass == 1 ? 7.0 * cells : 0.0;
+  b->n_launch += reps + 1;
+  return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "kernel bench launch");
+}
+
 extern "C" int sm_batch_set_schedule(sm_batch *b, int shape, int grid_mult) {
   if (!b || shape < 0 || shape >= NSHAPES || grid_mult < 1 || grid_mult > 64) return SM_EINVAL;
   if (!b->arena) return bfail(b, SM_ESTATE, "no arena bound");
