@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-paper", action="store_true", help="skip the fixed 2-V-cycle (paper) schedule")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels from the host instead of CUDA graphs "
                          "(profilers cannot see kernels inside conditional graph nodes)")
@@ -172,6 +173,7 @@ def run_batch_only(args):
 
 
 def run_gpu(args):
+    import numpy as np
     import torch
     import synth
     import paper_1708_08434_gb300 as pkg
@@ -326,7 +328,57 @@ def run_gpu(args):
         if not args.no_profile:
             vus32, _, vby32, _ = gm.kernel_bench(pkg.K_VCYCLE32, 10)
             mixed["fp32_vcycle_us"] = round(vus32, 2)
+        # accuracy of the form: the same charge solved by the mixed form to
+        # 1e-8 and by the FP64 path to 1e-12 (the FP64 path matches the CPU
+        # oracle element by element); potential and |E| on leaf cells
+        for gg in (g, gm):
+            gg.var(pkg.NE).copy_(ne_d)
+            gg.var(pkg.NI).copy_(ni_d)
+            gg.charge_rhs(Q, E0)
+        g.fmg(1e-12, 60)
+        gm.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+        gm.compute_field()
+        leaf = torch.from_numpy(np.asarray(g.tables()["leaf"], dtype=np.int64)).to(dev)
+        p64, p32 = g.var(pkg.PHI)[leaf], gm.var(pkg.PHI)[leaf]
+        e64, e32 = g.var(pkg.EMAG)[leaf], gm.var(pkg.EMAG)[leaf]
+        mixed["error_vs_fp64"] = {
+            "phi_max_rel": float((p32 - p64).abs().max() / p64.abs().max()),
+            "emag_max_rel": float((e32 - e64).abs().max() / e64.abs().max()),
+            "reference": "FP64 path converged to 1e-12 (element-wise parity with the CPU oracle)"}
         gm.close()
+    # the paper's schedule (Sec. 2.1.2, 2.4): one FMG solve, then Heun steps
+    # with exactly two V-cycles per potential update and the time step from
+    # the limits of Sec. 2.4
+    paper = None
+    if not args.no_paper:
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        g.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+        dt = g.dt_limit(Q, E0)
+        for _ in range(2):
+            _, dt, _, _ = g.advance(dt, Q, E0, 0.0, 2)
+        nsteps = 20
+        l0 = g.launch_count()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nsteps):
+            _, dt, c1, c2 = g.advance(dt, Q, E0, 0.0, 2)
+            assert (c1, c2) == (2, 2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        paper = {"steps_per_s": round(nsteps * world / (pms * 1e-3), 2),
+                 "solves_per_s": round(2 * nsteps * world / (pms * 1e-3), 2),
+                 "ms_per_step": round(pms / nsteps, 4),
+                 "mcells_vcycles_per_s": round(leaf_cells * 4 * nsteps * world / (pms * 1e-3) / 1e6, 1),
+                 "steps": nsteps, "gpu_launches": g.launch_count() - l0,
+                 "schedule": "2 V-cycles per solve, 2 solves per Heun step, dt from the Sec. 2.4 limits "
+                             "(host reads dt each step)"}
     batched = None if args.no_batch else bench_batch(args, dev, world)
     learned = None if args.no_learned else bench_learned(args, dev, world)
     steps = args.steps
@@ -352,6 +404,7 @@ def run_gpu(args):
         "clocks": clocks,
         "roofline": roof,
         "mixed_precision": mixed,
+        "paper_schedule": paper,
         "batched": batched,
         "learned_warm_start": learned,
     }
