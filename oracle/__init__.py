@@ -88,6 +88,9 @@ def _load():
         lib.orc_lookup.argtypes = [P, C.c_int, C.c_double]
         lib.orc_lookup.restype = C.c_double
         lib.orc_coarse_solve.argtypes = [P]
+        lib.orc_refine_flags.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, P]
+        lib.orc_regrid.argtypes = [P, P, ip, ip, ip]
+        lib.orc_regrid.restype = C.c_int
         _lib = lib
         return lib
 
@@ -166,6 +169,21 @@ class Oracle:
             raise ValueError("oracle refine_level(%d) refused" % level)
         self.dropped = dropped.value
         return r
+
+    # ---- refinement criterion and regridding (Sec. 2.5, Eq. 8) ----
+    def refine_flags(self, c0=1.0, c1=1.2, c0_deref=0.125, dx_deref=30e-6, buffer=3) -> np.ndarray:
+        """Per-box flags from the stored |E|: +1 refine, -1 derefinable, 0."""
+        f = np.zeros(self.n_boxes, np.int8)
+        self._lib.orc_refine_flags(self._h, c0, c1, c0_deref, dx_deref, buffer, _ptr(f))
+        return f
+
+    def regrid(self, flags):
+        """Apply per-box flags; returns (refined, derefined, dropped)."""
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+        assert flags.shape == (self.n_boxes,)
+        r, d, x = C.c_int(0), C.c_int(0), C.c_int(0)
+        self._lib.orc_regrid(self._h, _ptr(flags), C.byref(r), C.byref(d), C.byref(x))
+        return r.value, d.value, x.value
 
     # ---- fields ----
     def set(self, var: int, arr):

@@ -1,7 +1,8 @@
 /* oracle.c -- plain, slow, obviously correct CPU oracle for the per-time-step
  * path of arXiv:1708.08434 (Afivo-streamer): the geometric multigrid Poisson
  * solve on an octree of 8^3-cell boxes (Sec. 2.1.1-2.1.2, Eq. 1 and 5) and
- * the explicit drift-diffusion-reaction step (Sec. 2.2-2.4, Eq. 2-3, 6-7).
+ * the explicit drift-diffusion-reaction step (Sec. 2.2-2.4, Eq. 2-3, 6-7),
+ * and the refinement criterion with regridding (Sec. 2.5, Eq. 8).
  *
  * TEST INFRASTRUCTURE ONLY: loaded by tests/, the smoke check and the
  * CPU-baseline leg of bench.py.  The CUDA library never calls it and shares
@@ -957,4 +958,205 @@ int orc_advance(orc *o, double dt, double q, double eps, double tol, int max_cyc
   int st2 = orc_solve(o, tol, max_cycles, nu1, nu2, NULL, cycles2);
   orc_compute_field(o);
   return st ? st : st2;
+}
+
+/* ---------------------------------------------------------------------- */
+/* refinement criterion and regridding (Sec. 2.5, Eq. 8)                   */
+/* ---------------------------------------------------------------------- */
+
+/* Eq. 8 asks dx < c0 c1 / alpha(c1 |E|) of every cell.  With the ionization
+ * coefficient from the table (Sec. 2.3) a cell needs refinement where the
+ * criterion fails, alpha(c1 |E|) dx >= c0 c1 (no division).  A leaf box is
+ * flagged +1 when one of its cells needs refinement, or when a cell of a
+ * same-level leaf neighbour within `buffer` cells of it (Chebyshev distance
+ * in cells of that level) does, and its level is below the maximum.  A
+ * leaf above the base grid that is not flagged is derefinable (-1) when
+ * every cell satisfies the criterion with c0_deref and dx < dx_deref.
+ * Other boxes get 0.  Uses the stored |E| of the leaf cells. */
+void orc_refine_flags(orc *o, double c0, double c1, double c0_deref, double dx_deref, int buffer,
+                      int8_t *flags) {
+  unsigned char *need = calloc((size_t)512 * o->nbox, 1);
+  unsigned char *any = calloc((size_t)o->nbox, 1), *fine = calloc((size_t)o->nbox, 1);
+  for (int b = 0; b < o->nbox; ++b) {
+    flags[b] = 0;
+    if (!is_leaf(o, b)) continue;
+    double dx = spacing(o, o->lev[b]);
+    const double *em = box(o, V_EMAG, b);
+    int ok = dx < dx_deref;
+    for (int k = 0; k < NC; ++k)
+      for (int j = 0; j < NC; ++j)
+        for (int i = 0; i < NC; ++i) {
+          double a = orc_lookup(o, 2, c1 * em[IX(i, j, k)]);
+          if (a * dx >= c0 * c1) { need[(size_t)512 * b + i + 8 * j + 64 * k] = 1; any[b] = 1; }
+          if (!(a * dx < c0_deref * c1)) ok = 0;
+        }
+    fine[b] = (unsigned char)ok;
+  }
+  for (int b = 0; b < o->nbox; ++b) {
+    if (!is_leaf(o, b)) continue;
+    int marked = any[b];
+    for (int d = 0; d < 26 && !marked; ++d) {
+      int n = o->nbr[26 * b + d];
+      if (n < 0 || !is_leaf(o, n) || !any[n]) continue;
+      for (int c = 0; c < 512 && !marked; ++c) {
+        if (!need[(size_t)512 * n + c]) continue;
+        int g[3] = {o->ijk[3 * n] * NC + (c & 7), o->ijk[3 * n + 1] * NC + ((c >> 3) & 7),
+                    o->ijk[3 * n + 2] * NC + (c >> 6)};
+        int dist = 0;
+        for (int e = 0; e < 3; ++e) {
+          int lo = o->ijk[3 * b + e] * NC, hi = lo + NC - 1;
+          int de = g[e] < lo ? lo - g[e] : (g[e] > hi ? g[e] - hi : 0);
+          if (de > dist) dist = de;
+        }
+        if (dist <= buffer) marked = 1;
+      }
+    }
+    if (marked) {
+      if (o->lev[b] < o->lmax) flags[b] = 1;
+    } else if (fine[b] && o->lev[b] > o->lbase) {
+      flags[b] = -1;
+    }
+  }
+  free(need); free(any); free(fine);
+}
+
+typedef struct { int lev, i, j, k, src; uint64_t key; } orc_ent;
+
+static int ent_cmp(const void *pa, const void *pb) {
+  const orc_ent *a = pa, *b = pb;
+  if (a->lev != b->lev) return a->lev < b->lev ? -1 : 1;
+  return a->key < b->key ? -1 : (a->key > b->key ? 1 : 0);
+}
+
+/* Apply per-box flags (+1 refine, -1 derefine, leaves only; the layout of
+ * orc_refine_flags).  Refinement: a flagged leaf below the maximum level
+ * gets 8 children when all 26 neighbour positions of its level hold a box
+ * or lie outside the domain (proper nesting, Sec. 2.1.1); other requests
+ * are dropped.  Derefinement: a box whose 8 children are all leaves
+ * flagged -1 loses them, unless a neighbour of one of the children (not a
+ * sibling) has children or is refined in this call, which would break the
+ * nesting.  The mesh is rebuilt in (level, Morton) order; kept boxes keep
+ * all their data; new children get the potential by the linear
+ * prolongation (c + c_sx + c_sy + c_sz)/4 of their parent's cells and the
+ * densities by the same prolongation limited to 2c (mirror ghosts at the
+ * walls), every other variable zero.  Densities are restricted first, so a
+ * box that becomes a leaf holds the mean of its former children. */
+int orc_regrid(orc *o, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
+  restrict_densities(o, V_NE, V_NI);
+  int nb0 = o->nbox;
+  unsigned char *ref = calloc((size_t)nb0, 1), *der = calloc((size_t)nb0, 1);
+  int nref = 0, nder = 0, ndrop = 0;
+  for (int b = 0; b < nb0; ++b) {
+    if (!is_leaf(o, b) || flags[b] <= 0 || o->lev[b] >= o->lmax) continue;
+    int ok = 1;
+    for (int d = 0; d < 26; ++d) if (o->nbr[26 * b + d] == -2) ok = 0;
+    if (ok) { ref[b] = 1; ++nref; } else ++ndrop;
+  }
+  for (int p = 0; p < nb0; ++p) {
+    if (is_leaf(o, p)) continue;
+    int ok = 1;
+    for (int c = 0; c < 8 && ok; ++c) {
+      int ch = o->chl[8 * p + c];
+      if (!is_leaf(o, ch) || flags[ch] >= 0) ok = 0;
+    }
+    for (int c = 0; c < 8 && ok; ++c) {
+      int ch = o->chl[8 * p + c];
+      for (int d = 0; d < 26 && ok; ++d) {
+        int n = o->nbr[26 * ch + d];
+        if (n >= 0 && o->par[n] != p && (!is_leaf(o, n) || ref[n])) ok = 0;
+      }
+    }
+    if (ok) { der[p] = 1; ++nder; }
+  }
+  /* new box list: old boxes except children of derefined boxes, plus the
+   * children of refined leaves; their prolonged data computed on the old mesh */
+  int nnew = 0;
+  orc_ent *e = malloc(sizeof(orc_ent) * (size_t)(nb0 + 8 * nref));
+  double *pro = malloc(sizeof(double) * 3 * 512 * (size_t)(8 * nref + 1));
+  int npro = 0;
+  for (int b = 0; b < nb0; ++b) {
+    if (o->par[b] >= 0 && der[o->par[b]]) continue;
+    orc_ent x = {o->lev[b], o->ijk[3 * b], o->ijk[3 * b + 1], o->ijk[3 * b + 2], b, o->mort[b]};
+    e[nnew++] = x;
+    if (!ref[b]) continue;
+    int l = o->lev[b];
+    for (int c = 0; c < 8; ++c) {
+      int ci = 2 * o->ijk[3 * b] + (c & 1), cj = 2 * o->ijk[3 * b + 1] + ((c >> 1) & 1),
+          ck = 2 * o->ijk[3 * b + 2] + (c >> 2);
+      orc_ent y = {l + 1, ci, cj, ck, -1 - npro, morton(ci, cj, ck)};
+      e[nnew++] = y;
+      double *dst = pro + (size_t)3 * 512 * npro;
+      const int vars[3] = {V_PHI, V_NE, V_NI};
+      for (int v = 0; v < 3; ++v)
+        for (int kk = 0; kk < NC; ++kk)
+          for (int jj = 0; jj < NC; ++jj)
+            for (int ii = 0; ii < NC; ++ii) {
+              int G[3] = {ci * NC + ii, cj * NC + jj, ck * NC + kk};
+              int cc[3] = {G[0] >> 1, G[1] >> 1, G[2] >> 1};
+              double cval = cell_val(o, vars[v], l, cc), sum = cval;
+              for (int a = 0; a < 3; ++a) {
+                int q[3] = {cc[0], cc[1], cc[2]};
+                q[a] += (G[a] & 1) ? 1 : -1;
+                sum += v == 0 ? cell_val_bc(o, vars[v], l, q, cc, 0) : cell_val_mirror(o, vars[v], l, q, cc);
+              }
+              double val = 0.25 * sum;
+              if (v > 0 && val > 2.0 * cval) val = 2.0 * cval;
+              dst[(size_t)512 * v + ii + 8 * jj + 64 * kk] = val;
+            }
+      ++npro;
+    }
+  }
+  qsort(e, (size_t)nnew, sizeof(orc_ent), ent_cmp);
+  /* rebuild tables and fields */
+  int cap = o->cap > nnew ? o->cap : nnew;
+  int *lev = malloc(sizeof(int) * cap), *ijk = malloc(sizeof(int) * 3 * cap);
+  int *par = malloc(sizeof(int) * cap), *chl = malloc(sizeof(int) * 8 * cap);
+  int *nbr = malloc(sizeof(int) * 26 * cap);
+  uint64_t *mort = malloc(sizeof(uint64_t) * cap);
+  double *nv[NVAR];
+  for (int v = 0; v < NVAR; ++v) nv[v] = calloc((size_t)BS * cap, sizeof(double));
+  for (int b = 0; b < nnew; ++b) {
+    lev[b] = e[b].lev;
+    ijk[3 * b] = e[b].i; ijk[3 * b + 1] = e[b].j; ijk[3 * b + 2] = e[b].k;
+    mort[b] = e[b].key;
+    if (e[b].src >= 0) {
+      for (int v = 0; v < NVAR; ++v)
+        memcpy(nv[v] + (size_t)BS * b, o->v[v] + (size_t)BS * e[b].src, sizeof(double) * BS);
+    } else {
+      const double *src = pro + (size_t)3 * 512 * (-1 - e[b].src);
+      const int vars[3] = {V_PHI, V_NE, V_NI};
+      for (int v = 0; v < 3; ++v)
+        for (int c = 0; c < 512; ++c)
+          nv[vars[v]][(size_t)BS * b + IX(c & 7, (c >> 3) & 7, c >> 6)] = src[(size_t)512 * v + c];
+    }
+  }
+  free(o->lev); free(o->ijk); free(o->par); free(o->chl); free(o->nbr); free(o->mort);
+  for (int v = 0; v < NVAR; ++v) { free(o->v[v]); o->v[v] = nv[v]; }
+  o->lev = lev; o->ijk = ijk; o->par = par; o->chl = chl; o->nbr = nbr; o->mort = mort;
+  if (cap > o->cap) o->flux = realloc(o->flux, sizeof(double) * 3 * 9 * 64 * (size_t)cap);
+  o->cap = cap;
+  o->nbox = nnew;
+  int nlev = 0;
+  for (int b = 0; b < nnew; ++b) if (lev[b] + 1 > nlev) nlev = lev[b] + 1;
+  o->nlev = nlev;
+  for (int l = 0, b = 0; l <= nlev; ++l) {
+    while (b < nnew && lev[b] < l) ++b;
+    o->off[l] = b;
+  }
+  for (int l = nlev + 1; l <= MAXL + 1; ++l) o->off[l] = nnew;
+  for (int b = 0; b < nnew; ++b) {
+    par[b] = lev[b] ? find_box(o, lev[b] - 1, ijk[3 * b] >> 1, ijk[3 * b + 1] >> 1, ijk[3 * b + 2] >> 1) : -1;
+    for (int c = 0; c < 8; ++c)
+      chl[8 * b + c] = lev[b] + 1 < nlev ? find_box(o, lev[b] + 1, 2 * ijk[3 * b] + (c & 1),
+                                                    2 * ijk[3 * b + 1] + ((c >> 1) & 1), 2 * ijk[3 * b + 2] + (c >> 2))
+                                         : -2;
+    if (chl[8 * b] < 0)
+      for (int c = 0; c < 8; ++c) chl[8 * b + c] = -1;
+  }
+  for (int l = 0; l < nlev; ++l) set_neighbours(o, l);
+  free(e); free(pro); free(ref); free(der);
+  if (n_refined) *n_refined = nref;
+  if (n_derefined) *n_derefined = nder;
+  if (n_dropped) *n_dropped = ndrop;
+  return nref + nder;
 }

@@ -50,4 +50,8 @@ void orc_fluid_stage(orc *o, double dt);
 double orc_koren(double a, double b);
 double orc_lookup(const orc *o, int which, double e);
 void orc_coarse_solve(orc *o);
+void orc_refine_flags(orc *o, double c0, double c1, double c0_deref, double dx_deref,
+                      int buffer, int8_t *flags);
+int orc_regrid(orc *o, const int8_t *flags, int *n_refined, int *n_derefined,
+               int *n_dropped);
 #endif
