@@ -199,6 +199,41 @@ int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *re
  * top-level V-cycles including the last FMG one. */
 int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res);
 
+/* ---- refinement criterion and regridding (Sec. 2.5, Eq. 8) -------------- */
+
+/* Per-box flags from the stored |E| of the leaf cells (call after
+ * sm_compute_field).  Eq. 8 asks dx < c0 c1 / alpha(c1 |E|) of every cell,
+ * alpha from the coefficient table (linear interpolation, every operation
+ * rounded separately); a cell needs refinement where
+ * alpha(c1 |E|) dx >= c0 c1.  A leaf box gets +1 when one of its cells
+ * needs refinement, or a cell of a same-level leaf neighbour within
+ * `buffer` cells of it (Chebyshev distance) does, and its level is below
+ * the maximum; -1 (derefinable) when nothing marks it, every cell meets
+ * alpha(c1 |E|) dx < c0_deref c1, dx < dx_deref and it lies above the base
+ * grid; every other box 0.  The paper uses c0 = 1, c1 = 1.2, a buffer of 3
+ * cells, c0_deref = 1/8 and dx_deref = 30 um.
+ *   flags: HOST int8 [n_boxes] out, table order.  Synchronises.
+ * Errors: SM_EINVAL (buffer outside 0..8), SM_ESTATE (no octree, no table). */
+int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_deref, double dx_deref, int buffer,
+                    int8_t *flags);
+
+/* Regrid with per-box flags (HOST int8 [n_boxes], the layout of
+ * sm_refine_flags; only leaves and their parents are read).  Refinement:
+ * a leaf flagged > 0 below the maximum level gets 8 children when all 26
+ * neighbour positions of its level hold a box or lie outside the domain;
+ * other requests are dropped.  Derefinement: a box whose 8 children are
+ * leaves flagged < 0 loses them unless a non-sibling neighbour of a child
+ * has children or is refined in the same call.  Densities are restricted
+ * first; boxes are renumbered in (level, Morton) order; potential,
+ * right-hand side, |E|, rho and the current densities move with their
+ * boxes; new boxes get the potential and densities by the linear
+ * prolongation (c + c_sx + c_sy + c_sz)/4 of the parent's cells (densities
+ * limited to 2c, mirror ghosts at walls), other variables zero.  Tables,
+ * device pointers of sm_get_tables and captured solves are replaced.
+ * Out (may be NULL): refined boxes, derefined boxes, dropped requests.
+ * Synchronises.  Errors: SM_ESTATE (no octree), SM_ENOMEM (max_boxes). */
+int sm_regrid(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
+
 /* ---- field and fluid step (Sec. 2.3, 2.4) --------------------------------- */
 
 /* |E| on every leaf cell: face fields E = (phi_i - phi_{i+1})/dx, cell

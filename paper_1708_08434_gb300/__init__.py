@@ -62,6 +62,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs", "sm_set_pdl",
            "sm_set_persistent", "sm_persist_barrier_selftest",
            "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc", "sm_check_conversions",
+           "sm_refine_flags", "sm_regrid",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
            "sm_batch_set_graphs", "sm_batch_kernel_bench", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
@@ -116,6 +117,8 @@ def load():
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
         "sm_check_conversions": [C.c_longlong, C.c_ulonglong, P, P, P],
+        "sm_refine_flags": [P, D, D, D, D, I, P],
+        "sm_regrid": [P, P, pI, pI, pI],
         "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
         "sm_batch_destroy": [P],
         "sm_batch_arena_size": [P, C.POINTER(C.c_size_t)],
@@ -283,6 +286,21 @@ class Solver:
     def level_range(self, level: int):
         t = self._tables_raw()
         return t.level_offset[level], t.level_offset[level + 1]
+
+    # -- refinement criterion and regridding (Sec. 2.5, Eq. 8) --
+    def refine_flags(self, c0=1.0, c1=1.2, c0_deref=0.125, dx_deref=30e-6, buffer=3) -> np.ndarray:
+        """Per-box flags from the stored |E|: +1 refine, -1 derefinable, 0."""
+        f = np.zeros(self.n_boxes, np.int8)
+        self._ck(self._lib.sm_refine_flags(self._h, c0, c1, c0_deref, dx_deref, buffer, _hp(f)))
+        return f
+
+    def regrid(self, flags):
+        """Apply per-box flags; returns (refined, derefined, dropped)."""
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+        assert flags.shape == (self.n_boxes,)
+        r, d, x = C.c_int(), C.c_int(), C.c_int()
+        self._ck(self._lib.sm_regrid(self._h, _hp(flags), C.byref(r), C.byref(d), C.byref(x)))
+        return r.value, d.value, x.value
 
     # -- fields --
     def var(self, var: int):

@@ -368,7 +368,7 @@ __global__ void k_compact(int n, const int32_t *__restrict__ flag, const int32_t
   if (b < n && flag[b]) out[pos[b]] = b;
 }
 
-static int rebuild_leaves(sm_ctx *ctx) {
+int sm_rebuild_leaves(sm_ctx *ctx) {
   int n = ctx->n_boxes;
   k_mark_leaves<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->child, ctx->scan_a);
   ++ctx->n_launch;
@@ -387,6 +387,18 @@ static int rebuild_leaves(sm_ctx *ctx) {
   for (int l = 0; l <= ctx->n_levels; ++l) ctx->leaf_level_off[l] = h[l];
   ctx->n_leaves = h[ctx->n_levels];
   ctx->pdl_fence = true;  // level kernels read the new tables before their PDL wait
+  return SM_OK;
+}
+
+// neighbour tables (nbr, nbr6) of the boxes of level l from the level's
+// Morton-sorted range
+int sm_build_neighbours(sm_ctx *ctx, int l) {
+  const int lo = ctx->level_off[l], hi = ctx->level_off[l + 1];
+  const int cnt = (hi - lo) * 26;
+  if (cnt == 0) return SM_OK;
+  k_neighbours<<<(cnt + 255) / 256, 256, 0, ctx->stream>>>(lo, hi, l, ctx->ijk, ctx->morton, ctx->nbr, ctx->nbr6);
+  ++ctx->n_launch;
+  SM_CKL("neighbours");
   return SM_OK;
 }
 
@@ -417,7 +429,7 @@ extern "C" int sm_build_octree(sm_ctx *ctx, int *n_boxes) {
   ctx->n_boxes = n;
   ctx->n_levels = ctx->lbase + 1;
   for (int l = 0; l <= SM_MAX_LEVELS; ++l) ctx->level_off[l] = lo.off[l];
-  int st = rebuild_leaves(ctx);
+  int st = sm_rebuild_leaves(ctx);
   if (st) return st;
   if (n_boxes) *n_boxes = n;
   return SM_OK;
@@ -464,7 +476,7 @@ extern "C" int sm_refine_level(sm_ctx *ctx, int level, const int8_t *flags, int 
   ctx->n_boxes = hi;
   ctx->n_levels = level + 2;
   for (int l = level + 2; l <= SM_MAX_LEVELS; ++l) ctx->level_off[l] = hi;
-  return rebuild_leaves(ctx);
+  return sm_rebuild_leaves(ctx);
 }
 
 extern "C" int sm_get_tables(const sm_ctx *ctx, sm_tables *out) {

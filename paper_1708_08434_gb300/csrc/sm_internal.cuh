@@ -321,3 +321,5 @@ int sm_mg_fill_cf(sm_ctx *ctx, double *var, int level, int homog);
 int sm_fill_all_cf(sm_ctx *ctx, double *var);
 int sm_restrict_pair(sm_ctx *ctx, double *a, double *b);
 void sm_drop_graphs(sm_ctx *ctx);
+int sm_rebuild_leaves(sm_ctx *ctx);
+int sm_build_neighbours(sm_ctx *ctx, int level);
