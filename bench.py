@@ -379,6 +379,40 @@ def run_gpu(args):
                  "steps": nsteps, "gpu_launches": g.launch_count() - l0,
                  "schedule": "2 V-cycles per solve, 2 solves per Heun step, dt from the Sec. 2.4 limits "
                              "(host reads dt each step)"}
+    # refinement criterion (Eq. 8) and regridding on the benchmark mesh:
+    # flags with the paper's constants, then a regrid that changes the mesh
+    # (a stricter c0 refines), timed with CUDA events, and the way back
+    regrid = None
+    if not args.no_paper:
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        g.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+
+        def timed_ms(fn):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b), out
+
+        g.refine_flags()  # warm-up
+        fl_ms, flags = timed_ms(lambda: g.refine_flags())
+        nb0 = g.n_boxes
+        strict = g.refine_flags(0.25, 1.2, 0.125, 30e-6, 3)
+        room = (8192 - nb0) // 8 - 16            # the solver's max_boxes
+        strict[np.where(strict == 1)[0][max(room, 0):]] = 0
+        rg_ms, (nref, nder, ndrop) = timed_ms(lambda: g.regrid(strict))
+        nb1 = g.n_boxes
+        regrid = {"flags_ms": round(fl_ms, 3), "paper_flags": {"refine": int((flags == 1).sum()),
+                                                                "derefine": int((flags == -1).sum())},
+                  "regrid_ms": round(rg_ms, 3), "boxes": [nb0, nb1], "refined": nref, "derefined": nder,
+                  "dropped": ndrop, "criterion": "c0=0.25 (paper: 1), c1=1.2, buffer 3; flags with the paper's "
+                                                 "c0=1, c0_deref=1/8, dx_deref=30 um"}
     batched = None if args.no_batch else bench_batch(args, dev, world)
     learned = None if args.no_learned else bench_learned(args, dev, world)
     steps = args.steps
@@ -405,6 +439,7 @@ def run_gpu(args):
         "roofline": roof,
         "mixed_precision": mixed,
         "paper_schedule": paper,
+        "regrid": regrid,
         "batched": batched,
         "learned_warm_start": learned,
     }
