@@ -347,6 +347,44 @@ def run_gpu(args):
             "emag_max_rel": float((e32 - e64).abs().max() / e64.abs().max()),
             "reference": "FP64 path converged to 1e-12 (element-wise parity with the CPU oracle)"}
         gm.close()
+    # field (Sec. 2.3) and one Euler stage of the fluid update (Eq. 2-3, 6-7)
+    # against their rooflines: CUDA events around 20 calls each; the field
+    # call is the refinement-face fill + k_field, the stage is the face
+    # fill, the refinement fluxes, k_update and the density restriction
+    fluid = None
+    if not args.no_profile:
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        g.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+        dt = g.dt_limit(Q, E0)
+
+        def per_call(fn, n=20):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) * 1e3 / n
+
+        peak, _ = measured_peaks()
+        fus = per_call(g.compute_field)
+        sus = per_call(lambda: g.fluid_stage(dt))
+        fluid = {}
+        # FP64 instructions per leaf cell as counted by ncu on this workload
+        # (sm__inst_executed_pipe_fp64: k_field 27.4 with the FP64 square
+        # root of |E|, stage-1 k_update 112.8); bytes: compulsory traffic
+        for name, us, bpc, ipc in (("field (k_field)", fus, 16.0, 27.4), ("euler stage (k_update)", sus, 72.0, 112.8)):
+            fluid[name] = {"us": round(us, 2), "gbs": round(leaf_cells * bpc / (us * 1e-6) / 1e9, 1),
+                           "hbm_frac": round(leaf_cells * bpc / (us * 1e-6) / 1e9 / peak, 4),
+                           "fp64_ginstr": round(leaf_cells * ipc / (us * 1e-6) / 1e9, 1),
+                           "fp64_frac": round(leaf_cells * ipc / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4),
+                           "model_per_leaf_cell": {"bytes": bpc, "fp64_instr": ipc}}
     # the paper's schedule (Sec. 2.1.2, 2.4): one FMG solve, then Heun steps
     # with exactly two V-cycles per potential update and the time step from
     # the limits of Sec. 2.4
@@ -438,6 +476,7 @@ def run_gpu(args):
         "clocks": clocks,
         "roofline": roof,
         "mixed_precision": mixed,
+        "field_and_fluid": fluid,
         "paper_schedule": paper,
         "regrid": regrid,
         "batched": batched,
