@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-paper", action="store_true", help="skip the fixed 2-V-cycle (paper) schedule")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1e8-cell mesh (streamer9)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels from the host instead of CUDA graphs "
                          "(profilers cannot see kernels inside conditional graph nodes)")
@@ -58,7 +59,7 @@ def parse():
                     help="run V-cycles as one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the solver kernels without programmatic dependent launch")
-    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch"],
+    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch", "large"],
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
                          "schedule (small, fixed launch sequences for ncu captures)")
@@ -170,6 +171,79 @@ def run_batch_only(args):
     torch.cuda.synchronize()
     print(json.dumps({"mode": "batch", "solves": args.steps, "max_corrections": int(cyc.max())}), flush=True)
     b.close()
+
+
+def run_large(args):
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    print(json.dumps(large_mesh()), flush=True)
+
+
+def large_mesh():
+    """The largest mesh of the paper's runs (~1e8 cells, streamer9): FMG to
+    1e-8, one Heun step, and the FP64 V-cycle and smoother against their
+    rooflines; the same for the mixed-precision form (about 16 GB of device
+    memory per solver, one solver at a time)."""
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    Q, E0 = synth.E_CHARGE, synth.EPS0
+    dom, st = synth.workload("streamer9")
+    out = {"mode": "large", "workload": "streamer9"}
+    ne = ni = None
+    for prec, name in ((0, "fp64"), (pkg.MIXED, "mixed")):
+        t0 = time.perf_counter()
+        g = pkg.Solver(dom, max_boxes=1 << 18, precision=prec)
+        g.build_octree()
+        synth.refine_all(dom, st, g.level_ijk, g.refine_level)
+        g.set_table(synth.coefficient_table())
+        if ne is None:
+            t = g.tables()
+            ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+            out["boxes"], out["leaf_cells"], out["levels"] = g.n_boxes, g.n_leaves * 512, g.n_levels
+        g.upload(pkg.NE, ne)
+        g.upload(pkg.NI, ni)
+        g.charge_rhs(Q, E0)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+
+        def ev(fn):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(g.stream)
+            r = fn()
+            b.record(g.stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b), r
+
+        g.fmg(TOL, MAX_CYCLES)  # warm-up (captures the graphs)
+        g.charge_rhs(Q, E0)
+        fmg_ms, (rc, rel, cyc) = ev(lambda: g.fmg(TOL, MAX_CYCLES))
+        g.compute_field()
+        dt = g.dt_limit(Q, E0)
+        step_ms, (rc2, dtn, c1, c2) = ev(lambda: g.advance(dt, Q, E0, TOL, MAX_CYCLES))
+        r = {"setup_s": round(setup_s, 1), "fmg_ms": round(fmg_ms, 2), "fmg_cycles": cyc,
+             "heun_step_ms": round(step_ms, 2), "step_cycles": [c1, c2],
+             "solves_per_s": round(3 / ((fmg_ms + step_ms) * 1e-3), 3)}
+        peak, _ = measured_peaks()
+        kc = pkg.K_VCYCLE if prec == 0 else pkg.K_VCYCLE32
+        us, n, by, fl = g.kernel_bench(kc, 5)
+        r["vcycle"] = {"us": round(us, 1), "bytes": int(by), "hbm_frac": round(by / (us * 1e-6) / 1e9 / peak, 4)}
+        if fl:
+            r["vcycle"]["fp64_frac"] = round(fl / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4)
+        if prec == 0:
+            us, n, by, fl = g.kernel_bench(pkg.K_SMOOTH, 5)
+            r["k_rbgs"] = {"avg_launch_us": round(us, 2), "launches": n,
+                           "fp64_frac": round(fl / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4),
+                           "hbm_frac": round(by / (us * 1e-6) / 1e9 / peak, 4)}
+        out[name] = r
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_gpu(args):
@@ -451,6 +525,7 @@ def run_gpu(args):
                   "regrid_ms": round(rg_ms, 3), "boxes": [nb0, nb1], "refined": nref, "derefined": nder,
                   "dropped": ndrop, "criterion": "c0=0.25 (paper: 1), c1=1.2, buffer 3; flags with the paper's "
                                                  "c0=1, c0_deref=1/8, dx_deref=30 um"}
+    large = None if (args.no_large or rank != 0) else large_mesh()
     batched = None if args.no_batch else bench_batch(args, dev, world)
     learned = None if args.no_learned else bench_learned(args, dev, world)
     steps = args.steps
@@ -478,6 +553,7 @@ def run_gpu(args):
         "mixed_precision": mixed,
         "field_and_fluid": fluid,
         "paper_schedule": paper,
+        "large_mesh": large,
         "regrid": regrid,
         "batched": batched,
         "learned_warm_start": learned,
@@ -702,6 +778,8 @@ def main():
         run_reference(args)
     elif args.mode == "batch":
         run_batch_only(args)
+    elif args.mode == "large":
+        run_large(args)
     else:
         run_gpu(args)
 

@@ -144,6 +144,8 @@ def workload(name: str):
     uniform64     : unit cube, 64^3 cells as 512 boxes, Gaussian charge + noise
     streamer6     : 16 mm cube, base 64^3, 6 refinement levels, ~2.4e6 cells
     streamer8     : 16 mm cube, base 64^3, 8 refinement levels, ~1.7e7 cells
+    streamer9     : 16 mm cube, base 128^3, 9 refinement levels, ~1.0e8 cells
+                    (finest spacing 0.24 um; 226569 boxes)
     streamer_small: 16 mm cube, base 16^3, 3 refinement levels (test size)
     streamer_tiny : 16 mm cube, base 16^3, 1 refinement level (dense-solve size)
     """
@@ -157,6 +159,9 @@ def workload(name: str):
     if name == "streamer8":
         st = Streamer(refine_c=16.0, refine_tip=12e-3)
         return domain_streamer(8, 8, st), st
+    if name == "streamer9":
+        st = Streamer(refine_c=25.0, refine_tip=12.5e-3)
+        return domain_streamer(16, 9, st), st
     if name == "streamer_small":
         st = Streamer(refine_c=2.0, refine_tip=6e-3)
         return domain_streamer(2, 3, st), st
