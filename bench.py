@@ -75,6 +75,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, dev=None) -> float:
+    """Max of a per-rank float over all ranks of the initialised process
+    group (NCCL on GPUs, gloo in the CPU tests); the value itself on one
+    process.  Replicas are timed by their slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units per second of the whole job: every rank's units over the time
+    of the slowest rank (weak scaling: the per-rank work is fixed)."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -336,15 +355,10 @@ def run_gpu(args):
     clocks = clk.stop()
     if world > 1:
         dist.barrier()
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev)
     # end to end through the C ABI with host buffers (H2D + D2H every step)
     e2e_ms, _, _ = timed(args.steps, host_io=True)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
     # roofline of the dominant kernel: the red-black smoother, timed with
     # CUDA events around a graph of its launches in the V-cycle mix (every
     # level, both colours), or with --persistent the persistent V-cycle
@@ -390,10 +404,7 @@ def run_gpu(args):
             step_m()
         torch.cuda.synchronize()
         mms, mcyc, mlaunch = timed_m(args.steps)
-        if world > 1:
-            tt = torch.tensor([mms], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            mms = float(tt.item())
+        mms = max_over_ranks(mms, dev)
         mixed = {"value": round(SOLVES_PER_STEP * args.steps * world / (mms * 1e-3), 3),
                  "unit": "solves/s", "ms_per_step": round(mms / args.steps, 4),
                  "corrections_per_step": mcyc / args.steps, "gpu_launches": mlaunch,
@@ -530,8 +541,8 @@ def run_gpu(args):
     learned = None if args.no_learned else bench_learned(args, dev, world)
     steps = args.steps
     solves = SOLVES_PER_STEP * steps * world
-    value = solves / (ms * 1e-3)
-    e2e_value = solves / (e2e_ms * 1e-3)
+    value = whole_job_rate(SOLVES_PER_STEP * steps, world, ms)
+    e2e_value = whole_job_rate(SOLVES_PER_STEP * steps, world, e2e_ms)
     mcell_vc = leaf_cells * cycles * world / (ms * 1e-3) / 1e6
     res = {
         "metric": "Poisson solves/s to rel residual 1e-8 (octree FMG + Heun step, 3 solves/step)",
@@ -675,10 +686,7 @@ def bench_batch(args, dev, world):
         assert rc == 0, rc
         total += e0.elapsed_time(e1)
         cycles += int(cyc.max())
-    if world > 1:
-        tt = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(total, dev)
     cells, levels, launches = b.info()
     # per-kernel rooflines of the cycle (after the timed solves: the bench
     # launches overwrite the error arrays)
