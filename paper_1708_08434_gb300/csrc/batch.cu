@@ -154,6 +154,8 @@ __device__ __forceinline__ float wall_w(const Bc &bc, int a, int v, int N) {
 // FP64 potential: phi += (double)e.
 // Ring use at step p: planes p-2 .. p+1 are read, p+2 .. p+4 are in flight,
 // and plane p+5 is issued into the slot of plane p-3 (last read at step p-1).
+// The slots of planes -1 and N are zero-filled, so every update adds six
+// staged neighbours (the wall ghosts come in through the coefficient w).
 __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, int ncols, int k,
                                                  const BSolve *__restrict__ tab,
                                                  const unsigned char *__restrict__ active,
@@ -198,8 +200,23 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
         cdst[u] = ise ? smem_u32(&se[0][r * RW + c4]) : smem_u32(&sf[0][r * RW + c4]);
       }
     }
+    // error-plane copies into slot sl that only zero-fill it (planes -1 and
+    // N, the z neighbours beyond the grid, whose terms are then exact zeros)
+    auto zero_slot = [&](int sl) {
+      if (vec) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (chas[u] && cise[u])
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;\n" ::"r"(cdst[u] + (unsigned)sl * (EPL * 4u)),
+                         "l"(ev)
+                         : "memory");
+      } else {
+        for (int i = t; i < EPL; i += CT) cp_async<4>(&se[sl][i], ev, false);
+      }
+    };
     // copies of plane z (if it exists) as one commit group
     auto issue = [&](int z) {
+      if (z == N) zero_slot(z & (RING - 1));
       if (z < N) {
         const int sl = z & (RING - 1);
         const float *ez = ev + z * NN, *fz = fv + z * NN;
@@ -233,18 +250,18 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
       cp_commit();
     };
     // Gauss-Seidel update of the staged cell at e-plane index q (rhs index
-    // qf) of plane z: lo/hi tell whether planes z-1/z+1 exist, w is the
+    // qf) of the plane held in pz, with the planes below / above it in pm /
+    // pp (zero planes beyond the grid) and its rhs plane in fz; w is the
     // cell's wall coefficient
-    auto update = [&](int z, int q, int qf, float w, bool lo, bool hi) {
-      float *pz = se[z & (RING - 1)];
+    auto update = [&](float *pz, const float *pm, const float *pp, const float *fz, int q, int qf, float w) {
       const float c = pz[q];
       float s = pz[q - 1] + pz[q + 1];
       s += pz[q - RW];
       s += pz[q + RW];
-      if (lo) s += se[(z - 1) & (RING - 1)][q];
-      if (hi) s += se[(z + 1) & (RING - 1)][q];
+      s += pm[q];
+      s += pp[q];
       s = fmaf(w, c, s);
-      pz[q] = (s - h2 * sf[z & (RING - 1)][qf]) * (1.0f / 6.0f);
+      pz[q] = (s - h2 * fz[qf]) * (1.0f / 6.0f);
     };
     // this thread's two column cells (rows ya, ya+1) and its ring cell
     const int x = x0 + tx, ya = y0 + ty2;
@@ -264,26 +281,29 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
     const float rw = rin ? wall_w(bc, 0, rx, N) + wall_w(bc, 1, ry, N) : 0.f;
     const long long row0 = (long long)ya * N + x;
     __syncthreads();  // the previous column's planes are no longer read
+    zero_slot((-1) & (RING - 1));                 // plane -1, landing with plane 0's group
 #pragma unroll
     for (int z = 0; z < RING - 3; ++z) issue(z);  // planes 0 .. RING-4
     for (int p = 0; p <= N; ++p) {
       cp_wait<RING - 5>();  // this thread's copies of planes <= p+1 have landed
       __syncthreads();      // everyone's have; step p-1's reads of plane p-3 are done
       issue(p + RING - 3);
+      float *Pm2 = se[(p - 2) & (RING - 1)], *Pm1 = se[(p - 1) & (RING - 1)], *P0 = se[p & (RING - 1)],
+            *Pp1 = se[(p + 1) & (RING - 1)];
       if (p < N) {  // colour 0 on plane p: one column cell per thread, and the ring
-        const bool lo = p > 0, hi = p < N - 1;
         const float wz = wall_w(bc, 2, p, N);
+        const float *F0 = sf[p & (RING - 1)];
         if (in) {
           const int o = (x + ya + p) & 1;  // row offset of the colour-0 cell
-          update(p, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wz, lo, hi);
+          update(P0, Pm1, Pp1, F0, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wz);
         }
-        if (rin && !((rx + ry + p) & 1)) update(p, rq, rqf, rw + wz, lo, hi);
+        if (rin && !((rx + ry + p) & 1)) update(P0, Pm1, Pp1, F0, rq, rqf, rw + wz);
       }
       __syncthreads();
       if (p >= 1 && in) {  // colour 1 on plane p-1, then store both cells
         const int z = p - 1, o = ((x + ya + z) & 1) ^ 1;
-        update(z, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wall_w(bc, 2, z, N), z > 0, z < N - 1);
-        const float v0 = se[z & (RING - 1)][q0], v1 = se[z & (RING - 1)][q0 + RW];
+        update(Pm1, Pm2, P0, sf[z & (RING - 1)], q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wall_w(bc, 2, z, N));
+        const float v0 = Pm1[q0], v1 = Pm1[q0 + RW];
         const long long g = z * NN + row0;
         if (pv) {
           const double *ph = sph[z & (RING - 1)];
