@@ -631,8 +631,9 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
         }
         const double s = ((xm + xp) + (ym + yp)) + (zm + zp);
         const double r = fma(-fma(-6.0, c, s), inv_h2, o ? f1 : f0);
-        f32[o32 + p * NN + row0 + o * N] = cvt_f64_f32_rn(r);
-        const unsigned long long a = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+        const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+        f32[o32 + p * NN + row0 + o * N] = cvt_bits_f32_rn(rb);
+        const unsigned long long a = rb & 0x7fffffffffffffffull;
         m = a > m ? a : m;
       }
       if (p + 2 < N) {  // this set's next plane

@@ -192,42 +192,73 @@ __device__ __forceinline__ int fcell(int a, int i, int j, int k) {
 // no-op for a normal launch)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// Conversions between IEEE-754 binary64 and binary32 done with 32-bit
-// integer operations on the bit fields.  On this GPU the hardware
-// conversion instructions share the narrow FP64 pipe (at a fraction of the
-// fused multiply-add rate), so FP64 kernels that convert every cell lose
-// most of their FP64 throughput to them.  Normal results take the integer
-// path; zeros, subnormals, infinities and NaNs fall back to the hardware
-// conversion.  Both agree bit for bit with the hardware (checked by
-// sm_check_conversions).
+// Conversions between IEEE-754 binary64 and binary32 done with integer
+// operations on the bit fields.  On this GPU the hardware conversion
+// instructions share the narrow FP64 pipe, so FP64 kernels that convert
+// every cell lose FP64 throughput to them (and a hardware fallback on a
+// rare path is still issued for every cell once the compiler turns the
+// branch into a select).  Every class -- normal, subnormal, zero, infinity,
+// NaN -- is handled here; the results equal the hardware's bit for bit
+// (checked by sm_check_conversions; NaNs compared as NaNs).
 //
-// binary64 -> binary32, round to nearest, ties to even: keep the top 23 of
-// the 52 fraction bits, round on the 29 dropped bits; a carry out of the
-// fraction increments the exponent field (and reaches the infinity
-// encoding on overflow), which is the correctly rounded result.
-__device__ __forceinline__ float cvt_f64_f32_rn(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+// binary64 bit pattern -> binary32, round to nearest, ties to even: the
+// significand (with its hidden bit) is shifted right to the binary32
+// position -- 29 bits for normal results, more for subnormal ones -- and
+// rounded on the dropped bits; a carry into the exponent field is the
+// correctly rounded result, up to the infinity encoding on overflow.
+__device__ __forceinline__ float cvt_bits_f32_rn(unsigned long long b) {
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e >= 1 && e <= 254) {
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int fe = e - 1023 + 127;
+  if (fe >= 1 && fe <= 254) {  // normal binary32 result
     const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned rem = lo & 0x1fffffffu;
-    unsigned r = ((unsigned)e << 23) | m;
+    unsigned r = ((unsigned)fe << 23) | m;
     r += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
-    return __uint_as_float(r | (hi & 0x80000000u));
+    return __uint_as_float(r | sign);
   }
-  return __double2float_rn(d);
+  if (e == 0x7ff) {  // infinity or NaN (quiet, top payload bits kept)
+    const unsigned long long frac = b & 0x000fffffffffffffull;
+    return __uint_as_float(sign | (frac ? 0x7fc00000u | (unsigned)(frac >> 29) : 0x7f800000u));
+  }
+  if (fe > 254) return __uint_as_float(sign | 0x7f800000u);  // overflow
+  if (e == 0) return __uint_as_float(sign);                    // binary64 zero or subnormal
+  // subnormal or zero binary32 result: significand 1.f shifted by 29 + (1 - fe)
+  const int ts = 30 - fe;
+  if (ts > 54) return __uint_as_float(sign);
+  const unsigned long long M = (b & 0x000fffffffffffffull) | (1ull << 52);
+  const unsigned long long q = M >> ts, rem = M & ((1ull << ts) - 1ull), half = 1ull << (ts - 1);
+  const unsigned r = (unsigned)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
+  return __uint_as_float(sign | r);
+}
+__device__ __forceinline__ float cvt_f64_f32_rn(double d) {
+  return cvt_bits_f32_rn((unsigned long long)__double_as_longlong(d));
 }
 
-// binary32 -> binary64 (exact): re-bias the exponent, widen the fraction
+// binary32 -> binary64 (exact): re-bias the exponent and widen the
+// fraction; subnormals are normalised, infinities and NaNs keep their
+// class (NaNs quiet)
 __device__ __forceinline__ double cvt_f32_f64(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, frac = u & 0x7fffffu;
+  unsigned hi, lo;
   if (e != 0u && e != 255u) {
-    const unsigned hi = (u & 0x80000000u) | ((e + 1023u - 127u) << 20) | ((u & 0x7fffffu) >> 3);
-    return __hiloint2double((int)hi, (int)(u << 29));
+    hi = sign | ((e + 1023u - 127u) << 20) | (frac >> 3);
+    lo = u << 29;
+  } else if (e == 255u) {
+    hi = sign | 0x7ff00000u | (frac ? 0x00080000u : 0u) | (frac >> 3);
+    lo = frac << 29;
+  } else if (frac == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else {  // subnormal: value frac * 2^-149; normalise the leading one to bit 23
+    const int lz = __clz(frac) - 8;  // shifts that bring the leading one to bit 23
+    const unsigned m = (frac << lz) & 0x7fffffu;
+    hi = sign | ((unsigned)(1023 - 126 - lz) << 20) | (m >> 3);
+    lo = m << 29;
   }
-  return (double)f;
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // atomic max of a non-negative double through its bit pattern
