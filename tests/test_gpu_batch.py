@@ -87,6 +87,27 @@ def test_batch_odd_and_unaligned_sizes():
     b.close()
 
 
+@pytest.mark.parametrize("nu1,nu2", [(3, 1), (1, 3)])
+def test_batch_odd_sweep_counts(nu1, nu2):
+    """Odd numbers of sweeps: the error ends in the second buffer and is
+    copied back (pre-smoothing), or the last level-0 sweep is an odd one
+    (post-smoothing); same exact-solution bound."""
+    import torch
+    import paper_1708_08434_gb300 as pkg
+    sides = [32, 40, 16, 56]
+    b = pkg.Batch(sides, 1.0, BCT, BCV, nu1=nu1, nu2=nu2)
+    blobs = synth.batch_blobs(len(sides) + 9)[9:]
+    rhos = {}
+    for s, n in enumerate(sides):
+        rhos[s] = synth.blob_rho(int(n), blobs[s])
+        b.grid(b.rhs, s).copy_(torch.from_numpy(-rhos[s]))
+    b.phi.zero_()
+    rc, cyc, rel = b.solve(1e-9, 60)
+    assert rc == 0 and np.all(rel <= 1e-9)
+    check(b, rhos, range(len(sides)), 1e-7)
+    b.close()
+
+
 def test_batch_autotune_keeps_results():
     sides = [40, 48, 32, 56]
     b, rhos = make_batch(sides, seed_blobs=3)
