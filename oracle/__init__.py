@@ -38,7 +38,10 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
            "-o", tmp, src, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP over boxes when the compiler has it; plain loops otherwise
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:],
+                      stderr=subprocess.DEVNULL).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -91,8 +94,22 @@ def _load():
         lib.orc_refine_flags.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, P]
         lib.orc_regrid.argtypes = [P, P, ip, ip, ip]
         lib.orc_regrid.restype = C.c_int
+        lib.orc_set_threads.argtypes = [C.c_int]
+        lib.orc_set_threads.restype = C.c_int
+        lib.orc_set_threads(1)
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the per-box loops (1 at load; results do not depend on
+    it).  Returns the count in effect, 1 if built without OpenMP."""
+    return _load().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    """Threads the per-box loops use now."""
+    return _load().orc_set_threads(0)
 
 
 def koren(a: float, b: float) -> float:

@@ -24,6 +24,15 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* OpenMP over the boxes of one pass (Sec. 2.1.3: with one ghost layer per
+ * box, the boxes of a pass are independent).  Each box writes only its own
+ * cells and ghosts, and the only reductions are maxima, so every result is
+ * bit-identical for any thread count. */
+#define BOXES_PAR _Pragma("omp parallel for schedule(static)")
 
 #define NC 8                 /* cells per box side (Sec. 2.1.1, N = 8) */
 #define GH 2                 /* ghost layers stored */
@@ -192,6 +201,18 @@ void orc_destroy(orc *o) {
   free(o);
 }
 
+/* threads used by the box loops (1 when built without OpenMP); returns the
+ * count now in effect */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 int orc_n_boxes(const orc *o) { return o->nbox; }
 int orc_n_levels(const orc *o) { return o->nlev; }
 int orc_level_offset(const orc *o, int l) { return (l >= 0 && l <= o->nlev) ? o->off[l] : -1; }
@@ -311,6 +332,7 @@ static void face_cell(int f, int t, int u, int w, int c[3]) {
  * linear interpolation of the coarse cell c containing the ghost and its
  * two tangential coarse neighbours on the ghost's side. */
 static void fill_ghosts_phi(orc *o, int var, int l, int homog) {
+  BOXES_PAR
   for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
     double *p = box(o, var, b);
     for (int f = 0; f < 6; ++f) {
@@ -350,6 +372,7 @@ static void fill_ghosts_phi(orc *o, int var, int l, int homog) {
 /* Density ghosts, depth 2 (Sec. 2.3: two fine ghost values at refinement
  * boundaries for the Koren stencil, limited to twice the coarse value). */
 static void fill_ghosts_density(orc *o, int var, int l) {
+  BOXES_PAR
   for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
     double *p = box(o, var, b);
     for (int f = 0; f < 6; ++f) {
@@ -393,6 +416,7 @@ static void fill_ghosts_density(orc *o, int var, int l) {
 /* |E| ghosts, depth 1: same-level copy, Neumann at walls, and the value of
  * the coarse cell containing the ghost at refinement boundaries. */
 static void fill_ghosts_emag(orc *o, int l) {
+  BOXES_PAR
   for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
     double *p = box(o, V_EMAG, b);
     for (int f = 0; f < 6; ++f) {
@@ -437,6 +461,7 @@ static void smooth(orc *o, int l, int nu) {
   for (int s = 0; s < nu; ++s)
     for (int color = 0; color < 2; ++color) {
       fill_ghosts_phi(o, V_PHI, l, 0);
+      BOXES_PAR
       for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
         double *p = box(o, V_PHI, b), *f = box(o, V_RHS, b);
         for (int k = 0; k < NC; ++k)
@@ -463,6 +488,7 @@ static void residual_box(orc *o, int var_phi, int b, double *r) {
 /* average of the 8 children (cell-centred full weighting), for every box of
  * level l-1 that has children */
 static void restrict_level(orc *o, int l, int src, int dst) {
+  BOXES_PAR
   for (int pb = o->off[l - 1]; pb < o->off[l]; ++pb) {
     if (is_leaf(o, pb)) continue;
     double *d = box(o, dst, pb);
@@ -486,6 +512,7 @@ static void restrict_level(orc *o, int l, int src, int dst) {
  * the direction of the fine cell's offset.  add=1 adds it (correction),
  * add=0 overwrites (full solution in FMG). */
 static void prolong_level(orc *o, int l, int src, int dst, int homog, int add) {
+  BOXES_PAR
   for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
     double *d = box(o, dst, b);
     for (int k = 0; k < NC; ++k)
@@ -588,13 +615,16 @@ static void vcycle(orc *o, int top, int nu1, int nu2) {
   for (int l = top; l >= 1; --l) {
     smooth(o, l, nu1);
     fill_ghosts_phi(o, V_PHI, l, 0);
+    BOXES_PAR
     for (int b = o->off[l]; b < o->off[l + 1]; ++b) residual_box(o, V_PHI, b, box(o, V_RES, b));
     restrict_level(o, l, V_PHI, V_PHI);
+    BOXES_PAR
     for (int b = o->off[l - 1]; b < o->off[l]; ++b)
       memcpy(box(o, V_OLD, b), box(o, V_PHI, b), sizeof(double) * BS);
     restrict_level(o, l, V_RES, V_RHS);
     fill_ghosts_phi(o, V_PHI, l - 1, 0);
     double h2 = spacing(o, l - 1) * spacing(o, l - 1);
+    BOXES_PAR
     for (int b = o->off[l - 1]; b < o->off[l]; ++b) {
       if (is_leaf(o, b)) continue;
       double *p = box(o, V_PHI, b), *f = box(o, V_RHS, b);
@@ -606,6 +636,7 @@ static void vcycle(orc *o, int top, int nu1, int nu2) {
   }
   orc_coarse_solve(o);
   for (int l = 1; l <= top; ++l) {
+    BOXES_PAR
     for (int b = o->off[l - 1]; b < o->off[l]; ++b) {
       double *t = box(o, V_TMP, b), *p = box(o, V_PHI, b), *q = box(o, V_OLD, b);
       for (int c = 0; c < BS; ++c) t[c] = p[c] - q[c];
@@ -617,11 +648,13 @@ static void vcycle(orc *o, int top, int nu1, int nu2) {
 
 /* max over leaf cells (boxes without children, or on level top) of |r| */
 static double leaf_resmax(orc *o, int var_phi, int top) {
-  double m = 0.0, r[BS];
+  double m = 0.0;
   for (int l = 0; l <= top; ++l) {
     fill_ghosts_phi(o, var_phi, l, 0);
+#pragma omp parallel for schedule(static) reduction(max : m)
     for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
       if (!is_leaf(o, b) && l != top) continue;
+      double r[BS];
       residual_box(o, var_phi, b, r);
       for (int k = 0; k < NC; ++k)
         for (int j = 0; j < NC; ++j)
@@ -692,6 +725,7 @@ void orc_composite_residual(orc *o) {
   for (int l = top; l >= 1; --l) restrict_level(o, l, V_PHI, V_PHI);
   for (int l = 0; l <= top; ++l) {
     fill_ghosts_phi(o, V_PHI, l, 0);
+    BOXES_PAR
     for (int b = o->off[l]; b < o->off[l + 1]; ++b)
       if (is_leaf(o, b)) residual_box(o, V_PHI, b, box(o, V_RES, b));
   }
@@ -699,6 +733,7 @@ void orc_composite_residual(orc *o) {
 
 /* Eq. 5 right-hand side on leaf cells: f = -q (n_i - n_e)/eps, or -rho/eps */
 void orc_charge_rhs(orc *o, double q, double eps, int use_rho) {
+  BOXES_PAR
   for (int b = 0; b < o->nbox; ++b) {
     if (!is_leaf(o, b)) continue;
     double *f = box(o, V_RHS, b), *ne = box(o, V_NE, b), *ni = box(o, V_NI, b), *rho = box(o, V_RHO, b);
@@ -732,6 +767,7 @@ void orc_compute_field(orc *o) {
   for (int l = 0; l < o->nlev; ++l) {
     fill_ghosts_phi(o, V_PHI, l, 0);
     double h = spacing(o, l);
+    BOXES_PAR
     for (int b = o->off[l]; b < o->off[l + 1]; ++b) {
       double *p = box(o, V_PHI, b), *em = box(o, V_EMAG, b);
       for (int k = 0; k < NC; ++k)
@@ -793,6 +829,7 @@ static double *fluxp(orc *o, int b, int a) { return o->flux + ((size_t)b * 3 + a
  * is the face between cells m-1 and m along axis a, u,w the tangential
  * coordinates along axes (a+1)%3, (a+2)%3. */
 static void leaf_fluxes(orc *o, int var_n) {
+  BOXES_PAR
   for (int b = 0; b < o->nbox; ++b) {
     if (!is_leaf(o, b)) continue;
     double h = spacing(o, o->lev[b]);
@@ -826,6 +863,7 @@ static void leaf_fluxes(orc *o, int var_n) {
   }
   /* refinement boundaries: a coarse leaf face next to a refined box takes
    * the mean of the four fine face fluxes (conservation, Sec. 2.3) */
+  BOXES_PAR
   for (int b = 0; b < o->nbox; ++b) {
     if (!is_leaf(o, b)) continue;
     for (int f = 0; f < 6; ++f) {
@@ -871,6 +909,7 @@ static void euler_stage(orc *o, int sne, int sni, int dne, int dni, double dt) {
     fill_ghosts_emag(o, l);
   }
   leaf_fluxes(o, sne);
+  BOXES_PAR
   for (int b = 0; b < o->nbox; ++b) {
     if (!is_leaf(o, b)) continue;
     double h = spacing(o, o->lev[b]);
@@ -910,6 +949,7 @@ void orc_fluid_stage(orc *o, double dt) {
 double orc_dt_limit(orc *o, double q, double eps) {
   double m_adv = 0.0, m_ad = 0.0, m_drt = 0.0;
   for (int l = 0; l < o->nlev; ++l) fill_ghosts_phi(o, V_PHI, l, 0);
+#pragma omp parallel for schedule(static) reduction(max : m_adv, m_ad, m_drt)
   for (int b = 0; b < o->nbox; ++b) {
     if (!is_leaf(o, b)) continue;
     double h = spacing(o, o->lev[b]);

@@ -22,6 +22,10 @@ enum { ORC_PHI = 0, ORC_RHS = 1, ORC_RES = 2, ORC_NE = 3, ORC_NI = 4,
 orc *orc_create(double length, const double *origin, int nb, int max_level,
                 const int *bc_type, const double *bc_val);
 void orc_destroy(orc *o);
+/* OpenMP threads for the per-box loops (n >= 1; n < 1 only queries).
+ * Returns the count in effect; 1 when the library was built without
+ * OpenMP.  Results do not depend on it. */
+int orc_set_threads(int n);
 int orc_n_boxes(const orc *o);
 int orc_n_levels(const orc *o);
 int orc_level_offset(const orc *o, int level);

@@ -1,0 +1,58 @@
+"""The oracle's per-box loops run under OpenMP (Sec. 2.1.3: one ghost layer
+per box makes the boxes of a pass independent).  Every result must be
+bit-identical for any thread count: each box writes only its own cells and
+ghosts, and the only cross-box reductions are maxima."""
+import numpy as np
+
+import oracle
+import synth
+
+Q, EPS0 = synth.E_CHARGE, synth.EPS0
+
+
+def run_path(threads):
+    """FMG solve, field, time-step limit, one Heun step (two more solves),
+    refinement flags and a regrid on the small streamer mesh."""
+    used = oracle.set_threads(threads)
+    try:
+        dom, st = synth.workload("streamer_small")
+        o = oracle.build_mesh(dom, st)
+        o.set_table(synth.coefficient_table())
+        t = o.tables()
+        ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+        o.set(oracle.NE, ne)
+        o.set(oracle.NI, ni)
+        o.charge_rhs(Q, EPS0)
+        out = {"fmg": o.fmg(1e-8, 40)}
+        o.compute_field()
+        dt = o.dt_limit(Q, EPS0)
+        out["dt"] = dt
+        out["advance"] = o.advance(dt, Q, EPS0, 1e-8, 40)
+        for var in (oracle.PHI, oracle.NE, oracle.NI, oracle.EMAG):
+            out[var] = o.get(var)
+        flags = o.refine_flags(100.0, 100.0, 1.0, 1)
+        out["flags"] = flags
+        out["regrid"] = o.regrid(flags)
+        out["phi_after"] = o.get(oracle.PHI)
+        out["ne_after"] = o.get(oracle.NE)
+        return used, out
+    finally:
+        oracle.set_threads(1)
+
+
+def test_results_do_not_depend_on_thread_count():
+    used1, a = run_path(1)
+    used4, b = run_path(4)
+    assert used1 == 1
+    # a build without OpenMP runs one thread; the comparison still holds
+    assert used4 in (1, 4)
+    assert a.keys() == b.keys()
+    for key in a:
+        if isinstance(a[key], np.ndarray):
+            assert np.array_equal(a[key], b[key]), key
+        else:
+            assert a[key] == b[key], key
+    # the step solved and the regrid changed the mesh, so the comparison
+    # covered every loop
+    assert a["advance"][0] == 0 and a["advance"][2] > 0
+    assert a["regrid"][0] + a["regrid"][1] > 0
