@@ -358,7 +358,9 @@ int sm_batch_ptrs(const sm_batch *b, double **phi, double **rhs, long long *offs
 /* Solve every problem from its current phi until its relative residual
  * max|f - L phi| / max|f - L 0| <= tol or max_cycles corrections.  Out
  * (host arrays of n_solves, may be NULL): corrections and final relative
- * residual per solve.  SM_ENOCONV if a solve missed tol. Synchronises. */
+ * residual per solve.  SM_ENOCONV if a solve missed tol. Synchronises.
+ * A solve whose phi is all +0 on entry reuses the residual of phi = 0
+ * (computed for the denominator) as its first residual. */
 int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycles, double *rel_res);
 /* Autotuner: times `iters` corrections from phi = 0 for every candidate
  * restriction tile shape (8x8x8, 16x8x4, 32x4x4, 32x8x2

@@ -669,6 +669,73 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
   }
 }
 
+// Residual of phi = 0 on the finest grid of every solve flagged in `active`
+// (the denominators of the relative residual): r0 = f - L0, where L0 has
+// only the Dirichlet ghosts 2g of wall faces.  A cell with no Dirichlet face
+// takes f with no FP64 work (-(+0) * h^-2 + f = f bit for bit); the others
+// evaluate the same expression as k_bt_outer with every value +0, so both
+// kernels give the same bits for a potential that is all +0.  Also flags
+// (nz) the solves whose stored potential is not all +0.
+__global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols, int ncols,
+                                                  const BSolve *__restrict__ tab,
+                                                  const unsigned char *__restrict__ active,
+                                                  const double *__restrict__ phi,
+                                                  const double *__restrict__ f64, float *__restrict__ f32, Bc bc,
+                                                  unsigned long long *__restrict__ num,
+                                                  unsigned *__restrict__ nz) {
+  __shared__ unsigned long long red[CT / 32];
+  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    const int4 C = cols[it];
+    if (!active[C.x]) continue;  // uniform per block
+    const BSolve &S = tab[C.x];
+    const int N = S.N[0];
+    const long long o64 = S.off64, o32 = S.off[0], NN = (long long)N * N;
+    const double inv_h2 = S.inv_h2;
+    const int x = C.y * CX + tx, ya = C.z * CY + ty2;
+    unsigned long long m = 0;
+    unsigned nzb = 0;
+    for (int p = 0; p < N; ++p) {
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        const int y = ya + o;
+        if (x >= N || y >= N) continue;
+        const long long at = p * NN + (long long)y * N + x;
+        const double v = phi[o64 + at], f = f64[o64 + at];
+        nzb |= (unsigned)(__double2hiint(v) | __double2loint(v));
+        const bool w[6] = {x == 0 && bc.type[0], x == N - 1 && bc.type[1], y == 0 && bc.type[2],
+                           y == N - 1 && bc.type[3], p == 0 && bc.type[4], p == N - 1 && bc.type[5]};
+        double r = f;
+        if (w[0] | w[1] | w[2] | w[3] | w[4] | w[5]) {
+          double g[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) g[q] = w[q] ? bc.g2[q] - 0.0 : 0.0;
+          const double s = ((g[0] + g[1]) + (g[2] + g[3])) + (g[4] + g[5]);
+          r = fma(-fma(-6.0, 0.0, s), inv_h2, f);
+        }
+        const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+        f32[o32 + at] = cvt_bits_f32_rn(rb);
+        const unsigned long long a = rb & 0x7fffffffffffffffull;
+        m = a > m ? a : m;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if ((t & 31) == 0) red[t >> 5] = m;
+    const int any_nz = __syncthreads_or(nzb != 0);
+    if (t == 0) {
+      unsigned long long x2 = red[0];
+      for (int i = 1; i < CT / 32; ++i) x2 = red[i] > x2 ? red[i] : x2;
+      atomicMax(num + C.x, x2);
+      if (any_nz) atomicOr(nz + C.x, 1u);
+    }
+    __syncthreads();  // red[] is rewritten by the next column
+  }
+}
+
 // per-solve bookkeeping (one block): mode 0 -- denominators from the
 // residual of phi = 0, all solves active; mode 1 -- relative residuals,
 // cycles of the solves that ran, new active set and the loop condition
@@ -678,6 +745,8 @@ struct BState {
   int *cycles;
   unsigned char *active;
   int *any;
+  const unsigned *nz;  // per solve: stored potential not all +0
+  unsigned char *work;  // per solve: the first residual of the current potential is needed
 };
 
 __global__ void k_bt_check(cudaGraphConditionalHandle h, int in_graph, int n, BState st, int mode, int counted,
@@ -689,8 +758,13 @@ __global__ void k_bt_check(cudaGraphConditionalHandle h, int in_graph, int n, BS
   int maxc = (int)tolmax[1];
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     if (mode == 0) {
-      st.den[s] = st.num[s];
-      st.num[s] = 0;
+      // a potential that is all +0 has the residual just computed (the same
+      // bits): its max is the denominator, and the next residual pass skips it
+      const unsigned long long d = st.num[s];
+      const bool zero = st.nz[s] == 0;
+      st.den[s] = d;
+      st.num[s] = zero ? d : 0;
+      st.work[s] = zero ? 0 : 1;
       st.cycles[s] = 0;
       st.active[s] = 1;
       continue;
@@ -741,6 +815,8 @@ struct sm_batch {
   double *d_rel = nullptr, *d_tolmax = nullptr;
   int *d_cycles = nullptr, *d_any = nullptr;
   unsigned char *d_active = nullptr;
+  unsigned *d_nz = nullptr;          // per solve: potential not all +0
+  unsigned char *d_work = nullptr;   // per solve: first residual of the current potential needed
   double *h_tolmax = nullptr;
   // current schedule
   int shape = 0, gmult = 4, sms = 148;
@@ -870,7 +946,8 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
 }
 
 struct BLayout {
-  size_t tab, phi, f64, e32, e32b, f32, tiles, coarse, num, den, rel, tolmax, cycles, any, active, total;
+  size_t tab, phi, f64, e32, e32b, f32, tiles, coarse, num, den, rel, tolmax, cycles, any, active, nz, work,
+      total;
 };
 
 static BLayout blayout(const sm_batch *b) {
@@ -896,6 +973,8 @@ static BLayout blayout(const sm_batch *b) {
   L.cycles = take(sizeof(int) * b->n);
   L.any = take(sizeof(int));
   L.active = take(b->n);
+  L.nz = take(sizeof(unsigned) * b->n);
+  L.work = take(b->n);
   L.total = t;
   return L;
 }
@@ -1001,6 +1080,8 @@ extern "C" int sm_batch_bind_arena(sm_batch *b, void *dev_ptr, size_t bytes) {
   b->d_cycles = (int *)(a + L.cycles);
   b->d_any = (int *)(a + L.any);
   b->d_active = (unsigned char *)(a + L.active);
+  b->d_nz = (unsigned *)(a + L.nz);
+  b->d_work = (unsigned char *)(a + L.work);
   BCK(cudaMemsetAsync(a, 0, L.total, b->stream));
   BCK(cudaMemcpyAsync(b->d_tab, b->solves.data(), sizeof(BSolve) * b->n, cudaMemcpyHostToDevice, b->stream));
   return build_lists(b, 0);
@@ -1038,13 +1119,19 @@ static int grid_for(const sm_batch *b, size_t ntiles) {
 }
 
 static BState bstate(sm_batch *b) {
-  return {b->d_num, b->d_den, b->d_rel, b->d_cycles, b->d_active, b->d_any};
+  return {b->d_num, b->d_den, b->d_rel, b->d_cycles, b->d_active, b->d_any, b->d_nz, b->d_work};
 }
 
-static int outer(sm_batch *b, int zero_phi) {
+// FP64 residual of the solves flagged in `mask`; zero_phi: of phi = 0, also
+// flagging (d_nz) the solves whose stored potential is not all +0
+static int outer(sm_batch *b, int zero_phi, const unsigned char *mask) {
   size_t n0 = b->fine_cnt;
-  k_bt_outer<<<grid_for(b, n0), CT, OUTER_SMEM, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, b->d_active,
-                                                    b->phi, b->f64, b->f32, b->bc, zero_phi, b->d_num);
+  if (zero_phi)
+    k_bt_outer0<<<grid_for(b, n0), CT, 0, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, mask, b->phi,
+                                                       b->f64, b->f32, b->bc, b->d_num, b->d_nz);
+  else
+    k_bt_outer<<<grid_for(b, n0), CT, OUTER_SMEM, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, mask,
+                                                      b->phi, b->f64, b->f32, b->bc, 0, b->d_num);
   ++b->n_launch;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "outer residual launch");
 }
@@ -1144,12 +1231,13 @@ static int end_caps(sm_batch *b, cudaStream_t saved, int st) {
 static int prefix(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
   int st;
   if (cudaMemsetAsync(b->d_num, 0, sizeof(unsigned long long) * b->n, b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_nz, 0, sizeof(unsigned) * b->n, b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->d_active, 1, b->n, b->stream) != cudaSuccess)
     return bfail(b, SM_ECUDA, "memset");
-  if ((st = outer(b, 1))) return st;
+  if ((st = outer(b, 1, b->d_active))) return st;
   k_bt_check<<<1, 256, 0, b->stream>>>(h, in_graph, b->n, bstate(b), 0, 0, b->d_tolmax);
   ++b->n_launch;
-  if ((st = outer(b, 0))) return st;
+  if ((st = outer(b, 0, b->d_work))) return st;
   k_bt_check<<<1, 256, 0, b->stream>>>(h, in_graph, b->n, bstate(b), 1, 0, b->d_tolmax);
   ++b->n_launch;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "prefix launch");
@@ -1159,7 +1247,7 @@ static int prefix(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
 static int body_step(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
   int st;
   if ((st = bvcycle(b))) return st;
-  if ((st = outer(b, 0))) return st;
+  if ((st = outer(b, 0, b->d_active))) return st;
   k_bt_check<<<1, 256, 0, b->stream>>>(h, in_graph, b->n, bstate(b), 1, 1, b->d_tolmax);
   ++b->n_launch;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "body launch");

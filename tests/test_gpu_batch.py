@@ -156,3 +156,33 @@ def test_batch_graph_and_host_paths_identical():
         b.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_batch_mixed_starting_potentials():
+    """The first residual pass skips solves whose stored potential is all +0
+    (their residual is that of phi = 0, already computed for the
+    denominators).  In one batch: solves restarted from +0, solves kept at a
+    converged potential, and one restarted from -0.0 (not all +0 bits, so
+    it takes the full pass).  A solve restarted from +0 gives the same bits
+    as in a batch where every solve starts from +0; all reach the tolerance
+    and the spectral reference."""
+    sides = [32, 40, 24, 48]
+    fresh, rhos = make_batch(sides, seed_blobs=3)
+    rc, cyc_f, rel_f = fresh.solve(1e-10, 40)
+    assert rc == 0
+    phi_f = [fresh.grid(fresh.phi, s).cpu().numpy().copy() for s in range(len(sides))]
+    fresh.close()
+
+    b, _ = make_batch(sides, seed_blobs=3)
+    rc, _, _ = b.solve(1e-8, 40)
+    assert rc == 0
+    b.grid(b.phi, 1).zero_()
+    b.grid(b.phi, 3).fill_(-0.0)
+    rc, cyc, rel = b.solve(1e-10, 40)
+    assert rc == 0 and np.all(rel <= 1e-10)
+    assert np.array_equal(b.grid(b.phi, 1).cpu().numpy(), phi_f[1])
+    assert cyc[1] == cyc_f[1] and rel[1] == rel_f[1]
+    # converged starts need fewer corrections than the restarts
+    assert cyc[0] < cyc_f[0] and cyc[2] < cyc_f[2]
+    check(b, rhos, range(len(sides)), 1e-8)
+    b.close()
