@@ -694,7 +694,7 @@ def bench_batch(args, dev, world):
     # launches overwrite the error arrays)
     hbm = measured_peaks()[0]
     kern = {}
-    for kc, name in ((0, "k_bt_sweep level 0"), (1, "k_bt_outer (FP64 residual)"),
+    for kc, name in ((0, "k_bt_sweep level 0"), (1, "k_bt_outer (residual, fixed-point sum)"),
                      (2, "k_bt_prolong level 0"), (3, "k_bt_restrict level 0->1")):
         us, by, fl = b.kernel_bench(kc, 10)
         e = {"us": round(us, 2), "bytes": int(by), "gbs": round(by / (us * 1e-6) / 1e9, 1),
@@ -708,11 +708,12 @@ def bench_batch(args, dev, world):
            "max_corrections": cycles / args.steps,
            "gcells_corrections_per_s": round(cells * cycles * world / (total * 1e-3) / 1e9, 3),
            "schedule": {"tile": pkg.Batch.SHAPES[shape], "blocks_per_sm": gmult, "tuned_ms": round(tune_ms, 3)},
-           "gpu_launches": launches - l0, "dtype": "f32 cycles, f64 residual/accumulation/coarsest solve",
+           "gpu_launches": launches - l0,
+           "dtype": "f32 cycles; f64 residual (stencil sum exact in int64 fixed point), accumulation, coarsest solve",
            "workload": "256 unit-cube solves, sides 8*round(32*4^u/8), phi=0/1 on z plates",
            "kernels": kern,
            "kernels_note": "CUDA events around 10 back-to-back launches over all 256 solves; bytes = "
-                           "compulsory traffic (sweep 12 B, outer 20 B + 7 FP64 instr, prolong/restrict "
+                           "compulsory traffic (sweep 12 B, outer 20 B + 1 FP64 instr, prolong/restrict "
                            "8.5 B per fine cell); hbm peak %.1f GB/s measured, FP64 peak %.0f G instr/s"
                            % (hbm, FP64_PEAK_GINSTR)}
     b.close()

@@ -159,18 +159,20 @@ def _hp(a: np.ndarray):
 
 
 def check_conversions(n: int, seed: int = 0x5EED):
-    """Mismatches (FP64->FP32, FP32->FP64) of the library's integer-pipe
-    conversions against the hardware ones on n seeded bit patterns."""
+    """Mismatches (FP64->FP32, FP32->FP64, int64->FP64, FP64->fixed point)
+    of the library's integer-pipe conversions on n seeded bit patterns: the
+    first three against the hardware conversions, the fixed-point one
+    against exact FP64 scaling with the tie rule."""
     import torch
     lib = load()
-    scratch = torch.zeros(2, dtype=torch.int64, device="cuda")
-    out = np.zeros(2, np.uint64)
+    scratch = torch.zeros(4, dtype=torch.int64, device="cuda")
+    out = np.zeros(4, np.uint64)
     stream = torch.cuda.current_stream()
     rc = lib.sm_check_conversions(int(n), int(seed), C.c_void_p(scratch.data_ptr()), _hp(out),
                                   C.c_void_p(stream.cuda_stream))
     if rc != SM_OK:
         raise SmError(rc, "sm_check_conversions failed")
-    return int(out[0]), int(out[1])
+    return tuple(int(v) for v in out)
 
 
 class Solver:

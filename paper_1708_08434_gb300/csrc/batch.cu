@@ -151,7 +151,8 @@ __device__ __forceinline__ float wall_w(const Bc &bc, int a, int v, int N) {
 // from e = 0 (the first sweep of a level in a V-cycle): e_in is not read,
 // the staged error planes are zero-filled.  With phi != nullptr (level 0,
 // last sweep of a cycle) the swept error is not stored but added to the
-// FP64 potential: phi += (double)e.
+// FP64 potential, phi += (double)e, and emax of the solve is raised to the
+// largest exponent field of the new values.
 // Ring use at step p: planes p-2 .. p+1 are read, p+2 .. p+4 are in flight,
 // and plane p+5 is issued into the slot of plane p-3 (last read at step p-1).
 // The slots of planes -1 and N are zero-filled, so every update adds six
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
                                                  const unsigned char *__restrict__ active,
                                                  const float *__restrict__ e_in, float *__restrict__ e_out,
                                                  const float *__restrict__ f, Bc bc, double *__restrict__ phi,
-                                                 int zero_in) {
+                                                 unsigned *__restrict__ emax, int zero_in) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float(*se)[EPL] = reinterpret_cast<float(*)[EPL]>(smem_raw);
   float(*sf)[FPL] = reinterpret_cast<float(*)[FPL]>(smem_raw + sizeof(float) * RING * EPL);
@@ -280,6 +281,7 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
     const int rq = (ry - y0 + 2) * RW + (rx - x0 + 4), rqf = (ry - y0 + 1) * RW + (rx - x0 + 4);
     const float rw = rin ? wall_w(bc, 0, rx, N) + wall_w(bc, 1, ry, N) : 0.f;
     const long long row0 = (long long)ya * N + x;
+    unsigned em = 0;  // with phi: largest exponent field written
     __syncthreads();  // the previous column's planes are no longer read
     zero_slot((-1) & (RING - 1));                 // plane -1, landing with plane 0's group
 #pragma unroll
@@ -307,8 +309,10 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
         const long long g = z * NN + row0;
         if (pv) {
           const double *ph = sph[z & (RING - 1)];
-          pv[g] = ph[ty2 * CX + tx] + cvt_f32_f64(v0);
-          pv[g + N] = ph[(ty2 + 1) * CX + tx] + cvt_f32_f64(v1);
+          const double n0 = ph[ty2 * CX + tx] + cvt_f32_f64(v0), n1 = ph[(ty2 + 1) * CX + tx] + cvt_f32_f64(v1);
+          pv[g] = n0;
+          pv[g + N] = n1;
+          em = max(em, max(expo_of(n0), expo_of(n1)));
         } else {
           eo[g] = v0;
           eo[g + N] = v1;
@@ -316,6 +320,10 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
       }
     }
     cp_wait<0>();
+    if (pv) {  // uniform per block
+      em = __reduce_max_sync(0xffffffffu, em);
+      if ((t & 31) == 0 && em) atomicMax(emax + C.x, em);
+    }
   }
 }
 
@@ -456,12 +464,13 @@ __global__ void __launch_bounds__(CT) k_bt_prolong(const int4 *__restrict__ cols
 // exact FP64 solve of the error equation on the coarsest grid of each
 // listed solve (one block per solve): separable eigenbases per axis.  When
 // the coarsest grid is the finest (k = 0) the correction, rounded to FP32
-// like every other correction, is added to the FP64 potential directly.
+// like every other correction, is added to the FP64 potential directly (and
+// emax of the solve raised to the largest exponent field written).
 __global__ void __launch_bounds__(512) k_bt_coarse(const int *__restrict__ solves, int k,
                                                    const BSolve *__restrict__ tab,
                                                    const unsigned char *__restrict__ active,
                                                    float *__restrict__ e, const float *__restrict__ f, Bc bc,
-                                                   double *__restrict__ phi) {
+                                                   double *__restrict__ phi, unsigned *__restrict__ emax) {
   extern __shared__ double sm[];
   int s = solves[blockIdx.x];
   if (!active[s]) return;
@@ -515,47 +524,72 @@ __global__ void __launch_bounds__(512) k_bt_coarse(const int *__restrict__ solve
   // passes alternate x -> y -> x ...: the sixth ends in x
   if (k == 0) {
     double *pv = phi + S.off64;
-    for (int c = t; c < n3; c += blockDim.x) pv[c] += (double)(float)x[c];
+    unsigned em = 0;
+    for (int c = t; c < n3; c += blockDim.x) {
+      const double v = pv[c] + (double)(float)x[c];
+      pv[c] = v;
+      em = max(em, expo_of(v));
+    }
+    em = __reduce_max_sync(0xffffffffu, em);
+    if ((t & 31) == 0 && em) atomicMax(emax + s, em);
   } else {
     float *ev = e + S.off[k];
     for (int c = t; c < n3; c += blockDim.x) ev[c] = (float)x[c];
   }
 }
 
-// FP64 outer residual on the finest grids, column by column:
-// r = f - L phi (or of phi = 0 when zero_phi), its max norm per solve and
-// the FP32 copy of r as the error equation's rhs (the error itself starts
-// at zero: the first sweep does not read it).
-// Planes of phi (one-cell halo) are staged by asynchronous copies: at step
-// p planes p-1 .. p+1 are read, p+2 .. p+4 are in flight and plane p+5 is
-// issued into the slot of plane p-3; f is loaded into registers two
-// planes ahead.  phi is only read here.  Per cell: the six
-// neighbours (wall ghosts selected in place) summed pairwise, two fused
-// multiply-adds; the max norm is taken on the bit patterns of |r|.
+// Outer residual on the finest grids, column by column: r = f - L phi, its
+// max norm per solve and the FP32 copy of r as the error equation's rhs (the
+// error itself starts at zero: the first sweep does not read it).
+// The stencil sum S = (sum of the six neighbours) - 6 phi is formed exactly
+// in 64-bit fixed point on the integer pipe: each staged value is mapped
+// once to the nearest multiple of 2^(E - 1080), where E (at least 123)
+// bounds the exponent fields of the solve's potential (emax, raised by every
+// kernel that writes phi) and of the Dirichlet wall values 2g; the sum of
+// the integers then has no rounding at all.  r = f - S 2^(E-1080) h^-2 is
+// one FMA after S is rounded to binary64.  The error of r is at most
+// 6.5 2^(E-1080) h^-2 (the twelve mapped values) plus two roundings, below
+// that of the plain FP64 sum (five additions and a multiply-add rounding at
+// 2^-53 of values up to 2^(E-1022)), and the FP64 pipe does one operation
+// per cell instead of seven.  A solve whose potential holds an infinity or
+// a NaN gets NaN residuals.
+// Planes of phi (one-cell halo) are staged by asynchronous copies and
+// converted in place one step ahead: at step p planes p-1 .. p+1 are read,
+// plane p+2 is converted, p+3 .. p+4 are in flight and plane p+5 is issued
+// into the slot of plane p-3; f is loaded into registers two planes ahead.
+// The max norm is taken on the bit patterns of |r|.
 __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ cols, int ncols,
                                                  const BSolve *__restrict__ tab,
                                                  const unsigned char *__restrict__ active,
                                                  const double *__restrict__ phi, const double *__restrict__ f64,
-                                                 float *__restrict__ f32, Bc bc, int zero_phi,
+                                                 float *__restrict__ f32, Bc bc, const unsigned *__restrict__ emax,
                                                  unsigned long long *__restrict__ num) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double(*sp)[DPL] = reinterpret_cast<double(*)[DPL]>(smem_raw);
+  long long(*sp)[DPL] = reinterpret_cast<long long(*)[DPL]>(smem_raw);
   __shared__ unsigned long long red[CT / 32];
   const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  int ebc = 0;  // exponent bound of the Dirichlet wall values
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    if (bc.type[f]) ebc = max(ebc, (int)expo_of(bc.g2[f]));
   for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
     const int4 C = cols[it];
     if (!active[C.x]) continue;  // uniform per block
     const BSolve &S = tab[C.x];
     const int N = S.N[0];
     const long long o64 = S.off64, o32 = S.off[0], NN = (long long)N * N;
-    const double inv_h2 = S.inv_h2;
+    const int E = max(max((int)emax[C.x], ebc), 123);
+    const bool finite = E < 0x7ff;
+    // 2^(E-1080) h^-2, exact: a power of two (exponent field E - 57 >= 66)
+    // times h^-2
+    const double kk = S.inv_h2 * __longlong_as_double((long long)(finite ? E - 57 : 1023) << 52);
     const int x0 = C.y * CX, y0 = C.z * CY;
     const double *pv = phi + o64, *fv = f64 + o64;
     const bool vec = (N & 1) == 0;
     const int x = x0 + tx, ya = y0 + ty2;
     const bool in0 = x < N && ya < N, in1 = x < N && ya + 1 < N;
     auto issue = [&](int z) {
-      if (z < N && !zero_phi) {
+      if (z < N) {
         const int sl = z & (RING - 1);
         const double *pz = pv + z * NN;
         if (vec) {
@@ -574,14 +608,20 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
       }
       cp_commit();
     };
-    // Neighbour value across face f of a cell holding c: the staged value v,
-    // or at the wall the ghost c (Neumann) or 2g - c (Dirichlet).  The face
-    // type is uniform over the kernel, so the Neumann case is a select with
-    // no FP64 work (a per-cell branch would run for every warp holding one
-    // boundary lane).
-    auto nbv = [&](int f, bool at_wall, double v, double c) {
-      if (bc.type[f]) return at_wall ? bc.g2[f] - c : v;
-      return at_wall ? c : v;
+    // staged plane z -> fixed point, in place (the columns x0-1 .. x0+32
+    // that the stencil reads; cells outside the grid were zero-filled)
+    auto convert = [&](int z) {
+      if (z < N) {
+        long long *pz = sp[z & (RING - 1)];
+        for (int i = t; i < FR * (CX + 2); i += CT) {
+          const int j = (i / (CX + 2)) * RWD + 1 + i % (CX + 2);
+          pz[j] = fix_of_bits((unsigned long long)pz[j], E);
+        }
+      }
+    };
+    // ghost across wall face f of a cell holding c: c (Neumann) or 2g - c
+    auto wallv = [&](int f, long long c) {
+      return bc.type[f] ? fix_of_bits((unsigned long long)__double_as_longlong(bc.g2[f]), E) - c : c;
     };
     const long long row0 = (long long)ya * N + x;
     // f of planes p (set A for even p, B for odd p): loaded two steps ahead
@@ -594,44 +634,41 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
     __syncthreads();           // the previous column's planes are no longer read
 #pragma unroll
     for (int z = 0; z < RING - 3; ++z) issue(z);
+    cp_wait<RING - 5>();  // planes 0 and 1 have landed
+    __syncthreads();
+    convert(0);
+    convert(1);
     // NEU: all four in-plane faces are Neumann (a compile-time path: the
-    // ghosts are then selects of c, with no FP64 work for Dirichlet ghosts
-    // the compiler would otherwise compute on every cell)
+    // in-plane ghosts are then selects of c)
     auto step = [&](auto neu_tag, int p, double &f0, double &f1) {
       constexpr bool NEU = decltype(neu_tag)::value;
-      cp_wait<RING - 5>();
-      __syncthreads();
+      cp_wait<RING - 6>();  // this thread's copies of planes <= p+2 have landed
+      __syncthreads();      // everyone's have; planes <= p+1 are converted; step p-1's reads are done
       issue(p + RING - 3);
-      const double *pz = sp[p & (RING - 1)];
+      convert(p + 2);
+      const long long *pz = sp[p & (RING - 1)], *pm = sp[(p - 1) & (RING - 1)], *pp = sp[(p + 1) & (RING - 1)];
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         if (!(o ? in1 : in0)) continue;
         const int q = (ty2 + o + 1) * RWD + tx + 2, y = ya + o;
-        // phi = 0 (zero_phi): the staged planes are not loaded; every value is 0
-        const double c = zero_phi ? 0.0 : pz[q];
-        double xm, xp, ym, yp;
+        const long long c = pz[q];
+        long long xm, xp, ym, yp;
         if constexpr (NEU) {
-          xm = x == 0 ? c : (zero_phi ? 0.0 : pz[q - 1]);
-          xp = x == N - 1 ? c : (zero_phi ? 0.0 : pz[q + 1]);
-          ym = y == 0 ? c : (zero_phi ? 0.0 : pz[q - RWD]);
-          yp = y == N - 1 ? c : (zero_phi ? 0.0 : pz[q + RWD]);
+          xm = x == 0 ? c : pz[q - 1];
+          xp = x == N - 1 ? c : pz[q + 1];
+          ym = y == 0 ? c : pz[q - RWD];
+          yp = y == N - 1 ? c : pz[q + RWD];
         } else {
-          xm = nbv(0, x == 0, zero_phi ? 0.0 : pz[q - 1], c);
-          xp = nbv(1, x == N - 1, zero_phi ? 0.0 : pz[q + 1], c);
-          ym = nbv(2, y == 0, zero_phi ? 0.0 : pz[q - RWD], c);
-          yp = nbv(3, y == N - 1, zero_phi ? 0.0 : pz[q + RWD], c);
+          xm = x == 0 ? wallv(0, c) : pz[q - 1];
+          xp = x == N - 1 ? wallv(1, c) : pz[q + 1];
+          ym = y == 0 ? wallv(2, c) : pz[q - RWD];
+          yp = y == N - 1 ? wallv(3, c) : pz[q + RWD];
         }
-        double zm, zp;
-        if (p == 0 || p == N - 1) {  // uniform: the wall planes
-          zm = nbv(4, p == 0, (zero_phi || p == 0) ? 0.0 : sp[(p - 1) & (RING - 1)][q], c);
-          zp = nbv(5, p == N - 1, (zero_phi || p == N - 1) ? 0.0 : sp[(p + 1) & (RING - 1)][q], c);
-        } else {
-          zm = zero_phi ? 0.0 : sp[(p - 1) & (RING - 1)][q];
-          zp = zero_phi ? 0.0 : sp[(p + 1) & (RING - 1)][q];
-        }
-        const double s = ((xm + xp) + (ym + yp)) + (zm + zp);
-        const double r = fma(-fma(-6.0, c, s), inv_h2, o ? f1 : f0);
-        const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+        const long long zm = p == 0 ? wallv(4, c) : pm[q];
+        const long long zp = p == N - 1 ? wallv(5, c) : pp[q];
+        const long long sx = ((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c;  // exact
+        const double r = fma(-__longlong_as_double((long long)bits_of_s64_rn(sx)), kk, o ? f1 : f0);
+        const unsigned long long rb = finite ? (unsigned long long)__double_as_longlong(r) : 0x7ff8000000000000ull;
         f32[o32 + p * NN + row0 + o * N] = cvt_bits_f32_rn(rb);
         const unsigned long long a = rb & 0x7fffffffffffffffull;
         m = a > m ? a : m;
@@ -675,14 +712,15 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
 // takes f with no FP64 work (-(+0) * h^-2 + f = f bit for bit); the others
 // evaluate the same expression as k_bt_outer with every value +0, so both
 // kernels give the same bits for a potential that is all +0.  Also flags
-// (nz) the solves whose stored potential is not all +0.
+// (nz) the solves whose stored potential is not all +0 and raises emax to
+// the largest exponent field of the stored potential.
 __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols, int ncols,
                                                   const BSolve *__restrict__ tab,
                                                   const unsigned char *__restrict__ active,
                                                   const double *__restrict__ phi,
                                                   const double *__restrict__ f64, float *__restrict__ f32, Bc bc,
                                                   unsigned long long *__restrict__ num,
-                                                  unsigned *__restrict__ nz) {
+                                                  unsigned *__restrict__ nz, unsigned *__restrict__ emax) {
   __shared__ unsigned long long red[CT / 32];
   const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
   for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
@@ -694,7 +732,7 @@ __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols,
     const double inv_h2 = S.inv_h2;
     const int x = C.y * CX + tx, ya = C.z * CY + ty2;
     unsigned long long m = 0;
-    unsigned nzb = 0;
+    unsigned nzb = 0, em = 0;
     for (int p = 0; p < N; ++p) {
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
@@ -703,6 +741,7 @@ __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols,
         const long long at = p * NN + (long long)y * N + x;
         const double v = phi[o64 + at], f = f64[o64 + at];
         nzb |= (unsigned)(__double2hiint(v) | __double2loint(v));
+        em = max(em, expo_of(v));
         const bool w[6] = {x == 0 && bc.type[0], x == N - 1 && bc.type[1], y == 0 && bc.type[2],
                            y == N - 1 && bc.type[3], p == 0 && bc.type[4], p == N - 1 && bc.type[5]};
         double r = f;
@@ -725,6 +764,8 @@ __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols,
       m = v > m ? v : m;
     }
     if ((t & 31) == 0) red[t >> 5] = m;
+    em = __reduce_max_sync(0xffffffffu, em);
+    if ((t & 31) == 0 && em) atomicMax(emax + C.x, em);
     const int any_nz = __syncthreads_or(nzb != 0);
     if (t == 0) {
       unsigned long long x2 = red[0];
@@ -816,6 +857,7 @@ struct sm_batch {
   int *d_cycles = nullptr, *d_any = nullptr;
   unsigned char *d_active = nullptr;
   unsigned *d_nz = nullptr;          // per solve: potential not all +0
+  unsigned *d_emax = nullptr;        // per solve: bound of the potential's exponent fields
   unsigned char *d_work = nullptr;   // per solve: first residual of the current potential needed
   double *h_tolmax = nullptr;
   // current schedule
@@ -947,7 +989,7 @@ extern "C" int sm_batch_create(sm_batch **out, int n_solves, const int *cells_pe
 
 struct BLayout {
   size_t tab, phi, f64, e32, e32b, f32, tiles, coarse, num, den, rel, tolmax, cycles, any, active, nz, work,
-      total;
+      emax, total;
 };
 
 static BLayout blayout(const sm_batch *b) {
@@ -975,6 +1017,7 @@ static BLayout blayout(const sm_batch *b) {
   L.active = take(b->n);
   L.nz = take(sizeof(unsigned) * b->n);
   L.work = take(b->n);
+  L.emax = take(sizeof(unsigned) * b->n);
   L.total = t;
   return L;
 }
@@ -1082,6 +1125,7 @@ extern "C" int sm_batch_bind_arena(sm_batch *b, void *dev_ptr, size_t bytes) {
   b->d_active = (unsigned char *)(a + L.active);
   b->d_nz = (unsigned *)(a + L.nz);
   b->d_work = (unsigned char *)(a + L.work);
+  b->d_emax = (unsigned *)(a + L.emax);
   BCK(cudaMemsetAsync(a, 0, L.total, b->stream));
   BCK(cudaMemcpyAsync(b->d_tab, b->solves.data(), sizeof(BSolve) * b->n, cudaMemcpyHostToDevice, b->stream));
   return build_lists(b, 0);
@@ -1122,16 +1166,17 @@ static BState bstate(sm_batch *b) {
   return {b->d_num, b->d_den, b->d_rel, b->d_cycles, b->d_active, b->d_any, b->d_nz, b->d_work};
 }
 
-// FP64 residual of the solves flagged in `mask`; zero_phi: of phi = 0, also
-// flagging (d_nz) the solves whose stored potential is not all +0
+// residual of the solves flagged in `mask`; zero_phi: of phi = 0, also
+// flagging (d_nz) the solves whose stored potential is not all +0 and
+// setting their exponent bounds (d_emax, zeroed before)
 static int outer(sm_batch *b, int zero_phi, const unsigned char *mask) {
   size_t n0 = b->fine_cnt;
   if (zero_phi)
     k_bt_outer0<<<grid_for(b, n0), CT, 0, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, mask, b->phi,
-                                                       b->f64, b->f32, b->bc, b->d_num, b->d_nz);
+                                                       b->f64, b->f32, b->bc, b->d_num, b->d_nz, b->d_emax);
   else
     k_bt_outer<<<grid_for(b, n0), CT, OUTER_SMEM, b->stream>>>(b->d_tiles + b->fine_off, (int)n0, b->d_tab, mask,
-                                                      b->phi, b->f64, b->f32, b->bc, 0, b->d_num);
+                                                      b->phi, b->f64, b->f32, b->bc, b->d_emax, b->d_num);
   ++b->n_launch;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "outer residual launch");
 }
@@ -1150,7 +1195,7 @@ static int smooth_level(sm_batch *b, int k, int nu, bool from_zero, bool add_phi
     float *out = (s & 1) ? b->e32 : b->e32b;
     double *phi = (add_phi && s == nu - 1) ? b->phi : nullptr;
     k_bt_sweep<<<grid_for(b, n), CT, phi ? SWEEP_SMEM_PHI : SWEEP_SMEM, b->stream>>>(
-        cols, (int)n, k, b->d_tab, b->d_active, in, out, b->f32, b->bc, phi, (from_zero && s == 0) ? 1 : 0);
+        cols, (int)n, k, b->d_tab, b->d_active, in, out, b->f32, b->bc, phi, b->d_emax, (from_zero && s == 0) ? 1 : 0);
     ++b->n_launch;
   }
   if ((nu & 1) && !add_phi) {
@@ -1176,7 +1221,7 @@ static int coarse_at_level(sm_batch *b, int k) {
   size_t nc = b->coarse_cnt[k];
   if (nc) {
     k_bt_coarse<<<(int)nc, 512, coarse_smem(BMAXC), b->stream>>>(b->d_coarse + b->coarse_off[k], k, b->d_tab,
-                                                                b->d_active, b->e32, b->f32, b->bc, b->phi);
+                                                                b->d_active, b->e32, b->f32, b->bc, b->phi, b->d_emax);
     ++b->n_launch;
   }
   return SM_OK;
@@ -1232,6 +1277,7 @@ static int prefix(sm_batch *b, cudaGraphConditionalHandle h, int in_graph) {
   int st;
   if (cudaMemsetAsync(b->d_num, 0, sizeof(unsigned long long) * b->n, b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->d_nz, 0, sizeof(unsigned) * b->n, b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_emax, 0, sizeof(unsigned) * b->n, b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->d_active, 1, b->n, b->stream) != cudaSuccess)
     return bfail(b, SM_ECUDA, "memset");
   if ((st = outer(b, 1, b->d_active))) return st;
@@ -1416,9 +1462,11 @@ extern "C" int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult,
 
 // Time one kernel class over all solves (every solve active), CUDA events
 // on the batch stream around `reps` back-to-back launches.  Classes:
-// 0 level-0 sweep (e read, f read, e written: 12 B per cell), 1 FP64 outer
-// residual (phi and f read, FP32 rhs written: 20 B and 7 FP64 operations
-// per cell), 2 level-0 prolongation (fine e read and written, coarse e
+// 0 level-0 sweep (e read, f read, e written: 12 B per cell), 1 outer
+// residual (phi and f read, FP32 rhs written: 20 B and one FP64 operation
+// per cell, the stencil sum in fixed point on the integer pipe; the
+// exponent bounds are first taken from the stored potential, untimed),
+// 2 level-0 prolongation (fine e read and written, coarse e
 // read: 8.5 B per fine cell), 3 level-0 -> 1 restriction (fine e and f
 // read, coarse f written: 8.5 B per fine cell).  Leaves the potential and
 // the error arrays changed; a following solve starts from whatever phi
@@ -1436,6 +1484,11 @@ extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *
   const size_t nr = b->kmax >= 1 ? b->restr_cnt[1] : 0;
   if ((kclass != 1 && fine == 0) || (kclass == 3 && nr == 0)) return bfail(b, SM_ESTATE, "no level below 0");
   BCK(cudaMemsetAsync(b->d_active, 1, b->n, b->stream));
+  if (kclass == 1) {
+    BCK(cudaMemsetAsync(b->d_emax, 0, sizeof(unsigned) * b->n, b->stream));
+    BCK(cudaMemsetAsync(b->d_nz, 0, sizeof(unsigned) * b->n, b->stream));
+    if (int st = outer(b, 1, b->d_active)) return st;
+  }
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
@@ -1444,12 +1497,12 @@ extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *
       case 0:
         k_bt_sweep<<<grid_for(b, nsw), CT, SWEEP_SMEM, b->stream>>>(b->d_tiles + b->scol_off[0], (int)nsw, 0,
                                                                      b->d_tab, b->d_active, b->e32, b->e32b,
-                                                                     b->f32, b->bc, nullptr, 0);
+                                                                     b->f32, b->bc, nullptr, nullptr, 0);
         break;
       case 1:
         k_bt_outer<<<grid_for(b, b->fine_cnt), CT, OUTER_SMEM, b->stream>>>(
-            b->d_tiles + b->fine_off, (int)b->fine_cnt, b->d_tab, b->d_active, b->phi, b->f64, b->f32, b->bc, 0,
-            b->d_num);
+            b->d_tiles + b->fine_off, (int)b->fine_cnt, b->d_tab, b->d_active, b->phi, b->f64, b->f32, b->bc,
+            b->d_emax, b->d_num);
         break;
       case 2:
         k_bt_prolong<<<grid_for(b, nsw), CT, 0, b->stream>>>(b->d_tiles + b->scol_off[0], (int)nsw, 0, b->d_tab,
@@ -1474,7 +1527,7 @@ extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *
   const double per_cell[4] = {12.0, 20.0, 8.5, 8.5};
   if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
   if (bytes_per_launch) *bytes_per_launch = per_cell[kclass] * cells;
-  if (fp64_per_launch) *fp64_per_launch = kclass == 1 ? 7.0 * cells : 0.0;
+  if (fp64_per_launch) *fp64_per_launch = kclass == 1 ? 1.0 * cells : 0.0;
   b->n_launch += reps + 1;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "kernel bench launch");
 }

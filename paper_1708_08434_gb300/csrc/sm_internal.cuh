@@ -261,6 +261,49 @@ __device__ __forceinline__ double cvt_f32_f64(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Exact stencil sums in 64-bit fixed point (integer pipe).  A finite
+// binary64 value with biased exponent field e <= E is mapped to the nearest
+// multiple of 2^(E - 1080), ties away from zero, as a signed integer: its
+// 53-bit significand (hidden bit included; subnormals use e = 1) shifted by
+// e - E + 5, so |result| < 2^58 and sums of twelve such values cannot
+// overflow.  The rounding error is at most 2^(E - 1081), i.e. 2^-58 of the
+// largest value of that exponent.
+__device__ __forceinline__ long long fix_of_bits(unsigned long long b, int E) {
+  const int e = (int)((b >> 52) & 0x7ffull);
+  const unsigned long long m = (b & 0x000fffffffffffffull) | (e ? (1ull << 52) : 0ull);
+  const int sh = (e ? e : 1) - E + 5;
+  unsigned long long u;
+  if (sh >= 0) {
+    u = m << sh;
+  } else {
+    const int rs = -sh;
+    u = rs < 64 ? (m + (1ull << (rs - 1))) >> rs : 0ull;
+  }
+  return (long long)((b >> 63) ? 0ull - u : u);
+}
+
+// signed 64-bit integer -> binary64 bit pattern, round to nearest, ties to
+// even: the magnitude is normalised to bit 63, its top 53 bits form the
+// significand and the 11 dropped bits round it; a carry out of the
+// significand lands in the exponent field, which is then correct
+__device__ __forceinline__ unsigned long long bits_of_s64_rn(long long v) {
+  if (v == 0) return 0ull;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)u);
+  u <<= lz;
+  const unsigned long long rest = u & 0x7ffull;
+  unsigned long long r = sgn | (((unsigned long long)(1085 - lz) << 52) + (u >> 11));
+  r += (rest > 0x400ull || (rest == 0x400ull && (u & 0x800ull))) ? 1ull : 0ull;
+  return r;
+}
+
+// biased exponent field of a binary64 value (0 for zero and subnormals,
+// 0x7ff for infinities and NaNs)
+__device__ __forceinline__ unsigned expo_of(double d) {
+  return ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+}
+
 // atomic max of a non-negative double through its bit pattern
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *slot, double v) {
   atomicMax(slot, (unsigned long long)__double_as_longlong(v));
