@@ -588,16 +588,27 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
     const bool vec = (N & 1) == 0;
     const int x = x0 + tx, ya = y0 + ty2;
     const bool in0 = x < N && ya < N, in1 = x < N && ya + 1 < N;
+    // this thread's 16-byte chunks of a staged plane (at most two): slot-0
+    // shared offset, in-plane element offset, inside the grid
+    int cdst[2] = {-1, -1}, coff[2] = {0, 0};
+    bool cok[2] = {false, false};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = t + u * CT;
+      if (!vec || i >= FR * (RWD / 2)) continue;
+      const int r = i / (RWD / 2), c2 = 2 * (i % (RWD / 2)), y = y0 - 1 + r, xx = x0 - 2 + c2;
+      cok[u] = y >= 0 && y < N && xx >= 0 && xx < N;
+      coff[u] = cok[u] ? y * N + xx : 0;
+      cdst[u] = r * RWD + c2;
+    }
     auto issue = [&](int z) {
       if (z < N) {
         const int sl = z & (RING - 1);
         const double *pz = pv + z * NN;
         if (vec) {
-          for (int i = t; i < FR * (RWD / 2); i += CT) {
-            const int r = i / (RWD / 2), c2 = 2 * (i % (RWD / 2)), y = y0 - 1 + r, xx = x0 - 2 + c2;
-            const bool ok = y >= 0 && y < N && xx >= 0 && xx < N;
-            cp_async<16>(&sp[sl][r * RWD + c2], ok ? pz + y * N + xx : pz, ok);
-          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (cdst[u] >= 0) cp_async<16>(&sp[sl][cdst[u]], pz + coff[u], cok[u]);
         } else {
           for (int i = t; i < FR * RWD; i += CT) {
             const int y = y0 - 1 + i / RWD, xx = x0 - 2 + i % RWD;
@@ -610,13 +621,19 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
     };
     // staged plane z -> fixed point, in place (the columns x0-1 .. x0+32
     // that the stencil reads; cells outside the grid were zero-filled)
+    constexpr int NCV = FR * (CX + 2);  // values converted per plane
+    int cj[3];                          // this thread's (at most three), -1 for none
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = t + u * CT;
+      cj[u] = i < NCV ? (i / (CX + 2)) * RWD + 1 + i % (CX + 2) : -1;
+    }
     auto convert = [&](int z) {
       if (z < N) {
         long long *pz = sp[z & (RING - 1)];
-        for (int i = t; i < FR * (CX + 2); i += CT) {
-          const int j = (i / (CX + 2)) * RWD + 1 + i % (CX + 2);
-          pz[j] = fix_of_bits((unsigned long long)pz[j], E);
-        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (cj[u] >= 0) pz[cj[u]] = fix_of_bits((unsigned long long)pz[cj[u]], E);
       }
     };
     // ghost across wall face f of a cell holding c: c (Neumann) or 2g - c

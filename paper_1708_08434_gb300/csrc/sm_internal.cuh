@@ -268,18 +268,19 @@ __device__ __forceinline__ double cvt_f32_f64(float f) {
 // e - E + 5, so |result| < 2^58 and sums of twelve such values cannot
 // overflow.  The rounding error is at most 2^(E - 1081), i.e. 2^-58 of the
 // largest value of that exponent.
+//
+// Branch-free: M = significand * 2^5 (< 2^58), then a right shift by
+// rs = E - e >= 0; for rs >= 1 the last dropped bit is kept, incremented
+// and shifted out, which rounds half away from zero (shift counts above 63
+// give 0, as the result must).
 __device__ __forceinline__ long long fix_of_bits(unsigned long long b, int E) {
-  const int e = (int)((b >> 52) & 0x7ffull);
-  const unsigned long long m = (b & 0x000fffffffffffffull) | (e ? (1ull << 52) : 0ull);
-  const int sh = (e ? e : 1) - E + 5;
-  unsigned long long u;
-  if (sh >= 0) {
-    u = m << sh;
-  } else {
-    const int rs = -sh;
-    u = rs < 64 ? (m + (1ull << (rs - 1))) >> rs : 0ull;
-  }
-  return (long long)((b >> 63) ? 0ull - u : u);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned long long M = ((b & 0x000fffffffffffffull) | (e ? (1ull << 52) : 0ull)) << 5;
+  const int rs = E - (e ? e : 1);
+  const unsigned long long t1 = M >> min(max(rs - 1, 0), 63);
+  const unsigned long long u = rs > 0 ? (t1 + 1ull) >> 1 : t1;
+  return (long long)((hi >> 31) ? 0ull - u : u);
 }
 
 // signed 64-bit integer -> binary64 bit pattern, round to nearest, ties to
