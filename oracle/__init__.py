@@ -21,29 +21,35 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+QUAD_LIB_PATH = os.path.join(_BUILD, "libquad.so")
 _lock = threading.Lock()
 _lib = None
 
 PHI, RHS, RES, NE, NI, EMAG, RHO = range(7)
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (gcc, no GPU needed)."""
-    src = os.path.join(_HERE, "oracle.c")
-    if not force and os.path.exists(_LIB_PATH) and \
-            os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src),
-                                               os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        return _LIB_PATH
+def _compile(src: str, hdr: str, out: str, force: bool) -> str:
+    """gcc -O2 -ffp-contract=off src -> out (OpenMP when available)."""
+    if not force and os.path.exists(out) and \
+            os.path.getmtime(out) >= max(os.path.getmtime(src), os.path.getmtime(hdr)):
+        return out
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    tmp = out + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
            "-o", tmp, src, "-lm"]
     # OpenMP over boxes when the compiler has it; plain loops otherwise
     if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:],
                       stderr=subprocess.DEVNULL).returncode != 0:
         subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so and quad.c into
+    _build/libquad.so (gcc, no GPU needed); returns the first path."""
+    _compile(os.path.join(_HERE, "quad.c"), os.path.join(_HERE, "quad.h"), QUAD_LIB_PATH, force)
+    return _compile(os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle.h"), _LIB_PATH, force)
 
 
 def _load():

@@ -369,3 +369,140 @@ def cnn_initial_params(seed: int = SEED, gain: float = 1.0) -> np.ndarray:
         parts.append(gain * z * np.sqrt(2.0 / (ci * 27)))
         parts.append(np.zeros(co))
     return np.concatenate(parts).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# 2-D and axisymmetric domains (quadtree of 8^2-cell boxes).  In the
+# axisymmetric geometry x is the radius r (axis at x = 0) and y is z.
+# --------------------------------------------------------------------------
+CARTESIAN, AXISYMMETRIC = 0, 1
+CELLS2 = BOX * BOX
+
+
+@dataclasses.dataclass
+class Domain2:
+    """Square domain [origin, origin+length]^2 on a base grid of nb^2 boxes;
+    bc per face -x,+x,-y,+y.  Axisymmetric: origin x must be 0 and face -x
+    is the axis (no condition)."""
+    length: float
+    nb: int
+    max_level: int
+    geom: int = AXISYMMETRIC
+    bc_type: tuple = (NEUMANN, NEUMANN, DIRICHLET, DIRICHLET)
+    bc_val: tuple = (0.0, 0.0, 0.0, 1.0)
+    origin: tuple = (0.0, 0.0)
+
+    @property
+    def lbase(self) -> int:
+        lb = int(round(np.log2(self.nb)))
+        assert (1 << lb) == self.nb, "base boxes per side must be a power of two"
+        return lb
+
+    def h(self, level: int) -> float:
+        return self.length / (BOX * (1 << level))
+
+
+def cell_centres2(dom: Domain2, levels, ij):
+    """x, y of every cell of the given boxes, shape [nbox, 64] (x fastest)."""
+    levels = np.asarray(levels)
+    ij = np.asarray(ij, dtype=np.float64).reshape(-1, 2)
+    h = dom.length / (BOX * np.exp2(levels.astype(np.float64)))
+    loc = np.arange(BOX, dtype=np.float64) + 0.5
+    ii = np.tile(loc, BOX)
+    jj = np.repeat(loc, BOX)
+    x = dom.origin[0] + (ij[:, 0:1] * BOX + ii[None, :]) * h[:, None]
+    y = dom.origin[1] + (ij[:, 1:2] * BOX + jj[None, :]) * h[:, None]
+    return x, y
+
+
+@dataclasses.dataclass
+class Streamer2:
+    """The synthetic streamer in 2-D: channel of half-width `radius` around
+    x = x_axis (the symmetry axis r = 0 in the axisymmetric geometry, the
+    domain centre in Cartesian), above z_head, with a round head; densities
+    and the head's ion shell as in 3-D."""
+    length: float = 0.016
+    radius: float = 0.5e-3
+    z_head: float = 8.5e-3
+    n_channel: float = 1e19
+    n_head: float = 1e20
+    edge: float = 50e-6
+    shell: float = 20e-6
+    voltage: float = 25e3
+    x_axis: float = 0.0
+    refine_c: float = 10.0
+    refine_tip: float = 4.2e-3
+
+    def signed_distance(self, x, y):
+        da = np.abs(x - self.x_axis)
+        s_cyl = da - self.radius
+        s_sph = np.sqrt(da ** 2 + (y - self.z_head) ** 2) - self.radius
+        return np.where(y >= self.z_head, s_cyl, s_sph)
+
+    def tip_distance(self, x, y):
+        return np.hypot(x - self.x_axis, y - (self.z_head - self.radius))
+
+
+def streamer_densities2(dom: Domain2, st: Streamer2, levels, ij):
+    x, y = cell_centres2(dom, levels, ij)
+    s = st.signed_distance(x, y)
+    core = st.n_channel * smoothstep_edge(s, st.edge)
+    head = (y < st.z_head) & (s < 0.0) & (s >= -st.shell)
+    return core, core + np.where(head, st.n_head, 0.0)
+
+
+def streamer_refine_flags2(dom: Domain2, st: Streamer2, level: int, ij) -> np.ndarray:
+    """+1/0 per box of `level`: near the streamer surface and the tip, as in
+    3-D (half box diagonal + refine_c*h of the surface, half diagonal +
+    refine_tip/2^k of the tip)."""
+    ij = np.asarray(ij, dtype=np.float64).reshape(-1, 2)
+    hb = dom.length / (1 << level)
+    h = hb / BOX
+    c = np.array(dom.origin)[None, :] + (ij + 0.5) * hb
+    hd = np.sqrt(2.0) * hb / 2.0
+    s = np.abs(st.signed_distance(c[:, 0], c[:, 1]))
+    k = level - dom.lbase
+    td = st.tip_distance(c[:, 0], c[:, 1])
+    return ((s < hd + st.refine_c * h) & (td < hd + st.refine_tip * 2.0 ** (-k))).astype(np.int8)
+
+
+def refine_all2(dom: Domain2, st: Streamer2, get_level_ij, refine_level):
+    for level in range(dom.lbase, dom.lbase + dom.max_level):
+        ij = get_level_ij(level)
+        if len(ij) == 0:
+            break
+        refine_level(level, streamer_refine_flags2(dom, st, level, ij))
+
+
+def workload2(name: str):
+    """(Domain2, Streamer2|None) for a named 2-D workload.
+
+    axi_small   : axisymmetric 16 mm, base 4^2 boxes (32^2 cells), 3 levels (tests)
+    cart_small  : the same in Cartesian coordinates, channel at the centre
+    axi_streamer: axisymmetric 16 mm, base 64^2 boxes (512^2 cells), 8 levels
+                  (finest 0.12 um)
+    """
+    if name == "axi_small":
+        st = Streamer2(refine_c=2.0, refine_tip=6e-3)
+        return Domain2(0.016, 4, 3, AXISYMMETRIC, bc_val=(0.0, 0.0, 0.0, st.voltage)), st
+    if name == "cart_small":
+        st = Streamer2(refine_c=2.0, refine_tip=6e-3, x_axis=0.008)
+        return Domain2(0.016, 4, 3, CARTESIAN, bc_val=(0.0, 0.0, 0.0, st.voltage)), st
+    if name == "axi_streamer":
+        st = Streamer2(refine_c=12.0, refine_tip=8e-3)
+        return Domain2(0.016, 64, 8, AXISYMMETRIC, bc_val=(0.0, 0.0, 0.0, st.voltage)), st
+    raise KeyError(name)
+
+
+def manufactured_gaussian2(dom: Domain2, levels, ij, sigma=0.05):
+    """phi* = y + exp(-rho^2/(2 sigma^2)) around the centre (0.5, 0.5) of
+    the unit square, and rho = -lap(phi*) at cell centres.  Cartesian: the
+    2-D Laplacian, (rho^2/sigma^4 - 2/sigma^2) g.  Axisymmetric: the
+    Gaussian is centred on the axis at z = 0.5, a 3-D radial Gaussian, so
+    (1/r) d/dr(r dg/dr) + d2g/dz2 = (rho^2/sigma^4 - 3/sigma^2) g."""
+    x, y = cell_centres2(dom, levels, ij)
+    xc = 0.0 if dom.geom == AXISYMMETRIC else 0.5
+    r2 = (x - xc) ** 2 + (y - 0.5) ** 2
+    g = np.exp(-r2 / (2.0 * sigma ** 2))
+    dims = 3.0 if dom.geom == AXISYMMETRIC else 2.0
+    return y + g, -(r2 / sigma ** 4 - dims / sigma ** 2) * g

@@ -56,3 +56,33 @@ def test_results_do_not_depend_on_thread_count():
     # covered every loop
     assert a["advance"][0] == 0 and a["advance"][2] > 0
     assert a["regrid"][0] + a["regrid"][1] > 0
+
+
+def run_quad(threads):
+    from oracle import quad
+    quad.set_threads(threads)
+    try:
+        dom, st = synth.workload2("axi_small")
+        o = quad.build_mesh(dom, st)
+        o.set_table(synth.coefficient_table())
+        t = o.tables()
+        ne, ni = synth.streamer_densities2(dom, st, t["level"], t["ij"])
+        o.set(quad.NE, ne)
+        o.set(quad.NI, ni)
+        o.charge_rhs(Q, EPS0)
+        out = [o.fmg(1e-8, 40)]
+        o.compute_field()
+        dt = o.dt_limit(Q, EPS0)
+        out.append(o.advance(dt, Q, EPS0, 1e-8, 40))
+        return out, [o.get(v) for v in (quad.PHI, quad.NE, quad.NI, quad.EMAG)]
+    finally:
+        quad.set_threads(1)
+
+
+def test_quad_results_do_not_depend_on_thread_count():
+    a, fa = run_quad(1)
+    b, fb = run_quad(4)
+    assert a == b
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    assert a[1][0] == 0 and a[1][2] > 0
