@@ -69,7 +69,12 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
            "sm_cnn_last_error",
-           "sm_batch_last_error"]
+           "sm_batch_last_error",
+           "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
+           "sm_quad_refine_level", "sm_quad_get_tables", "sm_quad_var_ptr", "sm_quad_upload",
+           "sm_quad_download", "sm_quad_set_table", "sm_quad_charge_rhs", "sm_quad_fmg",
+           "sm_quad_solve", "sm_quad_compute_field", "sm_quad_dt_limit", "sm_quad_fluid_stage",
+           "sm_quad_advance", "sm_quad_launch_count", "sm_quad_last_error"]
 
 
 def library_path() -> str:
@@ -145,6 +150,25 @@ def load():
         "sm_cnn_stats": [P, pI, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), pD],
         "sm_cnn_last_error": [P],
         "sm_last_error": [P],
+        "sm_quad_create": [C.POINTER(P), P, I, I, I, P],
+        "sm_quad_destroy": [P],
+        "sm_quad_arena_size": [P, C.POINTER(C.c_size_t)],
+        "sm_quad_bind_arena": [P, P, C.c_size_t],
+        "sm_quad_refine_level": [P, I, P, pI, pI],
+        "sm_quad_get_tables": [P, pI, pI, P, P, P, P, P, P, P],
+        "sm_quad_var_ptr": [P, I, C.POINTER(P)],
+        "sm_quad_upload": [P, I, P],
+        "sm_quad_download": [P, I, P],
+        "sm_quad_set_table": [P, I, D, P, P, P],
+        "sm_quad_charge_rhs": [P, D, D, I],
+        "sm_quad_fmg": [P, D, I, pI, pD],
+        "sm_quad_solve": [P, D, I, pI, pD],
+        "sm_quad_compute_field": [P],
+        "sm_quad_dt_limit": [P, D, D, pD],
+        "sm_quad_fluid_stage": [P, D],
+        "sm_quad_advance": [P, D, D, D, D, I, pD, P],
+        "sm_quad_launch_count": [P, C.POINTER(C.c_longlong)],
+        "sm_quad_last_error": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -596,3 +620,149 @@ class Network:
         rel = (C.c_double * 2)()
         self._ck(self._lib.sm_cnn_stats(self._h, C.byref(n), C.byref(p), C.byref(k), rel))
         return {"samples": n.value, "predictions": p.value, "kept": k.value, "last_rel": (rel[0], rel[1])}
+
+
+class _QuadDomain(C.Structure):
+    _fields_ = [("length", C.c_double), ("origin", C.c_double * 2), ("nb", C.c_int),
+                ("max_level", C.c_int), ("geometry", C.c_int), ("bc_type", C.c_int * 4),
+                ("bc_val", C.c_double * 4)]
+
+
+class Quad:
+    """A quadtree of 8^2-cell boxes with its fields on the current CUDA
+    device: the 2-D (geometry 0) or axisymmetric (geometry 1) variant."""
+
+    def __init__(self, dom, max_boxes: int, nu1: int = 2, nu2: int = 2, stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise SmError(SM_ECUDA, "no CUDA device")
+        self._lib, self.torch, self.dom = lib, torch, dom
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d = _QuadDomain(dom.length, (C.c_double * 2)(*dom.origin), dom.nb, dom.max_level, dom.geom,
+                        (C.c_int * 4)(*dom.bc_type), (C.c_double * 4)(*dom.bc_val))
+        h = C.c_void_p()
+        rc = lib.sm_quad_create(C.byref(h), C.byref(d), int(max_boxes), nu1, nu2,
+                                C.c_void_p(self.stream.cuda_stream))
+        if rc != SM_OK:
+            raise SmError(rc, "sm_quad_create failed")
+        self._h = h
+        size = C.c_size_t()
+        self._ck(lib.sm_quad_arena_size(h, C.byref(size)))
+        self.arena = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+        self._ck(lib.sm_quad_bind_arena(h, C.c_void_p(self.arena.data_ptr()), size.value))
+        self.max_boxes = int(max_boxes)
+
+    def _ck(self, rc):
+        if rc not in (SM_OK, SM_ENOCONV):
+            raise SmError(rc, self._lib.sm_quad_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.sm_quad_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- tables ----
+    def counts(self):
+        nb, nl = C.c_int(), C.c_int()
+        self._ck(self._lib.sm_quad_get_tables(self._h, C.byref(nb), C.byref(nl), *([None] * 7)))
+        return nb.value, nl.value
+
+    @property
+    def n_boxes(self) -> int:
+        return self.counts()[0]
+
+    @property
+    def n_levels(self) -> int:
+        return self.counts()[1]
+
+    def tables(self) -> dict:
+        n, nl = self.counts()
+        t = {"level_offset": np.zeros(nl + 1, np.int32), "level": np.zeros(n, np.int32),
+             "ij": np.zeros((n, 2), np.int32), "morton": np.zeros(n, np.uint64),
+             "parent": np.zeros(n, np.int32), "child": np.zeros((n, 4), np.int32),
+             "nbr": np.zeros((n, 8), np.int32)}
+        self._ck(self._lib.sm_quad_get_tables(self._h, None, None, *(_hp(t[k]) for k in (
+            "level_offset", "level", "ij", "morton", "parent", "child", "nbr"))))
+        return t
+
+    def level_ij(self, level: int) -> np.ndarray:
+        t = self.tables()
+        if level >= len(t["level_offset"]) - 1:
+            return np.zeros((0, 2), np.int32)
+        return t["ij"][t["level_offset"][level]:t["level_offset"][level + 1]]
+
+    def refine_level(self, level: int, flags) -> int:
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+        new, dropped = C.c_int(), C.c_int()
+        self._ck(self._lib.sm_quad_refine_level(self._h, level, _hp(flags), C.byref(new), C.byref(dropped)))
+        self.dropped = dropped.value
+        return new.value
+
+    # ---- fields ----
+    def upload(self, var: int, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.n_boxes, 64)
+        self._ck(self._lib.sm_quad_upload(self._h, var, _hp(a)))
+
+    def download(self, var: int) -> np.ndarray:
+        a = np.zeros((self.n_boxes, 64), np.float64)
+        self._ck(self._lib.sm_quad_download(self._h, var, _hp(a)))
+        return a
+
+    def view(self, var: int):
+        """[n_boxes][64] device tensor view of a field (no copy)."""
+        ptr = C.c_void_p()
+        self._ck(self._lib.sm_quad_var_ptr(self._h, var, C.byref(ptr)))
+        off = ptr.value - self.arena.data_ptr()
+        n = self.n_boxes
+        return self.arena[off:off + 8 * 64 * n].view(self.torch.float64).view(n, 64)
+
+    def set_table(self, tab: dict):
+        mu = np.ascontiguousarray(tab["mu"], np.float64)
+        dc = np.ascontiguousarray(tab["diff"], np.float64)
+        al = np.ascontiguousarray(tab["alpha"], np.float64)
+        self._ck(self._lib.sm_quad_set_table(self._h, len(mu), float(tab["e_max"]), _hp(mu), _hp(dc), _hp(al)))
+
+    # ---- operations ----
+    def charge_rhs(self, q=1.0, eps=1.0, use_rho=False):
+        self._ck(self._lib.sm_quad_charge_rhs(self._h, q, eps, int(use_rho)))
+
+    def fmg(self, tol=1e-8, max_cycles=50):
+        cyc, rel = C.c_int(), C.c_double()
+        rc = self._ck(self._lib.sm_quad_fmg(self._h, tol, max_cycles, C.byref(cyc), C.byref(rel)))
+        return rc, rel.value, cyc.value
+
+    def solve(self, tol=1e-8, max_cycles=50):
+        cyc, rel = C.c_int(), C.c_double()
+        rc = self._ck(self._lib.sm_quad_solve(self._h, tol, max_cycles, C.byref(cyc), C.byref(rel)))
+        return rc, rel.value, cyc.value
+
+    def compute_field(self):
+        self._ck(self._lib.sm_quad_compute_field(self._h))
+
+    def dt_limit(self, q, eps) -> float:
+        dt = C.c_double()
+        self._ck(self._lib.sm_quad_dt_limit(self._h, q, eps, C.byref(dt)))
+        return dt.value
+
+    def fluid_stage(self, dt):
+        self._ck(self._lib.sm_quad_fluid_stage(self._h, dt))
+
+    def advance(self, dt, q, eps, tol=1e-8, max_cycles=50):
+        dtn = C.c_double()
+        cyc = np.zeros(2, np.int32)
+        rc = self._ck(self._lib.sm_quad_advance(self._h, dt, q, eps, tol, max_cycles, C.byref(dtn), _hp(cyc)))
+        return rc, dtn.value, int(cyc[0]), int(cyc[1])
+
+    def launch_count(self) -> int:
+        n = C.c_longlong()
+        self._ck(self._lib.sm_quad_launch_count(self._h, C.byref(n)))
+        return n.value

@@ -1,0 +1,1253 @@
+// quad.cu -- 2-D and axisymmetric variants (arXiv:1708.08434, Sec. 1 and
+// 2.1.1: quadtree grids; Sec. 2.1.2 multigrid; Sec. 2.2-2.4 fluid step) on a
+// quadtree of 8^2-cell boxes, in Cartesian (x, y) or cylindrical (r, z)
+// coordinates.
+//
+// Tables are built by host C++ (proper nesting, Morton order per level) and
+// copied into the arena; every field operation runs in the kernels below,
+// one warp per box: the box and the ghost layer a kernel needs are staged in
+// shared memory, with coarse values at refinement boundaries read through
+// the parent's 8-neighbour table (proper nesting guarantees every coarse
+// cell a ghost or a prolongation needs lies in the parent or one of its
+// neighbours).
+//
+// Discretisation (the paper gives no 2-D or cylindrical formulas; these are
+// the finite-volume forms of the 3-D rules):
+//   L phi = [w_lo (phi_W - phi) + w_hi (phi_E - phi) + (phi_S - phi) + (phi_N - phi)] / h^2
+// with w_lo = r_{i-1/2}/r_i, w_hi = r_{i+1/2}/r_i in cylindrical coordinates
+// (r at (index + 1/2) h from the axis, so w_lo = 0 on the axis) and 1 in
+// Cartesian; red-black Gauss-Seidel solves the cell's row of that operator;
+// restriction is the volume-weighted mean of the four children (weights
+// proportional to the centre radius); prolongation (2c + c_x + c_y)/4;
+// coarse-fine potential ghost phi_f/3 + 2 phihat/3, phihat = 3/4 c + 1/4 c_t;
+// fluxes as in 3-D with the radial divergence weighted like L and the
+// coarse flux at a refinement boundary the area-weighted mean of the two
+// fine fluxes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sm_quad.h"
+
+namespace {
+
+constexpr int QN = 8;            // cells per box side
+constexpr int QC = QN * QN;      // cells per box
+constexpr int WPB = 4;           // boxes (warps) per block
+constexpr int QT = 32 * WPB;     // threads per block
+constexpr int QMAXL = SM_MAX_LEVELS;
+constexpr int S1 = QN + 2;       // staged side with one ghost layer
+constexpr int S2 = QN + 4;       // staged side with two ghost layers
+
+// fields in the arena: the public sm_var numbering first
+enum { V_PHI = 0, V_RHS, V_RES, V_NE, V_NI, V_EMAG, V_RHO, V_OLD, V_TMP, V_NE0, V_NI0, V_NE1, V_NI1, NV };
+
+struct QBc {
+  int type[4];      // 0 Neumann zero (and the axis), 1 Dirichlet
+  double g2[4];     // 2 g
+};
+
+struct QTabs {
+  const int *lev, *par, *chl, *nbr8;
+  const int2 *ij;
+  const double *w;   // [box][8][2]: w_lo, w_hi of column i
+  const double *wv;  // [box][8]: volume (and y-face area) weight of column i
+};
+
+struct QLut {
+  const double *mu, *diff, *alpha;
+  int n;
+  double de;         // e_max / (n - 1)
+};
+
+__device__ __forceinline__ int dir8(int dx, int dy) {
+  const int d = (dx + 1) + 3 * (dy + 1);
+  return d < 4 ? d : d - 1;
+}
+__device__ __forceinline__ int face_dir8(int f) {
+  return f < 2 ? dir8(f ? 1 : -1, 0) : dir8(0, f == 3 ? 1 : -1);
+}
+// cell at depth t from face f (t = 0 inner layer, t < 0 ghost layers), u along the face
+__device__ __forceinline__ void face_cell(int f, int t, int u, int &ci, int &cj) {
+  const int v = (f & 1) ? QN - 1 - t : t;
+  if (f < 2) {
+    ci = v;
+    cj = u;
+  } else {
+    ci = u;
+    cj = v;
+  }
+}
+
+// Box of level l-1 holding coarse cell (cx, cy) (cells per side ncl),
+// found from p, the parent of the level-l box asking: -1 outside the
+// domain; -2 (and the error flag) when the box does not exist.
+__device__ __forceinline__ int coarse_box(const QTabs &T, int p, int cx, int cy, int ncl, unsigned *err) {
+  if (cx < 0 || cy < 0 || cx >= ncl || cy >= ncl) return -1;
+  const int2 P = T.ij[p];
+  const int dx = (cx >> 3) - P.x, dy = (cy >> 3) - P.y;
+  if (dx == 0 && dy == 0) return p;
+  int b = -2;
+  if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) b = T.nbr8[8 * p + dir8(dx, dy)];
+  if (b == -2) atomicOr(err, 1u);
+  return b;
+}
+
+// value of var at coarse cell q, or across the wall from coarse cell `from`
+// (inside): Dirichlet (homog ? 0 : 2g) - v, Neumann / axis v; mirror: always v
+__device__ double coarse_val(const double *var, const QTabs &T, int p, int qx, int qy, int fx, int fy, int ncl,
+                             const QBc &bc, int homog, bool mirror, unsigned *err) {
+  const int b = coarse_box(T, p, qx, qy, ncl, err);
+  if (b >= 0) return var[(size_t)b * QC + (qx & 7) + QN * (qy & 7)];
+  if (b == -2) return 0.0;
+  const int bf = coarse_box(T, p, fx, fy, ncl, err);
+  const double v = bf >= 0 ? var[(size_t)bf * QC + (fx & 7) + QN * (fy & 7)] : 0.0;
+  if (mirror) return v;
+  const int f = qx < 0 ? 0 : (qx >= ncl ? 1 : (qy < 0 ? 2 : 3));
+  return bc.type[f] ? (homog ? 0.0 : bc.g2[f]) - v : v;
+}
+
+// Stage box b of level l into s (S1 x S1, interior at (i+1, j+1)) with the
+// potential ghost rules: same-level copy, wall ghost, refinement boundary
+// phi_f/3 + 2 phihat/3.  `sel` (optional): per box, read `alt` instead of
+// `var` for boxes with children (the FAS step's restricted values).
+__device__ void stage_phi(const double *var, const double *alt, const QTabs &T, int b, int l, const QBc &bc,
+                          int homog, double *s, int lane, unsigned *err) {
+  auto src = [&](int box) { return (alt && T.chl[4 * box] >= 0) ? alt : var; };
+  const double *own = src(b);
+  for (int c = lane; c < QC; c += 32) s[(c / QN + 1) * S1 + c % QN + 1] = own[(size_t)b * QC + c];
+  __syncwarp();
+  const int f = lane >> 3, u = lane & 7;
+  int ci, cj, gi, gj;
+  face_cell(f, 0, u, ci, cj);
+  face_cell(f, -1, u, gi, gj);
+  const double inner = s[(cj + 1) * S1 + ci + 1];
+  const int nb = T.nbr8[8 * b + face_dir8(f)];
+  double v;
+  if (nb >= 0) {
+    int si, sj;
+    face_cell(f ^ 1, 0, u, si, sj);
+    v = src(nb)[(size_t)nb * QC + si + QN * sj];
+  } else if (nb == -1) {
+    v = bc.type[f] ? (homog ? 0.0 : bc.g2[f]) - inner : inner;
+  } else {
+    const int2 B = T.ij[b];
+    const int p = T.par[b], ncl = QN << (l - 1);
+    const int Gx = B.x * QN + gi, Gy = B.y * QN + gj, cx = Gx >> 1, cy = Gy >> 1;
+    int qx = cx, qy = cy;
+    if (f < 2) qy += (Gy & 1) ? 1 : -1;
+    else qx += (Gx & 1) ? 1 : -1;
+    // the coarse level of a refinement boundary holds no refined values
+    // here: the cells across the face belong to a leaf
+    const double c = coarse_val(var, T, p, cx, cy, cx, cy, ncl, bc, homog, false, err);
+    const double ct = coarse_val(var, T, p, qx, qy, cx, cy, ncl, bc, homog, false, err);
+    const double phat = 0.75 * c + 0.25 * ct;
+    v = inner / 3.0 + 2.0 * phat / 3.0;
+  }
+  s[(gj + 1) * S1 + gi + 1] = v;
+  __syncwarp();
+}
+
+// L phi at staged cell (i, j) of box b
+__device__ __forceinline__ double lap_s(const double *s, const QTabs &T, int b, int i, int j, double inv_h2) {
+  const double c = s[(j + 1) * S1 + i + 1];
+  const double wl = T.w[(size_t)b * 16 + 2 * i], wh = T.w[(size_t)b * 16 + 2 * i + 1];
+  return (wl * (s[(j + 1) * S1 + i] - c) + wh * (s[(j + 1) * S1 + i + 2] - c) + (s[j * S1 + i + 1] - c) +
+          (s[(j + 2) * S1 + i + 1] - c)) * inv_h2;
+}
+
+#define QWARP()                                  \
+  const int wv_ = threadIdx.x >> 5, lane = threadIdx.x & 31; \
+  const int k_ = blockIdx.x * WPB + wv_;
+
+// one colour pass of red-black Gauss-Seidel on the n boxes of level l
+__global__ void __launch_bounds__(QT) k_q_rbgs(int off, int n, int l, int colour, double *__restrict__ phi,
+                                               const double *__restrict__ rhs, QTabs T, QBc bc, double h2,
+                                               unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;  // the whole warp
+  const int b = off + k_;
+  double *s = sm[wv_];
+  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  const int j = lane >> 2, i = 2 * (lane & 3) + ((j + colour) & 1);
+  const double wl = T.w[(size_t)b * 16 + 2 * i], wh = T.w[(size_t)b * 16 + 2 * i + 1];
+  phi[(size_t)b * QC + i + QN * j] =
+      (wl * s[(j + 1) * S1 + i] + wh * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
+       h2 * rhs[(size_t)b * QC + i + QN * j]) /
+      (wl + wh + 2.0);
+}
+
+// Residual of every box of level l restricted to its parent's quadrant:
+// the restricted potential into old[parent] (committed by k_q_fas, so that
+// coarse values read for ghosts here stay unchanged), the restricted
+// residual into rhs[parent].  Volume-weighted mean of the four children.
+__global__ void __launch_bounds__(QT) k_q_resid_restrict(int off, int n, int l, const double *__restrict__ phi,
+                                                         double *__restrict__ rhs, double *__restrict__ old,
+                                                         QTabs T, QBc bc, double inv_h2, unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  __shared__ double sr[WPB][QC];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = off + k_;
+  double *s = sm[wv_];
+  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  for (int c = lane; c < QC; c += 32) {
+    const int i = c % QN, j = c / QN;
+    sr[wv_][c] = rhs[(size_t)b * QC + c] - lap_s(s, T, b, i, j, inv_h2);
+  }
+  __syncwarp();
+  const int p = T.par[b];
+  const int2 B = T.ij[b];
+  const int m = lane & 15, ii = m & 3, jj = m >> 2;
+  double sum = 0.0, wsum = 0.0;
+  for (int dj = 0; dj < 2; ++dj)
+    for (int di = 0; di < 2; ++di) {
+      const int i = 2 * ii + di, j = 2 * jj + dj;
+      const double w = T.wv[(size_t)b * QN + i];
+      sum += w * (lane < 16 ? s[(j + 1) * S1 + i + 1] : sr[wv_][i + QN * j]);
+      wsum += w;
+    }
+  const int I = 4 * (B.x & 1) + ii, J = 4 * (B.y & 1) + jj;
+  (lane < 16 ? old : rhs)[(size_t)p * QC + I + QN * J] = sum / wsum;
+}
+
+// Level l (all boxes): refined boxes take their restricted potential from
+// old and get the FAS right-hand side f += L phi; every box ends with
+// old = phi (the values the coarse correction is measured against).
+__global__ void __launch_bounds__(QT) k_q_fas(int off, int n, int l, double *__restrict__ phi,
+                                              double *__restrict__ rhs, double *__restrict__ old, QTabs T, QBc bc,
+                                              double inv_h2, unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = off + k_;
+  const bool refined = T.chl[4 * b] >= 0;
+  double *s = sm[wv_];
+  if (refined) stage_phi(phi, old, T, b, l, bc, 0, s, lane, err);
+  for (int c = lane; c < QC; c += 32) {
+    const size_t g = (size_t)b * QC + c;
+    if (refined) {
+      rhs[g] += lap_s(s, T, b, c % QN, c / QN, inv_h2);
+      phi[g] = old[g];
+    } else {
+      old[g] = phi[g];
+    }
+  }
+}
+
+// Prolongation to every box of level l: (2c + c_x + c_y)/4 of the parent
+// level.  corr: the correction phi - old (homogeneous wall ghosts) added to
+// phi; otherwise phi itself (FMG, wall values) replaces phi.
+__global__ void __launch_bounds__(QT) k_q_prolong(int off, int n, int l, double *__restrict__ phi,
+                                                  const double *__restrict__ old, int corr, QTabs T, QBc bc,
+                                                  unsigned *err) {
+  QWARP();
+  if (k_ >= n) return;
+  const int b = off + k_, p = T.par[b], ncl = QN << (l - 1);
+  const int2 B = T.ij[b];
+  auto cv = [&](int qx, int qy, int fx, int fy) {
+    const double a = coarse_val(phi, T, p, qx, qy, fx, fy, ncl, bc, corr, false, err);
+    return corr ? a - coarse_val(old, T, p, qx, qy, fx, fy, ncl, bc, corr, false, err) : a;
+  };
+  for (int c = lane; c < QC; c += 32) {
+    const int Gx = B.x * QN + c % QN, Gy = B.y * QN + c / QN, cx = Gx >> 1, cy = Gy >> 1;
+    const double sum = 2.0 * cv(cx, cy, cx, cy) + cv(cx + ((Gx & 1) ? 1 : -1), cy, cx, cy) +
+                       cv(cx, cy + ((Gy & 1) ? 1 : -1), cx, cy);
+    const size_t g = (size_t)b * QC + c;
+    if (corr) phi[g] += 0.25 * sum;
+    else phi[g] = 0.25 * sum;
+  }
+}
+
+// Exact level-0 solve (one box): phi = A^-1 (f - L0), A the operator's
+// matrix with homogeneous wall ghosts (inverted on the host), L0 the
+// operator of phi = 0 with the wall values.
+__global__ void k_q_coarse(double *__restrict__ phi, const double *__restrict__ rhs, const double *__restrict__ ainv,
+                           QTabs T, QBc bc, double inv_h2) {
+  __shared__ double r[QC];
+  const int c = threadIdx.x, i = c % QN, j = c / QN;
+  const double wl = T.w[2 * i], wh = T.w[2 * i + 1];
+  double l0 = 0.0;
+  if (i == 0 && bc.type[0]) l0 += wl * bc.g2[0];
+  if (i == QN - 1 && bc.type[1]) l0 += wh * bc.g2[1];
+  if (j == 0 && bc.type[2]) l0 += bc.g2[2];
+  if (j == QN - 1 && bc.type[3]) l0 += bc.g2[3];
+  r[c] = rhs[c] - l0 * inv_h2;
+  __syncthreads();
+  double acc = 0.0;
+  for (int k = 0; k < QC; ++k) acc += ainv[c * QC + k] * r[k];
+  phi[c] = acc;
+}
+
+__device__ __forceinline__ void max_bits(unsigned long long *slot, double v) {
+  unsigned long long x = (unsigned long long)__double_as_longlong(fabs(v));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, x);
+}
+
+// max |f - L var| over the leaf cells of all boxes (var = a zero array for
+// the denominator)
+__global__ void __launch_bounds__(QT) k_q_resmax(int n, const double *__restrict__ var,
+                                                 const double *__restrict__ rhs, QTabs T, QBc bc,
+                                                 const double *__restrict__ inv_h2, unsigned long long *slot,
+                                                 unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  if (T.chl[4 * b] >= 0) return;
+  double *s = sm[wv_];
+  const int l = T.lev[b];
+  stage_phi(var, nullptr, T, b, l, bc, 0, s, lane, err);
+  double m = 0.0;
+  for (int c = lane; c < QC; c += 32)
+    m = fmax(m, fabs(rhs[(size_t)b * QC + c] - lap_s(s, T, b, c % QN, c / QN, inv_h2[l])));
+  max_bits(slot, m);
+}
+
+// Eq. 5 on leaf cells
+__global__ void k_q_charge(int n, double *__restrict__ rhs, const double *__restrict__ ne,
+                           const double *__restrict__ ni, const double *__restrict__ rho, const int *__restrict__ chl,
+                           double q, double eps, int use_rho) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= (long long)n * QC) return;
+  if (chl[4 * (g / QC)] >= 0) return;
+  rhs[g] = use_rho ? -rho[g] / eps : -q * (ni[g] - ne[g]) / eps;
+}
+
+// |E| on leaf cells: face fields (phi_i - phi_{i+1})/h, cell components the
+// mean of the two faces; zero on refined boxes
+__global__ void __launch_bounds__(QT) k_q_field(int n, const double *__restrict__ phi, double *__restrict__ emag,
+                                                QTabs T, QBc bc, const double *__restrict__ inv_h,
+                                                unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  if (T.chl[4 * b] >= 0) {
+    for (int c = lane; c < QC; c += 32) emag[(size_t)b * QC + c] = 0.0;
+    return;
+  }
+  double *s = sm[wv_];
+  const int l = T.lev[b];
+  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  const double ih = inv_h[l];
+  for (int c = lane; c < QC; c += 32) {
+    const int i = c % QN, j = c / QN;
+    const double pc = s[(j + 1) * S1 + i + 1];
+    const double ex = ((s[(j + 1) * S1 + i] - pc) * ih + (pc - s[(j + 1) * S1 + i + 2]) * ih) / 2.0;
+    const double ey = ((s[j * S1 + i + 1] - pc) * ih + (pc - s[(j + 2) * S1 + i + 1]) * ih) / 2.0;
+    emag[(size_t)b * QC + c] = sqrt(ex * ex + ey * ey);
+  }
+}
+
+__device__ __forceinline__ double lut(const double *t, const QLut &L, double e) {
+  const double x = e / L.de;
+  if (x <= 0.0) return t[0];
+  if (x >= L.n - 1) return t[L.n - 1];
+  const int i = (int)x;
+  const double w = x - i;
+  return t[i] + w * (t[i + 1] - t[i]);
+}
+
+// psi(a/b) b of the Koren limiter, division-free (Eq. 7)
+__device__ __forceinline__ double koren(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  const double s = b > 0.0 ? 1.0 : -1.0, aa = fabs(a), bb = fabs(b);
+  double m = bb;
+  m = fmin(m, (2.0 * bb + aa) / 6.0);
+  m = fmin(m, aa);
+  return s * m;
+}
+
+// Stage the density n with two ghost layers (S2 x S2, interior at (i+2,
+// j+2)), the potential (S1) and |E| with one layer: density ghosts are
+// same-level copies, mirrors at walls and the axis, and at refinement
+// boundaries the prolongation (2c + c_x + c_y)/4 of the coarse cell
+// containing the ghost, limited to 2c; |E| ghosts the inner value at walls
+// and the coarse cell's value at refinement boundaries.
+__device__ void stage_fluid(const double *nv, const double *phi, const double *emag, const QTabs &T, int b,
+                            int l, const QBc &bc, double *sn, double *sp, double *se, int lane, unsigned *err) {
+  stage_phi(phi, nullptr, T, b, l, bc, 0, sp, lane, err);
+  for (int c = lane; c < QC; c += 32) {
+    sn[(c / QN + 2) * S2 + c % QN + 2] = nv[(size_t)b * QC + c];
+    se[(c / QN + 1) * S1 + c % QN + 1] = emag[(size_t)b * QC + c];
+  }
+  __syncwarp();
+  const int2 B = T.ij[b];
+  const int p = l > 0 ? T.par[b] : 0, ncl = l > 0 ? (QN << (l - 1)) : 0;
+  for (int g = lane; g < 64; g += 32) {  // density: 4 faces x 2 layers x 8
+    const int f = g >> 4, t = 1 + ((g >> 3) & 1), u = g & 7;
+    int gi, gj;
+    face_cell(f, -t, u, gi, gj);
+    const int nb = T.nbr8[8 * b + face_dir8(f)];
+    double v;
+    if (nb >= 0) {
+      int si, sj;
+      face_cell(f ^ 1, t - 1, u, si, sj);
+      v = nv[(size_t)nb * QC + si + QN * sj];
+    } else if (nb == -1) {
+      int mi, mj;
+      face_cell(f, t - 1, u, mi, mj);
+      v = sn[(mj + 2) * S2 + mi + 2];
+    } else {
+      const int Gx = B.x * QN + gi, Gy = B.y * QN + gj, cx = Gx >> 1, cy = Gy >> 1;
+      const double c = coarse_val(nv, T, p, cx, cy, cx, cy, ncl, bc, 0, true, err);
+      const double sum = 2.0 * c + coarse_val(nv, T, p, cx + ((Gx & 1) ? 1 : -1), cy, cx, cy, ncl, bc, 0, true, err) +
+                         coarse_val(nv, T, p, cx, cy + ((Gy & 1) ? 1 : -1), cx, cy, ncl, bc, 0, true, err);
+      v = fmin(0.25 * sum, 2.0 * c);
+    }
+    sn[(gj + 2) * S2 + gi + 2] = v;
+  }
+  {  // |E|: 4 faces x 8
+    const int f = lane >> 3, u = lane & 7;
+    int ci, cj, gi, gj;
+    face_cell(f, 0, u, ci, cj);
+    face_cell(f, -1, u, gi, gj);
+    const int nb = T.nbr8[8 * b + face_dir8(f)];
+    double v;
+    if (nb >= 0) {
+      int si, sj;
+      face_cell(f ^ 1, 0, u, si, sj);
+      v = emag[(size_t)nb * QC + si + QN * sj];
+    } else if (nb == -1) {
+      v = se[(cj + 1) * S1 + ci + 1];
+    } else {
+      const int cx = (B.x * QN + gi) >> 1, cy = (B.y * QN + gj) >> 1;
+      v = coarse_val(emag, T, p, cx, cy, cx, cy, ncl, bc, 0, true, err);
+    }
+    se[(gj + 1) * S1 + gi + 1] = v;
+  }
+  __syncwarp();
+}
+
+// flux through face m (between cells m-1 and m) along axis a at u
+__device__ __forceinline__ double face_flux(const double *sn, const double *sp, const double *se, int a, int m, int u,
+                                            double h, double ih, const QLut &L) {
+  auto N_ = [&](int t) { return a == 0 ? sn[(u + 2) * S2 + t + 2] : sn[(t + 2) * S2 + u + 2]; };
+  auto P_ = [&](int t) { return a == 0 ? sp[(u + 1) * S1 + t + 1] : sp[(t + 1) * S1 + u + 1]; };
+  auto E_ = [&](int t) { return a == 0 ? se[(u + 1) * S1 + t + 1] : se[(t + 1) * S1 + u + 1]; };
+  const double nL2 = N_(m - 2), nL = N_(m - 1), nR = N_(m), nR2 = N_(m + 1);
+  const double e_face = (P_(m - 1) - P_(m)) * ih, e_star = (E_(m - 1) + E_(m)) / 2.0;
+  const double mu = lut(L.mu, L, e_star), dc = lut(L.diff, L, e_star);
+  const double v = -mu * e_face;
+  const double nf = v < 0.0 ? nR - koren(nR2 - nR, nR - nL) : nL + koren(nL - nL2, nR - nL);
+  return v * nf - dc * (nR - nL) / h;
+  (void)h;
+}
+
+// Fine-side fluxes of every leaf box face that borders a coarser leaf:
+// cflux[box][face][u]
+__global__ void __launch_bounds__(QT) k_q_cf_flux(int n, const double *__restrict__ nv, const double *__restrict__ phi,
+                                                  const double *__restrict__ emag, double *__restrict__ cflux,
+                                                  QTabs T, QBc bc, QLut L, const double *__restrict__ hs,
+                                                  unsigned *err) {
+  __shared__ double snm[WPB][S2 * S2], spm[WPB][S1 * S1], sem[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  if (T.chl[4 * b] >= 0) return;
+  bool any = false;
+  for (int f = 0; f < 4; ++f) any |= T.nbr8[8 * b + face_dir8(f)] == -2;
+  if (!any) return;
+  const int l = T.lev[b];
+  stage_fluid(nv, phi, emag, T, b, l, bc, snm[wv_], spm[wv_], sem[wv_], lane, err);
+  const int f = lane >> 3, u = lane & 7;
+  if (T.nbr8[8 * b + face_dir8(f)] == -2)
+    cflux[(size_t)b * 32 + f * 8 + u] =
+        face_flux(snm[wv_], spm[wv_], sem[wv_], f >> 1, (f & 1) ? QN : 0, u, hs[l], 1.0 / hs[l], L);
+}
+
+// One forward Euler stage on every leaf box: dst = src - dt div F + dt
+// alpha mu |E| n_e (Eq. 2-3); a face next to a refined box takes the
+// area-weighted mean of the two fine fluxes from cflux.
+__global__ void __launch_bounds__(QT) k_q_update(int n, const double *__restrict__ ne, const double *__restrict__ ni,
+                                                 double *__restrict__ ne_out, double *__restrict__ ni_out,
+                                                 const double *__restrict__ phi, const double *__restrict__ emag,
+                                                 const double *__restrict__ cflux, QTabs T, QBc bc, QLut L,
+                                                 const double *__restrict__ hs, double dt, unsigned *err) {
+  __shared__ double snm[WPB][S2 * S2], spm[WPB][S1 * S1], sem[WPB][S1 * S1];
+  __shared__ double sf[WPB][2][(QN + 1) * QN];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  if (T.chl[4 * b] >= 0) return;
+  const int l = T.lev[b];
+  const double h = hs[l], ih = 1.0 / h;
+  stage_fluid(ne, phi, emag, T, b, l, bc, snm[wv_], spm[wv_], sem[wv_], lane, err);
+  for (int g = lane; g < 2 * (QN + 1) * QN; g += 32) {
+    const int a = g / ((QN + 1) * QN), r = g % ((QN + 1) * QN), m = r / QN, u = r % QN;
+    double F = face_flux(snm[wv_], spm[wv_], sem[wv_], a, m, u, h, ih, L);
+    if (m == 0 || m == QN) {
+      const int f = 2 * a + (m == QN ? 1 : 0);
+      const int nb = T.nbr8[8 * b + face_dir8(f)];
+      if (nb >= 0 && T.chl[4 * nb] >= 0) {  // refined neighbour: mean of its fine fluxes
+        int cx, cy;
+        if (a == 0) {
+          cx = (f & 1) ? 0 : 1;
+          cy = u >> 2;
+        } else {
+          cx = u >> 2;
+          cy = (f & 1) ? 0 : 1;
+        }
+        const int ch = T.chl[4 * nb + cx + 2 * cy];
+        double s = 0.0, ws = 0.0;
+        for (int du = 0; du < 2; ++du) {
+          const int uf = 2 * (u & 3) + du;
+          const double w = a == 0 ? 1.0 : T.wv[(size_t)ch * QN + uf];
+          s += w * cflux[(size_t)ch * 32 + (f ^ 1) * 8 + uf];
+          ws += w;
+        }
+        F = s / ws;
+      }
+    }
+    sf[wv_][a][m * QN + u] = F;
+  }
+  __syncwarp();
+  for (int c = lane; c < QC; c += 32) {
+    const int i = c % QN, j = c / QN;
+    const double wl = T.w[(size_t)b * 16 + 2 * i], wh = T.w[(size_t)b * 16 + 2 * i + 1];
+    const double div = (wh * sf[wv_][0][(i + 1) * QN + j] - wl * sf[wv_][0][i * QN + j]) / h +
+                       (sf[wv_][1][(j + 1) * QN + i] - sf[wv_][1][j * QN + i]) / h;
+    const double e = sem[wv_][(j + 1) * S1 + i + 1];
+    const size_t g = (size_t)b * QC + c;
+    const double src = lut(L.alpha, L, e) * lut(L.mu, L, e) * e * ne[g];
+    ne_out[g] = ne[g] - dt * div + dt * src;
+    ni_out[g] = ni[g] + dt * src;
+  }
+}
+
+// parents' quadrants := volume-weighted restriction of the n boxes of a level
+__global__ void __launch_bounds__(QT) k_q_restrict(int off, int n, double *__restrict__ v, QTabs T) {
+  QWARP();
+  if (k_ >= n) return;
+  const int b = off + k_;
+  if (lane >= 16) return;
+  const int p = T.par[b];
+  const int2 B = T.ij[b];
+  const int ii = lane & 3, jj = lane >> 2;
+  double sum = 0.0, wsum = 0.0;
+  for (int dj = 0; dj < 2; ++dj)
+    for (int di = 0; di < 2; ++di) {
+      const int i = 2 * ii + di, j = 2 * jj + dj;
+      const double w = T.wv[(size_t)b * QN + i];
+      sum += w * v[(size_t)b * QC + i + QN * j];
+      wsum += w;
+    }
+  v[(size_t)p * QC + 4 * (B.x & 1) + ii + QN * (4 * (B.y & 1) + jj)] = sum / wsum;
+}
+
+// time-step limits: max over leaf cells of sum|v_d|/dx, that plus 4D/dx^2,
+// and mu n_e (slots 0..2, bit patterns of non-negative doubles)
+__global__ void __launch_bounds__(QT) k_q_dt(int n, const double *__restrict__ phi, const double *__restrict__ emag,
+                                             const double *__restrict__ ne, QTabs T, QBc bc, QLut L,
+                                             const double *__restrict__ hs, unsigned long long *slots,
+                                             unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  if (T.chl[4 * b] >= 0) return;
+  const int l = T.lev[b];
+  double *s = sm[wv_];
+  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  const double h = hs[l];
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  for (int c = lane; c < QC; c += 32) {
+    const int i = c % QN, j = c / QN;
+    const double pc = s[(j + 1) * S1 + i + 1];
+    const double ex = ((s[(j + 1) * S1 + i] - pc) / h + (pc - s[(j + 1) * S1 + i + 2]) / h) / 2.0;
+    const double ey = ((s[j * S1 + i + 1] - pc) / h + (pc - s[(j + 2) * S1 + i + 1]) / h) / 2.0;
+    const double e = emag[(size_t)b * QC + c];
+    const double mu = lut(L.mu, L, e), dc = lut(L.diff, L, e);
+    const double adv = (fabs(mu * ex) + fabs(mu * ey)) / h;
+    m0 = fmax(m0, adv);
+    m1 = fmax(m1, adv + 2.0 * 2.0 * dc / (h * h));
+    m2 = fmax(m2, mu * ne[(size_t)b * QC + c]);
+  }
+  max_bits(slots, m0);
+  max_bits(slots + 1, m1);
+  max_bits(slots + 2, m2);
+}
+
+__global__ void k_q_average(long long n, double *__restrict__ a, const double *__restrict__ b0,
+                            const double *__restrict__ b1) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g < n) a[g] = (b0[g] + b1[g]) / 2.0;
+}
+
+int blocks_for(long long boxes) { return (int)std::max<long long>(1, (boxes + WPB - 1) / WPB); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct sm_quad {
+  sm_quad_domain dom{};
+  int max_boxes = 0, nu1 = 2, nu2 = 2, lbase = 0, lmax = 0;
+  cudaStream_t stream = nullptr;
+  QBc bc{};
+  std::string err;
+  long long launches = 0;
+  // host tables
+  std::vector<int> lev, ix, iy, par, chl, nbr8;
+  std::vector<uint64_t> mort;
+  std::vector<double> w, wv;
+  int nlev = 0;
+  int off[QMAXL + 2] = {0};
+  // arena
+  char *arena = nullptr;
+  int *d_lev = nullptr, *d_par = nullptr, *d_chl = nullptr, *d_nbr8 = nullptr;
+  int2 *d_ij = nullptr;
+  double *d_w = nullptr, *d_wv = nullptr;
+  double *var[NV] = {nullptr};
+  double *cflux = nullptr, *ainv = nullptr, *lut = nullptr, *d_h = nullptr;
+  unsigned long long *slots = nullptr;
+  unsigned *d_err = nullptr;
+  int lut_n = 0;
+  double lut_emax = 0.0;
+  double h[QMAXL], inv_h2[QMAXL];
+  std::vector<double> h_ainv;
+};
+
+namespace {
+
+int qfail(sm_quad *q, int code, const std::string &msg) {
+  if (q) q->err = msg;
+  return code;
+}
+
+uint64_t morton2(int i, int j) {
+  uint64_t k = 0;
+  for (int b = 0; b < 31; ++b) k |= (uint64_t)((i >> b) & 1) << (2 * b) | (uint64_t)((j >> b) & 1) << (2 * b + 1);
+  return k;
+}
+
+int dir8h(int dx, int dy) {
+  const int d = (dx + 1) + 3 * (dy + 1);
+  return d < 4 ? d : d - 1;
+}
+
+int find_box(const sm_quad *q, int l, int i, int j) {
+  const int n = 1 << l;
+  if (i < 0 || j < 0 || i >= n || j >= n) return -1;
+  if (l >= q->nlev) return -2;
+  const uint64_t key = morton2(i, j);
+  int lo = q->off[l], hi = q->off[l + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) / 2;
+    if (q->mort[mid] == key) return mid;
+    if (q->mort[mid] < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -2;
+}
+
+void add_box(sm_quad *q, int l, int i, int j, int parent) {
+  q->lev.push_back(l);
+  q->ix.push_back(i);
+  q->iy.push_back(j);
+  q->par.push_back(parent);
+  q->mort.push_back(morton2(i, j));
+  for (int c = 0; c < 4; ++c) q->chl.push_back(-1);
+  for (int d = 0; d < 8; ++d) q->nbr8.push_back(-2);
+  // radial weights of the box's columns (global x index gx at level l)
+  for (int c = 0; c < QN; ++c) {
+    const int gx = i * QN + c;
+    const bool cyl = q->dom.geometry == SM_AXISYMMETRIC;
+    q->w.push_back(cyl ? (double)gx / (gx + 0.5) : 1.0);
+    q->w.push_back(cyl ? (gx + 1.0) / (gx + 0.5) : 1.0);
+    q->wv.push_back(cyl ? gx + 0.5 : 1.0);
+  }
+}
+
+void set_neighbours(sm_quad *q, int l) {
+  for (int b = q->off[l]; b < q->off[l + 1]; ++b)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if (dx || dy) q->nbr8[8 * b + dir8h(dx, dy)] = find_box(q, l, q->ix[b] + dx, q->iy[b] + dy);
+}
+
+int n_boxes(const sm_quad *q) { return (int)q->lev.size(); }
+
+int upload_tables(sm_quad *q) {
+  const int n = n_boxes(q);
+  std::vector<int2> ij(n);
+  for (int b = 0; b < n; ++b) ij[b] = make_int2(q->ix[b], q->iy[b]);
+  cudaStream_t s = q->stream;
+  if (cudaMemcpyAsync(q->d_lev, q->lev.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_par, q->par.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_chl, q->chl.data(), sizeof(int) * 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_nbr8, q->nbr8.data(), sizeof(int) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_ij, ij.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_w, q->w.data(), sizeof(double) * 16 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_wv, q->wv.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "table upload");
+  return SM_OK;
+}
+
+QTabs tabs(const sm_quad *q) { return {q->d_lev, q->d_par, q->d_chl, q->d_nbr8, q->d_ij, q->d_w, q->d_wv}; }
+QLut qlut(const sm_quad *q) {
+  return {q->lut, q->lut + q->lut_n, q->lut + 2 * q->lut_n, q->lut_n, q->lut_emax / (q->lut_n - 1)};
+}
+
+// the level-0 operator with homogeneous wall ghosts (columns L e_k) and its
+// inverse by Gauss-Jordan elimination with partial pivoting (host)
+void coarse_inverse(sm_quad *q) {
+  const int n = QC;
+  std::vector<double> A((size_t)n * n, 0.0), I((size_t)n * n, 0.0);
+  const double ih2 = q->inv_h2[0];
+  for (int r = 0; r < n; ++r) {
+    const int i = r % QN, j = r / QN;
+    const double wl = q->w[2 * i], wh = q->w[2 * i + 1];
+    const double wf[4] = {wl, wh, 1.0, 1.0};
+    const int nbr[4] = {i > 0 ? r - 1 : -1, i < QN - 1 ? r + 1 : -1, j > 0 ? r - QN : -1, j < QN - 1 ? r + QN : -1};
+    for (int f = 0; f < 4; ++f) {
+      // L phi = sum_f w_f (phi_f - phi): a wall ghost is -phi (Dirichlet) or phi
+      A[(size_t)r * n + r] -= wf[f] * ih2;
+      if (nbr[f] >= 0) A[(size_t)r * n + nbr[f]] += wf[f] * ih2;
+      else A[(size_t)r * n + r] += (q->bc.type[f] ? -1.0 : 1.0) * wf[f] * ih2;
+    }
+    I[(size_t)r * n + r] = 1.0;
+  }
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)p * n + c])) p = r;
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)c * n + k], A[(size_t)p * n + k]);
+        std::swap(I[(size_t)c * n + k], I[(size_t)p * n + k]);
+      }
+    const double d = A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] /= d;
+      I[(size_t)c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double m = A[(size_t)r * n + c];
+      if (m == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)r * n + k] -= m * A[(size_t)c * n + k];
+        I[(size_t)r * n + k] -= m * I[(size_t)c * n + k];
+      }
+    }
+  }
+  q->h_ainv = I;
+}
+
+int check(sm_quad *q, const char *what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return qfail(q, SM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return SM_OK;
+}
+
+int level_count(const sm_quad *q, int l) { return q->off[l + 1] - q->off[l]; }
+
+void smooth(sm_quad *q, int l, int nu) {
+  const int n = level_count(q, l);
+  for (int s = 0; s < nu; ++s)
+    for (int c = 0; c < 2; ++c) {
+      k_q_rbgs<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, c, q->var[V_PHI], q->var[V_RHS], tabs(q),
+                                                   q->bc, q->h[l] * q->h[l], q->d_err);
+      ++q->launches;
+    }
+}
+
+void coarse_solve(sm_quad *q) {
+  k_q_coarse<<<1, QC, 0, q->stream>>>(q->var[V_PHI], q->var[V_RHS], q->ainv, tabs(q), q->bc, q->inv_h2[0]);
+  ++q->launches;
+}
+
+void vcycle(sm_quad *q, int top) {
+  for (int l = top; l >= 1; --l) {
+    smooth(q, l, q->nu1);
+    const int n = level_count(q, l), nc = level_count(q, l - 1);
+    k_q_resid_restrict<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, q->var[V_PHI], q->var[V_RHS],
+                                                             q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l], q->d_err);
+    k_q_fas<<<blocks_for(nc), QT, 0, q->stream>>>(q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS],
+                                                   q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
+    q->launches += 2;
+  }
+  coarse_solve(q);
+  for (int l = 1; l <= top; ++l) {
+    const int n = level_count(q, l);
+    k_q_prolong<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, q->var[V_PHI], q->var[V_OLD], 1, tabs(q),
+                                                      q->bc, q->d_err);
+    ++q->launches;
+    smooth(q, l, q->nu2);
+  }
+}
+
+// max leaf residual of var (the potential, or the zero array)
+int resmax(sm_quad *q, int v, double *out) {
+  const int n = n_boxes(q);
+  if (cudaMemsetAsync(q->slots + 4, 0, sizeof(unsigned long long), q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "memset");
+  k_q_resmax<<<blocks_for(n), QT, 0, q->stream>>>(n, q->var[v], q->var[V_RHS], tabs(q), q->bc, q->d_h + QMAXL,
+                                                   q->slots + 4, q->d_err);
+  ++q->launches;
+  unsigned long long bits = 0;
+  unsigned e = 0;
+  if (cudaMemcpyAsync(&bits, q->slots + 4, sizeof(bits), cudaMemcpyDeviceToHost, q->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&e, q->d_err, sizeof(e), cudaMemcpyDeviceToHost, q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "residual norm");
+  if (e) return qfail(q, SM_ESTATE, "a coarse box needed at a refinement boundary is missing");
+  double d;
+  std::memcpy(&d, &bits, sizeof(d));
+  *out = d;
+  return SM_OK;
+}
+
+int rel_residual(sm_quad *q, double *rel) {
+  double num = 0.0, den = 0.0;
+  if (cudaMemsetAsync(q->var[V_TMP], 0, sizeof(double) * QC * (size_t)n_boxes(q), q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "memset");
+  if (int st = resmax(q, V_PHI, &num)) return st;
+  if (int st = resmax(q, V_TMP, &den)) return st;
+  *rel = den > 0.0 ? num / den : num;
+  return SM_OK;
+}
+
+int solve_loop(sm_quad *q, double tol, int max_cycles, int c0, int *cycles, double *rel) {
+  int c = c0;
+  double r = 0.0;
+  if (c0 > 0) {
+    if (int st = rel_residual(q, &r)) return st;
+  }
+  while (c == 0 || (r > tol && c < max_cycles)) {
+    vcycle(q, q->nlev - 1);
+    ++c;
+    if (int st = check(q, "V-cycle")) return st;
+    if (int st = rel_residual(q, &r)) return st;
+  }
+  if (cycles) *cycles = c;
+  if (rel) *rel = r;
+  return r <= tol ? SM_OK : qfail(q, SM_ENOCONV, "tolerance not reached");
+}
+
+void restrict_all(sm_quad *q, int v) {
+  for (int l = q->nlev - 1; l >= 1; --l) {
+    const int n = level_count(q, l);
+    k_q_restrict<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, q->var[v], tabs(q));
+    ++q->launches;
+  }
+}
+
+int euler_stage(sm_quad *q, int sne, int sni, int dne, int dni, double dt) {
+  const int n = n_boxes(q);
+  k_q_cf_flux<<<blocks_for(n), QT, 0, q->stream>>>(n, q->var[sne], q->var[V_PHI], q->var[V_EMAG], q->cflux, tabs(q),
+                                                    q->bc, qlut(q), q->d_h, q->d_err);
+  k_q_update<<<blocks_for(n), QT, 0, q->stream>>>(n, q->var[sne], q->var[sni], q->var[dne], q->var[dni],
+                                                   q->var[V_PHI], q->var[V_EMAG], q->cflux, tabs(q), q->bc, qlut(q),
+                                                   q->d_h, dt, q->d_err);
+  q->launches += 2;
+  restrict_all(q, dne);
+  restrict_all(q, dni);
+  return check(q, "fluid stage");
+}
+
+int charge(sm_quad *q, double c, double eps, int use_rho) {
+  const long long cells = (long long)n_boxes(q) * QC;
+  k_q_charge<<<(int)((cells + 255) / 256), 256, 0, q->stream>>>(n_boxes(q), q->var[V_RHS], q->var[V_NE],
+                                                                  q->var[V_NI], q->var[V_RHO], q->d_chl, c, eps,
+                                                                  use_rho);
+  ++q->launches;
+  return check(q, "charge");
+}
+
+int field(sm_quad *q) {
+  const int n = n_boxes(q);
+  k_q_field<<<blocks_for(n), QT, 0, q->stream>>>(n, q->var[V_PHI], q->var[V_EMAG], tabs(q), q->bc,
+                                                  q->d_h + 2 * QMAXL, q->d_err);
+  ++q->launches;
+  return check(q, "field");
+}
+
+int dt_limit(sm_quad *q, double c, double eps, double *dt) {
+  const int n = n_boxes(q);
+  if (cudaMemsetAsync(q->slots, 0, 3 * sizeof(unsigned long long), q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "memset");
+  k_q_dt<<<blocks_for(n), QT, 0, q->stream>>>(n, q->var[V_PHI], q->var[V_EMAG], q->var[V_NE], tabs(q), q->bc,
+                                               qlut(q), q->d_h, q->slots, q->d_err);
+  ++q->launches;
+  unsigned long long bits[3];
+  if (cudaMemcpyAsync(bits, q->slots, sizeof(bits), cudaMemcpyDeviceToHost, q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "dt limit");
+  double m[3];
+  std::memcpy(m, bits, sizeof(m));
+  double d = 1e300;
+  if (m[0] > 0.0 && 0.5 / m[0] < d) d = 0.5 / m[0];
+  if (m[1] > 0.0 && 1.0 / m[1] < d) d = 1.0 / m[1];
+  if (m[2] > 0.0 && eps / (c * m[2]) < d) d = eps / (c * m[2]);
+  *dt = 0.9 * d;
+  return SM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" int sm_quad_create(sm_quad **out, const sm_quad_domain *dom, int max_boxes, int nu1, int nu2,
+                              void *stream) {
+  if (!out || !dom) return SM_EINVAL;
+  *out = nullptr;
+  int lb = 0;
+  while ((1 << lb) < dom->nb) ++lb;
+  if (dom->nb < 1 || (1 << lb) != dom->nb || dom->max_level < 0 || lb + dom->max_level >= QMAXL ||
+      !(dom->length > 0.0) || nu1 < 1 || nu2 < 1 || nu1 > 16 || nu2 > 16 ||
+      (dom->geometry != SM_CARTESIAN && dom->geometry != SM_AXISYMMETRIC))
+    return SM_EINVAL;
+  if (dom->geometry == SM_AXISYMMETRIC && dom->origin[0] != 0.0) return SM_EINVAL;
+  int dir = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (dom->bc_type[f] != 0 && dom->bc_type[f] != 1) return SM_EINVAL;
+    if (f > 0 || dom->geometry == SM_CARTESIAN) dir |= dom->bc_type[f];
+  }
+  if (!dir) return SM_EINVAL;
+  long long uniform = 0;
+  for (int l = 0; l <= lb; ++l) uniform += 1ll << (2 * l);
+  if (max_boxes < uniform) return SM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SM_ECUDA;
+  }
+  sm_quad *q = new sm_quad();
+  q->dom = *dom;
+  q->max_boxes = max_boxes;
+  q->nu1 = nu1;
+  q->nu2 = nu2;
+  q->lbase = lb;
+  q->lmax = lb + dom->max_level;
+  q->stream = (cudaStream_t)stream;
+  for (int f = 0; f < 4; ++f) {
+    const bool axis = dom->geometry == SM_AXISYMMETRIC && f == 0;
+    q->bc.type[f] = axis ? 0 : dom->bc_type[f];
+    q->bc.g2[f] = axis ? 0.0 : 2.0 * dom->bc_val[f];
+  }
+  for (int l = 0; l < QMAXL; ++l) {
+    q->h[l] = dom->length / (QN * (double)(1ll << l));
+    q->inv_h2[l] = 1.0 / (q->h[l] * q->h[l]);
+  }
+  // uniform levels, each in Morton order
+  for (int l = 0; l <= lb; ++l) {
+    q->off[l] = n_boxes(q);
+    const uint64_t nk = 1ull << (2 * l);
+    for (uint64_t key = 0; key < nk; ++key) {
+      int i = 0, j = 0;
+      for (int b = 0; b < 31; ++b) {
+        i |= (int)((key >> (2 * b)) & 1) << b;
+        j |= (int)((key >> (2 * b + 1)) & 1) << b;
+      }
+      add_box(q, l, i, j, l ? q->off[l - 1] + (int)(key >> 2) : -1);
+    }
+    q->off[l + 1] = n_boxes(q);
+  }
+  for (int l = 0; l < lb; ++l)
+    for (int b = q->off[l]; b < q->off[l + 1]; ++b)
+      for (int c = 0; c < 4; ++c) q->chl[4 * b + c] = q->off[l + 1] + (int)((q->mort[b] << 2) | (uint64_t)c);
+  q->nlev = lb + 1;
+  for (int l = 0; l <= lb; ++l) set_neighbours(q, l);
+  coarse_inverse(q);
+  *out = q;
+  return SM_OK;
+}
+
+extern "C" int sm_quad_destroy(sm_quad *q) {
+  delete q;
+  return SM_OK;
+}
+
+namespace {
+struct QLayout {
+  size_t lev, par, chl, nbr8, ij, w, wv, var[NV], cflux, ainv, lut, h, slots, err, total;
+};
+QLayout qlayout(const sm_quad *q) {
+  QLayout L{};
+  size_t t = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = t;
+    t = (t + bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t nb = (size_t)q->max_boxes;
+  L.lev = take(sizeof(int) * nb);
+  L.par = take(sizeof(int) * nb);
+  L.chl = take(sizeof(int) * 4 * nb);
+  L.nbr8 = take(sizeof(int) * 8 * nb);
+  L.ij = take(sizeof(int2) * nb);
+  L.w = take(sizeof(double) * 16 * nb);
+  L.wv = take(sizeof(double) * 8 * nb);
+  for (int v = 0; v < NV; ++v) L.var[v] = take(sizeof(double) * QC * nb);
+  L.cflux = take(sizeof(double) * 32 * nb);
+  L.ainv = take(sizeof(double) * QC * QC);
+  L.lut = take(sizeof(double) * 3 * 4096);
+  L.h = take(sizeof(double) * 3 * QMAXL);
+  L.slots = take(sizeof(unsigned long long) * 8);
+  L.err = take(sizeof(unsigned));
+  L.total = t;
+  return L;
+}
+}  // namespace
+
+extern "C" int sm_quad_arena_size(const sm_quad *q, size_t *bytes) {
+  if (!q || !bytes) return SM_EINVAL;
+  *bytes = qlayout(q).total;
+  return SM_OK;
+}
+
+extern "C" int sm_quad_bind_arena(sm_quad *q, void *dev_ptr, size_t bytes) {
+  if (!q || !dev_ptr) return SM_EINVAL;
+  const QLayout L = qlayout(q);
+  if (bytes < L.total) return qfail(q, SM_ENOMEM, "arena too small");
+  if (((uintptr_t)dev_ptr & 255) != 0) return qfail(q, SM_EINVAL, "arena not 256-byte aligned");
+  char *a = (char *)dev_ptr;
+  q->arena = a;
+  q->d_lev = (int *)(a + L.lev);
+  q->d_par = (int *)(a + L.par);
+  q->d_chl = (int *)(a + L.chl);
+  q->d_nbr8 = (int *)(a + L.nbr8);
+  q->d_ij = (int2 *)(a + L.ij);
+  q->d_w = (double *)(a + L.w);
+  q->d_wv = (double *)(a + L.wv);
+  for (int v = 0; v < NV; ++v) q->var[v] = (double *)(a + L.var[v]);
+  q->cflux = (double *)(a + L.cflux);
+  q->ainv = (double *)(a + L.ainv);
+  q->lut = (double *)(a + L.lut);
+  q->d_h = (double *)(a + L.h);
+  q->slots = (unsigned long long *)(a + L.slots);
+  q->d_err = (unsigned *)(a + L.err);
+  std::vector<double> hs(3 * QMAXL);
+  for (int l = 0; l < QMAXL; ++l) {
+    hs[l] = q->h[l];
+    hs[QMAXL + l] = q->inv_h2[l];
+    hs[2 * QMAXL + l] = 1.0 / q->h[l];
+  }
+  if (cudaMemsetAsync(a, 0, L.total, q->stream) != cudaSuccess ||
+      cudaMemcpyAsync(q->ainv, q->h_ainv.data(), sizeof(double) * QC * QC, cudaMemcpyHostToDevice, q->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(q->d_h, hs.data(), sizeof(double) * 3 * QMAXL, cudaMemcpyHostToDevice, q->stream) !=
+          cudaSuccess)
+    return qfail(q, SM_ECUDA, "arena initialisation");
+  return upload_tables(q);
+}
+
+extern "C" int sm_quad_refine_level(sm_quad *q, int level, const int8_t *flags, int *n_new, int *n_dropped) {
+  if (!q || !flags) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (level != q->nlev - 1 || level >= q->lmax) return qfail(q, SM_ESTATE, "not the finest refinable level");
+  std::vector<int> todo;
+  int dropped = 0;
+  for (int b = q->off[level]; b < q->off[level + 1]; ++b) {
+    if (flags[b - q->off[level]] <= 0) continue;
+    bool ok = true;
+    for (int d = 0; d < 8; ++d) ok &= q->nbr8[8 * b + d] != -2;
+    if (ok) todo.push_back(b);
+    else ++dropped;
+  }
+  if ((long long)n_boxes(q) + 4ll * (long long)todo.size() > q->max_boxes)
+    return qfail(q, SM_ENOMEM, "box capacity exceeded");
+  const int start = n_boxes(q);
+  for (int b : todo)
+    for (int c = 0; c < 4; ++c) {
+      const int nb = n_boxes(q);
+      add_box(q, level + 1, 2 * q->ix[b] + (c & 1), 2 * q->iy[b] + (c >> 1), b);
+      q->chl[4 * b + c] = nb;
+    }
+  if (n_new) *n_new = n_boxes(q) - start;
+  if (n_dropped) *n_dropped = dropped;
+  if (todo.empty()) return SM_OK;
+  q->off[level + 2] = n_boxes(q);
+  q->nlev = level + 2;
+  set_neighbours(q, level + 1);
+  // the new boxes' fields start at zero
+  for (int v = 0; v < NV; ++v)
+    if (cudaMemsetAsync(q->var[v] + (size_t)start * QC, 0, sizeof(double) * QC * (size_t)(n_boxes(q) - start),
+                        q->stream) != cudaSuccess)
+      return qfail(q, SM_ECUDA, "memset");
+  return upload_tables(q);
+}
+
+extern "C" int sm_quad_get_tables(const sm_quad *q, int *nb, int *nl, int32_t *level_offset, int32_t *level,
+                                  int32_t *ij, uint64_t *morton, int32_t *parent, int32_t *child, int32_t *nbr) {
+  if (!q) return SM_EINVAL;
+  const int n = n_boxes(q);
+  if (nb) *nb = n;
+  if (nl) *nl = q->nlev;
+  if (level_offset)
+    for (int l = 0; l <= q->nlev; ++l) level_offset[l] = q->off[l];
+  for (int b = 0; b < n; ++b) {
+    if (level) level[b] = q->lev[b];
+    if (ij) {
+      ij[2 * b] = q->ix[b];
+      ij[2 * b + 1] = q->iy[b];
+    }
+    if (morton) morton[b] = q->mort[b];
+    if (parent) parent[b] = q->par[b];
+    if (child)
+      for (int c = 0; c < 4; ++c) child[4 * b + c] = q->chl[4 * b + c];
+    if (nbr)
+      for (int d = 0; d < 8; ++d) nbr[8 * b + d] = q->nbr8[8 * b + d];
+  }
+  return SM_OK;
+}
+
+extern "C" int sm_quad_var_ptr(sm_quad *q, int v, double **dev) {
+  if (!q || !dev || v < 0 || v > V_RHO) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  *dev = q->var[v];
+  return SM_OK;
+}
+
+extern "C" int sm_quad_upload(sm_quad *q, int v, const double *host) {
+  if (!q || !host || v < 0 || v > V_RHO) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (cudaMemcpyAsync(q->var[v], host, sizeof(double) * QC * (size_t)n_boxes(q), cudaMemcpyHostToDevice,
+                      q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "upload");
+  return SM_OK;
+}
+
+extern "C" int sm_quad_download(sm_quad *q, int v, double *host) {
+  if (!q || !host || v < 0 || v > V_RHO) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (cudaMemcpyAsync(host, q->var[v], sizeof(double) * QC * (size_t)n_boxes(q), cudaMemcpyDeviceToHost,
+                      q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "download");
+  return SM_OK;
+}
+
+extern "C" int sm_quad_set_table(sm_quad *q, int n, double e_max, const double *mu, const double *diff,
+                                 const double *alpha) {
+  if (!q || !mu || !diff || !alpha || n < 2 || n > 4096 || !(e_max > 0.0)) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  std::vector<double> t(3 * (size_t)n);
+  std::memcpy(t.data(), mu, sizeof(double) * n);
+  std::memcpy(t.data() + n, diff, sizeof(double) * n);
+  std::memcpy(t.data() + 2 * n, alpha, sizeof(double) * n);
+  if (cudaMemcpyAsync(q->lut, t.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "table upload");
+  q->lut_n = n;
+  q->lut_emax = e_max;
+  return SM_OK;
+}
+
+extern "C" int sm_quad_charge_rhs(sm_quad *q, double c, double eps, int use_rho) {
+  if (!q || !(eps > 0.0)) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  return charge(q, c, eps, use_rho);
+}
+
+extern "C" int sm_quad_fmg(sm_quad *q, double tol, int max_cycles, int *cycles, double *rel) {
+  if (!q || max_cycles < 1 || !(tol >= 0.0)) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  const int top = q->nlev - 1;
+  restrict_all(q, V_RHS);
+  coarse_solve(q);
+  for (int l = 1; l <= top; ++l) {
+    const int n = level_count(q, l);
+    k_q_prolong<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, q->var[V_PHI], q->var[V_OLD], 0, tabs(q),
+                                                      q->bc, q->d_err);
+    ++q->launches;
+    vcycle(q, l);
+  }
+  if (int st = check(q, "FMG")) return st;
+  return solve_loop(q, tol, max_cycles, 1, cycles, rel);
+}
+
+extern "C" int sm_quad_solve(sm_quad *q, double tol, int max_cycles, int *cycles, double *rel) {
+  if (!q || max_cycles < 1 || !(tol >= 0.0)) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  return solve_loop(q, tol, max_cycles, 0, cycles, rel);
+}
+
+extern "C" int sm_quad_compute_field(sm_quad *q) {
+  if (!q) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  return field(q);
+}
+
+extern "C" int sm_quad_dt_limit(sm_quad *q, double c, double eps, double *dt) {
+  if (!q || !dt || !(eps > 0.0)) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
+  return dt_limit(q, c, eps, dt);
+}
+
+extern "C" int sm_quad_fluid_stage(sm_quad *q, double dt) {
+  if (!q) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
+  restrict_all(q, V_NE);
+  restrict_all(q, V_NI);
+  if (int st = euler_stage(q, V_NE, V_NI, V_NE1, V_NI1, dt)) return st;
+  const size_t bytes = sizeof(double) * QC * (size_t)n_boxes(q);
+  if (cudaMemcpyAsync(q->var[V_NE], q->var[V_NE1], bytes, cudaMemcpyDeviceToDevice, q->stream) != cudaSuccess ||
+      cudaMemcpyAsync(q->var[V_NI], q->var[V_NI1], bytes, cudaMemcpyDeviceToDevice, q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "copy");
+  return SM_OK;
+}
+
+extern "C" int sm_quad_advance(sm_quad *q, double dt, double c, double eps, double tol, int max_cycles,
+                               double *dt_next, int *cycles) {
+  if (!q || !(eps > 0.0) || max_cycles < 1) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
+  const size_t bytes = sizeof(double) * QC * (size_t)n_boxes(q);
+  const long long cells = (long long)n_boxes(q) * QC;
+  restrict_all(q, V_NE);
+  restrict_all(q, V_NI);
+  if (cudaMemcpyAsync(q->var[V_NE0], q->var[V_NE], bytes, cudaMemcpyDeviceToDevice, q->stream) != cudaSuccess ||
+      cudaMemcpyAsync(q->var[V_NI0], q->var[V_NI], bytes, cudaMemcpyDeviceToDevice, q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "copy");
+  if (int st = euler_stage(q, V_NE0, V_NI0, V_NE, V_NI, dt)) return st;
+  if (int st = charge(q, c, eps, 0)) return st;
+  int c1 = 0, c2 = 0;
+  const int st1 = solve_loop(q, tol, max_cycles, 0, &c1, nullptr);
+  if (st1 && st1 != SM_ENOCONV) return st1;
+  if (int st = field(q)) return st;
+  double dtn = 0.0;
+  if (int st = dt_limit(q, c, eps, &dtn)) return st;
+  if (int st = euler_stage(q, V_NE, V_NI, V_NE1, V_NI1, dt)) return st;
+  k_q_average<<<(int)((cells + 255) / 256), 256, 0, q->stream>>>(cells, q->var[V_NE], q->var[V_NE0], q->var[V_NE1]);
+  k_q_average<<<(int)((cells + 255) / 256), 256, 0, q->stream>>>(cells, q->var[V_NI], q->var[V_NI0], q->var[V_NI1]);
+  q->launches += 2;
+  if (int st = charge(q, c, eps, 0)) return st;
+  const int st2 = solve_loop(q, tol, max_cycles, 0, &c2, nullptr);
+  if (st2 && st2 != SM_ENOCONV) return st2;
+  if (int st = field(q)) return st;
+  if (dt_next) *dt_next = dtn;
+  if (cycles) {
+    cycles[0] = c1;
+    cycles[1] = c2;
+  }
+  if (cudaStreamSynchronize(q->stream) != cudaSuccess) return qfail(q, SM_ECUDA, "advance");
+  return st1 ? st1 : st2;
+}
+
+extern "C" int sm_quad_launch_count(const sm_quad *q, long long *n) {
+  if (!q || !n) return SM_EINVAL;
+  *n = q->launches;
+  return SM_OK;
+}
+
+extern "C" const char *sm_quad_last_error(const sm_quad *q) { return q ? q->err.c_str() : "null context"; }

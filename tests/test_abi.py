@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports
-every function include/sm_streamer.h declares; argument checks that need no
+every function include/*.h declares; argument checks that need no
 device work reject bad input.  No compute calls are made here."""
 import ctypes as C
 import os
@@ -11,7 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared():
-    src = open(os.path.join(ROOT, "include", "sm_streamer.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(sm_[a-z0-9_]+)\s*\(", src)))
 
@@ -65,3 +66,25 @@ def test_no_cpu_fallback_without_gpu(lib):
     assert lib.sm_create(C.byref(h), C.byref(cfg), C.byref(d), None) == pkg.SM_ECUDA
     with pytest.raises(pkg.SmError):
         pkg.Solver(__import__("synth").domain_uniform_cube(32), 4096)
+
+
+def test_quad_create_rejects_bad_domains(lib):
+    """sm_quad_create validates its arguments before touching a device."""
+    import paper_1708_08434_gb300 as pkg
+
+    def dom(**kw):
+        base = dict(length=1.0, origin=(0.0, 0.0), nb=4, max_level=2, geometry=1,
+                    bc_type=(0, 0, 1, 1), bc_val=(0.0, 0.0, 0.0, 1.0))
+        base.update(kw)
+        return pkg._QuadDomain(base["length"], (C.c_double * 2)(*base["origin"]), base["nb"],
+                               base["max_level"], base["geometry"], (C.c_int * 4)(*base["bc_type"]),
+                               (C.c_double * 4)(*base["bc_val"]))
+    h = C.c_void_p()
+    for d in (dom(nb=3), dom(nb=0), dom(max_level=-1), dom(max_level=40), dom(length=0.0),
+              dom(geometry=2), dom(origin=(1.0, 0.0)),           # the axis must be at x = 0
+              dom(bc_type=(1, 0, 0, 0)),                          # only the axis is Dirichlet
+              dom(bc_type=(0, 0, 2, 1))):
+        assert lib.sm_quad_create(C.byref(h), C.byref(d), 4096, 2, 2, None) == pkg.SM_EINVAL
+    good = dom()
+    for mb, nu1, nu2 in ((20, 2, 2), (4096, 0, 2), (4096, 2, 0)):  # 21 uniform boxes needed
+        assert lib.sm_quad_create(C.byref(h), C.byref(good), mb, nu1, nu2, None) == pkg.SM_EINVAL

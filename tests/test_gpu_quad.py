@@ -1,0 +1,226 @@
+"""Parity of the 2-D / axisymmetric CUDA path (sm_quad_* through the C ABI)
+with the CPU oracle (oracle/quad.c).
+
+Tables: bit-exact.  FP64 potential, field, densities: max |gpu - oracle| <=
+1e-12 x max |oracle| (both sides FP64; they differ only in rounding order
+and fused multiply-adds); |E| after a Heun step within that bound times
+max|phi| / (h_min max|E|), the amplification of a potential difference by
+the field's division by h.  Cycle counts to a tolerance agree exactly.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import quad
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+Q, EPS0 = synth.E_CHARGE, synth.EPS0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def pkg():
+    import paper_1708_08434_gb300 as p
+    return p
+
+
+def rel_err(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def gpu_quad(dom, st=None, max_boxes=1 << 15):
+    g = pkg().Quad(dom, max_boxes)
+    if st is not None:
+        synth.refine_all2(dom, st, g.level_ij, g.refine_level)
+    return g
+
+
+def pair(name):
+    dom, st = synth.workload2(name)
+    return dom, st, quad.build_mesh(dom, st), gpu_quad(dom, st)
+
+
+def load(dom, st, o, g):
+    t = o.tables()
+    ne, ni = synth.streamer_densities2(dom, st, t["level"], t["ij"])
+    p = pkg()
+    o.set(quad.NE, ne)
+    o.set(quad.NI, ni)
+    g.upload(p.NE, ne)
+    g.upload(p.NI, ni)
+    tab = synth.coefficient_table()
+    o.set_table(tab)
+    g.set_table(tab)
+    o.charge_rhs(Q, EPS0)
+    g.charge_rhs(Q, EPS0)
+    return t
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small", "axi_streamer"])
+def test_tables_bit_exact(name):
+    dom, st, o, g = pair(name)
+    to, tg = o.tables(), g.tables()
+    for k in ("level", "ij", "morton", "parent", "child", "nbr", "level_offset"):
+        assert np.array_equal(to[k], tg[k]), k
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_fmg_parity(name):
+    dom, st, o, g = pair(name)
+    load(dom, st, o, g)
+    # at 1e-8 the residual is far above its FP64 rounding floor, so the two
+    # sides' norms agree closely (near 1e-11 they differ in the 4th digit)
+    so = o.fmg(1e-8, 40)
+    sg = g.fmg(1e-8, 40)
+    assert so[0] == sg[0] == 0
+    assert so[2] == sg[2]
+    assert abs(so[1] - sg[1]) <= 1e-6 * so[1]
+    assert rel_err(g.download(pkg().PHI), o.get(quad.PHI)) <= TOL
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_fixed_cycles_parity(name):
+    """Three V-cycles from zero (no stopping test): every box of every level
+    agrees, coarse levels included."""
+    dom, st, o, g = pair(name)
+    load(dom, st, o, g)
+    o.vcycles(3)
+    rc, rel, cyc = g.solve(0.0, 3)
+    assert cyc == 3
+    assert rel == pytest.approx(o.rel_residual(), rel=1e-6)
+    assert rel_err(g.download(pkg().PHI), o.get(quad.PHI)) <= TOL
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_field_dt_and_stage_parity(name):
+    dom, st, o, g = pair(name)
+    t = load(dom, st, o, g)
+    o.fmg(1e-10, 40)
+    g.fmg(1e-10, 40)
+    o.compute_field()
+    g.compute_field()
+    p = pkg()
+    leaf = t["child"][:, 0] < 0
+    assert rel_err(g.download(p.EMAG)[leaf], o.get(quad.EMAG)[leaf]) <= TOL
+    dt = o.dt_limit(Q, EPS0)
+    assert g.dt_limit(Q, EPS0) == pytest.approx(dt, rel=TOL)
+    o.fluid_stage(dt)
+    g.fluid_stage(dt)
+    assert rel_err(g.download(p.NE)[leaf], o.get(quad.NE)[leaf]) <= TOL
+    assert rel_err(g.download(p.NI)[leaf], o.get(quad.NI)[leaf]) <= TOL
+    # refined boxes hold the restriction of their children on both sides
+    assert rel_err(g.download(p.NE), o.get(quad.NE)) <= TOL
+
+
+def check_advance(name, threads=1):
+    dom, st, o, g = pair(name)
+    t = load(dom, st, o, g)
+    quad.set_threads(threads)
+    try:
+        so = o.fmg(1e-8, 40)
+        sg = g.fmg(1e-8, 40)
+        assert so[2] == sg[2]
+        o.compute_field()
+        g.compute_field()
+        dt = o.dt_limit(Q, EPS0)
+        assert g.dt_limit(Q, EPS0) == pytest.approx(dt, rel=TOL)
+        ro = o.advance(dt, Q, EPS0, 1e-8, 40)
+        rg = g.advance(dt, Q, EPS0, 1e-8, 40)
+    finally:
+        quad.set_threads(1)
+    assert ro[0] == rg[0] == 0
+    assert ro[2:] == rg[2:], (ro, rg)
+    assert rg[1] == pytest.approx(ro[1], rel=TOL)
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    for vo, vg in ((quad.NE, p.NE), (quad.NI, p.NI), (quad.PHI, p.PHI)):
+        e = rel_err(g.download(vg)[leaf], o.get(vo)[leaf])
+        assert e <= TOL, (vo, e)
+    # |E| is a difference of potentials over h: a potential difference of
+    # TOL max|phi| becomes TOL max|phi| / h_min in |E|, i.e. the relative
+    # bound grows by max|phi| / (h_min max|E|) (2e4 on the benchmark mesh,
+    # whose finest spacing is 0.12 um)
+    eo, po = o.get(quad.EMAG)[leaf], o.get(quad.PHI)[leaf]
+    amp = max(1.0, np.abs(po).max() / (dom.h(o.n_levels - 1) * np.abs(eo).max()))
+    e = rel_err(g.download(p.EMAG)[leaf], eo)
+    assert e <= TOL * amp, (e, amp)
+    return g, leaf
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_heun_step_parity(name):
+    check_advance(name)
+
+
+def test_full_size_axi_streamer_parity():
+    """The benchmark workload (axisymmetric 16 mm, base 512^2 cells + 8
+    levels, 10113 boxes, 4.9e5 leaf cells): FMG to 1e-8, field, one Heun
+    step, element-wise parity (the oracle on all host cores)."""
+    g, leaf = check_advance("axi_streamer", threads=os.cpu_count() or 1)
+    assert leaf.sum() * 64 > 4.5e5
+
+
+def test_single_box_and_uniform_domains():
+    """Degenerate meshes: one box (FMG is the exact level-0 solve) and a
+    uniform grid without refinement, in both geometries."""
+    p = pkg()
+    for geom in (synth.CARTESIAN, synth.AXISYMMETRIC):
+        for nb in (1, 8):
+            dom = synth.Domain2(0.01, nb, 0, geom, bc_val=(0.0, 0.0, 0.0, 1e3))
+            o, g = quad.Quad(dom), gpu_quad(dom)
+            t = o.tables()
+            x, y = synth.cell_centres2(dom, t["level"], t["ij"])
+            rho = 1e-6 * np.exp(-((x - 0.004) ** 2 + (y - 0.005) ** 2) / 2e-6)
+            o.set(quad.RHO, rho)
+            g.upload(p.RHO, rho)
+            o.charge_rhs(1.0, EPS0, True)
+            g.charge_rhs(1.0, EPS0, True)
+            so, sg = o.fmg(1e-11, 40), g.fmg(1e-11, 40)
+            assert so[2] == sg[2]
+            assert rel_err(g.download(p.PHI), o.get(quad.PHI)) <= TOL
+
+
+@pytest.mark.parametrize("bct", [(1, 1, 0, 0), (1, 0, 1, 0), (0, 1, 0, 1)])
+def test_boundary_condition_mixes(bct):
+    p = pkg()
+    dom = synth.Domain2(1.0, 4, 2, synth.CARTESIAN, bc_type=bct, bc_val=(0.3, -0.2, 0.5, 1.0))
+    st = synth.Streamer2(length=1.0, radius=0.05, z_head=0.5, edge=0.01, shell=0.005, x_axis=0.5,
+                         refine_c=1.0, refine_tip=0.5)
+    o, g = quad.build_mesh(dom, st), gpu_quad(dom, st)
+    t = o.tables()
+    x, y = synth.cell_centres2(dom, t["level"], t["ij"])
+    rho = np.sin(3 * x) * np.cos(2 * y)
+    o.set(quad.RHO, rho)
+    g.upload(p.RHO, rho)
+    o.charge_rhs(1.0, 1.0, True)
+    g.charge_rhs(1.0, 1.0, True)
+    so, sg = o.fmg(1e-11, 40), g.fmg(1e-11, 40)
+    assert so[2] == sg[2]
+    assert rel_err(g.download(p.PHI), o.get(quad.PHI)) <= TOL
+
+
+def test_error_paths():
+    p = pkg()
+    dom, st = synth.workload2("axi_small")
+    g = gpu_quad(dom)
+    with pytest.raises(p.SmError):
+        g.refine_level(0, np.ones(1, np.int8))          # not the finest level
+    with pytest.raises(p.SmError):
+        g.dt_limit(Q, EPS0)                             # no table yet
+    with pytest.raises(p.SmError):
+        g.fluid_stage(1e-12)
+    small = p.Quad(dom, 21 + 3)                         # room for the uniform levels only
+    with pytest.raises(p.SmError):
+        small.refine_level(2, np.ones(16, np.int8))
