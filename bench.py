@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-paper", action="store_true", help="skip the fixed 2-V-cycle (paper) schedule")
     ap.add_argument("--no-large", action="store_true", help="skip the 1e8-cell mesh (streamer9)")
+    ap.add_argument("--no-axi", action="store_true", help="skip the axisymmetric (2-D) variant")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the same kernels from the host instead of CUDA graphs "
                          "(profilers cannot see kernels inside conditional graph nodes)")
@@ -61,10 +62,11 @@ def parse():
                     help="run V-cycles as one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the solver kernels without programmatic dependent launch")
-    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch", "large"],
+    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch", "large", "axi"],
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
-                         "schedule (small, fixed launch sequences for ncu captures)")
+                         "schedule (small, fixed launch sequences for ncu captures); "
+                         "large: the 1e8-cell mesh alone; axi: the axisymmetric variant alone")
     ap.add_argument("--batch-solves", type=int, default=256,
                     help="--mode batch only: solve the first N of the 256 batched problems (small ncu captures)")
     return ap.parse_args()
@@ -200,6 +202,15 @@ def run_large(args):
     torch.cuda.set_device(0)
     __graft_entry__.build()
     print(json.dumps(large_mesh()), flush=True)
+
+
+def run_axi(args):
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    print(json.dumps({"mode": "axi", **bench_axisymmetric(args, dev, 1)}), flush=True)
 
 
 def large_mesh():
@@ -539,6 +550,7 @@ def run_gpu(args):
                   "dropped": ndrop, "criterion": "c0=0.25 (paper: 1), c1=1.2, buffer 3; flags with the paper's "
                                                  "c0=1, c0_deref=1/8, dx_deref=30 um"}
     large = None if (args.no_large or rank != 0) else large_mesh()
+    axi = None if args.no_axi else bench_axisymmetric(args, dev, world)
     batched = None if args.no_batch else bench_batch(args, dev, world)
     learned = None if args.no_learned else bench_learned(args, dev, world)
     steps = args.steps
@@ -568,6 +580,7 @@ def run_gpu(args):
         "paper_schedule": paper,
         "large_mesh": large,
         "regrid": regrid,
+        "axisymmetric": axi,
         "batched": batched,
         "learned_warm_start": learned,
     }
@@ -579,6 +592,83 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def bench_axisymmetric(args, dev, world):
+    """The axisymmetric variant (quadtree of 8^2 boxes, cylindrical
+    operators): the streamer on its symmetry axis, 16 mm, base 512^2 cells +
+    8 levels (10113 boxes, 4.9e5 leaf cells, finest spacing 0.12 um).  A step
+    is the headline step in 2-D: FMG to 1e-8, field, dt, one Heun step (3
+    solves), densities copied in from device buffers; CUDA events on the
+    solver's stream, L2 flushed between steps.  Beside it the V-cycle alone
+    (10 back-to-back cycles) and its launch count."""
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    Q, E0 = synth.E_CHARGE, synth.EPS0
+    dom, st = synth.workload2("axi_streamer")
+    g = pkg.Quad(dom, 1 << 15)
+    synth.refine_all2(dom, st, g.level_ij, g.refine_level)
+    t = g.tables()
+    ne, ni = synth.streamer_densities2(dom, st, t["level"], t["ij"])
+    g.set_table(synth.coefficient_table())
+    ne_d, ni_d = torch.from_numpy(ne).to(dev), torch.from_numpy(ni).to(dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    stream = g.stream
+
+    def step():
+        g.view(pkg.NE).copy_(ne_d)
+        g.view(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        rc0, _, c0 = g.fmg(TOL, MAX_CYCLES)
+        g.compute_field()
+        dt = g.dt_limit(Q, E0)
+        rc1, _, c1, c2 = g.advance(dt, Q, E0, TOL, MAX_CYCLES)
+        assert rc0 == 0 and rc1 == 0, (rc0, rc1)
+        return c0 + c1 + c2
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    n = max(args.steps, 5)
+    total, cycles = 0.0, 0
+    l0 = g.launch_count()
+    for _ in range(n):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a, b = events()
+        a.record(stream)
+        cycles += step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    launches = g.launch_count() - l0
+    total = max_over_ranks(total, dev)
+    # the V-cycle alone
+    g.vcycles(2)
+    torch.cuda.synchronize()
+    lv = g.launch_count()
+    a, b = events()
+    a.record(stream)
+    g.vcycles(10)
+    b.record(stream)
+    torch.cuda.synchronize()
+    vus = a.elapsed_time(b) * 100.0
+    lv = (g.launch_count() - lv) // 10
+    leaf_cells = int((t["child"][:, 0] < 0).sum()) * 64
+    all_cells = len(t["level"]) * 64
+    res = {"value": round(whole_job_rate(SOLVES_PER_STEP * n, world, total), 3), "unit": "solves/s",
+           "ms_per_step": round(total / n, 4), "vcycles_per_step": cycles / n, "gpu_launches": launches,
+           "vcycle_us": round(vus, 2), "launches_per_vcycle": int(lv),
+           "gcells_per_s_vcycle": round(all_cells / (vus * 1e-6) / 1e9, 3),
+           "workload": "axi_streamer", "geometry": "axisymmetric (r, z)", "boxes": len(t["level"]),
+           "leaf_cells": leaf_cells, "levels": int(len(t["level_offset"]) - 1), "tol": TOL,
+           "dtype": "f64", "l2": "flushed between steps",
+           "note": "per-level launches driven from the host, one residual read per V-cycle"}
+    g.close()
+    return res
 
 
 def bench_learned(args, dev, world):
@@ -812,6 +902,8 @@ def main():
         run_batch_only(args)
     elif args.mode == "large":
         run_large(args)
+    elif args.mode == "axi":
+        run_axi(args)
     else:
         run_gpu(args)
 

@@ -114,6 +114,10 @@ int sm_quad_fmg(sm_quad *q, double tol, int max_cycles, int *cycles, double *rel
 /* V-cycles from the current potential, same stopping rule. */
 int sm_quad_solve(sm_quad *q, double tol, int max_cycles, int *cycles, double *rel);
 
+/* n V-cycles from the current potential with no residual evaluation
+ * (enqueue only; for timing and fixed schedules). */
+int sm_quad_vcycles(sm_quad *q, int n);
+
 /* |E| on leaf cells from the current potential (zero on refined boxes). */
 int sm_quad_compute_field(sm_quad *q);
 /* Time-step limits of Sec. 2.4 in two dimensions: 0.9 min(0.5 /

@@ -73,7 +73,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
            "sm_quad_refine_level", "sm_quad_get_tables", "sm_quad_var_ptr", "sm_quad_upload",
            "sm_quad_download", "sm_quad_set_table", "sm_quad_charge_rhs", "sm_quad_fmg",
-           "sm_quad_solve", "sm_quad_compute_field", "sm_quad_dt_limit", "sm_quad_fluid_stage",
+           "sm_quad_solve", "sm_quad_vcycles", "sm_quad_compute_field", "sm_quad_dt_limit", "sm_quad_fluid_stage",
            "sm_quad_advance", "sm_quad_launch_count", "sm_quad_last_error"]
 
 
@@ -163,6 +163,7 @@ def load():
         "sm_quad_charge_rhs": [P, D, D, I],
         "sm_quad_fmg": [P, D, I, pI, pD],
         "sm_quad_solve": [P, D, I, pI, pD],
+        "sm_quad_vcycles": [P, I],
         "sm_quad_compute_field": [P],
         "sm_quad_dt_limit": [P, D, D, pD],
         "sm_quad_fluid_stage": [P, D],
@@ -744,6 +745,10 @@ class Quad:
         cyc, rel = C.c_int(), C.c_double()
         rc = self._ck(self._lib.sm_quad_solve(self._h, tol, max_cycles, C.byref(cyc), C.byref(rel)))
         return rc, rel.value, cyc.value
+
+    def vcycles(self, n: int):
+        """n V-cycles, enqueued on the stream (no residual evaluation)."""
+        self._ck(self._lib.sm_quad_vcycles(self._h, int(n)))
 
     def compute_field(self):
         self._ck(self._lib.sm_quad_compute_field(self._h))

@@ -55,14 +55,14 @@ struct QBc {
 struct QTabs {
   const int *lev, *par, *chl, *nbr8;
   const int2 *ij;
-  const double *w;   // [box][8][2]: w_lo, w_hi of column i
+  const double *w;   // [box][8][3]: w_lo, w_hi, 1/(w_lo + w_hi + 2) of column i
   const double *wv;  // [box][8]: volume (and y-face area) weight of column i
 };
 
 struct QLut {
   const double *mu, *diff, *alpha;
   int n;
-  double de;         // e_max / (n - 1)
+  double inv_de;     // (n - 1) / e_max
 };
 
 __device__ __forceinline__ int dir8(int dx, int dy) {
@@ -147,7 +147,7 @@ __device__ void stage_phi(const double *var, const double *alt, const QTabs &T, 
     const double c = coarse_val(var, T, p, cx, cy, cx, cy, ncl, bc, homog, false, err);
     const double ct = coarse_val(var, T, p, qx, qy, cx, cy, ncl, bc, homog, false, err);
     const double phat = 0.75 * c + 0.25 * ct;
-    v = inner / 3.0 + 2.0 * phat / 3.0;
+    v = inner * (1.0 / 3.0) + phat * (2.0 / 3.0);
   }
   s[(gj + 1) * S1 + gi + 1] = v;
   __syncwarp();
@@ -156,7 +156,7 @@ __device__ void stage_phi(const double *var, const double *alt, const QTabs &T, 
 // L phi at staged cell (i, j) of box b
 __device__ __forceinline__ double lap_s(const double *s, const QTabs &T, int b, int i, int j, double inv_h2) {
   const double c = s[(j + 1) * S1 + i + 1];
-  const double wl = T.w[(size_t)b * 16 + 2 * i], wh = T.w[(size_t)b * 16 + 2 * i + 1];
+  const double wl = T.w[(size_t)b * 24 + 3 * i], wh = T.w[(size_t)b * 24 + 3 * i + 1];
   return (wl * (s[(j + 1) * S1 + i] - c) + wh * (s[(j + 1) * S1 + i + 2] - c) + (s[j * S1 + i + 1] - c) +
           (s[(j + 2) * S1 + i + 1] - c)) * inv_h2;
 }
@@ -176,11 +176,11 @@ __global__ void __launch_bounds__(QT) k_q_rbgs(int off, int n, int l, int colour
   double *s = sm[wv_];
   stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
   const int j = lane >> 2, i = 2 * (lane & 3) + ((j + colour) & 1);
-  const double wl = T.w[(size_t)b * 16 + 2 * i], wh = T.w[(size_t)b * 16 + 2 * i + 1];
+  const double *wc = T.w + (size_t)b * 24 + 3 * i;
   phi[(size_t)b * QC + i + QN * j] =
-      (wl * s[(j + 1) * S1 + i] + wh * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
-       h2 * rhs[(size_t)b * QC + i + QN * j]) /
-      (wl + wh + 2.0);
+      (wc[0] * s[(j + 1) * S1 + i] + wc[1] * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
+       h2 * rhs[(size_t)b * QC + i + QN * j]) *
+      wc[2];
 }
 
 // Residual of every box of level l restricted to its parent's quadrant:
@@ -272,7 +272,7 @@ __global__ void k_q_coarse(double *__restrict__ phi, const double *__restrict__ 
                            QTabs T, QBc bc, double inv_h2) {
   __shared__ double r[QC];
   const int c = threadIdx.x, i = c % QN, j = c / QN;
-  const double wl = T.w[2 * i], wh = T.w[2 * i + 1];
+  const double wl = T.w[3 * i], wh = T.w[3 * i + 1];
   double l0 = 0.0;
   if (i == 0 && bc.type[0]) l0 += wl * bc.g2[0];
   if (i == QN - 1 && bc.type[1]) l0 += wh * bc.g2[1];
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(QT) k_q_field(int n, const double *__restrict_
 }
 
 __device__ __forceinline__ double lut(const double *t, const QLut &L, double e) {
-  const double x = e / L.de;
+  const double x = e * L.inv_de;
   if (x <= 0.0) return t[0];
   if (x >= L.n - 1) return t[L.n - 1];
   const int i = (int)x;
@@ -364,7 +364,7 @@ __device__ __forceinline__ double koren(double a, double b) {
   if (a * b <= 0.0) return 0.0;
   const double s = b > 0.0 ? 1.0 : -1.0, aa = fabs(a), bb = fabs(b);
   double m = bb;
-  m = fmin(m, (2.0 * bb + aa) / 6.0);
+  m = fmin(m, (2.0 * bb + aa) * (1.0 / 6.0));
   m = fmin(m, aa);
   return s * m;
 }
@@ -441,7 +441,7 @@ __device__ __forceinline__ double face_flux(const double *sn, const double *sp, 
   const double mu = lut(L.mu, L, e_star), dc = lut(L.diff, L, e_star);
   const double v = -mu * e_face;
   const double nf = v < 0.0 ? nR - koren(nR2 - nR, nR - nL) : nL + koren(nL - nL2, nR - nL);
-  return v * nf - dc * (nR - nL) / h;
+  return v * nf - dc * (nR - nL) * ih;
   (void)h;
 }
 
@@ -515,9 +515,9 @@ __global__ void __launch_bounds__(QT) k_q_update(int n, const double *__restrict
   __syncwarp();
   for (int c = lane; c < QC; c += 32) {
     const int i = c % QN, j = c / QN;
-    const double wl = T.w[(size_t)b * 16 + 2 * i], wh = T.w[(size_t)b * 16 + 2 * i + 1];
-    const double div = (wh * sf[wv_][0][(i + 1) * QN + j] - wl * sf[wv_][0][i * QN + j]) / h +
-                       (sf[wv_][1][(j + 1) * QN + i] - sf[wv_][1][j * QN + i]) / h;
+    const double wl = T.w[(size_t)b * 24 + 3 * i], wh = T.w[(size_t)b * 24 + 3 * i + 1];
+    const double div = (wh * sf[wv_][0][(i + 1) * QN + j] - wl * sf[wv_][0][i * QN + j]) * ih +
+                       (sf[wv_][1][(j + 1) * QN + i] - sf[wv_][1][j * QN + i]) * ih;
     const double e = sem[wv_][(j + 1) * S1 + i + 1];
     const size_t g = (size_t)b * QC + c;
     const double src = lut(L.alpha, L, e) * lut(L.mu, L, e) * e * ne[g];
@@ -560,18 +560,18 @@ __global__ void __launch_bounds__(QT) k_q_dt(int n, const double *__restrict__ p
   const int l = T.lev[b];
   double *s = sm[wv_];
   stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
-  const double h = hs[l];
+  const double h = hs[l], ih = 1.0 / h;
   double m0 = 0.0, m1 = 0.0, m2 = 0.0;
   for (int c = lane; c < QC; c += 32) {
     const int i = c % QN, j = c / QN;
     const double pc = s[(j + 1) * S1 + i + 1];
-    const double ex = ((s[(j + 1) * S1 + i] - pc) / h + (pc - s[(j + 1) * S1 + i + 2]) / h) / 2.0;
-    const double ey = ((s[j * S1 + i + 1] - pc) / h + (pc - s[(j + 2) * S1 + i + 1]) / h) / 2.0;
+    const double ex = ((s[(j + 1) * S1 + i] - pc) * ih + (pc - s[(j + 1) * S1 + i + 2]) * ih) * 0.5;
+    const double ey = ((s[j * S1 + i + 1] - pc) * ih + (pc - s[(j + 2) * S1 + i + 1]) * ih) * 0.5;
     const double e = emag[(size_t)b * QC + c];
     const double mu = lut(L.mu, L, e), dc = lut(L.diff, L, e);
-    const double adv = (fabs(mu * ex) + fabs(mu * ey)) / h;
+    const double adv = (fabs(mu * ex) + fabs(mu * ey)) * ih;
     m0 = fmax(m0, adv);
-    m1 = fmax(m1, adv + 2.0 * 2.0 * dc / (h * h));
+    m1 = fmax(m1, adv + 2.0 * 2.0 * dc * (ih * ih));
     m2 = fmax(m2, mu * ne[(size_t)b * QC + c]);
   }
   max_bits(slots, m0);
@@ -665,8 +665,10 @@ void add_box(sm_quad *q, int l, int i, int j, int parent) {
   for (int c = 0; c < QN; ++c) {
     const int gx = i * QN + c;
     const bool cyl = q->dom.geometry == SM_AXISYMMETRIC;
-    q->w.push_back(cyl ? (double)gx / (gx + 0.5) : 1.0);
-    q->w.push_back(cyl ? (gx + 1.0) / (gx + 0.5) : 1.0);
+    const double wl = cyl ? (double)gx / (gx + 0.5) : 1.0, wh = cyl ? (gx + 1.0) / (gx + 0.5) : 1.0;
+    q->w.push_back(wl);
+    q->w.push_back(wh);
+    q->w.push_back(1.0 / (wl + wh + 2.0));
     q->wv.push_back(cyl ? gx + 0.5 : 1.0);
   }
 }
@@ -690,7 +692,7 @@ int upload_tables(sm_quad *q) {
       cudaMemcpyAsync(q->d_chl, q->chl.data(), sizeof(int) * 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_nbr8, q->nbr8.data(), sizeof(int) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_ij, ij.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(q->d_w, q->w.data(), sizeof(double) * 16 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_w, q->w.data(), sizeof(double) * 24 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_wv, q->wv.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return qfail(q, SM_ECUDA, "table upload");
@@ -699,7 +701,7 @@ int upload_tables(sm_quad *q) {
 
 QTabs tabs(const sm_quad *q) { return {q->d_lev, q->d_par, q->d_chl, q->d_nbr8, q->d_ij, q->d_w, q->d_wv}; }
 QLut qlut(const sm_quad *q) {
-  return {q->lut, q->lut + q->lut_n, q->lut + 2 * q->lut_n, q->lut_n, q->lut_emax / (q->lut_n - 1)};
+  return {q->lut, q->lut + q->lut_n, q->lut + 2 * q->lut_n, q->lut_n, (q->lut_n - 1) / q->lut_emax};
 }
 
 // the level-0 operator with homogeneous wall ghosts (columns L e_k) and its
@@ -710,7 +712,7 @@ void coarse_inverse(sm_quad *q) {
   const double ih2 = q->inv_h2[0];
   for (int r = 0; r < n; ++r) {
     const int i = r % QN, j = r / QN;
-    const double wl = q->w[2 * i], wh = q->w[2 * i + 1];
+    const double wl = q->w[3 * i], wh = q->w[3 * i + 1];
     const double wf[4] = {wl, wh, 1.0, 1.0};
     const int nbr[4] = {i > 0 ? r - 1 : -1, i < QN - 1 ? r + 1 : -1, j > 0 ? r - QN : -1, j < QN - 1 ? r + QN : -1};
     for (int f = 0; f < 4; ++f) {
@@ -992,7 +994,7 @@ QLayout qlayout(const sm_quad *q) {
   L.chl = take(sizeof(int) * 4 * nb);
   L.nbr8 = take(sizeof(int) * 8 * nb);
   L.ij = take(sizeof(int2) * nb);
-  L.w = take(sizeof(double) * 16 * nb);
+  L.w = take(sizeof(double) * 24 * nb);
   L.wv = take(sizeof(double) * 8 * nb);
   for (int v = 0; v < NV; ++v) L.var[v] = take(sizeof(double) * QC * nb);
   L.cflux = take(sizeof(double) * 32 * nb);
@@ -1178,6 +1180,13 @@ extern "C" int sm_quad_solve(sm_quad *q, double tol, int max_cycles, int *cycles
   if (!q || max_cycles < 1 || !(tol >= 0.0)) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   return solve_loop(q, tol, max_cycles, 0, cycles, rel);
+}
+
+extern "C" int sm_quad_vcycles(sm_quad *q, int n) {
+  if (!q || n < 0) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  for (int c = 0; c < n; ++c) vcycle(q, q->nlev - 1);
+  return check(q, "V-cycle");
 }
 
 extern "C" int sm_quad_compute_field(sm_quad *q) {
