@@ -54,6 +54,8 @@ struct QBc {
 
 struct QTabs {
   const int *lev, *par, *chl, *nbr8;
+  const int *pn;     // [box][9]: the parent's 3x3 neighbourhood, (dx+1) + 3 (dy+1) (-1 outside, -2 none)
+  const int *ref;    // [box]: bit f = face neighbour f has children, bit 4 = the box has children
   const int2 *ij;
   const double *w;   // [box][8][3]: w_lo, w_hi, 1/(w_lo + w_hi + 2) of column i
   const double *wv;  // [box][8]: volume (and y-face area) weight of column i
@@ -84,68 +86,95 @@ __device__ __forceinline__ void face_cell(int f, int t, int u, int &ci, int &cj)
   }
 }
 
-// Box of level l-1 holding coarse cell (cx, cy) (cells per side ncl),
-// found from p, the parent of the level-l box asking: -1 outside the
-// domain; -2 (and the error flag) when the box does not exist.
-__device__ __forceinline__ int coarse_box(const QTabs &T, int p, int cx, int cy, int ncl, unsigned *err) {
+// What a warp needs to know about its box, loaded in one round of
+// independent loads at kernel start (the tables are built on the host):
+// face neighbours, the parent's 3x3 neighbourhood, coordinates, level and
+// the refinement bits.  Every coarse or neighbour value a kernel reads is
+// then one dependent load away.
+struct BoxCtx {
+  int nb[4], pn[9];
+  int ix, iy, lev, ref;
+};
+
+__device__ __forceinline__ void load_ctx(const QTabs &T, int b, BoxCtx &c, int lane) {
+  if (lane < 4) c.nb[lane] = T.nbr8[8 * b + face_dir8(lane)];
+  else if (lane < 13) c.pn[lane - 4] = T.pn[9 * b + lane - 4];
+  else if (lane == 13) {
+    const int2 v = T.ij[b];
+    c.ix = v.x;
+    c.iy = v.y;
+  } else if (lane == 14) c.lev = T.lev[b];
+  else if (lane == 15) c.ref = T.ref[b];
+  __syncwarp();
+}
+
+// Box of level l-1 holding coarse cell (cx, cy) (cells per side ncl): -1
+// outside the domain; -2 (and the error flag) when it does not exist.
+__device__ __forceinline__ int coarse_box(const BoxCtx &C, int cx, int cy, int ncl, unsigned *err) {
   if (cx < 0 || cy < 0 || cx >= ncl || cy >= ncl) return -1;
-  const int2 P = T.ij[p];
-  const int dx = (cx >> 3) - P.x, dy = (cy >> 3) - P.y;
-  if (dx == 0 && dy == 0) return p;
+  const int dx = (cx >> 3) - (C.ix >> 1), dy = (cy >> 3) - (C.iy >> 1);
   int b = -2;
-  if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) b = T.nbr8[8 * p + dir8(dx, dy)];
-  if (b == -2) atomicOr(err, 1u);
+  if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) b = C.pn[(dx + 1) + 3 * (dy + 1)];
+  if (b < 0) {
+    atomicOr(err, 1u);
+    b = -2;
+  }
   return b;
 }
 
 // value of var at coarse cell q, or across the wall from coarse cell `from`
 // (inside): Dirichlet (homog ? 0 : 2g) - v, Neumann / axis v; mirror: always v
-__device__ double coarse_val(const double *var, const QTabs &T, int p, int qx, int qy, int fx, int fy, int ncl,
-                             const QBc &bc, int homog, bool mirror, unsigned *err) {
-  const int b = coarse_box(T, p, qx, qy, ncl, err);
-  if (b >= 0) return var[(size_t)b * QC + (qx & 7) + QN * (qy & 7)];
-  if (b == -2) return 0.0;
-  const int bf = coarse_box(T, p, fx, fy, ncl, err);
-  const double v = bf >= 0 ? var[(size_t)bf * QC + (fx & 7) + QN * (fy & 7)] : 0.0;
-  if (mirror) return v;
+__device__ __forceinline__ double coarse_val(const double *var, const BoxCtx &C, int qx, int qy, int fx, int fy,
+                                             int ncl, const QBc &bc, int homog, bool mirror, unsigned *err) {
+  const bool out = qx < 0 || qy < 0 || qx >= ncl || qy >= ncl;
+  const int b = coarse_box(C, out ? fx : qx, out ? fy : qy, ncl, err);
+  const double v = b >= 0 ? var[(size_t)b * QC + ((out ? fx : qx) & 7) + QN * ((out ? fy : qy) & 7)] : 0.0;
+  if (!out || mirror) return v;
   const int f = qx < 0 ? 0 : (qx >= ncl ? 1 : (qy < 0 ? 2 : 3));
   return bc.type[f] ? (homog ? 0.0 : bc.g2[f]) - v : v;
 }
 
-// Stage box b of level l into s (S1 x S1, interior at (i+1, j+1)) with the
-// potential ghost rules: same-level copy, wall ghost, refinement boundary
-// phi_f/3 + 2 phihat/3.  `sel` (optional): per box, read `alt` instead of
-// `var` for boxes with children (the FAS step's restricted values).
-__device__ void stage_phi(const double *var, const double *alt, const QTabs &T, int b, int l, const QBc &bc,
-                          int homog, double *s, int lane, unsigned *err) {
-  auto src = [&](int box) { return (alt && T.chl[4 * box] >= 0) ? alt : var; };
-  const double *own = src(b);
-  for (int c = lane; c < QC; c += 32) s[(c / QN + 1) * S1 + c % QN + 1] = own[(size_t)b * QC + c];
+// The first round of a box kernel: the box's own values (cells lane and
+// lane + 32) issued together with the context loads.
+__device__ __forceinline__ void begin_box(const double *var, const QTabs &T, int b, BoxCtx &C, int lane, double &v0,
+                                          double &v1) {
+  v0 = var[(size_t)b * QC + lane];
+  v1 = var[(size_t)b * QC + lane + 32];
+  load_ctx(T, b, C, lane);
+}
+
+// Stage box b into s (S1 x S1, interior at (i+1, j+1)) with the potential
+// ghost rules: same-level copy, wall ghost, refinement boundary
+// phi_f/3 + 2 phihat/3.  v0, v1: the box's own values (cells lane and
+// lane + 32).  With `alt`, neighbours with children are read from alt
+// instead of var (the FAS step's restricted values).
+__device__ void stage_phi(const double *var, const double *alt, const BoxCtx &C, int b, const QBc &bc, int homog,
+                          double *s, int lane, unsigned *err, double v0, double v1) {
+  s[(lane / QN + 1) * S1 + lane % QN + 1] = v0;
+  s[((lane + 32) / QN + 1) * S1 + lane % QN + 1] = v1;
   __syncwarp();
   const int f = lane >> 3, u = lane & 7;
   int ci, cj, gi, gj;
   face_cell(f, 0, u, ci, cj);
   face_cell(f, -1, u, gi, gj);
   const double inner = s[(cj + 1) * S1 + ci + 1];
-  const int nb = T.nbr8[8 * b + face_dir8(f)];
+  const int nb = C.nb[f];
   double v;
   if (nb >= 0) {
     int si, sj;
     face_cell(f ^ 1, 0, u, si, sj);
-    v = src(nb)[(size_t)nb * QC + si + QN * sj];
+    v = ((alt && ((C.ref >> f) & 1)) ? alt : var)[(size_t)nb * QC + si + QN * sj];
   } else if (nb == -1) {
     v = bc.type[f] ? (homog ? 0.0 : bc.g2[f]) - inner : inner;
   } else {
-    const int2 B = T.ij[b];
-    const int p = T.par[b], ncl = QN << (l - 1);
-    const int Gx = B.x * QN + gi, Gy = B.y * QN + gj, cx = Gx >> 1, cy = Gy >> 1;
+    const int ncl = QN << (C.lev - 1);
+    const int Gx = C.ix * QN + gi, Gy = C.iy * QN + gj, cx = Gx >> 1, cy = Gy >> 1;
     int qx = cx, qy = cy;
     if (f < 2) qy += (Gy & 1) ? 1 : -1;
     else qx += (Gx & 1) ? 1 : -1;
-    // the coarse level of a refinement boundary holds no refined values
-    // here: the cells across the face belong to a leaf
-    const double c = coarse_val(var, T, p, cx, cy, cx, cy, ncl, bc, homog, false, err);
-    const double ct = coarse_val(var, T, p, qx, qy, cx, cy, ncl, bc, homog, false, err);
+    // the cells across a refinement face belong to a leaf: var holds them
+    const double c = coarse_val(var, C, cx, cy, cx, cy, ncl, bc, homog, false, err);
+    const double ct = coarse_val(var, C, qx, qy, cx, cy, ncl, bc, homog, false, err);
     const double phat = 0.75 * c + 0.25 * ct;
     v = inner * (1.0 / 3.0) + phat * (2.0 / 3.0);
   }
@@ -162,25 +191,30 @@ __device__ __forceinline__ double lap_s(const double *s, const QTabs &T, int b, 
 }
 
 #define QWARP()                                  \
+  __shared__ BoxCtx ctx_[WPB];                   \
   const int wv_ = threadIdx.x >> 5, lane = threadIdx.x & 31; \
-  const int k_ = blockIdx.x * WPB + wv_;
+  const int k_ = blockIdx.x * WPB + wv_;         \
+  BoxCtx &C = ctx_[wv_];
 
 // one colour pass of red-black Gauss-Seidel on the n boxes of level l
 __global__ void __launch_bounds__(QT) k_q_rbgs(int off, int n, int l, int colour, double *__restrict__ phi,
-                                               const double *__restrict__ rhs, QTabs T, QBc bc, double h2,
+                                               const double *__restrict__ rhs, QTabs T, const __grid_constant__ QBc bc, double h2,
                                                unsigned *err) {
   __shared__ double sm[WPB][S1 * S1];
   QWARP();
   if (k_ >= n) return;  // the whole warp
   const int b = off + k_;
   double *s = sm[wv_];
-  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
   const int j = lane >> 2, i = 2 * (lane & 3) + ((j + colour) & 1);
   const double *wc = T.w + (size_t)b * 24 + 3 * i;
+  const double fr = rhs[(size_t)b * QC + i + QN * j], w0 = wc[0], w1 = wc[1], w2 = wc[2];
+  double v0, v1;
+  begin_box(phi, T, b, C, lane, v0, v1);
+  stage_phi(phi, nullptr, C, b, bc, 0, s, lane, err, v0, v1);
   phi[(size_t)b * QC + i + QN * j] =
-      (wc[0] * s[(j + 1) * S1 + i] + wc[1] * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
-       h2 * rhs[(size_t)b * QC + i + QN * j]) *
-      wc[2];
+      (w0 * s[(j + 1) * S1 + i] + w1 * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
+       h2 * fr) *
+      w2;
 }
 
 // Residual of every box of level l restricted to its parent's quadrant:
@@ -189,21 +223,23 @@ __global__ void __launch_bounds__(QT) k_q_rbgs(int off, int n, int l, int colour
 // residual into rhs[parent].  Volume-weighted mean of the four children.
 __global__ void __launch_bounds__(QT) k_q_resid_restrict(int off, int n, int l, const double *__restrict__ phi,
                                                          double *__restrict__ rhs, double *__restrict__ old,
-                                                         QTabs T, QBc bc, double inv_h2, unsigned *err) {
+                                                         QTabs T, const __grid_constant__ QBc bc, double inv_h2, unsigned *err) {
   __shared__ double sm[WPB][S1 * S1];
   __shared__ double sr[WPB][QC];
   QWARP();
   if (k_ >= n) return;
   const int b = off + k_;
   double *s = sm[wv_];
-  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  double v0, v1;
+  begin_box(phi, T, b, C, lane, v0, v1);
+  stage_phi(phi, nullptr, C, b, bc, 0, s, lane, err, v0, v1);
   for (int c = lane; c < QC; c += 32) {
     const int i = c % QN, j = c / QN;
     sr[wv_][c] = rhs[(size_t)b * QC + c] - lap_s(s, T, b, i, j, inv_h2);
   }
   __syncwarp();
-  const int p = T.par[b];
-  const int2 B = T.ij[b];
+  const int p = C.pn[4];
+  const int2 B = make_int2(C.ix, C.iy);
   const int m = lane & 15, ii = m & 3, jj = m >> 2;
   double sum = 0.0, wsum = 0.0;
   for (int dj = 0; dj < 2; ++dj)
@@ -221,23 +257,28 @@ __global__ void __launch_bounds__(QT) k_q_resid_restrict(int off, int n, int l, 
 // old and get the FAS right-hand side f += L phi; every box ends with
 // old = phi (the values the coarse correction is measured against).
 __global__ void __launch_bounds__(QT) k_q_fas(int off, int n, int l, double *__restrict__ phi,
-                                              double *__restrict__ rhs, double *__restrict__ old, QTabs T, QBc bc,
+                                              double *__restrict__ rhs, double *__restrict__ old, QTabs T, const __grid_constant__ QBc bc,
                                               double inv_h2, unsigned *err) {
   __shared__ double sm[WPB][S1 * S1];
   QWARP();
   if (k_ >= n) return;
   const int b = off + k_;
-  const bool refined = T.chl[4 * b] >= 0;
+  const size_t g0 = (size_t)b * QC + lane, g1 = g0 + 32;
+  const double o0 = old[g0], o1 = old[g1], f0 = rhs[g0], f1 = rhs[g1];
+  double v0, v1;
+  begin_box(phi, T, b, C, lane, v0, v1);
+  const bool refined = C.ref & 16;
   double *s = sm[wv_];
-  if (refined) stage_phi(phi, old, T, b, l, bc, 0, s, lane, err);
-  for (int c = lane; c < QC; c += 32) {
-    const size_t g = (size_t)b * QC + c;
-    if (refined) {
-      rhs[g] += lap_s(s, T, b, c % QN, c / QN, inv_h2);
-      phi[g] = old[g];
-    } else {
-      old[g] = phi[g];
-    }
+  if (refined) {
+    // the box's restricted values; neighbours with children read old too
+    stage_phi(phi, old, C, b, bc, 0, s, lane, err, o0, o1);
+    rhs[g0] = f0 + lap_s(s, T, b, lane % QN, lane / QN, inv_h2);
+    rhs[g1] = f1 + lap_s(s, T, b, lane % QN, lane / QN + 4, inv_h2);
+    phi[g0] = o0;
+    phi[g1] = o1;
+  } else {
+    old[g0] = v0;
+    old[g1] = v1;
   }
 }
 
@@ -245,15 +286,16 @@ __global__ void __launch_bounds__(QT) k_q_fas(int off, int n, int l, double *__r
 // level.  corr: the correction phi - old (homogeneous wall ghosts) added to
 // phi; otherwise phi itself (FMG, wall values) replaces phi.
 __global__ void __launch_bounds__(QT) k_q_prolong(int off, int n, int l, double *__restrict__ phi,
-                                                  const double *__restrict__ old, int corr, QTabs T, QBc bc,
+                                                  const double *__restrict__ old, int corr, QTabs T, const __grid_constant__ QBc bc,
                                                   unsigned *err) {
   QWARP();
   if (k_ >= n) return;
-  const int b = off + k_, p = T.par[b], ncl = QN << (l - 1);
-  const int2 B = T.ij[b];
+  const int b = off + k_, ncl = QN << (l - 1);
+  load_ctx(T, b, C, lane);
+  const int2 B = make_int2(C.ix, C.iy);
   auto cv = [&](int qx, int qy, int fx, int fy) {
-    const double a = coarse_val(phi, T, p, qx, qy, fx, fy, ncl, bc, corr, false, err);
-    return corr ? a - coarse_val(old, T, p, qx, qy, fx, fy, ncl, bc, corr, false, err) : a;
+    const double a = coarse_val(phi, C, qx, qy, fx, fy, ncl, bc, corr, false, err);
+    return corr ? a - coarse_val(old, C, qx, qy, fx, fy, ncl, bc, corr, false, err) : a;
   };
   for (int c = lane; c < QC; c += 32) {
     const int Gx = B.x * QN + c % QN, Gy = B.y * QN + c / QN, cx = Gx >> 1, cy = Gy >> 1;
@@ -269,7 +311,7 @@ __global__ void __launch_bounds__(QT) k_q_prolong(int off, int n, int l, double 
 // matrix with homogeneous wall ghosts (inverted on the host), L0 the
 // operator of phi = 0 with the wall values.
 __global__ void k_q_coarse(double *__restrict__ phi, const double *__restrict__ rhs, const double *__restrict__ ainv,
-                           QTabs T, QBc bc, double inv_h2) {
+                           QTabs T, const __grid_constant__ QBc bc, double inv_h2) {
   __shared__ double r[QC];
   const int c = threadIdx.x, i = c % QN, j = c / QN;
   const double wl = T.w[3 * i], wh = T.w[3 * i + 1];
@@ -297,17 +339,19 @@ __device__ __forceinline__ void max_bits(unsigned long long *slot, double v) {
 // max |f - L var| over the leaf cells of all boxes (var = a zero array for
 // the denominator)
 __global__ void __launch_bounds__(QT) k_q_resmax(int n, const double *__restrict__ var,
-                                                 const double *__restrict__ rhs, QTabs T, QBc bc,
+                                                 const double *__restrict__ rhs, QTabs T, const __grid_constant__ QBc bc,
                                                  const double *__restrict__ inv_h2, unsigned long long *slot,
                                                  unsigned *err) {
   __shared__ double sm[WPB][S1 * S1];
   QWARP();
   if (k_ >= n) return;
   const int b = k_;
-  if (T.chl[4 * b] >= 0) return;
+  double v0, v1;
+  begin_box(var, T, b, C, lane, v0, v1);
+  if (C.ref & 16) return;
   double *s = sm[wv_];
-  const int l = T.lev[b];
-  stage_phi(var, nullptr, T, b, l, bc, 0, s, lane, err);
+  const int l = C.lev;
+  stage_phi(var, nullptr, C, b, bc, 0, s, lane, err, v0, v1);
   double m = 0.0;
   for (int c = lane; c < QC; c += 32)
     m = fmax(m, fabs(rhs[(size_t)b * QC + c] - lap_s(s, T, b, c % QN, c / QN, inv_h2[l])));
@@ -327,19 +371,21 @@ __global__ void k_q_charge(int n, double *__restrict__ rhs, const double *__rest
 // |E| on leaf cells: face fields (phi_i - phi_{i+1})/h, cell components the
 // mean of the two faces; zero on refined boxes
 __global__ void __launch_bounds__(QT) k_q_field(int n, const double *__restrict__ phi, double *__restrict__ emag,
-                                                QTabs T, QBc bc, const double *__restrict__ inv_h,
+                                                QTabs T, const __grid_constant__ QBc bc, const double *__restrict__ inv_h,
                                                 unsigned *err) {
   __shared__ double sm[WPB][S1 * S1];
   QWARP();
   if (k_ >= n) return;
   const int b = k_;
-  if (T.chl[4 * b] >= 0) {
+  double v0, v1;
+  begin_box(phi, T, b, C, lane, v0, v1);
+  if (C.ref & 16) {
     for (int c = lane; c < QC; c += 32) emag[(size_t)b * QC + c] = 0.0;
     return;
   }
   double *s = sm[wv_];
-  const int l = T.lev[b];
-  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  const int l = C.lev;
+  stage_phi(phi, nullptr, C, b, bc, 0, s, lane, err, v0, v1);
   const double ih = inv_h[l];
   for (int c = lane; c < QC; c += 32) {
     const int i = c % QN, j = c / QN;
@@ -375,21 +421,22 @@ __device__ __forceinline__ double koren(double a, double b) {
 // boundaries the prolongation (2c + c_x + c_y)/4 of the coarse cell
 // containing the ghost, limited to 2c; |E| ghosts the inner value at walls
 // and the coarse cell's value at refinement boundaries.
-__device__ void stage_fluid(const double *nv, const double *phi, const double *emag, const QTabs &T, int b,
-                            int l, const QBc &bc, double *sn, double *sp, double *se, int lane, unsigned *err) {
-  stage_phi(phi, nullptr, T, b, l, bc, 0, sp, lane, err);
+__device__ void stage_fluid(const double *nv, const double *phi, const double *emag, const BoxCtx &C, int b,
+                            const QBc &bc, double *sn, double *sp, double *se, int lane, unsigned *err) {
+  const int l = C.lev;
+  stage_phi(phi, nullptr, C, b, bc, 0, sp, lane, err, phi[(size_t)b * QC + lane], phi[(size_t)b * QC + lane + 32]);
   for (int c = lane; c < QC; c += 32) {
     sn[(c / QN + 2) * S2 + c % QN + 2] = nv[(size_t)b * QC + c];
     se[(c / QN + 1) * S1 + c % QN + 1] = emag[(size_t)b * QC + c];
   }
   __syncwarp();
-  const int2 B = T.ij[b];
-  const int p = l > 0 ? T.par[b] : 0, ncl = l > 0 ? (QN << (l - 1)) : 0;
+  const int2 B = make_int2(C.ix, C.iy);
+  const int ncl = l > 0 ? (QN << (l - 1)) : 0;
   for (int g = lane; g < 64; g += 32) {  // density: 4 faces x 2 layers x 8
     const int f = g >> 4, t = 1 + ((g >> 3) & 1), u = g & 7;
     int gi, gj;
     face_cell(f, -t, u, gi, gj);
-    const int nb = T.nbr8[8 * b + face_dir8(f)];
+    const int nb = C.nb[f];
     double v;
     if (nb >= 0) {
       int si, sj;
@@ -401,9 +448,9 @@ __device__ void stage_fluid(const double *nv, const double *phi, const double *e
       v = sn[(mj + 2) * S2 + mi + 2];
     } else {
       const int Gx = B.x * QN + gi, Gy = B.y * QN + gj, cx = Gx >> 1, cy = Gy >> 1;
-      const double c = coarse_val(nv, T, p, cx, cy, cx, cy, ncl, bc, 0, true, err);
-      const double sum = 2.0 * c + coarse_val(nv, T, p, cx + ((Gx & 1) ? 1 : -1), cy, cx, cy, ncl, bc, 0, true, err) +
-                         coarse_val(nv, T, p, cx, cy + ((Gy & 1) ? 1 : -1), cx, cy, ncl, bc, 0, true, err);
+      const double c = coarse_val(nv, C, cx, cy, cx, cy, ncl, bc, 0, true, err);
+      const double sum = 2.0 * c + coarse_val(nv, C, cx + ((Gx & 1) ? 1 : -1), cy, cx, cy, ncl, bc, 0, true, err) +
+                         coarse_val(nv, C, cx, cy + ((Gy & 1) ? 1 : -1), cx, cy, ncl, bc, 0, true, err);
       v = fmin(0.25 * sum, 2.0 * c);
     }
     sn[(gj + 2) * S2 + gi + 2] = v;
@@ -413,7 +460,7 @@ __device__ void stage_fluid(const double *nv, const double *phi, const double *e
     int ci, cj, gi, gj;
     face_cell(f, 0, u, ci, cj);
     face_cell(f, -1, u, gi, gj);
-    const int nb = T.nbr8[8 * b + face_dir8(f)];
+    const int nb = C.nb[f];
     double v;
     if (nb >= 0) {
       int si, sj;
@@ -423,7 +470,7 @@ __device__ void stage_fluid(const double *nv, const double *phi, const double *e
       v = se[(cj + 1) * S1 + ci + 1];
     } else {
       const int cx = (B.x * QN + gi) >> 1, cy = (B.y * QN + gj) >> 1;
-      v = coarse_val(emag, T, p, cx, cy, cx, cy, ncl, bc, 0, true, err);
+      v = coarse_val(emag, C, cx, cy, cx, cy, ncl, bc, 0, true, err);
     }
     se[(gj + 1) * S1 + gi + 1] = v;
   }
@@ -449,20 +496,21 @@ __device__ __forceinline__ double face_flux(const double *sn, const double *sp, 
 // cflux[box][face][u]
 __global__ void __launch_bounds__(QT) k_q_cf_flux(int n, const double *__restrict__ nv, const double *__restrict__ phi,
                                                   const double *__restrict__ emag, double *__restrict__ cflux,
-                                                  QTabs T, QBc bc, QLut L, const double *__restrict__ hs,
+                                                  QTabs T, const __grid_constant__ QBc bc, QLut L, const double *__restrict__ hs,
                                                   unsigned *err) {
   __shared__ double snm[WPB][S2 * S2], spm[WPB][S1 * S1], sem[WPB][S1 * S1];
   QWARP();
   if (k_ >= n) return;
   const int b = k_;
-  if (T.chl[4 * b] >= 0) return;
+  load_ctx(T, b, C, lane);
+  if (C.ref & 16) return;
   bool any = false;
-  for (int f = 0; f < 4; ++f) any |= T.nbr8[8 * b + face_dir8(f)] == -2;
+  for (int f = 0; f < 4; ++f) any |= C.nb[f] == -2;
   if (!any) return;
-  const int l = T.lev[b];
-  stage_fluid(nv, phi, emag, T, b, l, bc, snm[wv_], spm[wv_], sem[wv_], lane, err);
+  const int l = C.lev;
+  stage_fluid(nv, phi, emag, C, b, bc, snm[wv_], spm[wv_], sem[wv_], lane, err);
   const int f = lane >> 3, u = lane & 7;
-  if (T.nbr8[8 * b + face_dir8(f)] == -2)
+  if (C.nb[f] == -2)
     cflux[(size_t)b * 32 + f * 8 + u] =
         face_flux(snm[wv_], spm[wv_], sem[wv_], f >> 1, (f & 1) ? QN : 0, u, hs[l], 1.0 / hs[l], L);
 }
@@ -473,24 +521,25 @@ __global__ void __launch_bounds__(QT) k_q_cf_flux(int n, const double *__restric
 __global__ void __launch_bounds__(QT) k_q_update(int n, const double *__restrict__ ne, const double *__restrict__ ni,
                                                  double *__restrict__ ne_out, double *__restrict__ ni_out,
                                                  const double *__restrict__ phi, const double *__restrict__ emag,
-                                                 const double *__restrict__ cflux, QTabs T, QBc bc, QLut L,
+                                                 const double *__restrict__ cflux, QTabs T, const __grid_constant__ QBc bc, QLut L,
                                                  const double *__restrict__ hs, double dt, unsigned *err) {
   __shared__ double snm[WPB][S2 * S2], spm[WPB][S1 * S1], sem[WPB][S1 * S1];
   __shared__ double sf[WPB][2][(QN + 1) * QN];
   QWARP();
   if (k_ >= n) return;
   const int b = k_;
-  if (T.chl[4 * b] >= 0) return;
-  const int l = T.lev[b];
+  load_ctx(T, b, C, lane);
+  if (C.ref & 16) return;
+  const int l = C.lev;
   const double h = hs[l], ih = 1.0 / h;
-  stage_fluid(ne, phi, emag, T, b, l, bc, snm[wv_], spm[wv_], sem[wv_], lane, err);
+  stage_fluid(ne, phi, emag, C, b, bc, snm[wv_], spm[wv_], sem[wv_], lane, err);
   for (int g = lane; g < 2 * (QN + 1) * QN; g += 32) {
     const int a = g / ((QN + 1) * QN), r = g % ((QN + 1) * QN), m = r / QN, u = r % QN;
     double F = face_flux(snm[wv_], spm[wv_], sem[wv_], a, m, u, h, ih, L);
     if (m == 0 || m == QN) {
       const int f = 2 * a + (m == QN ? 1 : 0);
-      const int nb = T.nbr8[8 * b + face_dir8(f)];
-      if (nb >= 0 && T.chl[4 * nb] >= 0) {  // refined neighbour: mean of its fine fluxes
+      const int nb = C.nb[f];
+      if ((C.ref >> f) & 1) {  // refined neighbour: mean of its fine fluxes
         int cx, cy;
         if (a == 0) {
           cx = (f & 1) ? 0 : 1;
@@ -531,9 +580,10 @@ __global__ void __launch_bounds__(QT) k_q_restrict(int off, int n, double *__res
   QWARP();
   if (k_ >= n) return;
   const int b = off + k_;
+  load_ctx(T, b, C, lane);
   if (lane >= 16) return;
-  const int p = T.par[b];
-  const int2 B = T.ij[b];
+  const int p = C.pn[4];
+  const int2 B = make_int2(C.ix, C.iy);
   const int ii = lane & 3, jj = lane >> 2;
   double sum = 0.0, wsum = 0.0;
   for (int dj = 0; dj < 2; ++dj)
@@ -549,17 +599,19 @@ __global__ void __launch_bounds__(QT) k_q_restrict(int off, int n, double *__res
 // time-step limits: max over leaf cells of sum|v_d|/dx, that plus 4D/dx^2,
 // and mu n_e (slots 0..2, bit patterns of non-negative doubles)
 __global__ void __launch_bounds__(QT) k_q_dt(int n, const double *__restrict__ phi, const double *__restrict__ emag,
-                                             const double *__restrict__ ne, QTabs T, QBc bc, QLut L,
+                                             const double *__restrict__ ne, QTabs T, const __grid_constant__ QBc bc, QLut L,
                                              const double *__restrict__ hs, unsigned long long *slots,
                                              unsigned *err) {
   __shared__ double sm[WPB][S1 * S1];
   QWARP();
   if (k_ >= n) return;
   const int b = k_;
-  if (T.chl[4 * b] >= 0) return;
-  const int l = T.lev[b];
+  double v0, v1;
+  begin_box(phi, T, b, C, lane, v0, v1);
+  if (C.ref & 16) return;
+  const int l = C.lev;
   double *s = sm[wv_];
-  stage_phi(phi, nullptr, T, b, l, bc, 0, s, lane, err);
+  stage_phi(phi, nullptr, C, b, bc, 0, s, lane, err, v0, v1);
   const double h = hs[l], ih = 1.0 / h;
   double m0 = 0.0, m1 = 0.0, m2 = 0.0;
   for (int c = lane; c < QC; c += 32) {
@@ -607,7 +659,7 @@ struct sm_quad {
   int off[QMAXL + 2] = {0};
   // arena
   char *arena = nullptr;
-  int *d_lev = nullptr, *d_par = nullptr, *d_chl = nullptr, *d_nbr8 = nullptr;
+  int *d_lev = nullptr, *d_par = nullptr, *d_chl = nullptr, *d_nbr8 = nullptr, *d_pn = nullptr, *d_ref = nullptr;
   int2 *d_ij = nullptr;
   double *d_w = nullptr, *d_wv = nullptr;
   double *var[NV] = {nullptr};
@@ -685,13 +737,30 @@ int n_boxes(const sm_quad *q) { return (int)q->lev.size(); }
 int upload_tables(sm_quad *q) {
   const int n = n_boxes(q);
   std::vector<int2> ij(n);
-  for (int b = 0; b < n; ++b) ij[b] = make_int2(q->ix[b], q->iy[b]);
+  std::vector<int> pn(9 * (size_t)n, -1), ref(n, 0);
+  for (int b = 0; b < n; ++b) {
+    ij[b] = make_int2(q->ix[b], q->iy[b]);
+    const int p = q->par[b];
+    if (p >= 0)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx)
+          pn[9 * (size_t)b + (dx + 1) + 3 * (dy + 1)] = (dx || dy) ? q->nbr8[8 * p + dir8h(dx, dy)] : p;
+    int r = q->chl[4 * b] >= 0 ? 16 : 0;
+    const int fd[4] = {dir8h(-1, 0), dir8h(1, 0), dir8h(0, -1), dir8h(0, 1)};
+    for (int f = 0; f < 4; ++f) {
+      const int nb = q->nbr8[8 * b + fd[f]];
+      if (nb >= 0 && q->chl[4 * nb] >= 0) r |= 1 << f;
+    }
+    ref[b] = r;
+  }
   cudaStream_t s = q->stream;
   if (cudaMemcpyAsync(q->d_lev, q->lev.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_par, q->par.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_chl, q->chl.data(), sizeof(int) * 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_nbr8, q->nbr8.data(), sizeof(int) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_ij, ij.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_pn, pn.data(), sizeof(int) * 9 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_ref, ref.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_w, q->w.data(), sizeof(double) * 24 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_wv, q->wv.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -699,7 +768,9 @@ int upload_tables(sm_quad *q) {
   return SM_OK;
 }
 
-QTabs tabs(const sm_quad *q) { return {q->d_lev, q->d_par, q->d_chl, q->d_nbr8, q->d_ij, q->d_w, q->d_wv}; }
+QTabs tabs(const sm_quad *q) {
+  return {q->d_lev, q->d_par, q->d_chl, q->d_nbr8, q->d_pn, q->d_ref, q->d_ij, q->d_w, q->d_wv};
+}
 QLut qlut(const sm_quad *q) {
   return {q->lut, q->lut + q->lut_n, q->lut + 2 * q->lut_n, q->lut_n, (q->lut_n - 1) / q->lut_emax};
 }
@@ -978,7 +1049,7 @@ extern "C" int sm_quad_destroy(sm_quad *q) {
 
 namespace {
 struct QLayout {
-  size_t lev, par, chl, nbr8, ij, w, wv, var[NV], cflux, ainv, lut, h, slots, err, total;
+  size_t lev, par, chl, nbr8, pn, ref, ij, w, wv, var[NV], cflux, ainv, lut, h, slots, err, total;
 };
 QLayout qlayout(const sm_quad *q) {
   QLayout L{};
@@ -993,6 +1064,8 @@ QLayout qlayout(const sm_quad *q) {
   L.par = take(sizeof(int) * nb);
   L.chl = take(sizeof(int) * 4 * nb);
   L.nbr8 = take(sizeof(int) * 8 * nb);
+  L.pn = take(sizeof(int) * 9 * nb);
+  L.ref = take(sizeof(int) * nb);
   L.ij = take(sizeof(int2) * nb);
   L.w = take(sizeof(double) * 24 * nb);
   L.wv = take(sizeof(double) * 8 * nb);
@@ -1025,6 +1098,8 @@ extern "C" int sm_quad_bind_arena(sm_quad *q, void *dev_ptr, size_t bytes) {
   q->d_par = (int *)(a + L.par);
   q->d_chl = (int *)(a + L.chl);
   q->d_nbr8 = (int *)(a + L.nbr8);
+  q->d_pn = (int *)(a + L.pn);
+  q->d_ref = (int *)(a + L.ref);
   q->d_ij = (int2 *)(a + L.ij);
   q->d_w = (double *)(a + L.w);
   q->d_wv = (double *)(a + L.wv);
