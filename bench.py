@@ -666,7 +666,8 @@ def bench_axisymmetric(args, dev, world):
            "workload": "axi_streamer", "geometry": "axisymmetric (r, z)", "boxes": len(t["level"]),
            "leaf_cells": leaf_cells, "levels": int(len(t["level_offset"]) - 1), "tol": TOL,
            "dtype": "f64", "l2": "flushed between steps",
-           "note": "per-level launches driven from the host, one residual read per V-cycle"}
+           "note": "per-level launches, each V-cycle a CUDA graph (one per top level), one residual "
+                   "read per V-cycle"}
     g.close()
     return res
 

@@ -132,7 +132,12 @@ int sm_quad_fluid_stage(sm_quad *q, double dt);
 int sm_quad_advance(sm_quad *q, double dt, double charge, double eps, double tol, int max_cycles,
                     double *dt_next, int *cycles);
 
-/* Kernel launches issued by this context so far. */
+/* on != 0 (the default): each V-cycle runs as a CUDA graph, captured per
+ * top level on first use and dropped when the mesh or the arena changes;
+ * 0: the same launches are issued from the host.  Results are identical. */
+int sm_quad_set_graphs(sm_quad *q, int on);
+/* Kernel launches issued by this context so far (a graph counts its
+ * kernels). */
 int sm_quad_launch_count(const sm_quad *q, long long *n);
 /* One-line reason of the last error of this context ("" if none). */
 const char *sm_quad_last_error(const sm_quad *q);

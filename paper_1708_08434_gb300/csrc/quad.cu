@@ -670,6 +670,17 @@ struct sm_quad {
   double lut_emax = 0.0;
   double h[QMAXL], inv_h2[QMAXL];
   std::vector<double> h_ainv;
+  // V-cycle graphs per top level (captured on first use, dropped when the
+  // mesh changes) and the launches each holds
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t vgraph[QMAXL] = {nullptr};
+  long long vgraph_launches[QMAXL] = {0};
+  bool graphs = true;
+  ~sm_quad() {
+    for (auto &g : vgraph)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap) cudaStreamDestroy(cap);
+  }
 };
 
 namespace {
@@ -864,6 +875,51 @@ void vcycle(sm_quad *q, int top) {
   }
 }
 
+void drop_graphs(sm_quad *q) {
+  for (int l = 0; l < QMAXL; ++l)
+    if (q->vgraph[l]) {
+      cudaGraphExecDestroy(q->vgraph[l]);
+      q->vgraph[l] = nullptr;
+    }
+}
+
+// One V-cycle with level `top` on top, as a CUDA graph captured on first
+// use (the same launches as vcycle; host launch gaps removed)
+int vcycle_g(sm_quad *q, int top) {
+  if (!q->graphs) {
+    vcycle(q, top);
+    return check(q, "V-cycle");
+  }
+  if (!q->vgraph[top]) {
+    if (!q->cap && cudaStreamCreateWithFlags(&q->cap, cudaStreamNonBlocking) != cudaSuccess)
+      return qfail(q, SM_ECUDA, "capture stream");
+    cudaStream_t saved = q->stream;
+    const long long l0 = q->launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(q->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return qfail(q, SM_ECUDA, "begin capture");
+    q->stream = q->cap;
+    vcycle(q, top);
+    q->stream = saved;
+    const cudaError_t e = cudaStreamEndCapture(q->cap, &g);
+    if (e != cudaSuccess || !g) {
+      cudaGetLastError();
+      return qfail(q, SM_ECUDA, "V-cycle capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&q->vgraph[top], g, 0);
+    cudaGraphDestroy(g);
+    q->vgraph_launches[top] = q->launches - l0;
+    q->launches = l0;
+    if (ei != cudaSuccess) {
+      q->vgraph[top] = nullptr;
+      return qfail(q, SM_ECUDA, "V-cycle instantiate");
+    }
+  }
+  if (cudaGraphLaunch(q->vgraph[top], q->stream) != cudaSuccess) return qfail(q, SM_ECUDA, "graph launch");
+  q->launches += q->vgraph_launches[top];
+  return SM_OK;
+}
+
 // max leaf residual of var (the potential, or the zero array)
 int resmax(sm_quad *q, int v, double *out) {
   const int n = n_boxes(q);
@@ -902,9 +958,8 @@ int solve_loop(sm_quad *q, double tol, int max_cycles, int c0, int *cycles, doub
     if (int st = rel_residual(q, &r)) return st;
   }
   while (c == 0 || (r > tol && c < max_cycles)) {
-    vcycle(q, q->nlev - 1);
+    if (int st = vcycle_g(q, q->nlev - 1)) return st;
     ++c;
-    if (int st = check(q, "V-cycle")) return st;
     if (int st = rel_residual(q, &r)) return st;
   }
   if (cycles) *cycles = c;
@@ -1093,6 +1148,7 @@ extern "C" int sm_quad_bind_arena(sm_quad *q, void *dev_ptr, size_t bytes) {
   if (bytes < L.total) return qfail(q, SM_ENOMEM, "arena too small");
   if (((uintptr_t)dev_ptr & 255) != 0) return qfail(q, SM_EINVAL, "arena not 256-byte aligned");
   char *a = (char *)dev_ptr;
+  drop_graphs(q);
   q->arena = a;
   q->d_lev = (int *)(a + L.lev);
   q->d_par = (int *)(a + L.par);
@@ -1153,6 +1209,7 @@ extern "C" int sm_quad_refine_level(sm_quad *q, int level, const int8_t *flags, 
   q->off[level + 2] = n_boxes(q);
   q->nlev = level + 2;
   set_neighbours(q, level + 1);
+  drop_graphs(q);
   // the new boxes' fields start at zero
   for (int v = 0; v < NV; ++v)
     if (cudaMemsetAsync(q->var[v] + (size_t)start * QC, 0, sizeof(double) * QC * (size_t)(n_boxes(q) - start),
@@ -1245,7 +1302,7 @@ extern "C" int sm_quad_fmg(sm_quad *q, double tol, int max_cycles, int *cycles, 
     k_q_prolong<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, q->var[V_PHI], q->var[V_OLD], 0, tabs(q),
                                                       q->bc, q->d_err);
     ++q->launches;
-    vcycle(q, l);
+    if (int st = vcycle_g(q, l)) return st;
   }
   if (int st = check(q, "FMG")) return st;
   return solve_loop(q, tol, max_cycles, 1, cycles, rel);
@@ -1260,7 +1317,8 @@ extern "C" int sm_quad_solve(sm_quad *q, double tol, int max_cycles, int *cycles
 extern "C" int sm_quad_vcycles(sm_quad *q, int n) {
   if (!q || n < 0) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
-  for (int c = 0; c < n; ++c) vcycle(q, q->nlev - 1);
+  for (int c = 0; c < n; ++c)
+    if (int st = vcycle_g(q, q->nlev - 1)) return st;
   return check(q, "V-cycle");
 }
 
@@ -1326,6 +1384,12 @@ extern "C" int sm_quad_advance(sm_quad *q, double dt, double c, double eps, doub
   }
   if (cudaStreamSynchronize(q->stream) != cudaSuccess) return qfail(q, SM_ECUDA, "advance");
   return st1 ? st1 : st2;
+}
+
+extern "C" int sm_quad_set_graphs(sm_quad *q, int on) {
+  if (!q) return SM_EINVAL;
+  q->graphs = on != 0;
+  return SM_OK;
 }
 
 extern "C" int sm_quad_launch_count(const sm_quad *q, long long *n) {

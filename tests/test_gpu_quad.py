@@ -225,3 +225,21 @@ def test_error_paths():
     small = p.Quad(dom, 21 + 3)                         # room for the uniform levels only
     with pytest.raises(p.SmError):
         small.refine_level(2, np.ones(16, np.int8))
+
+
+def test_graph_and_host_paths_identical():
+    """V-cycles as CUDA graphs and the same launches from the host give the
+    same bits; the launch count is the same either way."""
+    p = pkg()
+    out = []
+    for graphs in (True, False):
+        dom, st = synth.workload2("axi_small")
+        g = gpu_quad(dom, st)
+        g.set_graphs(graphs)
+        o = quad.build_mesh(dom, st)
+        load(dom, st, o, g)
+        l0 = g.launch_count()
+        rc, rel, cyc = g.fmg(1e-9, 40)
+        out.append((cyc, rel, g.download(p.PHI), g.launch_count() - l0))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and out[0][3] == out[1][3]
+    assert np.array_equal(out[0][2], out[1][2])
