@@ -136,6 +136,11 @@ int sm_quad_advance(sm_quad *q, double dt, double charge, double eps, double tol
  * top level on first use and dropped when the mesh or the arena changes;
  * 0: the same launches are issued from the host.  Results are identical. */
 int sm_quad_set_graphs(sm_quad *q, int on);
+/* on != 0 (the default): the V-cycle kernels are launched with programmatic
+ * dependent launch (each loads its box's tables while its predecessor
+ * drains, and waits for it before reading a field); 0: plain stream
+ * order.  Results are identical. */
+int sm_quad_set_pdl(sm_quad *q, int on);
 /* Kernel launches issued by this context so far (a graph counts its
  * kernels). */
 int sm_quad_launch_count(const sm_quad *q, long long *n);

@@ -74,7 +74,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_quad_refine_level", "sm_quad_get_tables", "sm_quad_var_ptr", "sm_quad_upload",
            "sm_quad_download", "sm_quad_set_table", "sm_quad_charge_rhs", "sm_quad_fmg",
            "sm_quad_solve", "sm_quad_vcycles", "sm_quad_compute_field", "sm_quad_dt_limit", "sm_quad_fluid_stage",
-           "sm_quad_advance", "sm_quad_set_graphs", "sm_quad_launch_count", "sm_quad_last_error"]
+           "sm_quad_advance", "sm_quad_set_graphs", "sm_quad_set_pdl", "sm_quad_launch_count", "sm_quad_last_error"]
 
 
 def library_path() -> str:
@@ -169,6 +169,7 @@ def load():
         "sm_quad_fluid_stage": [P, D],
         "sm_quad_advance": [P, D, D, D, D, I, pD, P],
         "sm_quad_set_graphs": [P, I],
+        "sm_quad_set_pdl": [P, I],
         "sm_quad_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_quad_last_error": [P],
     }
@@ -770,6 +771,9 @@ class Quad:
 
     def set_graphs(self, on: bool):
         self._ck(self._lib.sm_quad_set_graphs(self._h, int(bool(on))))
+
+    def set_pdl(self, on: bool):
+        self._ck(self._lib.sm_quad_set_pdl(self._h, int(bool(on))))
 
     def launch_count(self) -> int:
         n = C.c_longlong()

@@ -30,6 +30,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sm_quad.h"
@@ -134,13 +135,19 @@ __device__ __forceinline__ double coarse_val(const double *var, const BoxCtx &C,
   return bc.type[f] ? (homog ? 0.0 : bc.g2[f]) - v : v;
 }
 
-// The first round of a box kernel: the box's own values (cells lane and
-// lane + 32) issued together with the context loads.
+// Programmatic dependent launch: a kernel launched with it may start while
+// its predecessor drains; it loads only tables (which no kernel writes)
+// before this wait, and every field value after it.
+__device__ __forceinline__ void q_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// The start of a box kernel: the box's context, the wait for the
+// predecessor, then the box's own values (cells lane and lane + 32).
 __device__ __forceinline__ void begin_box(const double *var, const QTabs &T, int b, BoxCtx &C, int lane, double &v0,
                                           double &v1) {
+  load_ctx(T, b, C, lane);
+  q_wait();
   v0 = var[(size_t)b * QC + lane];
   v1 = var[(size_t)b * QC + lane + 32];
-  load_ctx(T, b, C, lane);
 }
 
 // Stage box b into s (S1 x S1, interior at (i+1, j+1)) with the potential
@@ -207,9 +214,10 @@ __global__ void __launch_bounds__(QT) k_q_rbgs(int off, int n, int l, int colour
   double *s = sm[wv_];
   const int j = lane >> 2, i = 2 * (lane & 3) + ((j + colour) & 1);
   const double *wc = T.w + (size_t)b * 24 + 3 * i;
-  const double fr = rhs[(size_t)b * QC + i + QN * j], w0 = wc[0], w1 = wc[1], w2 = wc[2];
+  const double w0 = wc[0], w1 = wc[1], w2 = wc[2];
   double v0, v1;
   begin_box(phi, T, b, C, lane, v0, v1);
+  const double fr = rhs[(size_t)b * QC + i + QN * j];
   stage_phi(phi, nullptr, C, b, bc, 0, s, lane, err, v0, v1);
   phi[(size_t)b * QC + i + QN * j] =
       (w0 * s[(j + 1) * S1 + i] + w1 * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
@@ -264,9 +272,9 @@ __global__ void __launch_bounds__(QT) k_q_fas(int off, int n, int l, double *__r
   if (k_ >= n) return;
   const int b = off + k_;
   const size_t g0 = (size_t)b * QC + lane, g1 = g0 + 32;
-  const double o0 = old[g0], o1 = old[g1], f0 = rhs[g0], f1 = rhs[g1];
   double v0, v1;
   begin_box(phi, T, b, C, lane, v0, v1);
+  const double o0 = old[g0], o1 = old[g1], f0 = rhs[g0], f1 = rhs[g1];
   const bool refined = C.ref & 16;
   double *s = sm[wv_];
   if (refined) {
@@ -292,6 +300,7 @@ __global__ void __launch_bounds__(QT) k_q_prolong(int off, int n, int l, double 
   if (k_ >= n) return;
   const int b = off + k_, ncl = QN << (l - 1);
   load_ctx(T, b, C, lane);
+  q_wait();
   const int2 B = make_int2(C.ix, C.iy);
   auto cv = [&](int qx, int qy, int fx, int fy) {
     const double a = coarse_val(phi, C, qx, qy, fx, fy, ncl, bc, corr, false, err);
@@ -315,6 +324,7 @@ __global__ void k_q_coarse(double *__restrict__ phi, const double *__restrict__ 
   __shared__ double r[QC];
   const int c = threadIdx.x, i = c % QN, j = c / QN;
   const double wl = T.w[3 * i], wh = T.w[3 * i + 1];
+  q_wait();
   double l0 = 0.0;
   if (i == 0 && bc.type[0]) l0 += wl * bc.g2[0];
   if (i == QN - 1 && bc.type[1]) l0 += wh * bc.g2[1];
@@ -503,6 +513,7 @@ __global__ void __launch_bounds__(QT) k_q_cf_flux(int n, const double *__restric
   if (k_ >= n) return;
   const int b = k_;
   load_ctx(T, b, C, lane);
+  q_wait();
   if (C.ref & 16) return;
   bool any = false;
   for (int f = 0; f < 4; ++f) any |= C.nb[f] == -2;
@@ -529,6 +540,7 @@ __global__ void __launch_bounds__(QT) k_q_update(int n, const double *__restrict
   if (k_ >= n) return;
   const int b = k_;
   load_ctx(T, b, C, lane);
+  q_wait();
   if (C.ref & 16) return;
   const int l = C.lev;
   const double h = hs[l], ih = 1.0 / h;
@@ -581,6 +593,7 @@ __global__ void __launch_bounds__(QT) k_q_restrict(int off, int n, double *__res
   if (k_ >= n) return;
   const int b = off + k_;
   load_ctx(T, b, C, lane);
+  q_wait();
   if (lane >= 16) return;
   const int p = C.pn[4];
   const int2 B = make_int2(C.ix, C.iy);
@@ -675,7 +688,7 @@ struct sm_quad {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t vgraph[QMAXL] = {nullptr};
   long long vgraph_launches[QMAXL] = {0};
-  bool graphs = true;
+  bool graphs = true, pdl = true;
   ~sm_quad() {
     for (auto &g : vgraph)
       if (g) cudaGraphExecDestroy(g);
@@ -840,37 +853,51 @@ int check(sm_quad *q, const char *what) {
 
 int level_count(const sm_quad *q, int l) { return q->off[l + 1] - q->off[l]; }
 
+// launch with programmatic dependent launch (every kernel of this file
+// waits for its predecessor before reading a field)
+template <typename... KArgs, typename... Args>
+void qlaunch(sm_quad *q, void (*k)(KArgs...), int grid, int block, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = q->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = q->pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+  ++q->launches;
+}
+
 void smooth(sm_quad *q, int l, int nu) {
   const int n = level_count(q, l);
   for (int s = 0; s < nu; ++s)
     for (int c = 0; c < 2; ++c) {
-      k_q_rbgs<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, c, q->var[V_PHI], q->var[V_RHS], tabs(q),
-                                                   q->bc, q->h[l] * q->h[l], q->d_err);
-      ++q->launches;
+      qlaunch(q, k_q_rbgs, blocks_for(n), QT, q->off[l], n, l, c, q->var[V_PHI], (const double *)q->var[V_RHS],
+              tabs(q), q->bc, q->h[l] * q->h[l], q->d_err);
     }
 }
 
 void coarse_solve(sm_quad *q) {
-  k_q_coarse<<<1, QC, 0, q->stream>>>(q->var[V_PHI], q->var[V_RHS], q->ainv, tabs(q), q->bc, q->inv_h2[0]);
-  ++q->launches;
+  qlaunch(q, k_q_coarse, 1, QC, q->var[V_PHI], (const double *)q->var[V_RHS], (const double *)q->ainv, tabs(q),
+          q->bc, q->inv_h2[0]);
 }
 
 void vcycle(sm_quad *q, int top) {
   for (int l = top; l >= 1; --l) {
     smooth(q, l, q->nu1);
     const int n = level_count(q, l), nc = level_count(q, l - 1);
-    k_q_resid_restrict<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, q->var[V_PHI], q->var[V_RHS],
-                                                             q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l], q->d_err);
-    k_q_fas<<<blocks_for(nc), QT, 0, q->stream>>>(q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS],
-                                                   q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
-    q->launches += 2;
+    qlaunch(q, k_q_resid_restrict, blocks_for(n), QT, q->off[l], n, l, (const double *)q->var[V_PHI],
+            q->var[V_RHS], q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l], q->d_err);
+    qlaunch(q, k_q_fas, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS], q->var[V_OLD],
+            tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
   }
   coarse_solve(q);
   for (int l = 1; l <= top; ++l) {
     const int n = level_count(q, l);
-    k_q_prolong<<<blocks_for(n), QT, 0, q->stream>>>(q->off[l], n, l, q->var[V_PHI], q->var[V_OLD], 1, tabs(q),
-                                                      q->bc, q->d_err);
-    ++q->launches;
+    qlaunch(q, k_q_prolong, blocks_for(n), QT, q->off[l], n, l, q->var[V_PHI], (const double *)q->var[V_OLD], 1,
+            tabs(q), q->bc, q->d_err);
     smooth(q, l, q->nu2);
   }
 }
@@ -1389,6 +1416,13 @@ extern "C" int sm_quad_advance(sm_quad *q, double dt, double c, double eps, doub
 extern "C" int sm_quad_set_graphs(sm_quad *q, int on) {
   if (!q) return SM_EINVAL;
   q->graphs = on != 0;
+  return SM_OK;
+}
+
+extern "C" int sm_quad_set_pdl(sm_quad *q, int on) {
+  if (!q) return SM_EINVAL;
+  q->pdl = on != 0;
+  drop_graphs(q);
   return SM_OK;
 }
 

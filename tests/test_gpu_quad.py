@@ -228,18 +228,20 @@ def test_error_paths():
 
 
 def test_graph_and_host_paths_identical():
-    """V-cycles as CUDA graphs and the same launches from the host give the
-    same bits; the launch count is the same either way."""
+    """V-cycles as CUDA graphs or from the host, with or without programmatic
+    dependent launch, give the same bits and the same launch count."""
     p = pkg()
     out = []
-    for graphs in (True, False):
+    for graphs, pdl in ((True, True), (True, False), (False, True), (False, False)):
         dom, st = synth.workload2("axi_small")
         g = gpu_quad(dom, st)
         g.set_graphs(graphs)
+        g.set_pdl(pdl)
         o = quad.build_mesh(dom, st)
         load(dom, st, o, g)
         l0 = g.launch_count()
         rc, rel, cyc = g.fmg(1e-9, 40)
         out.append((cyc, rel, g.download(p.PHI), g.launch_count() - l0))
-    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and out[0][3] == out[1][3]
-    assert np.array_equal(out[0][2], out[1][2])
+    for o_ in out[1:]:
+        assert o_[0] == out[0][0] and o_[1] == out[0][1] and o_[3] == out[0][3]
+        assert np.array_equal(o_[2], out[0][2])
