@@ -856,7 +856,32 @@ def cpu_baseline():
     return {"value": round(1.0 / sec_all, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": "one FMG solve to 1e-8 of the %s workload (%d top-level V-cycles), "
                       "plain C oracle, OpenMP over boxes on %d threads" % (WORKLOAD, cyc, cores),
-            "single_thread": {"value": round(1.0 / sec_one, 5), "unit": "solves/s", "cores": 1}}
+            "single_thread": {"value": round(1.0 / sec_one, 5), "unit": "solves/s", "cores": 1},
+            "axisymmetric": cpu_baseline_axi()}
+
+
+def cpu_baseline_axi():
+    """The 2-D oracle on all host cores: one FMG solve to 1e-8 of the
+    axisymmetric workload (the GPU's axisymmetric line beside it)."""
+    import synth
+    from oracle import quad
+    dom, st = synth.workload2("axi_streamer")
+    o = quad.build_mesh(dom, st)
+    t = o.tables()
+    ne, ni = synth.streamer_densities2(dom, st, t["level"], t["ij"])
+    o.set(quad.NE, ne)
+    o.set(quad.NI, ni)
+    o.charge_rhs(synth.E_CHARGE, synth.EPS0)
+    cores = quad.set_threads(host_cores())
+    try:
+        t0 = time.perf_counter()
+        st_, rel, cyc = o.fmg(TOL, MAX_CYCLES)
+        sec = time.perf_counter() - t0
+    finally:
+        quad.set_threads(1)
+    return {"value": round(1.0 / sec, 4), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": "one FMG solve to 1e-8 of axi_streamer (%d V-cycles), plain C oracle "
+                      "(oracle/quad.c), OpenMP over boxes" % cyc}
 
 
 def run_reference(args):
