@@ -39,6 +39,18 @@ NO_PDL = False
 PERSIST = False
 
 
+# DRAM bytes (read + write) per k_rbgs launch, mean over the 72 colour passes
+# of one streamer6 V-cycle (the mix the roofline's achieved figure averages):
+#   python bench.py --mode vcycle --steps 1 --no-graphs &&
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:k_rbgs --csv --log-file rbgs_dram.csv \
+#       python bench.py --mode vcycle --steps 1 --no-graphs
+# 370.0 MB read, 0 written over 72 launches (cold caches between launches).
+RBGS_TRAFFIC_PER_LAUNCH = 5139556
+RBGS_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 72 k_rbgs launches of one "
+                     "V-cycle (cold caches): 1.05x the algorithmic bytes per launch")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,7 +401,9 @@ def run_gpu(args):
         # 1480 G FP64 instructions/s, above the 629 G/s of the FP64 pipe
         roof = {"bound": "alu", "achieved": round(ginstr, 2), "peak": FP64_PEAK_GINSTR,
                 "unit": "G FP64 instructions/s", "frac": round(ginstr / FP64_PEAK_GINSTR, 4),
-                "traffic": None, "kernel": "k_persist" if PERSIST else "k_rbgs", "launches": kn,
+                "traffic": None if PERSIST else RBGS_TRAFFIC_PER_LAUNCH,
+                "traffic_note": None if PERSIST else RBGS_TRAFFIC_NOTE,
+                "kernel": "k_persist" if PERSIST else "k_rbgs", "launches": kn,
                 "avg_launch_us": round(us, 3), "bytes_per_launch": round(kbytes),
                 "fp64_instr_per_launch": round(kflops),
                 "hbm": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",

@@ -750,6 +750,8 @@ __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols,
     const int x = C.y * CX + tx, ya = C.z * CY + ty2;
     unsigned long long m = 0;
     unsigned nzb = 0, em = 0;
+    // four planes per step: their loads are in flight together
+#pragma unroll 4
     for (int p = 0; p < N; ++p) {
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
