@@ -784,6 +784,8 @@ static double lookup(const q2 *o, int which, double e) {
   return t[i] + w * (t[i + 1] - t[i]);
 }
 
+double q2_lookup(const q2 *o, int which, double e) { return lookup(o, which, e); }
+
 /* psi(a/b) b of the Koren limiter, psi(x) = max(0, min(1, (2+x)/6, x))
  * (Eq. 7), in the division-free form */
 static double koren(double a, double b) {
@@ -966,4 +968,213 @@ int q2_advance(q2 *o, double dt, double q, double eps, double tol, int max_cycle
   int st2 = q2_solve(o, tol, max_cycles, nu1, nu2, NULL, cycles2);
   q2_compute_field(o);
   return st ? st : st2;
+}
+
+/* ---------------------------------------------------------------------- */
+/* refinement criterion and regridding (Sec. 2.5, Eq. 8) in two dimensions */
+/* ---------------------------------------------------------------------- */
+
+/* As in 3-D: a cell needs refinement where alpha(c1 |E|) dx >= c0 c1 (Eq. 8
+ * fails).  A leaf box is flagged +1 when one of its cells needs it, or a
+ * needing cell of a same-level leaf neighbour (one of the 8) lies within
+ * `buffer` cells of it (Chebyshev distance in cells of that level), and its
+ * level is below the maximum.  A leaf above the base grid that is not
+ * flagged is derefinable (-1) when every cell has alpha(c1 |E|) dx <
+ * c0_deref c1 and dx < dx_deref.  Uses the stored |E| of the leaf cells. */
+void q2_refine_flags(q2 *o, double c0, double c1, double c0_deref, double dx_deref, int buffer,
+                     int8_t *flags) {
+  unsigned char *need = calloc((size_t)64 * o->nbox, 1);
+  unsigned char *any = calloc((size_t)o->nbox, 1), *fine = calloc((size_t)o->nbox, 1);
+  for (int b = 0; b < o->nbox; ++b) {
+    flags[b] = 0;
+    if (!is_leaf(o, b)) continue;
+    double dx = spacing(o, o->lev[b]);
+    const double *em = box(o, V_EMAG, b);
+    int ok = dx < dx_deref;
+    for (int j = 0; j < NC; ++j)
+      for (int i = 0; i < NC; ++i) {
+        double a = lookup(o, 2, c1 * em[IX(i, j)]);
+        if (a * dx >= c0 * c1) {
+          need[(size_t)64 * b + i + 8 * j] = 1;
+          any[b] = 1;
+        }
+        if (!(a * dx < c0_deref * c1)) ok = 0;
+      }
+    fine[b] = (unsigned char)ok;
+  }
+  for (int b = 0; b < o->nbox; ++b) {
+    if (!is_leaf(o, b)) continue;
+    int marked = any[b];
+    for (int d = 0; d < 8 && !marked; ++d) {
+      int n = o->nbr[8 * b + d];
+      if (n < 0 || !is_leaf(o, n) || !any[n]) continue;
+      for (int c = 0; c < 64 && !marked; ++c) {
+        if (!need[(size_t)64 * n + c]) continue;
+        int g[2] = {o->ij[2 * n] * NC + (c & 7), o->ij[2 * n + 1] * NC + (c >> 3)};
+        int dist = 0;
+        for (int e = 0; e < 2; ++e) {
+          int lo = o->ij[2 * b + e] * NC, hi = lo + NC - 1;
+          int de = g[e] < lo ? lo - g[e] : (g[e] > hi ? g[e] - hi : 0);
+          if (de > dist) dist = de;
+        }
+        if (dist <= buffer) marked = 1;
+      }
+    }
+    if (marked) {
+      if (o->lev[b] < o->lmax) flags[b] = 1;
+    } else if (fine[b] && o->lev[b] > o->lbase) {
+      flags[b] = -1;
+    }
+  }
+  free(need);
+  free(any);
+  free(fine);
+}
+
+typedef struct {
+  int lev, i, j, src;
+  uint64_t key;
+} q2_ent;
+
+static int ent_cmp(const void *pa, const void *pb) {
+  const q2_ent *a = pa, *b = pb;
+  if (a->lev != b->lev) return a->lev < b->lev ? -1 : 1;
+  return a->key < b->key ? -1 : (a->key > b->key ? 1 : 0);
+}
+
+/* Apply per-box flags (+1 refine, -1 derefine, leaves only), as in 3-D:
+ * refinement of a flagged leaf below the maximum level when all 8 neighbour
+ * positions of its level hold a box or lie outside the domain, otherwise
+ * dropped; a box whose 4 children are all leaves flagged -1 loses them,
+ * unless a neighbour of one of the children (not a sibling) has children or
+ * is refined in this call.  Rebuilt in (level, Morton) order; kept boxes
+ * keep all their data; new children get the potential by the prolongation
+ * (2c + c_sx + c_sy)/4 of their parent's cells and the densities by the
+ * same prolongation limited to 2c (mirror ghosts at walls and the axis),
+ * every other variable zero.  Densities are restricted first. */
+int q2_regrid(q2 *o, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
+  restrict_densities(o, V_NE, V_NI);
+  int nb0 = o->nbox;
+  unsigned char *ref = calloc((size_t)nb0, 1), *der = calloc((size_t)nb0, 1);
+  int nref = 0, nder = 0, ndrop = 0;
+  for (int b = 0; b < nb0; ++b) {
+    if (!is_leaf(o, b) || flags[b] <= 0 || o->lev[b] >= o->lmax) continue;
+    int ok = 1;
+    for (int d = 0; d < 8; ++d)
+      if (o->nbr[8 * b + d] == -2) ok = 0;
+    if (ok) {
+      ref[b] = 1;
+      ++nref;
+    } else {
+      ++ndrop;
+    }
+  }
+  for (int p = 0; p < nb0; ++p) {
+    if (is_leaf(o, p)) continue;
+    int ok = 1;
+    for (int c = 0; c < 4 && ok; ++c) {
+      int ch = o->chl[4 * p + c];
+      if (!is_leaf(o, ch) || flags[ch] >= 0) ok = 0;
+    }
+    for (int c = 0; c < 4 && ok; ++c) {
+      int ch = o->chl[4 * p + c];
+      for (int d = 0; d < 8 && ok; ++d) {
+        int n = o->nbr[8 * ch + d];
+        if (n >= 0 && o->par[n] != p && (!is_leaf(o, n) || ref[n])) ok = 0;
+      }
+    }
+    if (ok) {
+      der[p] = 1;
+      ++nder;
+    }
+  }
+  int nnew = 0;
+  q2_ent *e = malloc(sizeof(q2_ent) * (size_t)(nb0 + 4 * nref));
+  double *pro = malloc(sizeof(double) * 3 * 64 * (size_t)(4 * nref + 1));
+  int npro = 0;
+  for (int b = 0; b < nb0; ++b) {
+    if (o->par[b] >= 0 && der[o->par[b]]) continue;
+    q2_ent x = {o->lev[b], o->ij[2 * b], o->ij[2 * b + 1], b, o->mort[b]};
+    e[nnew++] = x;
+    if (!ref[b]) continue;
+    int l = o->lev[b];
+    for (int c = 0; c < 4; ++c) {
+      int ci = 2 * o->ij[2 * b] + (c & 1), cj = 2 * o->ij[2 * b + 1] + (c >> 1);
+      q2_ent y = {l + 1, ci, cj, -1 - npro, morton2(ci, cj)};
+      e[nnew++] = y;
+      double *dst = pro + (size_t)3 * 64 * npro;
+      const int vars[3] = {V_PHI, V_NE, V_NI};
+      for (int v = 0; v < 3; ++v)
+        for (int jj = 0; jj < NC; ++jj)
+          for (int ii = 0; ii < NC; ++ii) {
+            int G[2] = {ci * NC + ii, cj * NC + jj};
+            int cc[2] = {G[0] >> 1, G[1] >> 1};
+            double cval = cell_val(o, vars[v], l, cc), sum = 2.0 * cval;
+            for (int a = 0; a < 2; ++a) {
+              int q[2] = {cc[0], cc[1]};
+              q[a] += (G[a] & 1) ? 1 : -1;
+              sum += v == 0 ? cell_val_bc(o, vars[v], l, q, cc, 0) : cell_val_mirror(o, vars[v], l, q, cc);
+            }
+            double val = 0.25 * sum;
+            if (v > 0 && val > 2.0 * cval) val = 2.0 * cval;
+            dst[(size_t)64 * v + ii + 8 * jj] = val;
+          }
+      ++npro;
+    }
+  }
+  qsort(e, (size_t)nnew, sizeof(q2_ent), ent_cmp);
+  int cap = o->cap > nnew ? o->cap : nnew;
+  int *lev = malloc(sizeof(int) * cap), *ij = malloc(sizeof(int) * 2 * cap);
+  int *par = malloc(sizeof(int) * cap), *chl = malloc(sizeof(int) * 4 * cap);
+  int *nbr = malloc(sizeof(int) * 8 * cap);
+  uint64_t *mort = malloc(sizeof(uint64_t) * cap);
+  double *nv[NVAR];
+  for (int v = 0; v < NVAR; ++v) nv[v] = calloc((size_t)BS * cap, sizeof(double));
+  for (int b = 0; b < nnew; ++b) {
+    lev[b] = e[b].lev;
+    ij[2 * b] = e[b].i;
+    ij[2 * b + 1] = e[b].j;
+    mort[b] = e[b].key;
+    if (e[b].src >= 0) {
+      for (int v = 0; v < NVAR; ++v)
+        memcpy(nv[v] + (size_t)BS * b, o->v[v] + (size_t)BS * e[b].src, sizeof(double) * BS);
+    } else {
+      const double *src = pro + (size_t)3 * 64 * (-1 - e[b].src);
+      const int vars[3] = {V_PHI, V_NE, V_NI};
+      for (int v = 0; v < 3; ++v)
+        for (int c = 0; c < 64; ++c) nv[vars[v]][(size_t)BS * b + IX(c & 7, c >> 3)] = src[(size_t)64 * v + c];
+    }
+  }
+  free(o->lev); free(o->ij); free(o->par); free(o->chl); free(o->nbr); free(o->mort);
+  for (int v = 0; v < NVAR; ++v) {
+    free(o->v[v]);
+    o->v[v] = nv[v];
+  }
+  o->lev = lev; o->ij = ij; o->par = par; o->chl = chl; o->nbr = nbr; o->mort = mort;
+  if (cap > o->cap) o->flux = realloc(o->flux, sizeof(double) * FPB * (size_t)cap);
+  o->cap = cap;
+  o->nbox = nnew;
+  int nlev = 0;
+  for (int b = 0; b < nnew; ++b)
+    if (lev[b] + 1 > nlev) nlev = lev[b] + 1;
+  o->nlev = nlev;
+  for (int l = 0, b = 0; l <= nlev; ++l) {
+    while (b < nnew && lev[b] < l) ++b;
+    o->off[l] = b;
+  }
+  for (int l = nlev + 1; l <= MAXL + 1; ++l) o->off[l] = nnew;
+  for (int b = 0; b < nnew; ++b) {
+    par[b] = lev[b] ? find_box(o, lev[b] - 1, ij[2 * b] >> 1, ij[2 * b + 1] >> 1) : -1;
+    for (int c = 0; c < 4; ++c)
+      chl[4 * b + c] = lev[b] + 1 < nlev ? find_box(o, lev[b] + 1, 2 * ij[2 * b] + (c & 1), 2 * ij[2 * b + 1] + (c >> 1))
+                                         : -2;
+    if (chl[4 * b] < 0)
+      for (int c = 0; c < 4; ++c) chl[4 * b + c] = -1;
+  }
+  for (int l = 0; l < nlev; ++l) set_neighbours(o, l);
+  free(e); free(pro); free(ref); free(der);
+  if (n_refined) *n_refined = nref;
+  if (n_derefined) *n_derefined = nder;
+  if (n_dropped) *n_dropped = ndrop;
+  return nref + nder;
 }

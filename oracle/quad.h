@@ -40,6 +40,7 @@ void q2_set(q2 *o, int var, const double *src);
 void q2_get(const q2 *o, int var, double *dst);
 void q2_set_table(q2 *o, int n, double e_max, const double *mu, const double *diff,
                   const double *alpha);
+double q2_lookup(const q2 *o, int which, double e);
 void q2_charge_rhs(q2 *o, double q, double eps, int use_rho);
 int q2_fmg(q2 *o, double tol, int max_cycles, int nu1, int nu2, double *rel, int *cycles);
 int q2_vcycles(q2 *o, int n, int nu1, int nu2, double *rel);
@@ -53,4 +54,7 @@ void q2_fluid_stage(q2 *o, double dt);
 int q2_advance(q2 *o, double dt, double q, double eps, double tol, int max_cycles, int nu1,
                int nu2, double *dt_next, int *cycles1, int *cycles2);
 void q2_coarse_solve(q2 *o);
+void q2_refine_flags(q2 *o, double c0, double c1, double c0_deref, double dx_deref, int buffer,
+                     int8_t *flags);
+int q2_regrid(q2 *o, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
 #endif

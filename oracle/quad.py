@@ -59,6 +59,9 @@ def _load():
             "q2_fluid_stage": ([P, D], None),
             "q2_advance": ([P, D, D, D, D, I, I, I, dp, ip, ip], I),
             "q2_coarse_solve": ([P], None),
+            "q2_refine_flags": ([P, D, D, D, D, I, P], None),
+            "q2_lookup": ([P, I, D], D),
+            "q2_regrid": ([P, P, ip, ip, ip], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -139,6 +142,20 @@ class Quad:
         self.dropped = dropped.value
         return r
 
+    def refine_flags(self, c0=1.0, c1=1.2, c0_deref=0.125, dx_deref=30e-6, buffer=3) -> np.ndarray:
+        """Per-box flags from the stored |E| (Eq. 8): +1 refine, -1 derefinable, 0."""
+        f = np.zeros(self.n_boxes, np.int8)
+        self._lib.q2_refine_flags(self._h, c0, c1, c0_deref, dx_deref, buffer, _ptr(f))
+        return f
+
+    def regrid(self, flags):
+        """Apply per-box flags; returns (refined, derefined, dropped)."""
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+        assert flags.shape == (self.n_boxes,)
+        r, d, x = C.c_int(0), C.c_int(0), C.c_int(0)
+        self._lib.q2_regrid(self._h, _ptr(flags), C.byref(r), C.byref(d), C.byref(x))
+        return r.value, d.value, x.value
+
     def set(self, var: int, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.n_boxes, 64)
         self._lib.q2_set(self._h, var, _ptr(a))
@@ -153,6 +170,9 @@ class Quad:
         dc = np.ascontiguousarray(tab["diff"], np.float64)
         al = np.ascontiguousarray(tab["alpha"], np.float64)
         self._lib.q2_set_table(self._h, len(mu), tab["e_max"], _ptr(mu), _ptr(dc), _ptr(al))
+
+    def lookup(self, which: int, e: float) -> float:
+        return self._lib.q2_lookup(self._h, which, e)
 
     def charge_rhs(self, q=1.0, eps=1.0, use_rho=False):
         self._lib.q2_charge_rhs(self._h, q, eps, int(use_rho))
