@@ -132,6 +132,32 @@ int sm_quad_fluid_stage(sm_quad *q, double dt);
 int sm_quad_advance(sm_quad *q, double dt, double charge, double eps, double tol, int max_cycles,
                     double *dt_next, int *cycles);
 
+/* Refinement criterion (Sec. 2.5, Eq. 8) per leaf box from the stored |E|,
+ * the rules of sm_refine_flags on the quadtree: +1 where a cell has
+ * alpha(c1 |E|) dx >= c0 c1 (alpha from the table, each operation rounded
+ * on its own) or a needing cell of a same-level leaf neighbour (one of the
+ * 8) lies within `buffer` cells (Chebyshev distance), below the maximum
+ * level; -1 for a leaf above the base grid whose cells all have
+ * alpha(c1 |E|) dx < c0_deref c1 and dx < dx_deref; 0 otherwise.
+ * flags: host int8 [n_boxes] out.  0 <= buffer <= 8.  Synchronises.
+ * Errors: SM_EINVAL, SM_ESTATE (no table). */
+int sm_quad_refine_flags(sm_quad *q, double c0, double c1, double c0_deref, double dx_deref, int buffer,
+                         int8_t *flags);
+/* Regrid with per-box flags (host int8 [n_boxes], leaves only; the layout
+ * of sm_quad_refine_flags), the rules of sm_regrid: densities restricted
+ * first; a +1 leaf below the maximum level gets 4 children when all 8
+ * neighbour positions of its level are covered or outside the domain (else
+ * dropped); a box whose 4 children are all -1 leaves loses them unless a
+ * non-sibling neighbour of a child has children or is refined in the same
+ * call.  Boxes are renumbered in (level, Morton) order; kept boxes keep phi,
+ * f, n_e, n_i, |E| and rho; new children get phi, n_e, n_i by the
+ * prolongation (2c + c_x + c_y)/4 of their parent's cells (wall ghosts for
+ * phi; mirrors and the 2c limit for densities), the rest zero.  Out (may be
+ * NULL): refined boxes, derefined boxes, dropped requests.  Synchronises.
+ * Errors: SM_EINVAL, SM_ENOMEM (past max_boxes; the mesh is unchanged),
+ * SM_ESTATE. */
+int sm_quad_regrid(sm_quad *q, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
+
 /* on != 0 (the default): each V-cycle runs as a CUDA graph, captured per
  * top level on first use and dropped when the mesh or the arena changes;
  * 0: the same launches are issued from the host.  Results are identical. */

@@ -74,7 +74,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_quad_refine_level", "sm_quad_get_tables", "sm_quad_var_ptr", "sm_quad_upload",
            "sm_quad_download", "sm_quad_set_table", "sm_quad_charge_rhs", "sm_quad_fmg",
            "sm_quad_solve", "sm_quad_vcycles", "sm_quad_compute_field", "sm_quad_dt_limit", "sm_quad_fluid_stage",
-           "sm_quad_advance", "sm_quad_set_graphs", "sm_quad_set_pdl", "sm_quad_launch_count", "sm_quad_last_error"]
+           "sm_quad_advance", "sm_quad_refine_flags", "sm_quad_regrid", "sm_quad_set_graphs", "sm_quad_set_pdl", "sm_quad_launch_count", "sm_quad_last_error"]
 
 
 def library_path() -> str:
@@ -168,6 +168,8 @@ def load():
         "sm_quad_dt_limit": [P, D, D, pD],
         "sm_quad_fluid_stage": [P, D],
         "sm_quad_advance": [P, D, D, D, D, I, pD, P],
+        "sm_quad_refine_flags": [P, D, D, D, D, I, P],
+        "sm_quad_regrid": [P, P, pI, pI, pI],
         "sm_quad_set_graphs": [P, I],
         "sm_quad_set_pdl": [P, I],
         "sm_quad_launch_count": [P, C.POINTER(C.c_longlong)],
@@ -768,6 +770,20 @@ class Quad:
         cyc = np.zeros(2, np.int32)
         rc = self._ck(self._lib.sm_quad_advance(self._h, dt, q, eps, tol, max_cycles, C.byref(dtn), _hp(cyc)))
         return rc, dtn.value, int(cyc[0]), int(cyc[1])
+
+    def refine_flags(self, c0=1.0, c1=1.2, c0_deref=0.125, dx_deref=30e-6, buffer=3) -> np.ndarray:
+        """Per-box flags from the stored |E| (Eq. 8): +1 refine, -1 derefinable, 0."""
+        f = np.zeros(self.n_boxes, np.int8)
+        self._ck(self._lib.sm_quad_refine_flags(self._h, c0, c1, c0_deref, dx_deref, int(buffer), _hp(f)))
+        return f
+
+    def regrid(self, flags):
+        """Apply per-box flags; returns (refined, derefined, dropped)."""
+        flags = np.ascontiguousarray(flags, dtype=np.int8)
+        assert flags.shape == (self.n_boxes,)
+        r, d, x = C.c_int(), C.c_int(), C.c_int()
+        self._ck(self._lib.sm_quad_regrid(self._h, _hp(flags), C.byref(r), C.byref(d), C.byref(x)))
+        return r.value, d.value, x.value
 
     def set_graphs(self, on: bool):
         self._ck(self._lib.sm_quad_set_graphs(self._h, int(bool(on))))

@@ -650,6 +650,103 @@ __global__ void k_q_average(long long n, double *__restrict__ a, const double *_
   if (g < n) a[g] = (b0[g] + b1[g]) / 2.0;
 }
 
+// alpha(e) from the table with every operation rounded on its own (no fused
+// multiply-add), the arithmetic of the refinement test on both sides
+__device__ __forceinline__ double alpha_rn(const double *__restrict__ t, int n, double de, double e) {
+  const double x = __ddiv_rn(e, de);
+  if (x <= 0.0) return t[0];
+  if (x >= (double)(n - 1)) return t[n - 1];
+  const int i = (int)x;
+  const double w = __dsub_rn(x, (double)i);
+  return __dadd_rn(t[i], __dmul_rn(w, __dsub_rn(t[i + 1], t[i])));
+}
+
+// Eq. 8 on every leaf box (one warp per box, cells lane and lane + 32):
+// need[b] bit c where alpha(c1 |E|) dx >= c0 c1; fine[b] = 1 when every cell
+// has alpha(c1 |E|) dx < c0_deref c1 and dx < dx_deref
+__global__ void __launch_bounds__(QT) k_q_refcrit(int n, const double *__restrict__ emag, QTabs T,
+                                                  const double *__restrict__ alpha, int tab_n, double de, double c1,
+                                                  double c0c1, double c0dc1, double dxd,
+                                                  const double *__restrict__ hs, unsigned long long *__restrict__ need,
+                                                  unsigned char *__restrict__ fine) {
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  load_ctx(T, b, C, lane);
+  q_wait();
+  if (C.ref & 16) {
+    if (lane == 0) {
+      need[b] = 0ull;
+      fine[b] = 0;
+    }
+    return;
+  }
+  const double dx = hs[C.lev];
+  bool nd[2], ok = true;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double ad = __dmul_rn(alpha_rn(alpha, tab_n, de, __dmul_rn(c1, emag[(size_t)b * QC + lane + 32 * h])), dx);
+    nd[h] = ad >= c0c1;
+    ok &= ad < c0dc1;
+  }
+  const unsigned lo = __ballot_sync(0xffffffffu, nd[0]), hi = __ballot_sync(0xffffffffu, nd[1]);
+  const bool all = __all_sync(0xffffffffu, ok);
+  if (lane == 0) {
+    need[b] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+    fine[b] = (unsigned char)(all && dx < dxd);
+  }
+}
+
+// After a regrid, box b of the new mesh takes the data of old box
+// rg[10 b] (>= 0) from the snapshot snap[var][old box][64] (vars: phi,
+// n_e, n_i, f, |E|, rho), or, as a new child (rg[10 b] < 0), the
+// prolongation (2c + c_x + c_y)/4 of its old parent's cells, rg[10 b + 1 ..
+// 9] being the old parent's 3x3 neighbourhood: wall ghosts for the
+// potential, mirrors and the 2c limit for the densities; f, |E| and rho of
+// new boxes are zero.
+__global__ void __launch_bounds__(QT) k_q_regrid_move(int n, const int *__restrict__ rg,
+                                                      const double *__restrict__ snap, size_t stride,
+                                                      double *__restrict__ phi, double *__restrict__ ne,
+                                                      double *__restrict__ ni, double *__restrict__ rhs,
+                                                      double *__restrict__ emag, double *__restrict__ rho, QTabs T,
+                                                      const __grid_constant__ QBc bc, unsigned *err) {
+  QWARP();
+  if (k_ >= n) return;
+  const int b = k_;
+  double *dst[6] = {phi, ne, ni, rhs, emag, rho};
+  const int src = rg[10 * (size_t)b];
+  if (src >= 0) {
+    for (int v = 0; v < 6; ++v)
+      for (int c = lane; c < QC; c += 32) dst[v][(size_t)b * QC + c] = snap[v * stride + (size_t)src * QC + c];
+    return;
+  }
+  if (lane < 9) C.pn[lane] = rg[10 * (size_t)b + 1 + lane];
+  if (lane == 9) {
+    const int2 v = T.ij[b];
+    C.ix = v.x;
+    C.iy = v.y;
+  }
+  if (lane == 10) C.lev = T.lev[b];
+  __syncwarp();
+  const int ncl = QN << (C.lev - 1);
+  for (int c = lane; c < QC; c += 32) {
+    const int Gx = C.ix * QN + c % QN, Gy = C.iy * QN + c / QN, cx = Gx >> 1, cy = Gy >> 1;
+    const int qx = cx + ((Gx & 1) ? 1 : -1), qy = cy + ((Gy & 1) ? 1 : -1);
+    for (int v = 0; v < 3; ++v) {
+      const double *sv = snap + v * stride;
+      const bool mirror = v > 0;
+      const double cv = coarse_val(sv, C, cx, cy, cx, cy, ncl, bc, 0, mirror, err);
+      double val = 2.0 * cv;
+      val += coarse_val(sv, C, qx, cy, cx, cy, ncl, bc, 0, mirror, err);
+      val += coarse_val(sv, C, cx, qy, cx, cy, ncl, bc, 0, mirror, err);
+      val = 0.25 * val;
+      if (mirror && val > 2.0 * cv) val = 2.0 * cv;
+      dst[v][(size_t)b * QC + c] = val;
+    }
+    for (int v = 3; v < 6; ++v) dst[v][(size_t)b * QC + c] = 0.0;
+  }
+}
+
 int blocks_for(long long boxes) { return (int)std::max<long long>(1, (boxes + WPB - 1) / WPB); }
 
 }  // namespace
@@ -679,6 +776,10 @@ struct sm_quad {
   double *cflux = nullptr, *ainv = nullptr, *lut = nullptr, *d_h = nullptr;
   unsigned long long *slots = nullptr;
   unsigned *d_err = nullptr;
+  double *snap = nullptr;                 // regrid snapshot [6][max_boxes][64]
+  int *d_rg = nullptr;                    // regrid move descriptors [max_boxes][10]
+  unsigned long long *d_need = nullptr;   // refinement test: cells that need refinement, per box
+  unsigned char *d_fine = nullptr;        // refinement test: derefinable, per box
   int lut_n = 0;
   double lut_emax = 0.0;
   double h[QMAXL], inv_h2[QMAXL];
@@ -1131,7 +1232,8 @@ extern "C" int sm_quad_destroy(sm_quad *q) {
 
 namespace {
 struct QLayout {
-  size_t lev, par, chl, nbr8, pn, ref, ij, w, wv, var[NV], cflux, ainv, lut, h, slots, err, total;
+  size_t lev, par, chl, nbr8, pn, ref, ij, w, wv, var[NV], cflux, ainv, lut, h, slots, err, snap, rg, need, fine,
+      total;
 };
 QLayout qlayout(const sm_quad *q) {
   QLayout L{};
@@ -1158,6 +1260,10 @@ QLayout qlayout(const sm_quad *q) {
   L.h = take(sizeof(double) * 3 * QMAXL);
   L.slots = take(sizeof(unsigned long long) * 8);
   L.err = take(sizeof(unsigned));
+  L.snap = take(sizeof(double) * 6 * QC * nb);
+  L.rg = take(sizeof(int) * 10 * nb);
+  L.need = take(sizeof(unsigned long long) * nb);
+  L.fine = take(nb);
   L.total = t;
   return L;
 }
@@ -1193,6 +1299,10 @@ extern "C" int sm_quad_bind_arena(sm_quad *q, void *dev_ptr, size_t bytes) {
   q->d_h = (double *)(a + L.h);
   q->slots = (unsigned long long *)(a + L.slots);
   q->d_err = (unsigned *)(a + L.err);
+  q->snap = (double *)(a + L.snap);
+  q->d_rg = (int *)(a + L.rg);
+  q->d_need = (unsigned long long *)(a + L.need);
+  q->d_fine = (unsigned char *)(a + L.fine);
   std::vector<double> hs(3 * QMAXL);
   for (int l = 0; l < QMAXL; ++l) {
     hs[l] = q->h[l];
@@ -1411,6 +1521,182 @@ extern "C" int sm_quad_advance(sm_quad *q, double dt, double c, double eps, doub
   }
   if (cudaStreamSynchronize(q->stream) != cudaSuccess) return qfail(q, SM_ECUDA, "advance");
   return st1 ? st1 : st2;
+}
+
+// Eq. 8 with buffer and derefinement flags (the rules of the 3-D form on
+// the quadtree): the per-cell test on the GPU, the buffer (same-level leaf
+// neighbours within `buffer` cells, Chebyshev distance) on the host from
+// the per-box masks
+extern "C" int sm_quad_refine_flags(sm_quad *q, double c0, double c1, double c0_deref, double dx_deref, int buffer,
+                                    int8_t *flags) {
+  if (!q || !flags || buffer < 0 || buffer > QN) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
+  const int n = n_boxes(q);
+  const double de = q->lut_emax / (q->lut_n - 1);
+  qlaunch(q, k_q_refcrit, blocks_for(n), QT, n, (const double *)q->var[V_EMAG], tabs(q),
+          (const double *)(q->lut + 2 * q->lut_n), q->lut_n, de, c1, c0 * c1, c0_deref * c1, dx_deref,
+          (const double *)q->d_h, q->d_need, q->d_fine);
+  std::vector<unsigned long long> need(n);
+  std::vector<unsigned char> fine(n);
+  if (cudaMemcpyAsync(need.data(), q->d_need, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, q->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(fine.data(), q->d_fine, n, cudaMemcpyDeviceToHost, q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "refinement test");
+  // cells of a neighbour in direction (dx, dy) within `buffer` cells of the box
+  auto axis_ok = [&](int d, int i) { return d < 0 ? i >= QN - buffer : (d > 0 ? i <= buffer - 1 : true); };
+  unsigned long long mask[8];
+  for (int dy = -1, k = 0; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (!dx && !dy) continue;
+      unsigned long long m = 0;
+      for (int c = 0; c < QC; ++c)
+        if (axis_ok(dx, c % QN) && axis_ok(dy, c / QN)) m |= 1ull << c;
+      mask[k++] = m;
+    }
+  for (int b = 0; b < n; ++b) {
+    flags[b] = 0;
+    if (q->chl[4 * b] >= 0) continue;
+    bool marked = need[b] != 0;
+    for (int d = 0; d < 8 && !marked; ++d) {
+      const int nb = q->nbr8[8 * b + d];
+      if (nb >= 0 && q->chl[4 * nb] < 0 && (need[nb] & mask[d])) marked = true;
+    }
+    if (marked) {
+      if (q->lev[b] < q->lmax) flags[b] = 1;
+    } else if (fine[b] && q->lev[b] > q->lbase) {
+      flags[b] = -1;
+    }
+  }
+  return SM_OK;
+}
+
+extern "C" int sm_quad_regrid(sm_quad *q, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
+  if (!q || !flags) return SM_EINVAL;
+  if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
+  const int nb0 = n_boxes(q);
+  restrict_all(q, V_NE);
+  restrict_all(q, V_NI);
+  auto leaf = [&](int b) { return q->chl[4 * b] < 0; };
+  std::vector<char> ref(nb0, 0), der(nb0, 0);
+  int nref = 0, nder = 0, ndrop = 0;
+  for (int b = 0; b < nb0; ++b) {
+    if (!leaf(b) || flags[b] <= 0 || q->lev[b] >= q->lmax) continue;
+    bool ok = true;
+    for (int d = 0; d < 8; ++d) ok &= q->nbr8[8 * b + d] != -2;
+    if (ok) {
+      ref[b] = 1;
+      ++nref;
+    } else {
+      ++ndrop;
+    }
+  }
+  for (int p = 0; p < nb0; ++p) {
+    if (leaf(p)) continue;
+    bool ok = true;
+    for (int c = 0; c < 4 && ok; ++c) {
+      const int ch = q->chl[4 * p + c];
+      if (!leaf(ch) || flags[ch] >= 0) ok = false;
+    }
+    for (int c = 0; c < 4 && ok; ++c) {
+      const int ch = q->chl[4 * p + c];
+      for (int d = 0; d < 8 && ok; ++d) {
+        const int nb = q->nbr8[8 * ch + d];
+        if (nb >= 0 && q->par[nb] != p && (!leaf(nb) || ref[nb])) ok = false;
+      }
+    }
+    if (ok) {
+      der[p] = 1;
+      ++nder;
+    }
+  }
+  struct Ent {
+    int lev, i, j, src, par;
+    uint64_t key;
+  };
+  std::vector<Ent> e;
+  e.reserve(nb0 + 4 * (size_t)nref);
+  for (int b = 0; b < nb0; ++b) {
+    if (q->par[b] >= 0 && der[q->par[b]]) continue;
+    e.push_back({q->lev[b], q->ix[b], q->iy[b], b, -1, q->mort[b]});
+    if (!ref[b]) continue;
+    for (int c = 0; c < 4; ++c) {
+      const int ci = 2 * q->ix[b] + (c & 1), cj = 2 * q->iy[b] + (c >> 1);
+      e.push_back({q->lev[b] + 1, ci, cj, -1, b, morton2(ci, cj)});
+    }
+  }
+  if ((long long)e.size() > q->max_boxes) return qfail(q, SM_ENOMEM, "box capacity exceeded");
+  std::sort(e.begin(), e.end(), [](const Ent &a, const Ent &b) {
+    return a.lev != b.lev ? a.lev < b.lev : a.key < b.key;
+  });
+  // the old parent neighbourhoods of the new children, from the old tables
+  const int nnew = (int)e.size();
+  std::vector<int> rg(10 * (size_t)nnew, -1);
+  for (int b = 0; b < nnew; ++b) {
+    rg[10 * (size_t)b] = e[b].src;
+    if (e[b].src >= 0) continue;
+    const int p = e[b].par;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        rg[10 * (size_t)b + 1 + (dx + 1) + 3 * (dy + 1)] = (dx || dy) ? q->nbr8[8 * p + dir8h(dx, dy)] : p;
+  }
+  // snapshot of the old fields (the move writes the same arrays)
+  const int vars[6] = {V_PHI, V_NE, V_NI, V_RHS, V_EMAG, V_RHO};
+  const size_t stride = (size_t)q->max_boxes * QC;
+  for (int v = 0; v < 6; ++v)
+    if (cudaMemcpyAsync(q->snap + v * stride, q->var[vars[v]], sizeof(double) * QC * (size_t)nb0,
+                        cudaMemcpyDeviceToDevice, q->stream) != cudaSuccess)
+      return qfail(q, SM_ECUDA, "regrid snapshot");
+  // the new mesh, in (level, Morton) order
+  q->lev.clear();
+  q->ix.clear();
+  q->iy.clear();
+  q->par.clear();
+  q->chl.clear();
+  q->nbr8.clear();
+  q->mort.clear();
+  q->w.clear();
+  q->wv.clear();
+  for (const Ent &x : e) add_box(q, x.lev, x.i, x.j, -1);
+  int nlev = 0;
+  for (const Ent &x : e) nlev = std::max(nlev, x.lev + 1);
+  q->nlev = nlev;
+  for (int l = 0, b = 0; l <= nlev; ++l) {
+    while (b < nnew && q->lev[b] < l) ++b;
+    q->off[l] = b;
+  }
+  for (int l = nlev + 1; l <= QMAXL + 1; ++l) q->off[l] = nnew;
+  for (int b = 0; b < nnew; ++b) {
+    const int l = q->lev[b];
+    q->par[b] = l ? find_box(q, l - 1, q->ix[b] >> 1, q->iy[b] >> 1) : -1;
+    bool kids = l + 1 < nlev;
+    for (int c = 0; c < 4 && kids; ++c) {
+      const int ch = find_box(q, l + 1, 2 * q->ix[b] + (c & 1), 2 * q->iy[b] + (c >> 1));
+      if (ch < 0) kids = false;
+      else q->chl[4 * b + c] = ch;
+    }
+    if (!kids)
+      for (int c = 0; c < 4; ++c) q->chl[4 * b + c] = -1;
+  }
+  for (int l = 0; l < nlev; ++l) set_neighbours(q, l);
+  drop_graphs(q);
+  if (cudaMemcpyAsync(q->d_rg, rg.data(), sizeof(int) * rg.size(), cudaMemcpyHostToDevice, q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "regrid descriptors");
+  if (int st = upload_tables(q)) return st;
+  k_q_regrid_move<<<blocks_for(nnew), QT, 0, q->stream>>>(nnew, q->d_rg, q->snap, stride, q->var[V_PHI],
+                                                           q->var[V_NE], q->var[V_NI], q->var[V_RHS],
+                                                           q->var[V_EMAG], q->var[V_RHO], tabs(q), q->bc, q->d_err);
+  ++q->launches;
+  unsigned ev = 0;
+  if (cudaMemcpyAsync(&ev, q->d_err, sizeof(ev), cudaMemcpyDeviceToHost, q->stream) != cudaSuccess ||
+      cudaStreamSynchronize(q->stream) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "regrid move");
+  if (ev) return qfail(q, SM_ESTATE, "a coarse box needed by the regrid prolongation is missing");
+  if (n_refined) *n_refined = nref;
+  if (n_derefined) *n_derefined = nder;
+  if (n_dropped) *n_dropped = ndrop;
+  return SM_OK;
 }
 
 extern "C" int sm_quad_set_graphs(sm_quad *q, int on) {

@@ -245,3 +245,90 @@ def test_graph_and_host_paths_identical():
     for o_ in out[1:]:
         assert o_[0] == out[0][0] and o_[1] == out[0][1] and o_[3] == out[0][3]
         assert np.array_equal(o_[2], out[0][2])
+
+
+# ---- refinement criterion and regridding (Sec. 2.5, Eq. 8) ----
+def tip_field(dom, t, centre=(4e-3, 5e-3), e_peak=2e7, e_bg=1.5e6, sigma=1.5e-3):
+    x, y = synth.cell_centres2(dom, t["level"], t["ij"])
+    return e_bg + e_peak * np.exp(-((x - centre[0]) ** 2 + (y - centre[1]) ** 2) / (2 * sigma ** 2))
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_refine_flags_bit_exact(name):
+    """The same |E| on both sides: flags agree entry by entry, with and
+    without the buffer, with derefinements."""
+    p = pkg()
+    dom, st, o, g = pair(name)
+    load(dom, st, o, g)
+    em = tip_field(dom, o.tables())
+    o.set(quad.EMAG, em)
+    g.upload(p.EMAG, em)
+    for args in ((1.0, 1.2, 0.125, 30e-6, 3), (1.0, 1.2, 0.125, 30e-6, 0), (1.0, 1.2, 0.125, 1.0, 3),
+                 (0.05, 1.2, 0.125, 1.0, 8)):
+        fo, fg = o.refine_flags(*args), g.refine_flags(*args)
+        assert np.array_equal(fo, fg), args
+    assert (fo == 1).sum() > 0 and (fo == -1).sum() > 0
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_regrid_parity(name):
+    """The oracle's flags applied on both sides: tables bit-exact, kept and
+    prolonged data equal, then FMG on the new mesh agrees."""
+    p = pkg()
+    dom, st, o, g = pair(name)
+    load(dom, st, o, g)
+    t = o.tables()
+    x, y = synth.cell_centres2(dom, t["level"], t["ij"])
+    phi = dom.bc_val[3] * y / dom.length + 50.0 * np.sin(x * 400.0)
+    for side, var in ((o, quad.PHI), (g, p.PHI)):
+        (side.set if side is o else side.upload)(var, phi)
+    em = tip_field(dom, t)
+    o.set(quad.EMAG, em)
+    g.upload(p.EMAG, em)
+    f = o.refine_flags(1.0, 1.2, 0.125, 1.0, 3)
+    ro, rg = o.regrid(f), g.regrid(f)
+    assert ro == rg and ro[0] > 0 and ro[1] > 0 and ro[2] > 0, (ro, rg)
+    to, tg = o.tables(), g.tables()
+    for k in ("level", "ij", "morton", "parent", "child", "nbr", "level_offset"):
+        assert np.array_equal(to[k], tg[k]), k
+    for vo, vg in ((quad.PHI, p.PHI), (quad.NE, p.NE), (quad.NI, p.NI)):
+        assert rel_err(g.download(vg), o.get(vo)) <= TOL, vo
+    o.charge_rhs(Q, EPS0)
+    g.charge_rhs(Q, EPS0)
+    so, sg = o.fmg(1e-8, 40), g.fmg(1e-8, 40)
+    assert so[2] == sg[2]
+    assert rel_err(g.download(p.PHI), o.get(quad.PHI)) <= TOL
+
+
+@pytest.mark.parametrize("name,c0,dxd", [("axi_small", 0.005, 1.0), ("cart_small", 0.05, 30e-6)])
+def test_adaptive_step_parity(name, c0, dxd):
+    """Solve, field, flags from each side's own field (a stricter c0 than
+    the paper's, so that these small meshes refine), regrid, solve and one
+    Heun step on the new mesh."""
+    p = pkg()
+    dom, st, o, g = pair(name)
+    t = load(dom, st, o, g)
+    o.fmg(1e-8, 40)
+    g.fmg(1e-8, 40)
+    o.compute_field()
+    g.compute_field()
+    fo, fg = o.refine_flags(c0, 1.2, 0.125, dxd, 3), g.refine_flags(c0, 1.2, 0.125, dxd, 3)
+    assert np.array_equal(fo, fg)
+    ro, rg = o.regrid(fo), g.regrid(fg)
+    assert ro == rg and ro[0] > 0
+    to, tg = o.tables(), g.tables()
+    for k in ("level", "ij", "child", "nbr"):
+        assert np.array_equal(to[k], tg[k]), k
+    o.charge_rhs(Q, EPS0)
+    g.charge_rhs(Q, EPS0)
+    so, sg = o.fmg(1e-8, 40), g.fmg(1e-8, 40)
+    assert so[2] == sg[2]
+    o.compute_field()
+    g.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+    assert g.dt_limit(Q, EPS0) == pytest.approx(dt, rel=TOL)
+    ao, ag = o.advance(dt, Q, EPS0, 1e-8, 40), g.advance(dt, Q, EPS0, 1e-8, 40)
+    assert ao[2:] == ag[2:]
+    leaf = to["child"][:, 0] < 0
+    for vo, vg in ((quad.NE, p.NE), (quad.PHI, p.PHI)):
+        assert rel_err(g.download(vg)[leaf], o.get(vo)[leaf]) <= TOL, vo
