@@ -673,6 +673,28 @@ def bench_axisymmetric(args, dev, world):
     lv = (g.launch_count() - lv) // 10
     leaf_cells = int((t["child"][:, 0] < 0).sum()) * 64
     all_cells = len(t["level"]) * 64
+    # refinement criterion (Eq. 8) with the paper's constants, then a regrid
+    # with a stricter c0 that changes the mesh (CUDA events around each)
+    g.compute_field()
+
+    def timed_ms(fn):
+        torch.cuda.synchronize()
+        a_, b_ = events()
+        a_.record(stream)
+        out = fn()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        return a_.elapsed_time(b_), out
+
+    g.refine_flags()
+    fl_ms, flags = timed_ms(lambda: g.refine_flags())
+    strict = g.refine_flags(0.25, 1.2, 0.125, 30e-6, 3)
+    nb0 = g.n_boxes
+    rg_ms, (nref, nder, ndrop) = timed_ms(lambda: g.regrid(strict))
+    regrid = {"flags_ms": round(fl_ms, 3), "paper_flags": {"refine": int((flags == 1).sum()),
+                                                            "derefine": int((flags == -1).sum())},
+              "regrid_ms": round(rg_ms, 3), "boxes": [nb0, g.n_boxes], "refined": nref, "derefined": nder,
+              "dropped": ndrop, "criterion": "c0=0.25 (paper: 1), c1=1.2, buffer 3"}
     res = {"value": round(whole_job_rate(SOLVES_PER_STEP * n, world, total), 3), "unit": "solves/s",
            "ms_per_step": round(total / n, 4), "vcycles_per_step": cycles / n, "gpu_launches": launches,
            "vcycle_us": round(vus, 2), "launches_per_vcycle": int(lv),
@@ -681,7 +703,7 @@ def bench_axisymmetric(args, dev, world):
            "leaf_cells": leaf_cells, "levels": int(len(t["level_offset"]) - 1), "tol": TOL,
            "dtype": "f64", "l2": "flushed between steps",
            "note": "per-level launches, each V-cycle a CUDA graph (one per top level), one residual "
-                   "read per V-cycle"}
+                   "read per V-cycle", "regrid": regrid}
     g.close()
     return res
 
