@@ -840,7 +840,7 @@ def bench_batch(args, dev, world):
            "workload": "256 unit-cube solves, sides 8*round(32*4^u/8), phi=0/1 on z plates",
            "kernels": kern,
            "kernels_note": "CUDA events around 10 back-to-back launches over all 256 solves; bytes = "
-                           "compulsory traffic (sweep 12 B, outer 20 B + 1 FP64 instr, prolong/restrict "
+                           "compulsory traffic (sweep 12 B, outer 20 B + 2 FP64-pipe instr, prolong/restrict "
                            "8.5 B per fine cell); hbm peak %.1f GB/s measured, FP64 peak %.0f G instr/s"
                            % (hbm, FP64_PEAK_GINSTR)}
     b.close()

@@ -488,14 +488,13 @@ int sm_box_solve_noalloc(double length, int n_problems, const int32_t *bc_type, 
  * entry point compares both ways against the hardware on n seeded bit
  * patterns (SplitMix64 of seed + i; three quarters of them with exponents
  * at the edges of the FP32 range and fractions at the rounding boundary).
- * It also checks the int64 -> FP64 conversion (round to nearest even)
- * against the hardware, and the FP64 -> 64-bit fixed-point map of the
- * batched residual (nearest multiple of 2^(E-1080), ties away from zero)
- * against exact FP64 scaling, for E from the value's exponent to +70.
- *   d_scratch:  DEVICE uint64 [4], overwritten.
- *   mismatches: HOST uint64 [4] out: FP64->FP32, FP32->FP64, int64->FP64
- *               and FP64->fixed patterns whose result differs from the
- *               reference (NaN = NaN).
+ * It also checks the FP64 -> 64-bit fixed-point map of the batched
+ * residual (nearest multiple of 2^(E-1080), ties away from zero) against
+ * exact FP64 scaling, for E from the value's exponent to +70.
+ *   d_scratch:  DEVICE uint64 [3], overwritten.
+ *   mismatches: HOST uint64 [3] out: FP64->FP32, FP32->FP64 and FP64->fixed
+ *               patterns whose result differs from the reference (NaN =
+ *               NaN).
  * Synchronises the stream.  Errors: SM_EINVAL (n < 0, null pointer),
  * SM_ECUDA. */
 int sm_check_conversions(long long n, unsigned long long seed, unsigned long long *d_scratch,

@@ -188,14 +188,14 @@ def _hp(a: np.ndarray):
 
 
 def check_conversions(n: int, seed: int = 0x5EED):
-    """Mismatches (FP64->FP32, FP32->FP64, int64->FP64, FP64->fixed point)
-    of the library's integer-pipe conversions on n seeded bit patterns: the
-    first three against the hardware conversions, the fixed-point one
-    against exact FP64 scaling with the tie rule."""
+    """Mismatches (FP64->FP32, FP32->FP64, FP64->fixed point) of the
+    library's integer-pipe conversions on n seeded bit patterns: the first
+    two against the hardware conversions, the fixed-point one against exact
+    FP64 scaling with the tie rule."""
     import torch
     lib = load()
-    scratch = torch.zeros(4, dtype=torch.int64, device="cuda")
-    out = np.zeros(4, np.uint64)
+    scratch = torch.zeros(3, dtype=torch.int64, device="cuda")
+    out = np.zeros(3, np.uint64)
     stream = torch.cuda.current_stream()
     rc = lib.sm_check_conversions(int(n), int(seed), C.c_void_p(scratch.data_ptr()), _hp(out),
                                   C.c_void_p(stream.cuda_stream))

@@ -547,7 +547,8 @@ __global__ void __launch_bounds__(512) k_bt_coarse(const int *__restrict__ solve
 // bounds the exponent fields of the solve's potential (emax, raised by every
 // kernel that writes phi) and of the Dirichlet wall values 2g; the sum of
 // the integers then has no rounding at all.  r = f - S 2^(E-1080) h^-2 is
-// one FMA after S is rounded to binary64.  The error of r is at most
+// one FMA after S is rounded to binary64 (the hardware conversion, which
+// measured faster here than the same rounding on the integer pipe).  The error of r is at most
 // 6.5 2^(E-1080) h^-2 (the twelve mapped values) plus two roundings, below
 // that of the plain FP64 sum (five additions and a multiply-add rounding at
 // 2^-53 of values up to 2^(E-1022)), and the FP64 pipe does one operation
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
         const long long zm = p == 0 ? wallv(4, c) : pm[q];
         const long long zp = p == N - 1 ? wallv(5, c) : pp[q];
         const long long sx = ((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c;  // exact
-        const double r = fma(-__longlong_as_double((long long)bits_of_s64_rn(sx)), kk, o ? f1 : f0);
+        const double r = fma(-__ll2double_rn(sx), kk, o ? f1 : f0);
         const unsigned long long rb = finite ? (unsigned long long)__double_as_longlong(r) : 0x7ff8000000000000ull;
         f32[o32 + p * NN + row0 + o * N] = cvt_bits_f32_rn(rb);
         const unsigned long long a = rb & 0x7fffffffffffffffull;
@@ -1482,8 +1483,8 @@ extern "C" int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult,
 // Time one kernel class over all solves (every solve active), CUDA events
 // on the batch stream around `reps` back-to-back launches.  Classes:
 // 0 level-0 sweep (e read, f read, e written: 12 B per cell), 1 outer
-// residual (phi and f read, FP32 rhs written: 20 B and one FP64 operation
-// per cell, the stencil sum in fixed point on the integer pipe; the
+// residual (phi and f read, FP32 rhs written: 20 B and two FP64-pipe
+// operations per cell, the stencil sum in fixed point on the integer pipe; the
 // exponent bounds are first taken from the stored potential, untimed),
 // 2 level-0 prolongation (fine e read and written, coarse e
 // read: 8.5 B per fine cell), 3 level-0 -> 1 restriction (fine e and f
@@ -1546,7 +1547,7 @@ extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *
   const double per_cell[4] = {12.0, 20.0, 8.5, 8.5};
   if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
   if (bytes_per_launch) *bytes_per_launch = per_cell[kclass] * cells;
-  if (fp64_per_launch) *fp64_per_launch = kclass == 1 ? 1.0 * cells : 0.0;
+  if (fp64_per_launch) *fp64_per_launch = kclass == 1 ? 2.0 * cells : 0.0;  // the FMA and the int64 conversion
   b->n_launch += reps + 1;
   return cudaGetLastError() == cudaSuccess ? SM_OK : bfail(b, SM_ECUDA, "kernel bench launch");
 }

@@ -283,22 +283,6 @@ __device__ __forceinline__ long long fix_of_bits(unsigned long long b, int E) {
   return (long long)((hi >> 31) ? 0ull - u : u);
 }
 
-// signed 64-bit integer -> binary64 bit pattern, round to nearest, ties to
-// even: the magnitude is normalised to bit 63, its top 53 bits form the
-// significand and the 11 dropped bits round it; a carry out of the
-// significand lands in the exponent field, which is then correct
-__device__ __forceinline__ unsigned long long bits_of_s64_rn(long long v) {
-  if (v == 0) return 0ull;
-  const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const int lz = __clzll((long long)u);
-  u <<= lz;
-  const unsigned long long rest = u & 0x7ffull;
-  unsigned long long r = sgn | (((unsigned long long)(1085 - lz) << 52) + (u >> 11));
-  r += (rest > 0x400ull || (rest == 0x400ull && (u & 0x800ull))) ? 1ull : 0ull;
-  return r;
-}
-
 // biased exponent field of a binary64 value (0 for zero and subnormals,
 // 0x7ff for infinities and NaNs)
 __device__ __forceinline__ unsigned expo_of(double d) {
