@@ -54,7 +54,7 @@ RBGS_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean ove
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -136,10 +136,13 @@ class Clocks:
         self.p = None
 
     def start(self):
+        """Start sampling every 100 ms; returns once the first sample (taken
+        before the region, and left out) has arrived."""
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.p.stdout.readline()
         except OSError:
             self.p = None
 
