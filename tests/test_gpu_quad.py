@@ -332,3 +332,33 @@ def test_adaptive_step_parity(name, c0, dxd):
     leaf = to["child"][:, 0] < 0
     for vo, vg in ((quad.NE, p.NE), (quad.PHI, p.PHI)):
         assert rel_err(g.download(vg)[leaf], o.get(vo)[leaf]) <= TOL, vo
+
+
+def test_regrid_capacity_and_argument_errors():
+    """A regrid past max_boxes fails with SM_ENOMEM and leaves the mesh as it
+    was; a buffer outside 0..8 is rejected; a refinement with no flags adds
+    nothing."""
+    p = pkg()
+    dom, st = synth.workload2("axi_small")
+    o = quad.build_mesh(dom, st)
+    n0 = o.n_boxes
+    g = gpu_quad(dom, st, max_boxes=n0 + 3)          # room for less than one refinement
+    load(dom, st, o, g)
+    t0 = g.tables()
+    em = tip_field(dom, t0)
+    g.upload(p.EMAG, em)
+    f = g.refine_flags(1.0, 1.2, 0.125, 30e-6, 3)
+    assert (f == 1).sum() > 0
+    with pytest.raises(p.SmError) as ei:
+        g.regrid(f)
+    assert ei.value.code == p.SM_ENOMEM
+    t1 = g.tables()
+    for k in ("level", "ij", "child", "nbr", "level_offset"):
+        assert np.array_equal(t0[k], t1[k]), k
+    for bad in (-1, 9):
+        with pytest.raises(p.SmError) as ei:
+            g.refine_flags(1.0, 1.2, 0.125, 30e-6, bad)
+        assert ei.value.code == p.SM_EINVAL
+    g2 = gpu_quad(synth.Domain2(1.0, 2, 2, synth.CARTESIAN))
+    assert g2.refine_level(1, np.zeros(4, np.int8)) == 0
+    assert g2.n_boxes == 5 and g2.n_levels == 2
