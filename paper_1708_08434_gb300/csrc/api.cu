@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "sm_internal.cuh"
+#include "sm_nvtx.h"
 
 using namespace sm;
 
@@ -403,6 +404,7 @@ int sm_build_neighbours(sm_ctx *ctx, int l) {
 }
 
 extern "C" int sm_build_octree(sm_ctx *ctx, int *n_boxes) {
+  SM_RANGE();
   if (!ctx) return SM_EINVAL;
   if (!ctx->arena) return sm_fail(ctx, SM_ESTATE, "no arena bound");
   LevelOffsets lo;
@@ -436,6 +438,7 @@ extern "C" int sm_build_octree(sm_ctx *ctx, int *n_boxes) {
 }
 
 extern "C" int sm_refine_level(sm_ctx *ctx, int level, const int8_t *flags, int *n_new, int *n_dropped) {
+  SM_RANGE();
   if (!ctx || !flags) return SM_EINVAL;
   if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
   if (level != ctx->n_levels - 1 || level >= ctx->lmax)

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "sm_internal.cuh"
+#include "sm_nvtx.h"
 
 using namespace sm;
 
@@ -1417,6 +1418,7 @@ static int run(sm_batch *b, double tol, int max_cycles, int *iterations) {
 }
 
 extern "C" int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycles, double *rel_res) {
+  SM_RANGE();
   if (!b || max_cycles < 1) return SM_EINVAL;
   if (!b->arena) return bfail(b, SM_ESTATE, "no arena bound");
   int it = 0;
@@ -1440,6 +1442,7 @@ extern "C" int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycl
 // `iters` corrections (CUDA events around the graph launch) from phi = 0
 // and keep the fastest; phi is left at zero.
 extern "C" int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult, double *best_ms) {
+  SM_RANGE();
   if (!b || iters < 1) return SM_EINVAL;
   if (!b->arena) return bfail(b, SM_ESTATE, "no arena bound");
   cudaEvent_t e0, e1;

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "sm_internal.cuh"
+#include "sm_nvtx.h"
 
 using namespace sm;
 
@@ -610,6 +611,7 @@ extern "C" int sm_cnn_get_params(sm_cnn *c, float *host, int n) {
 // on upload); out [n][512] and optional per-layer activations of the first
 // min(n, 16) boxes ([n][4][16][512]: z1, a1, z2, a2)
 extern "C" int sm_cnn_forward(sm_cnn *c, const float *x_host, int n, float *out_host, float *acts_host) {
+  SM_RANGE();
   if (!c || !x_host || !out_host || n < 1 || n > c->max_boxes || !c->arena) return SM_EINVAL;
   std::vector<bf16> xb((size_t)n * NPOS * 2);
   for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(x_host[i]);
@@ -686,6 +688,7 @@ static uint64_t splitmix(uint64_t x) {
 // sample order of each epoch is a seeded shuffle (SplitMix64 keys).
 // Out: mean loss of the last epoch.
 extern "C" int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned long long seed, float *loss) {
+  SM_RANGE();
   if (!c || epochs < 1 || batch < 1 || !c->arena) return SM_EINVAL;
   if (c->n_samples < 1) return cfail(c, SM_ESTATE, "no recorded samples");
   int n = c->n_samples;

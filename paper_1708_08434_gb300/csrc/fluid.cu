@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include "sm_internal.cuh"
+#include "sm_nvtx.h"
 
 using namespace sm;
 
@@ -418,6 +419,7 @@ static int ready(sm_ctx *ctx) {
 }
 
 extern "C" int sm_compute_field(sm_ctx *ctx) {
+  SM_RANGE();
   int st = ready(ctx);
   if (st) return st;
   if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
@@ -461,6 +463,7 @@ static int dt_from_slots(sm_ctx *ctx, double q, double eps, double *dt) {
 }
 
 extern "C" int sm_dt_limit(sm_ctx *ctx, double q, double eps, double *dt) {
+  SM_RANGE();
   int st = ready(ctx);
   if (st) return st;
   if (!dt || ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");
@@ -496,6 +499,7 @@ static int stage(sm_ctx *ctx, int s, int d, int h0, double dt, double q, double 
 }
 
 extern "C" int sm_fluid_stage(sm_ctx *ctx, double dt) {
+  SM_RANGE();
   int st = ready(ctx);
   if (st) return st;
   if (ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");
@@ -510,6 +514,7 @@ extern "C" int sm_fluid_stage(sm_ctx *ctx, double dt) {
 
 extern "C" int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol, int max_cycles,
                                 double *dt_next, int *cycles) {
+  SM_RANGE();
   int st = ready(ctx);
   if (st) return st;
   if (ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include "sm_internal.cuh"
+#include "sm_nvtx.h"
 
 using namespace sm;
 
@@ -1484,6 +1485,7 @@ extern "C" int sm_fill_ghosts(sm_ctx *ctx, int var, int level) {
 }
 
 extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
+  SM_RANGE();
   int st = check_ready(ctx);
   if (st) return st;
   if (n_cycles < 0) return SM_EINVAL;
@@ -1498,6 +1500,7 @@ extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
 }
 
 extern "C" int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res) {
+  SM_RANGE();
   int st = check_ready(ctx);
   if (st) return st;
   if (max_cycles < 1) return SM_EINVAL;
@@ -1505,6 +1508,7 @@ extern "C" int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles,
 }
 
 extern "C" int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res) {
+  SM_RANGE();
   int st = check_ready(ctx);
   if (st) return st;
   if (max_cycles < 1) return SM_EINVAL;

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "sm_quad.h"
+#include "sm_nvtx.h"
 
 namespace {
 
@@ -1319,6 +1320,7 @@ extern "C" int sm_quad_bind_arena(sm_quad *q, void *dev_ptr, size_t bytes) {
 }
 
 extern "C" int sm_quad_refine_level(sm_quad *q, int level, const int8_t *flags, int *n_new, int *n_dropped) {
+  SM_RANGE();
   if (!q || !flags) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   if (level != q->nlev - 1 || level >= q->lmax) return qfail(q, SM_ESTATE, "not the finest refinable level");
@@ -1429,6 +1431,7 @@ extern "C" int sm_quad_charge_rhs(sm_quad *q, double c, double eps, int use_rho)
 }
 
 extern "C" int sm_quad_fmg(sm_quad *q, double tol, int max_cycles, int *cycles, double *rel) {
+  SM_RANGE();
   if (!q || max_cycles < 1 || !(tol >= 0.0)) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   const int top = q->nlev - 1;
@@ -1446,12 +1449,14 @@ extern "C" int sm_quad_fmg(sm_quad *q, double tol, int max_cycles, int *cycles, 
 }
 
 extern "C" int sm_quad_solve(sm_quad *q, double tol, int max_cycles, int *cycles, double *rel) {
+  SM_RANGE();
   if (!q || max_cycles < 1 || !(tol >= 0.0)) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   return solve_loop(q, tol, max_cycles, 0, cycles, rel);
 }
 
 extern "C" int sm_quad_vcycles(sm_quad *q, int n) {
+  SM_RANGE();
   if (!q || n < 0) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   for (int c = 0; c < n; ++c)
@@ -1460,12 +1465,14 @@ extern "C" int sm_quad_vcycles(sm_quad *q, int n) {
 }
 
 extern "C" int sm_quad_compute_field(sm_quad *q) {
+  SM_RANGE();
   if (!q) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   return field(q);
 }
 
 extern "C" int sm_quad_dt_limit(sm_quad *q, double c, double eps, double *dt) {
+  SM_RANGE();
   if (!q || !dt || !(eps > 0.0)) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
@@ -1473,6 +1480,7 @@ extern "C" int sm_quad_dt_limit(sm_quad *q, double c, double eps, double *dt) {
 }
 
 extern "C" int sm_quad_fluid_stage(sm_quad *q, double dt) {
+  SM_RANGE();
   if (!q) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
@@ -1488,6 +1496,7 @@ extern "C" int sm_quad_fluid_stage(sm_quad *q, double dt) {
 
 extern "C" int sm_quad_advance(sm_quad *q, double dt, double c, double eps, double tol, int max_cycles,
                                double *dt_next, int *cycles) {
+  SM_RANGE();
   if (!q || !(eps > 0.0) || max_cycles < 1) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
@@ -1529,6 +1538,7 @@ extern "C" int sm_quad_advance(sm_quad *q, double dt, double c, double eps, doub
 // the per-box masks
 extern "C" int sm_quad_refine_flags(sm_quad *q, double c0, double c1, double c0_deref, double dx_deref, int buffer,
                                     int8_t *flags) {
+  SM_RANGE();
   if (!q || !flags || buffer < 0 || buffer > QN) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   if (!q->lut_n) return qfail(q, SM_ESTATE, "no coefficient table");
@@ -1573,6 +1583,7 @@ extern "C" int sm_quad_refine_flags(sm_quad *q, double c0, double c1, double c0_
 }
 
 extern "C" int sm_quad_regrid(sm_quad *q, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
+  SM_RANGE();
   if (!q || !flags) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
   const int nb0 = n_boxes(q);

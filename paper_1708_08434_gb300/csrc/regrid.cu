@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "sm_internal.cuh"
+#include "sm_nvtx.h"
 
 using namespace sm;
 
@@ -176,6 +177,7 @@ struct Entry {
 
 extern "C" int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_deref, double dx_deref, int buffer,
                                int8_t *flags) {
+  SM_RANGE();
   if (!ctx || !flags || buffer < 0 || buffer > NC) return SM_EINVAL;
   if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
   if (ctx->tab_n < 2) return sm_fail(ctx, SM_ESTATE, "no coefficient table");
@@ -202,6 +204,7 @@ extern "C" int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_dere
 }
 
 extern "C" int sm_regrid(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
+  SM_RANGE();
   if (!ctx || !flags) return SM_EINVAL;
   if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
   int st;
