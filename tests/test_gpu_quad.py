@@ -362,3 +362,35 @@ def test_regrid_capacity_and_argument_errors():
     g2 = gpu_quad(synth.Domain2(1.0, 2, 2, synth.CARTESIAN))
     assert g2.refine_level(1, np.zeros(4, np.int8)) == 0
     assert g2.n_boxes == 5 and g2.n_levels == 2
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_paper_schedule_multi_step(name):
+    """The paper's schedule in 2-D (Sec. 2.1.2, 2.4): one FMG solve, then
+    eight Heun steps with exactly two V-cycles per potential update and the
+    time step from the limits of Sec. 2.4; both sides advance with the
+    oracle's time step, the GPU's own limit is compared with it, and the
+    fields agree element by element after every step."""
+    p = pkg()
+    dom, st, o, g = pair(name)
+    t = load(dom, st, o, g)
+    o.fmg(1e-8, 40)
+    g.fmg(1e-8, 40)
+    o.compute_field()
+    g.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+    assert g.dt_limit(Q, EPS0) == pytest.approx(dt, rel=TOL)
+    leaf = t["child"][:, 0] < 0
+    for step in range(8):
+        ro = o.advance(dt, Q, EPS0, 0.0, 2)
+        rg = g.advance(dt, Q, EPS0, 0.0, 2)
+        assert ro[2:] == rg[2:] == (2, 2), (step, ro, rg)
+        assert rg[1] == pytest.approx(ro[1], rel=TOL), step
+        for vo, vg in ((quad.NE, p.NE), (quad.NI, p.NI), (quad.PHI, p.PHI)):
+            e = rel_err(g.download(vg)[leaf], o.get(vo)[leaf])
+            assert e <= TOL, (step, vo, e)
+        eo, po = o.get(quad.EMAG)[leaf], o.get(quad.PHI)[leaf]
+        amp = max(1.0, np.abs(po).max() / (dom.h(o.n_levels - 1) * np.abs(eo).max()))
+        assert rel_err(g.download(p.EMAG)[leaf], eo) <= TOL * amp, step
+        dt = ro[1]
+    assert 1e-14 < o.rel_residual() < 1e-2
