@@ -81,6 +81,9 @@ def parse():
                          "large: the 1e8-cell mesh alone; axi: the axisymmetric variant alone")
     ap.add_argument("--batch-solves", type=int, default=256,
                     help="--mode batch only: solve the first N of the 256 batched problems (small ncu captures)")
+    ap.add_argument("--batch-schedule", type=int, nargs=2, default=None, metavar=("SHAPE", "BLOCKS_PER_SM"),
+                    help="--mode batch only: restriction schedule (0-3 tiles, 4 columns) and blocks per SM "
+                         "instead of the library default (tiles 0, 4 per SM)")
     return ap.parse_args()
 
 
@@ -203,6 +206,8 @@ def run_batch_only(args):
     b, _ = make_batch_workload(args.batch_solves)
     if args.no_graphs:
         b.set_graphs(False)
+    if args.batch_schedule:
+        b.set_schedule(*args.batch_schedule)
     for _ in range(args.steps):
         b.phi.zero_()
         rc, cyc, rel = b.solve(TOL, MAX_CYCLES)

@@ -363,10 +363,14 @@ int sm_batch_ptrs(const sm_batch *b, double **phi, double **rhs, long long *offs
  * (computed for the denominator) as its first residual. */
 int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycles, double *rel_res);
 /* Autotuner: times `iters` corrections from phi = 0 for every candidate
- * restriction tile shape (8x8x8, 16x8x4, 32x4x4, 32x8x2
- * cells) and grid size
- * (2, 4, 8 blocks per SM), keeps the fastest; leaves phi = 0.  Out: the
- * chosen shape index, blocks per SM and its time in ms. */
+ * restriction schedule (shape index 0..3: one thread per coarse cell over
+ * tiles of 8x8x8, 16x8x4, 32x4x4, 32x8x2 coarse cells; 4: one block per
+ * 32x16-cell fine column marching the fine planes, the sweep's columns, on
+ * levels with at least four columns per SM, 8x8x8 tiles on the others) and
+ * grid size (2, 4, 8 blocks per SM), keeps the fastest; leaves phi = 0.
+ * Out: the chosen shape index, blocks per SM and its time in ms.
+ * sm_batch_set_schedule sets both directly (SM_EINVAL outside 0..4 and
+ * 1..64). */
 int sm_batch_tune(sm_batch *b, int iters, int *shape, int *grid_mult, double *best_ms);
 int sm_batch_set_schedule(sm_batch *b, int shape, int grid_mult);
 /* Time one kernel class of the batched cycle over all solves: `reps`

@@ -449,7 +449,8 @@ class Solver:
 class Batch:
     """Many independent uniform-grid Poisson solves advanced together."""
 
-    SHAPES = ((8, 8, 8), (16, 8, 4), (32, 4, 4), (32, 8, 2))
+    # restriction schedules: coarse-cell tiles (x, y, z), then fine columns
+    SHAPES = ((8, 8, 8), (16, 8, 4), (32, 4, 4), (32, 8, 2), "columns")
 
     def __init__(self, sides, length=1.0, bc_type=(0, 0, 0, 0, 1, 1), bc_val=(0, 0, 0, 0, 0, 1.0),
                  nu1=2, nu2=2, stream=None):

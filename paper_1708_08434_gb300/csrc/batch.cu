@@ -31,9 +31,11 @@ namespace {
 constexpr int BMAXL = 8;          // levels per solve
 constexpr int BMAXC = 16;         // coarsest grid side limit
 constexpr int TILE_CELLS = 512;   // threads per tile
-constexpr int NSHAPES = 4;
-// candidate tile shapes (x, y, z), x fastest in memory
-constexpr int SHAPES[NSHAPES][3] = {{8, 8, 8}, {16, 8, 4}, {32, 4, 4}, {32, 8, 2}};
+constexpr int NSHAPES = 5;  // four 3-D tile shapes, then the column-marching restriction
+constexpr int SHAPE_COLS = 4;
+// candidate tile shapes (x, y, z), x fastest in memory; the column schedule
+// uses 8x8x8 tiles on the levels with less than a wave of columns
+constexpr int SHAPES[NSHAPES][3] = {{8, 8, 8}, {16, 8, 4}, {32, 4, 4}, {32, 8, 2}, {8, 8, 8}};
 constexpr int GRID_MULTS[3] = {2, 4, 8};
 
 struct BSolve {
@@ -375,6 +377,110 @@ __global__ void __launch_bounds__(TILE_CELLS) k_bt_restrict(const int4 *__restri
         }
     long long ic = gidx(Nc, X, Y, Z);
     f[S.off[k + 1] + ic] = acc * 0.125f;
+  }
+}
+
+// Restriction of the error equation's residual r = f - A e from level k to
+// f of level k+1, on the sweep columns of level k (the solves for which
+// level k is not the coarsest), marching the fine planes: each thread's two
+// rows (one coarse row) are summed, then x pairs by a lane shuffle, then the
+// two fine planes of a coarse plane in a register; the even lanes write 1/8
+// of the sum.  The error planes (one-cell halo, zero outside the grid, the
+// planes -1 and N zero) are staged in a ring of eight shared-memory slots by
+// 16-byte asynchronous copies issued four planes ahead, and each thread's
+// two f values are loaded two planes ahead into registers; walls enter
+// through the homogeneous ghost coefficient (+1 Neumann, -1 Dirichlet per
+// wall face).
+constexpr int RRW = CX + 8;     // staged row: x0-4 .. x0+35, whole 16-byte chunks
+constexpr int RFR = CY + 2;     // staged rows: y0-1 .. y0+16
+constexpr int RPL = RRW * RFR;  // floats per staged plane
+__global__ void __launch_bounds__(CT, 6) k_bt_restrict_col(const int4 *__restrict__ cols, int ncols, int k,
+                                                        const BSolve *__restrict__ tab,
+                                                        const unsigned char *__restrict__ active,
+                                                        const float *__restrict__ e, float *__restrict__ f, Bc bc) {
+  __shared__ __align__(16) float se[RING][RPL];
+  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    const int4 C = cols[it];
+    if (!active[C.x]) continue;  // uniform per block
+    const BSolve &S = tab[C.x];
+    const int N = S.N[k], Nc = S.N[k + 1];  // N = 2 Nc
+    const long long NN = (long long)N * N;
+    const float *ef = e + S.off[k], *ff = f + S.off[k];
+    float *fc = f + S.off[k + 1];
+    const float inv_h2 = 1.0f / S.h2f[k];
+    const int x0 = C.y * CX, y0 = C.z * CY, x = x0 + tx, ya = y0 + ty2;
+    const bool in = x < N && ya < N;  // N even, ya even: both rows or neither
+    const bool vec = (N & 3) == 0;
+    // this thread's 16-byte chunk of a staged plane (vec grids): slot-0
+    // offset, in-plane element offset, inside the grid
+    int cdst = -1, coff = 0;
+    bool cok = false;
+    if (vec && t < RFR * (RRW / 4)) {
+      const int r = t / (RRW / 4), c4 = 4 * (t % (RRW / 4)), y = y0 - 1 + r, xx = x0 - 4 + c4;
+      cok = y >= 0 && y < N && xx >= 0 && xx < N;
+      coff = cok ? y * N + xx : 0;
+      cdst = r * RRW + c4;
+    }
+    auto issue = [&](int z) {
+      const int sl = z & (RING - 1);
+      const bool zin = z >= 0 && z < N;
+      if (vec) {
+        if (cdst >= 0) cp_async<16>(&se[sl][cdst], ef + (zin ? z * NN + coff : 0), cok && zin);
+      } else {
+        for (int i = t; i < RPL; i += CT) {
+          const int y = y0 - 1 + i / RRW, xx = x0 - 4 + i % RRW;
+          const bool ok = zin && y >= 0 && y < N && xx >= 0 && xx < N;
+          cp_async<4>(&se[sl][i], ok ? ef + z * NN + y * N + xx : ef, ok);
+        }
+      }
+      cp_commit();
+    };
+    const int q0 = (ty2 + 1) * RRW + tx + 4;
+    const float wx = wall_w(bc, 0, x, N);
+    const float w0 = wx + wall_w(bc, 1, ya, N), w1 = wx + wall_w(bc, 1, ya + 1, N);
+    // this thread's two f values of planes z (fa) and z+1 (fb), loaded two
+    // planes ahead of their use
+    const float *frow = ff + (in ? (long long)ya * N + x : 0);
+    float fa0 = 0.f, fa1 = 0.f, fb0 = 0.f, fb1 = 0.f;
+    if (in) {
+      fa0 = __ldg(frow), fa1 = __ldg(frow + N);
+      if (N > 1) fb0 = __ldg(frow + NN), fb1 = __ldg(frow + NN + N);
+    }
+    float acc = 0.f;
+    __syncthreads();  // the previous column's planes are no longer read
+#pragma unroll
+    for (int z = -1; z <= 3; ++z) issue(z);
+    for (int z = 0; z < N; ++z) {
+      float fn0 = 0.f, fn1 = 0.f;
+      if (in && z + 2 < N) fn0 = __ldg(frow + (z + 2) * NN), fn1 = __ldg(frow + (z + 2) * NN + N);
+      cp_wait<2>();     // this thread's copies of planes <= z+1 have landed
+      __syncthreads();  // everyone's have; step z-1's reads are done
+      issue(z + 4);     // into the slot of plane z-4, last read at step z-3
+      const float *pm = se[(z - 1) & (RING - 1)], *pz = se[z & (RING - 1)], *pp = se[(z + 1) & (RING - 1)];
+      const float wz = wall_w(bc, 2, z, N);
+      float rs = 0.f;
+      if (in) {
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+          const int q = q0 + o * RRW;
+          const float c = pz[q];
+          float sum = pz[q - 1] + pz[q + 1];
+          sum += pz[q - RRW];
+          sum += pz[q + RRW];
+          sum += pm[q];
+          sum += pp[q];
+          sum = fmaf((o ? w1 : w0) + wz, c, sum);
+          rs += (o ? fa1 : fa0) - (sum - 6.0f * c) * inv_h2;
+        }
+      }
+      fa0 = fb0, fa1 = fb1, fb0 = fn0, fb1 = fn1;
+      rs += __shfl_xor_sync(0xffffffffu, rs, 1);
+      acc = (z & 1) ? acc + rs : rs;
+      if ((z & 1) && in && !(tx & 1))
+        fc[(long long)(z >> 1) * Nc * Nc + (long long)(ya >> 1) * Nc + (x >> 1)] = acc * 0.125f;
+    }
+    cp_wait<0>();
   }
 }
 
@@ -883,6 +989,7 @@ struct sm_batch {
   double *h_tolmax = nullptr;
   // current schedule
   int shape = 0, gmult = 4, sms = 148;
+  int rcol_per_sm = 1;  // resident column-restriction blocks per SM: its one-wave grid
   std::vector<size_t> restr_off, restr_cnt;  // per level index: restriction tiles
   std::vector<size_t> coarse_off, coarse_cnt;
   std::vector<size_t> scol_off, scol_cnt;  // per level index: sweep columns
@@ -1235,7 +1342,27 @@ static int set_attrs(sm_batch *b) {
   BCK(cudaFuncSetAttribute(k_bt_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem(BMAXC)));
   BCK(cudaFuncSetAttribute(k_bt_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_PHI));
   BCK(cudaFuncSetAttribute(k_bt_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUTER_SMEM));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->rcol_per_sm, k_bt_restrict_col, CT, 0));
+  b->rcol_per_sm = std::max(1, b->rcol_per_sm);
   return SM_OK;
+}
+
+// the column restriction runs as one wave of at most RCOL_PER_SM resident
+// blocks per SM whatever the grid multiplier: its blocks march whole
+// columns, longest first, and a second partial wave leaves SMs idle at the
+// end; four per SM (about five columns per block on the 256-solve
+// workload) balanced better than six (370 against 405 us)
+constexpr int RCOL_PER_SM = 4;
+static size_t rcol_wave(const sm_batch *b) { return (size_t)std::min(RCOL_PER_SM, b->rcol_per_sm) * b->sms; }
+static int rcol_grid(const sm_batch *b, size_t ncols) {
+  return (int)std::max<size_t>(1, std::min(rcol_wave(b), ncols));
+}
+// the column restriction of level k -> k+1 under the column schedule, on
+// levels with a full wave of columns (on the coarser ones one thread per
+// coarse cell keeps more SMs busy: 17 against 25 us on the third level of
+// the 256-solve workload)
+static bool rcol_use(const sm_batch *b, int k) {
+  return b->shape == SHAPE_COLS && b->scol_cnt[k] >= rcol_wave(b);
 }
 
 static int coarse_at_level(sm_batch *b, int k) {
@@ -1254,12 +1381,21 @@ static int bvcycle(sm_batch *b) {
   coarse_at_level(b, 0);  // solves whose finest grid is already the coarsest (adds to phi)
   for (int k = 0; k < b->kmax; ++k) {
     smooth_level(b, k, b->nu1, true, false);
-    size_t nr = b->restr_cnt[k + 1];
-    if (nr) {
-      k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[k + 1], (int)nr, k,
-                                                                   b->d_tab, b->d_active, b->e32, b->f32, b->bc,
-                                                                   shape_of(b));
-      ++b->n_launch;
+    if (rcol_use(b, k)) {
+      const size_t nc = b->scol_cnt[k];
+      if (nc) {
+        k_bt_restrict_col<<<rcol_grid(b, nc), CT, 0, b->stream>>>(b->d_tiles + b->scol_off[k], (int)nc, k, b->d_tab,
+                                                                 b->d_active, b->e32, b->f32, b->bc);
+        ++b->n_launch;
+      }
+    } else {
+      size_t nr = b->restr_cnt[k + 1];
+      if (nr) {
+        k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[k + 1], (int)nr, k,
+                                                                     b->d_tab, b->d_active, b->e32, b->f32, b->bc,
+                                                                     shape_of(b));
+        ++b->n_launch;
+      }
     }
     coarse_at_level(b, k + 1);
   }
@@ -1504,7 +1640,8 @@ extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *
   for (auto &q : b->solves)
     if (q.nlev > 1) fine += (long long)q.N[0] * q.N[0] * q.N[0];
   const size_t nsw = b->scol_cnt.empty() ? 0 : b->scol_cnt[0];
-  const size_t nr = b->kmax >= 1 ? b->restr_cnt[1] : 0;
+  const bool rcol = b->kmax >= 1 && rcol_use(b, 0);
+  const size_t nr = b->kmax >= 1 ? (rcol ? nsw : b->restr_cnt[1]) : 0;
   if ((kclass != 1 && fine == 0) || (kclass == 3 && nr == 0)) return bfail(b, SM_ESTATE, "no level below 0");
   BCK(cudaMemsetAsync(b->d_active, 1, b->n, b->stream));
   if (kclass == 1) {
@@ -1532,9 +1669,13 @@ extern "C" int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *
                                                              b->d_active, b->e32, b->bc);
         break;
       default:
-        k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[1], (int)nr, 0,
-                                                                     b->d_tab, b->d_active, b->e32, b->f32, b->bc,
-                                                                     shape_of(b));
+        if (rcol)
+          k_bt_restrict_col<<<rcol_grid(b, nr), CT, 0, b->stream>>>(b->d_tiles + b->scol_off[0], (int)nr, 0, b->d_tab,
+                                                                   b->d_active, b->e32, b->f32, b->bc);
+        else
+          k_bt_restrict<<<grid_for(b, nr), TILE_CELLS, 0, b->stream>>>(b->d_tiles + b->restr_off[1], (int)nr, 0,
+                                                                       b->d_tab, b->d_active, b->e32, b->f32, b->bc,
+                                                                       shape_of(b));
     }
   };
   launch();  // warm-up

@@ -112,18 +112,41 @@ def test_batch_autotune_keeps_results():
     sides = [40, 48, 32, 56]
     b, rhos = make_batch(sides, seed_blobs=3)
     shape, gmult, ms = b.tune(2)
-    assert 0 <= shape < 4 and gmult in (2, 4, 8) and ms > 0
+    assert 0 <= shape < 5 and gmult in (2, 4, 8) and ms > 0
     rc, cyc, rel = b.solve(1e-9, 40)
     assert rc == 0
     check(b, rhos, range(len(sides)), 1e-7)
     # every schedule gives the same potential to roundoff of FP32 cycles
     ref = b.phi.clone()
-    for sh in range(4):
+    for sh in range(5):
         b.set_schedule(sh, 2)
         b.phi.zero_()
         b.solve(1e-9, 40)
         d = (b.phi - ref).abs().max().item() / ref.abs().max().item()
         assert d <= 1e-7
+
+
+def test_batch_column_restriction_on_full_waves():
+    """Schedule 4 marches fine columns only on levels with at least four
+    columns per SM: enough 128^3 solves that level 0 has them (32 columns
+    each) while the coarser levels fall back to 8^3 tiles."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n128 = -(-4 * sms // 32)
+    sides = [128] * n128 + [40, 56]
+    b, rhos = make_batch(sides, seed_blobs=5, keep={0, n128 - 1, n128 + 1})
+    b.set_schedule(0, 4)
+    rc, _, rel = b.solve(1e-9, 40)
+    assert rc == 0 and np.all(rel <= 1e-9)
+    ref = b.phi.clone()
+    b.set_schedule(4, 4)
+    b.phi.zero_()
+    rc, _, rel = b.solve(1e-9, 40)
+    assert rc == 0 and np.all(rel <= 1e-9)
+    d = (b.phi - ref).abs().max().item() / ref.abs().max().item()
+    assert d <= 1e-7
+    check(b, rhos, (0, n128 - 1, n128 + 1), 1e-6)
+    b.close()
 
 
 def test_batch_rejects_too_large_coarsest():
