@@ -442,10 +442,10 @@ int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned long long 
  * finest levels (every stride-th) per solve; mode 2 predicts a warm start
  * for those boxes before each solve (taper != 0: the prediction is
  * weighted 1/4, 3/4 on the two outer cell layers of each axis) and keeps
- * it only if the relative residual of the predicted start is below judge
+ * it only if the relative residual of the predicted start is below accept
  * times that of the plain warm start (else the plain warm start); the
  * solve then iterates to its tolerance either way.  mode 0 detaches. */
-int sm_cnn_attach(sm_ctx *ctx, sm_cnn *c, int mode, int per_solve, int stride, int taper, double judge);
+int sm_cnn_attach(sm_ctx *ctx, sm_cnn *c, int mode, int per_solve, int stride, int taper, double accept);
 /* recorded samples, predictions made and kept, last residuals
  * (last_rel[0] plain start, last_rel[1] predicted start) */
 int sm_cnn_stats(const sm_cnn *c, int *n_samples, long long *predictions, long long *kept, double *last_rel);

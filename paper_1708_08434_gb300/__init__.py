@@ -618,8 +618,8 @@ class Network:
         self._ck(self._lib.sm_cnn_train(self._h, epochs, batch, lr, seed, C.byref(loss)))
         return loss.value
 
-    def attach(self, solver, mode, per_solve=512, stride=1, taper=False, judge=1.0):
-        self._ck(self._lib.sm_cnn_attach(solver._h, self._h, mode, per_solve, stride, int(taper), judge))
+    def attach(self, solver, mode, per_solve=512, stride=1, taper=False, accept=1.0):
+        self._ck(self._lib.sm_cnn_attach(solver._h, self._h, mode, per_solve, stride, int(taper), accept))
 
     def stats(self):
         n, p, k = C.c_int(), C.c_longlong(), C.c_longlong()

@@ -3,7 +3,7 @@
 // convolutional network predicts the change of the potential of a box from
 // its right-hand side and its previous potential.  It is trained on the GPU
 // by the kernels below on pairs the solver itself produces during a run;
-// the multigrid solve stays the judge (a prediction is kept only if it
+// the multigrid residual decides (a prediction is kept only if it
 // lowers the relative residual) and iterates to the same tolerance.
 //
 // Network per 8^3 box (weights BF16, activations rounded to BF16 as the
@@ -475,7 +475,7 @@ struct sm_cnn {
   int adam_step = 0;
   // attached solver
   int mode = 0, stride = 1, per_solve = 0, taper = 0;
-  double judge = 1.0;  // keep a prediction when rel_cnn < judge * rel_plain
+  double accept = 1.0;  // keep a prediction when rel_cnn < accept * rel_plain
   std::vector<int> pending;     // boxes recorded by the last pre-solve hook
   int pending_slot = 0;
   long long predictions = 0, kept = 0;
@@ -774,9 +774,9 @@ static int cnn_pre_solve(void *obj, sm_ctx *ctx) {
     ++c->predictions;
     c->last_rel_plain = rel_plain;
     c->last_rel_cnn = rel_cnn;
-    if (rel_cnn < c->judge * rel_plain) {
+    if (rel_cnn < c->accept * rel_plain) {
       ++c->kept;
-    } else {  // the judge rejects the prediction: plain warm start
+    } else {  // the residual test rejects the prediction: plain warm start
       CCK(cudaMemcpyAsync(ctx->phi, ctx->res, sizeof(double) * CELLS * (size_t)ctx->n_boxes,
                           cudaMemcpyDeviceToDevice, ctx->stream));
       if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
@@ -800,7 +800,7 @@ static int cnn_post_solve(void *obj, sm_ctx *ctx) {
 }
 
 extern "C" int sm_cnn_attach(sm_ctx *ctx, sm_cnn *c, int mode, int per_solve, int stride, int taper,
-                             double judge) {
+                             double accept) {
   if (!ctx) return SM_EINVAL;
   if (mode == 0 || !c) {
     ctx->hook_obj = nullptr;
@@ -808,13 +808,13 @@ extern "C" int sm_cnn_attach(sm_ctx *ctx, sm_cnn *c, int mode, int per_solve, in
     ctx->post_solve = nullptr;
     return SM_OK;
   }
-  if ((mode != 1 && mode != 2) || per_solve < 1 || stride < 1 || !c->arena || !(judge > 0.0)) return SM_EINVAL;
+  if ((mode != 1 && mode != 2) || per_solve < 1 || stride < 1 || !c->arena || !(accept > 0.0)) return SM_EINVAL;
   if (per_solve > c->max_boxes) return SM_EINVAL;
   c->mode = mode;
   c->per_solve = per_solve;
   c->stride = stride;
   c->taper = taper != 0;
-  c->judge = judge;
+  c->accept = accept;
   ctx->hook_obj = c;
   ctx->pre_solve = cnn_pre_solve;
   ctx->post_solve = cnn_post_solve;

@@ -3,7 +3,8 @@
 the gradient of the mean squared error (backward), bound 1e-5 relative;
 Adam against its textbook update; training on pairs the solver records;
 and what the trained network gains as a warm start (V-cycles), with the
-multigrid residual as the judge and the same tolerance met."""
+multigrid residual deciding whether a prediction is kept and the same
+tolerance met."""
 import numpy as np
 import pytest
 
@@ -162,7 +163,7 @@ def test_training_on_recorded_solves_reduces_loss():
 def test_learned_warm_start_gain():
     """Train on the first steps of a run, then predict on the following
     steps; the same run without the network is the reference.  Both meet
-    the tolerance on every solve; the judge never accepts a worse start."""
+    the tolerance on every solve; the residual test never keeps a worse start."""
     net = pkg().Network(8192, 1024)
     net.set_params(synth.cnn_initial_params())
     g1, c_rec = streamer_run(1, net, steps=6)
