@@ -218,20 +218,23 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
         for (int i = t; i < EPL; i += CT) cp_async<4>(&se[sl][i], ev, false);
       }
     };
-    // copies of plane z (if it exists) as one commit group
-    auto issue = [&](int z) {
-      if (z == N) zero_slot(z & (RING - 1));
+    // this thread's chunk sources in plane z, advanced one plane per issue
+    const float *csrc[2] = {(cise[0] ? ev : fv) + coff[0], (cise[1] ? ev : fv) + coff[1]};
+    const unsigned cstr[2] = {cise[0] ? EPL * 4u : FPL * 4u, cise[1] ? EPL * 4u : FPL * 4u};
+    // copies of plane z (if it exists) into slot sl = z mod RING as one
+    // commit group; called for z = 0, 1, 2, ... in order
+    auto issue = [&](int z, int sl) {
+      if (z == N) zero_slot(sl);
       if (z < N) {
-        const int sl = z & (RING - 1);
         const float *ez = ev + z * NN, *fz = fv + z * NN;
         if (vec) {
 #pragma unroll
           for (int u = 0; u < 2; ++u)
             if (chas[u]) {
-              const unsigned d = cdst[u] + (unsigned)sl * (cise[u] ? EPL * 4u : FPL * 4u);
-              asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d),
-                           "l"((cise[u] ? ez : fz) + coff[u]), "r"(cok[u] ? 16 : 0)
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(cdst[u] + (unsigned)sl * cstr[u]),
+                           "l"(csrc[u]), "r"(cok[u] ? 16 : 0)
                            : "memory");
+              csrc[u] += NN;
             }
         } else {
           for (int i = t; i < (ER + FR) * RW; i += CT) {
@@ -284,41 +287,50 @@ __global__ void __launch_bounds__(CT) k_bt_sweep(const int4 *__restrict__ cols, 
     const int rq = (ry - y0 + 2) * RW + (rx - x0 + 4), rqf = (ry - y0 + 1) * RW + (rx - x0 + 4);
     const float rw = rin ? wall_w(bc, 0, rx, N) + wall_w(bc, 1, ry, N) : 0.f;
     const long long row0 = (long long)ya * N + x;
+    float *eo_z = eo + row0;                         // this thread's cells of the plane stored next
+    double *pv_z = pv ? pv + row0 : nullptr;
+    const int par = (x + ya) & 1, rpar = (rx + ry) & 1;  // colour parities at plane 0
     unsigned em = 0;  // with phi: largest exponent field written
     __syncthreads();  // the previous column's planes are no longer read
-    zero_slot((-1) & (RING - 1));                 // plane -1, landing with plane 0's group
+    zero_slot((-1) & (RING - 1));  // plane -1, landing with plane 0's group
 #pragma unroll
-    for (int z = 0; z < RING - 3; ++z) issue(z);  // planes 0 .. RING-4
-    for (int p = 0; p <= N; ++p) {
-      cp_wait<RING - 5>();  // this thread's copies of planes <= p+1 have landed
-      __syncthreads();      // everyone's have; step p-1's reads of plane p-3 are done
-      issue(p + RING - 3);
-      float *Pm2 = se[(p - 2) & (RING - 1)], *Pm1 = se[(p - 1) & (RING - 1)], *P0 = se[p & (RING - 1)],
-            *Pp1 = se[(p + 1) & (RING - 1)];
-      if (p < N) {  // colour 0 on plane p: one column cell per thread, and the ring
-        const float wz = wall_w(bc, 2, p, N);
-        const float *F0 = sf[p & (RING - 1)];
-        if (in) {
-          const int o = (x + ya + p) & 1;  // row offset of the colour-0 cell
-          update(P0, Pm1, Pp1, F0, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wz);
+    for (int z = 0; z < RING - 3; ++z) issue(z, z);  // planes 0 .. RING-4
+    // steps p = pb + i, unrolled by the ring size so that every slot index
+    // and colour parity is a constant (pb is a multiple of RING)
+    for (int pb = 0; pb <= N; pb += RING) {
+#pragma unroll
+      for (int i = 0; i < RING; ++i) {
+        const int p = pb + i;
+        if (p > N) break;
+        cp_wait<RING - 5>();  // this thread's copies of planes <= p+1 have landed
+        __syncthreads();      // everyone's have; step p-1's reads of plane p-3 are done
+        issue(p + RING - 3, (i + RING - 3) & (RING - 1));
+        float *Pm2 = se[(i - 2) & (RING - 1)], *Pm1 = se[(i - 1) & (RING - 1)], *P0 = se[i & (RING - 1)],
+              *Pp1 = se[(i + 1) & (RING - 1)];
+        const int o = par ^ (i & 1);  // row offset of the colour-0 cell of plane p and the colour-1 cell of p-1
+        if (p < N) {                  // colour 0 on plane p: one column cell per thread, and the ring
+          const float wz = wall_w(bc, 2, p, N);
+          const float *F0 = sf[i & (RING - 1)];
+          if (in) update(P0, Pm1, Pp1, F0, q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wz);
+          if (rin && rpar == (i & 1)) update(P0, Pm1, Pp1, F0, rq, rqf, rw + wz);
         }
-        if (rin && !((rx + ry + p) & 1)) update(P0, Pm1, Pp1, F0, rq, rqf, rw + wz);
-      }
-      __syncthreads();
-      if (p >= 1 && in) {  // colour 1 on plane p-1, then store both cells
-        const int z = p - 1, o = ((x + ya + z) & 1) ^ 1;
-        update(Pm1, Pm2, P0, sf[z & (RING - 1)], q0 + o * RW, qf0 + o * RW, (o ? w1 : w0) + wall_w(bc, 2, z, N));
-        const float v0 = Pm1[q0], v1 = Pm1[q0 + RW];
-        const long long g = z * NN + row0;
-        if (pv) {
-          const double *ph = sph[z & (RING - 1)];
-          const double n0 = ph[ty2 * CX + tx] + cvt_f32_f64(v0), n1 = ph[(ty2 + 1) * CX + tx] + cvt_f32_f64(v1);
-          pv[g] = n0;
-          pv[g + N] = n1;
-          em = max(em, max(expo_of(n0), expo_of(n1)));
-        } else {
-          eo[g] = v0;
-          eo[g + N] = v1;
+        __syncthreads();
+        if (p >= 1 && in) {  // colour 1 on plane p-1, then store both cells
+          update(Pm1, Pm2, P0, sf[(i - 1) & (RING - 1)], q0 + o * RW, qf0 + o * RW,
+                 (o ? w1 : w0) + wall_w(bc, 2, p - 1, N));
+          const float v0 = Pm1[q0], v1 = Pm1[q0 + RW];
+          if (pv) {
+            const double *ph = sph[(i - 1) & (RING - 1)];
+            const double n0 = ph[ty2 * CX + tx] + cvt_f32_f64(v0), n1 = ph[(ty2 + 1) * CX + tx] + cvt_f32_f64(v1);
+            pv_z[0] = n0;
+            pv_z[N] = n1;
+            pv_z += NN;
+            em = max(em, max(expo_of(n0), expo_of(n1)));
+          } else {
+            eo_z[0] = v0;
+            eo_z[N] = v1;
+            eo_z += NN;
+          }
         }
       }
     }
