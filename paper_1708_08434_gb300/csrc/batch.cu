@@ -1001,6 +1001,11 @@ struct sm_batch {
   double *h_tolmax = nullptr;
   // current schedule
   int shape = 0, gmult = 4, sms = 148;
+  // one side stream per level for the exact coarse solves, forked from and
+  // joined back into the cycle's stream by events
+  cudaStream_t side[BMAXL] = {};
+  cudaEvent_t ev_fork[BMAXL] = {}, ev_join[BMAXL] = {};
+  unsigned pending = 0;  // levels whose coarse solve is not joined yet
   int rcol_per_sm = 1;  // resident column-restriction blocks per SM: its one-wave grid
   std::vector<size_t> restr_off, restr_cnt;  // per level index: restriction tiles
   std::vector<size_t> coarse_off, coarse_cnt;
@@ -1227,6 +1232,8 @@ static int build_lists(sm_batch *b, int shape) {
     b->coarse_off[k] = coarse.size();
     for (int s = 0; s < b->n; ++s)
       if (b->solves[s].nlev - 1 == k) coarse.push_back(s);
+    std::stable_sort(coarse.begin() + b->coarse_off[k], coarse.end(),
+                     [&](int u, int v) { return b->solves[u].N[k] > b->solves[v].N[k]; });
     b->coarse_cnt[k] = coarse.size() - b->coarse_off[k];
   }
   BCK(cudaMemcpyAsync(b->d_tiles, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice, b->stream));
@@ -1276,6 +1283,11 @@ extern "C" int sm_batch_destroy(sm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->cap2) cudaStreamDestroy(b->cap2);
+  for (int k = 0; k < BMAXL; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_fork[k]) cudaEventDestroy(b->ev_fork[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
   if (b->h_tolmax) cudaFreeHost(b->h_tolmax);
   delete b;
   return SM_OK;
@@ -1345,13 +1357,24 @@ static int smooth_level(sm_batch *b, int k, int nu, bool from_zero, bool add_phi
   return SM_OK;
 }
 
-static size_t coarse_smem(int n) {
+constexpr size_t coarse_smem(int n) {
   return sizeof(double) * (2 * (size_t)n * n * n + 3 * BMAXC * BMAXC + 3 * BMAXC);
 }
+// The exact coarse solve is bound by the FP64 pipe of its SM (a 15^3 grid:
+// 3e5 multiply-adds, about 75 us).  Its launches ask for more than half of
+// an SM's shared memory, so that one block runs per SM, and list the solves
+// largest first: the largest grids then each get an SM of their own.
+constexpr size_t COARSE_SMEM_LAUNCH = 116 * 1024;
+static_assert(COARSE_SMEM_LAUNCH >= coarse_smem(BMAXC), "coarse solve shared memory");
 
 // dynamic shared memory of the kernels that stage more than 48 KB
 static int set_attrs(sm_batch *b) {
-  BCK(cudaFuncSetAttribute(k_bt_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem(BMAXC)));
+  BCK(cudaFuncSetAttribute(k_bt_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COARSE_SMEM_LAUNCH));
+  for (int k = 1; k <= b->kmax && k < BMAXL; ++k) {
+    if (!b->side[k]) BCK(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+    if (!b->ev_fork[k]) BCK(cudaEventCreateWithFlags(&b->ev_fork[k], cudaEventDisableTiming));
+    if (!b->ev_join[k]) BCK(cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming));
+  }
   BCK(cudaFuncSetAttribute(k_bt_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_PHI));
   BCK(cudaFuncSetAttribute(k_bt_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OUTER_SMEM));
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->rcol_per_sm, k_bt_restrict_col, CT, 0));
@@ -1377,12 +1400,34 @@ static bool rcol_use(const sm_batch *b, int k) {
   return b->shape == SHAPE_COLS && b->scol_cnt[k] >= rcol_wave(b);
 }
 
+// exact solves of the solves whose coarsest grid is level k.  Level 0 runs
+// in the cycle's stream (it adds to phi); a deeper level runs on its side
+// stream, forked here and joined by coarse_join before the prolongation
+// from level k, so that the levels' solves overlap one another and the
+// coarser levels' smoothing of the other solves (disjoint grids).
 static int coarse_at_level(sm_batch *b, int k) {
   size_t nc = b->coarse_cnt[k];
-  if (nc) {
-    k_bt_coarse<<<(int)nc, 512, coarse_smem(BMAXC), b->stream>>>(b->d_coarse + b->coarse_off[k], k, b->d_tab,
-                                                                b->d_active, b->e32, b->f32, b->bc, b->phi, b->d_emax);
-    ++b->n_launch;
+  if (!nc) return SM_OK;
+  cudaStream_t st = b->stream;
+  if (k > 0) {
+    st = b->side[k];
+    BCK(cudaEventRecord(b->ev_fork[k], b->stream));
+    BCK(cudaStreamWaitEvent(st, b->ev_fork[k], 0));
+  }
+  k_bt_coarse<<<(int)nc, 512, COARSE_SMEM_LAUNCH, st>>>(b->d_coarse + b->coarse_off[k], k, b->d_tab, b->d_active,
+                                                       b->e32, b->f32, b->bc, b->phi, b->d_emax);
+  ++b->n_launch;
+  if (k > 0) {
+    BCK(cudaEventRecord(b->ev_join[k], st));
+    b->pending |= 1u << k;
+  }
+  return SM_OK;
+}
+
+static int coarse_join(sm_batch *b, int k) {
+  if (b->pending & (1u << k)) {
+    BCK(cudaStreamWaitEvent(b->stream, b->ev_join[k], 0));
+    b->pending &= ~(1u << k);
   }
   return SM_OK;
 }
@@ -1390,7 +1435,9 @@ static int coarse_at_level(sm_batch *b, int k) {
 // correction-scheme V-cycle on the error equation of every active solve,
 // ending with phi += e on the finest grids
 static int bvcycle(sm_batch *b) {
-  coarse_at_level(b, 0);  // solves whose finest grid is already the coarsest (adds to phi)
+  b->pending = 0;
+  // solves whose finest grid is already the coarsest (adds to phi)
+  if (int st = coarse_at_level(b, 0)) return st;
   for (int k = 0; k < b->kmax; ++k) {
     smooth_level(b, k, b->nu1, true, false);
     if (rcol_use(b, k)) {
@@ -1409,9 +1456,10 @@ static int bvcycle(sm_batch *b) {
         ++b->n_launch;
       }
     }
-    coarse_at_level(b, k + 1);
+    if (int st = coarse_at_level(b, k + 1)) return st;
   }
   for (int k = b->kmax - 1; k >= 0; --k) {
+    if (int st = coarse_join(b, k + 1)) return st;  // the prolongation reads level k+1
     size_t n = b->scol_cnt[k];
     if (n) {
       k_bt_prolong<<<grid_for(b, n), CT, 0, b->stream>>>(b->d_tiles + b->scol_off[k], (int)n, k, b->d_tab,
