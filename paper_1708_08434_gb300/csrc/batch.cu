@@ -434,11 +434,16 @@ __global__ void __launch_bounds__(CT, 6) k_bt_restrict_col(const int4 *__restric
       coff = cok ? y * N + xx : 0;
       cdst = r * RRW + c4;
     }
-    auto issue = [&](int z) {
-      const int sl = z & (RING - 1);
+    // this thread's chunk source in plane z (vec grids), advanced one plane
+    // per issue of a plane of the grid
+    const float *csrc = ef + coff;
+    // copies of plane z into slot sl = z mod RING (zero planes outside the
+    // grid); called for z = -1, 0, 1, ... in order
+    auto issue = [&](int z, int sl) {
       const bool zin = z >= 0 && z < N;
       if (vec) {
-        if (cdst >= 0) cp_async<16>(&se[sl][cdst], ef + (zin ? z * NN + coff : 0), cok && zin);
+        if (cdst >= 0) cp_async<16>(&se[sl][cdst], zin ? csrc : ef, cok && zin);
+        if (zin) csrc += NN;
       } else {
         for (int i = t; i < RPL; i += CT) {
           const int y = y0 - 1 + i / RRW, xx = x0 - 4 + i % RRW;
@@ -459,38 +464,50 @@ __global__ void __launch_bounds__(CT, 6) k_bt_restrict_col(const int4 *__restric
       fa0 = __ldg(frow), fa1 = __ldg(frow + N);
       if (N > 1) fb0 = __ldg(frow + NN), fb1 = __ldg(frow + NN + N);
     }
+    const float *fnext = frow + 2 * NN;  // f of plane z+2 at step z
+    float *fcz = fc + (long long)(ya >> 1) * Nc + (x >> 1);  // this thread's coarse cell, coarse plane z/2
     float acc = 0.f;
     __syncthreads();  // the previous column's planes are no longer read
 #pragma unroll
-    for (int z = -1; z <= 3; ++z) issue(z);
-    for (int z = 0; z < N; ++z) {
-      float fn0 = 0.f, fn1 = 0.f;
-      if (in && z + 2 < N) fn0 = __ldg(frow + (z + 2) * NN), fn1 = __ldg(frow + (z + 2) * NN + N);
-      cp_wait<2>();     // this thread's copies of planes <= z+1 have landed
-      __syncthreads();  // everyone's have; step z-1's reads are done
-      issue(z + 4);     // into the slot of plane z-4, last read at step z-3
-      const float *pm = se[(z - 1) & (RING - 1)], *pz = se[z & (RING - 1)], *pp = se[(z + 1) & (RING - 1)];
-      const float wz = wall_w(bc, 2, z, N);
-      float rs = 0.f;
-      if (in) {
+    for (int z = -1; z <= 3; ++z) issue(z, z & (RING - 1));
+    // steps z = zb + i, unrolled by the ring size so that every slot index
+    // is a constant (zb is a multiple of RING)
+    for (int zb = 0; zb < N; zb += RING) {
 #pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          const int q = q0 + o * RRW;
-          const float c = pz[q];
-          float sum = pz[q - 1] + pz[q + 1];
-          sum += pz[q - RRW];
-          sum += pz[q + RRW];
-          sum += pm[q];
-          sum += pp[q];
-          sum = fmaf((o ? w1 : w0) + wz, c, sum);
-          rs += (o ? fa1 : fa0) - (sum - 6.0f * c) * inv_h2;
+      for (int i = 0; i < RING; ++i) {
+        const int z = zb + i;
+        if (z >= N) break;
+        float fn0 = 0.f, fn1 = 0.f;
+        if (in && z + 2 < N) fn0 = __ldg(fnext), fn1 = __ldg(fnext + N);
+        fnext += NN;
+        cp_wait<2>();     // this thread's copies of planes <= z+1 have landed
+        __syncthreads();  // everyone's have; step z-1's reads are done
+        issue(z + 4, (i + 4) & (RING - 1));  // into the slot of plane z-4, last read at step z-3
+        const float *pm = se[(i - 1) & (RING - 1)], *pz = se[i & (RING - 1)], *pp = se[(i + 1) & (RING - 1)];
+        const float wz = wall_w(bc, 2, z, N);
+        float rs = 0.f;
+        if (in) {
+#pragma unroll
+          for (int o = 0; o < 2; ++o) {
+            const int q = q0 + o * RRW;
+            const float c = pz[q];
+            float sum = pz[q - 1] + pz[q + 1];
+            sum += pz[q - RRW];
+            sum += pz[q + RRW];
+            sum += pm[q];
+            sum += pp[q];
+            sum = fmaf((o ? w1 : w0) + wz, c, sum);
+            rs += (o ? fa1 : fa0) - (sum - 6.0f * c) * inv_h2;
+          }
+        }
+        fa0 = fb0, fa1 = fb1, fb0 = fn0, fb1 = fn1;
+        rs += __shfl_xor_sync(0xffffffffu, rs, 1);
+        acc = (i & 1) ? acc + rs : rs;
+        if (i & 1) {
+          if (in && !(tx & 1)) *fcz = acc * 0.125f;
+          fcz += (long long)Nc * Nc;
         }
       }
-      fa0 = fb0, fa1 = fb1, fb0 = fn0, fb1 = fn1;
-      rs += __shfl_xor_sync(0xffffffffu, rs, 1);
-      acc = (z & 1) ? acc + rs : rs;
-      if ((z & 1) && in && !(tx & 1))
-        fc[(long long)(z >> 1) * Nc * Nc + (long long)(ya >> 1) * Nc + (x >> 1)] = acc * 0.125f;
     }
     cp_wait<0>();
   }
@@ -501,9 +518,9 @@ __global__ void __launch_bounds__(CT, 6) k_bt_restrict_col(const int4 *__restric
 // per step.  The coarse planes Z-1 .. Z+1 of the column's coarse footprint
 // (with a one-cell halo, zero outside the grid) sit in a ring of four
 // shared-memory slots, plane Z+2 is loaded into registers during step Z;
-// the fine values of the next step are loaded one step ahead.  A coarse
-// neighbour outside the grid is the homogeneous wall ghost +c (Neumann) or
-// -c (Dirichlet), added through one coefficient per fine cell.
+// the fine values are loaded two steps ahead.  A coarse neighbour outside
+// the grid is the homogeneous wall ghost +c (Neumann) or -c (Dirichlet),
+// added through one coefficient per fine cell.
 constexpr int PX = CX / 2 + 2, PY = CY / 2 + 2, PPL = PX * PY;  // staged coarse plane
 __global__ void __launch_bounds__(CT) k_bt_prolong(const int4 *__restrict__ cols, int ncols, int k,
                                                    const BSolve *__restrict__ tab,
@@ -542,8 +559,15 @@ __global__ void __launch_bounds__(CT) k_bt_prolong(const int4 *__restrict__ cols
       return v;
     };
     const long long row0 = (long long)ya * N + x;
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;  // fine values of planes 2Z, 2Z+1 (rows ya, ya+1)
-    if (in) f0 = ef[row0], f1 = ef[row0 + N], f2 = ef[NN + row0], f3 = ef[NN + row0 + N];
+    // fine values (rows ya, ya+1) of planes 2Z, 2Z+1 (f) and 2Z+2, 2Z+3 (g);
+    // those of step Z+2 are loaded during step Z
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    if (in) {
+      f0 = ef[row0], f1 = ef[row0 + N], f2 = ef[NN + row0], f3 = ef[NN + row0 + N];
+      if (Nc > 1) g0 = ef[2 * NN + row0], g1 = ef[2 * NN + row0 + N], g2 = ef[3 * NN + row0], g3 = ef[3 * NN + row0 + N];
+    }
+    const float *enext = ef + 4 * NN + row0;  // plane 2Z+4 at step Z
+    float *eout = ef + row0;                  // plane 2Z at step Z
     __syncthreads();  // the previous column's coarse planes are no longer read
     if (t < PPL) {
       sc[0][t] = load_c(0);
@@ -551,31 +575,37 @@ __global__ void __launch_bounds__(CT) k_bt_prolong(const int4 *__restrict__ cols
     }
     float nxt = load_c(2);
     __syncthreads();
-    for (int Z = 0; Z < Nc; ++Z) {
-      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;  // the next step's fine values
-      if (in && Z + 1 < Nc) {
-        const long long b = (long long)(2 * Z + 2) * NN + row0;
-        g0 = ef[b], g1 = ef[b + N], g2 = ef[b + NN], g3 = ef[b + NN + N];
+    // steps Z = Zb + i, unrolled by the four slots so that every slot index
+    // is a constant (Zb is a multiple of 4)
+    for (int Zb = 0; Zb < Nc; Zb += 4) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int Z = Zb + i;
+        if (Z >= Nc) break;
+        float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
+        if (in && Z + 2 < Nc) h0 = enext[0], h1 = enext[N], h2 = enext[NN], h3 = enext[NN + N];
+        enext += 2 * NN;
+        if (in) {
+          const float *cz = sc[i & 3];
+          const float c = cz[qc], cxn = cz[qc + sx];
+          const float c_lo = (Z > 0) ? sc[(i - 1) & 3][qc] : 0.f;  // fine plane 2Z looks to Z-1
+          const float c_hi = (Z + 1 < Nc) ? sc[(i + 1) & 3][qc] : 0.f;
+          const float wz_lo = (Z == 0) ? ww(4) : 0.f, wz_hi = (Z == Nc - 1) ? ww(5) : 0.f;
+          const float cym = cz[qc - PX], cyp = cz[qc + PX];
+          // (c + c_x + c_y + c_z) with the wall ghosts, for the four fine cells
+          eout[0] = f0 + 0.25f * fmaf(wxy0 + wz_lo, c, ((c + cxn) + cym) + c_lo);
+          eout[N] = f1 + 0.25f * fmaf(wxy1 + wz_lo, c, ((c + cxn) + cyp) + c_lo);
+          eout[NN] = f2 + 0.25f * fmaf(wxy0 + wz_hi, c, ((c + cxn) + cym) + c_hi);
+          eout[NN + N] = f3 + 0.25f * fmaf(wxy1 + wz_hi, c, ((c + cxn) + cyp) + c_hi);
+        }
+        eout += 2 * NN;
+        __syncthreads();  // plane Z-2's slot is free
+        if (t < PPL) sc[(i + 2) & 3][t] = nxt;
+        nxt = load_c(Z + 3);
+        __syncthreads();
+        f0 = g0, f1 = g1, f2 = g2, f3 = g3;
+        g0 = h0, g1 = h1, g2 = h2, g3 = h3;
       }
-      if (in) {
-        const float *cz = sc[Z & 3];
-        const float c = cz[qc], cxn = cz[qc + sx];
-        const float c_lo = (Z > 0) ? sc[(Z - 1) & 3][qc] : 0.f;  // fine plane 2Z looks to Z-1
-        const float c_hi = (Z + 1 < Nc) ? sc[(Z + 1) & 3][qc] : 0.f;
-        const float wz_lo = (Z == 0) ? ww(4) : 0.f, wz_hi = (Z == Nc - 1) ? ww(5) : 0.f;
-        const float cym = cz[qc - PX], cyp = cz[qc + PX];
-        const long long b = (long long)(2 * Z) * NN + row0;
-        // (c + c_x + c_y + c_z) with the wall ghosts, for the four fine cells
-        ef[b] = f0 + 0.25f * fmaf(wxy0 + wz_lo, c, ((c + cxn) + cym) + c_lo);
-        ef[b + N] = f1 + 0.25f * fmaf(wxy1 + wz_lo, c, ((c + cxn) + cyp) + c_lo);
-        ef[b + NN] = f2 + 0.25f * fmaf(wxy0 + wz_hi, c, ((c + cxn) + cym) + c_hi);
-        ef[b + NN + N] = f3 + 0.25f * fmaf(wxy1 + wz_hi, c, ((c + cxn) + cyp) + c_hi);
-      }
-      __syncthreads();  // plane Z-2's slot is free
-      if (t < PPL) sc[(Z + 2) & 3][t] = nxt;
-      nxt = load_c(Z + 3);
-      __syncthreads();
-      f0 = g0, f1 = g1, f2 = g2, f3 = g3;
     }
   }
 }
