@@ -149,6 +149,29 @@ def test_batch_column_restriction_on_full_waves():
     b.close()
 
 
+def test_batch_column_restriction_scalar_copies():
+    """Grids of side 30 (N % 4 != 0) stage their planes with 4-byte copies;
+    enough of them (two columns each) that level 0 gets the column
+    restriction."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n30 = -(-4 * sms // 2)
+    sides = [30] * n30
+    b, rhos = make_batch(sides, seed_blobs=9, keep={0, n30 // 2, n30 - 1})
+    b.set_schedule(0, 4)
+    rc, _, rel = b.solve(1e-9, 40)
+    assert rc == 0 and np.all(rel <= 1e-9)
+    ref = b.phi.clone()
+    b.set_schedule(4, 4)
+    b.phi.zero_()
+    rc, _, rel = b.solve(1e-9, 40)
+    assert rc == 0 and np.all(rel <= 1e-9)
+    d = (b.phi - ref).abs().max().item() / ref.abs().max().item()
+    assert d <= 1e-7
+    check(b, rhos, (0, n30 // 2, n30 - 1), 1e-6)
+    b.close()
+
+
 def test_batch_rejects_too_large_coarsest():
     import paper_1708_08434_gb300 as pkg
     with pytest.raises(pkg.SmError):
