@@ -873,6 +873,7 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
   }
 }
 
+constexpr int OUTER0_BLOCKS = 4;  // resident blocks per SM (64 registers a thread)
 // Residual of phi = 0 on the finest grid of every solve flagged in `active`
 // (the denominators of the relative residual): r0 = f - L0, where L0 has
 // only the Dirichlet ghosts 2g of wall faces.  A cell with no Dirichlet face
@@ -881,7 +882,7 @@ __global__ void __launch_bounds__(CT, 5) k_bt_outer(const int4 *__restrict__ col
 // kernels give the same bits for a potential that is all +0.  Also flags
 // (nz) the solves whose stored potential is not all +0 and raises emax to
 // the largest exponent field of the stored potential.
-__global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols, int ncols,
+__global__ void __launch_bounds__(CT, OUTER0_BLOCKS) k_bt_outer0(const int4 *__restrict__ cols, int ncols,
                                                   const BSolve *__restrict__ tab,
                                                   const unsigned char *__restrict__ active,
                                                   const double *__restrict__ phi,
@@ -889,7 +890,7 @@ __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols,
                                                   unsigned long long *__restrict__ num,
                                                   unsigned *__restrict__ nz, unsigned *__restrict__ emax) {
   __shared__ unsigned long long red[CT / 32];
-  const int t = threadIdx.x, tx = t % CX, ty2 = 2 * (t / CX);
+  const int t = threadIdx.x;
   for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
     const int4 C = cols[it];
     if (!active[C.x]) continue;  // uniform per block
@@ -897,34 +898,64 @@ __global__ void __launch_bounds__(CT) k_bt_outer0(const int4 *__restrict__ cols,
     const int N = S.N[0];
     const long long o64 = S.off64, o32 = S.off[0], NN = (long long)N * N;
     const double inv_h2 = S.inv_h2;
-    const int x = C.y * CX + tx, ya = C.z * CY + ty2;
+    // this thread's cells: (x, y) and (x+1, y) of every plane
+    const int x = C.y * CX + 2 * (t % (CX / 2)), y = C.z * CY + t / (CX / 2);
     unsigned long long m = 0;
     unsigned nzb = 0, em = 0;
-    // four planes per step: their loads are in flight together
+    // in-plane Dirichlet ghosts of the two cells: ((g0 + g1) + (g2 + g3)),
+    // the first part of the wall sum, which does not change with the plane
+    bool wxy[2];
+    double sxy[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const bool w0 = x + u == 0 && bc.type[0], w1 = x + u == N - 1 && bc.type[1];
+      const bool w2 = y == 0 && bc.type[2], w3 = y == N - 1 && bc.type[3];
+      wxy[u] = w0 | w1 | w2 | w3;
+      const double g0 = w0 ? bc.g2[0] - 0.0 : 0.0, g1 = w1 ? bc.g2[1] - 0.0 : 0.0;
+      const double g2 = w2 ? bc.g2[2] - 0.0 : 0.0, g3 = w3 ? bc.g2[3] - 0.0 : 0.0;
+      sxy[u] = (g0 + g1) + (g2 + g3);
+    }
+    const bool in = x < N && y < N, vec = (N & 1) == 0;  // N even: both cells or neither, 16-byte aligned
+    const double *pz = phi + o64 + (long long)y * N + x, *fz = f64 + o64 + (long long)y * N + x;
+    float *rz = f32 + o32 + (long long)y * N + x;
+    // r of one cell from f, with the plane's wall terms (w4, w5)
+    auto resid = [&](int u, double f, bool w4, bool w5) {
+      double r = f;
+      if (wxy[u] | w4 | w5) {
+        const double g4 = w4 ? bc.g2[4] - 0.0 : 0.0, g5 = w5 ? bc.g2[5] - 0.0 : 0.0;
+        const double sw = sxy[u] + (g4 + g5);
+        r = fma(-fma(-6.0, 0.0, sw), inv_h2, f);
+      }
+      return (unsigned long long)__double_as_longlong(r);
+    };
+    auto take = [&](double v, unsigned long long rb) {
+      nzb |= (unsigned)(__double2hiint(v) | __double2loint(v));
+      em = max(em, expo_of(v));
+      const unsigned long long a = rb & 0x7fffffffffffffffull;
+      m = a > m ? a : m;
+    };
+    if (in) {
+      // four planes per step: their loads are in flight together
 #pragma unroll 4
-    for (int p = 0; p < N; ++p) {
+      for (int p = 0; p < N; ++p) {
+        const bool w4 = p == 0 && bc.type[4], w5 = p == N - 1 && bc.type[5];
+        const long long at = p * NN;
+        if (vec) {
+          const double2 v = *reinterpret_cast<const double2 *>(pz + at);
+          const double2 f = *reinterpret_cast<const double2 *>(fz + at);
+          const unsigned long long r0 = resid(0, f.x, w4, w5), r1 = resid(1, f.y, w4, w5);
+          *reinterpret_cast<float2 *>(rz + at) = make_float2(cvt_bits_f32_rn(r0), cvt_bits_f32_rn(r1));
+          take(v.x, r0);
+          take(v.y, r1);
+        } else {
 #pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        const int y = ya + o;
-        if (x >= N || y >= N) continue;
-        const long long at = p * NN + (long long)y * N + x;
-        const double v = phi[o64 + at], f = f64[o64 + at];
-        nzb |= (unsigned)(__double2hiint(v) | __double2loint(v));
-        em = max(em, expo_of(v));
-        const bool w[6] = {x == 0 && bc.type[0], x == N - 1 && bc.type[1], y == 0 && bc.type[2],
-                           y == N - 1 && bc.type[3], p == 0 && bc.type[4], p == N - 1 && bc.type[5]};
-        double r = f;
-        if (w[0] | w[1] | w[2] | w[3] | w[4] | w[5]) {
-          double g[6];
-#pragma unroll
-          for (int q = 0; q < 6; ++q) g[q] = w[q] ? bc.g2[q] - 0.0 : 0.0;
-          const double s = ((g[0] + g[1]) + (g[2] + g[3])) + (g[4] + g[5]);
-          r = fma(-fma(-6.0, 0.0, s), inv_h2, f);
+          for (int u = 0; u < 2; ++u)
+            if (x + u < N) {
+              const unsigned long long r = resid(u, fz[at + u], w4, w5);
+              rz[at + u] = cvt_bits_f32_rn(r);
+              take(pz[at + u], r);
+            }
         }
-        const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
-        f32[o32 + at] = cvt_bits_f32_rn(rb);
-        const unsigned long long a = rb & 0x7fffffffffffffffull;
-        m = a > m ? a : m;
       }
     }
 #pragma unroll

@@ -49,7 +49,7 @@ def check(b, rhos, sel, bound):
 
 
 def test_batch_uneven_sizes_against_spectral():
-    sides = [32, 40, 48, 56, 24, 16, 8, 72, 88, 64]
+    sides = [32, 40, 48, 56, 24, 16, 8, 72, 88, 64, 15]   # 15: odd, scalar loads
     b, rhos = make_batch(sides)
     rc, cyc, rel = b.solve(1e-8, 40)
     assert rc == 0 and np.all(rel <= 1e-8)
