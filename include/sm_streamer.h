@@ -367,7 +367,7 @@ int sm_batch_solve(sm_batch *b, double tol, int max_cycles, int *cycles, double 
  * tiles of 8x8x8, 16x8x4, 32x4x4, 32x8x2 coarse cells; 4: one block per
  * 32x16-cell fine column marching the fine planes, the sweep's columns, on
  * levels with at least four columns per SM, 8x8x8 tiles on the others) and
- * grid size (2, 4, 8 blocks per SM), keeps the fastest; leaves phi = 0.
+ * grid size (2, 4, 8, 16, 32 blocks per SM), keeps the fastest; leaves phi = 0.
  * Out: the chosen shape index, blocks per SM and its time in ms.
  * sm_batch_set_schedule sets both directly (SM_EINVAL outside 0..4 and
  * 1..64). */
