@@ -881,8 +881,11 @@ constexpr int OUTER0_BLOCKS = 4;  // resident blocks per SM (64 registers a thre
 // (the denominators of the relative residual): r0 = f - L0, where L0 has
 // only the Dirichlet ghosts 2g of wall faces.  A cell with no Dirichlet face
 // takes f with no FP64 work (-(+0) * h^-2 + f = f bit for bit); the others
-// evaluate the same expression as k_bt_outer with every value +0, so both
-// kernels give the same bits for a potential that is all +0.  Also flags
+// take r = f - S h^-2 with one rounding, S the FP64 sum of their ghosts.
+// k_bt_outer gives the same bits for a potential that is all +0 whenever
+// each 2g is a multiple of its fixed-point unit and S is exact (so for
+// plate values such as 0 and 2g = 2); otherwise the two differ by the
+// rounding of S and of the fixed-point map, both valid residuals.  Also flags
 // (nz) the solves whose stored potential is not all +0 and raises emax to
 // the largest exponent field of the stored potential.
 __global__ void __launch_bounds__(CT, OUTER0_BLOCKS) k_bt_outer0(const int4 *__restrict__ cols, int ncols,
