@@ -170,3 +170,57 @@ def test_heun_growth_closed_form():
     g = 1.0 + a + 0.5 * a * a
     assert np.max(np.abs(ne / 1e6 / g - 1.0)) <= 1e-12
     assert np.max(np.abs(ni / 1e6 / g - 1.0)) <= 1e-12
+
+
+def test_density_step_moves_by_first_order_upwind():
+    """The Koren-limited upwind face value (Eq. 6-7) reduces to first-order
+    upwinding at a discontinuity, where the limiter vanishes (a slope is
+    zero or changes sign).  A step n_e = 1 below z = L/2, 0 above, in a
+    uniform field with no diffusion and no source, after one Euler stage:
+    the first cell above the step holds exactly v dt / h and every other
+    cell is unchanged (electrons drift against E, here towards +z)."""
+    V = 1e4
+    dom, o, tab = plate_setup("uniform32", V)      # uniform field, no charge
+    tab = dict(tab, diff=np.zeros_like(tab["diff"]))
+    o.set_table(tab)
+    t = o.tables()
+    _, _, z = synth.cell_centres(dom, t["level"], t["ijk"])
+    n0 = (z < 0.5 * dom.length).astype(np.float64)
+    o.set(oracle.NE, n0)
+    o.set(oracle.NI, np.zeros_like(n0))
+    h = dom.h(o.n_levels - 1)
+    v = synth.MOBILITY * V / dom.length
+    dt = 0.25 * h / v
+    o.fluid_stage(dt)
+    lo, hi = o.level_range(o.n_levels - 1)
+    zl = z[lo:hi]
+    first = (zl > 0.5 * dom.length) & (zl < 0.5 * dom.length + h)
+    want = n0[lo:hi].copy()
+    want[first] = 0.25
+    assert first.sum() == 32 * 32
+    assert np.max(np.abs(o.get(oracle.NE)[lo:hi] - want)) <= 1e-13
+
+
+def test_field_exact_on_quadratic_potential():
+    """The cell field (Sec. 2.3) is the mean of each axis's two face fields,
+    a centred difference, exact on quadratics: for phi = a (z - zc)^2 +
+    b (x - xc)^2 the interior cells get |E| = hypot(2 b (x - xc),
+    2 a (z - zc)) to rounding."""
+    dom = synth.workload("uniform32")[0]
+    o = oracle.build_mesh(dom)
+    t = o.tables()
+    x, y, z = synth.cell_centres(dom, t["level"], t["ijk"])
+    a, b, xc, zc = 3.0, -1.5, 0.37, 0.61
+    o.set(oracle.PHI, a * (z - zc) ** 2 + b * (x - xc) ** 2)
+    o.compute_field()
+    lo, hi = o.level_range(o.n_levels - 1)
+    h = dom.h(o.n_levels - 1)
+    n = int(round(dom.length / h))
+    inner = np.ones((hi - lo, 512), bool)
+    for c in (x, y, z):
+        i = np.floor(c[lo:hi] / h).astype(int)
+        inner &= (i >= 1) & (i <= n - 2)
+    want = np.hypot(2 * b * (x[lo:hi] - xc), 2 * a * (z[lo:hi] - zc))
+    got = o.get(oracle.EMAG)[lo:hi]
+    assert inner.sum() == (n - 2) ** 3
+    assert np.max(np.abs(got[inner] - want[inner])) <= 1e-12 * np.max(want)
