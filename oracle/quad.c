@@ -798,6 +798,8 @@ static double koren(double a, double b) {
   return s * m;
 }
 
+double q2_koren(double a, double b) { return koren(a, b); }
+
 static double *fluxp(q2 *o, int b, int a) { return o->flux + (size_t)b * FPB + (size_t)a * (NC + 1) * NC; }
 
 /* Face fluxes of every leaf box, index [a][m][u]: m = 0..8 the face between

@@ -41,6 +41,8 @@ void q2_get(const q2 *o, int var, double *dst);
 void q2_set_table(q2 *o, int n, double e_max, const double *mu, const double *diff,
                   const double *alpha);
 double q2_lookup(const q2 *o, int which, double e);
+/* psi(a/b) b of the Koren limiter (Eq. 7), division-free */
+double q2_koren(double a, double b);
 void q2_charge_rhs(q2 *o, double q, double eps, int use_rho);
 int q2_fmg(q2 *o, double tol, int max_cycles, int nu1, int nu2, double *rel, int *cycles);
 int q2_vcycles(q2 *o, int n, int nu1, int nu2, double *rel);

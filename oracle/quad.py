@@ -61,6 +61,7 @@ def _load():
             "q2_coarse_solve": ([P], None),
             "q2_refine_flags": ([P, D, D, D, D, I, P], None),
             "q2_lookup": ([P, I, D], D),
+            "q2_koren": ([D, D], D),
             "q2_regrid": ([P, P, ip, ip, ip], I),
         }
         for name, (args, res) in sig.items():
@@ -74,6 +75,11 @@ def _load():
 
 def set_threads(n: int) -> int:
     return _load().q2_set_threads(int(n))
+
+
+def koren(a: float, b: float) -> float:
+    """psi(a/b) b of the Koren limiter (Eq. 7), as the 2-D oracle applies it."""
+    return _load().q2_koren(float(a), float(b))
 
 
 def _ptr(a):

@@ -224,3 +224,11 @@ def test_field_exact_on_quadratic_potential():
     got = o.get(oracle.EMAG)[lo:hi]
     assert inner.sum() == (n - 2) ** 3
     assert np.max(np.abs(got[inner] - want[inner])) <= 1e-12 * np.max(want)
+
+
+def test_dt_diffusion_limit_without_field():
+    """No field: the advection terms vanish and, with a tiny n_e, Sec. 2.4's
+    limit is the diffusion one, dt = 0.9 h^2 / (6 D) in three dimensions."""
+    dom, o, tab = plate_setup("uniform32", 0.0, n=1e6)
+    h = dom.h(o.n_levels - 1)
+    assert o.dt_limit(Q, EPS0) == pytest.approx(0.9 * h ** 2 / (6.0 * synth.DIFFUSION), rel=1e-12)

@@ -353,3 +353,100 @@ def test_heun_growth_closed_form(geom):
     lo, hi = o.level_range(o.n_levels - 1)
     got = o.get(quad.NE)[lo:hi] / 1e12
     assert np.max(np.abs(got - (1 + a + a * a / 2))) <= 1e-9
+
+
+def test_koren_matches_paper_form_and_textbook_limiter():
+    """The 2-D oracle's limiter: psi(a/b) b with psi as printed in Sec. 2.3
+    (division form), the textbook Koren limiter in the reciprocal variable,
+    and the midpoint on linear data."""
+    from test_oracle_fluid import koren_textbook, psi_paper
+    rng = np.random.default_rng(2)
+    for a, b in rng.standard_normal((2000, 2)) * 10.0 ** rng.integers(-3, 4, (2000, 2)):
+        assert quad.koren(a, b) == pytest.approx(psi_paper(a / b) * b, rel=1e-14, abs=1e-300)
+    assert quad.koren(1.0, 0.0) == 0.0 and quad.koren(0.0, 0.0) == 0.0
+    for x in np.linspace(0.01, 10.0, 499):
+        assert quad.koren(x, 1.0) == pytest.approx(0.5 * x * koren_textbook(1.0 / x), rel=1e-14)
+    for slope in (0.3, -2.0, 7.5):
+        assert quad.koren(slope, slope) == pytest.approx(0.5 * slope, rel=1e-15)
+
+
+def uniform_quad(geom, V, alpha=0.0, diff=None):
+    """One uniform level of 32^2 cells, phi = 0 / V on the z faces, a
+    neutral uniform charge (so the field is V/L along z), the coefficient
+    table with the given alpha (and D when given)."""
+    L = 0.016
+    dom = synth.Domain2(L, 4, 0, geom, bc_val=(0.0, 0.0, 0.0, V))
+    o = table_quad(dom, None, alpha=alpha)
+    if diff is not None:
+        tab = synth.coefficient_table()
+        tab["alpha"] = np.full_like(tab["alpha"], alpha)
+        tab["diff"] = np.full_like(tab["diff"], diff)
+        o.set_table(tab)
+    nb = o.n_boxes
+    o.set(quad.NE, np.full((nb, 64), 1e10))
+    o.set(quad.NI, np.full((nb, 64), 1e10))
+    o.charge_rhs(Q, EPS0)
+    o.fmg(1e-13, 40)
+    o.compute_field()
+    return dom, o
+
+
+@pytest.mark.parametrize("geom", [CART, AXI])
+def test_density_step_moves_by_first_order_upwind(geom):
+    """Koren upwinding reduces to first-order upwinding at a discontinuity
+    (the limiter vanishes there): a step n_e = 1 below z = L/2, 0 above, in
+    a uniform field along z with no diffusion and no source puts exactly
+    v dt / h into the first cell above the step after one Euler stage and
+    leaves every other cell unchanged (the axial fluxes carry no radial
+    weight)."""
+    V = 1e4
+    dom, o = uniform_quad(geom, V, diff=0.0)
+    t = o.tables()
+    _, z = synth.cell_centres2(dom, t["level"], t["ij"])
+    n0 = (z < 0.5 * dom.length).astype(np.float64)
+    o.set(quad.NE, n0)
+    o.set(quad.NI, np.zeros_like(n0))
+    h = dom.h(o.n_levels - 1)
+    v = synth.MOBILITY * V / dom.length
+    o.fluid_stage(0.25 * h / v)
+    lo, hi = o.level_range(o.n_levels - 1)
+    zl = z[lo:hi]
+    first = (zl > 0.5 * dom.length) & (zl < 0.5 * dom.length + h)
+    want = n0[lo:hi].copy()
+    want[first] = 0.25
+    assert first.sum() == 32
+    assert np.max(np.abs(o.get(quad.NE)[lo:hi] - want)) <= 1e-13
+
+
+def test_dt_diffusion_limit_without_field():
+    """No field: the advection terms vanish and, with a tiny n_e, Sec. 2.4's
+    limit is the diffusion one, dt = 0.9 h^2 / (4 D) in two dimensions."""
+    dom, o = uniform_quad(AXI, 0.0)
+    h = dom.h(o.n_levels - 1)
+    assert o.dt_limit(Q, EPS0) == pytest.approx(0.9 * h ** 2 / (4.0 * synth.DIFFUSION), rel=1e-12)
+
+
+@pytest.mark.parametrize("geom", [CART, AXI])
+def test_field_exact_on_quadratic_potential(geom):
+    """The cell field is the mean of each axis's two face fields, a centred
+    difference, exact on quadratics in both geometries: phi = a (z - zc)^2
+    + b (x - xc)^2 gives |E| = hypot(2 b (x - xc), 2 a (z - zc)) in the
+    interior cells."""
+    dom, o = uniform_quad(geom, 0.0)
+    t = o.tables()
+    x, z = synth.cell_centres2(dom, t["level"], t["ij"])
+    L = dom.length
+    a, b, xc, zc = 3.0 / L, -1.5 / L, 0.37 * L, 0.61 * L
+    o.set(quad.PHI, a * (z - zc) ** 2 + b * (x - xc) ** 2)
+    o.compute_field()
+    lo, hi = o.level_range(o.n_levels - 1)
+    h = dom.h(o.n_levels - 1)
+    n = int(round(L / h))
+    inner = np.ones((hi - lo, 64), bool)
+    for c in (x, z):
+        i = np.floor(c[lo:hi] / h).astype(int)
+        inner &= (i >= 1) & (i <= n - 2)
+    want = np.hypot(2 * b * (x[lo:hi] - xc), 2 * a * (z[lo:hi] - zc))
+    got = o.get(quad.EMAG)[lo:hi]
+    assert inner.sum() == (n - 2) ** 2
+    assert np.max(np.abs(got[inner] - want[inner])) <= 1e-12 * np.max(want)
