@@ -44,7 +44,8 @@ def test_spectral_matches_c_oracle_multigrid(n):
     assert np.abs(mg - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("n,bct", [(40, (0, 0, 1, 1, 1, 0)), (24, (1, 0, 0, 0, 1, 1)), (13, (1, 1, 1, 1, 1, 1))])
+@pytest.mark.parametrize("n,bct", [(40, (0, 0, 1, 1, 1, 0)), (24, (1, 0, 0, 0, 1, 1)), (13, (1, 1, 1, 1, 1, 1)),
+                                   (20, (0, 1, 1, 0, 0, 1))])   # last: Neumann low, Dirichlet high
 def test_spectral_reproduces_eigenvector(n, bct):
     i = np.arange(n) + 0.5
     def vec(lo, hi, p):
