@@ -201,7 +201,8 @@ def test_regrid_data_prolongation_and_kept_boxes():
     lin = lambda zz: g0 + (g1 - g0) * (zz - dom.origin[2]) / dom.length   # matches the z walls
     o.set(oracle.PHI, lin(z))
     rng = np.random.default_rng(7)
-    ne = 1e18 * (1.0 + rng.random((o.n_boxes, 512)))
+    # densities spread over orders of magnitude, so that the 2c limit acts
+    ne = 1e18 * rng.random((o.n_boxes, 512)) ** 4
     o.set(oracle.NE, ne)
     o.set(oracle.NI, 2.0 * ne)
     f = o.refine_flags(C0, C1, C0D, DXD, BUF)
@@ -225,7 +226,7 @@ def test_regrid_data_prolongation_and_kept_boxes():
     assert nr > 0
     t2 = o.tables()
     new = {v: o.get(v) for v in old}
-    n_new = 0
+    n_new = n_lim = 0
     for b in range(o.n_boxes):
         key = (int(t2["level"][b]), *map(int, t2["ijk"][b]))
         if key in oldkey:
@@ -250,8 +251,10 @@ def test_regrid_data_prolongation_and_kept_boxes():
                 want = 0.25 * s
                 if kind == "density" and want > 2.0 * cval:
                     want = 2.0 * cval
+                    n_lim += 1
                 assert new[v][b, c] == want, (key, c, v)
     assert n_new == 8 * nr
+    assert n_lim > 0
     # linear potential reproduced exactly in the new boxes
     x2, y2, z2 = synth.cell_centres(dom, t2["level"], t2["ijk"])
     assert np.abs(new[oracle.PHI] - lin(z2)).max() <= 1e-12 * max(abs(g0), abs(g1))
@@ -326,4 +329,56 @@ def test_regrid_derefinement_blocked_by_nesting():
     f[lo:hi] = -1
     assert o.regrid(f)[:2] == (0, 8)
     assert o.n_levels == 2
+    brute_force_check(o.tables(), dom.lbase + 1)
+
+
+def test_derefined_box_holds_the_mean_of_its_children():
+    """Densities are restricted before the mesh changes: a derefined box
+    becomes a leaf holding, per cell, the mean of its eight child cells."""
+    dom = synth.Domain(length=1.0, nb=2, max_level=3)
+    o = oracle.Oracle(dom)
+    f = np.zeros(o.n_boxes, np.int8)
+    f[o.level_range(1)[0]] = 1
+    assert o.regrid(f)[0] == 1
+    rng = np.random.default_rng(11)
+    o.set(oracle.NE, rng.random((o.n_boxes, 512)))
+    o.set(oracle.NI, np.zeros((o.n_boxes, 512)))
+    t = o.tables()
+    p = o.level_range(1)[0]
+    kids = t["child"][p]
+    ne = o.get(oracle.NE)
+    li, lj, lk = local_ijk(np.arange(512))
+    want = np.zeros(512)
+    for c in range(512):
+        I, J, K = li[c], lj[c], lk[c]
+        kid = kids[(I >> 2) + 2 * (J >> 2) + 4 * (K >> 2)]
+        cells = [ne[kid, (2 * (I & 3) + di) + 8 * (2 * (J & 3) + dj) + 64 * (2 * (K & 3) + dk)]
+                 for dk in (0, 1) for dj in (0, 1) for di in (0, 1)]
+        want[c] = np.mean(cells)
+    f = np.zeros(o.n_boxes, np.int8)
+    f[kids] = -1
+    assert o.regrid(f)[:2] == (0, 1)
+    t2 = o.tables()
+    b = [i for i in range(o.n_boxes) if t2["level"][i] == 1 and tuple(t2["ijk"][i]) == tuple(t["ijk"][p])][0]
+    assert t2["child"][b, 0] < 0
+    assert np.allclose(o.get(oracle.NE)[b], want, rtol=1e-14, atol=0)
+
+
+def test_derefinement_blocked_by_refinement_in_the_same_call():
+    """A box whose children touch a box refined in the same call keeps its
+    children (the new level would otherwise border a coarse leaf); the
+    refinement goes ahead."""
+    dom = synth.Domain(length=1.0, nb=2, max_level=3)
+    o = oracle.Oracle(dom)
+    f = np.zeros(o.n_boxes, np.int8)
+    lo, hi = o.level_range(1)
+    f[lo:hi] = 1
+    assert o.regrid(f)[0] == 8
+    t = o.tables()
+    at = {(int(t["level"][b]), *map(int, t["ijk"][b])): b for b in range(o.n_boxes)}
+    a = at[(1, 0, 0, 0)]
+    f = np.zeros(o.n_boxes, np.int8)
+    f[t["child"][a]] = -1                 # derefine the first level-1 box
+    f[at[(2, 2, 0, 0)]] = 1               # refine a level-2 box touching its children
+    assert o.regrid(f)[:2] == (1, 0)
     brute_force_check(o.tables(), dom.lbase + 1)
