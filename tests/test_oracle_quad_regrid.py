@@ -298,3 +298,60 @@ def test_regrid_derefinement_blocked_by_nesting():
     assert o.regrid(f)[:2] == (0, 4)
     assert o.n_levels == 2
     check_tables(o.tables(), 1)
+
+
+@pytest.mark.parametrize("geom", [synth.CARTESIAN, synth.AXISYMMETRIC])
+def test_derefined_box_holds_the_content_of_its_children(geom):
+    """Densities are restricted before the mesh changes: a derefined box
+    becomes a leaf whose cells hold the content of their four child cells,
+    the mean weighted by the cell volumes (the centre radii in cylindrical
+    coordinates)."""
+    o = quad.Quad(synth.Domain2(1.0, 2, 3, geom))
+    f = np.zeros(o.n_boxes, np.int8)
+    p = o.level_range(1)[0]
+    f[p] = 1
+    assert o.regrid(f)[0] == 1
+    rng = np.random.default_rng(12)
+    o.set(quad.NE, rng.random((o.n_boxes, 64)))
+    o.set(quad.NI, np.zeros((o.n_boxes, 64)))
+    t = o.tables()
+    kids = t["child"][p]
+    ne = o.get(quad.NE)
+    want = np.zeros(64)
+    for c in range(64):
+        I, J = c % 8, c // 8
+        kid = kids[(I >> 2) + 2 * (J >> 2)]
+        s = ws = 0.0
+        for dj in (0, 1):
+            for di in (0, 1):
+                i, j = 2 * (I & 3) + di, 2 * (J & 3) + dj
+                gx = int(t["ij"][kid, 0]) * 8 + i
+                w = gx + 0.5 if geom == synth.AXISYMMETRIC else 1.0
+                s += w * ne[kid, i + 8 * j]
+                ws += w
+        want[c] = s / ws
+    f = np.zeros(o.n_boxes, np.int8)
+    f[kids] = -1
+    assert o.regrid(f)[:2] == (0, 1)
+    t2 = o.tables()
+    b = [i for i in range(o.n_boxes) if t2["level"][i] == 1 and tuple(t2["ij"][i]) == tuple(t["ij"][p])][0]
+    assert t2["child"][b, 0] < 0
+    assert np.allclose(o.get(quad.NE)[b], want, rtol=1e-14, atol=0)
+
+
+def test_derefinement_blocked_by_refinement_in_the_same_call():
+    """A box whose children touch a box refined in the same call keeps its
+    children; the refinement goes ahead."""
+    o = quad.Quad(synth.Domain2(1.0, 2, 3, synth.CARTESIAN))
+    f = np.zeros(o.n_boxes, np.int8)
+    lo, hi = o.level_range(1)
+    f[lo:hi] = 1
+    assert o.regrid(f)[0] == 4
+    t = o.tables()
+    at = {(int(t["level"][b]), int(t["ij"][b, 0]), int(t["ij"][b, 1])): b for b in range(o.n_boxes)}
+    a = at[(1, 0, 0)]
+    f = np.zeros(o.n_boxes, np.int8)
+    f[t["child"][a]] = -1               # derefine the first level-1 box
+    f[at[(2, 2, 0)]] = 1                # refine a level-2 box touching its children
+    assert o.regrid(f)[:2] == (1, 0)
+    check_tables(o.tables(), 1)
