@@ -376,12 +376,16 @@ int sm_batch_set_schedule(sm_batch *b, int shape, int grid_mult);
 /* Time one kernel class of the batched cycle over all solves: `reps`
  * back-to-back launches between CUDA events on the batch stream, after one
  * warm-up launch.  kclass: 0 level-0 red-black sweep, 1 FP64 outer
- * residual, 2 level-0 prolongation, 3 level-0 -> 1 restriction.  Out (may
- * be NULL): microseconds per launch, algorithmic bytes per launch
- * (compulsory traffic: 12, 20, 8.5, 8.5 B per cell of the level) and FP64
- * operations per launch (7 per cell for class 1, else 0).  Overwrites the
- * error arrays and may leave phi changed (class 1 leaves it as it is).
- * Errors: SM_EINVAL, SM_ESTATE (no arena; no level below the finest). */
+ * residual, 2 level-0 prolongation, 3 level-0 -> 1 restriction in the
+ * current schedule (fine columns under schedule 4 when level 0 has at
+ * least four columns per SM, else coarse-cell tiles).  Out (may be NULL):
+ * microseconds per launch, algorithmic bytes per launch (compulsory
+ * traffic: 12, 20, 8.5, 8.5 B per cell of the level) and FP64-pipe
+ * operations per launch (2 per cell for class 1: the multiply-add and the
+ * int64 -> binary64 conversion of the fixed-point stencil sum; else 0).
+ * Overwrites the error arrays and may leave phi changed (class 1 leaves it
+ * as it is).  Errors: SM_EINVAL, SM_ESTATE (no arena; no level below the
+ * finest). */
 int sm_batch_kernel_bench(sm_batch *b, int kclass, int reps, double *us_per_launch, double *bytes_per_launch,
                           double *fp64_per_launch);
 /* Solves as one CUDA graph with the loop on the device (default) or as the
