@@ -339,8 +339,11 @@ int sm_launch_count(const sm_ctx *ctx, long long *n);
  * per-solve FP64 defect-correction loop; every level of all solves is one
  * grid-stride launch per phase over a work list (32x16-cell z-marching
  * columns for a whole red-black sweep, the prolongation and the FP64
- * residual, small 3-D tiles for the restriction); a batched solve is one CUDA
- * graph whose loop runs on the device; converged solves are masked out.
+ * residual; the same columns or small 3-D tiles for the restriction, as
+ * the schedule below chooses); the exact coarse solves of each level run
+ * on a stream of their own, forked from the cycle and joined before the
+ * prolongation from that level.  A batched solve is one CUDA graph whose
+ * loop runs on the device; converged solves are masked out.
  * Memory: sm_batch_arena_size / sm_batch_bind_arena as for sm_ctx.
  * Arrays (device, through sm_batch_ptrs): phi and rhs, FP64, the grids of
  * all solves one after another at the returned offsets (each a multiple of
