@@ -202,3 +202,23 @@ def test_charge_rhs_sign_and_scale():
     phi = o.get(oracle.PHI)[lo:hi]
     assert phi.min() > 0
     assert np.max(np.abs(phi - exact[lo:hi])) <= 2e-3 * rho0 * dom.length ** 2 / (8 * synth.EPS0)
+
+
+def test_fmg_does_not_depend_on_the_starting_potential():
+    """Full multigrid (Sec. 2.1.2) starts each finer level from the
+    interpolated coarse solution, replacing whatever the level held: the
+    result from a random starting potential equals the one from zero bit
+    for bit."""
+    dom, st = synth.workload("streamer_small")
+    out = []
+    for seed in (None, 5):
+        o = oracle.build_mesh(dom, st)
+        nb = o.n_boxes
+        rng = np.random.default_rng(9)
+        o.set(oracle.RHO, rng.standard_normal((nb, 512)))
+        o.charge_rhs(1.0, 1.0, True)
+        start = np.zeros((nb, 512)) if seed is None else np.random.default_rng(seed).standard_normal((nb, 512))
+        o.set(oracle.PHI, start)
+        o.fmg(1e-10, 40)
+        out.append(o.get(oracle.PHI))
+    assert np.array_equal(out[0], out[1])
