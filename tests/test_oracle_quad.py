@@ -450,3 +450,21 @@ def test_field_exact_on_quadratic_potential(geom):
     got = o.get(quad.EMAG)[lo:hi]
     assert inner.sum() == (n - 2) ** 2
     assert np.max(np.abs(got[inner] - want[inner])) <= 1e-12 * np.max(want)
+
+
+@pytest.mark.parametrize("name", ["axi_small", "cart_small"])
+def test_fmg_does_not_depend_on_the_starting_potential(name):
+    """Each finer level of the FMG ladder starts from the interpolated coarse
+    solution, replacing what it held: a random starting potential gives
+    the same bits as zero."""
+    dom, st = synth.workload2(name)
+    out = []
+    for seed in (None, 5):
+        o = quad.build_mesh(dom, st)
+        nb = o.n_boxes
+        o.set(quad.RHO, np.random.default_rng(9).standard_normal((nb, 64)))
+        o.charge_rhs(1.0, 1.0, True)
+        o.set(quad.PHI, np.zeros((nb, 64)) if seed is None else np.random.default_rng(seed).standard_normal((nb, 64)))
+        o.fmg(1e-10, 40)
+        out.append(o.get(quad.PHI))
+    assert np.array_equal(out[0], out[1])
