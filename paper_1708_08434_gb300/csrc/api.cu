@@ -60,7 +60,7 @@ struct ArenaPlan {
 struct Layout {
   size_t level, ijk, parent, child, nbr, nbr6, leaf, morton, scan_a, scan_b, count, flags;
   size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, e32, f32, old32, gh32,
-      total;
+      phx, gx, ghx, total;
 };
 
 static Layout plan(int cap, bool mixed) {
@@ -92,6 +92,9 @@ static Layout plan(int cap, bool mixed) {
   L.basis = p.take<double>(3 * 64 + 3 * 8);
   L.tab = p.take<double>(3 * 4096);
   L.dscal = p.take<unsigned long long>(SC_N);
+  L.phx = p.take<long long>(nc);
+  L.gx = p.take<long long>(nc);
+  L.ghx = p.take<long long>((size_t)cap * 6 * FACE);
   if (mixed) {
     L.e32 = p.take<float>(nc);
     L.f32 = p.take<float>(nc);
@@ -212,6 +215,9 @@ extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   ctx->basis = (double *)(a + L.basis);
   ctx->tab = (double *)(a + L.tab);
   ctx->dscal = (unsigned long long *)(a + L.dscal);
+  ctx->phx = (long long *)(a + L.phx);
+  ctx->gx = (long long *)(a + L.gx);
+  ctx->ghx = (long long *)(a + L.ghx);
   if (ctx->cfg.precision == SM_MIXED) {
     ctx->e32 = (float *)(a + L.e32);
     ctx->f32 = (float *)(a + L.f32);

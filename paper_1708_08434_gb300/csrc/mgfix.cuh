@@ -1,0 +1,633 @@
+// mgfix.cuh -- the FP64 solve's multigrid cycle in exact 64-bit fixed point
+// (Sec. 2.1.2: FAS V-cycle, red-black Gauss-Seidel, restriction,
+// prolongation and coarse-to-fine ghosts; included by multigrid.cu after
+// its per-box helpers).
+//
+// During an FP64 solve the potential of every box is held as an integer
+// multiple of one quantum q = 2^(E - 1080).  E is chosen per solve from the
+// largest exponent field among the potential, the Dirichlet ghost
+// constants 2g and every h_l^2 f, plus a margin of FX_MARGIN: every input
+// is then below 2^53 quanta and stored values must stay below 2^55
+// (FX_LIM), which keeps every intermediate sum inside 63 bits.  Sums of
+// neighbours are exact; each operation of the cycle rounds once, to the
+// nearest quantum with ties away from zero:
+//   smoother        phi = (sum of 6 neighbours + 6 G) / 6,
+//                   G = -h^2 f / 6 in quanta (rounded once per rhs),
+//   restriction     phi_c = (sum of 8 children) / 8,
+//   FAS rhs         G_c = (sum over children of (6 G + T) - 2 T_c) / 12,
+//                   T = h^2 L phi in quanta = sum of 6 neighbours - 6 phi,
+//   prolongation    (c + c_x + c_y + c_z) / 4,
+//   coarse-fine     ghost = (2 inner + Ghat) / 6, Ghat = 2c + c_t1 + c_t2.
+// The level-0 solve and the residual norm stay in FP64.  A value that
+// would leave the range sets error bit FX_ERR_OVF; the solve is then run
+// again from its unchanged FP64 inputs with a margin larger by 8.
+//
+// The fixed-point arrays of a box are stored colour by colour: the 256
+// red cells ((i+j+k) even, level-global) first, then the 256 black ones,
+// each half ordered (i/2) + 4j + 32k.  A colour pass of the red-black
+// smoother then reads only the other colour, the G of its own colour and
+// (at walls and refinement faces) its own face cells, and writes its own
+// colour in place: 12 bytes per cell and pass, with every load and store
+// of the box coalesced.
+#pragma once
+
+namespace fx {
+
+constexpr long long FX_LIM = 1ll << 55;     // |stored value| < FX_LIM quanta
+constexpr int FX_MARGIN = 5;                // E = exponent bound + margin
+constexpr int FX_EMIN = 64;                 // keeps q and q/h^2 normal
+constexpr unsigned long long FX_ERR_OVF = 8ull;
+
+__device__ __forceinline__ bool fx_bad(long long x) {
+  return (unsigned long long)(x + FX_LIM) >= (unsigned long long)(2 * FX_LIM);
+}
+
+// t / D rounded to the nearest integer, ties away from zero (D constant)
+template <unsigned D>
+__device__ __forceinline__ long long fx_rdiv(long long t) {
+  const unsigned long long u = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const unsigned long long r = (u + (D >> 1)) / D;
+  return t < 0 ? -(long long)r : (long long)r;
+}
+
+// t / 6 rounded to the nearest integer, ties towards +infinity, for
+// |t| < 1.5 * 2^62: a bias that is a multiple of 6 makes the dividend
+// non-negative, so the division is an unsigned one by a constant
+__device__ __forceinline__ long long fx_div6(long long t) {
+  return (long long)(((unsigned long long)t + (6ull << 60) + 3ull) / 6ull) - (1ll << 60);
+}
+
+// colour-split position of cell (i,j,k) of a box, and of natural cell
+// index c = i + 8j + 64k; natural cell of split position p
+__device__ __forceinline__ int xpos(int i, int j, int k) {
+  return (((i + j + k) & 1) << 8) | (i >> 1) | (j << 2) | (k << 5);
+}
+__device__ __forceinline__ int xsplit(int c) { return xpos(c & 7, (c >> 3) & 7, c >> 6); }
+__device__ __forceinline__ int xcell(int p) {
+  const int k = (p >> 5) & 7, j = (p >> 2) & 7;
+  return 2 * (p & 3) + ((j + k + (p >> 8)) & 1) + 8 * j + 64 * k;
+}
+
+// quantum q = 2^(E - 1080) as a double
+__device__ __forceinline__ double fx_q(int E) { return __longlong_as_double((long long)(E - 57) << 52); }
+
+// nearest multiple of the quantum, in quanta; `bad` set when the value is
+// not below 2^55 quanta (exponent field above E - 3, infinities, NaNs)
+__device__ __forceinline__ long long fx_of(double d, int E, bool &bad) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+  bad |= (int)((bits >> 52) & 0x7ffu) > E - 3;
+  return fix_of_bits(bits, E);
+}
+
+__device__ __forceinline__ int fx_E(const unsigned long long *sc) { return (int)sc[SC_FXE]; }
+__device__ __forceinline__ long long fx_2g(const unsigned long long *sc, int f) {
+  return (long long)sc[SC_FX2G + f];
+}
+
+// one flag per warp; every lane of the warp must call it
+__device__ __forceinline__ void fx_flag(bool bad, unsigned long long *sc) {
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(sc + SC_ERR, FX_ERR_OVF);
+}
+
+// Stage box b of the fixed-point potential v and its six face halos in
+// s[1000] (10^3, one ghost layer): same-level neighbour cells, Dirichlet
+// 2g - inner, Neumann inner, refinement faces (2 inner + Ghat)/6.
+__device__ __forceinline__ void fx_stage(const Grp &g, long long *s, const long long *v, const Nb &nbv,
+                                         const long long *ghx, int b, const Bc &bc, const unsigned long long *sc) {
+  const long long *p = v + (size_t)b * CELLS;
+  long long x[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) x[h] = p[g.t + h * GT];
+  const int slice = g.t >> 6, u = g.t & 7, w = (g.t >> 3) & 7;
+  long long hv[FPS];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f % NSL != slice) continue;
+    const int r = f / NSL;
+    const int nb = nbv.v[r];
+    if (nb >= 0) hv[r] = v[(size_t)nb * CELLS + xsplit(face_cell(f ^ 1, u, w))];
+    else if (nb == -2) hv[r] = ghx[(size_t)(6 * b + f) * FACE + u + NC * w];
+    else hv[r] = bc.type[f] ? fx_2g(sc, f) : 0;
+  }
+  g.sync();  // earlier users of s are done
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) s[s10(xcell(g.t + h * GT))] = x[h];
+  g.sync();
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f % NSL != slice) continue;
+    const int r = f / NSL, a = f >> 1;
+    const int q = s10(face_cell(f, u, w));
+    const int stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
+    const long long inner = s[q];
+    long long gv;
+    if (nbv.v[r] >= 0) gv = hv[r];
+    else if (nbv.v[r] == -1) gv = bc.type[f] ? hv[r] - inner : inner;
+    else gv = fx_div6(2 * inner + hv[r]);
+    s[q + ((f & 1) ? stride : -stride)] = gv;
+  }
+  g.sync();
+}
+
+// h^2 L phi in quanta at staged position q: sum of 6 neighbours - 6 phi
+__device__ __forceinline__ long long fx_T(const long long *s, int q) {
+  return s[q - 1] + s[q + 1] + s[q - 10] + s[q + 10] + s[q - 100] + s[q + 100] - 6 * s[q];
+}
+
+// ---------------------------------------------------------------------------
+// red-black Gauss-Seidel, one colour per pass
+// ---------------------------------------------------------------------------
+
+// One colour of a red-black sweep on box b (Sec. 2.1.2): the cells with
+// (i+j+k) % 2 == color get (sum of 6 neighbours + 6 G)/6 from the other
+// colour's values; the ghosts across walls and refinement faces are
+// evaluated from the updated cell's own current value.  True when a result
+// leaves the fixed-point range.
+__device__ __forceinline__ bool fx_color_box(const Grp &g, long long *s, int b, int color, long long *phx,
+                                             const long long *__restrict__ gx, const long long *__restrict__ ghx,
+                                             const Nb &nbv, const Bc &bc, const unsigned long long *sc) {
+  const size_t base = (size_t)b * CELLS;
+  const int oc = color ^ 1;
+  long long G[RPT], x[RPT];
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    G[h] = gx[base + (color << 8) + g.t + h * GT];
+    x[h] = phx[base + (oc << 8) + g.t + h * GT];
+  }
+  // halo cells next to this colour's face cells: the neighbour's face cell,
+  // or the ghost of the face cell itself
+  const int slice = g.t >> 6, u = g.t & 7, w = (g.t >> 3) & 7;
+  const int cw = (u + w) & 1;
+  long long hv[FPS], inn[FPS];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f % NSL != slice) continue;
+    const int r = f / NSL;
+    hv[r] = 0;
+    inn[r] = 0;
+    if (((cw + ((f & 1) ? 1 : 0)) & 1) != color) continue;  // the face cell has the other colour
+    const int nb = nbv.v[r];
+    if (nb >= 0) {
+      hv[r] = phx[(size_t)nb * CELLS + xsplit(face_cell(f ^ 1, u, w))];
+    } else {
+      inn[r] = phx[base + xsplit(face_cell(f, u, w))];
+      hv[r] = nb == -2 ? ghx[(size_t)(6 * b + f) * FACE + u + NC * w] : (bc.type[f] ? fx_2g(sc, f) : 0);
+    }
+  }
+  g.sync();  // earlier users of s are done
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) s[s10(xcell((oc << 8) + g.t + h * GT))] = x[h];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f % NSL != slice) continue;
+    if (((cw + ((f & 1) ? 1 : 0)) & 1) != color) continue;
+    const int r = f / NSL, a = f >> 1;
+    const int q = s10(face_cell(f, u, w));
+    const int stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
+    const int nb = nbv.v[r];
+    long long gv;
+    if (nb >= 0) gv = hv[r];
+    else if (nb == -1) gv = bc.type[f] ? hv[r] - inn[r] : inn[r];
+    else gv = fx_div6(2 * inn[r] + hv[r]);
+    s[q + ((f & 1) ? stride : -stride)] = gv;
+  }
+  g.sync();
+  bool bad = false;
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    const int pp = (color << 8) + g.t + h * GT;
+    const int q = s10(xcell(pp));
+    const long long v =
+        fx_div6(s[q - 1] + s[q + 1] + s[q - 10] + s[q + 10] + s[q - 100] + s[q + 100] + 6 * G[h]);
+    bad |= fx_bad(v);
+    phx[base + pp] = v;
+  }
+  return bad;
+}
+
+// ---------------------------------------------------------------------------
+// residual, restriction, FAS right-hand side, prolongation, ghosts
+// ---------------------------------------------------------------------------
+
+// Residual and restriction of box b (level l): the 64 cells of the parent
+// region get the mean of their 8 children (potential) and the undivided
+// sum over the children of 6 G + T (completed by fx_fas_box).
+__device__ __forceinline__ void fx_resid_restrict_box(const Grp &g, long long *s, long long *sr, int b,
+                                                      long long *phx, long long *gx, const long long *ghx,
+                                                      const Nb &nb, const Place &pl, const Bc &bc,
+                                                      const unsigned long long *sc) {
+  const size_t base = (size_t)b * CELLS;
+  long long G[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) G[h] = gx[base + g.t + h * GT];
+  fx_stage(g, s, phx, nb, ghx, b, bc, sc);
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int c = xcell(g.t + h * GT);
+    sr[c] = 6 * G[h] + fx_T(s, s10(c));
+  }
+  g.sync();
+  if (g.t >= 64) return;
+  const int ci = g.t & 3, cj = (g.t >> 2) & 3, ck = g.t >> 4;
+  long long ap = 0, ar = 0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        ap += s[s10(c)];
+        ar += sr[c];
+      }
+  const size_t cc = (size_t)pl.P * CELLS + xpos(4 * pl.ox + ci, 4 * pl.oy + cj, 4 * pl.oz + ck);
+  phx[cc] = fx_rdiv<8>(ap);
+  gx[cc] = ar;
+}
+
+// After restriction into box b (level l-1): keep a copy of the potential,
+// and on a refined box complete the FAS right-hand side
+// G = (sum of children's 6 G + T - 2 T_c) / 12.  True on overflow.
+__device__ __forceinline__ bool fx_fas_box(const Grp &g, long long *s, int b, const long long *phx, long long *oldx,
+                                           long long *gx, const long long *ghx, const Nb &nb, bool refined,
+                                           const Bc &bc, const unsigned long long *sc) {
+  const size_t base = (size_t)b * CELLS;
+  if (!refined) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      reinterpret_cast<longlong2 *>(oldx + base)[g.t + GT * h] =
+          reinterpret_cast<const longlong2 *>(phx + base)[g.t + GT * h];
+    return false;
+  }
+  long long P[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) P[h] = gx[base + g.t + h * GT];
+  fx_stage(g, s, phx, nb, ghx, b, bc, sc);
+  bool bad = false;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int pp = g.t + h * GT, q = s10(xcell(pp));
+    oldx[base + pp] = s[q];
+    const long long G = fx_rdiv<12>(P[h] - 2 * fx_T(s, q));
+    bad |= fx_bad(G);
+    gx[base + pp] = G;
+  }
+  return bad;
+}
+
+// Ghat = 2c + c_t1 + c_t2 of ghost cell (u,w) of refinement face F of box
+// b (level l) from the level l-1 potential (Dirichlet walls 2g - c)
+template <int F>
+__device__ __forceinline__ void fx_cf_value(const long long *phx, long long *ghx, const int32_t *__restrict__ nbr6,
+                                            const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk,
+                                            const Bc &bc, const unsigned long long *sc, int b, int u, int w,
+                                            unsigned long long *err) {
+  auto val = [&](int Q, int c) { return phx[(size_t)Q * CELLS + xsplit(c)]; };
+  auto wall = [&](int f, long long ctr) { return bc.type[f] ? fx_2g(sc, f) - ctr : ctr; };
+  long long c, c1, c2;
+  if (!cf_coarse3<F, long long>(val, wall, nbr6, parent, ijk, b, u, w, err, c, c1, c2)) return;
+  ghx[(size_t)(6 * b + F) * FACE + u + NC * w] = 2 * c + c1 + c2;
+}
+
+__device__ __forceinline__ void fx_cf_faces_box(int e, int nthreads, const long long *phx, long long *ghx,
+                                                const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
+                                                const int32_t *__restrict__ ijk, const Bc &bc,
+                                                const unsigned long long *sc, int b, unsigned long long *err) {
+  const int u = e & 7, w = (e >> 3) & 7, first = e >> 6, step = nthreads >> 6;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (f < first || (f - first) % step) continue;
+    if (__ldg(nbr6 + 6 * b + f) != -2) continue;
+    switch (f) {
+      case 0: fx_cf_value<0>(phx, ghx, nbr6, parent, ijk, bc, sc, b, u, w, err); break;
+      case 1: fx_cf_value<1>(phx, ghx, nbr6, parent, ijk, bc, sc, b, u, w, err); break;
+      case 2: fx_cf_value<2>(phx, ghx, nbr6, parent, ijk, bc, sc, b, u, w, err); break;
+      case 3: fx_cf_value<3>(phx, ghx, nbr6, parent, ijk, bc, sc, b, u, w, err); break;
+      case 4: fx_cf_value<4>(phx, ghx, nbr6, parent, ijk, bc, sc, b, u, w, err); break;
+      default: fx_cf_value<5>(phx, ghx, nbr6, parent, ijk, bc, sc, b, u, w, err); break;
+    }
+  }
+}
+
+// Prolongation into box b (level l) and the Ghat values of its refinement
+// faces: mode 0 adds the correction (phi - old of level l-1, homogeneous
+// wall ghosts), mode 1 overwrites with the prolonged solution (FMG).  The
+// coarse values of the 4^3 parent cells under b and their face neighbours
+// are staged once in sp[216].  True on overflow.
+__device__ __forceinline__ bool fx_prolong_box(const Grp &g, long long *sp, int b, int mode, long long *phx,
+                                               const long long *oldx, long long *ghx,
+                                               const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
+                                               const int32_t *__restrict__ ijk, const Bc &bc,
+                                               const unsigned long long *sc, unsigned long long *err) {
+  const int P = __ldg(parent + b);
+  const int o[3] = {__ldg(ijk + 3 * b) & 1, __ldg(ijk + 3 * b + 1) & 1, __ldg(ijk + 3 * b + 2) & 1};
+  auto val = [&](int Q, int c) {
+    const size_t x = (size_t)Q * CELLS + xsplit(c);
+    return mode ? phx[x] : phx[x] - oldx[x];
+  };
+  auto reg = [](int x, int y, int z) { return x + 6 * y + 36 * z; };
+  g.sync();  // earlier users of sp are done
+  if (g.t < 64) {
+    const int x = g.t & 3, y = (g.t >> 2) & 3, z = g.t >> 4;
+    sp[reg(x + 1, y + 1, z + 1)] = val(P, cidx(4 * o[0] + x, 4 * o[1] + y, 4 * o[2] + z));
+  }
+#pragma unroll
+  for (int F = 0; F < 6; ++F) {
+    const int slot = F < 4 ? 64 + 16 * F : 16 * (F - 4);
+    if (g.t < slot || g.t >= slot + 16) continue;
+    const int E = F >> 1, S = (F & 1) ? 1 : -1;
+    const int u = (g.t - slot) & 3, w = (g.t - slot) >> 2;
+    int rc[3], lc[3];
+    rc[E] = S > 0 ? 5 : 0;
+    rc[(E + 1) % 3] = u + 1;
+    rc[(E + 2) % 3] = w + 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lc[d] = 4 * o[d] - 1 + rc[d];
+    long long v;
+    if (lc[E] >= 0 && lc[E] < NC) {
+      v = val(P, cidx(lc[0], lc[1], lc[2]));
+    } else {
+      const int Qn = __ldg(nbr6 + 6 * P + F);
+      if (Qn >= 0) {
+        lc[E] = S > 0 ? 0 : NC - 1;
+        v = val(Qn, cidx(lc[0], lc[1], lc[2]));
+      } else {
+        lc[E] -= S;
+        const long long ctr = val(P, cidx(lc[0], lc[1], lc[2]));
+        if (Qn == -1) {
+          v = bc.type[F] ? (mode ? fx_2g(sc, F) : 0) - ctr : ctr;
+        } else {
+          atomicOr(err, 1ull);
+          v = ctr;
+        }
+      }
+    }
+    sp[reg(rc[0], rc[1], rc[2])] = v;
+  }
+  g.sync();
+  bool bad = false;
+  {
+    const int cc = g.t >> 1, dx = g.t & 1;
+    const int ci = cc & 3, cj = (cc >> 2) & 3, ck = cc >> 4;
+    const int q = reg(ci + 1, cj + 1, ck + 1);
+    const long long A = sp[q] + sp[q + (dx ? 1 : -1)];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const long long B = A + sp[q + (dy ? 6 : -6)];
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const long long v = fx_rdiv<4>(B + sp[q + (dz ? 36 : -36)]);
+        const size_t x = (size_t)b * CELLS + xpos(2 * ci + dx, 2 * cj + dy, 2 * ck + dz);
+        const long long nv = mode ? v : phx[x] + v;
+        bad |= fx_bad(nv);
+        phx[x] = nv;
+      }
+    }
+  }
+  fx_cf_faces_box(g.t, GT, phx, ghx, nbr6, parent, ijk, bc, sc, b, err);
+  return bad;
+}
+
+// max over a box group of a non-negative double given by its bit pattern
+// (NaN patterns order above every finite value and infinity), pushed to
+// *slot by thread 0 (red: GT/32 words of shared memory of the group)
+__device__ __forceinline__ void group_umax_to(const Grp &g, unsigned long long *slot, unsigned long long v,
+                                              unsigned long long *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, v, o);
+    v = x > v ? x : v;
+  }
+  if ((g.t & 31) == 0) red[g.t >> 5] = v;
+  g.sync();
+  if (g.t == 0) {
+    unsigned long long x = red[0];
+#pragma unroll
+    for (int i = 1; i < GT / 32; ++i) x = red[i] > x ? red[i] : x;
+    atomicMax(slot, x);
+  }
+  g.sync();
+}
+
+// max over the cells of leaf box b of |f - L phi| (FP64 f, fixed-point
+// phi), as the bit pattern of the non-negative double
+__device__ __forceinline__ unsigned long long fx_resid_max_box(const Grp &g, long long *s, int b, const long long *phx,
+                                                               const double *rhs, const long long *ghx,
+                                                               const Nb &nb, const Bc &bc,
+                                                               const unsigned long long *sc, double nqih2) {
+  const size_t base = (size_t)b * CELLS;
+  double f[CPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) f[h] = rhs[base + g.t + h * GT];
+  fx_stage(g, s, phx, nb, ghx, b, bc, sc);
+  unsigned long long m = 0;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const double r = fma(__ll2double_rn(fx_T(s, s10(g.t + h * GT))), nqih2, f[h]);
+    const unsigned long long a = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+    m = a > m ? a : m;
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// kernels (one box per block of GT threads unless stated)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(GT) k_fcolor(int lo, int color, long long *__restrict__ phx,
+                                               const long long *__restrict__ gx, const long long *__restrict__ ghx,
+                                               const int32_t *__restrict__ nbr6, Bc bc, unsigned long long *sc) {
+  __shared__ long long s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  pdl_wait();
+  const bool bad = fx_color_box(g, s, b, color, phx, gx, ghx, nb, bc, sc);
+  fx_flag(bad, sc);
+}
+
+__global__ void __launch_bounds__(GT) k_fresid_restrict(int lo, long long *__restrict__ phx, long long *__restrict__ gx,
+                                                        const long long *__restrict__ ghx,
+                                                        const int32_t *__restrict__ nbr6,
+                                                        const int32_t *__restrict__ parent,
+                                                        const int32_t *__restrict__ ijk, Bc bc,
+                                                        const unsigned long long *sc) {
+  __shared__ long long s[1000], sr[CELLS];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const Place pl = load_place(parent, ijk, b);
+  pdl_wait();
+  fx_resid_restrict_box(g, s, sr, b, phx, gx, ghx, nb, pl, bc, sc);
+}
+
+__global__ void __launch_bounds__(GT) k_ffas(int lo, const long long *__restrict__ phx, long long *__restrict__ oldx,
+                                             long long *__restrict__ gx, const long long *__restrict__ ghx,
+                                             const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child,
+                                             Bc bc, unsigned long long *sc) {
+  __shared__ long long s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const bool refined = __ldg(child + 8 * b) >= 0;
+  pdl_wait();
+  const bool bad = fx_fas_box(g, s, b, phx, oldx, gx, ghx, nb, refined, bc, sc);
+  fx_flag(bad, sc);
+}
+
+// leaf boxes of one level whose residual norm a prolongation launch
+// computes in extra blocks (n = 0: none)
+struct FxNorm {
+  const int32_t *leaf;
+  int n;
+  const double *rhs;
+  double inv_h2;
+  unsigned long long *slot;
+};
+
+// Blocks [0, n) prolong into boxes [lo, lo + n) of level l; blocks beyond
+// add the residual max of the leaf boxes of level l-1 (final once level l
+// is prolonged into) to nm.slot.
+__global__ void __launch_bounds__(GT) k_fprolong(int lo, int n, int mode, long long *__restrict__ phx,
+                                                 const long long *__restrict__ oldx, long long *__restrict__ ghx,
+                                                 const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
+                                                 const int32_t *__restrict__ ijk, Bc bc, unsigned long long *sc,
+                                                 FxNorm nm) {
+  __shared__ long long s[1000];
+  __shared__ unsigned long long red[GT / 32];
+  const Grp g = block_grp();
+  if ((int)blockIdx.x >= n) {
+    const int b = __ldg(nm.leaf + blockIdx.x - n);
+    const Nb nb = load_nb(g, nbr6, b);
+    pdl_wait();
+    const double nq = -fx_q(fx_E(sc)) * nm.inv_h2;
+    const unsigned long long m = fx_resid_max_box(g, s, b, phx, nm.rhs, ghx, nb, bc, sc, nq);
+    group_umax_to(g, nm.slot, m, red);
+    return;
+  }
+  pdl_wait();
+  const bool bad = fx_prolong_box(g, s, lo + blockIdx.x, mode, phx, oldx, ghx, nbr6, parent, ijk, bc, sc,
+                                  sc + SC_ERR);
+  fx_flag(bad, sc);
+}
+
+// Ghat values of the refinement faces of boxes [lo, lo + grid), 64 threads
+// per box
+__global__ void __launch_bounds__(64) k_ffill_cf(int lo, const long long *__restrict__ phx, long long *__restrict__ ghx,
+                                                 const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
+                                                 const int32_t *__restrict__ ijk, Bc bc, unsigned long long *sc) {
+  pdl_wait();
+  fx_cf_faces_box((int)threadIdx.x, 64, phx, ghx, nbr6, parent, ijk, bc, sc, lo + blockIdx.x, sc + SC_ERR);
+}
+
+// max over leaf cells of |f - L phi| into *slot (bit pattern of a double)
+__global__ void __launch_bounds__(GT) k_fresnorm(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
+                                                 const long long *__restrict__ phx, const double *__restrict__ rhs,
+                                                 const long long *__restrict__ ghx, const int32_t *__restrict__ nbr6,
+                                                 Bc bc, LevelH lh, unsigned long long *sc, unsigned long long *slot) {
+  __shared__ long long s[1000];
+  __shared__ unsigned long long red[GT / 32];
+  const Grp g = block_grp();
+  const int b = __ldg(leaf + blockIdx.x);
+  const Nb nb = load_nb(g, nbr6, b);
+  const int l = __ldg(level + b);
+  pdl_wait();
+  const double nq = -fx_q(fx_E(sc)) * lh.inv_h2[l];
+  group_umax_to(g, slot, fx_resid_max_box(g, s, b, phx, rhs, ghx, nb, bc, sc, nq), red);
+}
+
+// Level-0 exact solve (one box, CELLS threads): the FAS right-hand side of
+// level 0 from its G (f = -6 G q / h^2), the FP64 eigenbasis solve of the
+// double path with the Dirichlet values folded in, the result rounded to
+// quanta.
+__global__ void __launch_bounds__(CELLS) k_fcoarse(long long *__restrict__ phx, const long long *__restrict__ gx,
+                                                   const double *__restrict__ basis, Bc bc, double h2, double inv_h2,
+                                                   unsigned long long *sc) {
+  __shared__ double sm[2 * CELLS + 216];
+  pdl_wait();
+  const int E = fx_E(sc);
+  const double cf = -6.0 * fx_q(E) * inv_h2;
+  bool bad = false;
+  coarse_box_io<CELLS>(
+      (int)threadIdx.x, [] { __syncthreads(); }, sm, [&](int t) { return __ll2double_rn(gx[xsplit(t)]) * cf; },
+      [&](int t, double v) { phx[xsplit(t)] = fx_of(v, E, bad); }, basis, bc, h2, inv_h2, 0);
+  fx_flag(bad, sc);
+}
+
+// per-level constants of the scale computation: exponent bound of h_l^2
+// (|h^2 f| < 2^(expo(f) - 1022 + eh)) and -h_l^2 / 6
+struct FxLev {
+  int eh[MAXL];
+  double mh6[MAXL];
+};
+
+// largest exponent field of the potential and of h^2 f over all cells
+// (grid-stride over boxes) into sc[SC_FXI]
+__global__ void __launch_bounds__(256) k_fx_expo(int n_boxes, const int32_t *__restrict__ level,
+                                                 const double *__restrict__ phi, const double *__restrict__ rhs,
+                                                 FxLev fl, unsigned long long *sc) {
+  pdl_wait();
+  int m = 0;
+  const size_t total = (size_t)n_boxes * CELLS;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int l = __ldg(level + i / CELLS);
+    const int ep = (int)expo_of(phi[i]);
+    const int ef = (int)expo_of(rhs[i]);
+    m = max(m, max(ep, ef ? ef + fl.eh[l] : 0));
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(sc + SC_FXI, (unsigned long long)m);
+}
+
+// E = max(bound, expo(2g), FX_EMIN) + margin; the Dirichlet constants 2g
+// in quanta (one thread)
+__global__ void k_fx_scale(Bc bc, unsigned long long *sc) {
+  pdl_wait();
+  int m = (int)sc[SC_FXI];
+  for (int f = 0; f < 6; ++f)
+    if (bc.type[f]) m = max(m, (int)expo_of(bc.g2[f]));
+  const int E = max(m, FX_EMIN) + (int)sc[SC_FXM];
+  sc[SC_FXE] = (unsigned long long)E;
+  bool bad = false;
+  for (int f = 0; f < 6; ++f) sc[SC_FX2G + f] = (unsigned long long)(bc.type[f] ? fx_of(bc.g2[f], E, bad) : 0ll);
+  if (bad) sc[SC_ERR] |= FX_ERR_OVF;
+}
+
+// phx = phi and gx = -h^2 f / 6 in quanta, for every box (CELLS / GT pairs
+// per thread)
+__global__ void __launch_bounds__(GT) k_fx_init(const int32_t *__restrict__ level, const double *__restrict__ phi,
+                                                const double *__restrict__ rhs, long long *__restrict__ phx,
+                                                long long *__restrict__ gx, FxLev fl, unsigned long long *sc) {
+  const int b = blockIdx.x;
+  const int l = __ldg(level + b);
+  pdl_wait();
+  const int E = fx_E(sc);
+  const double mh6 = fl.mh6[l];
+  bool bad = false;
+  const size_t base = (size_t)b * CELLS;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int c = threadIdx.x + h * GT;
+    const size_t x = base + c, y = base + xsplit(c);
+    phx[y] = fx_of(phi[x], E, bad);
+    gx[y] = fx_of(rhs[x] * mh6, E, bad);
+  }
+  fx_flag(bad, sc);
+}
+
+// phi = phx q for every box, unless the solve left the fixed-point range
+// (its FP64 inputs then stay as they were for the next attempt)
+__global__ void __launch_bounds__(GT) k_fx_final(const long long *__restrict__ phx, double *__restrict__ phi,
+                                                 const unsigned long long *__restrict__ sc) {
+  pdl_wait();
+  if (sc[SC_ERR] & FX_ERR_OVF) return;
+  const double q = fx_q(fx_E(sc));
+  const size_t base = (size_t)blockIdx.x * CELLS;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int c = threadIdx.x + h * GT;
+    phi[base + c] = __ll2double_rn(phx[base + xsplit(c)]) * q;
+  }
+}
+
+}  // namespace fx

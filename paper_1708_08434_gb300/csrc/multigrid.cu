@@ -233,12 +233,12 @@ __device__ __forceinline__ void restrict1_box(const Grp &g, int b, const Place &
 
 // Value of a coarse-level quantity at local cell (q0,q1,q2) of box Q where
 // the cell may lie one step outside the box along axis E (direction S):
-// the neighbour box of the same level, or the physical-boundary ghost of
-// the cell `ctr` it left.  E and S are compile-time so that the boundary
-// table is indexed by constants.
-template <int E, int S, typename T, typename F>
-__device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, int Q, int q0, int q1, int q2, T ctr,
-                                       const Bc &bc, int homog, unsigned long long *err) {
+// the neighbour box of the same level, or the physical-boundary ghost
+// wall(f, ctr) of the cell `ctr` it left.  E and S are compile-time so that
+// the boundary table is indexed by constants.
+template <int E, int S, typename T, typename F, typename W>
+__device__ __forceinline__ T coarse_at(F val, W wall, const int32_t *__restrict__ nbr6, int Q, int q0, int q1, int q2,
+                                       T ctr, unsigned long long *err) {
   const int qe = E == 0 ? q0 : (E == 1 ? q1 : q2);
   if (qe >= 0 && qe < NC) return val(Q, cidx(q0, q1, q2));
   constexpr int f = 2 * E + (S > 0);
@@ -247,30 +247,28 @@ __device__ __forceinline__ T coarse_at(F val, const int32_t *__restrict__ nbr6, 
     const int w = S > 0 ? 0 : NC - 1;
     return val(Qn, cidx(E == 0 ? w : q0, E == 1 ? w : q1, E == 2 ? w : q2));
   }
-  if (Qn == -1) {
-    if (bc.type[f]) return (homog ? T(0) : bc_g2<T>(bc, f)) - ctr;
-    return ctr;
-  }
+  if (Qn == -1) return wall(f, ctr);
   atomicOr(err, 1ull);  // nesting violated: no coarse box where one must be
   return ctr;
 }
 
 // coarse_at with a run-time direction s along compile-time axis E
-template <int E, typename T, typename F>
-__device__ __forceinline__ T coarse_step(F val, const int32_t *__restrict__ nbr6, int Q, int q0, int q1, int q2,
-                                         int s, T ctr, const Bc &bc, int homog, unsigned long long *err) {
+template <int E, typename T, typename F, typename W>
+__device__ __forceinline__ T coarse_step(F val, W wall, const int32_t *__restrict__ nbr6, int Q, int q0, int q1,
+                                         int q2, int s, T ctr, unsigned long long *err) {
   if (s > 0)
-    return coarse_at<E, 1, T>(val, nbr6, Q, q0 + (E == 0), q1 + (E == 1), q2 + (E == 2), ctr, bc, homog, err);
-  return coarse_at<E, -1, T>(val, nbr6, Q, q0 - (E == 0), q1 - (E == 1), q2 - (E == 2), ctr, bc, homog, err);
+    return coarse_at<E, 1, T>(val, wall, nbr6, Q, q0 + (E == 0), q1 + (E == 1), q2 + (E == 2), ctr, err);
+  return coarse_at<E, -1, T>(val, wall, nbr6, Q, q0 - (E == 0), q1 - (E == 1), q2 - (E == 2), ctr, err);
 }
 
-// phihat = c/2 + c_t1/4 + c_t2/4 for ghost cell (u,w) of refinement face F
-// of box b (level l), from the level l-1 values of v
-template <int F, typename T>
-__device__ __forceinline__ void cf_value(const T *v, T *gh, const int32_t *__restrict__ nbr6,
-                                         const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk,
-                                         const Bc &bc, int homog, int b, int u, int w, unsigned long long *err) {
-  auto val = [&](int Q, int c) { return v[(size_t)Q * CELLS + c]; };
+// The three level l-1 values behind ghost cell (u,w) of refinement face F
+// of box b (level l): the coarse cell c containing the ghost and its two
+// tangential neighbours c1, c2 on the ghost's side.  False (error bit 2
+// set) when the parent has no neighbour across F.
+template <int F, typename T, typename V, typename W>
+__device__ __forceinline__ bool cf_coarse3(V val, W wall, const int32_t *__restrict__ nbr6,
+                                           const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk, int b,
+                                           int u, int w, unsigned long long *err, T &c, T &c1, T &c2) {
   constexpr int a = F >> 1, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
   int G[3];
   G[a] = NC * __ldg(ijk + 3 * b + a) + ((F & 1) ? NC : -1);
@@ -280,14 +278,29 @@ __device__ __forceinline__ void cf_value(const T *v, T *gh, const int32_t *__res
   const int Q = __ldg(nbr6 + 6 * P + F);
   if (Q < 0) {
     atomicOr(err, 2ull);
-    return;
+    return false;
   }
   const int l0 = (G[0] >> 1) - NC * __ldg(ijk + 3 * Q), l1 = (G[1] >> 1) - NC * __ldg(ijk + 3 * Q + 1),
             l2 = (G[2] >> 1) - NC * __ldg(ijk + 3 * Q + 2);
-  const T c = val(Q, cidx(l0, l1, l2));
+  c = val(Q, cidx(l0, l1, l2));
+  c1 = coarse_step<t1, T>(val, wall, nbr6, Q, l0, l1, l2, (G[t1] & 1) ? 1 : -1, c, err);
+  c2 = coarse_step<t2, T>(val, wall, nbr6, Q, l0, l1, l2, (G[t2] & 1) ? 1 : -1, c, err);
+  return true;
+}
+
+// phihat = c/2 + c_t1/4 + c_t2/4 for ghost cell (u,w) of refinement face F
+// of box b (level l), from the level l-1 values of v
+template <int F, typename T>
+__device__ __forceinline__ void cf_value(const T *v, T *gh, const int32_t *__restrict__ nbr6,
+                                         const int32_t *__restrict__ parent, const int32_t *__restrict__ ijk,
+                                         const Bc &bc, int homog, int b, int u, int w, unsigned long long *err) {
+  auto val = [&](int Q, int c) { return v[(size_t)Q * CELLS + c]; };
+  auto wall = [&](int f, T ctr) { return bc.type[f] ? (homog ? T(0) : bc_g2<T>(bc, f)) - ctr : ctr; };
+  T c, c1, c2;
+  if (!cf_coarse3<F, T>(val, wall, nbr6, parent, ijk, b, u, w, err, c, c1, c2)) return;
   T ph = T(0.5) * c;
-  ph += T(0.25) * coarse_step<t1, T>(val, nbr6, Q, l0, l1, l2, (G[t1] & 1) ? 1 : -1, c, bc, homog, err);
-  ph += T(0.25) * coarse_step<t2, T>(val, nbr6, Q, l0, l1, l2, (G[t2] & 1) ? 1 : -1, c, bc, homog, err);
+  ph += T(0.25) * c1;
+  ph += T(0.25) * c2;
   gh[(size_t)(6 * b + F) * FACE + u + NC * w] = ph;
 }
 
@@ -406,10 +419,10 @@ __device__ __forceinline__ void prolong_box(const Grp &g, T *sp, int b, int mode
 // eigenvalues of the 7-point operator, transform back.  NT threads (t0 the
 // thread's index, sync their barrier); sm: 2 x 512 + 216 doubles of shared
 // memory.
-template <int NT, typename T, typename Sync>
-__device__ __forceinline__ void coarse_box(int t0, Sync sync, double *sm, T *phi, const T *rhs,
-                                           const double *__restrict__ basis, const Bc &bc, double h2,
-                                           double inv_h2, int homog) {
+template <int NT, typename Sync, typename In, typename Out>
+__device__ __forceinline__ void coarse_box_io(int t0, Sync sync, double *sm, In rhs_of, Out store,
+                                              const double *__restrict__ basis, const Bc &bc, double h2,
+                                              double inv_h2, int homog) {
   double *x = sm, *y = sm + CELLS, *V = sm + 2 * CELLS, *lam = V + 192;
   for (int i = t0; i < 216; i += NT) {
     if (i < 192) V[i] = __ldg(basis + i);
@@ -419,7 +432,7 @@ __device__ __forceinline__ void coarse_box(int t0, Sync sync, double *sm, T *phi
   for (int h = 0; h < CELLS / NT; ++h) {
     const int t = t0 + h * NT;
     const int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
-    double r = (double)rhs[t];
+    double r = rhs_of(t);
     if (!homog) {
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
@@ -477,9 +490,19 @@ __device__ __forceinline__ void coarse_box(int t0, Sync sync, double *sm, T *phi
     const int t = t0 + h * NT, c0 = t & 7, c1 = (t >> 3) & 7, c2 = t >> 6;
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[2 * 64 + c2 * 8 + m] * y[cidx(c0, c1, m)];
-    phi[t] = (T)acc;
+    store(t, acc);
   }
   sync();  // sm is free again
+}
+
+// the level-0 solve on arrays of the value type T (FP64 or FP32 in memory)
+template <int NT, typename T, typename Sync>
+__device__ __forceinline__ void coarse_box(int t0, Sync sync, double *sm, T *phi, const T *rhs,
+                                           const double *__restrict__ basis, const Bc &bc, double h2,
+                                           double inv_h2, int homog) {
+  coarse_box_io<NT>(
+      t0, sync, sm, [&](int t) { return (double)rhs[t]; }, [&](int t, double v) { phi[t] = (T)v; }, basis, bc, h2,
+      inv_h2, homog);
 }
 
 // FP64 residual f - L v of the cells of this thread in leaf box b; the
@@ -699,8 +722,11 @@ __global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *s
   sc[SC_CYC] = c;
   sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
   double tol = __longlong_as_double((long long)sc[SC_TOL]);
-  cudaGraphSetConditional(h, (rel > tol && c < sc[SC_MAXC]) ? 1u : 0u);
+  const bool ovf = (sc[SC_ERR] & 8ull) != 0;  // fixed-point range left: the host runs the solve again
+  cudaGraphSetConditional(h, (rel > tol && c < sc[SC_MAXC] && !ovf) ? 1u : 0u);
 }
+
+#include "mgfix.cuh"
 
 // ---------------------------------------------------------------------------
 // persistent V-cycle kernel
@@ -929,6 +955,181 @@ constexpr size_t persist_smem() {
   return (size_t)PGROUPS * persist_group_smem<T>();
 }
 
+// The persistent kernel of the FP64 solve: the fixed-point phases of
+// mgfix.cuh between grid barriers (bit-identical to the per-level launches).
+struct PArgsX {
+  long long *phx, *gx, *oldx, *ghx;
+  const double *rhs;
+  const int32_t *nbr6, *parent, *ijk, *child, *leaf, *level;
+  const double *basis;
+  unsigned long long *sc;
+  Bc bc;
+  LevelH lh;
+  int level_off[MAXL + 1];
+  int n_levels, n_leaves, top, nu1, nu2;
+  int fmg, loop, bar_extra;  // as PArgs (the rhs restriction of FMG is done before the launch)
+};
+
+// shared memory of one box group: 10^3 staging plus 512 sums, or the
+// FP64 scratch of the level-0 solve, then GT/32 reduction words (bytes)
+constexpr size_t PX_STAGE = (1000 + CELLS) * sizeof(long long);
+static_assert((2 * CELLS + 216) * sizeof(double) <= PX_STAGE, "level-0 scratch fits");
+__host__ __device__ constexpr size_t persistx_group_smem() {
+  return PX_STAGE + (GT / 32) * sizeof(unsigned long long);
+}
+
+struct PersistX {
+  const PArgsX &a;
+  Grp g;
+  int gi, ng;
+  long long *s;
+  unsigned long long *red;
+  GridBar bar;
+
+  __device__ int lo(int l) const { return a.level_off[l]; }
+  __device__ int hi(int l) const { return a.level_off[l + 1]; }
+  __device__ bool empty(int l) const { return hi(l) == lo(l); }
+
+  __device__ bool smooth(int l, int nu) {
+    if (empty(l)) return true;
+    for (int it = 0; it < nu; ++it)
+      for (int color = 0; color < 2; ++color) {
+        for (int b = lo(l) + gi; b < hi(l); b += ng) {
+          const bool bad = fx::fx_color_box(g, s, b, color, a.phx, a.gx, a.ghx, load_nb(g, a.nbr6, b), a.bc, a.sc);
+          fx::fx_flag(bad, a.sc);
+        }
+        if (!bar.sync()) return false;
+      }
+    return true;
+  }
+
+  __device__ bool coarse() {
+    if (gi == 0) {
+      const int E = fx::fx_E(a.sc);
+      const double cf = -6.0 * fx::fx_q(E) * a.lh.inv_h2[0];
+      bool bad = false;
+      coarse_box_io<GT>(
+          g.t, [&] { g.sync(); }, (double *)s, [&](int t) { return __ll2double_rn(a.gx[fx::xsplit(t)]) * cf; },
+          [&](int t, double v) { a.phx[fx::xsplit(t)] = fx::fx_of(v, E, bad); }, a.basis, a.bc, a.lh.h2[0],
+          a.lh.inv_h2[0], 0);
+      fx::fx_flag(bad, a.sc);
+    }
+    return bar.sync();
+  }
+
+  __device__ bool prolong(int l, int mode) {
+    if (empty(l)) return true;
+    for (int b = lo(l) + gi; b < hi(l); b += ng) {
+      const bool bad = fx::fx_prolong_box(g, s, b, mode, a.phx, a.oldx, a.ghx, a.nbr6, a.parent, a.ijk, a.bc, a.sc,
+                                          a.sc + SC_ERR);
+      fx::fx_flag(bad, a.sc);
+    }
+    return bar.sync();
+  }
+
+  __device__ bool vcycle(int top) {
+    for (int l = top; l >= 1; --l) {
+      if (!smooth(l, a.nu1)) return false;
+      if (!empty(l)) {
+        for (int b = lo(l) + gi; b < hi(l); b += ng)
+          fx::fx_resid_restrict_box(g, s, s + 1000, b, a.phx, a.gx, a.ghx, load_nb(g, a.nbr6, b),
+                                    load_place(a.parent, a.ijk, b), a.bc, a.sc);
+        if (!bar.sync()) return false;
+      }
+      for (int b = lo(l - 1) + gi; b < hi(l - 1); b += ng) {
+        const bool bad = fx::fx_fas_box(g, s, b, a.phx, a.oldx, a.gx, a.ghx, load_nb(g, a.nbr6, b),
+                                        __ldg(a.child + 8 * b) >= 0, a.bc, a.sc);
+        fx::fx_flag(bad, a.sc);
+      }
+      if (!bar.sync()) return false;
+    }
+    if (!coarse()) return false;
+    for (int l = 1; l <= top; ++l) {
+      if (!prolong(l, 0)) return false;
+      if (!smooth(l, a.nu2)) return false;
+    }
+    return true;
+  }
+
+  __device__ bool ladder() {
+    if (!coarse()) return false;
+    for (int l = 1; l < a.n_levels; ++l) {
+      if (!prolong(l, 1)) return false;
+      if (!vcycle(l)) return false;
+    }
+    return true;
+  }
+
+  // max_leaf |f - L phi| into slot; true when the wait succeeded
+  __device__ bool resnorm(unsigned long long *slot) {
+    unsigned long long m = 0;
+    const double q = fx::fx_q(fx::fx_E(a.sc));
+    for (int i = gi; i < a.n_leaves; i += ng) {
+      const int b = __ldg(a.leaf + i);
+      const unsigned long long r = fx::fx_resid_max_box(g, s, b, a.phx, a.rhs, a.ghx, load_nb(g, a.nbr6, b), a.bc,
+                                                        a.sc, -q * a.lh.inv_h2[__ldg(a.level + b)]);
+      m = r > m ? r : m;
+    }
+    fx::group_umax_to(g, slot, m, red);
+    return bar.sync();
+  }
+};
+
+__global__ void __launch_bounds__(PGROUPS *GT, 1) k_persistx(const __grid_constant__ PArgsX a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int flag;
+  const int q = threadIdx.x / GT;
+  unsigned char *base = smem + (size_t)q * persistx_group_smem();
+  PersistX p{a, Grp{(int)threadIdx.x % GT, 1 + q}, q * (int)gridDim.x + (int)blockIdx.x, PGROUPS * (int)gridDim.x,
+             (long long *)base, (unsigned long long *)(base + PX_STAGE),
+             GridBar{(unsigned int *)(a.sc + SC_BAR), 0u, (unsigned int)a.bar_extra, &flag, a.sc + SC_ERR}};
+  int cyc = 0;
+  double rel = 0.0, num = 0.0;
+  const double den = __longlong_as_double((long long)a.sc[SC_DEN]);
+  const double tol = __longlong_as_double((long long)a.sc[SC_TOL]);
+  const unsigned long long maxc = a.sc[SC_MAXC];
+  int pass = 0;
+  auto test = [&]() -> int {  // 1 = go on, 0 = converged, limit or range left, -1 = barrier wait ran out
+    unsigned long long *slot = a.sc + SC_PN0 + (pass & 1);
+    if (!p.resnorm(slot)) return -1;
+    unsigned long long bits, err;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(bits) : "l"(slot) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(err) : "l"(a.sc + SC_ERR) : "memory");
+    num = __longlong_as_double((long long)bits);
+    rel = den > 0.0 ? num / den : num;
+    ++cyc;
+    ++pass;
+    return (rel > tol && (unsigned long long)cyc < maxc && !(err & fx::FX_ERR_OVF)) ? 1 : 0;
+  };
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sc[SC_PN0] = 0ull;
+    a.sc[SC_PN1] = 0ull;
+  }
+  if (!p.bar.sync()) return;
+  int go = 1;
+  if (a.fmg) {
+    if (!p.ladder()) return;
+    if (a.loop) {
+      go = test();
+      if (go < 0) return;
+    } else {
+      go = 0;
+    }
+  }
+  while (go) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && pass > 0) a.sc[SC_PN0 + (pass & 1)] = 0ull;
+    if (!p.vcycle(a.top)) return;
+    if (!a.loop) break;
+    go = test();
+    if (go < 0) return;
+  }
+  if (a.loop && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sc[SC_NORM] = (unsigned long long)__double_as_longlong(num);
+    a.sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
+    a.sc[SC_CYC] = (unsigned long long)cyc;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
@@ -941,7 +1142,6 @@ struct MG {
   int homog;  // error equation: homogeneous physical ghosts
 };
 
-static MG<double> mg64(sm_ctx *ctx) { return {ctx->phi, ctx->rhs, ctx->old, ctx->gh, 0}; }
 static MG<float> mg32(sm_ctx *ctx) { return {ctx->e32, ctx->f32, ctx->old32, ctx->gh32, 1}; }
 
 int sm_mg_fill_cf(sm_ctx *ctx, double *var, int l, int homog) {
@@ -1077,32 +1277,55 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top, int norm_slot = -1) {
 
 // Blocks of the persistent kernel that fit on the device at once (its
 // launches are cooperative, so all of them are resident together).
-template <typename T>
-static int persist_prepare(sm_ctx *ctx) {
-  const int idx = sizeof(T) == sizeof(double) ? 0 : 1;
+// Blocks of a persistent kernel that fit on the device at once (its
+// launches are cooperative, so all of them are resident together); idx 0:
+// the fixed-point FP64 kernel, 1: the FP32 kernel of the mixed form.
+template <typename K>
+static int persist_prepare_k(sm_ctx *ctx, K kernel, size_t smem, int idx) {
   if (ctx->persist_grid[idx]) return SM_OK;
-  const size_t smem = persist_smem<T>();
-  SM_CK(cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SM_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0, sms = 0, coop = 0;
   SM_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
   if (!coop) return sm_fail(ctx, SM_ECUDA, "device has no cooperative launch");
-  SM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<T>, PGROUPS * GT, smem));
+  SM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, PGROUPS * GT, smem));
   SM_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   if (per_sm < 1) return sm_fail(ctx, SM_ECUDA, "persistent kernel does not fit on one SM");
   ctx->persist_grid[idx] = per_sm * sms;
   return SM_OK;
 }
 
-// One cooperative launch of the persistent kernel on the arrays of m:
-// the FMG ladder (fmg), V-cycles with `top` as finest level, and with
-// loop set the FP64 residual test after each cycle until SC_TOL or SC_MAXC
-// is reached (SC_NORM, SC_REL, SC_CYC written at the end).  Without loop
-// one V-cycle runs (or only the ladder when fmg is set).
-template <typename T>
-static int persist_launch(sm_ctx *ctx, const MG<T> &m, int top, int fmg, int loop, int bar_extra = 0) {
-  int st = persist_prepare<T>(ctx);
+static int persist_prepare32(sm_ctx *ctx) {
+  return persist_prepare_k(ctx, k_persist<float>, persist_smem<float>(), 1);
+}
+static int persistx_prepare(sm_ctx *ctx) {
+  return persist_prepare_k(ctx, k_persistx, (size_t)PGROUPS * persistx_group_smem(), 0);
+}
+
+template <typename A, typename K>
+static int persist_coop_launch(sm_ctx *ctx, K kernel, const A &a, size_t smem, int idx) {
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_BAR, 0, sizeof(unsigned long long), ctx->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctx->persist_grid[idx]);
+  cfg.blockDim = dim3(PGROUPS * GT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++ctx->n_launch;
+  SM_CK(cudaLaunchKernelEx(&cfg, kernel, a));
+  return SM_OK;
+}
+
+// One cooperative launch of the FP32 persistent kernel (error equation of
+// the mixed form): the FMG ladder (fmg) or one V-cycle with `top` as
+// finest level.
+static int persist_launch(sm_ctx *ctx, const MG<float> &m, int top, int fmg, int loop, int bar_extra = 0) {
+  int st = persist_prepare32(ctx);
   if (st) return st;
-  PArgs<T> a;
+  PArgs<float> a;
   memset(&a, 0, sizeof a);
   a.phi = m.phi;
   a.rhs = m.rhs;
@@ -1131,27 +1354,44 @@ static int persist_launch(sm_ctx *ctx, const MG<T> &m, int top, int fmg, int loo
   a.fmg = fmg;
   a.loop = loop;
   a.bar_extra = bar_extra;
-  SM_CK(cudaMemsetAsync(ctx->dscal + SC_BAR, 0, sizeof(unsigned long long), ctx->stream));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ctx->persist_grid[sizeof(T) == sizeof(double) ? 0 : 1]);
-  cfg.blockDim = dim3(PGROUPS * GT);
-  cfg.dynamicSmemBytes = persist_smem<T>();
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  ++ctx->n_launch;
-  SM_CK(cudaLaunchKernelEx(&cfg, k_persist<T>, a));
-  return SM_OK;
+  return persist_coop_launch(ctx, k_persist<float>, a, persist_smem<float>(), 1);
 }
 
-// one V-cycle from `top` on the arrays of m: persistent or per-level launches
-template <typename T>
-static int cycle(sm_ctx *ctx, const MG<T> &m, int top) {
-  if (ctx->persist) return persist_launch(ctx, m, top, 0, 0);
-  return vcycle(ctx, m, top);
+// One cooperative launch of the fixed-point FP64 persistent kernel: the
+// FMG ladder (fmg; rhs already restricted), V-cycles with `top` as finest
+// level, and with loop set the residual test after each cycle until
+// SC_TOL or SC_MAXC is reached (SC_NORM, SC_REL, SC_CYC written at the
+// end).  Without loop one V-cycle runs (or only the ladder when fmg is set).
+static int persistx_launch(sm_ctx *ctx, int top, int fmg, int loop, int bar_extra = 0) {
+  int st = persistx_prepare(ctx);
+  if (st) return st;
+  PArgsX a;
+  memset(&a, 0, sizeof a);
+  a.phx = ctx->phx;
+  a.gx = ctx->gx;
+  a.oldx = (long long *)ctx->old;
+  a.ghx = ctx->ghx;
+  a.rhs = ctx->rhs;
+  a.nbr6 = ctx->nbr6;
+  a.parent = ctx->parent;
+  a.ijk = ctx->ijk;
+  a.child = ctx->child;
+  a.leaf = ctx->leaf;
+  a.level = ctx->level;
+  a.basis = ctx->basis;
+  a.sc = ctx->dscal;
+  a.bc = ctx->bc;
+  a.lh = ctx->lh;
+  for (int l = 0; l <= MAXL; ++l) a.level_off[l] = ctx->level_off[l];
+  a.n_levels = ctx->n_levels;
+  a.n_leaves = ctx->n_leaves;
+  a.top = top;
+  a.nu1 = ctx->cfg.nu1;
+  a.nu2 = ctx->cfg.nu2;
+  a.fmg = fmg;
+  a.loop = loop;
+  a.bar_extra = bar_extra;
+  return persist_coop_launch(ctx, k_persistx, a, (size_t)PGROUPS * persistx_group_smem(), 0);
 }
 
 static int leaf_norm(sm_ctx *ctx, double *v, int slot);
@@ -1213,13 +1453,18 @@ static int mixed_correction(sm_ctx *ctx, int ladder) {
   return leaf_resid32(ctx);
 }
 
+// internal status: a fixed-point solve left its range (never returned by
+// an entry point: the solve runs again with a larger margin)
+constexpr int SM_FX_RETRY = 100;
+
 static int read_scalars(sm_ctx *ctx) {
   SM_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
   SM_CK(cudaStreamSynchronize(ctx->stream));
   unsigned long long e;
   memcpy(&e, &ctx->hscal[SC_ERR], sizeof e);
   if (e & ERR_BARRIER) return sm_fail(ctx, SM_ETIMEOUT, "grid barrier of the persistent kernel timed out");
-  if (e) return sm_fail(ctx, SM_ESTATE, "device consistency check failed (flags 0x%llx)", e);
+  if (e & ~fx::FX_ERR_OVF) return sm_fail(ctx, SM_ESTATE, "device consistency check failed (flags 0x%llx)", e);
+  if (e) return SM_FX_RETRY;
   return SM_OK;
 }
 
@@ -1250,6 +1495,171 @@ static int check_ready(sm_ctx *ctx) {
   return SM_OK;
 }
 
+// ---- the FP64 solve in fixed point (kernels in mgfix.cuh) -----------------
+
+static fx::FxLev fx_levels(const sm_ctx *ctx) {
+  fx::FxLev fl;
+  for (int l = 0; l < MAXL; ++l) {
+    int e = 0;
+    frexp(ctx->lh.h2[l], &e);  // h^2 < 2^e
+    fl.eh[l] = e;
+    fl.mh6[l] = -ctx->lh.h2[l] / 6.0;
+  }
+  return fl;
+}
+
+// the exponent margin of the next solve's scale (host value, not captured)
+static int fx_set_margin(sm_ctx *ctx) {
+  const unsigned long long m = (unsigned long long)ctx->fx_margin;
+  memcpy(&ctx->hscal[SC_FXM], &m, sizeof m);
+  SM_CK(cudaMemcpyAsync(ctx->dscal + SC_FXM, ctx->hscal + SC_FXM, sizeof(double), cudaMemcpyHostToDevice,
+                        ctx->stream));
+  return SM_OK;
+}
+
+// Ghat of every refinement face (each level from the level below)
+static int fx_fill_cf(sm_ctx *ctx) {
+  if (ctx->lbase + 1 >= ctx->n_levels) return SM_OK;
+  const int lo = ctx->level_off[ctx->lbase + 1], n = ctx->n_boxes - lo;
+  if (n <= 0) return SM_OK;
+  sm_launch(ctx, fx::k_ffill_cf, n, 64, 0, lo, ctx->phx, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
+            ctx->dscal);
+  SM_CKL("fill Ghat");
+  return SM_OK;
+}
+
+// scale of the solve (from phi, every h^2 f and 2g), the potential and G
+// of every box in quanta, and (ghat) the refinement-face sums
+static int fx_prologue(sm_ctx *ctx, bool ghat) {
+  const fx::FxLev fl = fx_levels(ctx);
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_FXI, 0, sizeof(unsigned long long), ctx->stream));
+  const int grid = ctx->n_boxes < 608 ? 2 * ctx->n_boxes : 1216;
+  sm_launch(ctx, fx::k_fx_expo, grid, 256, 0, ctx->n_boxes, ctx->level, ctx->phi, ctx->rhs, fl, ctx->dscal);
+  sm_launch(ctx, fx::k_fx_scale, 1, 1, 0, ctx->bc, ctx->dscal);
+  sm_launch(ctx, fx::k_fx_init, ctx->n_boxes, GT, 0, ctx->level, ctx->phi, ctx->rhs, ctx->phx, ctx->gx, fl,
+            ctx->dscal);
+  SM_CKL("fixed-point prologue");
+  return ghat ? fx_fill_cf(ctx) : SM_OK;
+}
+
+// phi from the fixed-point potential (skipped on the device when the solve
+// left its range), then the FP64 interpolation values of phi
+static int fx_epilogue(sm_ctx *ctx) {
+  sm_launch(ctx, fx::k_fx_final, ctx->n_boxes, GT, 0, ctx->phx, ctx->phi, ctx->dscal);
+  SM_CKL("fixed-point epilogue");
+  return sm_fill_all_cf(ctx, ctx->phi);
+}
+
+// nu red-black sweeps of level l (two colour passes each, in place)
+static int fx_smooth(sm_ctx *ctx, int l, int nu) {
+  const int n = lvl_n(ctx, l);
+  if (!n) return SM_OK;
+  for (int s = 0; s < nu; ++s)
+    for (int color = 0; color < 2; ++color)
+      sm_launch(ctx, fx::k_fcolor, n, GT, 0, ctx->level_off[l], color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6,
+                ctx->bc, ctx->dscal);
+  SM_CKL("rbgs");
+  return SM_OK;
+}
+
+static int fx_coarse(sm_ctx *ctx) {
+  int st = ensure_basis(ctx);
+  if (st) return st;
+  sm_launch(ctx, fx::k_fcoarse, 1, CELLS, 0, ctx->phx, ctx->gx, ctx->basis, ctx->bc, ctx->lh.h2[0],
+            ctx->lh.inv_h2[0], ctx->dscal);
+  SM_CKL("coarse solve");
+  return SM_OK;
+}
+
+// leaves of level l whose residual norm goes to slot (none when slot < 0)
+static fx::FxNorm fx_norm_of(sm_ctx *ctx, int l, int slot) {
+  fx::FxNorm nm = {};
+  if (slot < 0 || l < 0) return nm;
+  nm.leaf = ctx->leaf + ctx->leaf_level_off[l];
+  nm.n = ctx->leaf_level_off[l + 1] - ctx->leaf_level_off[l];
+  nm.rhs = ctx->rhs;
+  nm.inv_h2 = ctx->lh.inv_h2[l];
+  nm.slot = ctx->dscal + slot;
+  return nm;
+}
+
+static int fx_prolong(sm_ctx *ctx, int l, int mode, fx::FxNorm nm) {
+  sm_launch(ctx, fx::k_fprolong, lvl_n(ctx, l) + nm.n, GT, 0, ctx->level_off[l], lvl_n(ctx, l), mode, ctx->phx,
+            (const long long *)ctx->old, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal, nm);
+  SM_CKL("prolong");
+  return SM_OK;
+}
+
+// residual max of the leaves listed at [off, off + n) into slot
+static int fx_leaf_norm(sm_ctx *ctx, int off, int n, int slot) {
+  if (n <= 0) return SM_OK;
+  sm_launch(ctx, fx::k_fresnorm, n, GT, 0, ctx->leaf + off, ctx->level, ctx->phx, ctx->rhs, ctx->ghx, ctx->nbr6,
+            ctx->bc, ctx->lh, ctx->dscal, ctx->dscal + slot);
+  SM_CKL("resnorm");
+  return SM_OK;
+}
+
+// FAS V-cycle in fixed point with `top` as finest level; with norm_slot >= 0
+// (top the finest level) max_leaf |f - L phi| is left in that slot.  The
+// Ghat values of every level <= top must match the level below on entry
+// (the prologue and every up-sweep leave them so).
+static int fx_vcycle(sm_ctx *ctx, int top, int norm_slot = -1) {
+  int st;
+  if (norm_slot >= 0)
+    SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
+  for (int l = top; l >= 1; --l) {
+    if ((st = fx_smooth(ctx, l, ctx->cfg.nu1))) return st;
+    sm_launch(ctx, fx::k_fresid_restrict, lvl_n(ctx, l), GT, 0, ctx->level_off[l], ctx->phx, ctx->gx, ctx->ghx,
+              ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
+    sm_launch(ctx, fx::k_ffas, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx, (long long *)ctx->old,
+              ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
+    SM_CKL("vcycle down");
+  }
+  if ((st = fx_coarse(ctx))) return st;
+  for (int l = 1; l <= top; ++l) {
+    if ((st = fx_prolong(ctx, l, 0, fx_norm_of(ctx, norm_slot >= 0 ? l - 1 : -1, norm_slot)))) return st;
+    if ((st = fx_smooth(ctx, l, ctx->cfg.nu2))) return st;
+  }
+  if (norm_slot >= 0) {
+    const int off = ctx->leaf_level_off[top];
+    return fx_leaf_norm(ctx, off, ctx->leaf_level_off[top + 1] - off, norm_slot);
+  }
+  return SM_OK;
+}
+
+// FMG ladder on the restricted right-hand side: level-0 solve, then for
+// each finer level the prolonged solution and one V-cycle with that level
+// on top (the residual of the result in norm_slot)
+static int fx_fmg_ladder(sm_ctx *ctx, int norm_slot) {
+  int st;
+  if ((st = fx_coarse(ctx))) return st;
+  for (int l = 1; l < ctx->n_levels; ++l) {
+    if ((st = fx_prolong(ctx, l, 1, fx::FxNorm{}))) return st;
+    if ((st = fx_vcycle(ctx, l, l == ctx->n_levels - 1 ? norm_slot : -1))) return st;
+  }
+  if (ctx->n_levels == 1) {
+    SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
+    return fx_leaf_norm(ctx, 0, ctx->n_leaves, norm_slot);
+  }
+  return SM_OK;
+}
+
+// Work of an FP64 solve before its cycle loop: the residual of phi = 0
+// (denominator, in FP64 with old as the zero field), the restricted rhs of
+// FMG, the fixed-point scale and arrays; FMG then runs its ladder (leaving
+// the residual of its result in SC_NORM) unless the persistent kernel will.
+static int fx_solve_prefix(sm_ctx *ctx, int fmg, bool ladder) {
+  int st;
+  SM_CK(cudaMemsetAsync(ctx->old, 0, sizeof(double) * CELLS * (size_t)ctx->n_boxes, ctx->stream));
+  if ((st = sm_fill_all_cf(ctx, ctx->old))) return st;
+  if ((st = leaf_norm(ctx, ctx->old, SC_DEN))) return st;
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_CYC, 0, sizeof(unsigned long long), ctx->stream));
+  if (fmg && (st = restrict_chain<double>(ctx, ctx->rhs, nullptr))) return st;
+  if ((st = fx_prologue(ctx, !fmg))) return st;
+  if (fmg && ladder) return fx_fmg_ladder(ctx, SC_NORM);
+  return SM_OK;
+}
+
 // ---- solve bodies shared by the graph and the direct paths ----------------
 //
 // kind 0: FP64 solve (warm start), 1: FP64 FMG, 2: mixed solve, 3: mixed FMG.
@@ -1261,10 +1671,8 @@ static int solve_prefix(sm_ctx *ctx, int kind) {
   int st;
   switch (kind) {
     case 0:
-      return solve_prologue(ctx);
     case 1:
-      if ((st = solve_prologue(ctx))) return st;
-      return fmg_ladder(ctx, mg64(ctx), SC_NORM);
+      return fx_solve_prefix(ctx, kind, true);
     case 2:
       if ((st = solve_prologue(ctx))) return st;
       return leaf_resid32(ctx);
@@ -1282,8 +1690,11 @@ static int solve_prefix(sm_ctx *ctx, int kind) {
 
 static int solve_body(sm_ctx *ctx, int kind) {
   if (kind >= 2) return mixed_correction(ctx, 0);
-  return vcycle(ctx, mg64(ctx), ctx->n_levels - 1, SC_NORM);
+  return fx_vcycle(ctx, ctx->n_levels - 1, SC_NORM);
 }
+
+// work after the cycle loop: the FP64 kinds convert the fixed-point result
+static int solve_suffix(sm_ctx *ctx, int kind) { return kind < 2 ? fx_epilogue(ctx) : SM_OK; }
 
 // ---- graph-captured solves with a device-side cycle loop ------------------
 
@@ -1333,16 +1744,18 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   }
   const int fmg = kind == 1 || kind == 3;
   if (ctx->persist) {
-    int st = kind < 2 ? persist_prepare<double>(ctx) : persist_prepare<float>(ctx);
+    int st = kind < 2 ? persistx_prepare(ctx) : persist_prepare32(ctx);
     if (st) return st;
   }
   if (ctx->persist && kind < 2) {
-    // prologue + one persistent launch holding the cycle loop
+    // prefix + one persistent launch holding the FMG ladder and the cycle
+    // loop + the conversion of the result
     SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     ctx->stream = ctx->cap;
     long long n0 = ctx->n_launch;
-    int st = solve_prologue(ctx);
-    if (!st) st = persist_launch(ctx, mg64(ctx), ctx->n_levels - 1, fmg, 1);
+    int st = fx_solve_prefix(ctx, fmg, false);
+    if (!st) st = persistx_launch(ctx, ctx->n_levels - 1, fmg, 1);
+    if (!st) st = fx_epilogue(ctx);
     if (st) return end_captures(ctx, saved, st);
     out->prefix_launches = ctx->n_launch - n0;
     out->body_launches = 0;
@@ -1403,6 +1816,9 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   if (cudaStreamEndCapture(ctx->cap2, &body) != cudaSuccess)
     return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end body capture"));
   ctx->stream = ctx->cap;
+  n0 = ctx->n_launch;
+  if ((st = solve_suffix(ctx, kind))) return end_captures(ctx, saved, st);
+  out->prefix_launches += ctx->n_launch - n0;
   if (cudaStreamEndCapture(ctx->cap, &whole) != cudaSuccess)
     return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end capture"));
   ctx->stream = saved;
@@ -1414,31 +1830,31 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   return SM_OK;
 }
 
-static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycles, double *rel_res) {
+// One attempt of a solve: SM_OK with the cycle count and relative
+// residual, SM_FX_RETRY when the fixed-point potential left its range (phi
+// is then unchanged), or an error.
+static int run_solve_once(sm_ctx *ctx, int kind, double tol, int max_cycles, int *cycles, double *rel_res) {
   int st;
   int c = 0;
   double rel = 0.0;
-  const int kind = (ctx->cfg.precision == SM_MIXED ? 2 : 0) + (fmg ? 1 : 0);
-  // stopping parameters of the device-side loops
-  ctx->hscal[SC_TOL] = tol;
-  unsigned long long mc = (unsigned long long)max_cycles;
-  memcpy(&ctx->hscal[SC_MAXC], &mc, sizeof mc);
-  SM_CK(cudaMemcpyAsync(ctx->dscal + SC_TOL, ctx->hscal + SC_TOL, 2 * sizeof(double), cudaMemcpyHostToDevice,
-                        ctx->stream));
+  const int fmg = kind & 1;
+  if (kind < 2 && (st = fx_set_margin(ctx))) return st;
   if (ctx->graphs) {
     sm_graph *g = graph_of(ctx, kind);
     if (!g->exec && (st = capture_solve(ctx, kind, g))) return st;
     SM_CK(cudaGraphLaunch(g->exec, ctx->stream));
-    if ((st = read_scalars(ctx))) return st;
+    st = read_scalars(ctx);
     unsigned long long cc;
     memcpy(&cc, &ctx->hscal[SC_CYC], sizeof cc);
     c = (int)cc;
     rel = ctx->hscal[SC_REL];
     ctx->n_launch += g->prefix_launches + g->body_launches * (long long)(fmg ? c - 1 : c);
+    if (st) return st;
   } else if (ctx->persist && kind < 2) {
     if ((st = ensure_basis(ctx))) return st;
-    if ((st = solve_prologue(ctx))) return st;
-    if ((st = persist_launch(ctx, mg64(ctx), ctx->n_levels - 1, fmg, 1))) return st;
+    if ((st = fx_solve_prefix(ctx, fmg, false))) return st;
+    if ((st = persistx_launch(ctx, ctx->n_levels - 1, fmg, 1))) return st;
+    if ((st = fx_epilogue(ctx))) return st;
     if ((st = read_scalars(ctx))) return st;
     unsigned long long cc;
     memcpy(&cc, &ctx->hscal[SC_CYC], sizeof cc);
@@ -1463,7 +1879,41 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
       rel = den > 0.0 ? num / den : num;
       go = rel > tol && c < max_cycles;
     }
+    if ((st = solve_suffix(ctx, kind))) return st;
   }
+  *cycles = c;
+  *rel_res = rel;
+  return SM_OK;
+}
+
+// after an attempt that left the fixed-point range: clear the flag and
+// widen the scale (false when the margin is exhausted)
+static int fx_widen(sm_ctx *ctx, bool *again) {
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_ERR, 0, sizeof(unsigned long long), ctx->stream));
+  *again = ctx->fx_margin < 5 + 4 * 8;
+  if (*again) ctx->fx_margin += 8;
+  return SM_OK;
+}
+
+static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycles, double *rel_res) {
+  int st;
+  int c = 0;
+  double rel = 0.0;
+  const int kind = (ctx->cfg.precision == SM_MIXED ? 2 : 0) + (fmg ? 1 : 0);
+  // stopping parameters of the device-side loops
+  ctx->hscal[SC_TOL] = tol;
+  unsigned long long mc = (unsigned long long)max_cycles;
+  memcpy(&ctx->hscal[SC_MAXC], &mc, sizeof mc);
+  SM_CK(cudaMemcpyAsync(ctx->dscal + SC_TOL, ctx->hscal + SC_TOL, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                        ctx->stream));
+  while ((st = run_solve_once(ctx, kind, tol, max_cycles, &c, &rel)) == SM_FX_RETRY) {
+    bool again = false;
+    if ((st = fx_widen(ctx, &again))) return st;
+    if (!again)
+      return sm_fail(ctx, SM_ENOCONV, "potential or right-hand side not finite or beyond 2^%d of its scale",
+                     ctx->fx_margin);
+  }
+  if (st) return st;
   if (cycles) *cycles = c;
   if (rel_res) *rel_res = rel;
   return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
@@ -1490,9 +1940,19 @@ extern "C" int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res) {
   if (st) return st;
   if (n_cycles < 0) return SM_EINVAL;
   if ((st = ensure_basis(ctx))) return st;
-  if ((st = solve_prologue(ctx))) return st;
-  for (int c = 0; c < n_cycles; ++c)
-    if ((st = cycle(ctx, mg64(ctx), ctx->n_levels - 1))) return st;
+  const int top = ctx->n_levels - 1;
+  for (;;) {
+    if ((st = fx_set_margin(ctx))) return st;
+    if ((st = fx_solve_prefix(ctx, 0, false))) return st;
+    for (int c = 0; c < n_cycles; ++c)
+      if ((st = ctx->persist ? persistx_launch(ctx, top, 0, 0) : fx_vcycle(ctx, top))) return st;
+    if ((st = fx_epilogue(ctx))) return st;
+    if ((st = read_scalars(ctx)) != SM_FX_RETRY) break;
+    bool again = false;
+    if ((st = fx_widen(ctx, &again))) return st;
+    if (!again) return sm_fail(ctx, SM_ENOCONV, "potential or right-hand side beyond the fixed-point range");
+  }
+  if (st) return st;
   double rel = 0.0;
   if ((st = rel_residual(ctx, &rel))) return st;
   if (rel_res) *rel_res = rel;
@@ -1528,7 +1988,7 @@ extern "C" int sm_persist_barrier_selftest(sm_ctx *ctx) {
   if ((st = ensure_basis(ctx))) return st;
   if ((st = read_scalars(ctx))) return st;  // no earlier error may be pending
   // every barrier waits for one block more than the grid holds
-  if ((st = persist_launch(ctx, mg64(ctx), ctx->n_levels - 1, 0, 0, 1))) return st;
+  if ((st = persistx_launch(ctx, ctx->n_levels - 1, 0, 0, 1))) return st;
   st = read_scalars(ctx);
   // the launch ended by itself: clear its flag so the context stays usable
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_ERR, 0, sizeof(unsigned long long), ctx->stream));
@@ -1550,19 +2010,25 @@ extern "C" int sm_set_pdl(sm_ctx *ctx, int enable) {
   return SM_OK;
 }
 
-// Algorithmic bytes and FP64 instructions of one FP64 V-cycle from `top`
-// (the per-level model stated with sm_kernel_bench).
-static void vcycle_model(const sm_ctx *ctx, int top, double *bytes, double *ops) {
+// Algorithmic bytes and FP64 instructions of one V-cycle from `top` (the
+// per-level model stated with sm_kernel_bench).  fixed: the FP64 solve's
+// fixed-point cycle (colour passes of 12 B per cell in its colour-split
+// layout, no FP64 work outside the level-0 solve); otherwise the FP32
+// cycle of the mixed form (colour passes of 8 B per cell).
+static void vcycle_model(const sm_ctx *ctx, int top, bool fixed, double *bytes, double *ops) {
   double by = 16.0 * CELLS, op = 60.0 * CELLS;  // level-0 solve
   const double sweeps = ctx->cfg.nu1 + ctx->cfg.nu2;
   for (int l = 1; l <= top; ++l) {
     const double n = (double)CELLS * lvl_n(ctx, l), nc = (double)CELLS * lvl_n(ctx, l - 1);
     const double refined = n / 8.0;  // cells of the refined boxes of level l-1
-    by += sweeps * 2.0 * 16.0 * n + 18.0 * n + 16.0 * nc + 16.0 * refined + 18.0 * n;
-    op += sweeps * 7.0 * n + 9.0 * n + 7.0 * refined + 3.0 * n;
+    if (fixed) {
+      by += sweeps * 24.0 * n + 18.0 * n + 16.0 * nc + 16.0 * refined + 18.0 * n;
+    } else {
+      by += 0.5 * (sweeps * 2.0 * 16.0 * n + 18.0 * n + 16.0 * nc + 16.0 * refined + 18.0 * n);
+    }
   }
   *bytes = by;
-  *ops = op;
+  *ops = fixed ? op : 0.0;
 }
 
 // Average launch duration of a kernel class (see the header for the
@@ -1574,16 +2040,19 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   if (kclass < 0 || kclass >= K_NCLASS || reps < 1) return SM_EINVAL;
   int top = ctx->n_levels - 1;
   if (top < 1) return SM_EINVAL;
-  if (kclass == K_PERSIST) {
+  if (kclass != K_VCYCLE32) {
+    // the fixed-point arrays and scale of the current potential
     if ((st = ensure_basis(ctx))) return st;
-    if ((st = solve_prologue(ctx))) return st;
-    MG<double> m = mg64(ctx);
-    if ((st = persist_launch(ctx, m, top, 0, 0))) return st;  // warm
+    if ((st = fx_set_margin(ctx))) return st;
+    if ((st = fx_solve_prefix(ctx, 0, false))) return st;
+  }
+  if (kclass == K_PERSIST) {
+    if ((st = persistx_launch(ctx, top, 0, 0))) return st;  // warm
     cudaEvent_t a, b;
     SM_CK(cudaEventCreate(&a));
     SM_CK(cudaEventCreate(&b));
     SM_CK(cudaEventRecord(a, ctx->stream));
-    for (int r = 0; r < reps && !st; ++r) st = persist_launch(ctx, m, top, 0, 0);
+    for (int r = 0; r < reps && !st; ++r) st = persistx_launch(ctx, top, 0, 0);
     SM_CK(cudaEventRecord(b, ctx->stream));
     SM_CK(cudaEventSynchronize(b));
     float ms = 0.f;
@@ -1591,9 +2060,10 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st) return st;
-    if ((st = read_scalars(ctx))) return st;
+    if ((st = read_scalars(ctx)) && st != SM_FX_RETRY) return st;
+    if (st == SM_FX_RETRY) SM_CK(cudaMemsetAsync(ctx->dscal + SC_ERR, 0, sizeof(unsigned long long), ctx->stream));
     double by, fl;
-    vcycle_model(ctx, top, &by, &fl);
+    vcycle_model(ctx, top, true, &by, &fl);
     if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
     if (launches) *launches = reps;
     if (bytes_per_launch) *bytes_per_launch = by;
@@ -1603,19 +2073,20 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   const bool whole = kclass == K_VCYCLE || kclass == K_VCYCLE32;
   if (kclass == K_VCYCLE32 && ctx->cfg.precision != SM_MIXED)
     return sm_fail(ctx, SM_EINVAL, "class 3 needs a mixed-precision context");
-  if (whole && (st = ensure_basis(ctx))) return st;
-  if (whole && (st = solve_prologue(ctx))) return st;
-  if (kclass == K_VCYCLE32 && (st = leaf_resid32(ctx))) return st;
+  if (kclass == K_VCYCLE32) {
+    if ((st = ensure_basis(ctx))) return st;
+    if ((st = solve_prologue(ctx))) return st;
+    if ((st = leaf_resid32(ctx))) return st;
+  }
   cudaStream_t saved = ctx->stream;
   if (!ctx->cap) SM_CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
   SM_CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
   ctx->stream = ctx->cap;
   long long n = 0, n0 = ctx->n_launch;
   double bytes = 0.0;
-  MG<double> m = mg64(ctx);
   for (int r = 0; r < reps; ++r) {
     if (kclass == K_VCYCLE) {
-      if ((st = vcycle(ctx, m, top))) break;
+      if ((st = fx_vcycle(ctx, top))) break;
       ++n;
       continue;
     }
@@ -1624,12 +2095,13 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
       ++n;
       continue;
     }
-    for (int l = top; l >= 1; --l)
-      for (int color = 0; color < 2; ++color) {
-        rbgs_pass(ctx, m, l, color);
-        ++n;
-        bytes += (double)lvl_n(ctx, l) * CELLS * 16.0;
-      }
+    // one red-black sweep (two colour passes) per level
+    for (int l = top; l >= 1; --l) {
+      if ((st = fx_smooth(ctx, l, 1))) break;
+      n += 2;
+      bytes += 2.0 * (double)lvl_n(ctx, l) * CELLS * 12.0;
+    }
+    if (st) break;
   }
   const long long kernels = ctx->n_launch - n0;
   cudaGraph_t g = nullptr;
@@ -1663,16 +2135,12 @@ extern "C" int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per
   if (launches) *launches = n;
   if (whole) {
     double by, fl;
-    vcycle_model(ctx, top, &by, &fl);
-    if (kclass == K_VCYCLE32) {  // same cells, 4-byte values, no FP64 work
-      by *= 0.5;
-      fl = 0.0;
-    }
+    vcycle_model(ctx, top, kclass == K_VCYCLE, &by, &fl);
     if (bytes_per_launch) *bytes_per_launch = by;
     if (flops_per_launch) *flops_per_launch = fl;
     return SM_OK;
   }
   if (bytes_per_launch) *bytes_per_launch = bytes / n;
-  if (flops_per_launch) *flops_per_launch = 3.5 * bytes / 16.0 / n;  // 7 per updated cell
+  if (flops_per_launch) *flops_per_launch = 0.0;  // integer arithmetic only
   return SM_OK;
 }

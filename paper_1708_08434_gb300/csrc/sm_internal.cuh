@@ -101,6 +101,12 @@ struct sm_ctx {
   double *ibuf[3] = {nullptr, nullptr, nullptr};  // ion density buffers
   int ncur = 0;                                   // current density buffer
   double *gh = nullptr;      // [max_boxes][6][64] coarse interpolation values
+  // fixed-point potential of the FP64 solve and its rhs term -h^2 f / 6
+  // (colour-split order within a box), and the refinement-face sums
+  // 2c + c_t1 + c_t2, all in quanta of the solve
+  long long *phx = nullptr, *gx = nullptr;                  // [max_boxes][512]
+  long long *ghx = nullptr;                                 // [max_boxes][6][64]
+  int fx_margin = 5;         // exponent margin of the fixed-point scale
   // FP32 error-equation arrays of the mixed-precision solve
   float *e32 = nullptr, *f32 = nullptr, *old32 = nullptr;  // [max_boxes][512]
   float *gh32 = nullptr;                                    // [max_boxes][6][64]
@@ -172,7 +178,11 @@ enum {
   SC_PN0 = 10,      // residual max of the persistent loop, even passes
   SC_PN1 = 11,      // residual max of the persistent loop, odd passes
   SC_BAR = 12,      // grid barrier arrival counter of the persistent kernel
-  SC_N = 16
+  SC_FXE = 16,      // fixed-point solve: exponent E of the quantum 2^(E - 1080)
+  SC_FXI = 17,      // fixed-point solve: exponent bound of the inputs (reduction)
+  SC_FXM = 18,      // fixed-point solve: margin added to the bound, set before a solve
+  SC_FX2G = 19,     // fixed-point solve: 2g of the six faces in quanta (19 .. 24)
+  SC_N = 32
 };
 
 namespace sm {

@@ -335,8 +335,9 @@ def test_repeated_graph_launch_and_launch_count():
     n2 = g.launch_count()
     assert r1[:3] == r2[:3]
     assert n2 - n1 == n1 - n0 - 1  # first call also built the level-0 basis
+    # two fused red-black sweeps per level and repetition, integer arithmetic only
     us, n, by, fl = g.kernel_bench(0, 3)
-    assert us > 0 and n == 3 * 2 * (g.n_levels - 1) and by > 0 and fl == pytest.approx(3.5 * by / 16)
+    assert us > 0 and n == 3 * 2 * (g.n_levels - 1) and by > 0 and fl == 0
     us, n, by, fl = g.kernel_bench(1, 3)
     assert us > 0 and n == 3 and by > 0 and fl > 0
     us2, n2, by2, fl2 = g.kernel_bench(2, 3)
