@@ -39,16 +39,16 @@ NO_PDL = False
 PERSIST = False
 
 
-# DRAM bytes (read + write) per k_rbgs launch, mean over the 72 colour passes
-# of one streamer6 V-cycle (the mix the roofline's achieved figure averages):
-#   python bench.py --mode vcycle --steps 1 --no-graphs &&
+# DRAM bytes (read + write) per k_fcolor launch, mean over the colour
+# passes of one kernel-bench sweep of every level of the benchmark mesh (the
+# mix the roofline's achieved figure averages); taken with
+#   python bench.py --mode kernels &&
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
-#       --clock-control none -k regex:k_rbgs --csv --log-file rbgs_dram.csv \
-#       python bench.py --mode vcycle --steps 1 --no-graphs
-# 370.0 MB read, 0 written over 72 launches (cold caches between launches).
-RBGS_TRAFFIC_PER_LAUNCH = 5139556
-RBGS_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 72 k_rbgs launches of one "
-                     "V-cycle (cold caches): 1.05x the algorithmic bytes per launch")
+#       --clock-control none -k regex:k_fcolor --csv --log-file fcolor_dram.csv \
+#       python bench.py --mode kernels
+# None until counters of the current kernel are recorded.
+FCOLOR_TRAFFIC_PER_LAUNCH = None
+FCOLOR_TRAFFIC_NOTE = "no ncu counters of the current k_fcolor recorded yet"
 
 
 def parse():
@@ -74,7 +74,7 @@ def parse():
                     help="run V-cycles as one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the solver kernels without programmatic dependent launch")
-    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "batch", "large", "axi"],
+    ap.add_argument("--mode", default="step", choices=["step", "vcycle", "kernels", "batch", "large", "axi"],
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
                          "schedule (small, fixed launch sequences for ncu captures); "
@@ -122,10 +122,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 pipe of GB300: 2 instructions per clock per SM (nominal 1.25 TFLOP/s
-# counting a fused multiply-add as 2; a DFMA loop measured 1.19-1.20 TFLOP/s
-# at 1.9-2.07 GHz), 152 SMs x 2.07 GHz x 2 = 629 G FP64 instructions/s
-FP64_PEAK_GINSTR = 629.0
+_FP64 = {}
+
+
+def fp64_rate():
+    """Measured FP64-pipe throughput in G instructions/s (probed once)."""
+    if "v" not in _FP64:
+        _FP64["v"] = fp64_peak()
+    return _FP64["v"]["ginstr_per_s"]
+
+
+def fp64_peak():
+    """The FP64 pipe's throughput measured on this GPU (sm_fp64_probe: 8
+    independent fused multiply-add chains per thread on every SM), with the
+    SM clocks sampled while it ran: G FP64 instructions/s."""
+    import torch
+    import paper_1708_08434_gb300 as pkg
+    pkg.fp64_probe(1 << 12)
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    rate, ms = pkg.fp64_probe(1 << 18)
+    clocks = clk.stop()
+    return {"ginstr_per_s": round(rate / 1e9, 1), "probe_ms": round(ms, 2), "clocks": clocks,
+            "how": "sm_fp64_probe: 8 x 256 threads per SM, 8 independent DFMA chains each"}
 
 
 class Clocks:
@@ -284,13 +304,12 @@ def large_mesh():
         kc = pkg.K_VCYCLE if prec == 0 else pkg.K_VCYCLE32
         us, n, by, fl = g.kernel_bench(kc, 5)
         r["vcycle"] = {"us": round(us, 1), "bytes": int(by), "hbm_frac": round(by / (us * 1e-6) / 1e9 / peak, 4)}
-        if fl:
-            r["vcycle"]["fp64_frac"] = round(fl / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4)
+        r["vcycle"]["gbs"] = round(by / (us * 1e-6) / 1e9, 1)
         if prec == 0:
             us, n, by, fl = g.kernel_bench(pkg.K_SMOOTH, 5)
-            r["k_rbgs"] = {"avg_launch_us": round(us, 2), "launches": n,
-                           "fp64_frac": round(fl / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4),
-                           "hbm_frac": round(by / (us * 1e-6) / 1e9 / peak, 4)}
+            r["k_fcolor"] = {"avg_launch_us": round(us, 2), "launches": n,
+                             "gbs": round(by / (us * 1e-6) / 1e9, 1),
+                             "hbm_frac": round(by / (us * 1e-6) / 1e9 / peak, 4)}
         out[name] = r
         g.close()
         del g
@@ -367,6 +386,21 @@ def run_gpu(args):
 
     step, timed = make_step(g)
 
+    if args.mode == "kernels":
+        # one kernel-bench pass of the colour kernel over every level and one
+        # V-cycle (the launches the roofline times; a small command for ncu)
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        out = {"mode": "kernels"}
+        for kc, name in ((pkg.K_SMOOTH, "k_fcolor"), (pkg.K_VCYCLE, "vcycle")):
+            us, n, by, fl = g.kernel_bench(kc, 1)
+            out[name] = {"avg_launch_us": round(us, 3), "launches": n, "bytes_per_launch": round(by)}
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        g.close()
+        return
     if args.mode == "vcycle":
         g.var(pkg.NE).copy_(ne_d)
         g.var(pkg.NI).copy_(ni_d)
@@ -389,46 +423,66 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(ms, dev)
+    # the FMG solve alone (the unit the CPU oracle's single-solve figure times)
+    fmg_only = None
+    if not args.no_profile:
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        g.charge_rhs(Q, E0)
+        g.fmg(TOL, MAX_CYCLES)
+        torch.cuda.synchronize()
+        fa = torch.cuda.Event(enable_timing=True)
+        fb = torch.cuda.Event(enable_timing=True)
+        fa.record(stream)
+        for _ in range(10):
+            g.charge_rhs(Q, E0)
+            _, _, fcyc = g.fmg(TOL, MAX_CYCLES)
+        fb.record(stream)
+        torch.cuda.synchronize()
+        fmg_only = {"solves_per_s": round(10 / (fa.elapsed_time(fb) * 1e-3), 2), "vcycles": fcyc,
+                    "note": "FMG to 1e-8 from phi = 0 on the same workload, 10 solves timed with CUDA events "
+                            "(L2 not flushed)"}
     # end to end through the C ABI with host buffers (H2D + D2H every step)
     e2e_ms, _, _ = timed(args.steps, host_io=True)
     e2e_ms = max_over_ranks(e2e_ms, dev)
-    # roofline of the dominant kernel: the red-black smoother, timed with
-    # CUDA events around a graph of its launches in the V-cycle mix (every
-    # level, both colours), or with --persistent the persistent V-cycle
-    # kernel (one cooperative launch per V-cycle, 20 launches); beside it the
-    # whole FP64 V-cycle of the per-level path (graph of 10 V-cycles)
+    # roofline of the dominant kernel: a colour pass of the red-black
+    # smoother (k_fcolor), timed with CUDA events around a graph of its
+    # launches in the V-cycle mix (every level, both colours), or with
+    # --persistent the persistent V-cycle kernel (one cooperative launch per
+    # V-cycle); beside it the whole FP64 V-cycle of the per-level path
     roof = None
+    f64 = None
+    if not args.no_profile:
+        fp64_rate()
+        f64 = _FP64["v"]
     if not args.no_profile:
         kclass = pkg.K_PERSIST if PERSIST else pkg.K_SMOOTH
         us, kn, kbytes, kflops = g.kernel_bench(kclass, 20)
         peak, kind = measured_peaks()
         gbs = kbytes / (us * 1e-6) / 1e9
-        ginstr = kflops / (us * 1e-6) / 1e9
-        # FP64 at 1/64 rate makes the level operations ALU-bound: a smoothing
-        # pass at 6780 GB/s moves 424 G cells/s and would need 3.5 x 424 =
-        # 1480 G FP64 instructions/s, above the 629 G/s of the FP64 pipe
-        roof = {"bound": "alu", "achieved": round(ginstr, 2), "peak": FP64_PEAK_GINSTR,
-                "unit": "G FP64 instructions/s", "frac": round(ginstr / FP64_PEAK_GINSTR, 4),
-                "traffic": None if PERSIST else RBGS_TRAFFIC_PER_LAUNCH,
-                "traffic_note": None if PERSIST else RBGS_TRAFFIC_NOTE,
-                "kernel": "k_persist" if PERSIST else "k_rbgs", "launches": kn,
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "peak_kind": kind + " (copy bandwidth)",
+                "traffic": None if PERSIST else FCOLOR_TRAFFIC_PER_LAUNCH,
+                "traffic_note": None if PERSIST else FCOLOR_TRAFFIC_NOTE,
+                "kernel": "k_persistx" if PERSIST else "k_fcolor", "launches": kn,
                 "avg_launch_us": round(us, 3), "bytes_per_launch": round(kbytes),
+                "bytes_model": ("12 B per cell of the level and colour pass: the other colour's potential "
+                                "and this colour's G read (4 + 4), this colour written (4); int64 fixed point"
+                                if not PERSIST else "V-cycle model, 24 B per cell and sweep"),
                 "fp64_instr_per_launch": round(kflops),
-                "hbm": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(gbs / peak, 4), "peak_kind": kind},
                 "note": ("mean over %d graph-launched colour passes of every level "
-                         "(the V-cycle mix), CUDA events on the launching stream" % kn) if not PERSIST else
-                        ("mean over %d launches, each one whole FP64 V-cycle, CUDA events on the "
-                         "launching stream; bytes and FP64 instructions from the per-level model" % kn)}
+                         "(the V-cycle mix), CUDA events on the launching stream; the level "
+                         "kernels use no FP64 instruction" % kn) if not PERSIST else
+                        ("mean over %d launches, each one whole V-cycle, CUDA events on the "
+                         "launching stream; bytes from the per-level model" % kn)}
         if not PERSIST:
             vus, vn, vbytes, vinstr = g.kernel_bench(pkg.K_VCYCLE, 10)
             roof["vcycle"] = {"us": round(vus, 2), "cycles": vn, "bytes": round(vbytes),
-                              "fp64_instr": round(vinstr),
-                              "achieved": round(vinstr / (vus * 1e-6) / 1e9, 2),
-                              "frac": round(vinstr / (vus * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4),
+                              "gbs": round(vbytes / (vus * 1e-6) / 1e9, 1),
                               "hbm_frac": round(vbytes / (vus * 1e-6) / 1e9 / peak, 4),
-                              "note": "whole FP64 V-cycle, per-level launches in a CUDA graph, "
-                                      "model bytes and FP64 instructions"}
+                              "fp64_instr": round(vinstr),
+                              "note": "whole FP64 V-cycle (fixed-point level kernels, FP64 level-0 solve), "
+                                      "per-level launches in a CUDA graph, bytes from the per-level model"}
     # the same step with the mixed-precision solve (FP32 error equation in an
     # FP64 defect-correction loop) on a second solver of the same workload
     mixed = None
@@ -493,9 +547,10 @@ def run_gpu(args):
             return a.elapsed_time(b) * 1e3 / n
 
         peak, _ = measured_peaks()
+        fpk = f64["ginstr_per_s"] if f64 else None
         fus = per_call(g.compute_field)
         sus = per_call(lambda: g.fluid_stage(dt))
-        fluid = {}
+        fluid = {"fp64_peak": f64}
         # FP64 instructions per leaf cell as counted by ncu on this workload
         # (sm__inst_executed_pipe_fp64: k_field 27.4 with the FP64 square
         # root of |E|, stage-1 k_update 112.8); bytes: compulsory traffic
@@ -503,7 +558,7 @@ def run_gpu(args):
             fluid[name] = {"us": round(us, 2), "gbs": round(leaf_cells * bpc / (us * 1e-6) / 1e9, 1),
                            "hbm_frac": round(leaf_cells * bpc / (us * 1e-6) / 1e9 / peak, 4),
                            "fp64_ginstr": round(leaf_cells * ipc / (us * 1e-6) / 1e9, 1),
-                           "fp64_frac": round(leaf_cells * ipc / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4),
+                           "fp64_frac": (round(leaf_cells * ipc / (us * 1e-6) / 1e9 / fpk, 4) if fpk else None),
                            "model_per_leaf_cell": {"bytes": bpc, "fp64_instr": ipc}}
     # the paper's schedule (Sec. 2.1.2, 2.4): one FMG solve, then Heun steps
     # with exactly two V-cycles per potential update and the time step from
@@ -572,6 +627,7 @@ def run_gpu(args):
                   "dropped": ndrop, "criterion": "c0=0.25 (paper: 1), c1=1.2, buffer 3; flags with the paper's "
                                                  "c0=1, c0_deref=1/8, dx_deref=30 um"}
     large = None if (args.no_large or rank != 0) else large_mesh()
+    configs = None if (args.no_large or rank != 0) else bench_configs()
     axi = None if args.no_axi else bench_axisymmetric(args, dev, world)
     batched = None if args.no_batch else bench_batch(args, dev, world)
     learned = None if args.no_learned else bench_learned(args, dev, world)
@@ -596,11 +652,13 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(2 * phi_out.numel() * 8)},
         "gpu_launches": launches,
         "clocks": clocks,
+        "fmg_only": fmg_only,
         "roofline": roof,
         "mixed_precision": mixed,
         "field_and_fluid": fluid,
         "paper_schedule": paper,
         "large_mesh": large,
+        "other_configs": configs,
         "regrid": regrid,
         "axisymmetric": axi,
         "batched": batched,
@@ -614,6 +672,99 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def bench_configs():
+    """The other single-GPU configurations at their own sizes:
+    uniform64 -- FP64 V(2,2) cycles to rel residual 1e-10 on the unit cube,
+    64^3 cells in 512 boxes, Gaussian charge plus 1e-3 seeded noise: solves
+    from phi = 0 and FMG, timed with CUDA events;
+    streamer8 -- the mixed-precision form on the 8-level mesh (1.7e7 leaf
+    cells): FMG to 1e-8, and its potential and |E| against the FP64 path
+    solved to 1e-12 on the same charge (the FP64 path matches the CPU oracle
+    element by element)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1708_08434_gb300 as pkg
+    Q, E0 = synth.E_CHARGE, synth.EPS0
+    out = {}
+
+    def ev(g, fn, n=1):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(g.stream)
+        for _ in range(n):
+            r = fn()
+        b.record(g.stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n, r
+
+    dom = synth.domain_uniform_cube(64)
+    g = pkg.Solver(dom, 1024)
+    g.build_octree()
+    t = g.tables()
+    rho = synth.gaussian_charge(dom, t["level"], t["ijk"], np.arange(len(t["level"])))
+    g.upload(pkg.RHO, rho)
+    g.charge_rhs(1.0, 1.0, True)
+    cells = g.n_leaves * 512
+
+    def from_zero():
+        g.var(pkg.PHI).zero_()
+        return g.solve(1e-10, 100)
+
+    from_zero()
+    ms_v, (rc, rel, cyc) = ev(g, from_zero, 10)
+    ms_f, (rcf, relf, cycf) = ev(g, lambda: g.fmg(1e-10, 100), 10)
+    us_vc, _, by_vc, _ = g.kernel_bench(pkg.K_VCYCLE, 20)
+    out["uniform64"] = {
+        "cells": cells, "levels": g.n_levels, "tol": 1e-10,
+        "vcycles_from_zero": {"solves_per_s": round(1e3 / ms_v, 1), "ms": round(ms_v, 3), "vcycles": cyc,
+                              "rel_residual": rel},
+        "fmg": {"solves_per_s": round(1e3 / ms_f, 1), "ms": round(ms_f, 3), "vcycles": cycf, "rel_residual": relf},
+        "vcycle_us": round(us_vc, 2),
+        "mcells_vcycles_per_s": round(cells * cyc / (ms_v * 1e-3) / 1e6, 1),
+        "note": "the working set (about 40 MB) stays in L2; L2 not flushed"}
+    g.close()
+
+    dom, st = synth.workload("streamer8")
+    sides = {}
+    ne = ni = None
+    for prec, name in ((0, "fp64"), (pkg.MIXED, "mixed")):
+        g = pkg.Solver(dom, max_boxes=1 << 16, precision=prec)
+        g.build_octree()
+        synth.refine_all(dom, st, g.level_ijk, g.refine_level)
+        if ne is None:
+            t = g.tables()
+            ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+        g.upload(pkg.NE, ne)
+        g.upload(pkg.NI, ni)
+        g.charge_rhs(Q, E0)
+        sides[name] = g
+    gf, gm = sides["fp64"], sides["mixed"]
+    gm.fmg(TOL, MAX_CYCLES)
+    ms_m, (rcm, relm, cycm) = ev(gm, lambda: gm.fmg(TOL, MAX_CYCLES), 5)
+    ms_d, (rcd, reld, cycd) = ev(gf, lambda: gf.fmg(TOL, MAX_CYCLES), 5)
+    gf.fmg(1e-12, 60)
+    gm.fmg(TOL, MAX_CYCLES)
+    gf.compute_field()
+    gm.compute_field()
+    leaf = torch.from_numpy(np.asarray(gf.tables()["leaf"], dtype=np.int64)).to(gf.var(pkg.PHI).device)
+    p64, p32 = gf.var(pkg.PHI)[leaf], gm.var(pkg.PHI)[leaf]
+    e64, e32 = gf.var(pkg.EMAG)[leaf], gm.var(pkg.EMAG)[leaf]
+    out["streamer8_mixed"] = {
+        "leaf_cells": gf.n_leaves * 512, "boxes": gf.n_boxes, "levels": gf.n_levels, "tol": TOL,
+        "mixed": {"solves_per_s": round(1e3 / ms_m, 2), "ms": round(ms_m, 3), "corrections": cycm},
+        "fp64": {"solves_per_s": round(1e3 / ms_d, 2), "ms": round(ms_d, 3), "vcycles": cycd},
+        "speedup_mixed_vs_fp64": round(ms_d / ms_m, 3),
+        "error_vs_fp64": {"phi_max_rel": float((p32 - p64).abs().max() / p64.abs().max()),
+                          "emag_max_rel": float((e32 - e64).abs().max() / e64.abs().max()),
+                          "reference": "FP64 path converged to 1e-12"},
+        "note": "FMG from phi = 0 to 1e-8, 5 solves each timed with CUDA events"}
+    gf.close()
+    gm.close()
+    return out
 
 
 def bench_axisymmetric(args, dev, world):
@@ -853,7 +1004,7 @@ def bench_batch(args, dev, world):
              "hbm_frac": round(by / (us * 1e-6) / 1e9 / hbm, 4)}
         if fl:
             e["fp64_ginstr"] = round(fl / (us * 1e-6) / 1e9, 1)
-            e["fp64_frac"] = round(fl / (us * 1e-6) / 1e9 / FP64_PEAK_GINSTR, 4)
+            e["fp64_frac"] = round(fl / (us * 1e-6) / 1e9 / fp64_rate(), 4)
         kern[name] = e
     res = {"value": round(256 * args.steps * world / (total * 1e-3), 2), "unit": "solves/s",
            "ms_per_batch": round(total / args.steps, 3), "solves_per_batch": 256, "cells": cells,
@@ -866,8 +1017,8 @@ def bench_batch(args, dev, world):
            "kernels": kern,
            "kernels_note": "CUDA events around 10 back-to-back launches over all 256 solves; bytes = "
                            "compulsory traffic (sweep 12 B, outer 20 B + 2 FP64-pipe instr, prolong/restrict "
-                           "8.5 B per fine cell); hbm peak %.1f GB/s measured, FP64 peak %.0f G instr/s"
-                           % (hbm, FP64_PEAK_GINSTR)}
+                           "8.5 B per fine cell); hbm peak %.1f GB/s measured, FP64 peak %.0f G instr/s "
+                           "measured (sm_fp64_probe)" % (hbm, fp64_rate())}
     b.close()
     return res
 
@@ -894,6 +1045,23 @@ def oracle_solve(o, ne, ni):
     return time.perf_counter() - t0, cyc
 
 
+def oracle_step(o, ne, ni):
+    """The GPU arm's step on the oracle: charge, FMG to 1e-8, field, time
+    step, one Heun step with its two solves to 1e-8 (3 solves)."""
+    import oracle
+    import synth
+    Q, E0 = synth.E_CHARGE, synth.EPS0
+    o.set(oracle.NE, ne)
+    o.set(oracle.NI, ni)
+    t0 = time.perf_counter()
+    o.charge_rhs(Q, E0)
+    _, _, c0 = o.fmg(TOL, MAX_CYCLES)
+    o.compute_field()
+    dt = o.dt_limit(Q, E0)
+    r = o.advance(dt, Q, E0, TOL, MAX_CYCLES)
+    return time.perf_counter() - t0, c0 + r[2] + r[3]
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -902,22 +1070,25 @@ def host_cores():
 
 
 def cpu_baseline():
-    """The oracle as it stands on one FMG solve of the same workload: on all
-    host cores (OpenMP over boxes, the paper's own CPU scheme) and on one
-    thread (about 10-20 s of CPU work each)."""
+    """The oracle as it stands on one step of the same workload (the GPU
+    arm's step: FMG, field, time step, Heun step; 3 solves) on all host
+    cores (OpenMP over boxes, the paper's own CPU scheme), and one FMG solve
+    on one thread (about 10-30 s of CPU work in all)."""
     import oracle
     o, ne, ni = oracle_case()
     cores = oracle.set_threads(host_cores())
     try:
-        sec_all, cyc = oracle_solve(o, ne, ni)
+        sec_all, cyc = oracle_step(o, ne, ni)
         oracle.set_threads(1)
-        sec_one, _ = oracle_solve(o, ne, ni)
+        sec_one, cyc1 = oracle_solve(o, ne, ni)
     finally:
         oracle.set_threads(1)
-    return {"value": round(1.0 / sec_all, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": "one FMG solve to 1e-8 of the %s workload (%d top-level V-cycles), "
-                      "plain C oracle, OpenMP over boxes on %d threads" % (WORKLOAD, cyc, cores),
-            "single_thread": {"value": round(1.0 / sec_one, 5), "unit": "solves/s", "cores": 1},
+    return {"value": round(SOLVES_PER_STEP / sec_all, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": "one step of the %s workload (FMG to 1e-8, field, time step, Heun step with two solves "
+                      "to 1e-8; %d V-cycles), plain C oracle, OpenMP over boxes on %d threads"
+                      % (WORKLOAD, cyc, cores),
+            "single_thread": {"value": round(1.0 / sec_one, 5), "unit": "solves/s", "cores": 1,
+                              "sample": "one FMG solve to 1e-8 (%d V-cycles)" % cyc1},
             "axisymmetric": cpu_baseline_axi()}
 
 
@@ -946,6 +1117,9 @@ def cpu_baseline_axi():
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, timed on the GPU arm's
+    own step (FMG + field + time step + Heun step: 3 solves to 1e-8) of the
+    same workload, on the host cores."""
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -954,13 +1128,14 @@ def run_reference(args):
     nthr = getattr(args, "ref_threads", 0)
     cores = oracle.set_threads(nthr if nthr > 0 else host_cores())
     for _ in range(args.warmup):
-        oracle_solve(o, ne, ni)
-    total = 0.0
+        oracle_step(o, ne, ni)
+    total, cycles = 0.0, 0
     for _ in range(args.steps):
-        sec, _ = oracle_solve(o, ne, ni)
+        sec, cyc = oracle_step(o, ne, ni)
         total += sec
+        cycles += cyc
     oracle.set_threads(1)
-    value = args.steps / total
+    value = SOLVES_PER_STEP * args.steps / total
     res = {
         "metric": "Poisson solves/s to rel residual 1e-8 (octree FMG + Heun step, 3 solves/step)",
         "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -968,8 +1143,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "tol": TOL, "nu": [2, 2]},
+        "vcycles_per_step": cycles / args.steps,
         "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": "each step = one FMG solve to 1e-8 of the workload, plain C oracle, "
+                         "sample": "each step = the GPU arm's step (charge, FMG to 1e-8, field, time step, "
+                                   "Heun step with two solves to 1e-8) of the workload, plain C oracle, "
                                    "OpenMP over boxes on %d threads" % cores},
         "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},

@@ -480,18 +480,35 @@ const char *sm_cnn_last_error(const sm_cnn *c);
  * The library allocates nothing: its only scratch (one eigenbasis per
  * problem) is a fixed device array of SM_NOALLOC_MAX_PROBLEMS x 1728 bytes
  * (1.77 MB) that every GPU loading the library holds until exit.  The first
- * call on a device looks up that array's device address (set-up, once per
- * device, with the device current); make that first call before any stream
- * capture.  All calls share the array and each call overwrites the slots of
- * its problems before reading them, so nothing needs clearing, but calls
- * that overlap on the GPU (different streams, or devices sharing nothing
- * else) race on it: order them.
+ * call on a device looks up that array's device address (set-up, with the
+ * device current); make that first call before any stream capture.  Every
+ * later call made outside a capture looks the address up again, so after a
+ * device reset (cudaDeviceReset) make one uncaptured call before capturing
+ * again.  Each device has its own copy of the array.  All calls on one
+ * device share it and each call overwrites the slots of its problems before
+ * reading them, so nothing needs clearing, but calls that overlap on the
+ * same device (different streams) race on it and must be ordered; calls on
+ * different devices are independent.  Device ordinals 0..63 are supported.
  * Errors: SM_ENOMEM if n_problems > SM_NOALLOC_MAX_PROBLEMS (the fixed
  * scratch is too small), SM_EINVAL (n_problems < 0, length <= 0, null
- * pointer), SM_ECUDA (no device, address lookup or launch failed). */
+ * pointer, device ordinal above 63), SM_ECUDA (no device, first call of a
+ * device inside a stream capture, address lookup or launch failed). */
 #define SM_NOALLOC_MAX_PROBLEMS 1024
 int sm_box_solve_noalloc(double length, int n_problems, const int32_t *bc_type, const double *bc_val,
                          const double *f, double *phi, void *stream);
+
+/* Throughput of the GPU's FP64 pipe, measured: one launch of 8 resident
+ * blocks of 256 threads per SM, each thread running 8 independent chains
+ * of `iters` fused multiply-adds x = x*a + b (after a shorter warm-up
+ * launch), timed with CUDA events on `stream`.  *fma_per_s receives the
+ * fused multiply-adds per second (one FP64-pipe instruction each; 2 flops),
+ * *ms_out (optional) the timed launch's duration.  d_scratch: one device
+ * word the kernel may write (a sink that keeps the arithmetic from being
+ * optimised away); the caller owns it.  No counterpart in the paper: it
+ * measures the roof of the FP64-bound fluid kernels (Sec. 2.3 fluxes,
+ * Sec. 2.4 time step).  Synchronises the stream.  Errors: SM_EINVAL
+ * (iters < 1, null pointers), SM_ECUDA (no device, launch failed). */
+int sm_fp64_probe(long long iters, unsigned long long *d_scratch, double *fma_per_s, double *ms_out, void *stream);
 
 /* Check of the library's own FP64 <-> FP32 conversions (not in the paper).
  * The FP64 kernels convert on the 32-bit integer pipe instead of with the

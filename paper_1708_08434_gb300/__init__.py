@@ -61,7 +61,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_mg_vcycle", "sm_mg_solve", "sm_mg_fmg", "sm_compute_field", "sm_dt_limit",
            "sm_fluid_stage", "sm_advance_fluid", "sm_kernel_bench", "sm_set_graphs", "sm_set_pdl",
            "sm_set_persistent", "sm_persist_barrier_selftest",
-           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc", "sm_check_conversions",
+           "sm_launch_count", "sm_last_error", "sm_box_solve_noalloc", "sm_check_conversions", "sm_fp64_probe",
            "sm_refine_flags", "sm_regrid",
            "sm_batch_create", "sm_batch_destroy", "sm_batch_arena_size", "sm_batch_bind_arena",
            "sm_batch_ptrs", "sm_batch_solve", "sm_batch_tune", "sm_batch_set_schedule", "sm_batch_info",
@@ -122,6 +122,7 @@ def load():
         "sm_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_box_solve_noalloc": [D, I, P, P, P, P, P],
         "sm_check_conversions": [C.c_longlong, C.c_ulonglong, P, P, P],
+        "sm_fp64_probe": [C.c_longlong, P, pD, pD, P],
         "sm_refine_flags": [P, D, D, D, D, I, P],
         "sm_regrid": [P, P, pI, pI, pI],
         "sm_batch_create": [C.POINTER(P), I, P, D, P, P, I, I, P],
@@ -202,6 +203,21 @@ def check_conversions(n: int, seed: int = 0x5EED):
     if rc != SM_OK:
         raise SmError(rc, "sm_check_conversions failed")
     return tuple(int(v) for v in out)
+
+
+def fp64_probe(iters: int = 1 << 16):
+    """Measured FP64-pipe throughput of this GPU: (fused multiply-adds per
+    second, duration of the timed launch in ms)."""
+    import torch
+    lib = load()
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rate, ms = C.c_double(0.0), C.c_double(0.0)
+    stream = torch.cuda.current_stream()
+    rc = lib.sm_fp64_probe(int(iters), C.c_void_p(sink.data_ptr()), C.byref(rate), C.byref(ms),
+                           C.c_void_p(stream.cuda_stream))
+    if rc != SM_OK:
+        raise SmError(rc, "sm_fp64_probe failed")
+    return rate.value, ms.value
 
 
 class Solver:

@@ -619,6 +619,55 @@ __global__ void k_check_cvt(long long n, unsigned long long seed, unsigned long 
 
 }  // namespace
 
+// FP64 pipe throughput probe: FP64_CHAINS independent fused multiply-add
+// chains per thread, iters steps each; the sum leaves through *sink only
+// when it equals an impossible value, so nothing is optimised away.
+constexpr int FP64_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_fp64_probe(long long iters, unsigned long long *sink) {
+  double x[FP64_CHAINS];
+  const double a = 1.0 + 1e-9 * threadIdx.x, b = 1e-7 * blockIdx.x;
+#pragma unroll
+  for (int c = 0; c < FP64_CHAINS; ++c) x[c] = 0.5 + 0.01 * c;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < FP64_CHAINS; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < FP64_CHAINS; ++c) s += x[c];
+  if (s == -1.0) sink[0] = (unsigned long long)__double_as_longlong(s);
+}
+
+extern "C" int sm_fp64_probe(long long iters, unsigned long long *d_scratch, double *fma_per_s, double *ms_out,
+                             void *stream) {
+  if (iters < 1 || !d_scratch || !fma_per_s) return SM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SM_ECUDA;
+  const int grid = 8 * sms, block = 256;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return SM_ECUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return SM_ECUDA;
+  }
+  k_fp64_probe<<<grid, block, 0, st>>>(iters / 8 + 1, d_scratch);  // warm-up
+  cudaEventRecord(a, st);
+  k_fp64_probe<<<grid, block, 0, st>>>(iters, d_scratch);
+  cudaEventRecord(b, st);
+  float ms = 0.f;
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms > 0.f;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!ok) return SM_ECUDA;
+  *fma_per_s = (double)grid * block * FP64_CHAINS * (double)iters / (ms * 1e-3);
+  if (ms_out) *ms_out = ms;
+  return SM_OK;
+}
+
 extern "C" int sm_check_conversions(long long n, unsigned long long seed, unsigned long long *d_scratch,
                                     unsigned long long *mismatches, void *stream) {
   if (n < 0 || !d_scratch || !mismatches) return SM_EINVAL;

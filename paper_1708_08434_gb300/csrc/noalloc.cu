@@ -24,19 +24,32 @@ using namespace sm;
 // until the process exits: SM_NOALLOC_MAX_PROBLEMS x 1728 bytes = 1.77 MB.
 static __device__ __align__(256) double g_box_scratch[SM_NOALLOC_MAX_PROBLEMS * SMX_BASIS_DOUBLES];
 
-// device address of g_box_scratch, looked up once per device
+// device address of g_box_scratch per device ordinal (at most
+// SMX_MAX_DEVICES devices).  It is looked up on a device's first call and
+// again on every call made outside a stream capture, so a context reset
+// (cudaDeviceReset), after which the module is reloaded and the array may
+// sit elsewhere, is picked up by the next uncaptured call; a captured call
+// uses the address of the last uncaptured one.
+#define SMX_MAX_DEVICES 64
 static std::mutex g_scratch_mtx;
-static double *g_scratch_ptr[64];
-static bool g_scratch_ready[64];
+static double *g_scratch_ptr[SMX_MAX_DEVICES];
+static bool g_scratch_ready[SMX_MAX_DEVICES];
 
-static int scratch_address(double **out) {
+static int scratch_address(cudaStream_t stream, double **out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SM_ECUDA;
+  }
+  if (dev < 0 || dev >= SMX_MAX_DEVICES) return SM_EINVAL;  // beyond the per-device address table
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
     cudaGetLastError();
     return SM_ECUDA;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mtx);
-  if (!g_scratch_ready[dev]) {
+  if (!g_scratch_ready[dev] || cs == cudaStreamCaptureStatusNone) {
+    if (cs != cudaStreamCaptureStatusNone) return SM_ECUDA;  // first call of the device inside a capture
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_box_scratch);
     if (e != cudaSuccess) {
@@ -128,7 +141,7 @@ extern "C" int sm_box_solve_noalloc(double length, int n_problems, const int32_t
   if (n_problems < 0 || !(length > 0.0)) return SM_EINVAL;
   if (n_problems > 0 && (!bc_type || !bc_val || !f || !phi)) return SM_EINVAL;
   double *scratch = nullptr;
-  int st = scratch_address(&scratch);
+  int st = scratch_address((cudaStream_t)stream, &scratch);
   if (st) return st;
   if (n_problems == 0) return SM_OK;
   double h = length / NC;

@@ -110,7 +110,8 @@ class Streamer:
     n_head: float = 1e20
     edge: float = 50e-6
     shell: float = 20e-6
-    background: float = 0.0
+    background: float = 0.0     # mean background density of electrons and ions (m^-3)
+    noise_cell: float = 0.0     # > 0: background 2U x mean, U drawn per cell of this spacing (m)
     voltage: float = 25e3
     refine_c: float = 10.0      # refine where |dist to surface| < box half-diagonal + C*h
     refine_tip: float = 4.2e-3  # ... and box within refine_tip/2^k of the tip (k = level above base)
@@ -146,7 +147,10 @@ def workload(name: str):
     streamer8     : 16 mm cube, base 64^3, 8 refinement levels, ~1.7e7 cells
     streamer9     : 16 mm cube, base 128^3, 9 refinement levels, ~1.0e8 cells
                     (finest spacing 0.24 um; 226569 boxes)
+    streamer9_bg  : streamer9 with a stochastic background of mean 1e13 m^-3
+                    drawn on the 500 um grid (the learned-form workload)
     streamer_small: 16 mm cube, base 16^3, 3 refinement levels (test size)
+    streamer_small_bg: streamer_small with the background of streamer9_bg
     streamer_tiny : 16 mm cube, base 16^3, 1 refinement level (dense-solve size)
     """
     if name == "uniform64":
@@ -162,8 +166,14 @@ def workload(name: str):
     if name == "streamer9":
         st = Streamer(refine_c=25.0, refine_tip=12.5e-3)
         return domain_streamer(16, 9, st), st
+    if name == "streamer9_bg":
+        st = Streamer(refine_c=25.0, refine_tip=12.5e-3, background=1e13, noise_cell=500e-6)
+        return domain_streamer(16, 9, st), st
     if name == "streamer_small":
         st = Streamer(refine_c=2.0, refine_tip=6e-3)
+        return domain_streamer(2, 3, st), st
+    if name == "streamer_small_bg":
+        st = Streamer(refine_c=2.0, refine_tip=6e-3, background=1e13, noise_cell=500e-6)
         return domain_streamer(2, 3, st), st
     if name == "streamer_tiny":
         st = Streamer(refine_c=0.0, refine_tip=1e-3)
@@ -224,13 +234,47 @@ def smoothstep_edge(s, width):
     return 1.0 - 3.0 * x ** 2 + 2.0 * x ** 3
 
 
-def streamer_densities(dom: Domain, st: Streamer, levels, ijk, noise=None, seed=SEED):
-    """Electron and ion densities of the synthetic streamer at cell centres."""
+def background_density(dom: Domain, st: Streamer, x, y, z, seed=SEED):
+    """Background density of electrons and ions at points (x, y, z).
+
+    With st.noise_cell = 0 it is the constant st.background.  Otherwise a
+    stochastic background in the manner of the paper's Sec. 3.2 (its case 3,
+    2U times the mean): one U in [0, 1) per cell of a uniform grid of spacing
+    st.noise_cell over the domain, drawn from SplitMix64(seed) with counter
+    i + n j + n^2 k, and linearly interpolated between those cells' centres
+    (trilinear; outside the outermost centres the nearest value along each
+    axis), so the noise is correlated over one coarse cell.
+    """
+    if st.noise_cell <= 0.0:
+        return np.full(np.shape(x), st.background)
+    n = int(round(dom.length / st.noise_cell))
+    idx = np.arange(n, dtype=np.uint64)
+    ctr = idx[None, None, :] + np.uint64(n) * idx[None, :, None] + np.uint64(n * n) * idx[:, None, None]
+    u = uniform01(seed, ctr)  # [k][j][i]
+    coords = []
+    for c, o in ((x, dom.origin[0]), (y, dom.origin[1]), (z, dom.origin[2])):
+        t = np.clip((np.asarray(c) - o) / st.noise_cell - 0.5, 0.0, n - 1.0)
+        i0 = np.minimum(np.floor(t).astype(np.int64), n - 2)
+        coords.append((i0, t - i0))
+    (i0, fx), (j0, fy), (k0, fz) = coords
+    val = np.zeros(np.shape(x))
+    for dk, wk in ((0, 1.0 - fz), (1, fz)):
+        for dj, wj in ((0, 1.0 - fy), (1, fy)):
+            for di, wi in ((0, 1.0 - fx), (1, fx)):
+                val = val + wk * wj * wi * u[k0 + dk, j0 + dj, i0 + di]
+    return 2.0 * st.background * val
+
+
+def streamer_densities(dom: Domain, st: Streamer, levels, ijk, seed=SEED):
+    """Electron and ion densities of the synthetic streamer at cell centres:
+    channel and head with the space-charge shell, plus the background (the
+    same for both species)."""
     x, y, z = cell_centres(dom, levels, ijk)
     s = st.signed_distance(x, y, z)
     core = st.n_channel * smoothstep_edge(s, st.edge)
-    ne = core + st.background
-    ni = core + st.background
+    bg = background_density(dom, st, x, y, z, seed)
+    ne = core + bg
+    ni = core + bg
     head = (z < st.z_head) & (s < 0.0) & (s >= -st.shell)
     ni = ni + np.where(head, st.n_head, 0.0)
     return ne, ni

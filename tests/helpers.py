@@ -48,3 +48,25 @@ def load_inputs(dom, st, o, g, tables=None):
     o.set_table(tab); g.set_table(tab)
     o.charge_rhs(Q, EPS0); g.charge_rhs(Q, EPS0)
     return (Q, EPS0, False)
+
+
+def box_scale(t, ref):
+    """Per box: max |ref| over the box, its 26 same-level neighbours and, at
+    refinement faces, its parent's neighbours -- the magnitudes that the
+    finite-volume update of the box combines, so the scale of its rounding
+    errors (ref: [nbox, 512])."""
+    m = np.abs(ref).max(axis=1)
+    nbr = t["nbr"]
+    s = np.maximum(m, np.where(nbr >= 0, m[np.clip(nbr, 0, None)], 0.0).max(axis=1))
+    par = t["parent"]
+    coarse = (nbr == -2).any(axis=1) & (par >= 0)
+    pn = nbr[np.clip(par, 0, None)]
+    ps = np.maximum(m[np.clip(par, 0, None)], np.where(pn >= 0, m[np.clip(pn, 0, None)], 0.0).max(axis=1))
+    return np.where(coarse, np.maximum(s, ps), s)
+
+
+def rel_err_local(a, b, t):
+    """max over cells of |a - b| / max(|b|, box_scale of the cell's box)."""
+    den = np.maximum(np.abs(b), box_scale(t, b)[:, None])
+    den = np.where(den > 0, den, 1.0)
+    return (np.abs(a - b) / den).max()

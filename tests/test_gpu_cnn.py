@@ -80,6 +80,32 @@ def test_forward_layerwise_against_fp64():
         assert (a1 > 0).mean() > 0.2 and (a2 > 0).mean() > 0.2   # ReLUs are exercised
 
 
+def test_forward_end_to_end_against_oracle():
+    """The oracle's own forward pass (FP64 arithmetic, hidden activations
+    rounded to BF16 after each ReLU) against the GPU output on the same BF16
+    inputs and weights.  The two agree to FP32 accumulation error except
+    where that error moves a hidden pre-activation across a BF16 rounding
+    boundary: the activation then differs by one BF16 step, 2^-8 of its
+    value.  Bound: max |gpu - oracle| <= 2^-8 max |oracle| over each box,
+    and no more than 1% of the outputs off by more than 1e-5 relative."""
+    p = params(11)
+    net = pkg().Network(64, 64)
+    net.set_params(p)
+    n = 8
+    x = inputs(n, 12)
+    out = net.forward(x)
+    pe = effective(p)
+    worst, off = 0.0, 0
+    for b in range(n):
+        ref = cnn.forward(pe, oracle_x(x[b]), round_acts=True)[-1]
+        got = out[b].reshape(8, 8, 8).astype(np.float64)
+        worst = max(worst, rel(got, ref))
+        off += int((np.abs(got - ref) > 1e-5 * np.abs(ref).max()).sum())
+    print("end-to-end forward: max rel %.3e, outputs beyond 1e-5: %d of %d" % (worst, off, n * 512))
+    assert worst <= 2.0 ** -8
+    assert off <= 0.01 * n * 512
+
+
 def test_gradient_against_fp64_backprop():
     p = params(3)
     net = pkg().Network(64, 64)

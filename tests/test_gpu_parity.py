@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import EPS0, Q, gpu_mesh, load_inputs, pair, rel_err
+from helpers import EPS0, Q, gpu_mesh, load_inputs, pair, rel_err, rel_err_local
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -166,6 +166,39 @@ def check_advance(name, tol_solve=1e-8):
 
 def test_heun_step_parity_small():
     check_advance("streamer_small")
+
+
+def test_heun_step_parity_with_stochastic_background():
+    """The streamer with the seeded stochastic background of the learned-form
+    workload (mean 1e13 m^-3 against 1e19-1e20 in the channel and head):
+    densities after FMG, field and one Heun step are compared cell by cell
+    against max(|oracle|, the largest |oracle| in the cell's box and its
+    neighbours), so background cells are held to their own scale, not to
+    the head's.  The error of an FP64 finite-volume update is a few units of
+    rounding of the largest density it combines; the same bound holds in
+    the streamer boxes, where the local scale is the head's."""
+    dom, st, o, g = pair("streamer_small_bg")
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    so = o.fmg(1e-8, 40)
+    sg = g.fmg(1e-8, 40)
+    assert so[2] == sg[2]
+    o.compute_field()
+    g.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+    ro = o.advance(dt, Q, EPS0, 1e-8, 40)
+    rg = g.advance(dt, Q, EPS0, 1e-8, 40)
+    assert ro[2:] == rg[2:]
+    leaf = t["child"][:, 0] < 0
+    p = pkg()
+    for vo, vg in ((oracle.NE, p.NE), (oracle.NI, p.NI)):
+        ref, got = o.get(vo), g.download(vg)
+        assert ref[leaf].min() > 0.0
+        e = rel_err_local(got, ref, t)
+        print("density", vo, "local-scale rel err %.3e" % e)
+        assert e <= TOL, (vo, e)
+    for vo, vg in ((oracle.PHI, p.PHI), (oracle.EMAG, p.EMAG)):
+        assert rel_err(g.download(vg)[leaf], o.get(vo)[leaf]) <= TOL
 
 
 @pytest.mark.slow
