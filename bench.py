@@ -46,9 +46,12 @@ PERSIST = False
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
 #       --clock-control none -k regex:k_fcolor --csv --log-file fcolor_dram.csv \
 #       python bench.py --mode kernels
-# None until counters of the current kernel are recorded.
-FCOLOR_TRAFFIC_PER_LAUNCH = None
-FCOLOR_TRAFFIC_NOTE = "no ncu counters of the current k_fcolor recorded yet"
+# Mean of the first 36 launches (the kernel-bench mix): 3.118 MB read, 0
+# written (profiles/k_fcolor_streamer6_dram.md).
+FCOLOR_TRAFFIC_PER_LAUNCH = 3118044
+FCOLOR_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 36 k_fcolor launches of "
+                       "one kernel-bench sweep of every level (cold caches): 0.85x the algorithmic bytes per "
+                       "launch, the colour's stores staying in L2")
 
 
 def parse():
@@ -74,6 +77,8 @@ def parse():
                     help="run V-cycles as one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the solver kernels without programmatic dependent launch")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="mesh of --mode kernels and --mode vcycle (the step and its metric use streamer6)")
     ap.add_argument("--mode", default="step", choices=["step", "vcycle", "kernels", "batch", "large", "axi"],
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
@@ -203,7 +208,7 @@ def build_gpu_case(precision=0):
     import synth
     import paper_1708_08434_gb300 as pkg
     dom, st = synth.workload(WORKLOAD)
-    g = pkg.Solver(dom, max_boxes=8192, precision=precision)
+    g = pkg.Solver(dom, max_boxes=8192 if WORKLOAD == "streamer6" else 1 << 18, precision=precision)
     if NO_GRAPHS:
         g.set_graphs(False)
     if NO_PDL:
@@ -1155,8 +1160,10 @@ def run_reference(args):
 
 
 def main():
-    global NO_GRAPHS, NO_PDL, PERSIST
+    global NO_GRAPHS, NO_PDL, PERSIST, WORKLOAD
     args = parse()
+    if args.mode in ("kernels", "vcycle"):
+        WORKLOAD = args.workload
     NO_GRAPHS = args.no_graphs
     NO_PDL = args.no_pdl
     PERSIST = args.persistent
