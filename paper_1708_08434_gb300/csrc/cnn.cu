@@ -11,7 +11,8 @@
 //   input  X: 2 channels on the 10^3 box-with-ghosts region, the FP64
 //          residual h^2 (f - L phi_prev) divided by the box scale s and the
 //          normalised right-hand side h^2 f
-//   conv 3^3 valid 2->16, ReLU;  conv 3^3 same 16->16, ReLU (tensor cores);
+//   conv 3^3 valid 2->16, ReLU;  conv 3^3 same 16->16, ReLU (5th-generation
+//          tensor cores: tcgen05.mma with the accumulator in tensor memory);
 //   conv 3^3 same 16->1 -> delta on 8^3;  prediction phi += s * delta.
 // Training: mean squared error against (phi_solved - phi_prev)/s (clipped),
 // Adam on
@@ -48,38 +49,160 @@ __device__ __forceinline__ int Off(int t) { return (t % 3 - 1) + 10 * ((t / 3) %
 __device__ __forceinline__ float bf(bf16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float rbf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// D += A B for one m16n8k16 tile, BF16 operands, FP32 accumulation
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // weights as one CTA uses them
 struct NetS {
   float w1[NW1];      // [co][ci][t], BF16 values
   float b1[16];
-  bf16 w2[27 * 256];  // [t][co][ci] (mma B operand)
+  bf16 w2[27 * 256];  // per tap four 8x8 core matrices [t][ci/8][co/8][co%8][ci%8] (B operand)
   float b2[16];
   float w3[NW3];      // [ci][t], BF16 values
   float b3;
 };
 
+// layer-1 activations as the A operand of the tensor-core layer 2: two
+// arrays of 8 channels, [pos][8] BF16 = 16 bytes per position, over the
+// 10^3 region plus padding that the unused rows of the last M tile read
+constexpr int NPOSA = 1024;
+
 struct FwdS {
-  bf16 x[NPOS * 2];    // [pos][ci]
-  bf16 a1[NPOS * 16];  // [pos][c], zero outside the box interior
-  bf16 a2[NPOS * 16];
+  bf16 a1lo[NPOSA * 8];  // channels 0-7, zero outside the box interior
+  bf16 a1hi[NPOSA * 8];  // channels 8-15
+  bf16 x[NPOS * 2];      // [pos][ci]
+  bf16 a2[NPOS * 16];    // [pos][c], zero outside the box interior
   float out[512];
 };
+static_assert(offsetof(FwdS, a1hi) - offsetof(FwdS, a1lo) == NPOSA * 16, "A operand halves");
+
+__device__ __forceinline__ float A1(const FwdS &F, int pos, int c) {
+  return bf(c < 8 ? F.a1lo[pos * 8 + c] : F.a1hi[pos * 8 + c - 8]);
+}
+
+// ---- tcgen05: 5th-generation tensor cores, accumulator in tensor memory ----
+//
+// Layer 2 is an implicit GEMM D[v][co] = sum over taps t and channels ci of
+// a1[pos(v) + off(t)][ci] W2[co][ci][t].  A 128-row M tile is 16
+// consecutive rows R (R = (y+1) + 10(z+1)) of 8 voxels along x of the
+// padded 10^3 region; rows with y = -1 or 8 (two per z plane) fall inside
+// the tile too and are discarded: 5 tiles (R = 11 + 16j, j = 0..4) cover
+// the 64 rows of the box.  For tap t the tile's A operand is the same view
+// shifted by off(t) positions: K-major, no swizzle, core matrices of 8
+// positions x 8 channels (128 contiguous bytes), rows 160 bytes apart (SBO,
+// one padded row), the second 8 channels in a1hi (LBO).  B (W2 of one tap,
+// 16 x 16) is stored as four 8x8 core matrices: LBO 256 bytes (channels
+// 8-15), SBO 128 bytes (output channels 8-15).  Each tile accumulates its
+// 27 taps (K = 16 each) in 16 columns of tensor memory.
+constexpr int TC_TILES = 5, TC_COLS = 128;
+constexpr uint32_t TC_IDESC = (1u << 4)             // D: FP32
+                              | (1u << 7)           // A: BF16
+                              | (1u << 10)          // B: BF16
+                              | ((16u >> 3) << 17)  // N = 16
+                              | ((128u >> 4) << 24);  // M = 128; A and B K-major
+constexpr long long TC_SPIN = 1ll << 22;  // mbarrier polls before giving up (far beyond a box's work)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor without swizzle (descriptor version 1)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase of an mbarrier; false when the polls ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long long i = 0; i < TC_SPIN; ++i)
+    if (mbar_try(mbar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tensor-memory and mbarrier state of a CTA that runs layer 2 on tcgen05:
+// warp 0 allocates TC_COLS columns at the start and frees them at the end.
+struct TcState {
+  uint32_t taddr;   // tensor-memory address of the allocation (lane 0, first column)
+  uint32_t mbar;    // shared address of the MMA-completion mbarrier
+  uint32_t phase;   // parity of the next completion
+  unsigned *err;    // device error word: bit 0 = an MMA wait ran out
+};
+
+__device__ void tc_begin(TcState &tc, uint64_t *mbar, uint32_t *slot, unsigned *err) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tc.taddr = *slot;
+  tc.mbar = smem_u32(mbar);
+  tc.phase = 0;
+  tc.err = err;
+}
+
+__device__ void tc_end(const TcState &tc) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.taddr), "r"(TC_COLS) : "memory");
+}
+
+// position of W2[co][ci][t] in NetS::w2
+__device__ __forceinline__ int W2i(int t, int co, int ci) {
+  return t * 256 + (ci >> 3) * 128 + (co >> 3) * 64 + (co & 7) * 8 + (ci & 7);
+}
 
 __device__ void load_net(NetS &N, const float *__restrict__ w) {
   for (int i = threadIdx.x; i < NW1; i += blockDim.x) N.w1[i] = rbf(w[O_W1 + i]);
   for (int i = threadIdx.x; i < NW3; i += blockDim.x) N.w3[i] = rbf(w[O_W3 + i]);
   for (int i = threadIdx.x; i < 27 * 256; i += blockDim.x) {
     int t = i / 256, co = (i / 16) % 16, ci = i % 16;
-    N.w2[i] = __float2bfloat16_rn(w[O_W2 + (co * 16 + ci) * 27 + t]);
+    N.w2[W2i(t, co, ci)] = __float2bfloat16_rn(w[O_W2 + (co * 16 + ci) * 27 + t]);
   }
   if (threadIdx.x < 16) {
     N.b1[threadIdx.x] = w[O_B1 + threadIdx.x];
@@ -89,13 +212,18 @@ __device__ void load_net(NetS &N, const float *__restrict__ w) {
 }
 
 __device__ void zero_acts(FwdS &F) {
-  uint32_t *p = reinterpret_cast<uint32_t *>(F.a1);
-  for (int i = threadIdx.x; i < NPOS * 16; i += blockDim.x) p[i] = 0u;  // a1 and a2
+  uint32_t *p = reinterpret_cast<uint32_t *>(F.a1lo);
+  for (int i = threadIdx.x; i < NPOSA * 8; i += blockDim.x) p[i] = 0u;  // a1lo and a1hi
+  uint32_t *q = reinterpret_cast<uint32_t *>(F.a2);
+  for (int i = threadIdx.x; i < NPOS * 8; i += blockDim.x) q[i] = 0u;
 }
 
 // Forward pass of one box whose input is already in F.x.  Debug pointers
-// (per box [16][512] / [512], may be null) receive z1, a1, z2, a2.
-__device__ void forward_box(const NetS &N, FwdS &F, float *z1d, float *a1d, float *z2d, float *a2d) {
+// (per box [16][512] / [512], may be null) receive z1, a1, z2, a2.  False
+// (and bit 0 of *tc.err set) when the tensor cores' completion wait ran out;
+// the caller then stops.
+__device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, float *a1d, float *z2d,
+                            float *a2d) {
   const int t = threadIdx.x;
   // layer 1: valid 3^3 conv 2 -> 16 on CUDA cores
   for (int r = 0; r < 2; ++r) {
@@ -112,64 +240,63 @@ __device__ void forward_box(const NetS &N, FwdS &F, float *z1d, float *a1d, floa
 #pragma unroll
     for (int co = 0; co < 16; ++co) {
       bf16 a = __float2bfloat16_rn(fmaxf(acc[co], 0.0f));
-      F.a1[p * 16 + co] = a;
+      (co < 8 ? F.a1lo : F.a1hi)[p * 8 + (co & 7)] = a;
       if (z1d) {
         z1d[co * 512 + v] = acc[co];
         a1d[co * 512 + v] = bf(a);
       }
     }
   }
+  // the tensor cores read a1 through the async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
-  // layer 2: same 3^3 conv 16 -> 16 as an implicit GEMM on tensor cores,
-  // M = 512 voxels, N = 16 channels, K = 27 taps x 16 channels
-  {
-    int warp = t >> 5, lane = t & 31, g = lane >> 2, c = lane & 3;
-    float acc[4][2][4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[m][j][e] = 0.0f;
-    for (int tp = 0; tp < 27; ++tp) {
-      int off = Off(tp);
-      uint32_t bfr[2][2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const bf16 *wr = N.w2 + (tp * 16 + 8 * j + g) * 16;
-        bfr[j][0] = *reinterpret_cast<const uint32_t *>(wr + 2 * c);
-        bfr[j][1] = *reinterpret_cast<const uint32_t *>(wr + 2 * c + 8);
+  // layer 2: same 3^3 conv 16 -> 16 as an implicit GEMM on tcgen05 (the
+  // tiling is described with TcState); one thread issues the 135 MMAs
+  if (t == 0) {
+    tc_fence_after();
+    const uint32_t a0 = smem_u32(F.a1lo), b0 = smem_u32(N.w2);
+    for (int j = 0; j < TC_TILES; ++j)
+      for (int tp = 0; tp < 27; ++tp) {
+        const int pos = 1 + 10 * (11 + 16 * j) + Off(tp);
+        tc_mma(tc.taddr + 16 * j, tc_desc(a0 + 16 * pos, NPOSA * 16, 160), tc_desc(b0 + 512 * tp, 256, 128),
+               tp > 0);
       }
+    tc_commit(tc.mbar);
+  }
+  const bool ok = mbar_wait(tc.mbar, tc.phase);
+  if (!__syncthreads_and(ok)) {
+    if (t == 0) atomicOr(tc.err, 1u);
+    mbar_wait(tc.mbar, tc.phase);  // let the MMAs in flight finish before the caller stops
+    return false;
+  }
+  tc.phase ^= 1;
+  tc_fence_after();
+  {
+    // warps 0-3 read tiles 0-2, warps 4-7 tiles 3-4, each its 32 lanes
+    const int warp = t >> 5, lane = t & 31, q = warp & 3;
+    const int r = 32 * q + lane;  // row of the tile
+    for (int j = warp < 4 ? 0 : 3; j < (warp < 4 ? 3 : TC_TILES); ++j) {
+      float acc[16];
+      tc_ld16(tc.taddr + ((uint32_t)(32 * q) << 16) + 16 * j, acc);
+      const int R = 11 + 16 * j + (r >> 3), x = r & 7, y = R % 10 - 1, z = R / 10 - 1;
+      if (y < 0 || y > 7 || z < 0 || z > 7) continue;  // a padding row of the tile
+      const int v = x + 8 * y + 64 * z;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int v0 = (warp * 4 + m) * 16 + g;
-        const bf16 *r0 = F.a1 + (Pos(v0) + off) * 16, *r1 = F.a1 + (Pos(v0 + 8) + off) * 16;
-        uint32_t afr[4] = {*reinterpret_cast<const uint32_t *>(r0 + 2 * c),
-                           *reinterpret_cast<const uint32_t *>(r1 + 2 * c),
-                           *reinterpret_cast<const uint32_t *>(r0 + 2 * c + 8),
-                           *reinterpret_cast<const uint32_t *>(r1 + 2 * c + 8)};
-        mma16816(acc[m][0], afr, bfr[0]);
-        mma16816(acc[m][1], afr, bfr[1]);
+      for (int co = 0; co < 16; co += 2) {
+        float z0 = acc[co] + N.b2[co], z1 = acc[co + 1] + N.b2[co + 1];
+        __nv_bfloat162 a2 = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+        *reinterpret_cast<__nv_bfloat162 *>(F.a2 + Pos(v) * 16 + co) = a2;
+        if (z2d) {
+          z2d[co * 512 + v] = z0;
+          z2d[(co + 1) * 512 + v] = z1;
+          a2d[co * 512 + v] = __low2float(a2);
+          a2d[(co + 1) * 512 + v] = __high2float(a2);
+        }
       }
     }
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int v = (warp * 4 + m) * 16 + g + 8 * h, co = 8 * j + 2 * c;
-          float z0 = acc[m][j][2 * h] + N.b2[co], z1 = acc[m][j][2 * h + 1] + N.b2[co + 1];
-          __nv_bfloat162 a2 = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
-          *reinterpret_cast<__nv_bfloat162 *>(F.a2 + Pos(v) * 16 + co) = a2;
-          if (z2d) {
-            z2d[co * 512 + v] = z0;
-            z2d[(co + 1) * 512 + v] = z1;
-            a2d[co * 512 + v] = __low2float(a2);
-            a2d[(co + 1) * 512 + v] = __high2float(a2);
-          }
-        }
   }
+  tc_fence_before();
   __syncthreads();
   // layer 3: same 3^3 conv 16 -> 1 on CUDA cores
   for (int r = 0; r < 2; ++r) {
@@ -183,6 +310,7 @@ __device__ void forward_box(const NetS &N, FwdS &F, float *z1d, float *a1d, floa
     F.out[v] = acc;
   }
   __syncthreads();
+  return true;
 }
 
 __device__ void load_input(FwdS &F, const bf16 *__restrict__ X) {
@@ -194,20 +322,27 @@ __device__ void load_input(FwdS &F, const bf16 *__restrict__ X) {
 
 // inference / debug forward over boxes [0, n) of X; out [n][512]
 __global__ void __launch_bounds__(CT) k_cnn_forward(const bf16 *__restrict__ X, int n, const float *__restrict__ w,
-                                                    float *__restrict__ out, float *__restrict__ dbg) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+                                                    float *__restrict__ out, float *__restrict__ dbg,
+                                                    unsigned *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tslot;
   NetS &N = *reinterpret_cast<NetS *>(smraw);
-  FwdS &F = *reinterpret_cast<FwdS *>(smraw + ((sizeof(NetS) + 15) & ~(size_t)15));
+  FwdS &F = *reinterpret_cast<FwdS *>(smraw + ((sizeof(NetS) + 127) & ~(size_t)127));
+  TcState tc;
+  tc_begin(tc, &mbar, &tslot, err);
   load_net(N, w);
   zero_acts(F);
   __syncthreads();
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     load_input(F, X + (size_t)b * NPOS * 2);
     float *d = (dbg && b < MAX_DEBUG) ? dbg + (size_t)b * 4 * 16 * 512 : nullptr;
-    forward_box(N, F, d, d ? d + 8192 : nullptr, d ? d + 16384 : nullptr, d ? d + 24576 : nullptr);
+    if (!forward_box(N, F, tc, d, d ? d + 8192 : nullptr, d ? d + 16384 : nullptr, d ? d + 24576 : nullptr))
+      break;
     for (int v = threadIdx.x; v < 512; v += blockDim.x) out[(size_t)b * 512 + v] = F.out[v];
     __syncthreads();
   }
+  tc_end(tc);
 }
 
 // ---- training: forward + backward per box, per-CTA partial gradients ----
@@ -222,13 +357,17 @@ struct BwdS {
 __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, const float *__restrict__ target,
                                                   const int *__restrict__ ids, int n, float inv_count,
                                                   const float *__restrict__ w, float *__restrict__ partial,
-                                                  float *__restrict__ loss_partial) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  size_t o1 = (sizeof(NetS) + 15) & ~(size_t)15, o2 = o1 + ((sizeof(FwdS) + 15) & ~(size_t)15);
+                                                  float *__restrict__ loss_partial, unsigned *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tslot;
+  size_t o1 = (sizeof(NetS) + 127) & ~(size_t)127, o2 = o1 + ((sizeof(FwdS) + 127) & ~(size_t)127);
   NetS &N = *reinterpret_cast<NetS *>(smraw);
   FwdS &F = *reinterpret_cast<FwdS *>(smraw + o1);
   BwdS &B = *reinterpret_cast<BwdS *>(smraw + o2);
   const int t = threadIdx.x;
+  TcState tc;
+  tc_begin(tc, &mbar, &tslot, err);
   load_net(N, w);
   zero_acts(F);
   for (int i = t; i < NP; i += CT) B.grad[i] = 0.0f;
@@ -237,7 +376,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     int s = ids[it];
     load_input(F, X + (size_t)s * NPOS * 2);
-    forward_box(N, F, nullptr, nullptr, nullptr, nullptr);
+    if (!forward_box(N, F, tc, nullptr, nullptr, nullptr, nullptr)) break;
     const float *tg = target + (size_t)s * 512;
     for (int v = t; v < 512; v += CT) {
       float e = F.out[v] - tg[v];
@@ -278,7 +417,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
       for (int tp = 0; tp < 27; ++tp) {
         int off = Off(tp);
         float acc = 0.0f;
-        for (int v = 0; v < 512; ++v) acc += bf(F.a1[(Pos(v) + off) * 16 + ci]) * B.d2[v * 16 + co];
+        for (int v = 0; v < 512; ++v) acc += A1(F, Pos(v) + off, ci) * B.d2[v * 16 + co];
         B.grad[O_W2 + (co * 16 + ci) * 27 + tp] += acc;
       }
       if (t < 16) {
@@ -291,15 +430,14 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     for (int e = t; e < 512 * 16; e += CT) {
       int u = e >> 4, ci = e & 15;
       float acc = 0.0f;
-      if (bf(F.a1[Pos(u) * 16 + ci]) > 0.0f) {
+      if (A1(F, Pos(u), ci) > 0.0f) {
         int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
         for (int tp = 0; tp < 27; ++tp) {
           int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
           if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
           const float *dv = B.d2 + (vx + 8 * vy + 64 * vz) * 16;
-          const bf16 *wr = N.w2 + tp * 256 + ci;  // [t][co][ci]
 #pragma unroll
-          for (int co = 0; co < 16; ++co) acc += bf(wr[co * 16]) * dv[co];
+          for (int co = 0; co < 16; ++co) acc += bf(N.w2[W2i(tp, co, ci)]) * dv[co];
         }
       }
       B.d1[e] = acc;
@@ -319,6 +457,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     }
     __syncthreads();
   }
+  tc_end(tc);
   float* dst = partial + (size_t)blockIdx.x * NP;
   for (int i = t; i < NP; i += CT) dst[i] = B.grad[i];
   // this CTA's loss
@@ -449,7 +588,7 @@ __global__ void k_cnn_apply(const int *__restrict__ boxes, int n, const float *_
   }
 }
 
-size_t fwd_smem() { return ((sizeof(NetS) + 15) & ~(size_t)15) + ((sizeof(FwdS) + 15) & ~(size_t)15); }
+size_t fwd_smem() { return ((sizeof(NetS) + 127) & ~(size_t)127) + ((sizeof(FwdS) + 127) & ~(size_t)127); }
 size_t train_smem() { return fwd_smem() + sizeof(BwdS); }
 
 }  // namespace
@@ -464,6 +603,7 @@ struct sm_cnn {
   char *arena = nullptr;
   float *w = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *partial = nullptr, *lossp = nullptr,
         *loss = nullptr;
+  unsigned *derr = nullptr;     // device error word of the network kernels
   bf16 *X = nullptr;            // samples [max_samples][1000][2]
   float *target = nullptr;      // [max_samples][512]
   float *scale = nullptr;       // [max_samples]
@@ -497,7 +637,8 @@ static int cfail(sm_cnn *c, int code, const char *msg) {
   } while (0)
 
 struct CLayout {
-  size_t w, m, v, grad, partial, lossp, loss, X, target, scale, phi_prev, Xp, out, sc_p, dbg, ids, boxes, total;
+  size_t w, m, v, grad, partial, lossp, loss, derr, X, target, scale, phi_prev, Xp, out, sc_p, dbg, ids, boxes,
+      total;
 };
 
 static CLayout clayout(int max_samples, int max_boxes, int sms) {
@@ -515,6 +656,7 @@ static CLayout clayout(int max_samples, int max_boxes, int sms) {
   L.partial = take(4 * (size_t)NP * sms);
   L.lossp = take(4 * (size_t)sms);
   L.loss = take(4);
+  L.derr = take(4);
   L.X = take(2 * (size_t)NPOS * 2 * max_samples);
   L.target = take(4 * (size_t)512 * max_samples);
   L.scale = take(4 * (size_t)max_samples);
@@ -572,6 +714,7 @@ extern "C" int sm_cnn_bind_arena(sm_cnn *c, void *dev_ptr, size_t bytes) {
   c->partial = (float *)(a + L.partial);
   c->lossp = (float *)(a + L.lossp);
   c->loss = (float *)(a + L.loss);
+  c->derr = (unsigned *)(a + L.derr);
   c->X = (bf16 *)(a + L.X);
   c->target = (float *)(a + L.target);
   c->scale = (float *)(a + L.scale);
@@ -607,6 +750,20 @@ extern "C" int sm_cnn_get_params(sm_cnn *c, float *host, int n) {
   return SM_OK;
 }
 
+// synchronise and read the network kernels' error word (cleared after
+// reading): a tensor-core completion wait that ran out is SM_ETIMEOUT
+static int check_derr(sm_cnn *c) {
+  unsigned e = 0;
+  CCK(cudaMemcpyAsync(&e, c->derr, 4, cudaMemcpyDeviceToHost, c->stream));
+  CCK(cudaStreamSynchronize(c->stream));
+  if (e) {
+    CCK(cudaMemsetAsync(c->derr, 0, 4, c->stream));
+    CCK(cudaStreamSynchronize(c->stream));
+    return cfail(c, SM_ETIMEOUT, "tensor-core completion wait ran out");
+  }
+  return SM_OK;
+}
+
 // forward of n explicit inputs (host [n][1000][2] floats, rounded to BF16
 // on upload); out [n][512] and optional per-layer activations of the first
 // min(n, 16) boxes ([n][4][16][512]: z1, a1, z2, a2)
@@ -617,21 +774,21 @@ extern "C" int sm_cnn_forward(sm_cnn *c, const float *x_host, int n, float *out_
   for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(x_host[i]);
   CCK(cudaMemcpyAsync(c->Xp, xb.data(), 2 * xb.size(), cudaMemcpyHostToDevice, c->stream));
   int grid = std::min(n, 4 * c->sms);
-  k_cnn_forward<<<grid, CT, fwd_smem(), c->stream>>>(c->Xp, n, c->w, c->out, acts_host ? c->dbg : nullptr);
+  k_cnn_forward<<<grid, CT, fwd_smem(), c->stream>>>(c->Xp, n, c->w, c->out, acts_host ? c->dbg : nullptr,
+                                                     c->derr);
   CCK(cudaGetLastError());
   CCK(cudaMemcpyAsync(out_host, c->out, 4 * (size_t)512 * n, cudaMemcpyDeviceToHost, c->stream));
   if (acts_host)
     CCK(cudaMemcpyAsync(acts_host, c->dbg, 4 * (size_t)std::min(n, MAX_DEBUG) * 4 * 16 * 512,
                         cudaMemcpyDeviceToHost, c->stream));
-  CCK(cudaStreamSynchronize(c->stream));
-  return SM_OK;
+  return check_derr(c);
 }
 
 static int grad_step(sm_cnn *c, int n, const int *ids_host) {
   CCK(cudaMemcpyAsync(c->ids, ids_host, 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream));
   int nblk = std::min(n, c->sms);
   k_cnn_train<<<nblk, CT, train_smem(), c->stream>>>(c->X, c->target, c->ids, n, 1.0f / (512.0f * n), c->w,
-                                                     c->partial, c->lossp);
+                                                     c->partial, c->lossp, c->derr);
   k_cnn_reduce<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->partial, nblk, c->grad, c->lossp, c->loss);
   CCK(cudaGetLastError());
   return SM_OK;
@@ -661,7 +818,7 @@ extern "C" int sm_cnn_gradient(sm_cnn *c, const float *x_host, const float *t_ho
   CCK(cudaMemcpyAsync(grad_host, c->grad, 4 * NP, cudaMemcpyDeviceToHost, c->stream));
   float l = 0.0f;
   CCK(cudaMemcpyAsync(&l, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
-  CCK(cudaStreamSynchronize(c->stream));
+  if ((st = check_derr(c))) return st;
   if (loss) *loss = l;
   c->n_samples = 0;
   return SM_OK;
@@ -708,7 +865,7 @@ extern "C" int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned
       if ((st = adam(c, lr))) return st;
       float l = 0.0f;
       CCK(cudaMemcpyAsync(&l, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
-      CCK(cudaStreamSynchronize(c->stream));
+      if ((st = check_derr(c))) return st;
       acc += l;
       ++nb;
     }
@@ -764,7 +921,8 @@ static int cnn_pre_solve(void *obj, sm_ctx *ctx) {
     CCK(cudaMemcpyAsync(c->boxes, boxes.data(), 4 * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
     k_cnn_gather<<<k, CT, 0, ctx->stream>>>(c->boxes, k, ctx->phi, ctx->rhs, ctx->gh, ctx->nbr6, ctx->level,
                                             ctx->child, ctx->bc, ctx->lh, c->Xp, c->sc_p, nullptr, 0);
-    k_cnn_forward<<<std::min(k, 4 * c->sms), CT, fwd_smem(), ctx->stream>>>(c->Xp, k, c->w, c->out, nullptr);
+    k_cnn_forward<<<std::min(k, 4 * c->sms), CT, fwd_smem(), ctx->stream>>>(c->Xp, k, c->w, c->out, nullptr,
+                                                                            c->derr);
     k_cnn_apply<<<k, CT, 0, ctx->stream>>>(c->boxes, k, c->out, c->sc_p, ctx->phi, c->taper);
     ctx->n_launch += 3;
     CCK(cudaGetLastError());

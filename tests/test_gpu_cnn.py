@@ -187,15 +187,41 @@ def test_training_on_recorded_solves_reduces_loss():
 
 
 def test_learned_warm_start_gain():
-    """Train on the first steps of a run, then predict on the following
-    steps; the same run without the network is the reference.  Both meet
-    the tolerance on every solve; the residual test never keeps a worse start."""
-    net = pkg().Network(8192, 1024)
+    """Train on the pairs recorded during the first steps of a run, then
+    measure what the network gained on pairs it never saw (recorded during
+    the following steps, with the trained weights frozen: Adam with a zero
+    learning rate only evaluates the loss): its mean squared error must be
+    below that of the zero prediction (the plain warm start, loss = mean of
+    t^2).  Measured: 57.1 against 58.5, a gain of 2.5% -- most unseen
+    targets sit at the clip of the per-box scaling, which a per-box network
+    with a 7^3 receptive field cannot predict.  In the solver the residual
+    test decides: a prediction is kept only when it lowers the relative
+    residual, so the learned run never takes more V-cycles than the plain
+    one; on this mesh the predictions are not kept."""
+    p_ = pkg()
+    net = p_.Network(8192, 1024)
     net.set_params(synth.cnn_initial_params())
-    g1, c_rec = streamer_run(1, net, steps=6)
+    streamer_run(1, net, steps=6)
     net.train(60, 32, 1e-3)
-    # same run again: record phase replayed without the network, then
-    # the evaluation steps with and without predictions
+    trained = net.get_params()
+    # held-out pairs: steps 7-10 of the same run, recorded by a second
+    # network that holds the trained weights
+    held = p_.Network(8192, 1024)
+    held.set_params(trained)
+    g_rec, _ = streamer_run(None, None, steps=6)
+    held.attach(g_rec, 1, per_solve=256)
+    dt = g_rec.dt_next
+    for _ in range(4):
+        rc, dt, c1, c2 = g_rec.advance(dt, Q, EPS0, 1e-8, 40)
+        assert rc == 0
+    held.attach(g_rec, 0)
+    assert held.stats()["samples"] >= 8 * 64
+    loss_trained = held.train(1, 64, 0.0)
+    held.set_params(np.zeros_like(trained))
+    loss_zero = held.train(1, 64, 0.0)
+    print("held-out loss: trained %.4e, zero prediction %.4e" % (loss_trained, loss_zero))
+    assert np.isfinite(loss_trained) and loss_trained < loss_zero
+    # the solver with predictions: same tolerance met, never more V-cycles
     g_plain, c_plain = streamer_run(None, None, steps=10)
     g_pred, _ = streamer_run(None, None, steps=6)
     net.attach(g_pred, 2, per_solve=1024, taper=True)
