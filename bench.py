@@ -119,6 +119,15 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max * 1e-3)
 
 
+def bf16_peak_tflops():
+    """Measured dense BF16 matmul throughput of this GPU (burst), TFLOP/s."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("bf16_tflops", 1900.0))
+    return 1900.0
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -558,9 +567,10 @@ def run_gpu(args):
         sus = per_call(lambda: g.fluid_stage(dt))
         fluid = {"fp64_peak": f64}
         # FP64 instructions per leaf cell as counted by ncu on this workload
-        # (sm__inst_executed_pipe_fp64: k_field 27.4 with the FP64 square
-        # root of |E|, stage-1 k_update 112.8); bytes: compulsory traffic
-        for name, us, bpc, ipc in (("field (k_field)", fus, 16.0, 27.4), ("euler stage (k_update)", sus, 72.0, 112.8)):
+        # (32 x smsp__inst_executed_pipe_fp64 / leaf cells: k_field 19.4 with
+        # the FP64 square root of |E|, stage-1 k_update 82.0); bytes:
+        # compulsory traffic
+        for name, us, bpc, ipc in (("field (k_field)", fus, 16.0, 19.4), ("euler stage (k_update)", sus, 72.0, 82.0)):
             fluid[name] = {"us": round(us, 2), "gbs": round(leaf_cells * bpc / (us * 1e-6) / 1e9, 1),
                            "hbm_frac": round(leaf_cells * bpc / (us * 1e-6) / 1e9 / peak, 4),
                            "fp64_ginstr": round(leaf_cells * ipc / (us * 1e-6) / 1e9, 1),
@@ -938,6 +948,19 @@ def bench_learned(args, dev, world):
     g.close()
     res = {"train_samples": samples, "train_epochs": 30, "train_s": round(train_s, 3),
            "final_loss": round(loss, 6)}
+    # the network kernels against the tensor-core roof: forward (inference)
+    # and a training gradient pass over 4096 recorded samples
+    bf16_peak = bf16_peak_tflops()
+    kern = {}
+    for kind, name in ((0, "forward (k_cnn_forward)"), (1, "gradient pass (k_cnn_train + reduce)")):
+        us, fl, tf = net.kernel_bench(kind, 4096, 10)
+        kern[name] = {"us": round(us, 1), "tflops_model": round(fl / (us * 1e-6) / 1e12, 2),
+                      "tensor_tflops": round(tf / (us * 1e-6) / 1e12, 2),
+                      "tensor_frac_of_bf16_peak": round(tf / (us * 1e-6) / 1e12 / bf16_peak, 4)}
+    res["network_kernels"] = kern
+    res["network_kernels_note"] = ("4096 boxes per launch, CUDA events; model FLOPs 16416 per voxel forward, 3x "
+                                   "for a gradient pass; tensor FLOPs = the 135 tcgen05 MMAs (128x16x16) per box "
+                                   "of layer 2; peak = measured BF16 burst %.1f TFLOP/s" % bf16_peak)
     for mode in ("plain", "learned"):
         g, dt = start()
         _, _, dt = steps(g, dt, n_train)

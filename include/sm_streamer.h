@@ -444,6 +444,17 @@ int sm_cnn_adam_step(sm_cnn *c, const float *grad_host, float lr);
  * Adam step after each; sample order shuffled per epoch from `seed`.  Out:
  * mean loss of the last epoch.  Synchronises. */
 int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned long long seed, float *loss);
+/* Timing of the network kernels (build form, no paper passage): the mean
+ * duration of `reps` launches (CUDA events on the network's stream, after
+ * one warm-up) over the first n recorded samples; kind 0: the forward
+ * kernel (n <= max_boxes), kind 1: one training gradient pass.  *flops: the
+ * model's FLOPs of one launch (16416 per voxel forward, 3x that for a
+ * gradient pass); *tensor_flops: those the tensor cores execute per launch
+ * (layer 2: 135 MMAs of 128x16x16 per box, padding rows included).
+ * Overwrites the prediction outputs.  Errors: SM_EINVAL (kind, n, reps),
+ * SM_ESTATE (fewer recorded samples than n), SM_ETIMEOUT, SM_ECUDA. */
+int sm_cnn_kernel_bench(sm_cnn *c, int kind, int n, int reps, double *us_per_launch, double *flops,
+                        double *tensor_flops);
 /* Couple the network to a solver's sm_advance_fluid: mode 1 records
  * (input, solved change) pairs of up to per_solve leaf boxes of the two
  * finest levels (every stride-th) per solve; mode 2 predicts a warm start

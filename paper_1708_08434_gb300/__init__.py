@@ -68,6 +68,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_batch_set_graphs", "sm_batch_kernel_bench", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
+           "sm_cnn_kernel_bench",
            "sm_cnn_last_error",
            "sm_batch_last_error",
            "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
@@ -149,6 +150,7 @@ def load():
         "sm_cnn_train": [P, I, I, C.c_float, C.c_ulonglong, C.POINTER(C.c_float)],
         "sm_cnn_attach": [P, P, I, I, I, I, D],
         "sm_cnn_stats": [P, pI, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), pD],
+        "sm_cnn_kernel_bench": [P, I, I, I, pD, pD, pD],
         "sm_cnn_last_error": [P],
         "sm_last_error": [P],
         "sm_quad_create": [C.POINTER(P), P, I, I, I, P],
@@ -636,6 +638,14 @@ class Network:
 
     def attach(self, solver, mode, per_solve=512, stride=1, taper=False, accept=1.0):
         self._ck(self._lib.sm_cnn_attach(solver._h, self._h, mode, per_solve, stride, int(taper), accept))
+
+    def kernel_bench(self, kind: int, n: int, reps: int = 10):
+        """(us per launch, model FLOPs, tensor-core FLOPs) of the forward
+        kernel (kind 0) or a training gradient pass (kind 1) over the first n
+        recorded samples."""
+        us, fl, tf = C.c_double(), C.c_double(), C.c_double()
+        self._ck(self._lib.sm_cnn_kernel_bench(self._h, kind, n, reps, C.byref(us), C.byref(fl), C.byref(tf)))
+        return us.value, fl.value, tf.value
 
     def stats(self):
         n, p, k = C.c_int(), C.c_longlong(), C.c_longlong()

@@ -73,9 +73,6 @@ struct FwdS {
 };
 static_assert(offsetof(FwdS, a1hi) - offsetof(FwdS, a1lo) == NPOSA * 16, "A operand halves");
 
-__device__ __forceinline__ float A1(const FwdS &F, int pos, int c) {
-  return bf(c < 8 ? F.a1lo[pos * 8 + c] : F.a1hi[pos * 8 + c - 8]);
-}
 
 // ---- tcgen05: 5th-generation tensor cores, accumulator in tensor memory ----
 //
@@ -90,7 +87,8 @@ __device__ __forceinline__ float A1(const FwdS &F, int pos, int c) {
 // one padded row), the second 8 channels in a1hi (LBO).  B (W2 of one tap,
 // 16 x 16) is stored as four 8x8 core matrices: LBO 256 bytes (channels
 // 8-15), SBO 128 bytes (output channels 8-15).  Each tile accumulates its
-// 27 taps (K = 16 each) in 16 columns of tensor memory.
+// 27 taps (K = 16 each) in 16 columns of tensor memory; the five tiles are
+// issued by five warps and complete one mbarrier phase together.
 constexpr int TC_TILES = 5, TC_COLS = 128;
 constexpr uint32_t TC_IDESC = (1u << 4)             // D: FP32
                               | (1u << 7)           // A: BF16
@@ -172,7 +170,7 @@ __device__ void tc_begin(TcState &tc, uint64_t *mbar, uint32_t *slot, unsigned *
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(TC_TILES) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -252,16 +250,16 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
   tc_fence_before();
   __syncthreads();
   // layer 2: same 3^3 conv 16 -> 16 as an implicit GEMM on tcgen05 (the
-  // tiling is described with TcState); one thread issues the 135 MMAs
-  if (t == 0) {
+  // tiling is described with TcState); lane 0 of warp j issues the 27 MMAs
+  // of tile j and commits them to the mbarrier (TC_TILES arrivals per box)
+  if ((t & 31) == 0 && (t >> 5) < TC_TILES) {
     tc_fence_after();
+    const int j = t >> 5;
     const uint32_t a0 = smem_u32(F.a1lo), b0 = smem_u32(N.w2);
-    for (int j = 0; j < TC_TILES; ++j)
-      for (int tp = 0; tp < 27; ++tp) {
-        const int pos = 1 + 10 * (11 + 16 * j) + Off(tp);
-        tc_mma(tc.taddr + 16 * j, tc_desc(a0 + 16 * pos, NPOSA * 16, 160), tc_desc(b0 + 512 * tp, 256, 128),
-               tp > 0);
-      }
+    for (int tp = 0; tp < 27; ++tp) {
+      const int pos = 1 + 10 * (11 + 16 * j) + Off(tp);
+      tc_mma(tc.taddr + 16 * j, tc_desc(a0 + 16 * pos, NPOSA * 16, 160), tc_desc(b0 + 512 * tp, 256, 128), tp > 0);
+    }
     tc_commit(tc.mbar);
   }
   const bool ok = mbar_wait(tc.mbar, tc.phase);
@@ -414,10 +412,11 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     // layer 2 weights: thread (co, ci) accumulates its 27 taps
     {
       int co = t >> 4, ci = t & 15;
+      const bf16 *a1c = (ci < 8 ? F.a1lo : F.a1hi) + (ci & 7);  // channel ci, 8 per position
       for (int tp = 0; tp < 27; ++tp) {
         int off = Off(tp);
         float acc = 0.0f;
-        for (int v = 0; v < 512; ++v) acc += A1(F, Pos(v) + off, ci) * B.d2[v * 16 + co];
+        for (int v = 0; v < 512; ++v) acc += bf(a1c[(Pos(v) + off) * 8]) * B.d2[v * 16 + co];
         B.grad[O_W2 + (co * 16 + ci) * 27 + tp] += acc;
       }
       if (t < 16) {
@@ -430,7 +429,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     for (int e = t; e < 512 * 16; e += CT) {
       int u = e >> 4, ci = e & 15;
       float acc = 0.0f;
-      if (A1(F, Pos(u), ci) > 0.0f) {
+      if (bf(((ci < 8 ? F.a1lo : F.a1hi) + (ci & 7))[Pos(u) * 8]) > 0.0f) {
         int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
         for (int tp = 0; tp < 27; ++tp) {
           int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
@@ -872,6 +871,51 @@ extern "C" int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned
     last = acc / nb;
   }
   if (loss) *loss = (float)last;
+  return SM_OK;
+}
+
+// Average duration of one launch over the first n recorded samples: kind 0
+// the forward kernel (inference), kind 1 a training gradient pass (forward,
+// backward, partial gradients, reduction).  FLOPs per launch from the
+// network's model: 16416 per voxel forward (layers of 1728, 13824 and 864),
+// twice that backward; tensor-core FLOPs: the 135 MMAs of a box (M 128,
+// N 16, K 16, padding rows of the tiles included).
+extern "C" int sm_cnn_kernel_bench(sm_cnn *c, int kind, int n, int reps, double *us_per_launch, double *flops,
+                                   double *tensor_flops) {
+  if (!c || !c->arena || (kind != 0 && kind != 1) || n < 1 || reps < 1) return SM_EINVAL;
+  if (n > c->n_samples) return cfail(c, SM_ESTATE, "fewer recorded samples than requested");
+  if (kind == 0 && n > c->max_boxes) return SM_EINVAL;
+  std::vector<int> ids(n);
+  for (int i = 0; i < n; ++i) ids[i] = i;
+  CCK(cudaMemcpyAsync(c->ids, ids.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+  auto launch = [&]() -> int {
+    if (kind == 0) {
+      k_cnn_forward<<<std::min(n, 4 * c->sms), CT, fwd_smem(), c->stream>>>(c->X, n, c->w, c->out, nullptr,
+                                                                            c->derr);
+      CCK(cudaGetLastError());
+      return SM_OK;
+    }
+    return grad_step(c, n, ids.data());
+  };
+  int st = launch();  // warm-up
+  if (st) return st;
+  cudaEvent_t a, b;
+  CCK(cudaEventCreate(&a));
+  CCK(cudaEventCreate(&b));
+  CCK(cudaEventRecord(a, c->stream));
+  for (int r = 0; r < reps && !st; ++r) st = launch();
+  CCK(cudaEventRecord(b, c->stream));
+  CCK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  CCK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st) return st;
+  if ((st = check_derr(c))) return st;
+  const double fwd = 16416.0 * 512.0 * n, tc = 135.0 * 2.0 * 128 * 16 * 16 * n;
+  if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
+  if (flops) *flops = kind == 0 ? fwd : 3.0 * fwd;
+  if (tensor_flops) *tensor_flops = tc;
   return SM_OK;
 }
 

@@ -18,50 +18,95 @@ int sm_mg_solve_internal(sm_ctx *ctx, double tol, int max_cycles, int *cycles);
 // device helpers
 // ---------------------------------------------------------------------------
 
-// Linear interpolation in two tables sampled at E_k = k e_max/(n-1),
-// clamped at both ends, at the same e: the index and weight are computed
-// once (the same arithmetic as two separate lookups).
-__device__ __forceinline__ void lookup2(const double *__restrict__ ta, const double *__restrict__ tb, int n,
-                                        double inv_de, double e, double &va, double &vb) {
-  double x = e * inv_de;
-  if (x <= 0.0) {
+// Non-negative doubles (no NaN) order as their bit patterns: clamps and
+// minima of such values are integer operations, off the FP64 pipe (2 FP64
+// instructions per clock and SM on this GPU).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double dabs(double x) { return __longlong_as_double(dbits(x) & 0x7fffffffffffffffll); }
+
+// floor(x) and x - floor(x) of a finite 0 < x < 2^30, exactly, from the bit
+// fields: the integer part is the significand shifted by the exponent, the
+// fraction the remaining significand bits renormalised (never subnormal:
+// at least 2^-52)
+__device__ __forceinline__ void split_frac(double x, int &i, double &w) {
+  const unsigned long long b = (unsigned long long)dbits(x);
+  const int e = (int)(b >> 52) - 1023;
+  if (e < 0) {
+    i = 0;
+    w = x;
+    return;
+  }
+  const unsigned long long m = (b & 0x000fffffffffffffull) | (1ull << 52);
+  const int sh = 52 - e;
+  i = (int)(m >> sh);
+  const unsigned long long fm = m & ((1ull << sh) - 1ull);
+  if (fm == 0ull) {
+    w = 0.0;
+    return;
+  }
+  const int top = 63 - __clzll((long long)fm);  // value fm 2^(e-52) = 1.f 2^(top + e - 52)
+  w = __longlong_as_double((long long)(((unsigned long long)(top + e - 52 + 1023) << 52) |
+                                       ((fm << (52 - top)) & 0x000fffffffffffffull)));
+}
+
+// Linear interpolation in two tables sampled at E_k = k e_max/(n-1) at
+// x = e (n-1)/e_max (given), clamped at both ends (Sec. 2.3): the index and
+// weight come from the bits of x; the interpolation a0 + w (a1 - a0) is
+// FP64.
+__device__ __forceinline__ void lookup2x(const double *__restrict__ ta, const double *__restrict__ tb, int n,
+                                         long long xmax, double x, double &va, double &vb) {
+  const long long bx = dbits(x);
+  if (bx <= 0) {  // x <= 0 (or -0)
     va = __ldg(ta);
     vb = __ldg(tb);
     return;
   }
-  if (x >= (double)(n - 1)) {
+  if (bx >= xmax) {  // x >= n - 1
     va = __ldg(ta + n - 1);
     vb = __ldg(tb + n - 1);
     return;
   }
-  int i = (int)x;
-  double w = x - (double)i;
+  int i;
+  double w;
+  split_frac(x, i, w);
   double a0 = __ldg(ta + i), a1 = __ldg(ta + i + 1), b0 = __ldg(tb + i), b1 = __ldg(tb + i + 1);
   va = a0 + w * (a1 - a0);
   vb = b0 + w * (b1 - b0);
 }
 
-// psi(a/b)*b for the Koren limiter psi(x) = max(0, min(1, (2+x)/6, x)),
-// without the division: 0 when a*b <= 0, else sign(b) min(|b|, (2|b|+|a|)/6, |a|)
+__device__ __forceinline__ void lookup2(const double *__restrict__ ta, const double *__restrict__ tb,
+                                        const Table &T, double e, double &va, double &vb) {
+  lookup2x(ta, tb, T.n, T.xmax, e * T.inv_de, va, vb);
+}
+
+// psi(a/b) b for the Koren limiter psi(x) = max(0, min(1, (2+x)/6, x)),
+// without the division: 0 when a b <= 0 (the sign of the product, tested on
+// its bits), else sign(b) min(|b|, (2|b| + |a|)/6, |a|) with the minimum
+// taken on the bit patterns
 __device__ __forceinline__ double koren(double a, double b) {
-  if (a * b <= 0.0) return 0.0;
-  double ab = fabs(b), aa = fabs(a);
-  double m = fmin(fmin(ab, (2.0 * ab + aa) * (1.0 / 6.0)), aa);
-  return b > 0.0 ? m : -m;
+  if (dbits(a * b) <= 0) return 0.0;
+  const double ab = dabs(b), aa = dabs(a);
+  long long m = dbits(ab);
+  m = min(m, dbits(fma(2.0, ab, aa) * (1.0 / 6.0)));
+  m = min(m, dbits(aa));
+  return __longlong_as_double(m | (dbits(b) & (long long)0x8000000000000000ull));
 }
 
 // Flux through the face between cells L and R (positive toward R):
-// v = -mu(E*) E_face, E* = (|E|_L + |E|_R)/2; advective part by Eq. 7 when
-// v >= 0 and Eq. 6 when v < 0; diffusive part -D(E*) (n_R - n_L)/dx.
+// v = -mu(E*) E_face with E_face = (p_L - p_R)/dx, E* = (|E|_L + |E|_R)/2;
+// advective part by Eq. 7 when v >= 0 and Eq. 6 when v < 0; diffusive part
+// -D(E*) (n_R - n_L)/dx.  Written as (-mu dp n_f - D dn)/dx: v < 0 exactly
+// when mu dp > 0.
 __device__ __forceinline__ double face_flux(double nL2, double nL, double nR, double nR2, double pL, double pR,
                                             double eL, double eR, double inv_h, const Table &tb) {
-  double e_face = (pL - pR) * inv_h;
-  double e_star = 0.5 * (eL + eR);
   double mu, dc;
-  lookup2(tb.mu, tb.diff, tb.n, tb.inv_de, e_star, mu, dc);
-  double v = -mu * e_face;
-  double nf = v < 0.0 ? nR - koren(nR2 - nR, nR - nL) : nL + koren(nL - nL2, nR - nL);
-  return v * nf - dc * (nR - nL) * inv_h;
+  lookup2x(tb.mu, tb.diff, tb.n, tb.xmax, (eL + eR) * tb.hinv_de, mu, dc);
+  const double t1 = mu * (pL - pR);
+  const double dn = nR - nL;
+  const bool up = dbits(t1) > 0;  // v < 0: the upwind cell is R
+  const double k = koren(up ? nR2 - nR : nL - nL2, dn);
+  const double nf = up ? nR - k : nL + k;
+  return fma(-t1, nf, -dc * dn) * inv_h;
 }
 
 // Density ghost (depth t = 1 or 2) across refinement face f of fine box b
@@ -149,14 +194,15 @@ __global__ void __launch_bounds__(512) k_field(const int32_t *__restrict__ leaf,
   const double *p = phi + (size_t)b * CELLS;
   double pc = p[t];
   double e2 = 0.0;
+  const double hh = 0.5 * ih;
   const int stride[3] = {1, NC, FACE};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double pm = c[a] > 0 ? p[t - stride[a]] : pot_ghost(phi, nbr6, gh, b, 2 * a, c[0], c[1], c[2], pc, bc, 0);
     double pp = c[a] < NC - 1 ? p[t + stride[a]]
                               : pot_ghost(phi, nbr6, gh, b, 2 * a + 1, c[0], c[1], c[2], pc, bc, 0);
-    double e = 0.5 * ((pm - pc) * ih + (pc - pp) * ih);
-    e2 += e * e;
+    const double e = (pm - pp) * hh;  // mean of (pm - pc)/dx and (pc - pp)/dx
+    e2 = fma(e, e, e2);
   }
   emag[(size_t)b * CELLS + t] = sqrt(e2);
 }
@@ -179,15 +225,15 @@ __device__ __forceinline__ void dt_terms(const double *__restrict__ phi, const d
   double pc = p[t];
   const int stride[3] = {1, NC, FACE};
   double mu, dc;
-  lookup2(tb.mu, tb.diff, tb.n, tb.inv_de, em, mu, dc);
+  lookup2(tb.mu, tb.diff, tb, em, mu, dc);
   double s = 0.0;
+  const double hh = 0.5 * ih;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double pm = c[a] > 0 ? p[t - stride[a]] : pot_ghost(phi, nbr6, gh, b, 2 * a, c[0], c[1], c[2], pc, bc, 0);
     double pp = c[a] < NC - 1 ? p[t + stride[a]]
                               : pot_ghost(phi, nbr6, gh, b, 2 * a + 1, c[0], c[1], c[2], pc, bc, 0);
-    double e = 0.5 * ((pm - pc) * ih + (pc - pp) * ih);
-    s += fabs(mu * e);
+    s += dabs(mu * ((pm - pp) * hh));  // the cell component: mean of the two face fields
   }
   adv = s * ih;
   ad = adv + 6.0 * dc * ih * ih;
@@ -377,7 +423,7 @@ __global__ void __launch_bounds__(512) k_update(
   double e = S.e[I10(ci, cj, ck)];
   double nes = S.n[I12(ci, cj, ck)];
   double alpha, mu;
-  lookup2(tb.alpha, tb.mu, tb.n, tb.inv_de, e, alpha, mu);
+  lookup2(tb.alpha, tb.mu, tb, e, alpha, mu);
   double src = alpha * mu * e * nes;
   double ne_new = nes - dt * div + dt * src;
   double ni_new = ni_src[base + t] + dt * src;
@@ -387,7 +433,7 @@ __global__ void __launch_bounds__(512) k_update(
   }
   ne_dst[base + t] = ne_new;
   ni_dst[base + t] = ni_new;
-  rhs[base + t] = -q * (ni_new - ne_new) * inv_eps;
+  rhs[base + t] = (ni_new - ne_new) * (-q * inv_eps);
   if (want_dt) {
     double adv, ad, drt;
     dt_terms(phi, gh, nbr6, bc, b, t, ih, e, nes, tb, adv, ad, drt);
@@ -409,6 +455,9 @@ static Table table_of(const sm_ctx *ctx) {
   tb.alpha = ctx->tab + 8192;
   tb.n = ctx->tab_n;
   tb.inv_de = (ctx->tab_n - 1) / ctx->tab_emax;
+  tb.hinv_de = 0.5 * tb.inv_de;
+  const double top = (double)(ctx->tab_n - 1);
+  memcpy(&tb.xmax, &top, sizeof top);
   return tb;
 }
 

@@ -56,6 +56,8 @@ struct Table {
   const double *mu, *diff, *alpha;
   int n;
   double inv_de;    // (n-1)/e_max
+  double hinv_de;   // (n-1)/(2 e_max): the index of the face value (e_L + e_R)/2 from e_L + e_R
+  long long xmax;   // bit pattern of the double n - 1 (upper clamp, compared as an integer)
 };
 
 // kernel classes for sm_kernel_bench
