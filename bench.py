@@ -80,11 +80,14 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="mesh of --mode kernels and --mode vcycle (the step and its metric use streamer6)")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "vcycle", "kernels", "batch", "large", "axi", "learned"],
+                    choices=["step", "vcycle", "kernels", "batch", "large", "axi", "learned", "network"],
                     help="vcycle: build the workload, then only run --steps V-cycles; "
                          "batch: only the batched solves, --steps solves with the default "
                          "schedule (small, fixed launch sequences for ncu captures); "
-                         "large: the 1e8-cell mesh alone; axi: the axisymmetric variant alone")
+                         "large: the 1e8-cell mesh alone; axi: the axisymmetric variant alone; "
+                         "network: the network kernels alone (--steps launches each)")
+    ap.add_argument("--net-samples", type=int, default=4096,
+                    help="--mode network only: synthetic samples (boxes) per launch")
     ap.add_argument("--batch-solves", type=int, default=256,
                     help="--mode batch only: solve the first N of the 256 batched problems (small ncu captures)")
     ap.add_argument("--batch-schedule", type=int, nargs=2, default=None, metavar=("SHAPE", "BLOCKS_PER_SM"),
@@ -126,6 +129,48 @@ def bf16_peak_tflops():
         with open(p) as f:
             return float(json.load(f).get("bf16_tflops", 1900.0))
     return 1900.0
+
+
+def network_kernels(net, n, reps):
+    """Forward and training-gradient-pass timing of the network kernels over
+    the first n recorded samples, against the measured BF16 peak."""
+    bf16_peak = bf16_peak_tflops()
+    kern = {}
+    for kind, name in ((0, "forward (k_cnn_forward)"), (1, "gradient pass (k_cnn_train + reduce)")):
+        us, fl, tf = net.kernel_bench(kind, n, reps)
+        kern[name] = {"us": round(us, 1), "tflops_model": round(fl / (us * 1e-6) / 1e12, 2),
+                      "tensor_tflops": round(tf / (us * 1e-6) / 1e12, 2),
+                      "tensor_frac_of_bf16_peak": round(tf / (us * 1e-6) / 1e12 / bf16_peak, 4)}
+    note = ("%d boxes per launch, CUDA events; model FLOPs 16416 per voxel forward, 3x for a gradient pass; "
+            "tensor FLOPs = the tcgen05 MMAs issued per box (forward 135 of 128x16x16; a gradient pass adds "
+            "405 of 128x16x16 and 288 of 128x48x16), discarded tile rows included; peak = measured BF16 "
+            "burst %.1f TFLOP/s" % (n, bf16_peak))
+    return kern, note
+
+
+def run_network(args):
+    """The network kernels alone on seeded synthetic samples (inputs uniform
+    in [-1, 1], targets normal with deviation 0.3): a small command for
+    kernel captures."""
+    import torch
+    import synth
+    import __graft_entry__
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    import paper_1708_08434_gb300 as pkg
+    n = args.net_samples
+    net = pkg.Network(n, n)
+    rng = np.random.default_rng(7)
+    p = synth.cnn_initial_params().astype(np.float32)
+    net.set_params(p)
+    net.load_samples(rng.uniform(-1.0, 1.0, (n, 1000, 2)).astype(np.float32),
+                     (0.3 * rng.standard_normal((n, 512))).astype(np.float32))
+    kern, note = network_kernels(net, n, max(1, args.steps))
+    net.close()
+    print(json.dumps({"mode": "network", "samples": n, "network_kernels": kern, "note": note}), flush=True)
 
 
 def measured_peaks():
@@ -950,17 +995,7 @@ def bench_learned(args, dev, world):
            "final_loss": round(loss, 6)}
     # the network kernels against the tensor-core roof: forward (inference)
     # and a training gradient pass over 4096 recorded samples
-    bf16_peak = bf16_peak_tflops()
-    kern = {}
-    for kind, name in ((0, "forward (k_cnn_forward)"), (1, "gradient pass (k_cnn_train + reduce)")):
-        us, fl, tf = net.kernel_bench(kind, 4096, 10)
-        kern[name] = {"us": round(us, 1), "tflops_model": round(fl / (us * 1e-6) / 1e12, 2),
-                      "tensor_tflops": round(tf / (us * 1e-6) / 1e12, 2),
-                      "tensor_frac_of_bf16_peak": round(tf / (us * 1e-6) / 1e12 / bf16_peak, 4)}
-    res["network_kernels"] = kern
-    res["network_kernels_note"] = ("4096 boxes per launch, CUDA events; model FLOPs 16416 per voxel forward, 3x "
-                                   "for a gradient pass; tensor FLOPs = the 135 tcgen05 MMAs (128x16x16) per box "
-                                   "of layer 2; peak = measured BF16 burst %.1f TFLOP/s" % bf16_peak)
+    res["network_kernels"], res["network_kernels_note"] = network_kernels(net, 4096, 10)
     for mode in ("plain", "learned"):
         g, dt = start()
         _, _, dt = steps(g, dt, n_train)
@@ -1339,6 +1374,8 @@ def main():
         run_axi(args)
     elif args.mode == "learned":
         run_learned(args)
+    elif args.mode == "network":
+        run_network(args)
     else:
         run_gpu(args)
 

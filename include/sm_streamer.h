@@ -412,8 +412,9 @@ const char *sm_batch_last_error(const sm_batch *b);
  *          maximum; output delta on 8^3; phi += s * delta.  Training target:
  *          (phi_solved - phi_prev)/s clipped to [-8, 8].
  *   layers: conv 3^3 valid 2->16 + ReLU, conv 3^3 same 16->16 + ReLU (BF16
- *          tensor-core GEMM), conv 3^3 same 16->1.  Weights BF16, operands
- *          rounded to BF16, FP32 accumulation, biases FP32.
+ *          tensor-core GEMM, its data and weight gradients too), conv 3^3
+ *          same 16->1.  Weights BF16, operands rounded to BF16, FP32
+ *          accumulation, biases FP32; gradients at FP32 accuracy.
  *   parameters (FP32, SM_CNN_PARAMS): W1[16][2][27], b1[16], W2[16][16][27],
  *          b2[16], W3[16][27], b3 with tap t = (dx+1) + 3(dy+1) + 9(dz+1).
  * Samples and inputs are kept in the network's own arena
@@ -437,6 +438,10 @@ int sm_cnn_forward(sm_cnn *c, const float *x_host, int n, float *out_host, float
  * pairs (HOST [n][1000][2], [n][512]); grad HOST [SM_CNN_PARAMS].
  * Overwrites recorded samples. */
 int sm_cnn_gradient(sm_cnn *c, const float *x_host, const float *t_host, int n, float *grad_host, float *loss);
+/* Replace the recorded samples by n explicit (input, target) pairs (HOST
+ * [n][1000][2] floats rounded to BF16, [n][512]; 1 <= n <= max_samples) for
+ * sm_cnn_train and sm_cnn_kernel_bench.  Errors: SM_EINVAL, SM_ECUDA. */
+int sm_cnn_load_samples(sm_cnn *c, const float *x_host, const float *t_host, int n);
 /* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) with an explicit
  * gradient (HOST [SM_CNN_PARAMS]). */
 int sm_cnn_adam_step(sm_cnn *c, const float *grad_host, float lr);
@@ -449,8 +454,10 @@ int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned long long 
  * one warm-up) over the first n recorded samples; kind 0: the forward
  * kernel (n <= max_boxes), kind 1: one training gradient pass.  *flops: the
  * model's FLOPs of one launch (16416 per voxel forward, 3x that for a
- * gradient pass); *tensor_flops: those the tensor cores execute per launch
- * (layer 2: 135 MMAs of 128x16x16 per box, padding rows included).
+ * gradient pass); *tensor_flops: those the tensor cores execute per launch,
+ * discarded tile rows included (per box: forward 135 MMAs of 128x16x16; a
+ * gradient pass adds 405 of 128x16x16 for the data gradient and 288 of
+ * 128x48x16 for the weight gradient of layer 2).
  * Overwrites the prediction outputs.  Errors: SM_EINVAL (kind, n, reps),
  * SM_ESTATE (fewer recorded samples than n), SM_ETIMEOUT, SM_ECUDA. */
 int sm_cnn_kernel_bench(sm_cnn *c, int kind, int n, int reps, double *us_per_launch, double *flops,

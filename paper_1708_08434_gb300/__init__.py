@@ -68,7 +68,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_batch_set_graphs", "sm_batch_kernel_bench", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
-           "sm_cnn_kernel_bench",
+           "sm_cnn_kernel_bench", "sm_cnn_load_samples",
            "sm_cnn_last_error",
            "sm_batch_last_error",
            "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
@@ -151,6 +151,7 @@ def load():
         "sm_cnn_attach": [P, P, I, I, I, I, D],
         "sm_cnn_stats": [P, pI, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), pD],
         "sm_cnn_kernel_bench": [P, I, I, I, pD, pD, pD],
+        "sm_cnn_load_samples": [P, P, P, I],
         "sm_cnn_last_error": [P],
         "sm_last_error": [P],
         "sm_quad_create": [C.POINTER(P), P, I, I, I, P],
@@ -626,6 +627,13 @@ class Network:
         loss = C.c_float()
         self._ck(self._lib.sm_cnn_gradient(self._h, _hp(x), _hp(t), x.shape[0], _hp(g), C.byref(loss)))
         return g, loss.value
+
+    def load_samples(self, x, t):
+        """Explicit (input, target) pairs ([n][1000][2], [n][512]) as the
+        recorded samples that train() and kernel_bench() use."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        self._ck(self._lib.sm_cnn_load_samples(self._h, _hp(x), _hp(t), x.shape[0]))
 
     def adam_step(self, g, lr):
         g = np.ascontiguousarray(g, dtype=np.float32)

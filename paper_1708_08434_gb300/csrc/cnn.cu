@@ -15,8 +15,10 @@
 //          tensor cores: tcgen05.mma with the accumulator in tensor memory);
 //   conv 3^3 same 16->1 -> delta on 8^3;  prediction phi += s * delta.
 // Training: mean squared error against (phi_solved - phi_prev)/s (clipped),
-// Adam on
-// FP32 master weights, gradients reduced in a fixed order (deterministic).
+// Adam on FP32 master weights, gradients reduced in a fixed order
+// (deterministic).  The backward pass of layer 2 (its data and weight
+// gradients) runs on the tensor cores too, on dL/dz2 split into three BF16
+// terms whose sum is its FP32 value, so the gradient keeps FP32 accuracy.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -59,42 +61,66 @@ struct NetS {
   float b3;
 };
 
-// layer-1 activations as the A operand of the tensor-core layer 2: two
-// arrays of 8 channels, [pos][8] BF16 = 16 bytes per position, over the
-// 10^3 region plus padding that the unused rows of the last M tile read
-constexpr int NPOSA = 1024;
+// Layer-1 activations as a tensor-core operand.  The 10^3 region (one ghost
+// layer) is stored row by row, R = y + 10 z in padded coordinates, each row
+// as 10 slots of channels 0-7 followed by 10 slots of channels 8-15 (a slot
+// is one position, 8 BF16 = 16 bytes): slot x + 10 half + 20 R.  Two rows
+// past the region take the reads of the discarded rows of the last tile.
+constexpr int A1_ROWS = 102, A1_SLOTS = 20 * A1_ROWS;
+__device__ __forceinline__ int A1S(int x, int half, int R) { return x + 10 * half + 20 * R; }
 
 struct FwdS {
-  bf16 a1lo[NPOSA * 8];  // channels 0-7, zero outside the box interior
-  bf16 a1hi[NPOSA * 8];  // channels 8-15
-  bf16 x[NPOS * 2];      // [pos][ci]
-  bf16 a2[NPOS * 16];    // [pos][c], zero outside the box interior
+  bf16 a1[A1_SLOTS * 8];  // zero outside the box interior
+  bf16 x[NPOS * 2];       // [pos][ci]
+  bf16 a2[1024 * 16];     // [pos][c], zero outside the box interior; training reuses it for dL/dz1
   float out[512];
 };
-static_assert(offsetof(FwdS, a1hi) - offsetof(FwdS, a1lo) == NPOSA * 16, "A operand halves");
+
+// dL/dz2 of training as a tensor-core operand: every value as the sum of
+// three BF16 terms (exact for an FP32 value), stored like a1 with the three
+// terms side by side in a row: slot x + 10 half + 20 term + 60 R.
+constexpr int D2_ROWS = 102, D2_SLOTS = 60 * D2_ROWS;
+__device__ __forceinline__ int D2S(int x, int term, int half, int R) { return x + 10 * half + 20 * term + 60 * R; }
 
 
 // ---- tcgen05: 5th-generation tensor cores, accumulator in tensor memory ----
 //
-// Layer 2 is an implicit GEMM D[v][co] = sum over taps t and channels ci of
-// a1[pos(v) + off(t)][ci] W2[co][ci][t].  A 128-row M tile is 16
-// consecutive rows R (R = (y+1) + 10(z+1)) of 8 voxels along x of the
-// padded 10^3 region; rows with y = -1 or 8 (two per z plane) fall inside
-// the tile too and are discarded: 5 tiles (R = 11 + 16j, j = 0..4) cover
-// the 64 rows of the box.  For tap t the tile's A operand is the same view
-// shifted by off(t) positions: K-major, no swizzle, core matrices of 8
-// positions x 8 channels (128 contiguous bytes), rows 160 bytes apart (SBO,
-// one padded row), the second 8 channels in a1hi (LBO).  B (W2 of one tap,
-// 16 x 16) is stored as four 8x8 core matrices: LBO 256 bytes (channels
-// 8-15), SBO 128 bytes (output channels 8-15).  Each tile accumulates its
-// 27 taps (K = 16 each) in 16 columns of tensor memory; the five tiles are
-// issued by five warps and complete one mbarrier phase together.
-constexpr int TC_TILES = 5, TC_COLS = 128;
-constexpr uint32_t TC_IDESC = (1u << 4)             // D: FP32
-                              | (1u << 7)           // A: BF16
-                              | (1u << 10)          // B: BF16
-                              | ((16u >> 3) << 17)  // N = 16
-                              | ((128u >> 4) << 24);  // M = 128; A and B K-major
+// Layer 2 (16 -> 16 channels, 3^3 taps) and both of its gradients are
+// implicit GEMMs on shifted views of the operands above, with no im2col
+// copy.  The shared-memory operands use the no-swizzle canonical layouts: a
+// core matrix is 8 rows of 16 contiguous bytes; K-major rows run along M
+// (or N) and hold 8 K values, MN-major rows run along K and hold 8 M (or N)
+// values; SBO is the byte stride between 8-wide M (N) groups, LBO between
+// 8-deep K groups.
+//
+// forward          D[v][co] = sum_{t,ci} a1[pos(v) + off(t)][ci] W2[co][ci][t].
+//   An M = 128 tile is 16 consecutive rows R of 8 voxels along x; rows with
+//   y = -1 or 8 (two per z plane) fall inside the tile and are discarded:
+//   5 tiles (R = 11 + 16j) cover the 64 rows of the box.  A of tap t: K-major
+//   view of a1 from the tile's first row shifted by off(t), SBO 320 (one
+//   row), LBO 160 (channels 8-15).  B: W2 of the tap as four 8x8 core
+//   matrices (LBO 256: ci 8-15; SBO 128: co 8-15).  27 MMAs (K = 16) per tile
+//   into 16 columns.
+// backward-data    dA1[q][ci] = sum_{t,co} dZ2[q - off(t)][co] W2[co][ci][t]:
+//   the same tiles over dZ2 shifted by -off(t) (SBO 960, LBO 160), one MMA per
+//   BF16 term (start + 320 term); B: W2 transposed (w2t).  81 MMAs per tile.
+// backward-weight  dW2[co][ci][t] = sum_v dZ2[v][co] a1[pos(v) + off(t)][ci]:
+//   voxels are K.  One accumulator per (dy, dz): M = 128 rows (g, c) of an
+//   MN-major view of a1 with SBO 16, so group g starts one position further
+//   along the row: g = 0-2 are channels 0-7 at dx = -1, 0, 1 and g = 10-12
+//   channels 8-15 at dx = -1, 0, 1 (the other ten groups are discarded); K
+//   rows are the 8 voxels of an x row, LBO 320 the next row.  B: MN-major
+//   view of dZ2, N = 48 = (term, half, co) with SBO 160, LBO 960.  32 MMAs
+//   (two x rows each) per box, accumulated over all boxes of the CTA.
+// Tensor memory of training: columns 0-79 the forward and backward-data
+// tiles, 80 + 48c the backward-weight accumulator of c = (dy+1) + 3(dz+1).
+constexpr int TC_TILES = 5, FWD_COLS = 128, TRAIN_COLS = 512, WG_COL0 = 80;
+constexpr uint32_t TC_KIND = (1u << 4)    // D: FP32
+                             | (1u << 7)  // A: BF16
+                             | (1u << 10);  // B: BF16
+constexpr uint32_t TC_IDESC = TC_KIND | ((16u >> 3) << 17) | ((128u >> 4) << 24);  // N 16, M 128, K-major
+constexpr uint32_t TC_IDESC_WG = TC_KIND | (1u << 15) | (1u << 16)               // A and B MN-major
+                                 | ((48u >> 3) << 17) | ((128u >> 4) << 24);      // N 48, M 128
 constexpr long long TC_SPIN = 1ll << 22;  // mbarrier polls before giving up (far beyond a box's work)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -105,11 +131,11 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -138,6 +164,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // 16 consecutive FP32 columns of this thread's tensor-memory lane
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
@@ -154,18 +181,19 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // Tensor-memory and mbarrier state of a CTA that runs layer 2 on tcgen05:
-// warp 0 allocates TC_COLS columns at the start and frees them at the end.
+// warp 0 allocates the columns at the start and frees them at the end.
 struct TcState {
   uint32_t taddr;   // tensor-memory address of the allocation (lane 0, first column)
   uint32_t mbar;    // shared address of the MMA-completion mbarrier
   uint32_t phase;   // parity of the next completion
+  uint32_t ncols;   // allocated columns (a power of two >= 32)
   unsigned *err;    // device error word: bit 0 = an MMA wait ran out
 };
 
-__device__ void tc_begin(TcState &tc, uint64_t *mbar, uint32_t *slot, unsigned *err) {
+__device__ void tc_begin(TcState &tc, uint64_t *mbar, uint32_t *slot, unsigned *err, uint32_t ncols) {
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(TC_COLS)
+                 "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -179,6 +207,7 @@ __device__ void tc_begin(TcState &tc, uint64_t *mbar, uint32_t *slot, unsigned *
   tc.taddr = *slot;
   tc.mbar = smem_u32(mbar);
   tc.phase = 0;
+  tc.ncols = ncols;
   tc.err = err;
 }
 
@@ -187,7 +216,23 @@ __device__ void tc_end(const TcState &tc) {
   __syncthreads();
   tc_fence_after();
   if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.taddr), "r"(TC_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.taddr), "r"(tc.ncols)
+                 : "memory");
+}
+
+// Bounded wait of every thread for the MMAs of the current phase; false
+// (and bit 0 of *tc.err set) when it ran out, after a second bounded wait
+// for the MMAs in flight
+__device__ bool tc_wait_all(TcState &tc) {
+  const bool ok = mbar_wait(tc.mbar, tc.phase);
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0) atomicOr(tc.err, 1u);
+    mbar_wait(tc.mbar, tc.phase);
+    return false;
+  }
+  tc.phase ^= 1;
+  tc_fence_after();
+  return true;
 }
 
 // position of W2[co][ci][t] in NetS::w2
@@ -209,11 +254,14 @@ __device__ void load_net(NetS &N, const float *__restrict__ w) {
   if (threadIdx.x == 0) N.b3 = w[O_B3];
 }
 
+__device__ void zero16(void *p, int bytes) {
+  uint4 *q = reinterpret_cast<uint4 *>(p);
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) q[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 __device__ void zero_acts(FwdS &F) {
-  uint32_t *p = reinterpret_cast<uint32_t *>(F.a1lo);
-  for (int i = threadIdx.x; i < NPOSA * 8; i += blockDim.x) p[i] = 0u;  // a1lo and a1hi
-  uint32_t *q = reinterpret_cast<uint32_t *>(F.a2);
-  for (int i = threadIdx.x; i < NPOS * 8; i += blockDim.x) q[i] = 0u;
+  zero16(F.a1, sizeof(F.a1));
+  zero16(F.a2, sizeof(F.a2));
 }
 
 // Forward pass of one box whose input is already in F.x.  Debug pointers
@@ -235,41 +283,35 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
 #pragma unroll
       for (int co = 0; co < 16; ++co) acc[co] += N.w1[(co * 2) * 27 + tp] * x0 + N.w1[(co * 2 + 1) * 27 + tp] * x1;
     }
+    bf16 *a1v = F.a1 + 8 * A1S((v & 7) + 1, 0, ((v >> 3) & 7) + 1 + 10 * ((v >> 6) + 1));
 #pragma unroll
     for (int co = 0; co < 16; ++co) {
       bf16 a = __float2bfloat16_rn(fmaxf(acc[co], 0.0f));
-      (co < 8 ? F.a1lo : F.a1hi)[p * 8 + (co & 7)] = a;
+      a1v[co < 8 ? co : 80 + (co - 8)] = a;
       if (z1d) {
         z1d[co * 512 + v] = acc[co];
         a1d[co * 512 + v] = bf(a);
       }
     }
   }
-  // the tensor cores read a1 through the async proxy
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  // the tensor cores read a1 (and the weights) through the async proxy
+  async_proxy_fence();
   tc_fence_before();
   __syncthreads();
-  // layer 2: same 3^3 conv 16 -> 16 as an implicit GEMM on tcgen05 (the
-  // tiling is described with TcState); lane 0 of warp j issues the 27 MMAs
-  // of tile j and commits them to the mbarrier (TC_TILES arrivals per box)
+  // layer 2 on tcgen05 (the tiling is described above TC_TILES): lane 0 of
+  // warp j issues the 27 MMAs of tile j and commits them to the mbarrier
   if ((t & 31) == 0 && (t >> 5) < TC_TILES) {
     tc_fence_after();
-    const int j = t >> 5;
-    const uint32_t a0 = smem_u32(F.a1lo), b0 = smem_u32(N.w2);
+    const int j = t >> 5, R0 = 11 + 16 * j;
+    const uint32_t a0 = smem_u32(F.a1), b0 = smem_u32(N.w2);
     for (int tp = 0; tp < 27; ++tp) {
-      const int pos = 1 + 10 * (11 + 16 * j) + Off(tp);
-      tc_mma(tc.taddr + 16 * j, tc_desc(a0 + 16 * pos, NPOSA * 16, 160), tc_desc(b0 + 512 * tp, 256, 128), tp > 0);
+      const int dx = tp % 3 - 1, dy = (tp / 3) % 3 - 1, dz = tp / 9 - 1;
+      tc_mma(tc.taddr + 16 * j, tc_desc(a0 + 16 * A1S(1 + dx, 0, R0 + dy + 10 * dz), 160, 320),
+             tc_desc(b0 + 512 * tp, 256, 128), TC_IDESC, tp > 0);
     }
     tc_commit(tc.mbar);
   }
-  const bool ok = mbar_wait(tc.mbar, tc.phase);
-  if (!__syncthreads_and(ok)) {
-    if (t == 0) atomicOr(tc.err, 1u);
-    mbar_wait(tc.mbar, tc.phase);  // let the MMAs in flight finish before the caller stops
-    return false;
-  }
-  tc.phase ^= 1;
-  tc_fence_after();
+  if (!tc_wait_all(tc)) return false;
   {
     // warps 0-3 read tiles 0-2, warps 4-7 tiles 3-4, each its 32 lanes
     const int warp = t >> 5, lane = t & 31, q = warp & 3;
@@ -328,7 +370,7 @@ __global__ void __launch_bounds__(CT) k_cnn_forward(const bf16 *__restrict__ X, 
   NetS &N = *reinterpret_cast<NetS *>(smraw);
   FwdS &F = *reinterpret_cast<FwdS *>(smraw + ((sizeof(NetS) + 127) & ~(size_t)127));
   TcState tc;
-  tc_begin(tc, &mbar, &tslot, err);
+  tc_begin(tc, &mbar, &tslot, err, FWD_COLS);
   load_net(N, w);
   zero_acts(F);
   __syncthreads();
@@ -344,13 +386,33 @@ __global__ void __launch_bounds__(CT) k_cnn_forward(const bf16 *__restrict__ X, 
 }
 
 // ---- training: forward + backward per box, per-CTA partial gradients ----
-struct BwdS {
-  float g3[512];        // dL/d out
-  float d2[512 * 16];   // dL/dz2 [v][c]
-  float d1[512 * 16];   // dL/dz1 [v][c]
-  float grad[NP];       // this CTA's gradient accumulator
+
+// gradient entries kept in shared memory, in parameter order without W2
+// (whose gradient accumulates in tensor memory)
+constexpr int G_W1 = 0, G_B1 = NW1, G_B2 = G_B1 + 16, G_W3 = G_B2 + 16, G_B3 = G_W3 + NW3, NG = G_B3 + 1;
+__device__ __forceinline__ int g_to_param(int i) { return i < G_B2 ? i : i + NW2; }
+
+struct TrainS {
+  bf16 w2t[27 * 256];     // backward-data B operand: [t][co/8][ci/8][ci%8][co%8]
+  bf16 d2[D2_SLOTS * 8];  // dL/dz2 as three BF16 terms, zero outside the box interior
+  float g3[512];          // dL/d out
+  float grad[NG];
+  float part[CT];         // per-thread sums of dL/dz2 (layer-2 bias)
   float red[CT / 32];
 };
+
+static_assert(offsetof(FwdS, a1) % 16 == 0 && offsetof(TrainS, d2) % 16 == 0 && offsetof(TrainS, w2t) % 16 == 0,
+              "tensor-core operands start on 16-byte boundaries");
+static_assert(((sizeof(NetS) + 127) & ~(size_t)127) + ((sizeof(FwdS) + 127) & ~(size_t)127) + sizeof(TrainS) <=
+                  227 * 1024,
+              "training shared memory");
+static_assert(sizeof(NetS) == 19140 && sizeof(FwdS) == 71456 && sizeof(TrainS) == 120164,
+              "layout the operand ranges were checked against");
+
+// position of W2[co][ci][t] in TrainS::w2t (ci is the N index, co the K index)
+__device__ __forceinline__ int W2Ti(int t, int co, int ci) {
+  return t * 256 + (co >> 3) * 128 + (ci >> 3) * 64 + (ci & 7) * 8 + (co & 7);
+}
 
 __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, const float *__restrict__ target,
                                                   const int *__restrict__ ids, int n, float inv_count,
@@ -359,114 +421,187 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tslot;
-  size_t o1 = (sizeof(NetS) + 127) & ~(size_t)127, o2 = o1 + ((sizeof(FwdS) + 127) & ~(size_t)127);
+  const size_t o1 = (sizeof(NetS) + 127) & ~(size_t)127, o2 = o1 + ((sizeof(FwdS) + 127) & ~(size_t)127);
   NetS &N = *reinterpret_cast<NetS *>(smraw);
   FwdS &F = *reinterpret_cast<FwdS *>(smraw + o1);
-  BwdS &B = *reinterpret_cast<BwdS *>(smraw + o2);
+  TrainS &S = *reinterpret_cast<TrainS *>(smraw + o2);
   const int t = threadIdx.x;
   TcState tc;
-  tc_begin(tc, &mbar, &tslot, err);
+  tc_begin(tc, &mbar, &tslot, err, TRAIN_COLS);
   load_net(N, w);
+  for (int i = t; i < 27 * 256; i += CT) {
+    const int tp = i / 256, co = (i / 16) % 16, ci = i % 16;
+    S.w2t[W2Ti(tp, co, ci)] = __float2bfloat16_rn(w[O_W2 + (co * 16 + ci) * 27 + tp]);
+  }
   zero_acts(F);
-  for (int i = t; i < NP; i += CT) B.grad[i] = 0.0f;
+  zero16(S.d2, sizeof(S.d2));
+  for (int i = t; i < NG; i += CT) S.grad[i] = 0.0f;
   float my_loss = 0.0f;
+  bool wg_acc = false;  // the backward-weight accumulators hold a sum
   __syncthreads();
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    int s = ids[it];
+    const int s = ids[it];
     load_input(F, X + (size_t)s * NPOS * 2);
     if (!forward_box(N, F, tc, nullptr, nullptr, nullptr, nullptr)) break;
     const float *tg = target + (size_t)s * 512;
     for (int v = t; v < 512; v += CT) {
-      float e = F.out[v] - tg[v];
+      const float e = F.out[v] - tg[v];
       my_loss += e * e * inv_count;
-      B.g3[v] = 2.0f * inv_count * e;
+      S.g3[v] = 2.0f * inv_count * e;
     }
     __syncthreads();
     // layer 3 weights and bias
     for (int e = t; e < NW3; e += CT) {
-      int ci = e / 27, tp = e % 27, off = Off(tp);
+      const int ci = e / 27, off = Off(e % 27);
       float acc = 0.0f;
-      for (int v = 0; v < 512; ++v) acc += bf(F.a2[(Pos(v) + off) * 16 + ci]) * B.g3[v];
-      B.grad[O_W3 + e] += acc;
+      for (int v = 0; v < 512; ++v) acc += bf(F.a2[(Pos(v) + off) * 16 + ci]) * S.g3[v];
+      S.grad[G_W3 + e] += acc;
     }
     if (t == 0) {
       float acc = 0.0f;
-      for (int v = 0; v < 512; ++v) acc += B.g3[v];
-      B.grad[O_B3] += acc;
+      for (int v = 0; v < 512; ++v) acc += S.g3[v];
+      S.grad[G_B3] += acc;
     }
-    // dL/dz2[u][c] = relu'(a2[u][c]) * sum_t W3[c][t] g3[u - d_t]
-    for (int e = t; e < 512 * 16; e += CT) {
-      int u = e >> 4, c = e & 15;
-      float acc = 0.0f;
-      if (bf(F.a2[Pos(u) * 16 + c]) > 0.0f) {
-        int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
-        for (int tp = 0; tp < 27; ++tp) {
-          int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
-          if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
-          acc += N.w3[c * 27 + tp] * B.g3[vx + 8 * vy + 64 * vz];
+    // dL/dz2[u][c] = relu'(a2[u][c]) sum_t W3[c][t] g3[u - d_t], as three
+    // BF16 terms h0 + h1 + h2 equal to the FP32 value (each remainder is
+    // exact in FP32 and the last has at most 8 significant bits)
+    {
+      float bsum = 0.0f;  // this thread's channel is t % 16
+      for (int e = t; e < 512 * 16; e += CT) {
+        const int u = e >> 4, c = e & 15;
+        const int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
+        float acc = 0.0f;
+        if (bf(F.a2[Pos(u) * 16 + c]) > 0.0f) {
+          for (int tp = 0; tp < 27; ++tp) {
+            const int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
+            if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
+            acc += N.w3[c * 27 + tp] * S.g3[vx + 8 * vy + 64 * vz];
+          }
+        }
+        bsum += acc;
+        const bf16 h0 = __float2bfloat16_rn(acc);
+        const float r1 = acc - bf(h0);
+        const bf16 h1 = __float2bfloat16_rn(r1);
+        const bf16 h2 = __float2bfloat16_rn(r1 - bf(h1));
+        const int R = (uy + 1) + 10 * (uz + 1), el = c & 7;
+        S.d2[8 * D2S(ux + 1, 0, c >> 3, R) + el] = h0;
+        S.d2[8 * D2S(ux + 1, 1, c >> 3, R) + el] = h1;
+        S.d2[8 * D2S(ux + 1, 2, c >> 3, R) + el] = h2;
+      }
+      S.part[t] = bsum;
+    }
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    // backward-data and backward-weight of layer 2 on tcgen05 (described
+    // above TC_TILES): lane 0 of warp j issues backward-data tile j and the
+    // backward-weight accumulators j and j + 5, then commits
+    if ((t & 31) == 0 && (t >> 5) < TC_TILES) {
+      tc_fence_after();
+      const int j = t >> 5, R0 = 11 + 16 * j;
+      const uint32_t a0 = smem_u32(F.a1), d0 = smem_u32(S.d2), b0 = smem_u32(S.w2t);
+      for (int tp = 0; tp < 27; ++tp) {
+        const int dx = tp % 3 - 1, dy = (tp / 3) % 3 - 1, dz = tp / 9 - 1;
+        const uint64_t bd = tc_desc(b0 + 512 * tp, 256, 128);
+        for (int m = 0; m < 3; ++m)
+          tc_mma(tc.taddr + 16 * j, tc_desc(d0 + 16 * D2S(1 - dx, m, 0, R0 - dy - 10 * dz), 160, 960), bd,
+                 TC_IDESC, tp > 0 || m > 0);
+      }
+      for (int c = j; c < 9; c += TC_TILES) {
+        const int dy = c % 3 - 1, dz = c / 3 - 1;
+        for (int p = 0; p < 32; ++p) {
+          const int R = (2 * (p & 3) + 1) + 10 * ((p >> 2) + 1);  // x rows y = 2 (p % 4), +1 of plane z = p / 4
+          tc_mma(tc.taddr + WG_COL0 + 48 * c, tc_desc(a0 + 16 * A1S(0, 0, R + dy + 10 * dz), 320, 16),
+                 tc_desc(d0 + 16 * D2S(1, 0, 0, R), 960, 160), TC_IDESC_WG, wg_acc || p > 0);
         }
       }
-      B.d2[e] = acc;
+      tc_commit(tc.mbar);
     }
-    __syncthreads();
-    // layer 2 weights: thread (co, ci) accumulates its 27 taps
+    wg_acc = true;
+    if (t < 16) {
+      float acc = 0.0f;
+      for (int i = t; i < CT; i += 16) acc += S.part[i];
+      S.grad[G_B2 + t] += acc;
+    }
+    if (!tc_wait_all(tc)) break;
+    // dL/dz1 = relu'(a1) dA1 on the interior voxels, into the a2 space
     {
-      int co = t >> 4, ci = t & 15;
-      const bf16 *a1c = (ci < 8 ? F.a1lo : F.a1hi) + (ci & 7);  // channel ci, 8 per position
-      for (int tp = 0; tp < 27; ++tp) {
-        int off = Off(tp);
+      float *d1 = reinterpret_cast<float *>(F.a2);
+      const int warp = t >> 5, lane = t & 31, q = warp & 3, r = 32 * q + lane;
+      for (int j = warp < 4 ? 0 : 3; j < (warp < 4 ? 3 : TC_TILES); ++j) {
+        float acc[16];
+        tc_ld16(tc.taddr + ((uint32_t)(32 * q) << 16) + 16 * j, acc);
+        const int R = 11 + 16 * j + (r >> 3), x = r & 7, y = R % 10 - 1, z = R / 10 - 1;
+        if (y < 0 || y > 7 || z < 0 || z > 7) continue;
+        const int v = x + 8 * y + 64 * z;
+        const bf16 *a1v = F.a1 + 8 * A1S(x + 1, 0, R);
+#pragma unroll
+        for (int ci = 0; ci < 16; ++ci) d1[v * 16 + ci] = bf(a1v[ci < 8 ? ci : 80 + (ci - 8)]) > 0.0f ? acc[ci] : 0.0f;
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // layer 1 weights and bias (valid conv on the 10^3 input)
+    {
+      const float *d1 = reinterpret_cast<const float *>(F.a2);
+      for (int e = t; e < NW1; e += CT) {
+        const int co = e / 54, ci = (e / 27) % 2, off = Off(e % 27);
         float acc = 0.0f;
-        for (int v = 0; v < 512; ++v) acc += bf(a1c[(Pos(v) + off) * 8]) * B.d2[v * 16 + co];
-        B.grad[O_W2 + (co * 16 + ci) * 27 + tp] += acc;
+        for (int v = 0; v < 512; ++v) acc += bf(F.x[2 * (Pos(v) + off) + ci]) * d1[v * 16 + co];
+        S.grad[G_W1 + e] += acc;
       }
       if (t < 16) {
         float acc = 0.0f;
-        for (int v = 0; v < 512; ++v) acc += B.d2[v * 16 + t];
-        B.grad[O_B2 + t] += acc;
+        for (int v = 0; v < 512; ++v) acc += d1[v * 16 + t];
+        S.grad[G_B1 + t] += acc;
       }
-    }
-    // dL/dz1[u][ci] = relu'(a1) * sum_t sum_co W2[co][ci][t] d2[u - d_t][co]
-    for (int e = t; e < 512 * 16; e += CT) {
-      int u = e >> 4, ci = e & 15;
-      float acc = 0.0f;
-      if (bf(((ci < 8 ? F.a1lo : F.a1hi) + (ci & 7))[Pos(u) * 8]) > 0.0f) {
-        int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
-        for (int tp = 0; tp < 27; ++tp) {
-          int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
-          if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
-          const float *dv = B.d2 + (vx + 8 * vy + 64 * vz) * 16;
-#pragma unroll
-          for (int co = 0; co < 16; ++co) acc += bf(N.w2[W2i(tp, co, ci)]) * dv[co];
-        }
-      }
-      B.d1[e] = acc;
     }
     __syncthreads();
-    // layer 1 weights and bias (valid conv on the 10^3 input)
-    for (int e = t; e < NW1; e += CT) {
-      int co = e / 54, ci = (e / 27) % 2, tp = e % 27, off = Off(tp);
-      float acc = 0.0f;
-      for (int v = 0; v < 512; ++v) acc += bf(F.x[2 * (Pos(v) + off) + ci]) * B.d1[v * 16 + co];
-      B.grad[O_W1 + e] += acc;
-    }
-    if (t < 16) {
-      float acc = 0.0f;
-      for (int v = 0; v < 512; ++v) acc += B.d1[v * 16 + t];
-      B.grad[O_B1 + t] += acc;
-    }
+    zero16(F.a2, sizeof(F.a2));  // layer 3 of the next box reads zeros outside the interior
     __syncthreads();
   }
+  float *dst = partial + (size_t)blockIdx.x * NP;
+  // W2 gradient: the three terms' columns of the useful rows of each
+  // backward-weight accumulator (lanes 0-23 and 80-103: warps 0, 2, 3)
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  {
+    const int warp = t >> 5, lane = t & 31, q = warp & 3;
+    if (warp < 4 && q != 1) {
+      const int L = 32 * q + lane, g = L >> 3, c8 = L & 7;
+      const bool use = g <= 2 || (g >= 10 && g <= 12);
+      const int ci = g <= 2 ? c8 : 8 + c8, dx = g <= 2 ? g - 1 : g - 11;
+      for (int c = 0; c < 9; ++c) {
+        float sum[16];
+#pragma unroll
+        for (int co = 0; co < 16; ++co) sum[co] = 0.0f;
+        if (wg_acc) {
+          for (int m = 0; m < 3; ++m) {
+            float v[16];
+            tc_ld16(tc.taddr + ((uint32_t)(32 * q) << 16) + WG_COL0 + 48 * c + 16 * m, v);
+#pragma unroll
+            for (int co = 0; co < 16; ++co) sum[co] += v[co];
+          }
+        }
+        if (use) {
+          const int tp = (dx + 1) + 3 * c;
+#pragma unroll
+          for (int co = 0; co < 16; ++co) dst[O_W2 + (co * 16 + ci) * 27 + tp] = sum[co];
+        }
+      }
+    }
+  }
   tc_end(tc);
-  float* dst = partial + (size_t)blockIdx.x * NP;
-  for (int i = t; i < NP; i += CT) dst[i] = B.grad[i];
+  for (int i = t; i < NG; i += CT) dst[g_to_param(i)] = S.grad[i];
   // this CTA's loss
   float v = my_loss;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((t & 31) == 0) B.red[t >> 5] = v;
+  if ((t & 31) == 0) S.red[t >> 5] = v;
   __syncthreads();
   if (t == 0) {
     float s = 0.0f;
-    for (int i = 0; i < CT / 32; ++i) s += B.red[i];
+    for (int i = 0; i < CT / 32; ++i) s += S.red[i];
     loss_partial[blockIdx.x] = s;
   }
 }
@@ -588,7 +723,7 @@ __global__ void k_cnn_apply(const int *__restrict__ boxes, int n, const float *_
 }
 
 size_t fwd_smem() { return ((sizeof(NetS) + 127) & ~(size_t)127) + ((sizeof(FwdS) + 127) & ~(size_t)127); }
-size_t train_smem() { return fwd_smem() + sizeof(BwdS); }
+size_t train_smem() { return fwd_smem() + sizeof(TrainS); }
 
 }  // namespace
 
@@ -823,6 +958,18 @@ extern "C" int sm_cnn_gradient(sm_cnn *c, const float *x_host, const float *t_ho
   return SM_OK;
 }
 
+// explicit (input, target) pairs as the recorded samples
+extern "C" int sm_cnn_load_samples(sm_cnn *c, const float *x_host, const float *t_host, int n) {
+  if (!c || !x_host || !t_host || n < 1 || n > c->max_samples || !c->arena) return SM_EINVAL;
+  std::vector<bf16> xb((size_t)n * NPOS * 2);
+  for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16_rn(x_host[i]);
+  CCK(cudaMemcpyAsync(c->X, xb.data(), 2 * xb.size(), cudaMemcpyHostToDevice, c->stream));
+  CCK(cudaMemcpyAsync(c->target, t_host, 4 * (size_t)512 * n, cudaMemcpyHostToDevice, c->stream));
+  CCK(cudaStreamSynchronize(c->stream));
+  c->n_samples = n;
+  return SM_OK;
+}
+
 // one Adam step with an explicit gradient (host [NP])
 extern "C" int sm_cnn_adam_step(sm_cnn *c, const float *grad_host, float lr) {
   if (!c || !grad_host || !c->arena) return SM_EINVAL;
@@ -878,8 +1025,8 @@ extern "C" int sm_cnn_train(sm_cnn *c, int epochs, int batch, float lr, unsigned
 // the forward kernel (inference), kind 1 a training gradient pass (forward,
 // backward, partial gradients, reduction).  FLOPs per launch from the
 // network's model: 16416 per voxel forward (layers of 1728, 13824 and 864),
-// twice that backward; tensor-core FLOPs: the 135 MMAs of a box (M 128,
-// N 16, K 16, padding rows of the tiles included).
+// twice that backward; tensor-core FLOPs: those of the MMAs issued,
+// discarded tile rows included.
 extern "C" int sm_cnn_kernel_bench(sm_cnn *c, int kind, int n, int reps, double *us_per_launch, double *flops,
                                    double *tensor_flops) {
   if (!c || !c->arena || (kind != 0 && kind != 1) || n < 1 || reps < 1) return SM_EINVAL;
@@ -912,7 +1059,11 @@ extern "C" int sm_cnn_kernel_bench(sm_cnn *c, int kind, int n, int reps, double 
   cudaEventDestroy(b);
   if (st) return st;
   if ((st = check_derr(c))) return st;
-  const double fwd = 16416.0 * 512.0 * n, tc = 135.0 * 2.0 * 128 * 16 * 16 * n;
+  // tensor-core work per box: forward 135 MMAs of 128 x 16 x 16; training
+  // adds backward-data (405 of 128 x 16 x 16) and backward-weight (288 of
+  // 128 x 48 x 16)
+  const double fwd = 16416.0 * 512.0 * n, mma16 = 2.0 * 128 * 16 * 16, mma48 = 2.0 * 128 * 48 * 16;
+  const double tc = kind == 0 ? 135.0 * mma16 * n : (540.0 * mma16 + 288.0 * mma48) * n;
   if (us_per_launch) *us_per_launch = 1e3 * ms / reps;
   if (flops) *flops = kind == 0 ? fwd : 3.0 * fwd;
   if (tensor_flops) *tensor_flops = tc;

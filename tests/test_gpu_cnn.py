@@ -134,6 +134,49 @@ def test_gradient_against_fp64_backprop():
         assert rel(a, b) <= TOL, name
 
 
+def test_gradient_accumulates_over_the_boxes_of_a_block():
+    """A gradient pass runs one block per SM at most, so with more boxes than
+    SMs a block takes several boxes, and the layer-2 weight gradient sums
+    over them in tensor memory.  The mean squared error over 50 copies of
+    the same 6 boxes has the gradient of the 6 boxes alone: compared with
+    the FP64 backpropagation of the 6 boxes at the same bound."""
+    p = params(13)
+    rep = 50
+    net = pkg().Network(6 * rep, 64)
+    net.set_params(p)
+    x = inputs(6, 14)
+    t = np.random.default_rng(15).standard_normal((6, 512)).astype(np.float32) * 0.3
+    out, acts = net.forward(x, acts=True)
+    g, loss = net.gradient(np.tile(x, (rep, 1, 1)), np.tile(t, (rep, 1)))
+    pe = effective(p)
+    ref = np.zeros(cnn.N_PARAMS)
+    for b in range(6):
+        ref += cnn.backward(pe, oracle_x(x[b]), acts[b, 1].reshape(16, 8, 8, 8).astype(np.float64),
+                            acts[b, 3].reshape(16, 8, 8, 8).astype(np.float64),
+                            out[b].reshape(8, 8, 8).astype(np.float64),
+                            t[b].reshape(8, 8, 8).astype(np.float64), 1.0 / (6 * 512))
+    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), cnn.unpack(g.astype(np.float64)),
+                          cnn.unpack(ref)):
+        assert rel(a, b) <= TOL, name
+
+
+def test_samples_loaded_explicitly_train_and_time():
+    """Explicit samples replace the recorded ones: training on them lowers
+    the loss, and the kernel timing runs over them."""
+    n = 256
+    net = pkg().Network(n, n)
+    net.set_params(params(16))
+    rng = np.random.default_rng(17)
+    net.load_samples(inputs(n, 18), (0.3 * rng.standard_normal((n, 512))).astype(np.float32))
+    assert net.stats()["samples"] == n
+    first = net.train(1, 64, 1e-3)
+    last = net.train(20, 64, 1e-3)
+    assert np.isfinite(last) and last < first
+    for kind in (0, 1):
+        us, fl, tf = net.kernel_bench(kind, n, 2)
+        assert us > 0 and fl > 0 and tf > 0
+
+
 def test_adam_against_textbook_update():
     p = params(6)
     net = pkg().Network(64, 64)
