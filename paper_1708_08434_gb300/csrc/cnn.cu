@@ -53,11 +53,11 @@ __device__ __forceinline__ float rbf(float x) { return __bfloat162float(__float2
 
 // weights as one CTA uses them
 struct NetS {
-  float w1[NW1];      // [co][ci][t], BF16 values
+  float w1[NW1];      // [t][co][ci], BF16 values (32 per tap)
   float b1[16];
   bf16 w2[27 * 256];  // per tap four 8x8 core matrices [t][ci/8][co/8][co%8][ci%8] (B operand)
   float b2[16];
-  float w3[NW3];      // [ci][t], BF16 values
+  float w3[NW3];      // [t][ci], BF16 values (16 per tap)
   float b3;
 };
 
@@ -241,8 +241,8 @@ __device__ __forceinline__ int W2i(int t, int co, int ci) {
 }
 
 __device__ void load_net(NetS &N, const float *__restrict__ w) {
-  for (int i = threadIdx.x; i < NW1; i += blockDim.x) N.w1[i] = rbf(w[O_W1 + i]);
-  for (int i = threadIdx.x; i < NW3; i += blockDim.x) N.w3[i] = rbf(w[O_W3 + i]);
+  for (int i = threadIdx.x; i < NW1; i += blockDim.x) N.w1[(i % 27) * 32 + i / 27] = rbf(w[O_W1 + i]);
+  for (int i = threadIdx.x; i < NW3; i += blockDim.x) N.w3[(i % 27) * 16 + i / 27] = rbf(w[O_W3 + i]);
   for (int i = threadIdx.x; i < 27 * 256; i += blockDim.x) {
     int t = i / 256, co = (i / 16) % 16, ci = i % 16;
     N.w2[W2i(t, co, ci)] = __float2bfloat16_rn(w[O_W2 + (co * 16 + ci) * 27 + t]);
@@ -252,6 +252,41 @@ __device__ void load_net(NetS &N, const float *__restrict__ w) {
     N.b2[threadIdx.x] = w[O_B2 + threadIdx.x];
   }
   if (threadIdx.x == 0) N.b3 = w[O_B3];
+}
+
+// 16 BF16 values (32 bytes, 16-byte aligned) as floats
+__device__ __forceinline__ void row16(const bf16 *p, float (&v)[16]) {
+  const uint4 u0 = *reinterpret_cast<const uint4 *>(p), u1 = *reinterpret_cast<const uint4 *>(p + 8);
+  const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[i]));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+// 16 floats (16-byte aligned)
+__device__ __forceinline__ void w16(const float *p, float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 f = reinterpret_cast<const float4 *>(p)[i];
+    v[4 * i] = f.x;
+    v[4 * i + 1] = f.y;
+    v[4 * i + 2] = f.z;
+    v[4 * i + 3] = f.w;
+  }
+}
+
+// sum over the 32 lanes of a warp (butterfly: every lane gets the total)
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 __device__ void zero16(void *p, int bytes) {
@@ -271,26 +306,39 @@ __device__ void zero_acts(FwdS &F) {
 __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, float *a1d, float *z2d,
                             float *a2d) {
   const int t = threadIdx.x;
-  // layer 1: valid 3^3 conv 2 -> 16 on CUDA cores
-  for (int r = 0; r < 2; ++r) {
-    int v = t + r * CT, p = Pos(v);
-    float acc[16];
+  // layer 1: valid 3^3 conv 2 -> 16 on CUDA cores, voxels t and t + CT per
+  // thread (the 32 weights of a tap are broadcast 16-byte loads)
+  {
+    const int p0 = Pos(t), p1 = Pos(t + CT);
+    float acc[2][16];
 #pragma unroll
-    for (int co = 0; co < 16; ++co) acc[co] = N.b1[co];
+    for (int co = 0; co < 16; ++co) acc[0][co] = acc[1][co] = N.b1[co];
     for (int tp = 0; tp < 27; ++tp) {
-      int q = p + Off(tp);
-      float x0 = bf(F.x[2 * q]), x1 = bf(F.x[2 * q + 1]);
+      const int off = Off(tp);
+      const float2 xa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (p0 + off)));
+      const float2 xb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (p1 + off)));
+      const float4 *wt = reinterpret_cast<const float4 *>(N.w1 + 32 * tp);
 #pragma unroll
-      for (int co = 0; co < 16; ++co) acc[co] += N.w1[(co * 2) * 27 + tp] * x0 + N.w1[(co * 2 + 1) * 27 + tp] * x1;
+      for (int k = 0; k < 8; ++k) {
+        const float4 wv = wt[k];  // W1[2k][0], W1[2k][1], W1[2k+1][0], W1[2k+1][1]
+        acc[0][2 * k] += wv.x * xa.x + wv.y * xa.y;
+        acc[0][2 * k + 1] += wv.z * xa.x + wv.w * xa.y;
+        acc[1][2 * k] += wv.x * xb.x + wv.y * xb.y;
+        acc[1][2 * k + 1] += wv.z * xb.x + wv.w * xb.y;
+      }
     }
-    bf16 *a1v = F.a1 + 8 * A1S((v & 7) + 1, 0, ((v >> 3) & 7) + 1 + 10 * ((v >> 6) + 1));
 #pragma unroll
-    for (int co = 0; co < 16; ++co) {
-      bf16 a = __float2bfloat16_rn(fmaxf(acc[co], 0.0f));
-      a1v[co < 8 ? co : 80 + (co - 8)] = a;
-      if (z1d) {
-        z1d[co * 512 + v] = acc[co];
-        a1d[co * 512 + v] = bf(a);
+    for (int r = 0; r < 2; ++r) {
+      const int v = t + r * CT;
+      bf16 *a1v = F.a1 + 8 * A1S((v & 7) + 1, 0, ((v >> 3) & 7) + 1 + 10 * ((v >> 6) + 1));
+#pragma unroll
+      for (int co = 0; co < 16; ++co) {
+        bf16 a = __float2bfloat16_rn(fmaxf(acc[r][co], 0.0f));
+        a1v[co < 8 ? co : 80 + (co - 8)] = a;
+        if (z1d) {
+          z1d[co * 512 + v] = acc[r][co];
+          a1d[co * 512 + v] = bf(a);
+        }
       }
     }
   }
@@ -338,16 +386,25 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
   }
   tc_fence_before();
   __syncthreads();
-  // layer 3: same 3^3 conv 16 -> 1 on CUDA cores
-  for (int r = 0; r < 2; ++r) {
-    int v = t + r * CT, p = Pos(v);
-    float acc = N.b3;
+  // layer 3: same 3^3 conv 16 -> 1 on CUDA cores, voxels t and t + CT per
+  // thread (a2 rows and the 16 weights of a tap as 16-byte loads)
+  {
+    const int p0 = Pos(t), p1 = Pos(t + CT);
+    float o0 = N.b3, o1 = N.b3;
     for (int tp = 0; tp < 27; ++tp) {
-      const bf16 *row = F.a2 + (p + Off(tp)) * 16;
+      const int off = Off(tp);
+      float a[16], b[16], wv[16];
+      row16(F.a2 + (p0 + off) * 16, a);
+      row16(F.a2 + (p1 + off) * 16, b);
+      w16(N.w3 + 16 * tp, wv);
 #pragma unroll
-      for (int ci = 0; ci < 16; ++ci) acc += N.w3[ci * 27 + tp] * bf(row[ci]);
+      for (int ci = 0; ci < 16; ++ci) {
+        o0 += wv[ci] * a[ci];
+        o1 += wv[ci] * b[ci];
+      }
     }
-    F.out[v] = acc;
+    F.out[t] = o0;
+    F.out[t + CT] = o1;
   }
   __syncthreads();
   return true;
@@ -425,7 +482,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
   NetS &N = *reinterpret_cast<NetS *>(smraw);
   FwdS &F = *reinterpret_cast<FwdS *>(smraw + o1);
   TrainS &S = *reinterpret_cast<TrainS *>(smraw + o2);
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   TcState tc;
   tc_begin(tc, &mbar, &tslot, err, TRAIN_COLS);
   load_net(N, w);
@@ -450,45 +507,89 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
       S.g3[v] = 2.0f * inv_count * e;
     }
     __syncthreads();
-    // layer 3 weights and bias
-    for (int e = t; e < NW3; e += CT) {
-      const int ci = e / 27, off = Off(e % 27);
-      float acc = 0.0f;
-      for (int v = 0; v < 512; ++v) acc += bf(F.a2[(Pos(v) + off) * 16 + ci]) * S.g3[v];
-      S.grad[G_W3 + e] += acc;
-    }
-    if (t == 0) {
-      float acc = 0.0f;
-      for (int v = 0; v < 512; ++v) acc += S.g3[v];
-      S.grad[G_B3] += acc;
-    }
-    // dL/dz2[u][c] = relu'(a2[u][c]) sum_t W3[c][t] g3[u - d_t], as three
-    // BF16 terms h0 + h1 + h2 equal to the FP32 value (each remainder is
-    // exact in FP32 and the last has at most 8 significant bits)
-    {
-      float bsum = 0.0f;  // this thread's channel is t % 16
-      for (int e = t; e < 512 * 16; e += CT) {
-        const int u = e >> 4, c = e & 15;
-        const int ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
-        float acc = 0.0f;
-        if (bf(F.a2[Pos(u) * 16 + c]) > 0.0f) {
-          for (int tp = 0; tp < 27; ++tp) {
-            const int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
-            if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
-            acc += N.w3[c * 27 + tp] * S.g3[vx + 8 * vy + 64 * vz];
-          }
-        }
-        bsum += acc;
-        const bf16 h0 = __float2bfloat16_rn(acc);
-        const float r1 = acc - bf(h0);
-        const bf16 h1 = __float2bfloat16_rn(r1);
-        const bf16 h2 = __float2bfloat16_rn(r1 - bf(h1));
-        const int R = (uy + 1) + 10 * (uz + 1), el = c & 7;
-        S.d2[8 * D2S(ux + 1, 0, c >> 3, R) + el] = h0;
-        S.d2[8 * D2S(ux + 1, 1, c >> 3, R) + el] = h1;
-        S.d2[8 * D2S(ux + 1, 2, c >> 3, R) + el] = h2;
+    // layer 3 weights: warp w takes taps w, w + 8, ...; lane l the voxels
+    // l + 32k, whose sums the warp then adds (fixed order); bias: warp 7
+    for (int tp = warp; tp < 27; tp += CT / 32) {
+      const int off = Off(tp);
+      float acc[16];
+#pragma unroll
+      for (int ci = 0; ci < 16; ++ci) acc[ci] = 0.0f;
+      for (int v = lane; v < 512; v += 32) {
+        float a[16];
+        row16(F.a2 + (Pos(v) + off) * 16, a);
+        const float g = S.g3[v];
+#pragma unroll
+        for (int ci = 0; ci < 16; ++ci) acc[ci] += a[ci] * g;
       }
-      S.part[t] = bsum;
+#pragma unroll
+      for (int ci = 0; ci < 16; ++ci) acc[ci] = warp_sum(acc[ci]);
+      if (lane == 0)
+#pragma unroll
+        for (int ci = 0; ci < 16; ++ci) S.grad[G_W3 + ci * 27 + tp] += acc[ci];
+    }
+    if (warp == CT / 32 - 1) {
+      float acc = 0.0f;
+      for (int v = lane; v < 512; v += 32) acc += S.g3[v];
+      acc = warp_sum(acc);
+      if (lane == 0) S.grad[G_B3] += acc;
+    }
+    // dL/dz2[u][c] = relu'(a2[u][c]) sum_t W3[c][t] g3[u - d_t] for voxels
+    // t and t + CT, stored as three BF16 terms h0 + h1 + h2 equal to the
+    // FP32 value (each remainder is exact in FP32 and the last has at most 8
+    // significant bits)
+    {
+      float bsum[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) bsum[c] = 0.0f;
+#pragma unroll 1
+      for (int r = 0; r < 2; ++r) {
+        const int u = t + r * CT, ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
+        for (int tp = 0; tp < 27; ++tp) {
+          const int vx = ux - (tp % 3 - 1), vy = uy - ((tp / 3) % 3 - 1), vz = uz - (tp / 9 - 1);
+          if (vx < 0 || vx > 7 || vy < 0 || vy > 7 || vz < 0 || vz > 7) continue;
+          const float g = S.g3[vx + 8 * vy + 64 * vz];
+          float wv[16];
+          w16(N.w3 + 16 * tp, wv);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] += wv[c] * g;
+        }
+        float a2v[16];
+        row16(F.a2 + Pos(u) * 16, a2v);
+        const int R = (uy + 1) + 10 * (uz + 1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t t0[4], t1[4], t2[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            bf16 hv[3][2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int c = 8 * h + 2 * k + e;
+              const float d = a2v[c] > 0.0f ? acc[c] : 0.0f;
+              bsum[c] += d;
+              hv[0][e] = __float2bfloat16_rn(d);
+              const float r1 = d - bf(hv[0][e]);
+              hv[1][e] = __float2bfloat16_rn(r1);
+              hv[2][e] = __float2bfloat16_rn(r1 - bf(hv[1][e]));
+            }
+            t0[k] = pack2(hv[0][0], hv[0][1]);
+            t1[k] = pack2(hv[1][0], hv[1][1]);
+            t2[k] = pack2(hv[2][0], hv[2][1]);
+          }
+          *reinterpret_cast<uint4 *>(S.d2 + 8 * D2S(ux + 1, 0, h, R)) = make_uint4(t0[0], t0[1], t0[2], t0[3]);
+          *reinterpret_cast<uint4 *>(S.d2 + 8 * D2S(ux + 1, 1, h, R)) = make_uint4(t1[0], t1[1], t1[2], t1[3]);
+          *reinterpret_cast<uint4 *>(S.d2 + 8 * D2S(ux + 1, 2, h, R)) = make_uint4(t2[0], t2[1], t2[2], t2[3]);
+        }
+      }
+      // layer-2 bias: per warp, then the warps in order (below)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) bsum[c] = warp_sum(bsum[c]);
+      if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S.part[16 * warp + c] = bsum[c];
     }
     async_proxy_fence();
     tc_fence_before();
@@ -520,14 +621,14 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     wg_acc = true;
     if (t < 16) {
       float acc = 0.0f;
-      for (int i = t; i < CT; i += 16) acc += S.part[i];
+      for (int i = 0; i < CT / 32; ++i) acc += S.part[16 * i + t];
       S.grad[G_B2 + t] += acc;
     }
     if (!tc_wait_all(tc)) break;
     // dL/dz1 = relu'(a1) dA1 on the interior voxels, into the a2 space
     {
       float *d1 = reinterpret_cast<float *>(F.a2);
-      const int warp = t >> 5, lane = t & 31, q = warp & 3, r = 32 * q + lane;
+      const int q = warp & 3, r = 32 * q + lane;
       for (int j = warp < 4 ? 0 : 3; j < (warp < 4 ? 3 : TC_TILES); ++j) {
         float acc[16];
         tc_ld16(tc.taddr + ((uint32_t)(32 * q) << 16) + 16 * j, acc);
@@ -541,18 +642,43 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     }
     tc_fence_before();
     __syncthreads();
-    // layer 1 weights and bias (valid conv on the 10^3 input)
+    // layer 1 weights (valid conv on the 10^3 input): warp w takes taps
+    // w, w + 8, ...; lane l the voxels l + 32k, whose sums the warp adds
     {
       const float *d1 = reinterpret_cast<const float *>(F.a2);
-      for (int e = t; e < NW1; e += CT) {
-        const int co = e / 54, ci = (e / 27) % 2, off = Off(e % 27);
-        float acc = 0.0f;
-        for (int v = 0; v < 512; ++v) acc += bf(F.x[2 * (Pos(v) + off) + ci]) * d1[v * 16 + co];
-        S.grad[G_W1 + e] += acc;
+      for (int tp = warp; tp < 27; tp += CT / 32) {
+        const int off = Off(tp);
+        float acc[32];  // [co][ci]
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+        for (int v = lane; v < 512; v += 32) {
+          const float2 xv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (Pos(v) + off)));
+          float dv[16];
+          w16(d1 + 16 * v, dv);
+#pragma unroll
+          for (int co = 0; co < 16; ++co) {
+            acc[2 * co] += xv.x * dv[co];
+            acc[2 * co + 1] += xv.y * dv[co];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = warp_sum(acc[i]);
+        if (lane == 0)
+#pragma unroll
+          for (int i = 0; i < 32; ++i) S.grad[G_W1 + i * 27 + tp] += acc[i];
       }
+      // layer-1 bias: thread t sums channel t % 16 over 32 voxels, then the
+      // 16 partial sums of a channel in order
+      {
+        const int c = t & 15, v0 = 32 * (t >> 4);
+        float acc = 0.0f;
+        for (int v = v0; v < v0 + 32; ++v) acc += d1[16 * v + c];
+        S.part[t] = acc;
+      }
+      __syncthreads();
       if (t < 16) {
         float acc = 0.0f;
-        for (int v = 0; v < 512; ++v) acc += d1[v * 16 + t];
+        for (int i = 0; i < 16; ++i) acc += S.part[16 * i + t];
         S.grad[G_B1 + t] += acc;
       }
     }
@@ -567,7 +693,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
   __syncthreads();
   tc_fence_after();
   {
-    const int warp = t >> 5, lane = t & 31, q = warp & 3;
+    const int q = warp & 3;
     if (warp < 4 && q != 1) {
       const int L = 32 * q + lane, g = L >> 3, c8 = L & 7;
       const bool use = g <= 2 || (g >= 10 && g <= 12);
