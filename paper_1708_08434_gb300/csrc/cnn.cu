@@ -68,11 +68,15 @@ struct NetS {
 // past the region take the reads of the discarded rows of the last tile.
 constexpr int A1_ROWS = 102, A1_SLOTS = 20 * A1_ROWS;
 __device__ __forceinline__ int A1S(int x, int half, int R) { return x + 10 * half + 20 * R; }
+// slot of voxel v (channels 0-7), and the slot offset of tap t
+__device__ __forceinline__ int VS(int v) { return A1S((v & 7) + 1, 0, ((v >> 3) & 7) + 1 + 10 * ((v >> 6) + 1)); }
+__device__ __forceinline__ int SOff(int t) { return (t % 3 - 1) + 20 * ((t / 3) % 3 - 1) + 200 * (t / 9 - 1); }
 
 struct FwdS {
   bf16 a1[A1_SLOTS * 8];  // zero outside the box interior
   bf16 x[NPOS * 2];       // [pos][ci]
-  bf16 a2[1024 * 16];     // [pos][c], zero outside the box interior; training reuses it for dL/dz1
+  bf16 a2[1024 * 16];     // a1's layout (100 rows), zero outside the box interior; training
+                          // reuses the space for dL/dz1 ([16][512] FP32)
   float out[512];
 };
 
@@ -254,9 +258,9 @@ __device__ void load_net(NetS &N, const float *__restrict__ w) {
   if (threadIdx.x == 0) N.b3 = w[O_B3];
 }
 
-// 16 BF16 values (32 bytes, 16-byte aligned) as floats
-__device__ __forceinline__ void row16(const bf16 *p, float (&v)[16]) {
-  const uint4 u0 = *reinterpret_cast<const uint4 *>(p), u1 = *reinterpret_cast<const uint4 *>(p + 8);
+// the 16 channels at slot s of an array in a1's layout, as floats
+__device__ __forceinline__ void row16(const bf16 *a, int s, float (&v)[16]) {
+  const uint4 u0 = *reinterpret_cast<const uint4 *>(a + 8 * s), u1 = *reinterpret_cast<const uint4 *>(a + 8 * (s + 10));
   const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -370,11 +374,12 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
       const int R = 11 + 16 * j + (r >> 3), x = r & 7, y = R % 10 - 1, z = R / 10 - 1;
       if (y < 0 || y > 7 || z < 0 || z > 7) continue;  // a padding row of the tile
       const int v = x + 8 * y + 64 * z;
+      uint32_t pk[8];
 #pragma unroll
       for (int co = 0; co < 16; co += 2) {
         float z0 = acc[co] + N.b2[co], z1 = acc[co + 1] + N.b2[co + 1];
         __nv_bfloat162 a2 = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
-        *reinterpret_cast<__nv_bfloat162 *>(F.a2 + Pos(v) * 16 + co) = a2;
+        pk[co >> 1] = *reinterpret_cast<const uint32_t *>(&a2);
         if (z2d) {
           z2d[co * 512 + v] = z0;
           z2d[(co + 1) * 512 + v] = z1;
@@ -382,6 +387,9 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
           a2d[(co + 1) * 512 + v] = __high2float(a2);
         }
       }
+      const int s = A1S(x + 1, 0, R);
+      *reinterpret_cast<uint4 *>(F.a2 + 8 * s) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4 *>(F.a2 + 8 * (s + 10)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
   }
   tc_fence_before();
@@ -389,13 +397,13 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
   // layer 3: same 3^3 conv 16 -> 1 on CUDA cores, voxels t and t + CT per
   // thread (a2 rows and the 16 weights of a tap as 16-byte loads)
   {
-    const int p0 = Pos(t), p1 = Pos(t + CT);
+    const int s0 = VS(t), s1 = VS(t + CT);
     float o0 = N.b3, o1 = N.b3;
     for (int tp = 0; tp < 27; ++tp) {
-      const int off = Off(tp);
+      const int so = SOff(tp);
       float a[16], b[16], wv[16];
-      row16(F.a2 + (p0 + off) * 16, a);
-      row16(F.a2 + (p1 + off) * 16, b);
+      row16(F.a2, s0 + so, a);
+      row16(F.a2, s1 + so, b);
       w16(N.w3 + 16 * tp, wv);
 #pragma unroll
       for (int ci = 0; ci < 16; ++ci) {
@@ -510,13 +518,13 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     // layer 3 weights: warp w takes taps w, w + 8, ...; lane l the voxels
     // l + 32k, whose sums the warp then adds (fixed order); bias: warp 7
     for (int tp = warp; tp < 27; tp += CT / 32) {
-      const int off = Off(tp);
+      const int so = SOff(tp);
       float acc[16];
 #pragma unroll
       for (int ci = 0; ci < 16; ++ci) acc[ci] = 0.0f;
       for (int v = lane; v < 512; v += 32) {
         float a[16];
-        row16(F.a2 + (Pos(v) + off) * 16, a);
+        row16(F.a2, VS(v) + so, a);
         const float g = S.g3[v];
 #pragma unroll
         for (int ci = 0; ci < 16; ++ci) acc[ci] += a[ci] * g;
@@ -557,7 +565,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
           for (int c = 0; c < 16; ++c) acc[c] += wv[c] * g;
         }
         float a2v[16];
-        row16(F.a2 + Pos(u) * 16, a2v);
+        row16(F.a2, VS(u), a2v);
         const int R = (uy + 1) + 10 * (uz + 1);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -626,6 +634,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     }
     if (!tc_wait_all(tc)) break;
     // dL/dz1 = relu'(a1) dA1 on the interior voxels, into the a2 space
+    // ([channel][voxel]: the lanes of a warp touch consecutive words)
     {
       float *d1 = reinterpret_cast<float *>(F.a2);
       const int q = warp & 3, r = 32 * q + lane;
@@ -637,7 +646,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
         const int v = x + 8 * y + 64 * z;
         const bf16 *a1v = F.a1 + 8 * A1S(x + 1, 0, R);
 #pragma unroll
-        for (int ci = 0; ci < 16; ++ci) d1[v * 16 + ci] = bf(a1v[ci < 8 ? ci : 80 + (ci - 8)]) > 0.0f ? acc[ci] : 0.0f;
+        for (int ci = 0; ci < 16; ++ci) d1[ci * 512 + v] = bf(a1v[ci < 8 ? ci : 80 + (ci - 8)]) > 0.0f ? acc[ci] : 0.0f;
       }
     }
     tc_fence_before();
@@ -654,7 +663,8 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
         for (int v = lane; v < 512; v += 32) {
           const float2 xv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (Pos(v) + off)));
           float dv[16];
-          w16(d1 + 16 * v, dv);
+#pragma unroll
+          for (int co = 0; co < 16; ++co) dv[co] = d1[co * 512 + v];
 #pragma unroll
           for (int co = 0; co < 16; ++co) {
             acc[2 * co] += xv.x * dv[co];
@@ -667,18 +677,18 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
 #pragma unroll
           for (int i = 0; i < 32; ++i) S.grad[G_W1 + i * 27 + tp] += acc[i];
       }
-      // layer-1 bias: thread t sums channel t % 16 over 32 voxels, then the
-      // 16 partial sums of a channel in order
+      // layer-1 bias: thread t sums channel t / 16 over the voxels t % 16 +
+      // 16i, then the 16 partial sums of a channel in order
       {
-        const int c = t & 15, v0 = 32 * (t >> 4);
+        const int c = t >> 4, g = t & 15;
         float acc = 0.0f;
-        for (int v = v0; v < v0 + 32; ++v) acc += d1[16 * v + c];
+        for (int v = g; v < 512; v += 16) acc += d1[c * 512 + v];
         S.part[t] = acc;
       }
       __syncthreads();
       if (t < 16) {
         float acc = 0.0f;
-        for (int i = 0; i < 16; ++i) acc += S.part[16 * i + t];
+        for (int g = 0; g < 16; ++g) acc += S.part[16 * t + g];
         S.grad[G_B1 + t] += acc;
       }
     }
