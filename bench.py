@@ -612,10 +612,10 @@ def run_gpu(args):
         sus = per_call(lambda: g.fluid_stage(dt))
         fluid = {"fp64_peak": f64}
         # FP64 instructions per leaf cell as counted by ncu on this workload
-        # (32 x smsp__inst_executed_pipe_fp64 / leaf cells: k_field 19.4 with
-        # the FP64 square root of |E|, stage-1 k_update 82.0); bytes:
+        # (32 x smsp__inst_executed_pipe_fp64 / leaf cells: k_field 17.4 with
+        # the FP64 square root of |E|, stage-1 k_update 64.0); bytes:
         # compulsory traffic
-        for name, us, bpc, ipc in (("field (k_field)", fus, 16.0, 19.4), ("euler stage (k_update)", sus, 72.0, 82.0)):
+        for name, us, bpc, ipc in (("field (k_field)", fus, 16.0, 17.4), ("euler stage (k_update)", sus, 72.0, 64.0)):
             fluid[name] = {"us": round(us, 2), "gbs": round(leaf_cells * bpc / (us * 1e-6) / 1e9, 1),
                            "hbm_frac": round(leaf_cells * bpc / (us * 1e-6) / 1e9 / peak, 4),
                            "fp64_ginstr": round(leaf_cells * ipc / (us * 1e-6) / 1e9, 1),

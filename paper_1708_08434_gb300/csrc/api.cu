@@ -90,7 +90,7 @@ static Layout plan(int cap, bool mixed) {
   L.gh = p.take<double>((size_t)cap * 6 * FACE);
   L.cflux = p.take<double>((size_t)cap * 6 * FACE);
   L.basis = p.take<double>(3 * 64 + 3 * 8);
-  L.tab = p.take<double>(3 * 4096);
+  L.tab = p.take<double>(6 * 4096);  // mu, D, alpha and their slopes t[i+1] - t[i]
   L.dscal = p.take<unsigned long long>(SC_N);
   L.phx = p.take<long long>(nc);
   L.gx = p.take<long long>(nc);
@@ -156,7 +156,7 @@ extern "C" int sm_create(sm_ctx **out, const sm_config *cfg, const sm_domain *do
     ctx->lh.h2[l] = h * h;
     ctx->lh.inv_h2[l] = 1.0 / (h * h);
   }
-  if (cudaMallocHost((void **)&ctx->hscal, sizeof(double) * SC_N) != cudaSuccess) {
+  if (cudaMallocHost((void **)&ctx->hscal, sizeof(double) * 2 * SC_N) != cudaSuccess) {  // + staged copy
     delete ctx;
     return SM_ECUDA;
   }
@@ -553,9 +553,16 @@ extern "C" int sm_set_table(sm_ctx *ctx, int n, double e_max, const double *mu, 
                             const double *alpha) {
   if (!ctx || !mu || !diff || !alpha || n < 2 || n > 4096 || !(e_max > 0.0)) return SM_EINVAL;
   if (!ctx->arena) return sm_fail(ctx, SM_ESTATE, "no arena bound");
-  SM_CK(cudaMemcpyAsync(ctx->tab, mu, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ctx->tab + 4096, diff, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ctx->tab + 8192, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  // each table and its slopes t[i+1] - t[i] (the FP64 differences that
+  // linear interpolation forms, computed once here)
+  std::vector<double> all(6 * 4096, 0.0);
+  const double *src[3] = {mu, diff, alpha};
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < n; ++i) {
+      all[4096 * k + i] = src[k][i];
+      all[4096 * (3 + k) + i] = i + 1 < n ? src[k][i + 1] - src[k][i] : 0.0;
+    }
+  SM_CK(cudaMemcpyAsync(ctx->tab, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice, ctx->stream));
   // the host arrays may be released right after the call
   SM_CK(cudaStreamSynchronize(ctx->stream));
   ctx->tab_n = n;

@@ -51,9 +51,10 @@ __device__ __forceinline__ void split_frac(double x, int &i, double &w) {
 
 // Linear interpolation in two tables sampled at E_k = k e_max/(n-1) at
 // x = e (n-1)/e_max (given), clamped at both ends (Sec. 2.3): the index and
-// weight come from the bits of x; the interpolation a0 + w (a1 - a0) is
-// FP64.
-__device__ __forceinline__ void lookup2x(const double *__restrict__ ta, const double *__restrict__ tb, int n,
+// weight come from the bits of x; the interpolation a0 + w (a1 - a0) is one
+// FP64 FMA each, with the slope a1 - a0 stored beside the table (sa, sb).
+__device__ __forceinline__ void lookup2x(const double *__restrict__ ta, const double *__restrict__ sa,
+                                         const double *__restrict__ tb, const double *__restrict__ sb, int n,
                                          long long xmax, double x, double &va, double &vb) {
   const long long bx = dbits(x);
   if (bx <= 0) {  // x <= 0 (or -0)
@@ -69,22 +70,18 @@ __device__ __forceinline__ void lookup2x(const double *__restrict__ ta, const do
   int i;
   double w;
   split_frac(x, i, w);
-  double a0 = __ldg(ta + i), a1 = __ldg(ta + i + 1), b0 = __ldg(tb + i), b1 = __ldg(tb + i + 1);
-  va = a0 + w * (a1 - a0);
-  vb = b0 + w * (b1 - b0);
-}
-
-__device__ __forceinline__ void lookup2(const double *__restrict__ ta, const double *__restrict__ tb,
-                                        const Table &T, double e, double &va, double &vb) {
-  lookup2x(ta, tb, T.n, T.xmax, e * T.inv_de, va, vb);
+  va = fma(w, __ldg(sa + i), __ldg(ta + i));
+  vb = fma(w, __ldg(sb + i), __ldg(tb + i));
 }
 
 // psi(a/b) b for the Koren limiter psi(x) = max(0, min(1, (2+x)/6, x)),
-// without the division: 0 when a b <= 0 (the sign of the product, tested on
-// its bits), else sign(b) min(|b|, (2|b| + |a|)/6, |a|) with the minimum
-// taken on the bit patterns
+// without the division: 0 when a b <= 0 (a or b is +-0, or their signs
+// differ: tested on the bits, with no product), else
+// sign(b) min(|b|, (2|b| + |a|)/6, |a|) with the minimum taken on the bit
+// patterns
 __device__ __forceinline__ double koren(double a, double b) {
-  if (dbits(a * b) <= 0) return 0.0;
+  const long long ba = dbits(a), bb = dbits(b);
+  if ((ba ^ bb) < 0 || (ba << 1) == 0 || (bb << 1) == 0) return 0.0;
   const double ab = dabs(b), aa = dabs(a);
   long long m = dbits(ab);
   m = min(m, dbits(fma(2.0, ab, aa) * (1.0 / 6.0)));
@@ -92,21 +89,30 @@ __device__ __forceinline__ double koren(double a, double b) {
   return __longlong_as_double(m | (dbits(b) & (long long)0x8000000000000000ull));
 }
 
-// Flux through the face between cells L and R (positive toward R):
-// v = -mu(E*) E_face with E_face = (p_L - p_R)/dx, E* = (|E|_L + |E|_R)/2;
-// advective part by Eq. 7 when v >= 0 and Eq. 6 when v < 0; diffusive part
-// -D(E*) (n_R - n_L)/dx.  Written as (-mu dp n_f - D dn)/dx: v < 0 exactly
-// when mu dp > 0.
-__device__ __forceinline__ double face_flux(double nL2, double nL, double nR, double nR2, double pL, double pR,
-                                            double eL, double eR, double inv_h, const Table &tb) {
+// dx times the flux through the face between cells L and R (positive
+// toward R): v = -mu(E*) E_face with E_face = (p_L - p_R)/dx,
+// E* = (|E|_L + |E|_R)/2 at table index x; advective part by Eq. 7 when
+// v >= 0 and Eq. 6 when v < 0; diffusive part -D(E*) (n_R - n_L)/dx.
+// Written as -mu dp n_f - D dn: v < 0 exactly when mu dp > 0.
+__device__ __forceinline__ double face_flux_h(double nL2, double nL, double nR, double nR2, double pL, double pR,
+                                              double x, const Table &tb) {
   double mu, dc;
-  lookup2x(tb.mu, tb.diff, tb.n, tb.xmax, (eL + eR) * tb.hinv_de, mu, dc);
+  lookup2x(tb.mu, tb.dmu, tb.diff, tb.ddiff, tb.n, tb.xmax, x, mu, dc);
   const double t1 = mu * (pL - pR);
   const double dn = nR - nL;
   const bool up = dbits(t1) > 0;  // v < 0: the upwind cell is R
-  const double k = koren(up ? nR2 - nR : nL - nL2, dn);
-  const double nf = up ? nR - k : nL + k;
-  return fma(-t1, nf, -dc * dn) * inv_h;
+  // the operands are selected first, so each path costs one FP64 operation
+  const double k = koren((up ? nR2 : nL) - (up ? nR : nL2), dn);
+  const double nf = (up ? nR : nL) + __longlong_as_double(dbits(k) ^ (up ? (long long)0x8000000000000000ull : 0ll));
+  return fma(-t1, nf, -dc * dn);
+}
+
+// 2 x, exactly, on the integer pipe, for 0 <= x < 2^1023 (not NaN):
+// doubling adds one to the exponent field of a normal value and shifts the
+// bits of a subnormal one (a carry into the exponent field is the result)
+__device__ __forceinline__ double twice(double x) {
+  const long long b = dbits(x);
+  return __longlong_as_double((b >> 52) ? b + (1ll << 52) : b << 1);
 }
 
 // Density ghost (depth t = 1 or 2) across refinement face f of fine box b
@@ -193,18 +199,18 @@ __global__ void __launch_bounds__(512) k_field(const int32_t *__restrict__ leaf,
   double ih = lh.inv_h[level[b]];
   const double *p = phi + (size_t)b * CELLS;
   double pc = p[t];
-  double e2 = 0.0;
-  const double hh = 0.5 * ih;
   const int stride[3] = {1, NC, FACE};
+  double d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double pm = c[a] > 0 ? p[t - stride[a]] : pot_ghost(phi, nbr6, gh, b, 2 * a, c[0], c[1], c[2], pc, bc, 0);
     double pp = c[a] < NC - 1 ? p[t + stride[a]]
                               : pot_ghost(phi, nbr6, gh, b, 2 * a + 1, c[0], c[1], c[2], pc, bc, 0);
-    const double e = (pm - pp) * hh;  // mean of (pm - pc)/dx and (pc - pp)/dx
-    e2 = fma(e, e, e2);
+    d[a] = pm - pp;
   }
-  emag[(size_t)b * CELLS + t] = sqrt(e2);
+  // |E| = |(p_-d - p_+d)| / (2 dx) summed in quadrature: each component is
+  // the mean of (p_-d - p_c)/dx and (p_c - p_+d)/dx
+  emag[(size_t)b * CELLS + t] = sqrt(fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]))) * (0.5 * ih);
 }
 
 // Eq. 5 right-hand side on leaf cells
@@ -215,29 +221,52 @@ __global__ void __launch_bounds__(512) k_charge(const int32_t *__restrict__ leaf
   rhs[x] = use_rho ? -rho[x] * inv_eps : -q * (ni[x] - ne[x]) * inv_eps;
 }
 
-// per-cell time-step quantities: sum_d mu |E_d|/dx, plus 2*3*D/dx^2, mu n_e
+// per-cell time-step quantities at table index x of the cell's |E|:
+// sum_d mu |E_d|/dx with E_d = (p_{-d} - p_{+d})/(2 dx) (the mean of the two
+// face fields), that plus 6 D/dx^2, and mu n_e
 __device__ __forceinline__ void dt_terms(const double *__restrict__ phi, const double *__restrict__ gh,
-                                         const int32_t *__restrict__ nbr6, const Bc &bc, int b, int t, double ih,
-                                         double em, double ne, const Table &tb, double &adv, double &ad,
+                                         const int32_t *__restrict__ nbr6, const Bc &bc, int b, int t, double ih2,
+                                         double x, double ne, const Table &tb, double &adv, double &ad,
                                          double &drt) {
   int c[3] = {t & 7, (t >> 3) & 7, t >> 6};
   const double *p = phi + (size_t)b * CELLS;
   double pc = p[t];
   const int stride[3] = {1, NC, FACE};
   double mu, dc;
-  lookup2(tb.mu, tb.diff, tb, em, mu, dc);
-  double s = 0.0;
-  const double hh = 0.5 * ih;
+  lookup2x(tb.mu, tb.dmu, tb.diff, tb.ddiff, tb.n, tb.xmax, x, mu, dc);
+  double d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double pm = c[a] > 0 ? p[t - stride[a]] : pot_ghost(phi, nbr6, gh, b, 2 * a, c[0], c[1], c[2], pc, bc, 0);
     double pp = c[a] < NC - 1 ? p[t + stride[a]]
                               : pot_ghost(phi, nbr6, gh, b, 2 * a + 1, c[0], c[1], c[2], pc, bc, 0);
-    s += dabs(mu * ((pm - pp) * hh));  // the cell component: mean of the two face fields
+    d[a] = dabs(pm - pp);
   }
-  adv = s * ih;
-  ad = adv + 6.0 * dc * ih * ih;
+  adv = (mu * ((d[0] + d[1]) + d[2])) * (0.5 * ih2);
+  ad = fma(6.0 * ih2, dc, adv);
   drt = mu * ne;
+}
+
+// block maxima of three non-negative quantities (negative values count as
+// 0) into slots[0..2], compared as bit patterns on the integer pipe; red:
+// 3 * (blockDim.x / 32) words of shared memory
+__device__ __forceinline__ void block_max3_to(unsigned long long *slots, double a, double b, double c,
+                                              long long *red) {
+  long long v[3] = {max(dbits(a), 0ll), max(dbits(b), 0ll), max(dbits(c), 0ll)};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = max(v[i], __shfl_xor_sync(0xffffffffu, v[i], o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) red[3 * wid + i] = v[i];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[3 * w + threadIdx.x]);
+    atomicMax(slots + threadIdx.x, (unsigned long long)m);
+  }
 }
 
 __global__ void __launch_bounds__(512) k_dt(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
@@ -245,17 +274,13 @@ __global__ void __launch_bounds__(512) k_dt(const int32_t *__restrict__ leaf, co
                                             const double *__restrict__ emag, const double *__restrict__ ne,
                                             const int32_t *__restrict__ nbr6, Bc bc, LevelH lh, Table tb,
                                             unsigned long long *slots) {
-  __shared__ double red[16];
+  __shared__ long long red[48];
   int b = leaf[blockIdx.x];
   int t = threadIdx.x;
   size_t x = (size_t)b * CELLS + t;
   double adv, ad, drt;
-  dt_terms(phi, gh, nbr6, bc, b, t, lh.inv_h[level[b]], emag[x], ne[x], tb, adv, ad, drt);
-  block_max_to(slots + SC_ADV, adv, red);
-  __syncthreads();
-  block_max_to(slots + SC_AD, ad, red);
-  __syncthreads();
-  block_max_to(slots + SC_DRT, drt, red);
+  dt_terms(phi, gh, nbr6, bc, b, t, lh.inv_h2[level[b]], emag[x] * tb.inv_de, ne[x], tb, adv, ad, drt);
+  block_max3_to(slots + SC_ADV, adv, ad, drt, red);
 }
 
 // Fine-side fluxes through the refinement faces of leaf boxes (64 threads
@@ -285,10 +310,11 @@ __global__ void __launch_bounds__(64) k_cf_flux(const int32_t *__restrict__ leaf
     double pg = p0 * (1.0 / 3.0) + (2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + fcell(a, c0[0], c0[1], c0[2])];
     double e0 = emag[base + cidx(c0[0], c0[1], c0[2])];
     double eg = emag_cf_ghost(emag, nbr6, parent, ijk, b, f, u, w);
+    const double x = (e0 + eg) * tb.hinv_de;
     double F;
-    if (f & 1) F = face_flux(n1, n0, g1, g2, p0, pg, e0, eg, ih, tb);
-    else F = face_flux(g2, g1, n0, n1, pg, p0, eg, e0, ih, tb);
-    cflux[(size_t)(6 * b + f) * FACE + u + NC * w] = F;
+    if (f & 1) F = face_flux_h(n1, n0, g1, g2, p0, pg, x, tb);
+    else F = face_flux_h(g2, g1, n0, n1, pg, p0, x, tb);
+    cflux[(size_t)(6 * b + f) * FACE + u + NC * w] = F * ih;
   }
 }
 
@@ -296,18 +322,29 @@ __global__ void __launch_bounds__(64) k_cf_flux(const int32_t *__restrict__ leaf
 struct UpdSmem {
   double n[12 * 12 * 12];   // density with 2 ghost layers on faces
   double p[10 * 10 * 10];   // potential with 1 ghost layer
-  double e[10 * 10 * 10];   // |E| with 1 ghost layer
-  double F[3 * 9 * 64];     // face fluxes [a][m][w][u]
-  double red[16];
+  double x[10 * 10 * 10];   // half table index |E| (n-1)/(2 e_max), 1 ghost layer
+  double F[3 * 9 * 64];     // face fluxes times dx [a][m][w][u]
+  long long red[48];
 };
 __device__ __forceinline__ int I12(int i, int j, int k) { return (i + 2) + 12 * ((j + 2) + 12 * (k + 2)); }
 __device__ __forceinline__ int I10(int i, int j, int k) { return (i + 1) + 10 * ((j + 1) + 10 * (k + 1)); }
+
+// index in a staged box of pitch P (O ghost layers) of the cell with
+// coordinate ca along axis a and u, w along axes (a+1)%3, (a+2)%3 (no
+// arrays indexed at run time: those would live in local memory)
+template <int P, int O>
+__device__ __forceinline__ int lin_axis(int a, int ca, int u, int w) {
+  const int x = a == 0 ? ca : (a == 1 ? w : u);
+  const int y = a == 0 ? u : (a == 1 ? ca : w);
+  const int z = a == 0 ? w : (a == 1 ? u : ca);
+  return (x + O) + P * ((y + O) + P * (z + O));
+}
 
 // One forward-Euler stage on a leaf box: dst = src + dt F(src), with
 // F = -div(flux) + alpha mu |E| n_e for electrons and the same source for
 // ions.  heun != 0: dst = (n0 + src + dt F(src))/2.  Also writes the Eq. 5
 // right-hand side from dst, and with want_dt the time-step maxima of src.
-__global__ void __launch_bounds__(512) k_update(
+__global__ void __launch_bounds__(512, 3) k_update(
     const int32_t *__restrict__ leaf, const int32_t *__restrict__ level, const double *__restrict__ ne_src,
     const double *__restrict__ ni_src, const double *__restrict__ ne0, const double *__restrict__ ni0,
     double *__restrict__ ne_dst, double *__restrict__ ni_dst, const double *__restrict__ phi,
@@ -320,72 +357,67 @@ __global__ void __launch_bounds__(512) k_update(
   int b = leaf[blockIdx.x];
   int t = threadIdx.x;
   int l = level[b];
-  double ih = lh.inv_h[l];
+  const double h = lh.h[l], ih2 = lh.inv_h2[l];
   size_t base = (size_t)b * CELLS;
   int ci = t & 7, cj = (t >> 3) & 7, ck = t >> 6;
+  const double e = emag[base + t];
+  const double xh = e * tb.hinv_de;  // the cell's table index is 2 xh, exactly e (n-1)/e_max
   S.n[I12(ci, cj, ck)] = ne_src[base + t];
   S.p[I10(ci, cj, ck)] = phi[base + t];
-  S.e[I10(ci, cj, ck)] = emag[base + t];
+  S.x[I10(ci, cj, ck)] = xh;
   __syncthreads();
   // face halos: thread -> (face, face cell)
   if (t < 6 * FACE) {
-    int f = t >> 6, fc = t & 63;
-    int u = fc & 7, w = fc >> 3;
-    int nb = nbr6[6 * b + f];
-    int c0[3], c1[3], g1[3], g2[3];
-    face_loc(f, 0, u, w, c0);
-    face_loc(f, 1, u, w, c1);
-    face_loc(f, -1, u, w, g1);
-    face_loc(f, -2, u, w, g2);
-    double n0 = S.n[I12(c0[0], c0[1], c0[2])], n1 = S.n[I12(c1[0], c1[1], c1[2])];
-    double p0 = S.p[I10(c0[0], c0[1], c0[2])], e0 = S.e[I10(c0[0], c0[1], c0[2])];
-    double vg1, vg2, pg, eg;
+    const int f = t >> 6, fc = t & 63;
+    const int u = fc & 7, w = fc >> 3, a = f >> 1, hi = f & 1;
+    const int nb = nbr6[6 * b + f];
+    // depths 0, 1 inside the face and the ghosts -1, -2 along axis a
+    const int d0 = hi ? NC - 1 : 0, d1 = hi ? NC - 2 : 1, dg1 = hi ? NC : -1, dg2 = hi ? NC + 1 : -2;
+    const int r0 = lin_axis<10, 1>(a, d0, u, w);
+    double n0 = S.n[lin_axis<12, 2>(a, d0, u, w)], n1 = S.n[lin_axis<12, 2>(a, d1, u, w)];
+    double p0 = S.p[r0], x0 = S.x[r0];
+    double vg1, vg2, pg, xg;
     if (nb >= 0) {
-      int m0[3], m1[3];
-      face_loc(f ^ 1, 0, u, w, m0);
-      face_loc(f ^ 1, 1, u, w, m1);
+      // the neighbour's cells at depths 0 and 1 of its opposite face
+      const int m0 = lin_axis<8, 0>(a, hi ? 0 : NC - 1, u, w), m1 = lin_axis<8, 0>(a, hi ? 1 : NC - 2, u, w);
       size_t nbase = (size_t)nb * CELLS;
-      vg1 = ne_src[nbase + cidx(m0[0], m0[1], m0[2])];
-      vg2 = ne_src[nbase + cidx(m1[0], m1[1], m1[2])];
-      pg = phi[nbase + cidx(m0[0], m0[1], m0[2])];
-      eg = child[8 * nb] < 0 ? emag[nbase + cidx(m0[0], m0[1], m0[2])] : 0.0;
+      vg1 = ne_src[nbase + m0];
+      vg2 = ne_src[nbase + m1];
+      pg = phi[nbase + m0];
+      xg = child[8 * nb] < 0 ? emag[nbase + m0] * tb.hinv_de : 0.0;
     } else if (nb == -1) {
       vg1 = n0;
       vg2 = n1;
       pg = bc.type[f] ? 2.0 * bc.val[f] - p0 : p0;
-      eg = e0;
+      xg = x0;
     } else {
       vg1 = density_cf_ghost(ne_src, nbr6, parent, ijk, b, f, 1, u, w, slots + SC_ERR);
       vg2 = density_cf_ghost(ne_src, nbr6, parent, ijk, b, f, 2, u, w, slots + SC_ERR);
-      pg = p0 * (1.0 / 3.0) + (2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + fcell(f >> 1, c0[0], c0[1], c0[2])];
-      eg = emag_cf_ghost(emag, nbr6, parent, ijk, b, f, u, w);
+      pg = p0 * (1.0 / 3.0) + (2.0 / 3.0) * gh[(size_t)(6 * b + f) * FACE + u + NC * w];
+      xg = emag_cf_ghost(emag, nbr6, parent, ijk, b, f, u, w) * tb.hinv_de;
     }
-    S.n[I12(g1[0], g1[1], g1[2])] = vg1;
-    S.n[I12(g2[0], g2[1], g2[2])] = vg2;
-    S.p[I10(g1[0], g1[1], g1[2])] = pg;
-    S.e[I10(g1[0], g1[1], g1[2])] = eg;
+    S.n[lin_axis<12, 2>(a, dg1, u, w)] = vg1;
+    S.n[lin_axis<12, 2>(a, dg2, u, w)] = vg2;
+    const int rg = lin_axis<10, 1>(a, dg1, u, w);
+    S.p[rg] = pg;
+    S.x[rg] = xg;
   }
   __syncthreads();
   // fluxes: 3 axes x 9 faces x 64
   for (int x = t; x < 3 * 9 * FACE; x += blockDim.x) {
     int a = x / (9 * FACE), rem = x % (9 * FACE);
     int m = rem >> 6, u = rem & 7, w = (rem >> 3) & 7;
-    int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
     double F;
     bool done = false;
     if (m == 0 || m == NC) {
       int f = 2 * a + (m == NC);
       int nb = nbr6[6 * b + f];
       if (nb == -2) {
-        F = cflux[(size_t)(6 * b + f) * FACE + u + NC * w];
+        F = cflux[(size_t)(6 * b + f) * FACE + u + NC * w] * h;
         done = true;
       } else if (nb >= 0 && child[8 * nb] >= 0) {
         // coarse side of a refinement face: mean of the 4 fine fluxes
-        int cidx3[3];
-        cidx3[a] = (f & 1) ? 0 : 1;
-        cidx3[t1] = u >> 2;
-        cidx3[t2] = w >> 2;
-        int ch = child[8 * nb + cidx3[0] + 2 * cidx3[1] + 4 * cidx3[2]];
+        int ch = child[8 * nb + lin_axis<2, 0>(a, (f & 1) ? 0 : 1, u >> 2, w >> 2)];
         const double *cf = cflux + (size_t)(6 * ch + (f ^ 1)) * FACE;
         int uf = 2 * (u & 3), wf = 2 * (w & 3);
         double s = 0.0;
@@ -393,40 +425,32 @@ __global__ void __launch_bounds__(512) k_update(
         s += cf[uf + 1 + NC * wf];
         s += cf[uf + NC * (wf + 1)];
         s += cf[uf + 1 + NC * (wf + 1)];
-        F = s * 0.25;
+        F = (s * 0.25) * h;
         done = true;
       }
     }
     if (!done) {
-      int c[4][3];
-      for (int s = 0; s < 4; ++s) {
-        c[s][a] = m - 2 + s;
-        c[s][t1] = u;
-        c[s][t2] = w;
-      }
-      F = face_flux(S.n[I12(c[0][0], c[0][1], c[0][2])], S.n[I12(c[1][0], c[1][1], c[1][2])],
-                    S.n[I12(c[2][0], c[2][1], c[2][2])], S.n[I12(c[3][0], c[3][1], c[3][2])],
-                    S.p[I10(c[1][0], c[1][1], c[1][2])], S.p[I10(c[2][0], c[2][1], c[2][2])],
-                    S.e[I10(c[1][0], c[1][1], c[1][2])], S.e[I10(c[2][0], c[2][1], c[2][2])], ih, tb);
+      // cells m-2 .. m+1 along axis a
+      const int q = lin_axis<12, 2>(a, m - 2, u, w), sq = a == 0 ? 1 : (a == 1 ? 12 : 144);
+      const int r = lin_axis<10, 1>(a, m - 1, u, w), sr = a == 0 ? 1 : (a == 1 ? 10 : 100);
+      F = face_flux_h(S.n[q], S.n[q + sq], S.n[q + 2 * sq], S.n[q + 3 * sq], S.p[r], S.p[r + sr],
+                      S.x[r] + S.x[r + sr], tb);
     }
     S.F[(a * 9 + m) * FACE + u + NC * w] = F;
   }
   __syncthreads();
-  // update
-  int c[3] = {ci, cj, ck};
-  double div = 0.0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int u = c[(a + 1) % 3], w = c[(a + 2) % 3], m = c[a];
-    div += (S.F[(a * 9 + m + 1) * FACE + u + NC * w] - S.F[(a * 9 + m) * FACE + u + NC * w]) * ih;
-  }
-  double e = S.e[I10(ci, cj, ck)];
+  // update: div = sum over axes of the flux differences (times dx) / dx^2
+  const double *Fx = S.F + (0 * 9 + ci) * FACE + cj + NC * ck;
+  const double *Fy = S.F + (1 * 9 + cj) * FACE + ck + NC * ci;
+  const double *Fz = S.F + (2 * 9 + ck) * FACE + ci + NC * cj;
+  const double div = ((Fx[FACE] - Fx[0]) + (Fy[FACE] - Fy[0]) + (Fz[FACE] - Fz[0])) * ih2;
   double nes = S.n[I12(ci, cj, ck)];
+  const double x = twice(xh);  // e (n-1)/e_max
   double alpha, mu;
-  lookup2(tb.alpha, tb.mu, tb, e, alpha, mu);
+  lookup2x(tb.alpha, tb.dalpha, tb.mu, tb.dmu, tb.n, tb.xmax, x, alpha, mu);
   double src = alpha * mu * e * nes;
-  double ne_new = nes - dt * div + dt * src;
-  double ni_new = ni_src[base + t] + dt * src;
+  double ne_new = fma(dt, src - div, nes);
+  double ni_new = fma(dt, src, ni_src[base + t]);
   if (heun) {
     ne_new = 0.5 * (ne0[base + t] + ne_new);
     ni_new = 0.5 * (ni0[base + t] + ni_new);
@@ -436,12 +460,8 @@ __global__ void __launch_bounds__(512) k_update(
   rhs[base + t] = (ni_new - ne_new) * (-q * inv_eps);
   if (want_dt) {
     double adv, ad, drt;
-    dt_terms(phi, gh, nbr6, bc, b, t, ih, e, nes, tb, adv, ad, drt);
-    block_max_to(slots + SC_ADV, adv, S.red);
-    __syncthreads();
-    block_max_to(slots + SC_AD, ad, S.red);
-    __syncthreads();
-    block_max_to(slots + SC_DRT, drt, S.red);
+    dt_terms(phi, gh, nbr6, bc, b, t, ih2, x, nes, tb, adv, ad, drt);
+    block_max3_to(slots + SC_ADV, adv, ad, drt, S.red);
   }
 }
 
@@ -453,6 +473,9 @@ static Table table_of(const sm_ctx *ctx) {
   tb.mu = ctx->tab;
   tb.diff = ctx->tab + 4096;
   tb.alpha = ctx->tab + 8192;
+  tb.dmu = ctx->tab + 3 * 4096;
+  tb.ddiff = ctx->tab + 4 * 4096;
+  tb.dalpha = ctx->tab + 5 * 4096;
   tb.n = ctx->tab_n;
   tb.inv_de = (ctx->tab_n - 1) / ctx->tab_emax;
   tb.hinv_de = 0.5 * tb.inv_de;
@@ -496,19 +519,24 @@ extern "C" int sm_restrict_densities(sm_ctx *ctx) {
   return sm_restrict_pair(ctx, ctx->nbuf[ctx->ncur], ctx->ibuf[ctx->ncur]);
 }
 
-static int dt_from_slots(sm_ctx *ctx, double q, double eps, double *dt) {
-  SM_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
-  SM_CK(cudaStreamSynchronize(ctx->stream));
+// dt from time-step maxima already copied to host scalars hs (SC_N words)
+static int dt_of(sm_ctx *ctx, const double *hs, double q, double eps, double *dt) {
   unsigned long long e;
-  memcpy(&e, &ctx->hscal[SC_ERR], sizeof e);
+  memcpy(&e, &hs[SC_ERR], sizeof e);
   if (e) return sm_fail(ctx, SM_ESTATE, "device consistency check failed (flags 0x%llx)", e);
-  double m_adv = ctx->hscal[SC_ADV], m_ad = ctx->hscal[SC_AD], m_drt = ctx->hscal[SC_DRT];
+  double m_adv = hs[SC_ADV], m_ad = hs[SC_AD], m_drt = hs[SC_DRT];
   double d = 1e300;
   if (m_adv > 0.0 && 0.5 / m_adv < d) d = 0.5 / m_adv;
   if (m_ad > 0.0 && 1.0 / m_ad < d) d = 1.0 / m_ad;
   if (m_drt > 0.0 && eps / (q * m_drt) < d) d = eps / (q * m_drt);
   *dt = 0.9 * d;
   return SM_OK;
+}
+
+static int dt_from_slots(sm_ctx *ctx, double q, double eps, double *dt) {
+  SM_CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  return dt_of(ctx, ctx->hscal, q, eps, dt);
 }
 
 extern "C" int sm_dt_limit(sm_ctx *ctx, double q, double eps, double *dt) {
@@ -582,13 +610,18 @@ extern "C" int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, do
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_ADV, 0, 3 * sizeof(unsigned long long), ctx->stream));
   if ((st = stage(ctx, B, C, A, dt, q, eps, 1))) return st;
   ctx->ncur = C;
-  double dtn = 0.0;
-  if ((st = dt_from_slots(ctx, q, eps, &dtn))) return st;
+  // the maxima go to the staged host copy without a wait: the solve below
+  // synchronises before they are read
+  double *staged = ctx->hscal + SC_N;
+  SM_CK(cudaMemcpyAsync(staged, ctx->dscal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
   if (ctx->pre_solve && (st = ctx->pre_solve(ctx->hook_obj, ctx))) return st;
   st2 = sm_mg_solve(ctx, tol, max_cycles, &c2, nullptr);
   if (st2 && st2 != SM_ENOCONV) return st2;
   if (ctx->post_solve && (st = ctx->post_solve(ctx->hook_obj, ctx))) return st;
   if ((st = sm_compute_field(ctx))) return st;
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  double dtn = 0.0;
+  if ((st = dt_of(ctx, staged, q, eps, &dtn))) return st;
   if (dt_next) *dt_next = dtn;
   if (cycles) {
     cycles[0] = c1;

@@ -54,6 +54,7 @@ struct LevelH {
 // transport-coefficient lookup table (device arrays)
 struct Table {
   const double *mu, *diff, *alpha;
+  const double *dmu, *ddiff, *dalpha;  // slopes t[i+1] - t[i]
   int n;
   double inv_de;    // (n-1)/e_max
   double hinv_de;   // (n-1)/(2 e_max): the index of the face value (e_L + e_R)/2 from e_L + e_R
@@ -123,7 +124,7 @@ struct sm_ctx {
   int n_boxes = 0, n_levels = 0, n_leaves = 0;
   int level_off[SM_MAX_LEVELS + 1] = {0};
   int leaf_level_off[SM_MAX_LEVELS + 1] = {0};
-  double *hscal = nullptr;   // pinned host scalars
+  double *hscal = nullptr;   // pinned host scalars [SC_N], then a staged copy [SC_N]
   bool basis_ready = false;
   double den = 0.0;          // residual norm of phi == 0 (current rhs)
 
