@@ -594,25 +594,51 @@ __global__ void k_fx_scale(Bc bc, unsigned long long *sc) {
 }
 
 // phx = phi and gx = -h^2 f / 6 in quanta, for every box (CELLS / GT pairs
-// per thread)
-__global__ void __launch_bounds__(GT) k_fx_init(const int32_t *__restrict__ level, const double *__restrict__ phi,
+// per thread); with den, on leaf boxes also max |f - L 0| into *den, the
+// residual of the zero potential that relative residuals divide by: its
+// ghosts are 2g at Dirichlet walls and 0 everywhere else (same-level and
+// refinement faces, Neumann walls), so L 0 is the sum of the wall
+// constants of the cell's Dirichlet faces (added in face order) / h^2
+__global__ void __launch_bounds__(GT) k_fx_init(const int32_t *__restrict__ level, const int32_t *__restrict__ child,
+                                                const int32_t *__restrict__ nbr6, const double *__restrict__ phi,
                                                 const double *__restrict__ rhs, long long *__restrict__ phx,
-                                                long long *__restrict__ gx, FxLev fl, unsigned long long *sc) {
+                                                long long *__restrict__ gx, FxLev fl, Bc bc, LevelH lh,
+                                                unsigned long long *sc, unsigned long long *den) {
+  __shared__ double red[GT / 32];
   const int b = blockIdx.x;
   const int l = __ldg(level + b);
+  const bool leaf = den && __ldg(child + 8 * b) < 0;
+  int wall = 0;  // bit f: face f is a Dirichlet wall
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    if (bc.type[f] && __ldg(nbr6 + 6 * b + f) == -1) wall |= 1 << f;
   pdl_wait();
   const int E = fx_E(sc);
-  const double mh6 = fl.mh6[l];
+  const double mh6 = fl.mh6[l], ih2 = lh.inv_h2[l];
   bool bad = false;
+  double m = 0.0;
   const size_t base = (size_t)b * CELLS;
 #pragma unroll
   for (int h = 0; h < CPT; ++h) {
     const int c = threadIdx.x + h * GT;
     const size_t x = base + c, y = base + xsplit(c);
+    const double f = rhs[x];
     phx[y] = fx_of(phi[x], E, bad);
-    gx[y] = fx_of(rhs[x] * mh6, E, bad);
+    gx[y] = fx_of(f * mh6, E, bad);
+    if (leaf) {
+      const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+      double sum = 0.0;
+      if ((wall & 1) && i == 0) sum += bc.g2[0];
+      if ((wall & 2) && i == NC - 1) sum += bc.g2[1];
+      if ((wall & 4) && j == 0) sum += bc.g2[2];
+      if ((wall & 8) && j == NC - 1) sum += bc.g2[3];
+      if ((wall & 16) && k == 0) sum += bc.g2[4];
+      if ((wall & 32) && k == NC - 1) sum += bc.g2[5];
+      m = fmax(m, fabs(fma(-sum, ih2, f)));
+    }
   }
   fx_flag(bad, sc);
+  if (leaf) group_max_to(block_grp(), den, m, red);
 }
 
 // phi = phx q for every box, unless the solve left the fixed-point range

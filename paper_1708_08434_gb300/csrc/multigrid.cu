@@ -1529,15 +1529,17 @@ static int fx_fill_cf(sm_ctx *ctx) {
 }
 
 // scale of the solve (from phi, every h^2 f and 2g), the potential and G
-// of every box in quanta, and (ghat) the refinement-face sums
+// of every box in quanta with the residual norm of the zero potential in
+// SC_DEN, and (ghat) the refinement-face sums
 static int fx_prologue(sm_ctx *ctx, bool ghat) {
   const fx::FxLev fl = fx_levels(ctx);
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_FXI, 0, sizeof(unsigned long long), ctx->stream));
+  SM_CK(cudaMemsetAsync(ctx->dscal + SC_DEN, 0, sizeof(unsigned long long), ctx->stream));
   const int grid = ctx->n_boxes < 608 ? 2 * ctx->n_boxes : 1216;
   sm_launch(ctx, fx::k_fx_expo, grid, 256, 0, ctx->n_boxes, ctx->level, ctx->phi, ctx->rhs, fl, ctx->dscal);
   sm_launch(ctx, fx::k_fx_scale, 1, 1, 0, ctx->bc, ctx->dscal);
-  sm_launch(ctx, fx::k_fx_init, ctx->n_boxes, GT, 0, ctx->level, ctx->phi, ctx->rhs, ctx->phx, ctx->gx, fl,
-            ctx->dscal);
+  sm_launch(ctx, fx::k_fx_init, ctx->n_boxes, GT, 0, ctx->level, ctx->child, ctx->nbr6, ctx->phi, ctx->rhs,
+            ctx->phx, ctx->gx, fl, ctx->bc, ctx->lh, ctx->dscal, ctx->dscal + SC_DEN);
   SM_CKL("fixed-point prologue");
   return ghat ? fx_fill_cf(ctx) : SM_OK;
 }
@@ -1644,15 +1646,12 @@ static int fx_fmg_ladder(sm_ctx *ctx, int norm_slot) {
   return SM_OK;
 }
 
-// Work of an FP64 solve before its cycle loop: the residual of phi = 0
-// (denominator, in FP64 with old as the zero field), the restricted rhs of
-// FMG, the fixed-point scale and arrays; FMG then runs its ladder (leaving
-// the residual of its result in SC_NORM) unless the persistent kernel will.
+// Work of an FP64 solve before its cycle loop: the restricted rhs of FMG,
+// the fixed-point scale and arrays with the residual norm of phi = 0 (the
+// denominator); FMG then runs its ladder (leaving the residual of its
+// result in SC_NORM) unless the persistent kernel will.
 static int fx_solve_prefix(sm_ctx *ctx, int fmg, bool ladder) {
   int st;
-  SM_CK(cudaMemsetAsync(ctx->old, 0, sizeof(double) * CELLS * (size_t)ctx->n_boxes, ctx->stream));
-  if ((st = sm_fill_all_cf(ctx, ctx->old))) return st;
-  if ((st = leaf_norm(ctx, ctx->old, SC_DEN))) return st;
   SM_CK(cudaMemsetAsync(ctx->dscal + SC_CYC, 0, sizeof(unsigned long long), ctx->stream));
   if (fmg && (st = restrict_chain<double>(ctx, ctx->rhs, nullptr))) return st;
   if ((st = fx_prologue(ctx, !fmg))) return st;
