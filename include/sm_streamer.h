@@ -288,6 +288,23 @@ int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
 int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, long long *launches,
                     double *bytes_per_launch, double *fp64_per_launch);
 
+/* Per-solve metrics log (no paper passage): with a path, every
+ * sm_mg_solve and sm_mg_fmg (also those inside sm_advance_fluid) appends one
+ * JSON line to that file (opened for appending; path NULL or "" closes it):
+ *   seq, call ("fmg" | "solve"), precision ("fp64" | "mixed"), path
+ *   ("graph" | "host" | "persistent"), boxes, levels, leaf_cells, tol,
+ *   status (the call's return code), cycles, rel (final relative residual),
+ *   residual_history (relative residual after each cycle, the first 64;
+ *   an FMG ladder is cycle 1; empty for the persistent kernel), ms (CUDA
+ *   events around the call, retries of a widened fixed-point scale
+ *   included), vcycle_bytes (the per-level algorithmic model of
+ *   sm_kernel_bench class 2, FP32 arrays for the mixed form's cycles being
+ *   counted as FP64), bytes (vcycle_bytes x cycles), gbs (bytes / ms),
+ *   hbm_frac (gbs / hbm_peak_gbs, null when hbm_peak_gbs <= 0).
+ * Logging synchronises the stream after each solve (the solves do anyway).
+ * Errors: SM_EINVAL (file cannot be opened), SM_ECUDA. */
+int sm_set_metrics_log(sm_ctx *ctx, const char *path, double hbm_peak_gbs);
+
 /* Solves run as CUDA graphs (captured on first use per octree, with the
  * cycle loop and its stopping test on the device) when enabled (default),
  * or as individually launched kernels with a host loop when disabled.

@@ -68,7 +68,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_batch_set_graphs", "sm_batch_kernel_bench", "sm_cnn_create", "sm_cnn_destroy", "sm_cnn_arena_size",
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
-           "sm_cnn_kernel_bench", "sm_cnn_load_samples",
+           "sm_cnn_kernel_bench", "sm_cnn_load_samples", "sm_set_metrics_log",
            "sm_cnn_last_error",
            "sm_batch_last_error",
            "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
@@ -152,6 +152,7 @@ def load():
         "sm_cnn_stats": [P, pI, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), pD],
         "sm_cnn_kernel_bench": [P, I, I, I, pD, pD, pD],
         "sm_cnn_load_samples": [P, P, P, I],
+        "sm_set_metrics_log": [P, C.c_char_p, D],
         "sm_cnn_last_error": [P],
         "sm_last_error": [P],
         "sm_quad_create": [C.POINTER(P), P, I, I, I, P],
@@ -453,6 +454,11 @@ class Solver:
         self._ck(self._lib.sm_kernel_bench(self._h, kclass, reps, C.byref(us), C.byref(n), C.byref(by),
                                            C.byref(fl)))
         return us.value, n.value, by.value, fl.value
+
+    def set_metrics_log(self, path, hbm_peak_gbs: float = 0.0):
+        """Append one JSON line per solve (cycles, residual history, time,
+        algorithmic bytes, bandwidth) to `path`; None closes the log."""
+        self._ck(self._lib.sm_set_metrics_log(self._h, path.encode() if path else None, float(hbm_peak_gbs)))
 
     def set_persistent(self, enable: bool):
         """V-cycles as one persistent cooperative launch, or as per-level

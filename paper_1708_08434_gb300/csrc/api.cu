@@ -59,7 +59,7 @@ struct ArenaPlan {
 // layout shared by sm_arena_size and sm_bind_arena
 struct Layout {
   size_t level, ijk, parent, child, nbr, nbr6, leaf, morton, scan_a, scan_b, count, flags;
-  size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, e32, f32, old32, gh32,
+  size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, hist, e32, f32, old32, gh32,
       phx, gx, ghx, total;
 };
 
@@ -92,6 +92,7 @@ static Layout plan(int cap, bool mixed) {
   L.basis = p.take<double>(3 * 64 + 3 * 8);
   L.tab = p.take<double>(6 * 4096);  // mu, D, alpha and their slopes t[i+1] - t[i]
   L.dscal = p.take<unsigned long long>(SC_N);
+  L.hist = p.take<double>(SM_HIST);
   L.phx = p.take<long long>(nc);
   L.gx = p.take<long long>(nc);
   L.ghx = p.take<long long>((size_t)cap * 6 * FACE);
@@ -170,6 +171,9 @@ extern "C" int sm_destroy(sm_ctx *ctx) {
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
   if (ctx->hscal) cudaFreeHost(ctx->hscal);
+  if (ctx->mlog) fclose(ctx->mlog);
+  for (cudaEvent_t e : ctx->mlog_ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return SM_OK;
 }
@@ -215,6 +219,7 @@ extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   ctx->basis = (double *)(a + L.basis);
   ctx->tab = (double *)(a + L.tab);
   ctx->dscal = (unsigned long long *)(a + L.dscal);
+  ctx->hist = (double *)(a + L.hist);
   ctx->phx = (long long *)(a + L.phx);
   ctx->gx = (long long *)(a + L.gx);
   ctx->ghx = (long long *)(a + L.ghx);

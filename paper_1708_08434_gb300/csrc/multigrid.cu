@@ -712,8 +712,9 @@ __global__ void __launch_bounds__(GT) k_add_corr(const int32_t *__restrict__ lea
 
 // Stopping test of the device-side cycle loop: relative residual of the
 // last norm, cycle count (+inc), and the loop condition
-// rel > tol && cycles < max.
-__global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *sc, int inc) {
+// rel > tol && cycles < max; the relative residual of cycle c also goes to
+// hist[c - 1] (the first SM_HIST cycles).
+__global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *sc, int inc, double *hist) {
   pdl_wait();
   double num = __longlong_as_double((long long)sc[SC_NORM]);
   double den = __longlong_as_double((long long)sc[SC_DEN]);
@@ -721,6 +722,7 @@ __global__ void k_loop_check(cudaGraphConditionalHandle h, unsigned long long *s
   unsigned long long c = sc[SC_CYC] + (unsigned long long)inc;
   sc[SC_CYC] = c;
   sc[SC_REL] = (unsigned long long)__double_as_longlong(rel);
+  if (c >= 1 && c <= (unsigned long long)SM_HIST) hist[c - 1] = rel;
   double tol = __longlong_as_double((long long)sc[SC_TOL]);
   const bool ovf = (sc[SC_ERR] & 8ull) != 0;  // fixed-point range left: the host runs the solve again
   cudaGraphSetConditional(h, (rel > tol && c < sc[SC_MAXC] && !ovf) ? 1u : 0u);
@@ -1789,7 +1791,7 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   n0 = ctx->n_launch;
   if ((st = solve_prefix(ctx, kind))) return end_captures(ctx, saved, st);
   if (fmg) {
-    sm_launch(ctx, k_loop_check, 1, 1, 0, h, ctx->dscal, 1);
+    sm_launch(ctx, k_loop_check, 1, 1, 0, h, ctx->dscal, 1, ctx->hist);
   }
   out->prefix_launches = ctx->n_launch - n0;
   if (cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess)
@@ -1810,7 +1812,7 @@ static int capture_solve(sm_ctx *ctx, int kind, sm_graph *out) {
   ctx->stream = ctx->cap2;
   n0 = ctx->n_launch;
   if ((st = solve_body(ctx, kind))) return end_captures(ctx, saved, st);
-  sm_launch(ctx, k_loop_check, 1, 1, 0, h, ctx->dscal, 1);
+  sm_launch(ctx, k_loop_check, 1, 1, 0, h, ctx->dscal, 1, ctx->hist);
   out->body_launches = ctx->n_launch - n0;
   if (cudaStreamEndCapture(ctx->cap2, &body) != cudaSuccess)
     return end_captures(ctx, saved, sm_fail(ctx, SM_ECUDA, "end body capture"));
@@ -1863,11 +1865,13 @@ static int run_solve_once(sm_ctx *ctx, int kind, double tol, int max_cycles, int
     if ((st = ensure_basis(ctx))) return st;
     if ((st = solve_prefix(ctx, kind))) return st;
     bool go = true;
+    ctx->hhist.clear();
     if (fmg) {
       c = 1;
       if ((st = read_scalars(ctx))) return st;
       double num = ctx->hscal[SC_NORM], den = ctx->hscal[SC_DEN];
       rel = den > 0.0 ? num / den : num;
+      ctx->hhist.push_back(rel);
       go = rel > tol && c < max_cycles;
     }
     while (go) {
@@ -1876,6 +1880,7 @@ static int run_solve_once(sm_ctx *ctx, int kind, double tol, int max_cycles, int
       if ((st = read_scalars(ctx))) return st;
       double num = ctx->hscal[SC_NORM], den = ctx->hscal[SC_DEN];
       rel = den > 0.0 ? num / den : num;
+      ctx->hhist.push_back(rel);
       go = rel > tol && c < max_cycles;
     }
     if ((st = solve_suffix(ctx, kind))) return st;
@@ -1894,7 +1899,87 @@ static int fx_widen(sm_ctx *ctx, bool *again) {
   return SM_OK;
 }
 
+static void vcycle_model(const sm_ctx *ctx, int top, bool fixed, double *bytes, double *ops);
+
+static void json_num(FILE *f, double v) {
+  if (v == v && v - v == 0.0) fprintf(f, "%.17g", v);
+  else fputs("null", f);
+}
+
+// one JSON line of the metrics log for the solve that just ended (its
+// stream synchronised): cycles, relative residual after each cycle, time
+// from the events around the call (retries of a widened fixed-point scale
+// included), algorithmic bytes of the V-cycles (the per-level model of
+// sm_kernel_bench class 2 times the cycle count; an FMG ladder counts as
+// one cycle) and the bandwidth they imply
+static int log_solve(sm_ctx *ctx, int fmg, int kind, double tol, int c, double rel, int st) {
+  SM_CK(cudaEventRecord(ctx->mlog_ev[1], ctx->stream));
+  SM_CK(cudaEventSynchronize(ctx->mlog_ev[1]));
+  float ms = 0.0f;
+  SM_CK(cudaEventElapsedTime(&ms, ctx->mlog_ev[0], ctx->mlog_ev[1]));
+  std::vector<double> hist;
+  const char *path = "persistent";
+  if (ctx->graphs) {
+    path = "graph";
+    hist.resize((size_t)std::max(0, std::min(c, SM_HIST)));
+    if (!hist.empty())
+      SM_CK(cudaMemcpy(hist.data(), ctx->hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost));
+  } else if (!(ctx->persist && kind < 2)) {
+    path = "host";
+    hist = ctx->hhist;
+  }
+  double by = 0.0, ops = 0.0;
+  if (ctx->n_levels > 1) vcycle_model(ctx, ctx->n_levels - 1, kind < 2, &by, &ops);
+  const double bytes = by * c, gbs = ms > 0.0f ? bytes / (ms * 1e-3) / 1e9 : 0.0;
+  FILE *f = ctx->mlog;
+  fprintf(f, "{\"seq\": %lld, \"call\": \"%s\", \"precision\": \"%s\", \"path\": \"%s\", ",
+          ++ctx->mlog_seq, fmg ? "fmg" : "solve", kind < 2 ? "fp64" : "mixed", path);
+  fprintf(f, "\"boxes\": %d, \"levels\": %d, \"leaf_cells\": %lld, \"tol\": ", ctx->n_boxes, ctx->n_levels,
+          (long long)ctx->n_leaves * CELLS);
+  json_num(f, tol);
+  fprintf(f, ", \"status\": %d, \"cycles\": %d, \"rel\": ", st, c);
+  json_num(f, rel);
+  fputs(", \"residual_history\": [", f);
+  for (size_t i = 0; i < hist.size(); ++i) {
+    if (i) fputs(", ", f);
+    json_num(f, hist[i]);
+  }
+  fputs("], \"ms\": ", f);
+  json_num(f, ms);
+  fputs(", \"vcycle_bytes\": ", f);
+  json_num(f, by);
+  fputs(", \"bytes\": ", f);
+  json_num(f, bytes);
+  fputs(", \"gbs\": ", f);
+  json_num(f, gbs);
+  fputs(", \"hbm_frac\": ", f);
+  if (ctx->mlog_peak > 0.0) json_num(f, gbs / ctx->mlog_peak);
+  else fputs("null", f);
+  fputs("}\n", f);
+  fflush(f);
+  return SM_OK;
+}
+
+static int run_solve_logged(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycles, double *rel_res);
+
 static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycles, double *rel_res) {
+  if (!ctx->mlog) return run_solve_logged(ctx, fmg, tol, max_cycles, cycles, rel_res);
+  SM_CK(cudaEventRecord(ctx->mlog_ev[0], ctx->stream));
+  int c = 0;
+  double rel = 0.0;
+  const int st = run_solve_logged(ctx, fmg, tol, max_cycles, &c, &rel);
+  if (st == SM_OK || st == SM_ENOCONV) {
+    const int kind = (ctx->cfg.precision == SM_MIXED ? 2 : 0) + (fmg ? 1 : 0);
+    const int lst = log_solve(ctx, fmg, kind, tol, c, rel, st);
+    if (lst) return lst;
+  }
+  if (cycles) *cycles = c;
+  if (rel_res) *rel_res = rel;
+  return st;
+}
+
+// the solve itself (run_solve adds the metrics line when a log is open)
+static int run_solve_logged(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycles, double *rel_res) {
   int st;
   int c = 0;
   double rel = 0.0;
@@ -1916,6 +2001,23 @@ static int run_solve(sm_ctx *ctx, int fmg, double tol, int max_cycles, int *cycl
   if (cycles) *cycles = c;
   if (rel_res) *rel_res = rel;
   return rel <= tol ? SM_OK : sm_fail(ctx, SM_ENOCONV, "residual %.3e > tol %.3e after %d cycles", rel, tol, c);
+}
+
+extern "C" int sm_set_metrics_log(sm_ctx *ctx, const char *path, double hbm_peak_gbs) {
+  if (!ctx) return SM_EINVAL;
+  if (ctx->mlog) {
+    fclose(ctx->mlog);
+    ctx->mlog = nullptr;
+  }
+  if (!path || !*path) return SM_OK;
+  if (!ctx->mlog_ev[0]) {
+    SM_CK(cudaEventCreate(&ctx->mlog_ev[0]));
+    SM_CK(cudaEventCreate(&ctx->mlog_ev[1]));
+  }
+  ctx->mlog = fopen(path, "a");
+  if (!ctx->mlog) return sm_fail(ctx, SM_EINVAL, "cannot open the metrics log %s", path);
+  ctx->mlog_peak = hbm_peak_gbs > 0.0 ? hbm_peak_gbs : 0.0;
+  return SM_OK;
 }
 
 // relative residual of the current potential (denominator recomputed);

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <string>
 #include <utility>
@@ -115,8 +116,9 @@ struct sm_ctx {
   float *gh32 = nullptr;                                    // [max_boxes][6][64]
   double *cflux = nullptr;   // [max_boxes][6][64] fine-side refinement fluxes
   double *basis = nullptr;   // level-0 eigenbasis: [3][64] vectors, [3][8] eigenvalues
-  double *tab = nullptr;     // [3][4096] coefficient table
+  double *tab = nullptr;     // [6][4096] coefficient tables and their slopes
   unsigned long long *dscal = nullptr;  // device scalars (max reductions, flags)
+  double *hist = nullptr;    // [SM_HIST] relative residual after each cycle of the last solve
   int tab_n = 0;
   double tab_emax = 0.0;
 
@@ -130,6 +132,13 @@ struct sm_ctx {
 
   // kernels launched so far (diagnostics)
   long long n_launch = 0;
+
+  // per-solve metrics log (JSON lines), off unless a path was given
+  FILE *mlog = nullptr;
+  double mlog_peak = 0.0;               // HBM GB/s the line's fraction divides by (0: none)
+  long long mlog_seq = 0;
+  cudaEvent_t mlog_ev[2] = {nullptr, nullptr};
+  std::vector<double> hhist;            // cycle history of the host-loop path
 
   // optional hooks around the solves of sm_advance_fluid (learned warm start)
   void *hook_obj = nullptr;
@@ -187,6 +196,9 @@ enum {
   SC_FX2G = 19,     // fixed-point solve: 2g of the six faces in quanta (19 .. 24)
   SC_N = 32
 };
+
+// cycles of a solve whose relative residual the metrics log keeps
+constexpr int SM_HIST = 64;
 
 namespace sm {
 
