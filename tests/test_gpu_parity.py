@@ -121,6 +121,28 @@ def test_field_parity():
     assert g.dt_limit(Q, EPS0) == pytest.approx(o.dt_limit(Q, EPS0), rel=TOL)
 
 
+@pytest.mark.parametrize("name", ["streamer_small", "streamer_small_bg"])
+def test_field_from_the_same_potential(name):
+    """|E| of k_field against the oracle's field computed from the GPU's own
+    solved potential (all boxes, so refinement ghosts agree too): without
+    the solver's conditioning every leaf cell agrees to 1e-12 of its own
+    value, plus 1e-15 max|E| where the field nearly vanishes; and the time
+    step from the same potential and field to 1e-12."""
+    dom, st, o, g = pair(name)
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    g.fmg(1e-10, 30)
+    p = pkg()
+    o.set(oracle.PHI, g.download(p.PHI))
+    o.compute_field()
+    g.compute_field()
+    leaf = t["child"][:, 0] < 0
+    eo, eg = o.get(oracle.EMAG)[leaf], g.download(p.EMAG)[leaf]
+    bad = np.abs(eg - eo) > TOL * np.abs(eo) + 1e-3 * TOL * np.abs(eo).max()
+    assert not bad.any(), (np.abs(eg - eo)[bad][:5], eo[bad][:5])
+    assert g.dt_limit(Q, EPS0) == pytest.approx(o.dt_limit(Q, EPS0), rel=TOL)
+
+
 def test_fluid_stage_parity():
     dom, st, o, g = pair("streamer_small")
     t = o.tables()
