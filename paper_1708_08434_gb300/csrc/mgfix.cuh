@@ -446,6 +446,126 @@ __global__ void __launch_bounds__(GT) k_fcolor(int lo, int color, long long *__r
   fx_flag(bad, sc);
 }
 
+// ---------------------------------------------------------------------------
+// red-black Gauss-Seidel by rows: one thread per x row of the colour
+// ---------------------------------------------------------------------------
+//
+// In the colour-split layout the 4 cells of colour c in the x row (j, k)
+// of a box are contiguous (4j + 32k of the colour's half), and so are the
+// other colour's 4 cells of that row.  A cell i = 2q + p of the row
+// (p = (c + j + k) & 1) has its y and z neighbours at the same q in the
+// other colour's rows (j+-1, k) and (j, k+-1), and its x neighbours at
+// q - 1 + p and q + p in the other colour's own row; only one cell of the
+// row (q = 0 when p = 0, q = 3 when p = 1) reaches across an x face.  A
+// thread updates the 4 cells of its row: the other colour's rows of the
+// box are staged once in shared memory (32 bytes per row), the rows
+// across the box's y and z faces and the x-face value are read by the
+// threads that need them, and ghosts at walls and refinement faces are
+// formed from the row's own current values as in fx_color_box.  The sums
+// are the same exact integer sums, so the results are bit-identical.
+constexpr int RBOX = 2;  // boxes per block, 64 threads each
+
+// the 4 values at p (16-byte aligned)
+__device__ __forceinline__ void row_ld(const long long *p, long long (&v)[4]) {
+  const longlong2 a = reinterpret_cast<const longlong2 *>(p)[0], b = reinterpret_cast<const longlong2 *>(p)[1];
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// ghosts of face f for the 4 cells i = 2q + p of a face row (own: the
+// cells' current values; gi: ghx index of the face cell of q = 0, stride
+// gs per q) when the face is a wall or a refinement face
+__device__ __forceinline__ void row_ghost(int nb, int f, const long long (&own)[4], const long long *ghx,
+                                          size_t gi, int gs, const Bc &bc, const unsigned long long *sc,
+                                          long long (&g)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (nb == -1) g[q] = bc.type[f] ? fx_2g(sc, f) - own[q] : own[q];
+    else g[q] = fx_div6(2 * own[q] + ghx[gi + (size_t)gs * q]);
+  }
+}
+
+__global__ void __launch_bounds__(64 * RBOX) k_fcolor_rows(int lo, int n, int color, long long *__restrict__ phx,
+                                                           const long long *__restrict__ gx,
+                                                           const long long *__restrict__ ghx,
+                                                           const int32_t *__restrict__ nbr6, Bc bc,
+                                                           unsigned long long *sc) {
+  __shared__ longlong2 srow[RBOX][64][2];  // the other colour's rows of each box
+  const int sub = threadIdx.x >> 6, r = threadIdx.x & 63;
+  const int bi = blockIdx.x * RBOX + sub;
+  const bool live = bi < n;
+  const int b = lo + (live ? bi : n - 1);
+  const int j = r & 7, k = r >> 3, p = (color + j + k) & 1, oc = color ^ 1;
+  const int fxf = p;  // x face reached by this row: 0 (-x) when p = 0, 1 (+x) when p = 1
+  const int fyf = j == 0 ? 2 : (j == NC - 1 ? 3 : -1), fzf = k == 0 ? 4 : (k == NC - 1 ? 5 : -1);
+  const int nbx = __ldg(nbr6 + 6 * b + fxf);
+  const int nby = fyf >= 0 ? __ldg(nbr6 + 6 * b + fyf) : 0;
+  const int nbz = fzf >= 0 ? __ldg(nbr6 + 6 * b + fzf) : 0;
+  pdl_wait();
+  const size_t base = (size_t)b * CELLS;
+  const int ro = 4 * j + 32 * k;
+  long long G[4], R[4];
+  row_ld(gx + base + (color << 8) + ro, G);
+  row_ld(phx + base + (oc << 8) + ro, R);
+  srow[sub][r][0] = make_longlong2(R[0], R[1]);
+  srow[sub][r][1] = make_longlong2(R[2], R[3]);
+  // the row's own current values, for ghosts at walls and refinement faces
+  long long own[4] = {0, 0, 0, 0};
+  if (nbx < 0 || nby < 0 || nbz < 0) row_ld(phx + base + (color << 8) + ro, own);
+  __syncthreads();
+  long long ym[4], yp[4], zm[4], zp[4];
+  auto srow_ld = [&](int rr, long long (&v)[4]) {
+    const longlong2 a = srow[sub][rr][0], c2 = srow[sub][rr][1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = c2.x;
+    v[3] = c2.y;
+  };
+  // y faces: the neighbour's row (7, k) or (0, k) of the other colour
+  if (j > 0) srow_ld(r - 1, ym);
+  else if (nby >= 0) row_ld(phx + (size_t)nby * CELLS + (oc << 8) + 4 * (NC - 1) + 32 * k, ym);
+  else row_ghost(nby, 2, own, ghx, (size_t)(6 * b + 2) * FACE + k + NC * p, 2 * NC, bc, sc, ym);
+  if (j < NC - 1) srow_ld(r + 1, yp);
+  else if (nby >= 0) row_ld(phx + (size_t)nby * CELLS + (oc << 8) + 32 * k, yp);
+  else row_ghost(nby, 3, own, ghx, (size_t)(6 * b + 3) * FACE + k + NC * p, 2 * NC, bc, sc, yp);
+  // z faces: the neighbour's row (j, 7) or (j, 0)
+  if (k > 0) srow_ld(r - 8, zm);
+  else if (nbz >= 0) row_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j + 32 * (NC - 1), zm);
+  else row_ghost(nbz, 4, own, ghx, (size_t)(6 * b + 4) * FACE + p + NC * j, 2, bc, sc, zm);
+  if (k < NC - 1) srow_ld(r + 8, zp);
+  else if (nbz >= 0) row_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j, zp);
+  else row_ghost(nbz, 5, own, ghx, (size_t)(6 * b + 5) * FACE + p + NC * j, 2, bc, sc, zp);
+  // x: the one value across the x face (cell i = 0 when p = 0, i = 7 when p = 1)
+  long long xg;
+  {
+    const long long oe = p ? own[3] : own[0];  // the row's cell at the face
+    if (nbx >= 0) {
+      xg = phx[(size_t)nbx * CELLS + (oc << 8) + ro + (p ? 0 : 3)];
+    } else if (nbx == -1) {
+      xg = bc.type[fxf] ? fx_2g(sc, fxf) - oe : oe;
+    } else {
+      xg = fx_div6(2 * oe + ghx[(size_t)(6 * b + fxf) * FACE + j + NC * k]);
+    }
+  }
+  bool bad = false;
+  long long v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const long long xm = p ? R[q] : (q == 0 ? xg : R[q - 1]);
+    const long long xp = p ? (q == 3 ? xg : R[q + 1]) : R[q];
+    v[q] = fx_div6(xm + xp + ym[q] + yp[q] + zm[q] + zp[q] + 6 * G[q]);
+    bad |= fx_bad(v[q]);
+  }
+  if (live) {
+    longlong2 *dst = reinterpret_cast<longlong2 *>(phx + base + (color << 8) + ro);
+    dst[0] = make_longlong2(v[0], v[1]);
+    dst[1] = make_longlong2(v[2], v[3]);
+  }
+  fx_flag(bad && live, sc);
+}
+
 __global__ void __launch_bounds__(GT) k_fresid_restrict(int lo, long long *__restrict__ phx, long long *__restrict__ gx,
                                                         const long long *__restrict__ ghx,
                                                         const int32_t *__restrict__ nbr6,

@@ -1554,14 +1554,25 @@ static int fx_epilogue(sm_ctx *ctx) {
   return sm_fill_all_cf(ctx, ctx->phi);
 }
 
-// nu red-black sweeps of level l (two colour passes each, in place)
+// nu red-black sweeps of level l (two colour passes each, in place).  A
+// level of many boxes runs the row kernel (4 cells and 16-byte row loads
+// per thread, fewer instructions per cell); a level that is one partial
+// wave of blocks runs the box kernel (2 cells per thread, twice the warps
+// to hide its load latency).  Both give the same bits.
+constexpr int FX_ROWS_MIN = 2048;  // boxes of a level from which the row kernel runs
+
 static int fx_smooth(sm_ctx *ctx, int l, int nu) {
   const int n = lvl_n(ctx, l);
   if (!n) return SM_OK;
   for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color)
-      sm_launch(ctx, fx::k_fcolor, n, GT, 0, ctx->level_off[l], color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6,
-                ctx->bc, ctx->dscal);
+    for (int color = 0; color < 2; ++color) {
+      if (n >= FX_ROWS_MIN)
+        sm_launch(ctx, fx::k_fcolor_rows, (n + fx::RBOX - 1) / fx::RBOX, 64 * fx::RBOX, 0, ctx->level_off[l], n,
+                  color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6, ctx->bc, ctx->dscal);
+      else
+        sm_launch(ctx, fx::k_fcolor, n, GT, 0, ctx->level_off[l], color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6,
+                  ctx->bc, ctx->dscal);
+    }
   SM_CKL("rbgs");
   return SM_OK;
 }
