@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(GT) k_fcolor(int lo, int color, long long *__r
 // threads that need them, and ghosts at walls and refinement faces are
 // formed from the row's own current values as in fx_color_box.  The sums
 // are the same exact integer sums, so the results are bit-identical.
-constexpr int RBOX = 2;  // boxes per block, 64 threads each
+constexpr int RBOX = 1;  // boxes per block, 64 threads each
 
 // the 4 values at p (16-byte aligned)
 __device__ __forceinline__ void row_ld(const long long *p, long long (&v)[4]) {
@@ -487,12 +487,14 @@ __device__ __forceinline__ void row_ghost(int nb, int f, const long long (&own)[
   }
 }
 
-__global__ void __launch_bounds__(64 * RBOX) k_fcolor_rows(int lo, int n, int color, long long *__restrict__ phx,
+__global__ void __launch_bounds__(64 * RBOX, 16 / RBOX) k_fcolor_rows(int lo, int n, int color, long long *__restrict__ phx,
                                                            const long long *__restrict__ gx,
                                                            const long long *__restrict__ ghx,
                                                            const int32_t *__restrict__ nbr6, Bc bc,
                                                            unsigned long long *sc) {
-  __shared__ longlong2 srow[RBOX][64][2];  // the other colour's rows of each box
+  // the other colour's rows of each box, first and second halves apart
+  // (lanes on consecutive rows read consecutive 16-byte words)
+  __shared__ longlong2 srow[RBOX][2][64];
   const int sub = threadIdx.x >> 6, r = threadIdx.x & 63;
   const int bi = blockIdx.x * RBOX + sub;
   const bool live = bi < n;
@@ -506,49 +508,50 @@ __global__ void __launch_bounds__(64 * RBOX) k_fcolor_rows(int lo, int n, int co
   pdl_wait();
   const size_t base = (size_t)b * CELLS;
   const int ro = 4 * j + 32 * k;
+  // every global load first: G, the other colour's row, the row's own
+  // values (for ghosts at walls and refinement faces), the rows across a y
+  // or z face and the value across the x face
   long long G[4], R[4];
   row_ld(gx + base + (color << 8) + ro, G);
   row_ld(phx + base + (oc << 8) + ro, R);
-  srow[sub][r][0] = make_longlong2(R[0], R[1]);
-  srow[sub][r][1] = make_longlong2(R[2], R[3]);
-  // the row's own current values, for ghosts at walls and refinement faces
   long long own[4] = {0, 0, 0, 0};
   if (nbx < 0 || nby < 0 || nbz < 0) row_ld(phx + base + (color << 8) + ro, own);
-  __syncthreads();
   long long ym[4], yp[4], zm[4], zp[4];
+  if (j == 0) {
+    if (nby >= 0) row_ld(phx + (size_t)nby * CELLS + (oc << 8) + 4 * (NC - 1) + 32 * k, ym);
+    else row_ghost(nby, 2, own, ghx, (size_t)(6 * b + 2) * FACE + k + NC * p, 2 * NC, bc, sc, ym);
+  } else if (j == NC - 1) {
+    if (nby >= 0) row_ld(phx + (size_t)nby * CELLS + (oc << 8) + 32 * k, yp);
+    else row_ghost(nby, 3, own, ghx, (size_t)(6 * b + 3) * FACE + k + NC * p, 2 * NC, bc, sc, yp);
+  }
+  if (k == 0) {
+    if (nbz >= 0) row_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j + 32 * (NC - 1), zm);
+    else row_ghost(nbz, 4, own, ghx, (size_t)(6 * b + 4) * FACE + p + NC * j, 2, bc, sc, zm);
+  } else if (k == NC - 1) {
+    if (nbz >= 0) row_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j, zp);
+    else row_ghost(nbz, 5, own, ghx, (size_t)(6 * b + 5) * FACE + p + NC * j, 2, bc, sc, zp);
+  }
+  long long xg;
+  {
+    const long long oe = p ? own[3] : own[0];  // the row's cell at the face
+    if (nbx >= 0) xg = phx[(size_t)nbx * CELLS + (oc << 8) + ro + (p ? 0 : 3)];
+    else if (nbx == -1) xg = bc.type[fxf] ? fx_2g(sc, fxf) - oe : oe;
+    else xg = fx_div6(2 * oe + ghx[(size_t)(6 * b + fxf) * FACE + j + NC * k]);
+  }
+  srow[sub][0][r] = make_longlong2(R[0], R[1]);
+  srow[sub][1][r] = make_longlong2(R[2], R[3]);
+  __syncthreads();
   auto srow_ld = [&](int rr, long long (&v)[4]) {
-    const longlong2 a = srow[sub][rr][0], c2 = srow[sub][rr][1];
+    const longlong2 a = srow[sub][0][rr], c2 = srow[sub][1][rr];
     v[0] = a.x;
     v[1] = a.y;
     v[2] = c2.x;
     v[3] = c2.y;
   };
-  // y faces: the neighbour's row (7, k) or (0, k) of the other colour
   if (j > 0) srow_ld(r - 1, ym);
-  else if (nby >= 0) row_ld(phx + (size_t)nby * CELLS + (oc << 8) + 4 * (NC - 1) + 32 * k, ym);
-  else row_ghost(nby, 2, own, ghx, (size_t)(6 * b + 2) * FACE + k + NC * p, 2 * NC, bc, sc, ym);
   if (j < NC - 1) srow_ld(r + 1, yp);
-  else if (nby >= 0) row_ld(phx + (size_t)nby * CELLS + (oc << 8) + 32 * k, yp);
-  else row_ghost(nby, 3, own, ghx, (size_t)(6 * b + 3) * FACE + k + NC * p, 2 * NC, bc, sc, yp);
-  // z faces: the neighbour's row (j, 7) or (j, 0)
   if (k > 0) srow_ld(r - 8, zm);
-  else if (nbz >= 0) row_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j + 32 * (NC - 1), zm);
-  else row_ghost(nbz, 4, own, ghx, (size_t)(6 * b + 4) * FACE + p + NC * j, 2, bc, sc, zm);
   if (k < NC - 1) srow_ld(r + 8, zp);
-  else if (nbz >= 0) row_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j, zp);
-  else row_ghost(nbz, 5, own, ghx, (size_t)(6 * b + 5) * FACE + p + NC * j, 2, bc, sc, zp);
-  // x: the one value across the x face (cell i = 0 when p = 0, i = 7 when p = 1)
-  long long xg;
-  {
-    const long long oe = p ? own[3] : own[0];  // the row's cell at the face
-    if (nbx >= 0) {
-      xg = phx[(size_t)nbx * CELLS + (oc << 8) + ro + (p ? 0 : 3)];
-    } else if (nbx == -1) {
-      xg = bc.type[fxf] ? fx_2g(sc, fxf) - oe : oe;
-    } else {
-      xg = fx_div6(2 * oe + ghx[(size_t)(6 * b + fxf) * FACE + j + NC * k]);
-    }
-  }
   bool bad = false;
   long long v[4];
 #pragma unroll
