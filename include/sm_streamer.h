@@ -305,6 +305,14 @@ int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, lo
  * Errors: SM_EINVAL (file cannot be opened), SM_ECUDA. */
 int sm_set_metrics_log(sm_ctx *ctx, const char *path, double hbm_peak_gbs);
 
+/* Levels of at least min_boxes boxes (default 2048; 0: every level) run
+ * the fixed-point smoother and residual-restriction kernels with one
+ * thread per x row of a box (16-byte row loads, fewer instructions per
+ * cell); smaller levels run the kernels with one 128-thread group per box
+ * (more warps per box for latency).  Both give bit-identical results; the
+ * choice is performance only.  Errors: SM_EINVAL for min_boxes < 0. */
+int sm_set_row_kernels(sm_ctx *ctx, int min_boxes);
+
 /* Solves run as CUDA graphs (captured on first use per octree, with the
  * cycle loop and its stopping test on the device) when enabled (default),
  * or as individually launched kernels with a host loop when disabled.

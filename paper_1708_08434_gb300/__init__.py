@@ -69,6 +69,7 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
            "sm_cnn_kernel_bench", "sm_cnn_load_samples", "sm_set_metrics_log",
+           "sm_set_row_kernels",
            "sm_cnn_last_error",
            "sm_batch_last_error",
            "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
@@ -153,6 +154,7 @@ def load():
         "sm_cnn_kernel_bench": [P, I, I, I, pD, pD, pD],
         "sm_cnn_load_samples": [P, P, P, I],
         "sm_set_metrics_log": [P, C.c_char_p, D],
+        "sm_set_row_kernels": [P, I],
         "sm_cnn_last_error": [P],
         "sm_last_error": [P],
         "sm_quad_create": [C.POINTER(P), P, I, I, I, P],
@@ -459,6 +461,10 @@ class Solver:
         """Append one JSON line per solve (cycles, residual history, time,
         algorithmic bytes, bandwidth) to `path`; None closes the log."""
         self._ck(self._lib.sm_set_metrics_log(self._h, path.encode() if path else None, float(hbm_peak_gbs)))
+
+    def set_row_kernels(self, min_boxes: int):
+        """Levels of at least min_boxes boxes run the row kernels (0: all)."""
+        self._ck(self._lib.sm_set_row_kernels(self._h, int(min_boxes)))
 
     def set_persistent(self, enable: bool):
         """V-cycles as one persistent cooperative launch, or as per-level

@@ -569,6 +569,147 @@ __global__ void __launch_bounds__(64 * RBOX, 16 / RBOX) k_fcolor_rows(int lo, in
   fx_flag(bad && live, sc);
 }
 
+// ---------------------------------------------------------------------------
+// residual and restriction by rows: one thread per x row of 8 cells
+// ---------------------------------------------------------------------------
+
+// the 8 values of x row (j, k) of a box in natural order i = 0..7 from the
+// two colour quads of the row (colour c holds the cells i = 2q + p_c,
+// p_c = (c + j + k) & 1)
+__device__ __forceinline__ void row8_from(const long long (&q0)[4], const long long (&q1)[4], int j, int k,
+                                          long long (&v)[8]) {
+  const int p0 = (j + k) & 1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[2 * q] = p0 ? q1[q] : q0[q];
+    v[2 * q + 1] = p0 ? q0[q] : q1[q];
+  }
+}
+
+__device__ __forceinline__ void row8_ld(const long long *box, int j, int k, long long (&v)[8]) {
+  long long a[4], c[4];
+  row_ld(box + 4 * j + 32 * k, a);
+  row_ld(box + 256 + 4 * j + 32 * k, c);
+  row8_from(a, c, j, k, v);
+}
+
+// ghosts of face f for the 8 cells of a face row from the row's own values
+// (wall or refinement face; gi, gs: ghx index of the face cell of i = 0
+// and its stride per i)
+__device__ __forceinline__ void row8_ghost(int nb, int f, const long long (&v)[8], const long long *ghx, size_t gi,
+                                           int gs, const Bc &bc, const unsigned long long *sc, long long (&g)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (nb == -1) g[i] = bc.type[f] ? fx_2g(sc, f) - v[i] : v[i];
+    else g[i] = fx_div6(2 * v[i] + ghx[gi + (size_t)gs * i]);
+  }
+}
+
+// Residual and restriction of box b (as fx_resid_restrict_box) with one
+// thread per x row: the row's 8 values of 6 G + T (T = h^2 L phi in quanta)
+// and of phi are summed in x pairs, then over the 2 x 2 rows of a coarse
+// row with lane shuffles (rows j ^ 1 and k ^ 1 are lanes ^ 1 and ^ 8); the
+// lanes of even j and k write the 4 coarse cells.  Exact integer sums: the
+// same bits as the box kernel.
+__global__ void __launch_bounds__(64, 12) k_fresid_restrict_rows(int lo, long long *__restrict__ phx,
+                                                                 long long *__restrict__ gx,
+                                                                 const long long *__restrict__ ghx,
+                                                                 const int32_t *__restrict__ nbr6,
+                                                                 const int32_t *__restrict__ parent,
+                                                                 const int32_t *__restrict__ ijk, Bc bc,
+                                                                 const unsigned long long *sc) {
+  __shared__ longlong2 srow[4][64];  // the rows of the box, four 16-byte chunks apart
+  const int r = threadIdx.x, j = r & 7, k = r >> 3;
+  const int b = lo + blockIdx.x;
+  const int fyf = j == 0 ? 2 : (j == NC - 1 ? 3 : -1), fzf = k == 0 ? 4 : (k == NC - 1 ? 5 : -1);
+  const int nx0 = __ldg(nbr6 + 6 * b), nx1 = __ldg(nbr6 + 6 * b + 1);
+  const int nby = fyf >= 0 ? __ldg(nbr6 + 6 * b + fyf) : 0;
+  const int nbz = fzf >= 0 ? __ldg(nbr6 + 6 * b + fzf) : 0;
+  const Place pl = load_place(parent, ijk, b);
+  pdl_wait();
+  const size_t base = (size_t)b * CELLS;
+  // global loads first: the row (both colours), its G, the rows across y
+  // and z faces and the values across both x faces
+  long long q0[4], q1[4], v[8], acc[8];
+  row_ld(phx + base + 4 * j + 32 * k, q0);
+  row_ld(phx + base + 256 + 4 * j + 32 * k, q1);
+  row8_from(q0, q1, j, k, v);
+  row8_ld(gx + base, j, k, acc);
+  long long xm, xp;
+  if (nx0 >= 0) xm = phx[(size_t)nx0 * CELLS + xpos(NC - 1, j, k)];
+  else if (nx0 == -1) xm = bc.type[0] ? fx_2g(sc, 0) - v[0] : v[0];
+  else xm = fx_div6(2 * v[0] + ghx[(size_t)(6 * b) * FACE + j + NC * k]);
+  if (nx1 >= 0) xp = phx[(size_t)nx1 * CELLS + xpos(0, j, k)];
+  else if (nx1 == -1) xp = bc.type[1] ? fx_2g(sc, 1) - v[NC - 1] : v[NC - 1];
+  else xp = fx_div6(2 * v[NC - 1] + ghx[(size_t)(6 * b + 1) * FACE + j + NC * k]);
+  // 6 G + T = 6 G - 6 phi + the six neighbours, the rows added as they come
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    acc[i] = 6 * acc[i] - 6 * v[i] + (i > 0 ? v[i - 1] : xm) + (i < NC - 1 ? v[i + 1] : xp);
+  auto add8 = [&](const long long (&w)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] += w[i];
+  };
+  {
+    long long w[8];
+    if (j == 0) {
+      if (nby >= 0) row8_ld(phx + (size_t)nby * CELLS, NC - 1, k, w);
+      else row8_ghost(nby, 2, v, ghx, (size_t)(6 * b + 2) * FACE + k, NC, bc, sc, w);
+      add8(w);
+    } else if (j == NC - 1) {
+      if (nby >= 0) row8_ld(phx + (size_t)nby * CELLS, 0, k, w);
+      else row8_ghost(nby, 3, v, ghx, (size_t)(6 * b + 3) * FACE + k, NC, bc, sc, w);
+      add8(w);
+    }
+    if (k == 0) {
+      if (nbz >= 0) row8_ld(phx + (size_t)nbz * CELLS, j, NC - 1, w);
+      else row8_ghost(nbz, 4, v, ghx, (size_t)(6 * b + 4) * FACE + NC * j, 1, bc, sc, w);
+      add8(w);
+    } else if (k == NC - 1) {
+      if (nbz >= 0) row8_ld(phx + (size_t)nbz * CELLS, j, 0, w);
+      else row8_ghost(nbz, 5, v, ghx, (size_t)(6 * b + 5) * FACE + NC * j, 1, bc, sc, w);
+      add8(w);
+    }
+  }
+  srow[0][r] = make_longlong2(q0[0], q0[1]);
+  srow[1][r] = make_longlong2(q0[2], q0[3]);
+  srow[2][r] = make_longlong2(q1[0], q1[1]);
+  srow[3][r] = make_longlong2(q1[2], q1[3]);
+  __syncthreads();
+  auto srow8 = [&](int rr, int jj, int kk) {
+    long long a4[4], c4[4], w[8];
+    const longlong2 t0 = srow[0][rr], t1 = srow[1][rr], t2 = srow[2][rr], t3 = srow[3][rr];
+    a4[0] = t0.x; a4[1] = t0.y; a4[2] = t1.x; a4[3] = t1.y;
+    c4[0] = t2.x; c4[1] = t2.y; c4[2] = t3.x; c4[3] = t3.y;
+    row8_from(a4, c4, jj, kk, w);
+    add8(w);
+  };
+  if (j > 0) srow8(r - 1, j - 1, k);
+  if (j < NC - 1) srow8(r + 1, j + 1, k);
+  if (k > 0) srow8(r - 8, j, k - 1);
+  if (k < NC - 1) srow8(r + 8, j, k + 1);
+  long long sp[4], sa[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    sp[c] = v[2 * c] + v[2 * c + 1];
+    sa[c] = acc[2 * c] + acc[2 * c + 1];
+    sp[c] += __shfl_xor_sync(0xffffffffu, sp[c], 1);
+    sa[c] += __shfl_xor_sync(0xffffffffu, sa[c], 1);
+    sp[c] += __shfl_xor_sync(0xffffffffu, sp[c], 8);
+    sa[c] += __shfl_xor_sync(0xffffffffu, sa[c], 8);
+  }
+  if (((j | k) & 1) == 0) {
+    const size_t pb = (size_t)pl.P * CELLS;
+    const int cy = 4 * pl.oy + (j >> 1), cz = 4 * pl.oz + (k >> 1);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const size_t cc = pb + xpos(4 * pl.ox + c, cy, cz);
+      phx[cc] = fx_rdiv<8>(sp[c]);
+      gx[cc] = sa[c];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(GT) k_fresid_restrict(int lo, long long *__restrict__ phx, long long *__restrict__ gx,
                                                         const long long *__restrict__ ghx,
                                                         const int32_t *__restrict__ nbr6,

@@ -1555,18 +1555,16 @@ static int fx_epilogue(sm_ctx *ctx) {
 }
 
 // nu red-black sweeps of level l (two colour passes each, in place).  A
-// level of many boxes runs the row kernel (4 cells and 16-byte row loads
-// per thread, fewer instructions per cell); a level that is one partial
-// wave of blocks runs the box kernel (2 cells per thread, twice the warps
-// to hide its load latency).  Both give the same bits.
-constexpr int FX_ROWS_MIN = 2048;  // boxes of a level from which the row kernel runs
-
+// level of at least ctx->rows_min boxes runs the row kernel (4 cells and
+// 16-byte row loads per thread, fewer instructions per cell); a level that
+// is one partial wave of blocks runs the box kernel (2 cells per thread,
+// twice the warps to hide its load latency).  Both give the same bits.
 static int fx_smooth(sm_ctx *ctx, int l, int nu) {
   const int n = lvl_n(ctx, l);
   if (!n) return SM_OK;
   for (int s = 0; s < nu; ++s)
     for (int color = 0; color < 2; ++color) {
-      if (n >= FX_ROWS_MIN)
+      if (n >= ctx->rows_min)
         sm_launch(ctx, fx::k_fcolor_rows, (n + fx::RBOX - 1) / fx::RBOX, 64 * fx::RBOX, 0, ctx->level_off[l], n,
                   color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6, ctx->bc, ctx->dscal);
       else
@@ -1624,8 +1622,12 @@ static int fx_vcycle(sm_ctx *ctx, int top, int norm_slot = -1) {
     SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
   for (int l = top; l >= 1; --l) {
     if ((st = fx_smooth(ctx, l, ctx->cfg.nu1))) return st;
-    sm_launch(ctx, fx::k_fresid_restrict, lvl_n(ctx, l), GT, 0, ctx->level_off[l], ctx->phx, ctx->gx, ctx->ghx,
-              ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
+    if (lvl_n(ctx, l) >= ctx->rows_min)
+      sm_launch(ctx, fx::k_fresid_restrict_rows, lvl_n(ctx, l), 64, 0, ctx->level_off[l], ctx->phx, ctx->gx,
+                ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
+    else
+      sm_launch(ctx, fx::k_fresid_restrict, lvl_n(ctx, l), GT, 0, ctx->level_off[l], ctx->phx, ctx->gx, ctx->ghx,
+                ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
     sm_launch(ctx, fx::k_ffas, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx, (long long *)ctx->old,
               ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
     SM_CKL("vcycle down");
@@ -2112,6 +2114,13 @@ extern "C" int sm_set_persistent(sm_ctx *ctx, int enable) {
   if (!ctx) return SM_EINVAL;
   if (ctx->persist != (enable != 0)) sm_drop_graphs(ctx);
   ctx->persist = enable != 0;
+  return SM_OK;
+}
+
+extern "C" int sm_set_row_kernels(sm_ctx *ctx, int min_boxes) {
+  if (!ctx || min_boxes < 0) return SM_EINVAL;
+  if (ctx->rows_min != min_boxes) sm_drop_graphs(ctx);
+  ctx->rows_min = min_boxes;
   return SM_OK;
 }
 

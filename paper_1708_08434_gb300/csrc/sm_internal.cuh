@@ -111,6 +111,7 @@ struct sm_ctx {
   long long *phx = nullptr, *gx = nullptr;                  // [max_boxes][512]
   long long *ghx = nullptr;                                 // [max_boxes][6][64]
   int fx_margin = 5;         // exponent margin of the fixed-point scale
+  int rows_min = 2048;       // boxes of a level from which its fixed-point kernels work by rows
   // FP32 error-equation arrays of the mixed-precision solve
   float *e32 = nullptr, *f32 = nullptr, *old32 = nullptr;  // [max_boxes][512]
   float *gh32 = nullptr;                                    // [max_boxes][6][64]

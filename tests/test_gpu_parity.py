@@ -143,6 +143,44 @@ def test_field_from_the_same_potential(name):
     assert g.dt_limit(Q, EPS0) == pytest.approx(o.dt_limit(Q, EPS0), rel=TOL)
 
 
+@pytest.mark.parametrize("name", ["streamer_small", "streamer_small_bg", "uniform64"])
+def test_row_kernels_bit_identical(name):
+    """The row kernels of the fixed-point cycle (colour pass, residual and
+    restriction), forced onto every level, give the same bits as the box
+    kernels: FMG, then a warm-started solve to a tighter tolerance, on the
+    captured graphs and on the host loop."""
+    dom, st = synth.workload(name)
+    p = pkg()
+    out = []
+    for rows in (1 << 30, 0):
+        g = gpu_mesh(dom, st)
+        t = g.tables()
+        if st is None:
+            rho = synth.gaussian_charge(dom, t["level"], t["ijk"], np.arange(len(t["level"])))
+            g.upload(p.RHO, rho)
+            g.charge_rhs(1.0, 1.0, True)
+        else:
+            ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+            g.upload(p.NE, ne)
+            g.upload(p.NI, ni)
+            g.charge_rhs(Q, EPS0)
+        g.set_row_kernels(rows)
+        r1 = g.fmg(1e-8, 30)
+        phi1 = g.download(p.PHI)
+        r2 = g.solve(1e-11, 30)
+        phi2 = g.download(p.PHI)
+        g.set_graphs(False)
+        r3 = g.solve(1e-12, 30)
+        phi3 = g.download(p.PHI)
+        out.append((r1, r2, r3, phi1, phi2, phi3))
+        g.close()
+    a, b = out
+    for x, y in zip(a[:3], b[:3]):
+        assert x == y
+    for x, y in zip(a[3:], b[3:]):
+        assert np.array_equal(x.view(np.int64), y.view(np.int64))
+
+
 def test_fluid_stage_parity():
     dom, st, o, g = pair("streamer_small")
     t = o.tables()
