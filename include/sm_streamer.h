@@ -306,10 +306,10 @@ int sm_kernel_bench(sm_ctx *ctx, int kclass, int reps, double *us_per_launch, lo
 int sm_set_metrics_log(sm_ctx *ctx, const char *path, double hbm_peak_gbs);
 
 /* Levels of at least min_boxes boxes (default 2048; 0: every level) run
- * the fixed-point smoother and residual-restriction kernels with one
- * thread per x row of a box (16-byte row loads, fewer instructions per
- * cell); smaller levels run the kernels with one 128-thread group per box
- * (more warps per box for latency).  Both give bit-identical results; the
+ * the fixed-point smoother, residual-restriction and prolongation kernels
+ * with one thread per x row of a box (16-byte row loads, fewer
+ * instructions per cell); smaller levels run the kernels with one
+ * 128-thread group per box (more warps per box for latency).  Both give bit-identical results; the
  * choice is performance only.  Errors: SM_EINVAL for min_boxes < 0. */
 int sm_set_row_kernels(sm_ctx *ctx, int min_boxes);
 

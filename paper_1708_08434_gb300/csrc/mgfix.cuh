@@ -775,6 +775,119 @@ __global__ void __launch_bounds__(GT) k_fprolong(int lo, int n, int mode, long l
   fx_flag(bad, sc);
 }
 
+// Prolongation by rows (large levels): blocks of 128 threads take two boxes
+// of level l, one thread per fine x row of a box.  The 6^3 coarse values
+// (the 4^3 parent cells under the box and their face neighbours, as in
+// fx_prolong_box) are staged per box; each thread forms its row's 8 fine
+// values (c + c_x + c_y + c_z)/4 and adds them to (mode 0) or writes them
+// over (mode 1) its row with 16-byte loads and stores, then the box's Ghat
+// values.  Blocks beyond the prolongation measure leaf residuals as in
+// k_fprolong.  The same integer sums: the bits of k_fprolong.
+__global__ void __launch_bounds__(128) k_fprolong_rows(int lo, int n, int mode, long long *__restrict__ phx,
+                                                       const long long *__restrict__ oldx,
+                                                       long long *__restrict__ ghx,
+                                                       const int32_t *__restrict__ nbr6,
+                                                       const int32_t *__restrict__ parent,
+                                                       const int32_t *__restrict__ ijk, Bc bc,
+                                                       unsigned long long *sc, FxNorm nm) {
+  __shared__ long long sm[1000];  // two 216-value coarse regions, or a norm block's staged box
+  __shared__ unsigned long long red[GT / 32];
+  const int nblk = (n + 1) >> 1;
+  if ((int)blockIdx.x >= nblk) {
+    const Grp g = block_grp();
+    const int b = __ldg(nm.leaf + blockIdx.x - nblk);
+    const Nb nb = load_nb(g, nbr6, b);
+    pdl_wait();
+    const double nq = -fx_q(fx_E(sc)) * nm.inv_h2;
+    const unsigned long long m = fx_resid_max_box(g, sm, b, phx, nm.rhs, ghx, nb, bc, sc, nq);
+    group_umax_to(g, nm.slot, m, red);
+    return;
+  }
+  const int sub = threadIdx.x >> 6, r = threadIdx.x & 63;
+  const int bi = 2 * blockIdx.x + sub;
+  const bool live = bi < n;
+  const int b = lo + (live ? bi : n - 1);
+  const int P = __ldg(parent + b);
+  const int ox = __ldg(ijk + 3 * b) & 1, oy = __ldg(ijk + 3 * b + 1) & 1, oz = __ldg(ijk + 3 * b + 2) & 1;
+  long long *sp = sm + 216 * sub;
+  auto val = [&](int Q, int c) {
+    const size_t x = (size_t)Q * CELLS + xsplit(c);
+    return mode ? phx[x] : phx[x] - oldx[x];
+  };
+  auto reg = [](int x, int y, int z) { return x + 6 * y + 36 * z; };
+  pdl_wait();
+  {
+    const int x = r & 3, y = (r >> 2) & 3, z = r >> 4;
+    sp[reg(x + 1, y + 1, z + 1)] = val(P, cidx(4 * ox + x, 4 * oy + y, 4 * oz + z));
+  }
+  // face neighbours of the parent region: region coordinate 0 or 5 along
+  // the face axis E, u + 1 and w + 1 along (E+1)%3 and (E+2)%3
+  for (int e = r; e < 96; e += 64) {
+    const int F = e >> 4, E = F >> 1, S = (F & 1) ? 1 : -1;
+    const int u = e & 3, w = (e >> 2) & 3, ce = S > 0 ? 5 : 0;
+    const int rx = E == 0 ? ce : (E == 1 ? w + 1 : u + 1);
+    const int ry = E == 0 ? u + 1 : (E == 1 ? ce : w + 1);
+    const int rz = E == 0 ? w + 1 : (E == 1 ? u + 1 : ce);
+    int lx = 4 * ox - 1 + rx, ly = 4 * oy - 1 + ry, lz = 4 * oz - 1 + rz;
+    const int le = E == 0 ? lx : (E == 1 ? ly : lz);
+    long long v;
+    if (le >= 0 && le < NC) {
+      v = val(P, cidx(lx, ly, lz));
+    } else {
+      const int Qn = __ldg(nbr6 + 6 * P + F);
+      if (Qn >= 0) {
+        const int wrap = S > 0 ? 0 : NC - 1;
+        v = val(Qn, cidx(E == 0 ? wrap : lx, E == 1 ? wrap : ly, E == 2 ? wrap : lz));
+      } else {
+        const long long ctr =
+            val(P, cidx(lx - (E == 0 ? S : 0), ly - (E == 1 ? S : 0), lz - (E == 2 ? S : 0)));
+        if (Qn == -1) {
+          v = bc.type[F] ? (mode ? fx_2g(sc, F) : 0) - ctr : ctr;
+        } else {
+          atomicOr(sc + SC_ERR, 1ull);
+          v = ctr;
+        }
+      }
+    }
+    sp[reg(rx, ry, rz)] = v;
+  }
+  const int j = r & 7, k = r >> 3;
+  const size_t base = (size_t)b * CELLS;
+  long long q0[4], q1[4], f[8];
+  row_ld(phx + base + 4 * j + 32 * k, q0);
+  row_ld(phx + base + 256 + 4 * j + 32 * k, q1);
+  row8_from(q0, q1, j, k, f);
+  __syncthreads();
+  bool bad = false;
+  {
+    const int y = (j >> 1) + 1, z = (k >> 1) + 1, sy = (j & 1) ? 6 : -6, sz = (k & 1) ? 36 : -36;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = reg((i >> 1) + 1, y, z);
+      const long long v = fx_rdiv<4>(sp[q] + sp[q + ((i & 1) ? 1 : -1)] + sp[q + sy] + sp[q + sz]);
+      f[i] = mode ? v : f[i] + v;
+      bad |= fx_bad(f[i]);
+    }
+  }
+  if (live) {
+    const int p0 = (j + k) & 1;
+    long long a[4], c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = p0 ? f[2 * q + 1] : f[2 * q];
+      c[q] = p0 ? f[2 * q] : f[2 * q + 1];
+    }
+    longlong2 *d0 = reinterpret_cast<longlong2 *>(phx + base + 4 * j + 32 * k);
+    longlong2 *d1 = reinterpret_cast<longlong2 *>(phx + base + 256 + 4 * j + 32 * k);
+    d0[0] = make_longlong2(a[0], a[1]);
+    d0[1] = make_longlong2(a[2], a[3]);
+    d1[0] = make_longlong2(c[0], c[1]);
+    d1[1] = make_longlong2(c[2], c[3]);
+    fx_cf_faces_box(r, 64, phx, ghx, nbr6, parent, ijk, bc, sc, b, sc + SC_ERR);
+  }
+  fx_flag(bad && live, sc);
+}
+
 // Ghat values of the refinement faces of boxes [lo, lo + grid), 64 threads
 // per box
 __global__ void __launch_bounds__(64) k_ffill_cf(int lo, const long long *__restrict__ phx, long long *__restrict__ ghx,

@@ -1597,8 +1597,13 @@ static fx::FxNorm fx_norm_of(sm_ctx *ctx, int l, int slot) {
 }
 
 static int fx_prolong(sm_ctx *ctx, int l, int mode, fx::FxNorm nm) {
-  sm_launch(ctx, fx::k_fprolong, lvl_n(ctx, l) + nm.n, GT, 0, ctx->level_off[l], lvl_n(ctx, l), mode, ctx->phx,
-            (const long long *)ctx->old, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal, nm);
+  const int n = lvl_n(ctx, l);
+  if (n >= ctx->rows_min)
+    sm_launch(ctx, fx::k_fprolong_rows, (n + 1) / 2 + nm.n, 128, 0, ctx->level_off[l], n, mode, ctx->phx,
+              (const long long *)ctx->old, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal, nm);
+  else
+    sm_launch(ctx, fx::k_fprolong, n + nm.n, GT, 0, ctx->level_off[l], n, mode, ctx->phx,
+              (const long long *)ctx->old, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal, nm);
   SM_CKL("prolong");
   return SM_OK;
 }
