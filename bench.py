@@ -37,6 +37,7 @@ L2_BYTES = 129 * 2 ** 20
 NO_GRAPHS = False
 NO_PDL = False
 PERSIST = False
+ROW_KERNELS = None
 
 
 # DRAM bytes (read + write) per k_fcolor launch, mean over the colour
@@ -75,6 +76,8 @@ def parse():
                          "(profilers cannot see kernels inside conditional graph nodes)")
     ap.add_argument("--persistent", action="store_true",
                     help="run V-cycles as one persistent cooperative launch instead of per-level launches")
+    ap.add_argument("--row-kernels", type=int, default=None, metavar="MIN_BOXES",
+                    help="levels of at least MIN_BOXES boxes run the row kernels (library default 2048; 0: all)")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the solver kernels without programmatic dependent launch")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -270,6 +273,8 @@ def build_gpu_case(precision=0):
         g.set_pdl(False)
     if PERSIST:
         g.set_persistent(True)
+    if ROW_KERNELS is not None:
+        g.set_row_kernels(ROW_KERNELS)
     g.build_octree()
     synth.refine_all(dom, st, g.level_ijk, g.refine_level)
     t = g.tables()
@@ -1358,13 +1363,14 @@ def run_reference(args):
 
 
 def main():
-    global NO_GRAPHS, NO_PDL, PERSIST, WORKLOAD
+    global NO_GRAPHS, NO_PDL, PERSIST, WORKLOAD, ROW_KERNELS
     args = parse()
     if args.mode in ("kernels", "vcycle"):
         WORKLOAD = args.workload
     NO_GRAPHS = args.no_graphs
     NO_PDL = args.no_pdl
     PERSIST = args.persistent
+    ROW_KERNELS = args.row_kernels
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":
