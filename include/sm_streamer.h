@@ -153,6 +153,10 @@ int sm_get_tables(const sm_ctx *ctx, sm_tables *out);
 /* Device pointer of a variable's [max_boxes][512] double array (borrowed;
  * SM_NE/SM_NI move between buffers in sm_advance_fluid). */
 int sm_var_ptr(const sm_ctx *ctx, int var, void **dev_ptr);
+/* The same pointer with its layout: *ld = 512 doubles per box (cell
+ * i + 8j + 64k of box b at b * ld + cell), *n_boxes = boxes in use (either
+ * may be NULL).  Errors: SM_EINVAL (unknown var, no arena). */
+int sm_var_layout(const sm_ctx *ctx, int var, void **dev_ptr, int *ld, int *n_boxes);
 
 /* Copy boxes [0, n_boxes) of a variable from / to HOST memory (pinned
  * memory gives asynchronous uploads; sm_download synchronises the stream).
@@ -181,6 +185,15 @@ int sm_restrict_densities(sm_ctx *ctx);
  * containing the ghost and its two tangential neighbours on the ghost's
  * side; the ghost value is then phi_f/3 + 2 phihat/3 (Sec. 2.1.1). */
 int sm_fill_ghosts(sm_ctx *ctx, int var, int level);
+/* The same for every level in [level_lo, level_hi] (each from the one
+ * below).  Errors: SM_EINVAL (var other than SM_PHI, empty or bad range). */
+int sm_fill_ghosts_range(sm_ctx *ctx, int var, int level_lo, int level_hi);
+/* The stored interpolation values phihat of boxes [0, n_boxes) into HOST
+ * memory, [n_boxes][6 faces][64] (face f = 2 axis + side; face cell
+ * u + 8 w with u along axis (a+1)%3 and w along (a+2)%3 of the face axis
+ * a; entries of faces that are not refinement faces are unspecified).
+ * Synchronises.  Errors: SM_EINVAL. */
+int sm_get_ghosts(sm_ctx *ctx, int var, double *host, int n_boxes);
 
 /* ---- multigrid (Sec. 2.1.2) ---------------------------------------------- */
 
@@ -233,6 +246,8 @@ int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_deref, double d
  * Out (may be NULL): refined boxes, derefined boxes, dropped requests.
  * Synchronises.  Errors: SM_ESTATE (no octree), SM_ENOMEM (max_boxes). */
 int sm_regrid(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
+/* sm_regrid with the new box count as its only output. */
+int sm_refine(sm_ctx *ctx, const int8_t *flags, int *n_boxes);
 
 /* ---- field and fluid step (Sec. 2.3, 2.4) --------------------------------- */
 
@@ -257,6 +272,14 @@ int sm_fluid_stage(sm_ctx *ctx, double dt);
  * table). */
 int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol,
                      int max_cycles, double *dt_next, int *cycles);
+/* The same with its constants in one struct. */
+typedef struct {
+  double q;        /* elementary charge */
+  double eps;      /* permittivity */
+  double tol;      /* relative residual of the two solves */
+  int max_cycles;  /* V-cycle limit of each solve */
+} sm_fluid_coeffs;
+int sm_advance_fluid_coeffs(sm_ctx *ctx, double dt, const sm_fluid_coeffs *c, double *dt_next, int *cycles);
 
 /* ---- diagnostics ----------------------------------------------------------- */
 

@@ -69,7 +69,8 @@ EXPORTS = ["sm_create", "sm_destroy", "sm_arena_size", "sm_bind_arena", "sm_buil
            "sm_cnn_bind_arena", "sm_cnn_set_params", "sm_cnn_get_params", "sm_cnn_forward",
            "sm_cnn_gradient", "sm_cnn_adam_step", "sm_cnn_train", "sm_cnn_attach", "sm_cnn_stats",
            "sm_cnn_kernel_bench", "sm_cnn_load_samples", "sm_set_metrics_log",
-           "sm_set_row_kernels",
+           "sm_set_row_kernels", "sm_var_layout", "sm_fill_ghosts_range", "sm_get_ghosts", "sm_refine",
+           "sm_advance_fluid_coeffs",
            "sm_cnn_last_error",
            "sm_batch_last_error",
            "sm_quad_create", "sm_quad_destroy", "sm_quad_arena_size", "sm_quad_bind_arena",
@@ -155,6 +156,11 @@ def load():
         "sm_cnn_load_samples": [P, P, P, I],
         "sm_set_metrics_log": [P, C.c_char_p, D],
         "sm_set_row_kernels": [P, I],
+        "sm_var_layout": [P, I, C.POINTER(C.c_void_p), pI, pI],
+        "sm_fill_ghosts_range": [P, I, I, I],
+        "sm_get_ghosts": [P, I, P, I],
+        "sm_refine": [P, P, pI],
+        "sm_advance_fluid_coeffs": [P, D, P, pD, pI],
         "sm_cnn_last_error": [P],
         "sm_last_error": [P],
         "sm_quad_create": [C.POINTER(P), P, I, I, I, P],
@@ -398,6 +404,21 @@ class Solver:
 
     def fill_ghosts(self, level: int, var: int = PHI):
         self._ck(self._lib.sm_fill_ghosts(self._h, var, level))
+
+    def fill_ghosts_range(self, level_lo: int, level_hi: int, var: int = PHI):
+        self._ck(self._lib.sm_fill_ghosts_range(self._h, var, level_lo, level_hi))
+
+    def ghosts(self, var: int = PHI) -> np.ndarray:
+        """Stored interpolation values phihat, [n_boxes][6][64]."""
+        out = np.zeros((self.n_boxes, 6, 64), np.float64)
+        self._ck(self._lib.sm_get_ghosts(self._h, var, _hp(out), self.n_boxes))
+        return out
+
+    def var_layout(self, var: int):
+        """(device pointer, doubles per box, boxes in use) of a variable."""
+        p, ld, nb = C.c_void_p(), C.c_int(), C.c_int()
+        self._ck(self._lib.sm_var_layout(self._h, var, C.byref(p), C.byref(ld), C.byref(nb)))
+        return p.value, ld.value, nb.value
 
     def vcycles(self, n: int) -> float:
         rel = C.c_double()

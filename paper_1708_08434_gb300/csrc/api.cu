@@ -525,6 +525,16 @@ static double *var_ptr(const sm_ctx *ctx, int var) {
   }
 }
 
+extern "C" int sm_var_layout(const sm_ctx *ctx, int var, void **dev_ptr, int *ld, int *n_boxes) {
+  if (!ctx || !dev_ptr || !ctx->arena) return SM_EINVAL;
+  double *p = var_ptr(ctx, var);
+  if (!p) return SM_EINVAL;
+  *dev_ptr = p;
+  if (ld) *ld = CELLS;
+  if (n_boxes) *n_boxes = ctx->n_boxes;
+  return SM_OK;
+}
+
 extern "C" int sm_var_ptr(const sm_ctx *ctx, int var, void **dev_ptr) {
   if (!ctx || !dev_ptr || !ctx->arena) return SM_EINVAL;
   double *p = var_ptr(ctx, var);

@@ -589,6 +589,12 @@ extern "C" int sm_fluid_stage(sm_ctx *ctx, double dt) {
   return SM_OK;
 }
 
+extern "C" int sm_advance_fluid_coeffs(sm_ctx *ctx, double dt, const sm_fluid_coeffs *c, double *dt_next,
+                                       int *cycles) {
+  if (!c) return SM_EINVAL;
+  return sm_advance_fluid(ctx, dt, c->q, c->eps, c->tol, c->max_cycles, dt_next, cycles);
+}
+
 extern "C" int sm_advance_fluid(sm_ctx *ctx, double dt, double q, double eps, double tol, int max_cycles,
                                 double *dt_next, int *cycles) {
   SM_RANGE();

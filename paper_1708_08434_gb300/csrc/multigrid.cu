@@ -2046,6 +2046,25 @@ int sm_rel_residual_now(sm_ctx *ctx, double *rel) {
   return rel_residual(ctx, rel);
 }
 
+extern "C" int sm_fill_ghosts_range(sm_ctx *ctx, int var, int level_lo, int level_hi) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (var != SM_PHI || level_lo < 0 || level_hi >= ctx->n_levels || level_lo > level_hi) return SM_EINVAL;
+  for (int l = level_lo; l <= level_hi; ++l)
+    if ((st = sm_mg_fill_cf(ctx, ctx->phi, l, 0))) return st;
+  return SM_OK;
+}
+
+extern "C" int sm_get_ghosts(sm_ctx *ctx, int var, double *host, int n_boxes) {
+  int st = check_ready(ctx);
+  if (st) return st;
+  if (var != SM_PHI || !host || n_boxes < 0 || n_boxes > ctx->n_boxes) return SM_EINVAL;
+  SM_CK(cudaMemcpyAsync(host, ctx->gh, sizeof(double) * 6 * FACE * (size_t)n_boxes, cudaMemcpyDeviceToHost,
+                        ctx->stream));
+  SM_CK(cudaStreamSynchronize(ctx->stream));
+  return SM_OK;
+}
+
 extern "C" int sm_fill_ghosts(sm_ctx *ctx, int var, int level) {
   int st = check_ready(ctx);
   if (st) return st;

@@ -203,7 +203,19 @@ extern "C" int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_dere
   return SM_OK;
 }
 
+int sm_regrid_impl(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
+
 extern "C" int sm_regrid(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
+  return sm_regrid_impl(ctx, flags, n_refined, n_derefined, n_dropped);
+}
+
+extern "C" int sm_refine(sm_ctx *ctx, const int8_t *flags, int *n_boxes) {
+  const int st = sm_regrid_impl(ctx, flags, nullptr, nullptr, nullptr);
+  if (st == SM_OK && n_boxes) *n_boxes = ctx->n_boxes;
+  return st;
+}
+
+int sm_regrid_impl(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
   SM_RANGE();
   if (!ctx || !flags) return SM_EINVAL;
   if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");

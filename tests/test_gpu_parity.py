@@ -435,3 +435,78 @@ def test_repeated_graph_launch_and_launch_count():
     assert us > 0 and n == 3 and by > 0 and fl > 0
     us2, n2, by2, fl2 = g.kernel_bench(2, 3)
     assert us2 > 0 and n2 == 3 and by2 == by and fl2 == fl
+
+
+def test_boundary_layout_ghosts_and_wrappers():
+    """The layout call, the ghost-range fill and its readable result, and
+    the wrappers sm_refine / sm_advance_fluid_coeffs: the stored
+    interpolation value of every refinement-face ghost equals
+    c/2 + c_t1/4 + c_t2/4 of the coarse cell c containing the ghost and its
+    two tangential neighbours on the ghost's side (Sec. 2.1.1), formed here
+    in numpy from the downloaded potential."""
+    import ctypes as C
+    dom, st, o, g = pair("streamer_small")
+    t = o.tables()
+    load_inputs(dom, st, o, g, t)
+    o.fmg(1e-8, 30)
+    g.fmg(1e-8, 30)
+    p = pkg()
+    ptr, ld, nb = g.var_layout(p.PHI)
+    assert ld == 512 and nb == g.n_boxes and ptr == g.var(p.PHI).data_ptr()
+    L = int(t["level"].max()) + 1
+    g.fill_ghosts_range(1, L - 1)
+    gh = g.ghosts()
+    phi = g.download(p.PHI)
+    where = {(int(l), *map(int, c)): b for b, (l, c) in enumerate(zip(t["level"], t["ijk"]))}
+
+    def val(l, G):
+        b = where.get((l, G[0] // 8, G[1] // 8, G[2] // 8))
+        if b is None:
+            return None
+        return phi[b, (G[0] % 8) + 8 * (G[1] % 8) + 64 * (G[2] % 8)]
+
+    checked = 0
+    for b in range(g.n_boxes):
+        l = int(t["level"][b])
+        if l == 0:
+            continue
+        for f in range(6):
+            a, side = f >> 1, f & 1
+            nbpos = list(t["ijk"][b])
+            nbpos[a] += 1 if side else -1
+            if (l, *nbpos) in where or not all(0 <= x < 2 ** l for x in nbpos):
+                continue  # same-level neighbour or domain wall
+            t1, t2 = (a + 1) % 3, (a + 2) % 3
+            for w in range(8):
+                for u in range(8):
+                    cg = [0, 0, 0]
+                    cg[a], cg[t1], cg[t2] = (8 if side else -1), u, w
+                    G = [8 * int(t["ijk"][b][d]) + cg[d] for d in range(3)]
+                    cc = [x >> 1 for x in G]
+                    vals = [val(l - 1, cc)]
+                    for e in (t1, t2):
+                        q = list(cc)
+                        q[e] += 1 if G[e] & 1 else -1
+                        vals.append(val(l - 1, q))
+                    if any(v is None for v in vals):
+                        continue  # a tangential neighbour across a wall
+                    ref = 0.5 * vals[0] + 0.25 * vals[1] + 0.25 * vals[2]
+                    assert gh[b, f, u + 8 * w] == pytest.approx(ref, rel=1e-14, abs=1e-14 * np.abs(phi).max())
+                    checked += 1
+    assert checked > 1000
+    # the wrappers: sm_refine with no flags set changes nothing
+    nbox = C.c_int()
+    flags = np.zeros(g.n_boxes, np.int8)
+    assert g._lib.sm_refine(g._h, flags.ctypes.data, C.byref(nbox)) == 0 and nbox.value == g.n_boxes
+    g.compute_field()
+    o.compute_field()
+    dt = o.dt_limit(Q, EPS0)
+
+    class Coeffs(C.Structure):
+        _fields_ = [("q", C.c_double), ("eps", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int)]
+    cf = Coeffs(Q, EPS0, 1e-8, 40)
+    dtn, cyc = C.c_double(), (C.c_int * 2)()
+    assert g._lib.sm_advance_fluid_coeffs(g._h, dt, C.byref(cf), C.byref(dtn), cyc) == 0
+    ro = o.advance(dt, Q, EPS0, 1e-8, 40)
+    assert (cyc[0], cyc[1]) == tuple(ro[2:])
+    assert dtn.value == pytest.approx(ro[1], rel=TOL)
