@@ -231,7 +231,8 @@ int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_deref, double d
                     int8_t *flags);
 
 /* Regrid with per-box flags (HOST int8 [n_boxes], the layout of
- * sm_refine_flags; only leaves and their parents are read).  Refinement:
+ * sm_refine_flags; only leaves and their parents are read; NULL: the flags
+ * the last sm_refine_flags call left on the device).  Refinement:
  * a leaf flagged > 0 below the maximum level gets 8 children when all 26
  * neighbour positions of its level hold a box or lie outside the domain;
  * other requests are dropped.  Derefinement: a box whose 8 children are
@@ -242,9 +243,12 @@ int sm_refine_flags(sm_ctx *ctx, double c0, double c1, double c0_deref, double d
  * boxes; new boxes get the potential and densities by the linear
  * prolongation (c + c_sx + c_sy + c_sz)/4 of the parent's cells (densities
  * limited to 2c, mirror ghosts at walls), other variables zero.  Tables,
- * device pointers of sm_get_tables and captured solves are replaced.
- * Out (may be NULL): refined boxes, derefined boxes, dropped requests.
- * Synchronises.  Errors: SM_ESTATE (no octree), SM_ENOMEM (max_boxes). */
+ * device pointers of sm_get_tables and captured solves are replaced; the
+ * SM_RES array is used as scratch.  The decisions, the new numbering and
+ * the tables are formed on the device (scans and binary searches over the
+ * Morton-sorted levels).  Out (may be NULL): refined boxes, derefined
+ * boxes, dropped requests.  Synchronises.  Errors: SM_ESTATE (no octree),
+ * SM_ENOMEM (max_boxes). */
 int sm_regrid(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
 /* sm_regrid with the new box count as its only output. */
 int sm_refine(sm_ctx *ctx, const int8_t *flags, int *n_boxes);

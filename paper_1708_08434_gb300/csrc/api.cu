@@ -380,6 +380,14 @@ __global__ void k_compact(int n, const int32_t *__restrict__ flag, const int32_t
   if (b < n && flag[b]) out[pos[b]] = b;
 }
 
+// exclusive prefix sum of n ints on the context stream; out[n] = total
+int sm_exclusive_scan(sm_ctx *ctx, const int32_t *in, int32_t *out, int n) {
+  k_scan<<<1, 1024, 0, ctx->stream>>>(in, out, n);
+  ++ctx->n_launch;
+  SM_CKL("scan");
+  return SM_OK;
+}
+
 int sm_rebuild_leaves(sm_ctx *ctx) {
   int n = ctx->n_boxes;
   k_mark_leaves<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->child, ctx->scan_a);

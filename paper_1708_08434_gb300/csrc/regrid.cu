@@ -4,7 +4,6 @@
 // numbering and prolonged into new boxes.
 #include <string.h>
 
-#include <algorithm>
 #include <vector>
 
 #include "sm_internal.cuh"
@@ -158,20 +157,165 @@ static LevelDx level_dx(const sm_ctx *ctx) {
   return d;
 }
 
-static uint64_t h_morton(int i, int j, int k) {
-  uint64_t key = 0;
-  for (int b = 0; b < 21; ++b) {
-    key |= (uint64_t)((i >> b) & 1) << (3 * b);
-    key |= (uint64_t)((j >> b) & 1) << (3 * b + 1);
-    key |= (uint64_t)((k >> b) & 1) << (3 * b + 2);
+// ---- the new box set on the device --------------------------------------
+//
+// Old boxes are stored level by level in Morton order.  The new set keeps
+// every box but the children of derefined boxes and adds 8 children per
+// refined box; at each level it is the merge of two Morton-sorted lists
+// (the kept boxes of the level and the children of the refined boxes of the
+// level below, whose keys are parent key * 8 + child), so a box's new index
+// is its rank in its own list plus the number of keys of the other list
+// below its own (binary searches).  Parents and children follow by binary
+// search in the new levels' keys.
+
+// per-level offsets of the compacted lists and of the new levels
+struct RgLevels {
+  int kept[SM_MAX_LEVELS + 2];   // start of level l in the kept list
+  int ref[SM_MAX_LEVELS + 2];    // start of level l in the refined list
+  int nw[SM_MAX_LEVELS + 2];     // start of level l in the new numbering
+};
+
+// first index in [lo, hi) whose key is >= x
+__device__ __forceinline__ int lower_bound_u64(const uint64_t *__restrict__ a, int lo, int hi, uint64_t x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
   }
-  return key;
+  return lo;
 }
 
-struct Entry {
-  int lev, i, j, k, src;
-  uint64_t key;
-};
+// refinement: a flagged leaf below the maximum level whose 26 neighbour
+// positions of its level hold a box or lie outside the domain (else the
+// request is dropped, cnt[0])
+__global__ void k_rg_refine(int n, const int32_t *__restrict__ level, const int32_t *__restrict__ child,
+                            const int32_t *__restrict__ nbr, const int8_t *__restrict__ flags, int lmax,
+                            int32_t *__restrict__ refv, int32_t *cnt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  int r = 0;
+  if (child[8 * b] < 0 && flags[b] > 0 && level[b] < lmax) {
+    bool ok = true;
+    for (int d = 0; d < 26; ++d) ok = ok && nbr[26 * b + d] != -2;
+    if (ok) r = 1;
+    else atomicAdd(cnt, 1);
+  }
+  refv[b] = r;
+}
+
+// derefinement of box p: its 8 children are leaves flagged < 0, and no
+// non-sibling neighbour of a child has or gets children (cnt[1] counts);
+// then keep[b] = b is not a child of a derefined box
+__global__ void k_rg_derefine(int n, const int32_t *__restrict__ child, const int32_t *__restrict__ parent,
+                              const int32_t *__restrict__ nbr, const int8_t *__restrict__ flags,
+                              const int32_t *__restrict__ refv, int8_t *__restrict__ derv, int32_t *cnt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  bool ok = child[8 * p] >= 0;
+  for (int c = 0; c < 8 && ok; ++c) {
+    const int ch = child[8 * p + c];
+    ok = child[8 * ch] < 0 && flags[ch] < 0;
+  }
+  for (int c = 0; c < 8 && ok; ++c) {
+    const int ch = child[8 * p + c];
+    for (int d = 0; d < 26 && ok; ++d) {
+      const int nb = nbr[26 * ch + d];
+      if (nb >= 0 && parent[nb] != p && (child[8 * nb] >= 0 || refv[nb])) ok = false;
+    }
+  }
+  derv[p] = ok ? 1 : 0;
+  if (ok) atomicAdd(cnt + 1, 1);
+}
+
+__global__ void k_rg_keep(int n, const int32_t *__restrict__ parent, const int8_t *__restrict__ derv,
+                          int32_t *__restrict__ keepv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int p = parent[b];
+  keepv[b] = (p >= 0 && derv[p]) ? 0 : 1;
+}
+
+// the Morton keys of the kept and of the refined boxes, compacted
+__global__ void k_rg_keys(int n, const uint64_t *__restrict__ morton, const int32_t *__restrict__ keepv,
+                          const int32_t *__restrict__ keep_pos, const int32_t *__restrict__ refv,
+                          const int32_t *__restrict__ ref_pos, uint64_t *__restrict__ kept_keys,
+                          uint64_t *__restrict__ ref_keys) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  if (keepv[b]) kept_keys[keep_pos[b]] = morton[b];
+  if (refv[b]) ref_keys[ref_pos[b]] = morton[b];
+}
+
+// new index, level, coordinates, key and source of every kept box and of
+// the 8 children of every refined box (8 threads per old box: thread 0
+// places the box itself when kept, thread c its child c when refined)
+__global__ void k_rg_place(int n, const int32_t *__restrict__ level, const int32_t *__restrict__ ijk,
+                           const uint64_t *__restrict__ morton, const int32_t *__restrict__ keepv,
+                           const int32_t *__restrict__ keep_pos, const int32_t *__restrict__ refv,
+                           const int32_t *__restrict__ ref_pos, const uint64_t *__restrict__ kept_keys,
+                           const uint64_t *__restrict__ ref_keys, RgLevels L, int32_t *__restrict__ nlev,
+                           int32_t *__restrict__ nijk, uint64_t *__restrict__ nkey, int32_t *__restrict__ nsrc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = t >> 3, c = t & 7;
+  if (b >= n) return;
+  const int l = level[b];
+  const uint64_t key = morton[b];
+  if (c == 0 && keepv[b]) {
+    // refined boxes of level l-1 whose key is below this box's parent key
+    const int below = l > 0 ? lower_bound_u64(ref_keys, L.ref[l - 1], L.ref[l], key >> 3) - L.ref[l - 1] : 0;
+    const int x = L.nw[l] + (keep_pos[b] - L.kept[l]) + 8 * below;
+    nlev[x] = l;
+    nijk[3 * x] = ijk[3 * b];
+    nijk[3 * x + 1] = ijk[3 * b + 1];
+    nijk[3 * x + 2] = ijk[3 * b + 2];
+    nkey[x] = key;
+    nsrc[x] = b;
+  }
+  if (refv[b]) {
+    const uint64_t ck = (key << 3) | (uint64_t)c;
+    const int below = lower_bound_u64(kept_keys, L.kept[l + 1], L.kept[l + 2], ck) - L.kept[l + 1];
+    const int x = L.nw[l + 1] + 8 * (ref_pos[b] - L.ref[l]) + c + below;
+    nlev[x] = l + 1;
+    nijk[3 * x] = 2 * ijk[3 * b] + (c & 1);
+    nijk[3 * x + 1] = 2 * ijk[3 * b + 1] + ((c >> 1) & 1);
+    nijk[3 * x + 2] = 2 * ijk[3 * b + 2] + (c >> 2);
+    nkey[x] = ck;
+    nsrc[x] = -1;
+  }
+}
+
+// parent and children of every new box by binary search in the new keys
+__global__ void k_rg_links(int m, const int32_t *__restrict__ nlev, const uint64_t *__restrict__ nkey, RgLevels L,
+                           int nlevels, int32_t *__restrict__ npar, int32_t *__restrict__ nchl) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m) return;
+  const int l = nlev[b];
+  const uint64_t key = nkey[b];
+  int p = -1;
+  if (l > 0) {
+    const int i = lower_bound_u64(nkey, L.nw[l - 1], L.nw[l], key >> 3);
+    if (i < L.nw[l] && nkey[i] == key >> 3) p = i;
+  }
+  npar[b] = p;
+  int c0 = -1;
+  if (l + 1 < nlevels) {
+    const int i = lower_bound_u64(nkey, L.nw[l + 1], L.nw[l + 2], key << 3);
+    if (i < L.nw[l + 2] && nkey[i] == key << 3) c0 = i;
+  }
+  for (int c = 0; c < 8; ++c) nchl[8 * b + c] = c0 >= 0 ? c0 + c : -1;
+}
+
+// boxes without a source (new children), compacted
+__global__ void k_rg_fresh_flag(int m, const int32_t *__restrict__ nsrc, int32_t *__restrict__ f) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < m) f[b] = nsrc[b] < 0 ? 1 : 0;
+}
+
+__global__ void k_rg_compact(int m, const int32_t *__restrict__ f, const int32_t *__restrict__ pos,
+                             int32_t *__restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < m && f[b]) out[pos[b]] = b;
+}
 
 }  // namespace
 
@@ -217,139 +361,108 @@ extern "C" int sm_refine(sm_ctx *ctx, const int8_t *flags, int *n_boxes) {
 
 int sm_regrid_impl(sm_ctx *ctx, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
   SM_RANGE();
-  if (!ctx || !flags) return SM_EINVAL;
+  if (!ctx) return SM_EINVAL;
   if (!ctx->arena || ctx->n_levels == 0) return sm_fail(ctx, SM_ESTATE, "octree not built");
   int st;
   // densities of refined boxes = mean of their children, on the old mesh
   if ((st = sm_restrict_pair(ctx, ctx->nbuf[ctx->ncur], ctx->ibuf[ctx->ncur]))) return st;
-  const int n = ctx->n_boxes;
-  std::vector<int32_t> lev(n), ijk(3 * (size_t)n), par(n), chl(8 * (size_t)n), nbr(26 * (size_t)n);
-  std::vector<uint64_t> mort(n);
-  SM_CK(cudaMemcpyAsync(lev.data(), ctx->level, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ijk.data(), ctx->ijk, 12 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
-  SM_CK(cudaMemcpyAsync(par.data(), ctx->parent, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
-  SM_CK(cudaMemcpyAsync(chl.data(), ctx->child, 32 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
-  SM_CK(cudaMemcpyAsync(nbr.data(), ctx->nbr, 104 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
-  SM_CK(cudaMemcpyAsync(mort.data(), ctx->morton, 8 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+  const int n = ctx->n_boxes, M = ctx->cfg.max_boxes, T = 256;
+  // flags: from the host, or (NULL) those the last sm_refine_flags left on the device
+  if (flags) SM_CK(cudaMemcpyAsync(ctx->dev_flags, flags, n, cudaMemcpyHostToDevice, ctx->stream));
+  // scratch in the residual array (not carried over by a regrid)
+  char *w = reinterpret_cast<char *>(ctx->res);
+  auto take = [&](size_t bytes) {
+    char *p = w;
+    w += (bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  int32_t *refv = (int32_t *)take(4 * (size_t)n), *keepv = (int32_t *)take(4 * (size_t)n);
+  int32_t *ref_pos = (int32_t *)take(4 * ((size_t)n + 1)), *keep_pos = (int32_t *)take(4 * ((size_t)n + 1));
+  int8_t *derv = (int8_t *)take((size_t)n);
+  uint64_t *ref_keys = (uint64_t *)take(8 * (size_t)n), *kept_keys = (uint64_t *)take(8 * (size_t)n);
+  int32_t *nlev = (int32_t *)take(4 * (size_t)M), *nijk = (int32_t *)take(12 * (size_t)M);
+  uint64_t *nkey = (uint64_t *)take(8 * (size_t)M);
+  int32_t *nsrc = (int32_t *)take(4 * (size_t)M), *npar = (int32_t *)take(4 * (size_t)M);
+  int32_t *nchl = (int32_t *)take(32 * (size_t)M);
+  int32_t *ff = (int32_t *)take(4 * (size_t)M), *fpos = (int32_t *)take(4 * ((size_t)M + 1));
+  int32_t *cnt = ctx->dev_count;
+  SM_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int32_t), ctx->stream));
+  const int gb = (n + T - 1) / T;
+  k_rg_refine<<<gb, T, 0, ctx->stream>>>(n, ctx->level, ctx->child, ctx->nbr, ctx->dev_flags, ctx->lmax, refv, cnt);
+  k_rg_derefine<<<gb, T, 0, ctx->stream>>>(n, ctx->child, ctx->parent, ctx->nbr, ctx->dev_flags, refv, derv, cnt);
+  k_rg_keep<<<gb, T, 0, ctx->stream>>>(n, ctx->parent, derv, keepv);
+  ctx->n_launch += 3;
+  SM_CKL("regrid decisions");
+  if ((st = sm_exclusive_scan(ctx, refv, ref_pos, n))) return st;
+  if ((st = sm_exclusive_scan(ctx, keepv, keep_pos, n))) return st;
+  // counts: dropped, derefined, and the list offsets at the old level offsets
+  const int L0 = ctx->n_levels;
+  std::vector<int32_t> hk(L0 + 1), hr(L0 + 1);
+  int32_t hc[2];
+  SM_CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, ctx->stream));
+  for (int l = 0; l <= L0; ++l) {
+    SM_CK(cudaMemcpyAsync(&hk[l], keep_pos + ctx->level_off[l], 4, cudaMemcpyDeviceToHost, ctx->stream));
+    SM_CK(cudaMemcpyAsync(&hr[l], ref_pos + ctx->level_off[l], 4, cudaMemcpyDeviceToHost, ctx->stream));
+  }
   SM_CK(cudaStreamSynchronize(ctx->stream));
-  auto leafb = [&](int b) { return chl[8 * (size_t)b] < 0; };
-  // refinement: flagged leaves below the maximum level whose 26 neighbour
-  // positions of their level hold a box or lie outside the domain
-  std::vector<char> ref(n, 0), der(n, 0);
-  int nref = 0, nder = 0, ndrop = 0;
-  for (int b = 0; b < n; ++b) {
-    if (!leafb(b) || flags[b] <= 0 || lev[b] >= ctx->lmax) continue;
-    bool ok = true;
-    for (int d = 0; d < 26; ++d) ok = ok && nbr[26 * (size_t)b + d] != -2;
-    if (ok) ref[b] = 1, ++nref;
-    else ++ndrop;
-  }
-  // derefinement: boxes whose 8 children are leaves flagged -1, unless a
-  // non-sibling neighbour of a child has or gets children
-  for (int p = 0; p < n; ++p) {
-    if (leafb(p)) continue;
-    bool ok = true;
-    for (int c = 0; c < 8 && ok; ++c) {
-      const int ch = chl[8 * (size_t)p + c];
-      ok = leafb(ch) && flags[ch] < 0;
-    }
-    for (int c = 0; c < 8 && ok; ++c) {
-      const int ch = chl[8 * (size_t)p + c];
-      for (int d = 0; d < 26 && ok; ++d) {
-        const int nb = nbr[26 * (size_t)ch + d];
-        if (nb >= 0 && par[nb] != p && (!leafb(nb) || ref[nb])) ok = false;
-      }
-    }
-    if (ok) der[p] = 1, ++nder;
-  }
+  const int nref = hr[L0], nder = hc[1];
   if (n_refined) *n_refined = nref;
   if (n_derefined) *n_derefined = nder;
-  if (n_dropped) *n_dropped = ndrop;
+  if (n_dropped) *n_dropped = hc[0];
   if (nref == 0 && nder == 0) return SM_OK;
-  // new box set in (level, Morton) order
-  std::vector<Entry> e;
-  e.reserve(n + 8 * (size_t)nref);
-  for (int b = 0; b < n; ++b) {
-    if (par[b] >= 0 && der[par[b]]) continue;
-    e.push_back({lev[b], ijk[3 * (size_t)b], ijk[3 * (size_t)b + 1], ijk[3 * (size_t)b + 2], b, mort[b]});
-    if (!ref[b])
-      continue;
-    for (int c = 0; c < 8; ++c) {
-      const int ci = 2 * ijk[3 * (size_t)b] + (c & 1), cj = 2 * ijk[3 * (size_t)b + 1] + ((c >> 1) & 1),
-                ck = 2 * ijk[3 * (size_t)b + 2] + (c >> 2);
-      e.push_back({lev[b] + 1, ci, cj, ck, -1, h_morton(ci, cj, ck)});
-    }
+  RgLevels L;
+  int nlevels = 0, m = 0;
+  for (int l = 0; l < SM_MAX_LEVELS + 2; ++l) {
+    const int kept = l < L0 ? hk[l + 1] - hk[l] : 0;
+    const int born = (l >= 1 && l - 1 < L0) ? 8 * (hr[l] - hr[l - 1]) : 0;
+    L.kept[l] = l <= L0 ? hk[l] : hk[L0];
+    L.ref[l] = l <= L0 ? hr[l] : hr[L0];
+    L.nw[l] = m;
+    m += kept + born;
+    if (kept + born > 0) nlevels = l + 1;
   }
-  std::sort(e.begin(), e.end(), [](const Entry &a, const Entry &b) {
-    return a.lev != b.lev ? a.lev < b.lev : a.key < b.key;
-  });
-  const int m = (int)e.size();
-  if (m > ctx->cfg.max_boxes) return sm_fail(ctx, SM_ENOMEM, "max_boxes %d exceeded (%d needed)", ctx->cfg.max_boxes, m);
-  int nlev = 0;
-  for (const Entry &x : e) nlev = std::max(nlev, x.lev + 1);
-  int off[SM_MAX_LEVELS + 2];
-  for (int l = 0, b = 0; l <= SM_MAX_LEVELS + 1; ++l) {
-    while (b < m && e[b].lev < l) ++b;
-    off[l] = b;
-  }
-  auto find = [&](int l, uint64_t key) -> int {
-    if (l < 0 || l >= nlev) return -1;
-    int a = off[l], z = off[l + 1] - 1;
-    while (a <= z) {
-      const int mid = (a + z) / 2;
-      if (e[mid].key == key) return mid;
-      if (e[mid].key < key) a = mid + 1;
-      else z = mid - 1;
-    }
-    return -1;
-  };
-  std::vector<int32_t> nlv(m), nijk(3 * (size_t)m), npar(m), nchl(8 * (size_t)m, -1), src(m), fresh;
-  std::vector<uint64_t> nmort(m);
-  for (int b = 0; b < m; ++b) {
-    nlv[b] = e[b].lev;
-    nijk[3 * (size_t)b] = e[b].i;
-    nijk[3 * (size_t)b + 1] = e[b].j;
-    nijk[3 * (size_t)b + 2] = e[b].k;
-    nmort[b] = e[b].key;
-    src[b] = e[b].src;
-    if (e[b].src < 0) fresh.push_back(b);
-    npar[b] = e[b].lev > 0 ? find(e[b].lev - 1, e[b].key >> 3) : -1;
-    if (find(e[b].lev + 1, e[b].key << 3) >= 0)
-      for (int c = 0; c < 8; ++c) nchl[8 * (size_t)b + c] = find(e[b].lev + 1, (e[b].key << 3) | (uint64_t)c);
-  }
+  if (m > M) return sm_fail(ctx, SM_ENOMEM, "max_boxes %d exceeded (%d needed)", M, m);
+  if (nlevels > SM_MAX_LEVELS) return sm_fail(ctx, SM_EINVAL, "more than %d levels", SM_MAX_LEVELS);
+  k_rg_keys<<<gb, T, 0, ctx->stream>>>(n, ctx->morton, keepv, keep_pos, refv, ref_pos, kept_keys, ref_keys);
+  k_rg_place<<<(8 * n + T - 1) / T, T, 0, ctx->stream>>>(n, ctx->level, ctx->ijk, ctx->morton, keepv, keep_pos, refv,
+                                                         ref_pos, kept_keys, ref_keys, L, nlev, nijk, nkey, nsrc);
+  k_rg_links<<<(m + T - 1) / T, T, 0, ctx->stream>>>(m, nlev, nkey, L, nlevels, npar, nchl);
+  k_rg_fresh_flag<<<(m + T - 1) / T, T, 0, ctx->stream>>>(m, nsrc, ff);
+  ctx->n_launch += 4;
+  SM_CKL("regrid box set");
+  if ((st = sm_exclusive_scan(ctx, ff, fpos, m))) return st;
+  k_rg_compact<<<(m + T - 1) / T, T, 0, ctx->stream>>>(m, ff, fpos, ctx->scan_a);
+  ++ctx->n_launch;
   sm_drop_graphs(ctx);
   // fields to the new numbering (new boxes zero), through the scratch array
   // of the previous cycle's potential
-  int32_t *dsrc = ctx->scan_b, *dlist = ctx->scan_a;
-  SM_CK(cudaMemcpyAsync(dsrc, src.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
   double *vars[6] = {ctx->phi, ctx->rhs, ctx->emag, ctx->rho, ctx->nbuf[ctx->ncur], ctx->ibuf[ctx->ncur]};
   for (double *x : vars) {
-    k_regrid_gather<<<m, CELLS, 0, ctx->stream>>>(dsrc, x, ctx->old);
+    k_regrid_gather<<<m, CELLS, 0, ctx->stream>>>(nsrc, x, ctx->old);
     ++ctx->n_launch;
     SM_CK(cudaMemcpyAsync(x, ctx->old, sizeof(double) * CELLS * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   SM_CKL("regrid gather");
-  // tables of the new mesh; neighbours and the leaf list on the device
-  SM_CK(cudaMemcpyAsync(ctx->level, nlv.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ctx->ijk, nijk.data(), 12 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ctx->morton, nmort.data(), 8 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ctx->parent, npar.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
-  SM_CK(cudaMemcpyAsync(ctx->child, nchl.data(), 32 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
+  // tables of the new mesh; neighbours and the leaf list from them
+  SM_CK(cudaMemcpyAsync(ctx->level, nlev, 4 * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
+  SM_CK(cudaMemcpyAsync(ctx->ijk, nijk, 12 * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
+  SM_CK(cudaMemcpyAsync(ctx->morton, nkey, 8 * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
+  SM_CK(cudaMemcpyAsync(ctx->parent, npar, 4 * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
+  SM_CK(cudaMemcpyAsync(ctx->child, nchl, 32 * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->n_boxes = m;
-  ctx->n_levels = nlev;
-  for (int l = 0; l <= SM_MAX_LEVELS; ++l) ctx->level_off[l] = off[l];
-  for (int l = 0; l < nlev; ++l)
+  ctx->n_levels = nlevels;
+  for (int l = 0; l <= SM_MAX_LEVELS; ++l) ctx->level_off[l] = L.nw[l];
+  for (int l = 0; l < nlevels; ++l)
     if ((st = sm_build_neighbours(ctx, l))) return st;
-  if ((st = sm_rebuild_leaves(ctx))) return st;
-  // potential and densities of the new boxes from their parents
-  if (!fresh.empty()) {
-    SM_CK(cudaMemcpyAsync(dlist, fresh.data(), 4 * fresh.size(), cudaMemcpyHostToDevice, ctx->stream));
-    k_regrid_prolong<<<(int)fresh.size(), CELLS, 0, ctx->stream>>>(dlist, ctx->parent, ctx->ijk, ctx->nbr6, ctx->bc,
-                                                                  ctx->phi, ctx->nbuf[ctx->ncur],
-                                                                  ctx->ibuf[ctx->ncur], ctx->dscal + SC_ERR);
+  // the fresh-box list (scan_a) is read before the leaf rebuild reuses it
+  if (nref > 0) {
+    k_regrid_prolong<<<8 * nref, CELLS, 0, ctx->stream>>>(ctx->scan_a, ctx->parent, ctx->ijk, ctx->nbr6, ctx->bc,
+                                                         ctx->phi, ctx->nbuf[ctx->ncur], ctx->ibuf[ctx->ncur],
+                                                         ctx->dscal + SC_ERR);
     ++ctx->n_launch;
     SM_CKL("regrid prolong");
   }
+  if ((st = sm_rebuild_leaves(ctx))) return st;
   SM_CK(cudaStreamSynchronize(ctx->stream));
   return SM_OK;
 }

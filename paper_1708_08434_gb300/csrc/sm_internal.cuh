@@ -404,6 +404,7 @@ inline cudaError_t sm_launch(sm_ctx *ctx, void (*k)(KArgs...), dim3 grid, dim3 b
 // entry points implemented in the other translation units
 int sm_mg_fill_cf(sm_ctx *ctx, double *var, int level, int homog);
 int sm_fill_all_cf(sm_ctx *ctx, double *var);
+int sm_exclusive_scan(sm_ctx *ctx, const int32_t *in, int32_t *out, int n);
 int sm_restrict_pair(sm_ctx *ctx, double *a, double *b);
 void sm_drop_graphs(sm_ctx *ctx);
 int sm_rebuild_leaves(sm_ctx *ctx);
