@@ -333,6 +333,8 @@ def large_mesh():
     for prec, name in ((0, "fp64"), (pkg.MIXED, "mixed")):
         t0 = time.perf_counter()
         g = pkg.Solver(dom, max_boxes=1 << 18, precision=prec)
+        if ROW_KERNELS is not None:
+            g.set_row_kernels(ROW_KERNELS)
         g.build_octree()
         synth.refine_all(dom, st, g.level_ijk, g.refine_level)
         g.set_table(synth.coefficient_table())
@@ -375,7 +377,7 @@ def large_mesh():
             r["colour_pass"] = {"avg_launch_us": round(us, 2), "launches": n,
                                 "gbs": round(by / (us * 1e-6) / 1e9, 1),
                                 "hbm_frac": round(by / (us * 1e-6) / 1e9 / peak, 4),
-                                "kernels": "k_fcolor_rows on levels of >= 2048 boxes, k_fcolor below"}
+                                "kernels": "k_fcolor_rows on levels of >= 2048 boxes, k_fcolor_half below"}
         out[name] = r
         g.close()
         del g
@@ -1042,6 +1044,8 @@ def bench_learned_c4(n_rec=100, n_eval=100, epochs=10):
 
     def solver(prec):
         g = pkg.Solver(dom, max_boxes=1 << 18, precision=prec)
+        if ROW_KERNELS is not None:
+            g.set_row_kernels(ROW_KERNELS)
         g.build_octree()
         synth.refine_all(dom, st, g.level_ijk, g.refine_level)
         g.set_table(tab)

@@ -569,6 +569,96 @@ __global__ void __launch_bounds__(64 * RBOX, 16 / RBOX) k_fcolor_rows(int lo, in
   fx_flag(bad && live, sc);
 }
 
+// The same colour pass with two threads per x row (128 per box): thread
+// (r, h) updates the cells q = 2h, 2h + 1 of row r, with 16-byte loads and
+// stores of its half rows; the other colour's own row is staged by the two
+// halves and the value across the middle of the row read back from shared
+// memory.  Half the work per thread of k_fcolor_rows and the warp count of
+// the box kernel, for levels that are one partial wave of blocks.
+__device__ __forceinline__ void half_ld(const long long *p, long long (&v)[2]) {
+  const longlong2 a = *reinterpret_cast<const longlong2 *>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+}
+
+__global__ void __launch_bounds__(128) k_fcolor_half(int lo, int color, long long *__restrict__ phx,
+                                                     const long long *__restrict__ gx,
+                                                     const long long *__restrict__ ghx,
+                                                     const int32_t *__restrict__ nbr6, Bc bc,
+                                                     unsigned long long *sc) {
+  __shared__ longlong2 srow[64][2];  // the other colour's rows: half h of row r at [r][h]
+  const int t = threadIdx.x, r = t >> 1, h = t & 1;
+  const int b = lo + blockIdx.x;
+  const int j = r & 7, k = r >> 3, p = (color + j + k) & 1, oc = color ^ 1;
+  // this half holds the row's x-face cell when p == h (q = 0 for p = 0, q = 3 for p = 1)
+  const bool xface = p == h;
+  const int fyf = j == 0 ? 2 : (j == NC - 1 ? 3 : -1), fzf = k == 0 ? 4 : (k == NC - 1 ? 5 : -1);
+  const int nbx = xface ? __ldg(nbr6 + 6 * b + p) : 0;
+  const int nby = fyf >= 0 ? __ldg(nbr6 + 6 * b + fyf) : 0;
+  const int nbz = fzf >= 0 ? __ldg(nbr6 + 6 * b + fzf) : 0;
+  pdl_wait();
+  const size_t base = (size_t)b * CELLS;
+  const int ro = 4 * j + 32 * k + 2 * h;  // first of this half's two entries
+  long long G[2], R[2];
+  half_ld(gx + base + (color << 8) + ro, G);
+  half_ld(phx + base + (oc << 8) + ro, R);
+  long long own[2] = {0, 0};
+  if (nbx < 0 || nby < 0 || nbz < 0) half_ld(phx + base + (color << 8) + ro, own);
+  long long ym[2], yp[2], zm[2], zp[2];
+  auto ghost2 = [&](int nb, int f, size_t gi, int gs, long long (&g)[2]) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (nb == -1) g[e] = bc.type[f] ? fx_2g(sc, f) - own[e] : own[e];
+      else g[e] = fx_div6(2 * own[e] + ghx[gi + (size_t)gs * e]);
+    }
+  };
+  // face cell indices of q = 2h: y faces k + 8 i, z faces i + 8 j, i = 2q + p
+  const int i0 = 4 * h + p;
+  if (j == 0) {
+    if (nby >= 0) half_ld(phx + (size_t)nby * CELLS + (oc << 8) + 4 * (NC - 1) + 32 * k + 2 * h, ym);
+    else ghost2(nby, 2, (size_t)(6 * b + 2) * FACE + k + NC * i0, 2 * NC, ym);
+  } else if (j == NC - 1) {
+    if (nby >= 0) half_ld(phx + (size_t)nby * CELLS + (oc << 8) + 32 * k + 2 * h, yp);
+    else ghost2(nby, 3, (size_t)(6 * b + 3) * FACE + k + NC * i0, 2 * NC, yp);
+  }
+  if (k == 0) {
+    if (nbz >= 0) half_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j + 32 * (NC - 1) + 2 * h, zm);
+    else ghost2(nbz, 4, (size_t)(6 * b + 4) * FACE + i0 + NC * j, 2, zm);
+  } else if (k == NC - 1) {
+    if (nbz >= 0) half_ld(phx + (size_t)nbz * CELLS + (oc << 8) + 4 * j + 2 * h, zp);
+    else ghost2(nbz, 5, (size_t)(6 * b + 5) * FACE + i0 + NC * j, 2, zp);
+  }
+  long long xg = 0;
+  if (xface) {
+    const long long oe = p ? own[1] : own[0];
+    if (nbx >= 0) xg = phx[(size_t)nbx * CELLS + (oc << 8) + 4 * j + 32 * k + (p ? 0 : 3)];
+    else if (nbx == -1) xg = bc.type[p] ? fx_2g(sc, p) - oe : oe;
+    else xg = fx_div6(2 * oe + ghx[(size_t)(6 * b + p) * FACE + j + NC * k]);
+  }
+  srow[r][h] = make_longlong2(R[0], R[1]);
+  __syncthreads();
+  if (j > 0) half_ld(reinterpret_cast<const long long *>(&srow[r - 1][h]), ym);
+  if (j < NC - 1) half_ld(reinterpret_cast<const long long *>(&srow[r + 1][h]), yp);
+  if (k > 0) half_ld(reinterpret_cast<const long long *>(&srow[r - 8][h]), zm);
+  if (k < NC - 1) half_ld(reinterpret_cast<const long long *>(&srow[r + 8][h]), zp);
+  // x neighbours of q = 2h + e: p = 0 -> R[q - 1], R[q]; p = 1 -> R[q], R[q + 1];
+  // the entry beyond this half is the other half's nearest one (or the face value)
+  const longlong2 other = srow[r][h ^ 1];
+  const long long left = h ? other.y : xg;    // entry q = 2h - 1 (p = 0 uses it)
+  const long long right = h ? xg : other.x;   // entry q = 2h + 2 (p = 1 uses it)
+  bool bad = false;
+  long long v[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const long long xm = p ? R[e] : (e == 0 ? left : R[0]);
+    const long long xp = p ? (e == 1 ? right : R[1]) : R[e];
+    v[e] = fx_div6(xm + xp + ym[e] + yp[e] + zm[e] + zp[e] + 6 * G[e]);
+    bad |= fx_bad(v[e]);
+  }
+  *reinterpret_cast<longlong2 *>(phx + base + (color << 8) + ro) = make_longlong2(v[0], v[1]);
+  fx_flag(bad, sc);
+}
+
 // ---------------------------------------------------------------------------
 // residual and restriction by rows: one thread per x row of 8 cells
 // ---------------------------------------------------------------------------

@@ -1557,8 +1557,9 @@ static int fx_epilogue(sm_ctx *ctx) {
 // nu red-black sweeps of level l (two colour passes each, in place).  A
 // level of at least ctx->rows_min boxes runs the row kernel (4 cells and
 // 16-byte row loads per thread, fewer instructions per cell); a level that
-// is one partial wave of blocks runs the box kernel (2 cells per thread,
-// twice the warps to hide its load latency).  Both give the same bits.
+// is one partial wave of blocks runs the half-row kernel (2 cells per
+// thread, twice the warps to hide its load latency).  Both give the bits
+// of the box kernel (fx_color_box, which the persistent kernel runs).
 static int fx_smooth(sm_ctx *ctx, int l, int nu) {
   const int n = lvl_n(ctx, l);
   if (!n) return SM_OK;
@@ -1568,8 +1569,8 @@ static int fx_smooth(sm_ctx *ctx, int l, int nu) {
         sm_launch(ctx, fx::k_fcolor_rows, (n + fx::RBOX - 1) / fx::RBOX, 64 * fx::RBOX, 0, ctx->level_off[l], n,
                   color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6, ctx->bc, ctx->dscal);
       else
-        sm_launch(ctx, fx::k_fcolor, n, GT, 0, ctx->level_off[l], color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6,
-                  ctx->bc, ctx->dscal);
+        sm_launch(ctx, fx::k_fcolor_half, n, 128, 0, ctx->level_off[l], color, ctx->phx, ctx->gx, ctx->ghx,
+                  ctx->nbr6, ctx->bc, ctx->dscal);
     }
   SM_CKL("rbgs");
   return SM_OK;
