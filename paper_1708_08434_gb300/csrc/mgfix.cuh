@@ -978,6 +978,101 @@ __global__ void __launch_bounds__(128) k_fprolong_rows(int lo, int n, int mode, 
   fx_flag(bad && live, sc);
 }
 
+// Prolongation with two threads per fine x row (128 per box, small
+// levels): thread (r, h) forms the 4 fine cells i = 4h .. 4h + 3 of row r
+// and updates them with one 16-byte load and store per colour.  Staging,
+// Ghat values and the leaf-residual blocks as in k_fprolong; the same bits.
+__global__ void __launch_bounds__(GT) k_fprolong_half(int lo, int n, int mode, long long *__restrict__ phx,
+                                                      const long long *__restrict__ oldx,
+                                                      long long *__restrict__ ghx,
+                                                      const int32_t *__restrict__ nbr6,
+                                                      const int32_t *__restrict__ parent,
+                                                      const int32_t *__restrict__ ijk, Bc bc,
+                                                      unsigned long long *sc, FxNorm nm) {
+  __shared__ long long sm[1000];  // the 216-value coarse region, or a norm block's staged box
+  __shared__ unsigned long long red[GT / 32];
+  const Grp g = block_grp();
+  if ((int)blockIdx.x >= n) {
+    const int b = __ldg(nm.leaf + blockIdx.x - n);
+    const Nb nb = load_nb(g, nbr6, b);
+    pdl_wait();
+    const double nq = -fx_q(fx_E(sc)) * nm.inv_h2;
+    const unsigned long long m = fx_resid_max_box(g, sm, b, phx, nm.rhs, ghx, nb, bc, sc, nq);
+    group_umax_to(g, nm.slot, m, red);
+    return;
+  }
+  const int t = threadIdx.x, b = lo + blockIdx.x;
+  const int P = __ldg(parent + b);
+  const int ox = __ldg(ijk + 3 * b) & 1, oy = __ldg(ijk + 3 * b + 1) & 1, oz = __ldg(ijk + 3 * b + 2) & 1;
+  long long *sp = sm;
+  auto val = [&](int Q, int c) {
+    const size_t x = (size_t)Q * CELLS + xsplit(c);
+    return mode ? phx[x] : phx[x] - oldx[x];
+  };
+  auto reg = [](int x, int y, int z) { return x + 6 * y + 36 * z; };
+  pdl_wait();
+  if (t < 64) {
+    const int x = t & 3, y = (t >> 2) & 3, z = t >> 4;
+    sp[reg(x + 1, y + 1, z + 1)] = val(P, cidx(4 * ox + x, 4 * oy + y, 4 * oz + z));
+  }
+  // face neighbours of the parent region (96 items: threads 64-127, then 0-31)
+  const int e = t >= 64 ? t - 64 : t + 64;
+  if (e < 96) {
+    const int F = e >> 4, E = F >> 1, S = (F & 1) ? 1 : -1;
+    const int u = e & 3, w = (e >> 2) & 3, ce = S > 0 ? 5 : 0;
+    const int rx = E == 0 ? ce : (E == 1 ? w + 1 : u + 1);
+    const int ry = E == 0 ? u + 1 : (E == 1 ? ce : w + 1);
+    const int rz = E == 0 ? w + 1 : (E == 1 ? u + 1 : ce);
+    const int lx = 4 * ox - 1 + rx, ly = 4 * oy - 1 + ry, lz = 4 * oz - 1 + rz;
+    const int le = E == 0 ? lx : (E == 1 ? ly : lz);
+    long long v;
+    if (le >= 0 && le < NC) {
+      v = val(P, cidx(lx, ly, lz));
+    } else {
+      const int Qn = __ldg(nbr6 + 6 * P + F);
+      if (Qn >= 0) {
+        const int wrap = S > 0 ? 0 : NC - 1;
+        v = val(Qn, cidx(E == 0 ? wrap : lx, E == 1 ? wrap : ly, E == 2 ? wrap : lz));
+      } else {
+        const long long ctr =
+            val(P, cidx(lx - (E == 0 ? S : 0), ly - (E == 1 ? S : 0), lz - (E == 2 ? S : 0)));
+        if (Qn == -1) {
+          v = bc.type[F] ? (mode ? fx_2g(sc, F) : 0) - ctr : ctr;
+        } else {
+          atomicOr(sc + SC_ERR, 1ull);
+          v = ctr;
+        }
+      }
+    }
+    sp[reg(rx, ry, rz)] = v;
+  }
+  const int r = t >> 1, h = t & 1, j = r & 7, k = r >> 3, p0 = (j + k) & 1;
+  const size_t base = (size_t)b * CELLS;
+  const int ro = 4 * j + 32 * k + 2 * h;
+  long long a[2], c[2];
+  half_ld(phx + base + ro, a);        // colour 0, entries q = 2h, 2h + 1
+  half_ld(phx + base + 256 + ro, c);  // colour 1
+  g.sync();
+  bool bad = false;
+  {
+    const int y = (j >> 1) + 1, z = (k >> 1) + 1, sy = (j & 1) ? 6 : -6, sz = (k & 1) ? 36 : -36;
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) {
+      const int i = 4 * h + e4;
+      const int q = reg((i >> 1) + 1, y, z);
+      const long long v = fx_rdiv<4>(sp[q] + sp[q + ((i & 1) ? 1 : -1)] + sp[q + sy] + sp[q + sz]);
+      // cell i is entry e4 >> 1 of colour 0 when (i + j + k) is even, else of colour 1
+      long long &cell = ((e4 + p0) & 1) ? c[e4 >> 1] : a[e4 >> 1];
+      cell = mode ? v : cell + v;
+      bad |= fx_bad(cell);
+    }
+  }
+  *reinterpret_cast<longlong2 *>(phx + base + ro) = make_longlong2(a[0], a[1]);
+  *reinterpret_cast<longlong2 *>(phx + base + 256 + ro) = make_longlong2(c[0], c[1]);
+  fx_cf_faces_box(t, GT, phx, ghx, nbr6, parent, ijk, bc, sc, b, sc + SC_ERR);
+  fx_flag(bad, sc);
+}
+
 // Ghat values of the refinement faces of boxes [lo, lo + grid), 64 threads
 // per box
 __global__ void __launch_bounds__(64) k_ffill_cf(int lo, const long long *__restrict__ phx, long long *__restrict__ ghx,

@@ -1603,7 +1603,7 @@ static int fx_prolong(sm_ctx *ctx, int l, int mode, fx::FxNorm nm) {
     sm_launch(ctx, fx::k_fprolong_rows, (n + 1) / 2 + nm.n, 128, 0, ctx->level_off[l], n, mode, ctx->phx,
               (const long long *)ctx->old, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal, nm);
   else
-    sm_launch(ctx, fx::k_fprolong, n + nm.n, GT, 0, ctx->level_off[l], n, mode, ctx->phx,
+    sm_launch(ctx, fx::k_fprolong_half, n + nm.n, GT, 0, ctx->level_off[l], n, mode, ctx->phx,
               (const long long *)ctx->old, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal, nm);
   SM_CKL("prolong");
   return SM_OK;
