@@ -39,7 +39,8 @@ constexpr int NW1 = 16 * 2 * 27, NW2 = 16 * 16 * 27, NW3 = 16 * 27;
 constexpr int O_W1 = 0, O_B1 = NW1, O_W2 = O_B1 + 16, O_B2 = O_W2 + NW2, O_W3 = O_B2 + 16, O_B3 = O_W3 + NW3;
 constexpr int NP = O_B3 + 1;  // 8241 parameters
 constexpr int NPOS = 1000;    // 10^3 positions of a box with one ghost layer
-constexpr int CT = 256;       // threads per CTA
+constexpr int CT = 256;       // threads per CTA (inference, sample preparation)
+constexpr int TT = 512;       // threads per CTA of the training kernel (one CTA per SM)
 constexpr int MAX_DEBUG = 16;
 
 typedef __nv_bfloat16 bf16;
@@ -307,33 +308,42 @@ __device__ void zero_acts(FwdS &F) {
 // (per box [16][512] / [512], may be null) receive z1, a1, z2, a2.  False
 // (and bit 0 of *tc.err set) when the tensor cores' completion wait ran out;
 // the caller then stops.
+template <int NT>  // threads of the block: 512 / NT voxels per thread
 __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, float *a1d, float *z2d,
                             float *a2d) {
+  constexpr int VPT = 512 / NT;
   const int t = threadIdx.x;
-  // layer 1: valid 3^3 conv 2 -> 16 on CUDA cores, voxels t and t + CT per
+  // layer 1: valid 3^3 conv 2 -> 16 on CUDA cores, voxels t + r NT per
   // thread (the 32 weights of a tap are broadcast 16-byte loads)
   {
-    const int p0 = Pos(t), p1 = Pos(t + CT);
-    float acc[2][16];
+    int pv[VPT];
+    float acc[VPT][16];
 #pragma unroll
-    for (int co = 0; co < 16; ++co) acc[0][co] = acc[1][co] = N.b1[co];
+    for (int r = 0; r < VPT; ++r) {
+      pv[r] = Pos(t + r * NT);
+#pragma unroll
+      for (int co = 0; co < 16; ++co) acc[r][co] = N.b1[co];
+    }
     for (int tp = 0; tp < 27; ++tp) {
       const int off = Off(tp);
-      const float2 xa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (p0 + off)));
-      const float2 xb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (p1 + off)));
+      float2 xv[VPT];
+#pragma unroll
+      for (int r = 0; r < VPT; ++r)
+        xv[r] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(F.x + 2 * (pv[r] + off)));
       const float4 *wt = reinterpret_cast<const float4 *>(N.w1 + 32 * tp);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const float4 wv = wt[k];  // W1[2k][0], W1[2k][1], W1[2k+1][0], W1[2k+1][1]
-        acc[0][2 * k] += wv.x * xa.x + wv.y * xa.y;
-        acc[0][2 * k + 1] += wv.z * xa.x + wv.w * xa.y;
-        acc[1][2 * k] += wv.x * xb.x + wv.y * xb.y;
-        acc[1][2 * k + 1] += wv.z * xb.x + wv.w * xb.y;
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+          acc[r][2 * k] += wv.x * xv[r].x + wv.y * xv[r].y;
+          acc[r][2 * k + 1] += wv.z * xv[r].x + wv.w * xv[r].y;
+        }
       }
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int v = t + r * CT;
+    for (int r = 0; r < VPT; ++r) {
+      const int v = t + r * NT;
       bf16 *a1v = F.a1 + 8 * A1S((v & 7) + 1, 0, ((v >> 3) & 7) + 1 + 10 * ((v >> 6) + 1));
 #pragma unroll
       for (int co = 0; co < 16; ++co) {
@@ -365,10 +375,10 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
   }
   if (!tc_wait_all(tc)) return false;
   {
-    // warps 0-3 read tiles 0-2, warps 4-7 tiles 3-4, each its 32 lanes
+    // warp w reads lanes 32 (w % 4) .. +31 of the tiles j = w / 4 + k (NT / 128)
     const int warp = t >> 5, lane = t & 31, q = warp & 3;
     const int r = 32 * q + lane;  // row of the tile
-    for (int j = warp < 4 ? 0 : 3; j < (warp < 4 ? 3 : TC_TILES); ++j) {
+    for (int j = warp >> 2; j < TC_TILES; j += NT / 128) {
       float acc[16];
       tc_ld16(tc.taddr + ((uint32_t)(32 * q) << 16) + 16 * j, acc);
       const int R = 11 + 16 * j + (r >> 3), x = r & 7, y = R % 10 - 1, z = R / 10 - 1;
@@ -394,25 +404,30 @@ __device__ bool forward_box(const NetS &N, FwdS &F, TcState &tc, float *z1d, flo
   }
   tc_fence_before();
   __syncthreads();
-  // layer 3: same 3^3 conv 16 -> 1 on CUDA cores, voxels t and t + CT per
+  // layer 3: same 3^3 conv 16 -> 1 on CUDA cores, voxels t + r NT per
   // thread (a2 rows and the 16 weights of a tap as 16-byte loads)
   {
-    const int s0 = VS(t), s1 = VS(t + CT);
-    float o0 = N.b3, o1 = N.b3;
+    int sv[VPT];
+    float o[VPT];
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) {
+      sv[r] = VS(t + r * NT);
+      o[r] = N.b3;
+    }
     for (int tp = 0; tp < 27; ++tp) {
       const int so = SOff(tp);
-      float a[16], b[16], wv[16];
-      row16(F.a2, s0 + so, a);
-      row16(F.a2, s1 + so, b);
+      float wv[16];
       w16(N.w3 + 16 * tp, wv);
 #pragma unroll
-      for (int ci = 0; ci < 16; ++ci) {
-        o0 += wv[ci] * a[ci];
-        o1 += wv[ci] * b[ci];
+      for (int r = 0; r < VPT; ++r) {
+        float a[16];
+        row16(F.a2, sv[r] + so, a);
+#pragma unroll
+        for (int ci = 0; ci < 16; ++ci) o[r] += wv[ci] * a[ci];
       }
     }
-    F.out[t] = o0;
-    F.out[t + CT] = o1;
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) F.out[t + r * NT] = o[r];
   }
   __syncthreads();
   return true;
@@ -442,7 +457,7 @@ __global__ void __launch_bounds__(CT) k_cnn_forward(const bf16 *__restrict__ X, 
   for (int b = blockIdx.x; b < n; b += gridDim.x) {
     load_input(F, X + (size_t)b * NPOS * 2);
     float *d = (dbg && b < MAX_DEBUG) ? dbg + (size_t)b * 4 * 16 * 512 : nullptr;
-    if (!forward_box(N, F, tc, d, d ? d + 8192 : nullptr, d ? d + 16384 : nullptr, d ? d + 24576 : nullptr))
+    if (!forward_box<CT>(N, F, tc, d, d ? d + 8192 : nullptr, d ? d + 16384 : nullptr, d ? d + 24576 : nullptr))
       break;
     for (int v = threadIdx.x; v < 512; v += blockDim.x) out[(size_t)b * 512 + v] = F.out[v];
     __syncthreads();
@@ -462,8 +477,8 @@ struct TrainS {
   bf16 d2[D2_SLOTS * 8];  // dL/dz2 as three BF16 terms, zero outside the box interior
   float g3[512];          // dL/d out
   float grad[NG];
-  float part[CT];         // per-thread sums of dL/dz2 (layer-2 bias)
-  float red[CT / 32];
+  float part[TT];         // per-thread partial sums of the bias gradients
+  float red[TT / 32];
 };
 
 static_assert(offsetof(FwdS, a1) % 16 == 0 && offsetof(TrainS, d2) % 16 == 0 && offsetof(TrainS, w2t) % 16 == 0,
@@ -471,7 +486,7 @@ static_assert(offsetof(FwdS, a1) % 16 == 0 && offsetof(TrainS, d2) % 16 == 0 && 
 static_assert(((sizeof(NetS) + 127) & ~(size_t)127) + ((sizeof(FwdS) + 127) & ~(size_t)127) + sizeof(TrainS) <=
                   227 * 1024,
               "training shared memory");
-static_assert(sizeof(NetS) == 19140 && sizeof(FwdS) == 71456 && sizeof(TrainS) == 120164,
+static_assert(sizeof(NetS) == 19140 && sizeof(FwdS) == 71456 && sizeof(TrainS) == 121220,
               "layout the operand ranges were checked against");
 
 // position of W2[co][ci][t] in TrainS::w2t (ci is the N index, co the K index)
@@ -479,7 +494,7 @@ __device__ __forceinline__ int W2Ti(int t, int co, int ci) {
   return t * 256 + (co >> 3) * 128 + (ci >> 3) * 64 + (ci & 7) * 8 + (co & 7);
 }
 
-__global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, const float *__restrict__ target,
+__global__ void __launch_bounds__(TT, 1) k_cnn_train(const bf16 *__restrict__ X, const float *__restrict__ target,
                                                   const int *__restrict__ ids, int n, float inv_count,
                                                   const float *__restrict__ w, float *__restrict__ partial,
                                                   float *__restrict__ loss_partial, unsigned *__restrict__ err) {
@@ -494,22 +509,22 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
   TcState tc;
   tc_begin(tc, &mbar, &tslot, err, TRAIN_COLS);
   load_net(N, w);
-  for (int i = t; i < 27 * 256; i += CT) {
+  for (int i = t; i < 27 * 256; i += TT) {
     const int tp = i / 256, co = (i / 16) % 16, ci = i % 16;
     S.w2t[W2Ti(tp, co, ci)] = __float2bfloat16_rn(w[O_W2 + (co * 16 + ci) * 27 + tp]);
   }
   zero_acts(F);
   zero16(S.d2, sizeof(S.d2));
-  for (int i = t; i < NG; i += CT) S.grad[i] = 0.0f;
+  for (int i = t; i < NG; i += TT) S.grad[i] = 0.0f;
   float my_loss = 0.0f;
   bool wg_acc = false;  // the backward-weight accumulators hold a sum
   __syncthreads();
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int s = ids[it];
     load_input(F, X + (size_t)s * NPOS * 2);
-    if (!forward_box(N, F, tc, nullptr, nullptr, nullptr, nullptr)) break;
+    if (!forward_box<TT>(N, F, tc, nullptr, nullptr, nullptr, nullptr)) break;
     const float *tg = target + (size_t)s * 512;
-    for (int v = t; v < 512; v += CT) {
+    for (int v = t; v < 512; v += TT) {
       const float e = F.out[v] - tg[v];
       my_loss += e * e * inv_count;
       S.g3[v] = 2.0f * inv_count * e;
@@ -517,7 +532,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     __syncthreads();
     // layer 3 weights: warp w takes taps w, w + 8, ...; lane l the voxels
     // l + 32k, whose sums the warp then adds (fixed order); bias: warp 7
-    for (int tp = warp; tp < 27; tp += CT / 32) {
+    for (int tp = warp; tp < 27; tp += TT / 32) {
       const int so = SOff(tp);
       float acc[16];
 #pragma unroll
@@ -535,14 +550,14 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
 #pragma unroll
         for (int ci = 0; ci < 16; ++ci) S.grad[G_W3 + ci * 27 + tp] += acc[ci];
     }
-    if (warp == CT / 32 - 1) {
+    if (warp == TT / 32 - 1) {
       float acc = 0.0f;
       for (int v = lane; v < 512; v += 32) acc += S.g3[v];
       acc = warp_sum(acc);
       if (lane == 0) S.grad[G_B3] += acc;
     }
     // dL/dz2[u][c] = relu'(a2[u][c]) sum_t W3[c][t] g3[u - d_t] for voxels
-    // t and t + CT, stored as three BF16 terms h0 + h1 + h2 equal to the
+    // t + r TT, stored as three BF16 terms h0 + h1 + h2 equal to the
     // FP32 value (each remainder is exact in FP32 and the last has at most 8
     // significant bits)
     {
@@ -550,8 +565,8 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
 #pragma unroll
       for (int c = 0; c < 16; ++c) bsum[c] = 0.0f;
 #pragma unroll 1
-      for (int r = 0; r < 2; ++r) {
-        const int u = t + r * CT, ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
+      for (int r = 0; r < 512 / TT; ++r) {
+        const int u = t + r * TT, ux = u & 7, uy = (u >> 3) & 7, uz = u >> 6;
         float acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
@@ -629,7 +644,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     wg_acc = true;
     if (t < 16) {
       float acc = 0.0f;
-      for (int i = 0; i < CT / 32; ++i) acc += S.part[16 * i + t];
+      for (int i = 0; i < TT / 32; ++i) acc += S.part[16 * i + t];
       S.grad[G_B2 + t] += acc;
     }
     if (!tc_wait_all(tc)) break;
@@ -638,7 +653,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     {
       float *d1 = reinterpret_cast<float *>(F.a2);
       const int q = warp & 3, r = 32 * q + lane;
-      for (int j = warp < 4 ? 0 : 3; j < (warp < 4 ? 3 : TC_TILES); ++j) {
+      for (int j = warp >> 2; j < TC_TILES; j += TT / 128) {
         float acc[16];
         tc_ld16(tc.taddr + ((uint32_t)(32 * q) << 16) + 16 * j, acc);
         const int R = 11 + 16 * j + (r >> 3), x = r & 7, y = R % 10 - 1, z = R / 10 - 1;
@@ -655,7 +670,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     // w, w + 8, ...; lane l the voxels l + 32k, whose sums the warp adds
     {
       const float *d1 = reinterpret_cast<const float *>(F.a2);
-      for (int tp = warp; tp < 27; tp += CT / 32) {
+      for (int tp = warp; tp < 27; tp += TT / 32) {
         const int off = Off(tp);
         float acc[32];  // [co][ci]
 #pragma unroll
@@ -677,18 +692,19 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
 #pragma unroll
           for (int i = 0; i < 32; ++i) S.grad[G_W1 + i * 27 + tp] += acc[i];
       }
-      // layer-1 bias: thread t sums channel t / 16 over the voxels t % 16 +
-      // 16i, then the 16 partial sums of a channel in order
+      // layer-1 bias: thread t sums channel t / G over the voxels t % G +
+      // G i (G = TT / 16), then the G partial sums of a channel in order
       {
-        const int c = t >> 4, g = t & 15;
+        constexpr int G = TT / 16;
+        const int c = t / G, g = t % G;
         float acc = 0.0f;
-        for (int v = g; v < 512; v += 16) acc += d1[c * 512 + v];
+        for (int v = g; v < 512; v += G) acc += d1[c * 512 + v];
         S.part[t] = acc;
       }
       __syncthreads();
       if (t < 16) {
         float acc = 0.0f;
-        for (int g = 0; g < 16; ++g) acc += S.part[16 * t + g];
+        for (int g = 0; g < TT / 16; ++g) acc += S.part[(TT / 16) * t + g];
         S.grad[G_B1 + t] += acc;
       }
     }
@@ -729,7 +745,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
     }
   }
   tc_end(tc);
-  for (int i = t; i < NG; i += CT) dst[g_to_param(i)] = S.grad[i];
+  for (int i = t; i < NG; i += TT) dst[g_to_param(i)] = S.grad[i];
   // this CTA's loss
   float v = my_loss;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -737,7 +753,7 @@ __global__ void __launch_bounds__(CT) k_cnn_train(const bf16 *__restrict__ X, co
   __syncthreads();
   if (t == 0) {
     float s = 0.0f;
-    for (int i = 0; i < CT / 32; ++i) s += S.red[i];
+    for (int i = 0; i < TT / 32; ++i) s += S.red[i];
     loss_partial[blockIdx.x] = s;
   }
 }
@@ -1057,7 +1073,7 @@ extern "C" int sm_cnn_forward(sm_cnn *c, const float *x_host, int n, float *out_
 static int grad_step(sm_cnn *c, int n, const int *ids_host) {
   CCK(cudaMemcpyAsync(c->ids, ids_host, 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream));
   int nblk = std::min(n, c->sms);
-  k_cnn_train<<<nblk, CT, train_smem(), c->stream>>>(c->X, c->target, c->ids, n, 1.0f / (512.0f * n), c->w,
+  k_cnn_train<<<nblk, TT, train_smem(), c->stream>>>(c->X, c->target, c->ids, n, 1.0f / (512.0f * n), c->w,
                                                      c->partial, c->lossp, c->derr);
   k_cnn_reduce<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->partial, nblk, c->grad, c->lossp, c->loss);
   CCK(cudaGetLastError());
