@@ -1218,7 +1218,39 @@ def bench_batch(args, dev, world):
             e["fp64_ginstr"] = round(fl / (us * 1e-6) / 1e9, 1)
             e["fp64_frac"] = round(fl / (us * 1e-6) / 1e9 / fp64_rate(), 4)
         kern[name] = e
+    # the same problems one at a time (a batch of one each, same kernels and
+    # schedule): 16 problems spread over the size range, timed after a
+    # warm-up solve each, scaled to the 256 solves by their cell counts
+    order = np.argsort(sides)
+    pick = [int(order[i]) for i in np.linspace(0, len(sides) - 1, 16).round().astype(int)]
+    blobs = synth.batch_blobs(len(sides))
+    one_ms, one_cells = 0.0, 0
+    for s_ in pick:
+        n_ = int(sides[s_])
+        b1 = pkg.Batch([n_], 1.0, (0, 0, 0, 0, 1, 1), (0, 0, 0, 0, 0, 1.0))
+        b1.grid(b1.rhs, 0).copy_(torch.from_numpy(-synth.blob_rho(n_, blobs[s_])))
+        b1.set_schedule(shape, gmult)
+        b1.phi.zero_()
+        b1.solve(TOL, MAX_CYCLES)
+        b1.phi.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b1.stream)
+        rc1, _, _ = b1.solve(TOL, MAX_CYCLES)
+        e1.record(b1.stream)
+        torch.cuda.synchronize()
+        assert rc1 == 0, rc1
+        one_ms += e0.elapsed_time(e1)
+        one_cells += n_ ** 3
+        b1.close()
+    one_total_ms = one_ms * float(np.sum(np.asarray(sides, np.float64) ** 3)) / one_cells
+    one = {"sample": "16 of the 256 problems spread over the size range, each solved alone (a batch of one, "
+                     "same kernels and schedule) after a warm-up solve; time scaled to all 256 by cell count",
+           "solves_per_s": round(256 / (one_total_ms * 1e-3), 2),
+           "batched_speedup": round((256 * args.steps / (total * 1e-3)) / (256 / (one_total_ms * 1e-3)), 2)}
     res = {"value": round(256 * args.steps * world / (total * 1e-3), 2), "unit": "solves/s",
+           "one_at_a_time": one,
            "ms_per_batch": round(total / args.steps, 3), "solves_per_batch": 256, "cells": cells,
            "max_corrections": cycles / args.steps,
            "gcells_corrections_per_s": round(cells * cycles * world / (total * 1e-3) / 1e9, 3),
