@@ -153,9 +153,12 @@ int sm_quad_refine_flags(sm_quad *q, double c0, double c1, double c0_deref, doub
  * f, n_e, n_i, |E| and rho; new children get phi, n_e, n_i by the
  * prolongation (2c + c_x + c_y)/4 of their parent's cells (wall ghosts for
  * phi; mirrors and the 2c limit for densities), the rest zero.  Out (may be
- * NULL): refined boxes, derefined boxes, dropped requests.  Synchronises.
- * Errors: SM_EINVAL, SM_ENOMEM (past max_boxes; the mesh is unchanged),
- * SM_ESTATE. */
+ * NULL): refined boxes, derefined boxes, dropped requests.  The decisions,
+ * the new box set and its tables are formed on the device (scratch in the
+ * arena's per-call work fields); the host reads the counts once and then
+ * the new tables for sm_quad_get_tables and sm_quad_refine_flags.
+ * Synchronises.  Errors: SM_EINVAL, SM_ENOMEM (past max_boxes; the mesh is
+ * unchanged), SM_ESTATE. */
 int sm_quad_regrid(sm_quad *q, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped);
 
 /* on != 0 (the default): each V-cycle runs as a CUDA graph, captured per

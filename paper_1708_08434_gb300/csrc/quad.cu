@@ -3,8 +3,10 @@
 // quadtree of 8^2-cell boxes, in Cartesian (x, y) or cylindrical (r, z)
 // coordinates.
 //
-// Tables are built by host C++ (proper nesting, Morton order per level) and
-// copied into the arena; every field operation runs in the kernels below,
+// The initial mesh's tables are built by host C++ (proper nesting, Morton
+// order per level) and copied into the arena; a regrid forms the new box set
+// and its tables on the device (k_qrg_*) and the host keeps a copy of them
+// for its own queries.  Every field operation runs in the kernels below,
 // one warp per box: the box and the ghost layer a kernel needs are staged in
 // shared memory, with coarse values at refinement boundaries read through
 // the parent's 8-neighbour table (proper nesting guarantees every coarse
@@ -748,6 +750,278 @@ __global__ void __launch_bounds__(QT) k_q_regrid_move(int n, const int *__restri
   }
 }
 
+// ---- regrid: the new box set on the device ---------------------------------
+//
+// Old boxes are stored level by level in Morton order.  The new set keeps
+// every box but the children of derefined boxes and adds 4 children per
+// refined box; each new level is the merge of two Morton-sorted lists (the
+// kept boxes of the level and the children of the refined boxes of the level
+// below, whose keys are parent key * 4 + child), so a box's new index is its
+// rank in its own list plus the count of keys of the other list below its
+// own (binary searches).  Parents, children and same-level neighbours follow
+// by binary search in the new levels' keys.
+
+// per-level starts of the compacted lists and of the new levels
+struct QRgLevels {
+  int kept[QMAXL + 2];  // level l in the kept list
+  int ref[QMAXL + 2];   // level l in the refined list
+  int nw[QMAXL + 2];    // level l in the new numbering
+};
+struct QOffsets {
+  int v[QMAXL + 2];
+};
+
+// Morton key of (i, j) within its level: bit b of i to bit 2b, of j to 2b + 1
+__device__ __forceinline__ uint64_t qmorton(int i, int j) {
+  auto spread = [](unsigned v) {
+    uint64_t x = v & 0x7fffffffu;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+  };
+  return spread((unsigned)i) | (spread((unsigned)j) << 1);
+}
+
+// first index in [lo, hi) whose key is >= x
+__device__ __forceinline__ int qlower_bound(const uint64_t *__restrict__ a, int lo, int hi, uint64_t x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// refinement: a flagged leaf below the maximum level whose 8 neighbour
+// positions of its level hold a box or lie outside the domain (else the
+// request is dropped: cnt[0])
+__global__ void k_qrg_refine(int n, const int *__restrict__ lev, const int *__restrict__ chl,
+                             const int *__restrict__ nbr8, const int8_t *__restrict__ flags, int lmax,
+                             int *__restrict__ refv, int *cnt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  int r = 0;
+  if (chl[4 * b] < 0 && flags[b] > 0 && lev[b] < lmax) {
+    bool ok = true;
+    for (int d = 0; d < 8; ++d) ok = ok && nbr8[8 * b + d] != -2;
+    if (ok) r = 1;
+    else atomicAdd(cnt, 1);
+  }
+  refv[b] = r;
+}
+
+// derefinement of box p: its 4 children are leaves flagged < 0 and no
+// neighbour of a child outside the siblings has or gets children (cnt[1]
+// counts them)
+__global__ void k_qrg_derefine(int n, const int *__restrict__ chl, const int *__restrict__ par,
+                               const int *__restrict__ nbr8, const int8_t *__restrict__ flags,
+                               const int *__restrict__ refv, int *__restrict__ derv, int *cnt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  bool ok = chl[4 * p] >= 0;
+  for (int c = 0; c < 4 && ok; ++c) {
+    const int ch = chl[4 * p + c];
+    ok = chl[4 * ch] < 0 && flags[ch] < 0;
+  }
+  for (int c = 0; c < 4 && ok; ++c) {
+    const int ch = chl[4 * p + c];
+    for (int d = 0; d < 8 && ok; ++d) {
+      const int nb = nbr8[8 * ch + d];
+      if (nb >= 0 && par[nb] != p && (chl[4 * nb] >= 0 || refv[nb])) ok = false;
+    }
+  }
+  derv[p] = ok ? 1 : 0;
+  if (ok) atomicAdd(cnt + 1, 1);
+}
+
+// keepv[b] = b is not a child of a derefined box
+__global__ void k_qrg_keep(int n, const int *__restrict__ par, const int *__restrict__ derv,
+                           int *__restrict__ keepv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int p = par[b];
+  keepv[b] = (p >= 0 && derv[p]) ? 0 : 1;
+}
+
+// exclusive prefix sums of two int arrays of n entries (block y = 0: in0 ->
+// out0, y = 1: in1 -> out1), out[n] = the total: each thread sums a
+// contiguous chunk, the chunk sums are scanned in the block, then each
+// thread writes its chunk's prefixes
+__global__ void __launch_bounds__(1024) k_qrg_scan2(const int *__restrict__ in0, int *__restrict__ out0,
+                                                    const int *__restrict__ in1, int *__restrict__ out1, int n) {
+  __shared__ int wsum[32];
+  const int *in = blockIdx.y ? in1 : in0;
+  int *out = blockIdx.y ? out1 : out0;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int chunk = (n + 1023) / 1024, lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  int x = s;  // inclusive scan of the chunk sums: warps, then the warp totals
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int v = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    wsum[lane] = v;
+  }
+  __syncthreads();
+  int run = x - s + (w ? wsum[w - 1] : 0);
+  for (int i = lo; i < hi; ++i) {
+    const int v = in[i];
+    out[i] = run;
+    run += v;
+  }
+  if (t == 1023) out[n] = wsum[31];
+}
+
+// the counts the host needs in one array: dropped and derefined requests,
+// then the kept and the refined list positions at the old level offsets
+__global__ void k_qrg_counts(const int *__restrict__ cnt, const int *__restrict__ keep_pos,
+                             const int *__restrict__ ref_pos, QOffsets off, int nl, int *__restrict__ out) {
+  const int t = threadIdx.x;
+  if (t < 2) out[t] = cnt[t];
+  if (t <= nl) {
+    out[2 + t] = keep_pos[off.v[t]];
+    out[3 + nl + t] = ref_pos[off.v[t]];
+  }
+}
+
+// the Morton keys of the kept and of the refined boxes, compacted
+__global__ void k_qrg_keys(int n, const int2 *__restrict__ ij, const int *__restrict__ keepv,
+                           const int *__restrict__ keep_pos, const int *__restrict__ refv,
+                           const int *__restrict__ ref_pos, uint64_t *__restrict__ kept_keys,
+                           uint64_t *__restrict__ ref_keys) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int2 v = ij[b];
+  const uint64_t key = qmorton(v.x, v.y);
+  if (keepv[b]) kept_keys[keep_pos[b]] = key;
+  if (refv[b]) ref_keys[ref_pos[b]] = key;
+}
+
+// new index, level, coordinates and key of every kept box and of the 4
+// children of every refined box (4 threads per old box: thread 0 places the
+// box itself when kept, thread c its child c when refined), with the move
+// descriptor of the new box: its old index, or -1 and the old parent's 3x3
+// neighbourhood (old numbering) for a new child
+__global__ void k_qrg_place(int n, const int *__restrict__ lev, const int2 *__restrict__ ij,
+                            const int *__restrict__ nbr8, const int *__restrict__ keepv,
+                            const int *__restrict__ keep_pos, const int *__restrict__ refv,
+                            const int *__restrict__ ref_pos, const uint64_t *__restrict__ kept_keys,
+                            const uint64_t *__restrict__ ref_keys, QRgLevels L, int *__restrict__ nlev,
+                            int2 *__restrict__ nij, uint64_t *__restrict__ nkey, int *__restrict__ rg) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = t >> 2, c = t & 3;
+  if (b >= n) return;
+  const int l = lev[b];
+  const int2 v = ij[b];
+  const uint64_t key = qmorton(v.x, v.y);
+  if (c == 0 && keepv[b]) {
+    // children of refined boxes of level l-1 whose parent key is below this box's
+    const int below = l > 0 ? qlower_bound(ref_keys, L.ref[l - 1], L.ref[l], key >> 2) - L.ref[l - 1] : 0;
+    const int x = L.nw[l] + (keep_pos[b] - L.kept[l]) + 4 * below;
+    nlev[x] = l;
+    nij[x] = v;
+    nkey[x] = key;
+    rg[10 * (size_t)x] = b;
+  }
+  if (refv[b]) {
+    const uint64_t ck = (key << 2) | (uint64_t)c;
+    const int below = qlower_bound(kept_keys, L.kept[l + 1], L.kept[l + 2], ck) - L.kept[l + 1];
+    const int x = L.nw[l + 1] + 4 * (ref_pos[b] - L.ref[l]) + c + below;
+    nlev[x] = l + 1;
+    nij[x] = make_int2(2 * v.x + (c & 1), 2 * v.y + (c >> 1));
+    nkey[x] = ck;
+    int *r = rg + 10 * (size_t)x;
+    r[0] = -1;
+    for (int k = 0; k < 9; ++k) r[1 + k] = k == 4 ? b : nbr8[8 * b + (k < 4 ? k : k - 1)];
+  }
+}
+
+// parent and children of every new box by binary search in the new keys
+__global__ void k_qrg_links(int m, const int *__restrict__ nlev, const uint64_t *__restrict__ nkey, QRgLevels L,
+                            int nlevels, int *__restrict__ par, int *__restrict__ chl) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m) return;
+  const int l = nlev[b];
+  const uint64_t key = nkey[b];
+  int p = -1;
+  if (l > 0) {
+    const int i = qlower_bound(nkey, L.nw[l - 1], L.nw[l], key >> 2);
+    if (i < L.nw[l] && nkey[i] == key >> 2) p = i;
+  }
+  par[b] = p;
+  int c0 = -1;  // the first child; the four siblings are consecutive keys
+  if (l + 1 < nlevels) {
+    const int i = qlower_bound(nkey, L.nw[l + 1], L.nw[l + 2], key << 2);
+    if (i + 3 < L.nw[l + 2] && nkey[i] == key << 2 && nkey[i + 3] == ((key << 2) | 3ull)) c0 = i;
+  }
+  for (int c = 0; c < 4; ++c) chl[4 * b + c] = c0 >= 0 ? c0 + c : -1;
+}
+
+// same-level neighbours (8 threads per new box, direction d): -1 outside
+// the domain, -2 where the level holds no box
+__global__ void k_qrg_nbr(int m, const int *__restrict__ nlev, const int2 *__restrict__ nij,
+                          const uint64_t *__restrict__ nkey, QRgLevels L, int *__restrict__ nbr8) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = t >> 3, d = t & 7;
+  if (b >= m) return;
+  const int k = d < 4 ? d : d + 1, dx = k % 3 - 1, dy = k / 3 - 1;
+  const int l = nlev[b], side = 1 << l;
+  const int2 v = nij[b];
+  const int i = v.x + dx, j = v.y + dy;
+  int r = -1;
+  if (i >= 0 && j >= 0 && i < side && j < side) {
+    const uint64_t key = qmorton(i, j);
+    const int x = qlower_bound(nkey, L.nw[l], L.nw[l + 1], key);
+    r = (x < L.nw[l + 1] && nkey[x] == key) ? x : -2;
+  }
+  nbr8[8 * b + d] = r;
+}
+
+// the tables derived from the links: the parent's 3x3 neighbourhood, the
+// refinement bits and the column weights (8 threads per new box, column c)
+__global__ void k_qrg_derived(int m, int cyl, const int *__restrict__ par, const int *__restrict__ chl,
+                              const int *__restrict__ nbr8, const int2 *__restrict__ ij, int *__restrict__ pn,
+                              int *__restrict__ ref, double *__restrict__ w, double *__restrict__ wv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = t >> 3, c = t & 7;
+  if (b >= m) return;
+  const int p = par[b];
+  const int k = c < 4 ? c : c + 1;  // the 3x3 slots other than the centre
+  pn[9 * (size_t)b + k] = p >= 0 ? nbr8[8 * p + c] : -1;
+  if (c == 0) {
+    pn[9 * (size_t)b + 4] = p;
+    int r = chl[4 * b] >= 0 ? 16 : 0;
+    const int fd[4] = {3, 4, 1, 6};  // faces -x, +x, -y, +y among the 8 directions
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr8[8 * b + fd[f]];
+      if (nb >= 0 && chl[4 * nb] >= 0) r |= 1 << f;
+    }
+    ref[b] = r;
+  }
+  // column weights, each operation rounded on its own as on the host
+  const int gx = ij[b].x * QN + c;
+  const double g = (double)gx, gh = __dadd_rn(g, 0.5);
+  const double wl = cyl ? __ddiv_rn(g, gh) : 1.0, wh = cyl ? __ddiv_rn(__dadd_rn(g, 1.0), gh) : 1.0;
+  w[24 * (size_t)b + 3 * c] = wl;
+  w[24 * (size_t)b + 3 * c + 1] = wh;
+  w[24 * (size_t)b + 3 * c + 2] = __ddiv_rn(1.0, __dadd_rn(__dadd_rn(wl, wh), 2.0));
+  wv[8 * (size_t)b + c] = cyl ? gh : 1.0;
+}
+
 int blocks_for(long long boxes) { return (int)std::max<long long>(1, (boxes + WPB - 1) / WPB); }
 
 }  // namespace
@@ -765,7 +1039,6 @@ struct sm_quad {
   // host tables
   std::vector<int> lev, ix, iy, par, chl, nbr8;
   std::vector<uint64_t> mort;
-  std::vector<double> w, wv;
   int nlev = 0;
   int off[QMAXL + 2] = {0};
   // arena
@@ -831,6 +1104,18 @@ int find_box(const sm_quad *q, int l, int i, int j) {
   return -2;
 }
 
+// weights of the column with global x index gx (at its box's level):
+// w_lo, w_hi, 1/(w_lo + w_hi + 2) and the volume weight; the same roundings
+// as the device's regrid tables (col_weights_dev)
+void col_weights(const sm_quad *q, int gx, double *w3, double *wv) {
+  const bool cyl = q->dom.geometry == SM_AXISYMMETRIC;
+  const double wl = cyl ? (double)gx / (gx + 0.5) : 1.0, wh = cyl ? (gx + 1.0) / (gx + 0.5) : 1.0;
+  w3[0] = wl;
+  w3[1] = wh;
+  w3[2] = 1.0 / (wl + wh + 2.0);
+  *wv = cyl ? gx + 0.5 : 1.0;
+}
+
 void add_box(sm_quad *q, int l, int i, int j, int parent) {
   q->lev.push_back(l);
   q->ix.push_back(i);
@@ -839,16 +1124,6 @@ void add_box(sm_quad *q, int l, int i, int j, int parent) {
   q->mort.push_back(morton2(i, j));
   for (int c = 0; c < 4; ++c) q->chl.push_back(-1);
   for (int d = 0; d < 8; ++d) q->nbr8.push_back(-2);
-  // radial weights of the box's columns (global x index gx at level l)
-  for (int c = 0; c < QN; ++c) {
-    const int gx = i * QN + c;
-    const bool cyl = q->dom.geometry == SM_AXISYMMETRIC;
-    const double wl = cyl ? (double)gx / (gx + 0.5) : 1.0, wh = cyl ? (gx + 1.0) / (gx + 0.5) : 1.0;
-    q->w.push_back(wl);
-    q->w.push_back(wh);
-    q->w.push_back(1.0 / (wl + wh + 2.0));
-    q->wv.push_back(cyl ? gx + 0.5 : 1.0);
-  }
 }
 
 void set_neighbours(sm_quad *q, int l) {
@@ -864,8 +1139,10 @@ int upload_tables(sm_quad *q) {
   const int n = n_boxes(q);
   std::vector<int2> ij(n);
   std::vector<int> pn(9 * (size_t)n, -1), ref(n, 0);
+  std::vector<double> w(24 * (size_t)n), wv(8 * (size_t)n);
   for (int b = 0; b < n; ++b) {
     ij[b] = make_int2(q->ix[b], q->iy[b]);
+    for (int c = 0; c < QN; ++c) col_weights(q, q->ix[b] * QN + c, &w[24 * (size_t)b + 3 * c], &wv[8 * (size_t)b + c]);
     const int p = q->par[b];
     if (p >= 0)
       for (int dy = -1; dy <= 1; ++dy)
@@ -887,8 +1164,8 @@ int upload_tables(sm_quad *q) {
       cudaMemcpyAsync(q->d_ij, ij.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_pn, pn.data(), sizeof(int) * 9 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q->d_ref, ref.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(q->d_w, q->w.data(), sizeof(double) * 24 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(q->d_wv, q->wv.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_w, w.data(), sizeof(double) * 24 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_wv, wv.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return qfail(q, SM_ECUDA, "table upload");
   return SM_OK;
@@ -909,7 +1186,9 @@ void coarse_inverse(sm_quad *q) {
   const double ih2 = q->inv_h2[0];
   for (int r = 0; r < n; ++r) {
     const int i = r % QN, j = r / QN;
-    const double wl = q->w[3 * i], wh = q->w[3 * i + 1];
+    double w3[3], wvol;
+    col_weights(q, i, w3, &wvol);  // level 0: box 0, global column i
+    const double wl = w3[0], wh = w3[1];
     const double wf[4] = {wl, wh, 1.0, 1.0};
     const int nbr[4] = {i > 0 ? r - 1 : -1, i < QN - 1 ? r + 1 : -1, j > 0 ? r - QN : -1, j < QN - 1 ? r + QN : -1};
     for (int f = 0; f < 4; ++f) {
@@ -1582,131 +1861,121 @@ extern "C" int sm_quad_refine_flags(sm_quad *q, double c0, double c1, double c0_
   return SM_OK;
 }
 
+// The new box set, its tables and the move descriptors are formed on the
+// device (k_qrg_*); the host reads the request counts and per-level list
+// sizes once, then the new tables for its own copy of the mesh.
 extern "C" int sm_quad_regrid(sm_quad *q, const int8_t *flags, int *n_refined, int *n_derefined, int *n_dropped) {
   SM_RANGE();
   if (!q || !flags) return SM_EINVAL;
   if (!q->arena) return qfail(q, SM_ESTATE, "no arena bound");
-  const int nb0 = n_boxes(q);
+  const int n = n_boxes(q), M = q->max_boxes, L0 = q->nlev, T = 256;
+  cudaStream_t s = q->stream;
   restrict_all(q, V_NE);
   restrict_all(q, V_NI);
-  auto leaf = [&](int b) { return q->chl[4 * b] < 0; };
-  std::vector<char> ref(nb0, 0), der(nb0, 0);
-  int nref = 0, nder = 0, ndrop = 0;
-  for (int b = 0; b < nb0; ++b) {
-    if (!leaf(b) || flags[b] <= 0 || q->lev[b] >= q->lmax) continue;
-    bool ok = true;
-    for (int d = 0; d < 8; ++d) ok &= q->nbr8[8 * b + d] != -2;
-    if (ok) {
-      ref[b] = 1;
-      ++nref;
-    } else {
-      ++ndrop;
-    }
-  }
-  for (int p = 0; p < nb0; ++p) {
-    if (leaf(p)) continue;
-    bool ok = true;
-    for (int c = 0; c < 4 && ok; ++c) {
-      const int ch = q->chl[4 * p + c];
-      if (!leaf(ch) || flags[ch] >= 0) ok = false;
-    }
-    for (int c = 0; c < 4 && ok; ++c) {
-      const int ch = q->chl[4 * p + c];
-      for (int d = 0; d < 8 && ok; ++d) {
-        const int nb = q->nbr8[8 * ch + d];
-        if (nb >= 0 && q->par[nb] != p && (!leaf(nb) || ref[nb])) ok = false;
-      }
-    }
-    if (ok) {
-      der[p] = 1;
-      ++nder;
-    }
-  }
-  struct Ent {
-    int lev, i, j, src, par;
-    uint64_t key;
+  // scratch in the per-call work fields (V_OLD onwards: nothing there
+  // outlives a call)
+  char *wp = reinterpret_cast<char *>(q->var[V_OLD]);
+  auto take = [&](size_t bytes) {
+    char *p = wp;
+    wp += (bytes + 255) & ~(size_t)255;
+    return p;
   };
-  std::vector<Ent> e;
-  e.reserve(nb0 + 4 * (size_t)nref);
-  for (int b = 0; b < nb0; ++b) {
-    if (q->par[b] >= 0 && der[q->par[b]]) continue;
-    e.push_back({q->lev[b], q->ix[b], q->iy[b], b, -1, q->mort[b]});
-    if (!ref[b]) continue;
-    for (int c = 0; c < 4; ++c) {
-      const int ci = 2 * q->ix[b] + (c & 1), cj = 2 * q->iy[b] + (c >> 1);
-      e.push_back({q->lev[b] + 1, ci, cj, -1, b, morton2(ci, cj)});
-    }
-  }
-  if ((long long)e.size() > q->max_boxes) return qfail(q, SM_ENOMEM, "box capacity exceeded");
-  std::sort(e.begin(), e.end(), [](const Ent &a, const Ent &b) {
-    return a.lev != b.lev ? a.lev < b.lev : a.key < b.key;
-  });
-  // the old parent neighbourhoods of the new children, from the old tables
-  const int nnew = (int)e.size();
-  std::vector<int> rg(10 * (size_t)nnew, -1);
-  for (int b = 0; b < nnew; ++b) {
-    rg[10 * (size_t)b] = e[b].src;
-    if (e[b].src >= 0) continue;
-    const int p = e[b].par;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx)
-        rg[10 * (size_t)b + 1 + (dx + 1) + 3 * (dy + 1)] = (dx || dy) ? q->nbr8[8 * p + dir8h(dx, dy)] : p;
-  }
-  // snapshot of the old fields (the move writes the same arrays)
-  const int vars[6] = {V_PHI, V_NE, V_NI, V_RHS, V_EMAG, V_RHO};
-  const size_t stride = (size_t)q->max_boxes * QC;
-  for (int v = 0; v < 6; ++v)
-    if (cudaMemcpyAsync(q->snap + v * stride, q->var[vars[v]], sizeof(double) * QC * (size_t)nb0,
-                        cudaMemcpyDeviceToDevice, q->stream) != cudaSuccess)
-      return qfail(q, SM_ECUDA, "regrid snapshot");
-  // the new mesh, in (level, Morton) order
-  q->lev.clear();
-  q->ix.clear();
-  q->iy.clear();
-  q->par.clear();
-  q->chl.clear();
-  q->nbr8.clear();
-  q->mort.clear();
-  q->w.clear();
-  q->wv.clear();
-  for (const Ent &x : e) add_box(q, x.lev, x.i, x.j, -1);
-  int nlev = 0;
-  for (const Ent &x : e) nlev = std::max(nlev, x.lev + 1);
-  q->nlev = nlev;
-  for (int l = 0, b = 0; l <= nlev; ++l) {
-    while (b < nnew && q->lev[b] < l) ++b;
-    q->off[l] = b;
-  }
-  for (int l = nlev + 1; l <= QMAXL + 1; ++l) q->off[l] = nnew;
-  for (int b = 0; b < nnew; ++b) {
-    const int l = q->lev[b];
-    q->par[b] = l ? find_box(q, l - 1, q->ix[b] >> 1, q->iy[b] >> 1) : -1;
-    bool kids = l + 1 < nlev;
-    for (int c = 0; c < 4 && kids; ++c) {
-      const int ch = find_box(q, l + 1, 2 * q->ix[b] + (c & 1), 2 * q->iy[b] + (c >> 1));
-      if (ch < 0) kids = false;
-      else q->chl[4 * b + c] = ch;
-    }
-    if (!kids)
-      for (int c = 0; c < 4; ++c) q->chl[4 * b + c] = -1;
-  }
-  for (int l = 0; l < nlev; ++l) set_neighbours(q, l);
-  drop_graphs(q);
-  if (cudaMemcpyAsync(q->d_rg, rg.data(), sizeof(int) * rg.size(), cudaMemcpyHostToDevice, q->stream) != cudaSuccess)
-    return qfail(q, SM_ECUDA, "regrid descriptors");
-  if (int st = upload_tables(q)) return st;
-  k_q_regrid_move<<<blocks_for(nnew), QT, 0, q->stream>>>(nnew, q->d_rg, q->snap, stride, q->var[V_PHI],
-                                                           q->var[V_NE], q->var[V_NI], q->var[V_RHS],
-                                                           q->var[V_EMAG], q->var[V_RHO], tabs(q), q->bc, q->d_err);
-  ++q->launches;
-  unsigned ev = 0;
-  if (cudaMemcpyAsync(&ev, q->d_err, sizeof(ev), cudaMemcpyDeviceToHost, q->stream) != cudaSuccess ||
-      cudaStreamSynchronize(q->stream) != cudaSuccess)
-    return qfail(q, SM_ECUDA, "regrid move");
-  if (ev) return qfail(q, SM_ESTATE, "a coarse box needed by the regrid prolongation is missing");
+  int8_t *dflags = (int8_t *)take((size_t)n);
+  int *refv = (int *)take(4 * (size_t)n), *keepv = (int *)take(4 * (size_t)n), *derv = (int *)take(4 * (size_t)n);
+  int *ref_pos = (int *)take(4 * ((size_t)n + 1)), *keep_pos = (int *)take(4 * ((size_t)n + 1));
+  uint64_t *ref_keys = (uint64_t *)take(8 * (size_t)n), *kept_keys = (uint64_t *)take(8 * (size_t)n);
+  int *nlev = (int *)take(4 * (size_t)M);
+  int2 *nij = (int2 *)take(8 * (size_t)M);
+  uint64_t *nkey = (uint64_t *)take(8 * (size_t)M);
+  int *cnt = (int *)take(8), *counts = (int *)take(4 * (2 * QMAXL + 8));
+  const int gb = (n + T - 1) / T;
+  if (cudaMemcpyAsync(dflags, flags, (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(cnt, 0, 8, s) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "regrid flags");
+  k_qrg_refine<<<gb, T, 0, s>>>(n, q->d_lev, q->d_chl, q->d_nbr8, dflags, q->lmax, refv, cnt);
+  k_qrg_derefine<<<gb, T, 0, s>>>(n, q->d_chl, q->d_par, q->d_nbr8, dflags, refv, derv, cnt);
+  k_qrg_keep<<<gb, T, 0, s>>>(n, q->d_par, derv, keepv);
+  k_qrg_scan2<<<dim3(1, 2), 1024, 0, s>>>(refv, ref_pos, keepv, keep_pos, n);
+  QOffsets off{};
+  for (int l = 0; l <= L0; ++l) off.v[l] = q->off[l];
+  k_qrg_counts<<<1, 32, 0, s>>>(cnt, keep_pos, ref_pos, off, L0, counts);
+  q->launches += 5;
+  std::vector<int> hc(3 + 2 * L0 + 1);
+  if (int st = check(q, "regrid decisions")) return st;
+  if (cudaMemcpyAsync(hc.data(), counts, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "regrid counts");
+  const int *hk = &hc[2], *hr = &hc[3 + L0];
+  const int nref = hr[L0], nder = hc[1];
   if (n_refined) *n_refined = nref;
   if (n_derefined) *n_derefined = nder;
-  if (n_dropped) *n_dropped = ndrop;
+  if (n_dropped) *n_dropped = hc[0];
+  if (nref == 0 && nder == 0) return SM_OK;
+  QRgLevels L{};
+  int nlevels = 0, m = 0;
+  for (int l = 0; l < QMAXL + 2; ++l) {
+    const int kept = l < L0 ? hk[l + 1] - hk[l] : 0;
+    const int born = (l >= 1 && l - 1 < L0) ? 4 * (hr[l] - hr[l - 1]) : 0;
+    L.kept[l] = l <= L0 ? hk[l] : hk[L0];
+    L.ref[l] = l <= L0 ? hr[l] : hr[L0];
+    L.nw[l] = m;
+    m += kept + born;
+    if (kept + born > 0) nlevels = l + 1;
+  }
+  if (m > M) return qfail(q, SM_ENOMEM, "box capacity exceeded");
+  k_qrg_keys<<<gb, T, 0, s>>>(n, q->d_ij, keepv, keep_pos, refv, ref_pos, kept_keys, ref_keys);
+  k_qrg_place<<<(4 * n + T - 1) / T, T, 0, s>>>(n, q->d_lev, q->d_ij, q->d_nbr8, keepv, keep_pos, refv, ref_pos,
+                                               kept_keys, ref_keys, L, nlev, nij, nkey, q->d_rg);
+  q->launches += 2;
+  // snapshot of the old fields (the move writes the same arrays)
+  const int vars[6] = {V_PHI, V_NE, V_NI, V_RHS, V_EMAG, V_RHO};
+  const size_t stride = (size_t)M * QC;
+  for (int v = 0; v < 6; ++v)
+    if (cudaMemcpyAsync(q->snap + v * stride, q->var[vars[v]], sizeof(double) * QC * (size_t)n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return qfail(q, SM_ECUDA, "regrid snapshot");
+  // the new tables in place of the old ones
+  if (cudaMemcpyAsync(q->d_lev, nlev, sizeof(int) * m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->d_ij, nij, sizeof(int2) * m, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "regrid tables");
+  const int gm = (m + T - 1) / T, gm8 = (8 * m + T - 1) / T;
+  k_qrg_links<<<gm, T, 0, s>>>(m, nlev, nkey, L, nlevels, q->d_par, q->d_chl);
+  k_qrg_nbr<<<gm8, T, 0, s>>>(m, nlev, nij, nkey, L, q->d_nbr8);
+  k_qrg_derived<<<gm8, T, 0, s>>>(m, q->dom.geometry == SM_AXISYMMETRIC, q->d_par, q->d_chl, q->d_nbr8, q->d_ij,
+                                  q->d_pn, q->d_ref, q->d_w, q->d_wv);
+  q->launches += 3;
+  if (int st = check(q, "regrid tables")) return st;
+  drop_graphs(q);
+  k_q_regrid_move<<<blocks_for(m), QT, 0, s>>>(m, q->d_rg, q->snap, stride, q->var[V_PHI], q->var[V_NE],
+                                               q->var[V_NI], q->var[V_RHS], q->var[V_EMAG], q->var[V_RHO], tabs(q),
+                                               q->bc, q->d_err);
+  ++q->launches;
+  // the host's copy of the new mesh
+  std::vector<int2> hij(m);
+  q->lev.resize(m);
+  q->par.resize(m);
+  q->chl.resize(4 * (size_t)m);
+  q->nbr8.resize(8 * (size_t)m);
+  q->mort.resize(m);
+  unsigned ev = 0;
+  if (cudaMemcpyAsync(q->lev.data(), q->d_lev, sizeof(int) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hij.data(), q->d_ij, sizeof(int2) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->par.data(), q->d_par, sizeof(int) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->chl.data(), q->d_chl, sizeof(int) * 4 * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->nbr8.data(), q->d_nbr8, sizeof(int) * 8 * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(q->mort.data(), nkey, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&ev, q->d_err, sizeof(ev), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return qfail(q, SM_ECUDA, "regrid move");
+  q->ix.resize(m);
+  q->iy.resize(m);
+  for (int b = 0; b < m; ++b) {
+    q->ix[b] = hij[b].x;
+    q->iy[b] = hij[b].y;
+  }
+  q->nlev = nlevels;
+  for (int l = 0; l <= QMAXL + 1; ++l) q->off[l] = l <= nlevels ? L.nw[l] : m;
+  if (ev) return qfail(q, SM_ESTATE, "a coarse box needed by the regrid prolongation is missing");
   return SM_OK;
 }
 

@@ -326,6 +326,41 @@ def test_regrid_parity(name):
     assert rel_err(g.download(p.PHI), o.get(quad.PHI)) <= TOL
 
 
+def test_regrid_parity_full_size_axi_streamer():
+    """The benchmark mesh (10113 boxes): a regrid that refines and
+    derefines hundreds of boxes, with prefix sums over many entries per
+    thread, gives the oracle's tables and data."""
+    p = pkg()
+    dom, st = synth.workload2("axi_streamer")
+    o = quad.build_mesh(dom, st)
+    g = gpu_quad(dom, st, max_boxes=1 << 16)
+    t = load(dom, st, o, g)
+    x, y = synth.cell_centres2(dom, t["level"], t["ij"])
+    phi = dom.bc_val[3] * y / dom.length + 50.0 * np.sin(x * 400.0)
+    o.set(quad.PHI, phi)
+    g.upload(p.PHI, phi)
+    em = tip_field(dom, t)
+    o.set(quad.EMAG, em)
+    g.upload(p.EMAG, em)
+    f = o.refine_flags(0.25, 1.2, 0.125, 30e-6, 3)
+    ro, rg = o.regrid(f), g.regrid(f)
+    assert ro == rg and ro[0] > 100 and ro[1] > 100, (ro, rg)
+    to, tg = o.tables(), g.tables()
+    assert len(to["level"]) > 9000
+    for k in ("level", "ij", "morton", "parent", "child", "nbr", "level_offset"):
+        assert np.array_equal(to[k], tg[k]), k
+    for vo, vg in ((quad.PHI, p.PHI), (quad.NE, p.NE), (quad.NI, p.NI), (quad.EMAG, p.EMAG)):
+        assert rel_err(g.download(vg), o.get(vo)) <= TOL, vo
+    # a second regrid from the device's own tables (derefining what the
+    # first one refined is allowed, the rules decide)
+    f2 = o.refine_flags(1.0, 1.2, 0.125, 30e-6, 3)
+    assert np.array_equal(f2, g.refine_flags(1.0, 1.2, 0.125, 30e-6, 3))
+    assert o.regrid(f2) == g.regrid(f2)
+    to, tg = o.tables(), g.tables()
+    for k in ("level", "ij", "morton", "parent", "child", "nbr", "level_offset"):
+        assert np.array_equal(to[k], tg[k]), k
+
+
 @pytest.mark.parametrize("name,c0,dxd", [("axi_small", 0.005, 1.0), ("cart_small", 0.05, 30e-6)])
 def test_adaptive_step_parity(name, c0, dxd):
     """Solve, field, flags from each side's own field (a stricter c0 than
