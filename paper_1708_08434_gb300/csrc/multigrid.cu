@@ -564,14 +564,105 @@ __global__ void __launch_bounds__(GT) k_rbgs(int lo, int color, T *__restrict__ 
   rbgs_box(g, s, b, color, phi, rhs, gh, nb, bc, h2, homog);
 }
 
+// Three levels of the 8-child average chain in one launch.  A block takes a
+// box b and writes its restriction into up to `depth` (1-3) ancestors: the
+// 4^3 cells of its parent region, then the 2^3 cells of the grandparent that
+// those 64 values cover, then the one cell of the great-grandparent that
+// those 8 cover, each an 8-value sum in the order of restrict1_box times
+// 1/8, so that every value equals the one the level-by-level chain writes.
+// Blocks [0, nb) take the boxes lo.. of the group's finest level (depth
+// d0), the next nl1 blocks the leaves leaf[lo1..] of the level below (depth
+// d0 - 1) and the last nl2 the leaves leaf[lo2..] of the level below that
+// (depth d0 - 2): every refined box of the three levels below the finest is
+// then complete, from values complete before the launch.
 template <typename T>
-__global__ void __launch_bounds__(GT) k_restrict1(int lo, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(64) k_restrict3(int lo, int nb, int lo1, int nl1, int lo2, int d0,
+                                                  const int32_t *__restrict__ leaf,
+                                                  const int32_t *__restrict__ parent,
                                                   const int32_t *__restrict__ ijk, T *__restrict__ a,
                                                   T *__restrict__ a2) {
-  const int b = lo + blockIdx.x;
-  const Place pl = load_place(parent, ijk, b);
+  __shared__ T sp[2][64], sg[2][8];
+  const int blk = blockIdx.x, t = threadIdx.x;
+  int b, depth;
+  if (blk < nb) {
+    b = lo + blk;
+    depth = d0;
+  } else if (blk < nb + nl1) {
+    b = __ldg(leaf + lo1 + blk - nb);
+    depth = d0 - 1;
+  } else {
+    b = __ldg(leaf + lo2 + blk - nb - nl1);
+    depth = d0 - 2;
+  }
+  // ancestors and octants: P of b, G of P, Q of G
+  const int P = __ldg(parent + b);
+  const int ob[3] = {__ldg(ijk + 3 * b) & 1, __ldg(ijk + 3 * b + 1) & 1, __ldg(ijk + 3 * b + 2) & 1};
+  int G = -1, Q = -1, op[3] = {0, 0, 0}, og[3] = {0, 0, 0};
+  if (depth >= 2) {
+    G = __ldg(parent + P);
+    for (int d = 0; d < 3; ++d) op[d] = __ldg(ijk + 3 * P + d) & 1;
+  }
+  if (depth >= 3) {
+    Q = __ldg(parent + G);
+    for (int d = 0; d < 3; ++d) og[d] = __ldg(ijk + 3 * G + d) & 1;
+  }
   pdl_wait();
-  restrict1_box(block_grp(), b, pl, a, a2);
+  const int ci = t & 3, cj = (t >> 2) & 3, ck = t >> 4;
+  const size_t fb = (size_t)b * CELLS;
+  T s = 0, s2 = 0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const int c = cidx(2 * ci + di, 2 * cj + dj, 2 * ck + dk);
+        s += a[fb + c];
+        if (a2) s2 += a2[fb + c];
+      }
+  const T v = s * T(0.125), v2 = s2 * T(0.125);
+  const size_t pc = (size_t)P * CELLS + cidx(4 * ob[0] + ci, 4 * ob[1] + cj, 4 * ob[2] + ck);
+  a[pc] = v;
+  if (a2) a2[pc] = v2;
+  if (depth < 2) return;  // uniform per block
+  sp[0][t] = v;
+  sp[1][t] = v2;
+  __syncthreads();
+  if (t < 8) {
+    const int ei = t & 1, ej = (t >> 1) & 1, ek = t >> 2;
+    T g = 0, g2 = 0;
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+          const int c = (2 * ei + di) + 4 * (2 * ej + dj) + 16 * (2 * ek + dk);
+          g += sp[0][c];
+          g2 += sp[1][c];
+        }
+    const T w = g * T(0.125), w2 = g2 * T(0.125);
+    const size_t gc = (size_t)G * CELLS + cidx(4 * op[0] + 2 * ob[0] + ei, 4 * op[1] + 2 * ob[1] + ej,
+                                               4 * op[2] + 2 * ob[2] + ek);
+    a[gc] = w;
+    if (a2) a2[gc] = w2;
+    sg[0][t] = w;
+    sg[1][t] = w2;
+  }
+  if (depth < 3) return;
+  __syncthreads();
+  if (t == 0) {
+    T q = 0, q2 = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {  // e = di + 2 dj + 4 dk: the restrict1_box order
+      q += sg[0][e];
+      q2 += sg[1][e];
+    }
+    const size_t qc = (size_t)Q * CELLS + cidx(4 * og[0] + 2 * op[0] + ob[0], 4 * og[1] + 2 * op[1] + ob[1],
+                                               4 * og[2] + 2 * op[2] + ob[2]);
+    a[qc] = q * T(0.125);
+    if (a2) a2[qc] = q2 * T(0.125);
+  }
 }
 
 template <typename T>
@@ -1169,10 +1260,15 @@ int sm_fill_all_cf(sm_ctx *ctx, double *var) {
 
 template <typename T>
 static int restrict_chain(sm_ctx *ctx, T *a, T *a2) {
-  for (int l = ctx->n_levels - 1; l >= 1; --l) {
-    int n = lvl_n(ctx, l);
-    if (!n) continue;
-    sm_launch(ctx, k_restrict1<T>, n, 64, 0, ctx->level_off[l], ctx->parent, ctx->ijk, a, a2);
+  // groups of three levels, finest first (k_restrict3)
+  for (int l = ctx->n_levels - 1; l >= 1; l -= 3) {
+    const int d0 = l < 3 ? l : 3;
+    const int nb = lvl_n(ctx, l);
+    const int lo1 = d0 >= 2 ? ctx->leaf_level_off[l - 1] : 0, nl1 = d0 >= 2 ? ctx->leaf_level_off[l] - lo1 : 0;
+    const int lo2 = d0 >= 3 ? ctx->leaf_level_off[l - 2] : 0, nl2 = d0 >= 3 ? ctx->leaf_level_off[l - 1] - lo2 : 0;
+    if (nb + nl1 + nl2 == 0) continue;
+    sm_launch(ctx, k_restrict3<T>, nb + nl1 + nl2, 64, 0, ctx->level_off[l], nb, lo1, nl1, lo2, d0, ctx->leaf,
+              ctx->parent, ctx->ijk, a, a2);
   }
   SM_CKL("restrict");
   return SM_OK;
