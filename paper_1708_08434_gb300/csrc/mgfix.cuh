@@ -1098,21 +1098,85 @@ __global__ void __launch_bounds__(GT) k_fresnorm(const int32_t *__restrict__ lea
   group_umax_to(g, slot, fx_resid_max_box(g, s, b, phx, rhs, ghx, nb, bc, sc, nq), red);
 }
 
-// Level-0 exact solve (one box, CELLS threads): the FAS right-hand side of
-// level 0 from its G (f = -6 G q / h^2), the FP64 eigenbasis solve of the
-// double path with the Dirichlet values folded in, the result rounded to
-// quanta.
-__global__ void __launch_bounds__(CELLS) k_fcoarse(long long *__restrict__ phx, const long long *__restrict__ gx,
-                                                   const double *__restrict__ basis, Bc bc, double h2, double inv_h2,
-                                                   unsigned long long *sc) {
-  __shared__ double sm[2 * CELLS + 216];
+// Level-0 exact solve: the FAS right-hand side of level 0 from its G
+// (f = -6 G q / h^2), the FP64 eigenbasis solve of the double path
+// (coarse_box_io) with the Dirichlet values folded in, the result rounded
+// to quanta.  It is split over a cluster of 8 blocks of 64 threads (eight
+// SMs' FP64 pipes instead of one).  The transforms keep the order of
+// coarse_box_io (x, y, z forward; x, y, z backward) and each coefficient is
+// the same 8-term sum in the same order, so the result has the bits of the
+// one-block solve (which the persistent kernel runs).
+// Block r first holds the z-plane r (rhs, x and y forward), then the y-slab
+// r (z forward from the 8 planes in the other blocks' shared memory, the
+// eigenvalue scaling, x backward), then the x-slab r (y backward from the 8
+// y-slabs, z backward, store).
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(64)
+    k_fcoarse8(long long *__restrict__ phx, const long long *__restrict__ gx, const double *__restrict__ basis,
+               Bc bc, double h2, double inv_h2, unsigned long long *sc) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double pa[64], pb[64], sd[64], se[64], V[192], lam[24];
+  const int r = (int)cl.block_rank(), t = threadIdx.x, lo = t & 7, hi = t >> 3;
+  for (int i = t; i < 216; i += 64) {
+    if (i < 192) V[i] = __ldg(basis + i);
+    else lam[i - 192] = __ldg(basis + i);
+  }
   pdl_wait();
   const int E = fx_E(sc);
   const double cf = -6.0 * fx_q(E) * inv_h2;
+  {  // plane c2 = r, cell (lo, hi, r)
+    const int c[3] = {lo, hi, r};
+    double v = __ll2double_rn(gx[xsplit(cidx(lo, hi, r))]) * cf;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int q = c[f >> 1] + ((f & 1) ? 1 : -1);
+      if ((q < 0 || q >= NC) && bc.type[f]) v -= 2.0 * bc.val[f] * inv_h2;
+    }
+    pa[t] = v;
+  }
+  __syncthreads();
+  {
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[0 * 64 + m * 8 + lo] * pa[m + 8 * hi];
+    pb[t] = acc;
+  }
+  __syncthreads();
+  {
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[1 * 64 + m * 8 + hi] * pb[lo + 8 * m];
+    pa[t] = acc;  // read by the other blocks after the cluster barrier
+  }
+  cl.sync();
+  {  // y-slab c1 = r, cell (lo, r, hi)
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) {
+      const double *pm = cl.map_shared_rank(pa, m);
+      acc += V[2 * 64 + m * 8 + hi] * pm[lo + 8 * r];
+    }
+    pb[t] = acc * h2 / (lam[lo] + lam[8 + r] + lam[16 + hi]);
+  }
+  __syncthreads();
+  {
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[0 * 64 + lo * 8 + m] * pb[m + 8 * hi];
+    sd[t] = acc;  // read by the other blocks after the cluster barrier
+  }
+  cl.sync();
+  {  // x-slab c0 = r, cell (r, lo, hi)
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) {
+      const double *pm = cl.map_shared_rank(sd, m);
+      acc += V[1 * 64 + lo * 8 + m] * pm[r + 8 * hi];
+    }
+    se[t] = acc;
+  }
+  cl.sync();  // the other blocks' reads of sd are done; se is complete
   bool bad = false;
-  coarse_box_io<CELLS>(
-      (int)threadIdx.x, [] { __syncthreads(); }, sm, [&](int t) { return __ll2double_rn(gx[xsplit(t)]) * cf; },
-      [&](int t, double v) { phx[xsplit(t)] = fx_of(v, E, bad); }, basis, bc, h2, inv_h2, 0);
+  {
+    double acc = 0.0;
+    for (int m = 0; m < NC; ++m) acc += V[2 * 64 + hi * 8 + m] * se[lo + 8 * m];
+    phx[xsplit(cidx(r, lo, hi))] = fx_of(acc, E, bad);
+  }
   fx_flag(bad, sc);
 }
 

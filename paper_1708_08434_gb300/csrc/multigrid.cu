@@ -8,6 +8,7 @@
 // solve, FP32 for the error equation of the mixed-precision form, whose
 // outer defect-correction loop (residual, accumulation, level-0 solve)
 // stays in FP64.
+#include <cooperative_groups.h>
 #include <math.h>
 #include <string.h>
 
@@ -1675,7 +1676,7 @@ static int fx_smooth(sm_ctx *ctx, int l, int nu) {
 static int fx_coarse(sm_ctx *ctx) {
   int st = ensure_basis(ctx);
   if (st) return st;
-  sm_launch(ctx, fx::k_fcoarse, 1, CELLS, 0, ctx->phx, ctx->gx, ctx->basis, ctx->bc, ctx->lh.h2[0],
+  sm_launch(ctx, fx::k_fcoarse8, 8, 64, 0, ctx->phx, ctx->gx, ctx->basis, ctx->bc, ctx->lh.h2[0],
             ctx->lh.inv_h2[0], ctx->dscal);
   SM_CKL("coarse solve");
   return SM_OK;
