@@ -1160,12 +1160,19 @@ __global__ void __launch_bounds__(GT) k_fresnorm(const int32_t *__restrict__ lea
 // r (z forward from the 8 planes in the other blocks' shared memory, the
 // eigenvalue scaling, x backward), then the x-slab r (y backward from the 8
 // y-slabs, z backward, store).
+// With fas != 0 it first completes the FAS right-hand side of the level-0
+// box (the work of k_ffas on it: every face is a wall), each block for its
+// plane from the whole box staged with its wall ghosts; the box's potential
+// is only written after the last cluster barrier, when every block has
+// read it.
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(64)
-    k_fcoarse8(long long *__restrict__ phx, const long long *__restrict__ gx, const double *__restrict__ basis,
-               Bc bc, double h2, double inv_h2, unsigned long long *sc) {
+    k_fcoarse8(long long *__restrict__ phx, long long *__restrict__ gx, long long *__restrict__ oldx,
+               const double *__restrict__ basis, Bc bc, double h2, double inv_h2, int fas,
+               unsigned long long *sc) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double pa[64], pb[64], sd[64], se[64], V[192], lam[24];
+  __shared__ long long sx[1000];
   const int r = (int)cl.block_rank(), t = threadIdx.x, lo = t & 7, hi = t >> 3;
   for (int i = t; i < 216; i += 64) {
     if (i < 192) V[i] = __ldg(basis + i);
@@ -1174,9 +1181,30 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(64)
   pdl_wait();
   const int E = fx_E(sc);
   const double cf = -6.0 * fx_q(E) * inv_h2;
+  bool bad = false;
+  const int pp = xsplit(cidx(lo, hi, r));
+  long long G;
+  if (fas) {
+    for (int i = t; i < CELLS; i += 64) sx[s10(i)] = phx[xsplit(i)];
+    __syncthreads();
+    for (int i = t; i < 6 * FACE; i += 64) {
+      const int f = i >> 6, u = i & 7, w = (i >> 3) & 7, a = f >> 1;
+      const int q = s10(face_cell(f, u, w)), stride = a == 0 ? 1 : (a == 1 ? 10 : 100);
+      const long long inner = sx[q];
+      sx[q + ((f & 1) ? stride : -stride)] = bc.type[f] ? fx_2g(sc, f) - inner : inner;
+    }
+    __syncthreads();
+    const int q = s10(cidx(lo, hi, r));
+    oldx[pp] = sx[q];
+    G = fx_rdiv<12>(gx[pp] - 2 * fx_T(sx, q));
+    bad |= fx_bad(G);
+    gx[pp] = G;
+  } else {
+    G = gx[pp];
+  }
   {  // plane c2 = r, cell (lo, hi, r)
     const int c[3] = {lo, hi, r};
-    double v = __ll2double_rn(gx[xsplit(cidx(lo, hi, r))]) * cf;
+    double v = __ll2double_rn(G) * cf;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const int q = c[f >> 1] + ((f & 1) ? 1 : -1);
@@ -1221,7 +1249,6 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(64)
     se[t] = acc;
   }
   cl.sync();  // the other blocks' reads of sd are done; se is complete
-  bool bad = false;
   {
     double acc = 0.0;
     for (int m = 0; m < NC; ++m) acc += V[2 * 64 + hi * 8 + m] * se[lo + 8 * m];

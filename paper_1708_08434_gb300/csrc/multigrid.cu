@@ -1676,11 +1676,13 @@ static int fx_smooth(sm_ctx *ctx, int l, int nu, bool skip_first = false) {
   return SM_OK;
 }
 
-static int fx_coarse(sm_ctx *ctx) {
+// level-0 solve; fas: complete level 0's FAS right-hand side first (the
+// down leg of a V-cycle has restricted into it)
+static int fx_coarse(sm_ctx *ctx, bool fas = false) {
   int st = ensure_basis(ctx);
   if (st) return st;
-  sm_launch(ctx, fx::k_fcoarse8, 8, 64, 0, ctx->phx, ctx->gx, ctx->basis, ctx->bc, ctx->lh.h2[0],
-            ctx->lh.inv_h2[0], ctx->dscal);
+  sm_launch(ctx, fx::k_fcoarse8, 8, 64, 0, ctx->phx, ctx->gx, (long long *)ctx->old, ctx->basis, ctx->bc,
+            ctx->lh.h2[0], ctx->lh.inv_h2[0], (int)fas, ctx->dscal);
   SM_CKL("coarse solve");
   return SM_OK;
 }
@@ -1741,12 +1743,12 @@ static int fx_vcycle(sm_ctx *ctx, int top, int norm_slot = -1) {
     if (fused)
       sm_launch(ctx, fx::k_ffas_color0, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx,
                 (long long *)ctx->old, ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
-    else
+    else if (l - 1 >= 1)  // level 0's FAS completion runs in the level-0 solve
       sm_launch(ctx, fx::k_ffas, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx, (long long *)ctx->old,
                 ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
     SM_CKL("vcycle down");
   }
-  if ((st = fx_coarse(ctx))) return st;
+  if ((st = fx_coarse(ctx, top >= 1))) return st;
   for (int l = 1; l <= top; ++l) {
     if ((st = fx_prolong(ctx, l, 0, fx_norm_of(ctx, norm_slot >= 0 ? l - 1 : -1, norm_slot)))) return st;
     if ((st = fx_smooth(ctx, l, ctx->cfg.nu2))) return st;
