@@ -125,6 +125,18 @@ __device__ __forceinline__ T staged_sum(const T *s, int q) {
 // One colour of a red-black Gauss-Seidel sweep on box b: phi = (sum of 6
 // neighbours - h^2 f)/6 on the cells with (i+j+k) % 2 == color (level-global
 // parity; box origins are multiples of 8).
+// Gauss-Seidel value of staged cell c: (sum of 6 neighbours - h^2 f) / 6
+template <typename T>
+__device__ __forceinline__ T rbgs_value(const T *s, int c, T f, T h2) {
+  return (staged_sum(s, s10(c)) - h2 * f) * T(1.0 / 6.0);
+}
+
+// natural index of the n-th cell of a colour in a box
+__device__ __forceinline__ int colour_cell(int n, int color) {
+  const int k = n >> 5, j = (n >> 2) & 7;
+  return cidx(((n & 3) << 1) | ((j + k + color) & 1), j, k);
+}
+
 template <typename T>
 __device__ __forceinline__ void rbgs_box(const Grp &g, T *s, int b, int color, T *phi, const T *rhs, const T *gh,
                                          const Nb &nb, const Bc &bc, T h2, int homog) {
@@ -133,14 +145,12 @@ __device__ __forceinline__ void rbgs_box(const Grp &g, T *s, int b, int color, T
   T f[RPT];
 #pragma unroll
   for (int h = 0; h < RPT; ++h) {
-    const int n = g.t + h * GT;  // n-th cell of the colour
-    const int k = n >> 5, j = (n >> 2) & 7;
-    c[h] = cidx(((n & 3) << 1) | ((j + k + color) & 1), j, k);
+    c[h] = colour_cell(g.t + h * GT, color);
     f[h] = rhs[base + c[h]];
   }
   stage_box(g, s, phi, nb, gh, b, bc, homog, color);
 #pragma unroll
-  for (int h = 0; h < RPT; ++h) phi[base + c[h]] = (staged_sum(s, s10(c[h])) - h2 * f[h]) * T(1.0 / 6.0);
+  for (int h = 0; h < RPT; ++h) phi[base + c[h]] = rbgs_value(s, c[h], f[h], h2);
 }
 
 // parent of box b and the octant of the parent that b covers
@@ -191,6 +201,19 @@ __device__ __forceinline__ void resid_restrict_box(const Grp &g, T *s, T *sr, in
 
 // After restriction into box b (level l-1): keep a copy of phi, and on a
 // refined box complete the FAS right-hand side f = avg(r_fine) + L phi.
+// FAS step of a refined box already staged in s: old = phi, rhs += L phi
+template <typename T>
+__device__ __forceinline__ void fas_staged(const Grp &g, const T *s, int b, T *old, T *rhs, T inv_h2) {
+  const size_t base = (size_t)b * CELLS;
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int c = g.t + h * GT, q = s10(c);
+    const T p = s[q];
+    old[base + c] = p;
+    rhs[base + c] += (staged_sum(s, q) - T(6) * p) * inv_h2;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void fas_box(const Grp &g, T *s, int b, T *phi, T *old, T *rhs, const T *gh,
                                         const Nb &nb, bool refined, const Bc &bc, T inv_h2, int homog) {
@@ -201,13 +224,7 @@ __device__ __forceinline__ void fas_box(const Grp &g, T *s, int b, T *phi, T *ol
     return;
   }
   stage_box(g, s, phi, nb, gh, b, bc, homog);
-#pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int c = g.t + h * GT, q = s10(c);
-    const T p = s[q];
-    old[base + c] = p;
-    rhs[base + c] += (staged_sum(s, q) - T(6) * p) * inv_h2;
-  }
+  fas_staged(g, s, b, old, rhs, inv_h2);
 }
 
 // plain 8-child average of one or two variables from box b into its parent
@@ -677,6 +694,39 @@ __global__ void __launch_bounds__(GT) k_fas(int lo, T *__restrict__ phi, T *__re
   const bool refined = __ldg(child + 8 * b) >= 0;
   pdl_wait();
   fas_box(g, s, b, phi, old, rhs, gh, nb, refined, bc, inv_h2, homog);
+}
+
+// k_fas fused with the first colour pass (colour 0) of the smoothing that
+// follows it on the same level: the box and its halos staged once serve the
+// FAS step and the colour-0 update (which reads colour-1 cells and halo
+// values, none of which the pass or the FAS step changes); the box's new
+// rhs is read back after the block barrier.  The same operations as k_fas
+// followed by k_rbgs with colour 0.
+template <typename T>
+__global__ void __launch_bounds__(GT) k_fas_rbgs0(int lo, T *__restrict__ phi, T *__restrict__ old,
+                                                  T *__restrict__ rhs, const T *__restrict__ gh,
+                                                  const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child,
+                                                  Bc bc, T inv_h2, T h2, int homog) {
+  __shared__ T s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const bool refined = __ldg(child + 8 * b) >= 0;
+  pdl_wait();
+  const size_t base = (size_t)b * CELLS;
+  stage_box(g, s, phi, nb, gh, b, bc, homog);
+  if (refined) {
+    fas_staged(g, s, b, old, rhs, inv_h2);
+  } else {
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) old[base + g.t + h * GT] = s[s10(g.t + h * GT)];
+  }
+  g.sync();
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    const int c = colour_cell(g.t + h * GT, 0);
+    phi[base + c] = rbgs_value(s, c, rhs[base + c], h2);
+  }
 }
 
 template <typename T>
@@ -1285,11 +1335,14 @@ static int rbgs_pass(sm_ctx *ctx, const MG<T> &m, int l, int color) {
   return SM_OK;
 }
 
+// nu red-black sweeps of level l; with skip_first the first colour pass has
+// already run (k_fas_rbgs0)
 template <typename T>
-static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu) {
+static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu, bool skip_first = false) {
   if (!lvl_n(ctx, l)) return SM_OK;
   for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color) rbgs_pass(ctx, m, l, color);
+    for (int color = 0; color < 2; ++color)
+      if (!(skip_first && s == 0 && color == 0)) rbgs_pass(ctx, m, l, color);
   SM_CKL("rbgs");
   return SM_OK;
 }
@@ -1349,14 +1402,20 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top, int norm_slot = -1) {
   int st;
   if (norm_slot >= 0)
     SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
+  bool fused = false;  // the first colour pass of level l ran with its FAS step
   for (int l = top; l >= 1; --l) {
-    if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
+    if ((st = smooth(ctx, m, l, ctx->cfg.nu1, fused))) return st;
     sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
               ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
               (T)ctx->lh.inv_h2[l], m.homog);
-    sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
-              ctx->nbr6, ctx->child, ctx->bc,
-              (T)ctx->lh.inv_h2[l - 1], m.homog);
+    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0;
+    if (fused)
+      sm_launch(ctx, k_fas_rbgs0<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+                ctx->nbr6, ctx->child, ctx->bc, (T)ctx->lh.inv_h2[l - 1], (T)ctx->lh.h2[l - 1], m.homog);
+    else
+      sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+                ctx->nbr6, ctx->child, ctx->bc,
+                (T)ctx->lh.inv_h2[l - 1], m.homog);
     SM_CKL("vcycle down");
   }
   if ((st = coarse_solve(ctx, m))) return st;
