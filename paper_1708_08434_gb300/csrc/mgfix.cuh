@@ -829,56 +829,6 @@ __global__ void __launch_bounds__(GT) k_ffas(int lo, const long long *__restrict
   fx_flag(bad, sc);
 }
 
-// k_ffas fused with the first colour pass (colour 0) of the smoothing that
-// follows it on the same level, for levels of one partial wave of blocks:
-// the box and its face halos are staged once (fx_stage) for the FAS
-// right-hand side and for the colour-0 update, which reads only colour-1
-// cells and halo values, none of which the pass changes.  The same
-// integer operations as k_ffas followed by a colour-0 pass, so the same
-// bits.  Colour 0 is the first half of the split layout: positions
-// g.t + h GT with h < RPT.
-__global__ void __launch_bounds__(GT) k_ffas_color0(int lo, long long *__restrict__ phx,
-                                                    long long *__restrict__ oldx, long long *__restrict__ gx,
-                                                    const long long *__restrict__ ghx,
-                                                    const int32_t *__restrict__ nbr6,
-                                                    const int32_t *__restrict__ child, Bc bc,
-                                                    unsigned long long *sc) {
-  __shared__ long long s[1000];
-  const Grp g = block_grp();
-  const int b = lo + blockIdx.x;
-  const Nb nb = load_nb(g, nbr6, b);
-  const bool refined = __ldg(child + 8 * b) >= 0;
-  pdl_wait();
-  const size_t base = (size_t)b * CELLS;
-  long long P[CPT];  // children's sums of 6 G + T (refined box) or G (leaf box)
-#pragma unroll
-  for (int h = 0; h < CPT; ++h) P[h] = gx[base + g.t + h * GT];
-  fx_stage(g, s, phx, nb, ghx, b, bc, sc);
-  bool bad = false;
-  long long G0[RPT];
-#pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const int pp = g.t + h * GT, q = s10(xcell(pp));
-    oldx[base + pp] = s[q];
-    long long G = P[h];
-    if (refined) {
-      G = fx_rdiv<12>(P[h] - 2 * fx_T(s, q));
-      bad |= fx_bad(G);
-      gx[base + pp] = G;
-    }
-    if (h < RPT) G0[h] = G;
-  }
-#pragma unroll
-  for (int h = 0; h < RPT; ++h) {
-    const int pp = g.t + h * GT, q = s10(xcell(pp));
-    const long long v =
-        fx_div6(s[q - 1] + s[q + 1] + s[q - 10] + s[q + 10] + s[q - 100] + s[q + 100] + 6 * G0[h]);
-    bad |= fx_bad(v);
-    phx[base + pp] = v;
-  }
-  fx_flag(bad, sc);
-}
-
 // leaf boxes of one level whose residual norm a prolongation launch
 // computes in extra blocks (n = 0: none)
 struct FxNorm {

@@ -696,39 +696,6 @@ __global__ void __launch_bounds__(GT) k_fas(int lo, T *__restrict__ phi, T *__re
   fas_box(g, s, b, phi, old, rhs, gh, nb, refined, bc, inv_h2, homog);
 }
 
-// k_fas fused with the first colour pass (colour 0) of the smoothing that
-// follows it on the same level: the box and its halos staged once serve the
-// FAS step and the colour-0 update (which reads colour-1 cells and halo
-// values, none of which the pass or the FAS step changes); the box's new
-// rhs is read back after the block barrier.  The same operations as k_fas
-// followed by k_rbgs with colour 0.
-template <typename T>
-__global__ void __launch_bounds__(GT) k_fas_rbgs0(int lo, T *__restrict__ phi, T *__restrict__ old,
-                                                  T *__restrict__ rhs, const T *__restrict__ gh,
-                                                  const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child,
-                                                  Bc bc, T inv_h2, T h2, int homog) {
-  __shared__ T s[1000];
-  const Grp g = block_grp();
-  const int b = lo + blockIdx.x;
-  const Nb nb = load_nb(g, nbr6, b);
-  const bool refined = __ldg(child + 8 * b) >= 0;
-  pdl_wait();
-  const size_t base = (size_t)b * CELLS;
-  stage_box(g, s, phi, nb, gh, b, bc, homog);
-  if (refined) {
-    fas_staged(g, s, b, old, rhs, inv_h2);
-  } else {
-#pragma unroll
-    for (int h = 0; h < CPT; ++h) old[base + g.t + h * GT] = s[s10(g.t + h * GT)];
-  }
-  g.sync();
-#pragma unroll
-  for (int h = 0; h < RPT; ++h) {
-    const int c = colour_cell(g.t + h * GT, 0);
-    phi[base + c] = rbgs_value(s, c, rhs[base + c], h2);
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(GT) k_resid_restrict(int lo, T *__restrict__ phi, T *__restrict__ rhs,
                                                        const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
@@ -1335,14 +1302,11 @@ static int rbgs_pass(sm_ctx *ctx, const MG<T> &m, int l, int color) {
   return SM_OK;
 }
 
-// nu red-black sweeps of level l; with skip_first the first colour pass has
-// already run (k_fas_rbgs0)
 template <typename T>
-static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu, bool skip_first = false) {
+static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu) {
   if (!lvl_n(ctx, l)) return SM_OK;
   for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color)
-      if (!(skip_first && s == 0 && color == 0)) rbgs_pass(ctx, m, l, color);
+    for (int color = 0; color < 2; ++color) rbgs_pass(ctx, m, l, color);
   SM_CKL("rbgs");
   return SM_OK;
 }
@@ -1402,20 +1366,14 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top, int norm_slot = -1) {
   int st;
   if (norm_slot >= 0)
     SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
-  bool fused = false;  // the first colour pass of level l ran with its FAS step
   for (int l = top; l >= 1; --l) {
-    if ((st = smooth(ctx, m, l, ctx->cfg.nu1, fused))) return st;
+    if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
     sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
               ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
               (T)ctx->lh.inv_h2[l], m.homog);
-    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0;
-    if (fused)
-      sm_launch(ctx, k_fas_rbgs0<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
-                ctx->nbr6, ctx->child, ctx->bc, (T)ctx->lh.inv_h2[l - 1], (T)ctx->lh.h2[l - 1], m.homog);
-    else
-      sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
-                ctx->nbr6, ctx->child, ctx->bc,
-                (T)ctx->lh.inv_h2[l - 1], m.homog);
+    sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+              ctx->nbr6, ctx->child, ctx->bc,
+              (T)ctx->lh.inv_h2[l - 1], m.homog);
     SM_CKL("vcycle down");
   }
   if ((st = coarse_solve(ctx, m))) return st;
@@ -1716,14 +1674,11 @@ static int fx_epilogue(sm_ctx *ctx) {
 // is one partial wave of blocks runs the half-row kernel (2 cells per
 // thread, twice the warps to hide its load latency).  Both give the bits
 // of the box kernel (fx_color_box, which the persistent kernel runs).
-// nu red-black sweeps of level l; with skip_first the first colour pass has
-// already run (k_ffas_color0)
-static int fx_smooth(sm_ctx *ctx, int l, int nu, bool skip_first = false) {
+static int fx_smooth(sm_ctx *ctx, int l, int nu) {
   const int n = lvl_n(ctx, l);
   if (!n) return SM_OK;
   for (int s = 0; s < nu; ++s)
     for (int color = 0; color < 2; ++color) {
-      if (skip_first && s == 0 && color == 0) continue;
       if (n >= ctx->rows_min)
         sm_launch(ctx, fx::k_fcolor_rows, (n + fx::RBOX - 1) / fx::RBOX, 64 * fx::RBOX, 0, ctx->level_off[l], n,
                   color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6, ctx->bc, ctx->dscal);
@@ -1787,22 +1742,15 @@ static int fx_vcycle(sm_ctx *ctx, int top, int norm_slot = -1) {
   int st;
   if (norm_slot >= 0)
     SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
-  bool fused = false;  // the first colour pass of level l ran with its FAS completion
   for (int l = top; l >= 1; --l) {
-    if ((st = fx_smooth(ctx, l, ctx->cfg.nu1, fused))) return st;
+    if ((st = fx_smooth(ctx, l, ctx->cfg.nu1))) return st;
     if (lvl_n(ctx, l) >= ctx->rows_min)
       sm_launch(ctx, fx::k_fresid_restrict_rows, lvl_n(ctx, l), 64, 0, ctx->level_off[l], ctx->phx, ctx->gx,
                 ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
     else
       sm_launch(ctx, fx::k_fresid_restrict, lvl_n(ctx, l), GT, 0, ctx->level_off[l], ctx->phx, ctx->gx, ctx->ghx,
                 ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
-    // on a coarser level of one partial wave the FAS completion also runs
-    // that level's first colour pass
-    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0 && lvl_n(ctx, l - 1) < ctx->rows_min;
-    if (fused)
-      sm_launch(ctx, fx::k_ffas_color0, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx,
-                (long long *)ctx->old, ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
-    else if (l - 1 >= 1)  // level 0's FAS completion runs in the level-0 solve
+    if (l - 1 >= 1)  // level 0's FAS completion runs in the level-0 solve
       sm_launch(ctx, fx::k_ffas, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx, (long long *)ctx->old,
                 ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
     SM_CKL("vcycle down");

@@ -293,48 +293,6 @@ __global__ void __launch_bounds__(QT) k_q_fas(int off, int n, int l, double *__r
   }
 }
 
-// k_q_fas fused with the first colour pass (colour 0) of the smoothing that
-// follows it on level l: the box staged for the FAS step (neighbours with
-// children read from old, which their own FAS step copies into phi) also
-// serves the colour-0 update, which reads colour-1 cells and ghosts only;
-// the warp's rhs and phi writes are ordered before it by __syncwarp.  The
-// same operations as k_q_fas followed by k_q_rbgs with colour 0.
-__global__ void __launch_bounds__(QT) k_q_fas_rbgs0(int off, int n, int l, double *__restrict__ phi,
-                                                    double *__restrict__ rhs, double *__restrict__ old, QTabs T,
-                                                    const __grid_constant__ QBc bc, double inv_h2, double h2,
-                                                    unsigned *err) {
-  __shared__ double sm[WPB][S1 * S1];
-  QWARP();
-  if (k_ >= n) return;
-  const int b = off + k_;
-  const size_t g0 = (size_t)b * QC + lane, g1 = g0 + 32;
-  double v0, v1;
-  begin_box(phi, T, b, C, lane, v0, v1);
-  const double o0 = old[g0], o1 = old[g1], f0 = rhs[g0], f1 = rhs[g1];
-  const bool refined = C.ref & 16;
-  double *s = sm[wv_];
-  const int j = lane >> 2, i = 2 * (lane & 3) + (j & 1);  // this lane's colour-0 cell
-  const double *wc = T.w + (size_t)b * 24 + 3 * i;
-  const double w0 = wc[0], w1 = wc[1], w2 = wc[2];
-  if (refined) {
-    stage_phi(phi, old, C, b, bc, 0, s, lane, err, o0, o1);
-    rhs[g0] = f0 + lap_s(s, T, b, lane % QN, lane / QN, inv_h2);
-    rhs[g1] = f1 + lap_s(s, T, b, lane % QN, lane / QN + 4, inv_h2);
-    phi[g0] = o0;
-    phi[g1] = o1;
-  } else {
-    old[g0] = v0;
-    old[g1] = v1;
-    stage_phi(phi, old, C, b, bc, 0, s, lane, err, v0, v1);
-  }
-  __syncwarp();
-  const double fr = rhs[(size_t)b * QC + i + QN * j];
-  phi[(size_t)b * QC + i + QN * j] =
-      (w0 * s[(j + 1) * S1 + i] + w1 * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
-       h2 * fr) *
-      w2;
-}
-
 // Prolongation to every box of level l: (2c + c_x + c_y)/4 of the parent
 // level.  corr: the correction phi - old (homogeneous wall ghosts) added to
 // phi; otherwise phi itself (FMG, wall values) replaces phi.
@@ -1293,13 +1251,10 @@ void qlaunch(sm_quad *q, void (*k)(KArgs...), int grid, int block, Args &&...arg
   ++q->launches;
 }
 
-// nu red-black sweeps of level l; with skip_first the first colour pass has
-// already run (k_q_fas_rbgs0)
-void smooth(sm_quad *q, int l, int nu, bool skip_first = false) {
+void smooth(sm_quad *q, int l, int nu) {
   const int n = level_count(q, l);
   for (int s = 0; s < nu; ++s)
     for (int c = 0; c < 2; ++c) {
-      if (skip_first && s == 0 && c == 0) continue;
       qlaunch(q, k_q_rbgs, blocks_for(n), QT, q->off[l], n, l, c, q->var[V_PHI], (const double *)q->var[V_RHS],
               tabs(q), q->bc, q->h[l] * q->h[l], q->d_err);
     }
@@ -1311,19 +1266,13 @@ void coarse_solve(sm_quad *q) {
 }
 
 void vcycle(sm_quad *q, int top) {
-  bool fused = false;  // the first colour pass of level l ran with its FAS step
   for (int l = top; l >= 1; --l) {
-    smooth(q, l, q->nu1, fused);
+    smooth(q, l, q->nu1);
     const int n = level_count(q, l), nc = level_count(q, l - 1);
     qlaunch(q, k_q_resid_restrict, blocks_for(n), QT, q->off[l], n, l, (const double *)q->var[V_PHI],
             q->var[V_RHS], q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l], q->d_err);
-    fused = l - 1 >= 1;
-    if (fused)
-      qlaunch(q, k_q_fas_rbgs0, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS],
-              q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l - 1], q->h[l - 1] * q->h[l - 1], q->d_err);
-    else
-      qlaunch(q, k_q_fas, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS],
-              q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
+    qlaunch(q, k_q_fas, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS], q->var[V_OLD],
+            tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
   }
   coarse_solve(q);
   for (int l = 1; l <= top; ++l) {

@@ -510,3 +510,35 @@ def test_boundary_layout_ghosts_and_wrappers():
     ro = o.advance(dt, Q, EPS0, 1e-8, 40)
     assert (cyc[0], cyc[1]) == tuple(ro[2:])
     assert dtn.value == pytest.approx(ro[1], rel=TOL)
+
+
+def test_repeatable_bits_full_size_streamer6():
+    """Blocks of one launch never read what another block of it writes: the
+    same solves on fresh solvers give the same bits, on the captured graphs
+    and on the host loop, with and without programmatic dependent launch
+    (FMG, one more V-cycle, a warm-started solve to 1e-11; 2.4e6 leaf
+    cells, where every level is one partial wave of blocks)."""
+    dom, st = synth.workload("streamer6")
+    p = __import__("paper_1708_08434_gb300")
+    runs = []
+    for graphs, pdl in ((True, True), (True, True), (False, True), (False, False)):
+        g = gpu_mesh(dom, st, max_boxes=8192)
+        t = g.tables()
+        ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+        g.upload(p.NE, ne)
+        g.upload(p.NI, ni)
+        g.charge_rhs(Q, EPS0)
+        g.set_graphs(graphs)
+        g.set_pdl(pdl)
+        out = [g.fmg(1e-30, 1)[2]]
+        out.append(g.download(p.PHI).view(np.int64).copy())
+        g.vcycles(1)
+        out.append(g.download(p.PHI).view(np.int64).copy())
+        out.append(g.solve(1e-11, 30)[2])
+        out.append(g.download(p.PHI).view(np.int64).copy())
+        runs.append(out)
+        g.close()
+    for r in runs[1:]:
+        assert r[0] == runs[0][0] and r[3] == runs[0][3]
+        for k in (1, 2, 4):
+            assert np.array_equal(r[k], runs[0][k]), k

@@ -455,3 +455,27 @@ def test_paper_schedule_multi_step(name):
         assert rel_err(g.download(p.EMAG)[leaf], eo) <= TOL * amp, step
         dt = ro[1]
     assert 1e-14 < o.rel_residual() < 1e-2
+
+
+def test_repeatable_bits_full_size_axi_streamer():
+    """The same FMG solve and Heun step on two fresh quadtree solvers give
+    the same bits (no block of a launch reads what another block of it
+    writes)."""
+    p = pkg()
+    dom, st = synth.workload2("axi_streamer")
+    runs = []
+    for _ in range(2):
+        g = gpu_quad(dom, st)
+        t = g.tables()
+        ne, ni = synth.streamer_densities2(dom, st, t["level"], t["ij"])
+        g.upload(p.NE, ne)
+        g.upload(p.NI, ni)
+        g.set_table(synth.coefficient_table())
+        g.charge_rhs(Q, EPS0)
+        c1 = g.fmg(1e-8, 40)[2]
+        g.compute_field()
+        dt = g.dt_limit(Q, EPS0)
+        c2 = g.advance(dt, Q, EPS0, 1e-8, 40)[2:]
+        runs.append((c1, c2, g.download(p.PHI).view(np.int64).copy(), g.download(p.NE).view(np.int64).copy()))
+    assert runs[0][0] == runs[1][0] and runs[0][1] == runs[1][1]
+    assert np.array_equal(runs[0][2], runs[1][2]) and np.array_equal(runs[0][3], runs[1][3])
