@@ -232,3 +232,22 @@ def test_batch_mixed_starting_potentials():
     assert cyc[0] < cyc_f[0] and cyc[2] < cyc_f[2]
     check(b, rhos, range(len(sides)), 1e-8)
     b.close()
+
+
+def test_repeatable_bits_batch64():
+    """The first 64 solves of the workload solved on two fresh batches (the
+    tuned schedule, captured graph) give the same bits."""
+    sides = synth.batch_sizes(256)[:64]
+    out, sched = [], None
+    for _ in range(2):
+        b, _ = make_batch(sides)
+        if sched is None:
+            sched = b.tune(1)[:2]
+        b.set_schedule(*sched)
+        b.phi.zero_()
+        rc, cyc, rel = b.solve(1e-8, 30)
+        assert rc == 0
+        out.append((cyc.copy(), b.phi.cpu().numpy().view(np.int64).copy()))
+        b.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])

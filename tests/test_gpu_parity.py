@@ -542,3 +542,30 @@ def test_repeatable_bits_full_size_streamer6():
         assert r[0] == runs[0][0] and r[3] == runs[0][3]
         for k in (1, 2, 4):
             assert np.array_equal(r[k], runs[0][k]), k
+
+
+def test_repeatable_bits_heun_step_fp64_and_mixed():
+    """An FMG solve, the field, the time step and a Heun step (two Euler
+    stages, two warm-started solves) on streamer6 give the same bits on two
+    fresh solvers, for the FP64 and the mixed-precision forms."""
+    dom, st = synth.workload("streamer6")
+    p = __import__("paper_1708_08434_gb300")
+    for prec in (p.FP64, p.MIXED):
+        runs = []
+        for _ in range(2):
+            g = gpu_mesh(dom, st, max_boxes=8192, precision=prec)
+            t = g.tables()
+            ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
+            g.upload(p.NE, ne)
+            g.upload(p.NI, ni)
+            g.set_table(synth.coefficient_table())
+            g.charge_rhs(Q, EPS0)
+            c0 = g.fmg(1e-8, 30)[2]
+            g.compute_field()
+            dt = g.dt_limit(Q, EPS0)
+            r = g.advance(dt, Q, EPS0, 1e-8, 30)
+            runs.append((c0, r, [g.download(v).view(np.int64).copy() for v in (p.PHI, p.NE, p.NI, p.EMAG)]))
+            g.close()
+        assert runs[0][0] == runs[1][0] and runs[0][1] == runs[1][1], prec
+        for a, b in zip(runs[0][2], runs[1][2]):
+            assert np.array_equal(a, b), prec
