@@ -215,7 +215,7 @@ __device__ __forceinline__ bool fx_color_box(const Grp &g, long long *s, int b, 
 __device__ __forceinline__ void fx_resid_restrict_box(const Grp &g, long long *s, long long *sr, int b,
                                                       long long *phx, long long *gx, const long long *ghx,
                                                       const Nb &nb, const Place &pl, const Bc &bc,
-                                                      const unsigned long long *sc) {
+                                                      const unsigned long long *sc, long long *oldx = nullptr) {
   const size_t base = (size_t)b * CELLS;
   long long G[CPT];
 #pragma unroll
@@ -241,7 +241,9 @@ __device__ __forceinline__ void fx_resid_restrict_box(const Grp &g, long long *s
         ar += sr[c];
       }
   const size_t cc = (size_t)pl.P * CELLS + xpos(4 * pl.ox + ci, 4 * pl.oy + cj, 4 * pl.oz + ck);
-  phx[cc] = fx_rdiv<8>(ap);
+  const long long v = fx_rdiv<8>(ap);
+  phx[cc] = v;
+  if (oldx) oldx[cc] = v;
   gx[cc] = ar;
 }
 
@@ -800,19 +802,34 @@ __global__ void __launch_bounds__(64, 12) k_fresid_restrict_rows(int lo, long lo
   }
 }
 
-__global__ void __launch_bounds__(GT) k_fresid_restrict(int lo, long long *__restrict__ phx, long long *__restrict__ gx,
+// Blocks [0, n) take the boxes lo.. of level l.  With oldx != nullptr the
+// restricted values also go to oldx (the FAS copy of the level below), and
+// blocks [n, n + nl) copy the leaf boxes leaf[0, nl) of the level below
+// into oldx, so that k_ffas_color0 finds the whole level's values as they
+// are before its colour pass in oldx.
+__global__ void __launch_bounds__(GT) k_fresid_restrict(int lo, int n, long long *__restrict__ phx,
+                                                        long long *__restrict__ gx,
                                                         const long long *__restrict__ ghx,
                                                         const int32_t *__restrict__ nbr6,
                                                         const int32_t *__restrict__ parent,
                                                         const int32_t *__restrict__ ijk, Bc bc,
-                                                        const unsigned long long *sc) {
+                                                        const unsigned long long *sc, long long *__restrict__ oldx,
+                                                        const int32_t *__restrict__ leaf) {
   __shared__ long long s[1000], sr[CELLS];
   const Grp g = block_grp();
+  if ((int)blockIdx.x >= n) {
+    const int b = __ldg(leaf + blockIdx.x - n);
+    pdl_wait();
+    const size_t base = (size_t)b * CELLS;
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) oldx[base + g.t + h * GT] = phx[base + g.t + h * GT];
+    return;
+  }
   const int b = lo + blockIdx.x;
   const Nb nb = load_nb(g, nbr6, b);
   const Place pl = load_place(parent, ijk, b);
   pdl_wait();
-  fx_resid_restrict_box(g, s, sr, b, phx, gx, ghx, nb, pl, bc, sc);
+  fx_resid_restrict_box(g, s, sr, b, phx, gx, ghx, nb, pl, bc, sc, oldx);
 }
 
 __global__ void __launch_bounds__(GT) k_ffas(int lo, const long long *__restrict__ phx, long long *__restrict__ oldx,
@@ -826,6 +843,58 @@ __global__ void __launch_bounds__(GT) k_ffas(int lo, const long long *__restrict
   const bool refined = __ldg(child + 8 * b) >= 0;
   pdl_wait();
   const bool bad = fx_fas_box(g, s, b, phx, oldx, gx, ghx, nb, refined, bc, sc);
+  fx_flag(bad, sc);
+}
+
+// k_ffas fused with the first colour pass (colour 0) of the smoothing that
+// follows it on the same level, for levels of one partial wave of blocks.
+// The FAS term of a box reads its neighbours' face cells, whose colour-0
+// values the neighbours' own blocks of this launch overwrite; so every value
+// is staged from oldx, which the restriction launch before (k_fresid_restrict
+// with oldx) filled with the whole level as it is now and which nothing in
+// this launch writes.  The box staged once serves the FAS right-hand side
+// and the colour-0 update (which reads colour-1 cells and halo values only).
+// The same integer operations as k_ffas followed by a colour-0 pass: the
+// same bits.  Colour 0 is the first half of the split layout: positions
+// g.t + h GT with h < RPT.
+__global__ void __launch_bounds__(GT) k_ffas_color0(int lo, long long *__restrict__ phx,
+                                                    const long long *__restrict__ oldx, long long *__restrict__ gx,
+                                                    const long long *__restrict__ ghx,
+                                                    const int32_t *__restrict__ nbr6,
+                                                    const int32_t *__restrict__ child, Bc bc,
+                                                    unsigned long long *sc) {
+  __shared__ long long s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const bool refined = __ldg(child + 8 * b) >= 0;
+  pdl_wait();
+  const size_t base = (size_t)b * CELLS;
+  long long P[CPT];  // children's sums of 6 G + T (refined box) or G (leaf box)
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) P[h] = gx[base + g.t + h * GT];
+  fx_stage(g, s, oldx, nb, ghx, b, bc, sc);
+  bool bad = false;
+  long long G0[RPT];
+#pragma unroll
+  for (int h = 0; h < CPT; ++h) {
+    const int pp = g.t + h * GT, q = s10(xcell(pp));
+    long long G = P[h];
+    if (refined) {
+      G = fx_rdiv<12>(P[h] - 2 * fx_T(s, q));
+      bad |= fx_bad(G);
+      gx[base + pp] = G;
+    }
+    if (h < RPT) G0[h] = G;
+  }
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    const int pp = g.t + h * GT, q = s10(xcell(pp));
+    const long long v =
+        fx_div6(s[q - 1] + s[q + 1] + s[q - 10] + s[q + 10] + s[q - 100] + s[q + 100] + 6 * G0[h]);
+    bad |= fx_bad(v);
+    phx[base + pp] = v;
+  }
   fx_flag(bad, sc);
 }
 

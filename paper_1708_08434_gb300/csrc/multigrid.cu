@@ -1674,11 +1674,14 @@ static int fx_epilogue(sm_ctx *ctx) {
 // is one partial wave of blocks runs the half-row kernel (2 cells per
 // thread, twice the warps to hide its load latency).  Both give the bits
 // of the box kernel (fx_color_box, which the persistent kernel runs).
-static int fx_smooth(sm_ctx *ctx, int l, int nu) {
+// nu red-black sweeps of level l; with skip_first the first colour pass has
+// already run (k_ffas_color0)
+static int fx_smooth(sm_ctx *ctx, int l, int nu, bool skip_first = false) {
   const int n = lvl_n(ctx, l);
   if (!n) return SM_OK;
   for (int s = 0; s < nu; ++s)
     for (int color = 0; color < 2; ++color) {
+      if (skip_first && s == 0 && color == 0) continue;
       if (n >= ctx->rows_min)
         sm_launch(ctx, fx::k_fcolor_rows, (n + fx::RBOX - 1) / fx::RBOX, 64 * fx::RBOX, 0, ctx->level_off[l], n,
                   color, ctx->phx, ctx->gx, ctx->ghx, ctx->nbr6, ctx->bc, ctx->dscal);
@@ -1742,15 +1745,26 @@ static int fx_vcycle(sm_ctx *ctx, int top, int norm_slot = -1) {
   int st;
   if (norm_slot >= 0)
     SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
+  bool fused = false;  // the first colour pass of level l has run (k_ffas_color0)
   for (int l = top; l >= 1; --l) {
-    if ((st = fx_smooth(ctx, l, ctx->cfg.nu1))) return st;
-    if (lvl_n(ctx, l) >= ctx->rows_min)
+    if ((st = fx_smooth(ctx, l, ctx->cfg.nu1, fused))) return st;
+    // on a level of one partial wave below another, the FAS completion also
+    // runs the level's first colour pass; the restriction then copies the
+    // whole level below into old first
+    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0 && lvl_n(ctx, l) < ctx->rows_min && lvl_n(ctx, l - 1) < ctx->rows_min;
+    if (lvl_n(ctx, l) >= ctx->rows_min) {
       sm_launch(ctx, fx::k_fresid_restrict_rows, lvl_n(ctx, l), 64, 0, ctx->level_off[l], ctx->phx, ctx->gx,
                 ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
-    else
-      sm_launch(ctx, fx::k_fresid_restrict, lvl_n(ctx, l), GT, 0, ctx->level_off[l], ctx->phx, ctx->gx, ctx->ghx,
-                ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal);
-    if (l - 1 >= 1)  // level 0's FAS completion runs in the level-0 solve
+    } else {
+      const int nl = fused ? ctx->leaf_level_off[l] - ctx->leaf_level_off[l - 1] : 0;
+      sm_launch(ctx, fx::k_fresid_restrict, lvl_n(ctx, l) + nl, GT, 0, ctx->level_off[l], lvl_n(ctx, l), ctx->phx,
+                ctx->gx, ctx->ghx, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, ctx->dscal,
+                fused ? (long long *)ctx->old : nullptr, ctx->leaf + ctx->leaf_level_off[l - 1]);
+    }
+    if (fused)
+      sm_launch(ctx, fx::k_ffas_color0, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx,
+                (const long long *)ctx->old, ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
+    else if (l - 1 >= 1)  // level 0's FAS completion runs in the level-0 solve
       sm_launch(ctx, fx::k_ffas, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], ctx->phx, (long long *)ctx->old,
                 ctx->gx, ctx->ghx, ctx->nbr6, ctx->child, ctx->bc, ctx->dscal);
     SM_CKL("vcycle down");
