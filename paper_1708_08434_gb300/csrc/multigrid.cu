@@ -169,7 +169,7 @@ __device__ __forceinline__ Place load_place(const int32_t *__restrict__ parent, 
 template <typename T>
 __device__ __forceinline__ void resid_restrict_box(const Grp &g, T *s, T *sr, int b, T *phi, T *rhs, const T *gh,
                                                    const Nb &nb, const Place &pl, const Bc &bc, T inv_h2,
-                                                   int homog) {
+                                                   int homog, T *old = nullptr) {
   const size_t base = (size_t)b * CELLS;
   T f[CPT];
 #pragma unroll
@@ -195,7 +195,9 @@ __device__ __forceinline__ void resid_restrict_box(const Grp &g, T *s, T *sr, in
         ar += sr[c];
       }
   const size_t cc = (size_t)pl.P * CELLS + cidx(4 * pl.ox + ci, 4 * pl.oy + cj, 4 * pl.oz + ck);
-  phi[cc] = ap * T(0.125);
+  const T v = ap * T(0.125);
+  phi[cc] = v;
+  if (old) old[cc] = v;
   rhs[cc] = ar * T(0.125);
 }
 
@@ -697,18 +699,65 @@ __global__ void __launch_bounds__(GT) k_fas(int lo, T *__restrict__ phi, T *__re
 }
 
 template <typename T>
-__global__ void __launch_bounds__(GT) k_resid_restrict(int lo, T *__restrict__ phi, T *__restrict__ rhs,
+// Blocks [0, n) take the boxes lo.. of level l.  With old != nullptr the
+// restricted values also go to old, and blocks [n, n + nl) copy the leaf
+// boxes leaf[0, nl) of the level below into old (for k_fas_rbgs0).
+__global__ void __launch_bounds__(GT) k_resid_restrict(int lo, int n, T *__restrict__ phi, T *__restrict__ rhs,
                                                        const T *__restrict__ gh, const int32_t *__restrict__ nbr6,
                                                        const int32_t *__restrict__ parent,
                                                        const int32_t *__restrict__ ijk, Bc bc, T inv_h2,
-                                                       int homog) {
+                                                       int homog, T *__restrict__ old, const int32_t *__restrict__ leaf) {
   __shared__ T s[1000], sr[CELLS];
   const Grp g = block_grp();
+  if ((int)blockIdx.x >= n) {
+    const int b = __ldg(leaf + blockIdx.x - n);
+    pdl_wait();
+    const size_t base = (size_t)b * CELLS;
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) old[base + g.t + h * GT] = phi[base + g.t + h * GT];
+    return;
+  }
   const int b = lo + blockIdx.x;
   const Nb nb = load_nb(g, nbr6, b);
   const Place pl = load_place(parent, ijk, b);
   pdl_wait();
-  resid_restrict_box(g, s, sr, b, phi, rhs, gh, nb, pl, bc, inv_h2, homog);
+  resid_restrict_box(g, s, sr, b, phi, rhs, gh, nb, pl, bc, inv_h2, homog, old);
+}
+
+// k_fas fused with the first colour pass (colour 0) of the smoothing that
+// follows it on the same level.  The FAS term of a box reads its
+// neighbours' face cells, whose colour-0 values the neighbours' own blocks
+// of this launch overwrite; so every value is staged from old, which the
+// restriction launch before (k_resid_restrict with old) filled with the
+// whole level as it is now and which nothing in this launch writes.  The
+// box's new rhs is read back after the block barrier.  The same operations
+// as k_fas followed by k_rbgs with colour 0.
+template <typename T>
+__global__ void __launch_bounds__(GT) k_fas_rbgs0(int lo, T *__restrict__ phi, const T *__restrict__ old,
+                                                  T *__restrict__ rhs, const T *__restrict__ gh,
+                                                  const int32_t *__restrict__ nbr6, const int32_t *__restrict__ child,
+                                                  Bc bc, T inv_h2, T h2, int homog) {
+  __shared__ T s[1000];
+  const Grp g = block_grp();
+  const int b = lo + blockIdx.x;
+  const Nb nb = load_nb(g, nbr6, b);
+  const bool refined = __ldg(child + 8 * b) >= 0;
+  pdl_wait();
+  const size_t base = (size_t)b * CELLS;
+  stage_box(g, s, old, nb, gh, b, bc, homog);
+  if (refined) {
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) {
+      const int c = g.t + h * GT, q = s10(c);
+      rhs[base + c] += (staged_sum(s, q) - T(6) * s[q]) * inv_h2;
+    }
+  }
+  g.sync();
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    const int c = colour_cell(g.t + h * GT, 0);
+    phi[base + c] = rbgs_value(s, c, rhs[base + c], h2);
+  }
 }
 
 // leaf boxes of one level whose FP64 residual norm a prolongation launch
@@ -1302,11 +1351,14 @@ static int rbgs_pass(sm_ctx *ctx, const MG<T> &m, int l, int color) {
   return SM_OK;
 }
 
+// nu red-black sweeps of level l; with skip_first the first colour pass has
+// already run (k_fas_rbgs0)
 template <typename T>
-static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu) {
+static int smooth(sm_ctx *ctx, const MG<T> &m, int l, int nu, bool skip_first = false) {
   if (!lvl_n(ctx, l)) return SM_OK;
   for (int s = 0; s < nu; ++s)
-    for (int color = 0; color < 2; ++color) rbgs_pass(ctx, m, l, color);
+    for (int color = 0; color < 2; ++color)
+      if (!(skip_first && s == 0 && color == 0)) rbgs_pass(ctx, m, l, color);
   SM_CKL("rbgs");
   return SM_OK;
 }
@@ -1366,14 +1418,23 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top, int norm_slot = -1) {
   int st;
   if (norm_slot >= 0)
     SM_CK(cudaMemsetAsync(ctx->dscal + norm_slot, 0, sizeof(unsigned long long), ctx->stream));
+  bool fused = false;  // the first colour pass of level l has run (k_fas_rbgs0)
   for (int l = top; l >= 1; --l) {
-    if ((st = smooth(ctx, m, l, ctx->cfg.nu1))) return st;
-    sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l), GT, 0, ctx->level_off[l], m.phi, m.rhs, m.gh,
-              ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc,
-              (T)ctx->lh.inv_h2[l], m.homog);
-    sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
-              ctx->nbr6, ctx->child, ctx->bc,
-              (T)ctx->lh.inv_h2[l - 1], m.homog);
+    if ((st = smooth(ctx, m, l, ctx->cfg.nu1, fused))) return st;
+    // above level 0 the FAS step also runs the level's first colour pass;
+    // the restriction then copies the whole level below into old first
+    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0;
+    const int nl = fused ? ctx->leaf_level_off[l] - ctx->leaf_level_off[l - 1] : 0;
+    sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l) + nl, GT, 0, ctx->level_off[l], lvl_n(ctx, l), m.phi, m.rhs,
+              m.gh, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, (T)ctx->lh.inv_h2[l], m.homog,
+              fused ? m.old : nullptr, ctx->leaf + ctx->leaf_level_off[l - 1]);
+    if (fused)
+      sm_launch(ctx, k_fas_rbgs0<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, (const T *)m.old, m.rhs,
+                m.gh, ctx->nbr6, ctx->child, ctx->bc, (T)ctx->lh.inv_h2[l - 1], (T)ctx->lh.h2[l - 1], m.homog);
+    else
+      sm_launch(ctx, k_fas<T>, lvl_n(ctx, l - 1), GT, 0, ctx->level_off[l - 1], m.phi, m.old, m.rhs, m.gh,
+                ctx->nbr6, ctx->child, ctx->bc,
+                (T)ctx->lh.inv_h2[l - 1], m.homog);
     SM_CKL("vcycle down");
   }
   if ((st = coarse_solve(ctx, m))) return st;

@@ -157,9 +157,10 @@ __device__ __forceinline__ void begin_box(const double *var, const QTabs &T, int
 // ghost rules: same-level copy, wall ghost, refinement boundary
 // phi_f/3 + 2 phihat/3.  v0, v1: the box's own values (cells lane and
 // lane + 32).  With `alt`, neighbours with children are read from alt
-// instead of var (the FAS step's restricted values).
+// instead of var (the FAS step's restricted values); with alt_all every
+// same-level neighbour is.
 __device__ void stage_phi(const double *var, const double *alt, const BoxCtx &C, int b, const QBc &bc, int homog,
-                          double *s, int lane, unsigned *err, double v0, double v1) {
+                          double *s, int lane, unsigned *err, double v0, double v1, bool alt_all = false) {
   s[(lane / QN + 1) * S1 + lane % QN + 1] = v0;
   s[((lane + 32) / QN + 1) * S1 + lane % QN + 1] = v1;
   __syncwarp();
@@ -173,7 +174,7 @@ __device__ void stage_phi(const double *var, const double *alt, const BoxCtx &C,
   if (nb >= 0) {
     int si, sj;
     face_cell(f ^ 1, 0, u, si, sj);
-    v = ((alt && ((C.ref >> f) & 1)) ? alt : var)[(size_t)nb * QC + si + QN * sj];
+    v = ((alt && (alt_all || ((C.ref >> f) & 1))) ? alt : var)[(size_t)nb * QC + si + QN * sj];
   } else if (nb == -1) {
     v = bc.type[f] ? (homog ? 0.0 : bc.g2[f]) - inner : inner;
   } else {
@@ -232,13 +233,25 @@ __global__ void __launch_bounds__(QT) k_q_rbgs(int off, int n, int l, int colour
 // the restricted potential into old[parent] (committed by k_q_fas, so that
 // coarse values read for ghosts here stay unchanged), the restricted
 // residual into rhs[parent].  Volume-weighted mean of the four children.
+// Warps [0, n) take the boxes of level l; warps [n, n + nc) the boxes
+// coff.. of level l-1, copying those without children into old (so that
+// k_q_fas_rbgs0 finds the whole level in old).
 __global__ void __launch_bounds__(QT) k_q_resid_restrict(int off, int n, int l, const double *__restrict__ phi,
                                                          double *__restrict__ rhs, double *__restrict__ old,
-                                                         QTabs T, const __grid_constant__ QBc bc, double inv_h2, unsigned *err) {
+                                                         QTabs T, const __grid_constant__ QBc bc, double inv_h2, unsigned *err,
+                                                         int coff = 0, int nc = 0) {
   __shared__ double sm[WPB][S1 * S1];
   __shared__ double sr[WPB][QC];
   QWARP();
-  if (k_ >= n) return;
+  if (k_ >= n) {
+    if (k_ >= n + nc) return;
+    const int bc2 = coff + k_ - n;
+    const bool leaf = __ldg(T.chl + 4 * bc2) < 0;
+    q_wait();
+    if (leaf)
+      for (int c = lane; c < QC; c += 32) old[(size_t)bc2 * QC + c] = phi[(size_t)bc2 * QC + c];
+    return;
+  }
   const int b = off + k_;
   double *s = sm[wv_];
   double v0, v1;
@@ -291,6 +304,48 @@ __global__ void __launch_bounds__(QT) k_q_fas(int off, int n, int l, double *__r
     old[g0] = v0;
     old[g1] = v1;
   }
+}
+
+// k_q_fas fused with the first colour pass (colour 0) of the smoothing that
+// follows it on level l.  The FAS term of a box reads its neighbours' face
+// cells, whose colour-0 values the neighbours' own warps of this launch
+// overwrite; so the box and every same-level neighbour value are read from
+// old, which the restriction launch before filled with the whole level as
+// it is now (k_q_resid_restrict with nc) and which nothing in this launch
+// writes.  The staged box serves the FAS step and the colour-0 update (which
+// reads colour-1 cells and ghosts only); the warp's rhs and phi writes are
+// ordered before the update by __syncwarp.  The same operations as k_q_fas
+// followed by k_q_rbgs with colour 0.
+__global__ void __launch_bounds__(QT) k_q_fas_rbgs0(int off, int n, int l, double *__restrict__ phi,
+                                                    double *__restrict__ rhs, const double *__restrict__ old,
+                                                    QTabs T, const __grid_constant__ QBc bc, double inv_h2, double h2,
+                                                    unsigned *err) {
+  __shared__ double sm[WPB][S1 * S1];
+  QWARP();
+  if (k_ >= n) return;
+  const int b = off + k_;
+  const size_t g0 = (size_t)b * QC + lane, g1 = g0 + 32;
+  double o0, o1;
+  begin_box(old, T, b, C, lane, o0, o1);
+  const double f0 = rhs[g0], f1 = rhs[g1];
+  const bool refined = C.ref & 16;
+  double *s = sm[wv_];
+  const int j = lane >> 2, i = 2 * (lane & 3) + (j & 1);  // this lane's colour-0 cell
+  const double *wc = T.w + (size_t)b * 24 + 3 * i;
+  const double w0 = wc[0], w1 = wc[1], w2 = wc[2];
+  stage_phi(phi, old, C, b, bc, 0, s, lane, err, o0, o1, true);
+  if (refined) {
+    rhs[g0] = f0 + lap_s(s, T, b, lane % QN, lane / QN, inv_h2);
+    rhs[g1] = f1 + lap_s(s, T, b, lane % QN, lane / QN + 4, inv_h2);
+    phi[g0] = o0;
+    phi[g1] = o1;
+  }
+  __syncwarp();
+  const double fr = rhs[(size_t)b * QC + i + QN * j];
+  phi[(size_t)b * QC + i + QN * j] =
+      (w0 * s[(j + 1) * S1 + i] + w1 * s[(j + 1) * S1 + i + 2] + s[j * S1 + i + 1] + s[(j + 2) * S1 + i + 1] -
+       h2 * fr) *
+      w2;
 }
 
 // Prolongation to every box of level l: (2c + c_x + c_y)/4 of the parent
@@ -1251,10 +1306,13 @@ void qlaunch(sm_quad *q, void (*k)(KArgs...), int grid, int block, Args &&...arg
   ++q->launches;
 }
 
-void smooth(sm_quad *q, int l, int nu) {
+// nu red-black sweeps of level l; with skip_first the first colour pass has
+// already run (k_q_fas_rbgs0)
+void smooth(sm_quad *q, int l, int nu, bool skip_first = false) {
   const int n = level_count(q, l);
   for (int s = 0; s < nu; ++s)
     for (int c = 0; c < 2; ++c) {
+      if (skip_first && s == 0 && c == 0) continue;
       qlaunch(q, k_q_rbgs, blocks_for(n), QT, q->off[l], n, l, c, q->var[V_PHI], (const double *)q->var[V_RHS],
               tabs(q), q->bc, q->h[l] * q->h[l], q->d_err);
     }
@@ -1266,13 +1324,22 @@ void coarse_solve(sm_quad *q) {
 }
 
 void vcycle(sm_quad *q, int top) {
+  bool fused = false;  // the first colour pass of level l has run (k_q_fas_rbgs0)
   for (int l = top; l >= 1; --l) {
-    smooth(q, l, q->nu1);
+    smooth(q, l, q->nu1, fused);
     const int n = level_count(q, l), nc = level_count(q, l - 1);
-    qlaunch(q, k_q_resid_restrict, blocks_for(n), QT, q->off[l], n, l, (const double *)q->var[V_PHI],
-            q->var[V_RHS], q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l], q->d_err);
-    qlaunch(q, k_q_fas, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS], q->var[V_OLD],
-            tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
+    // below the top level but above level 0 the FAS step also runs the first
+    // colour pass; the restriction then copies the level's leaves into old
+    fused = l - 1 >= 1;
+    const int ncp = fused ? nc : 0;
+    qlaunch(q, k_q_resid_restrict, blocks_for(n + ncp), QT, q->off[l], n, l, (const double *)q->var[V_PHI],
+            q->var[V_RHS], q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l], q->d_err, q->off[l - 1], ncp);
+    if (fused)
+      qlaunch(q, k_q_fas_rbgs0, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS],
+              (const double *)q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l - 1], q->h[l - 1] * q->h[l - 1], q->d_err);
+    else
+      qlaunch(q, k_q_fas, blocks_for(nc), QT, q->off[l - 1], nc, l - 1, q->var[V_PHI], q->var[V_RHS],
+              q->var[V_OLD], tabs(q), q->bc, q->inv_h2[l - 1], q->d_err);
   }
   coarse_solve(q);
   for (int l = 1; l <= top; ++l) {
