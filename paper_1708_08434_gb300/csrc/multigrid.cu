@@ -1421,9 +1421,10 @@ static int vcycle(sm_ctx *ctx, const MG<T> &m, int top, int norm_slot = -1) {
   bool fused = false;  // the first colour pass of level l has run (k_fas_rbgs0)
   for (int l = top; l >= 1; --l) {
     if ((st = smooth(ctx, m, l, ctx->cfg.nu1, fused))) return st;
-    // above level 0 the FAS step also runs the level's first colour pass;
-    // the restriction then copies the whole level below into old first
-    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0;
+    // on a level of one partial wave below another (above level 0) the FAS
+    // step also runs the level's first colour pass; the restriction then
+    // copies the whole level below into old first
+    fused = l - 1 >= 1 && ctx->cfg.nu1 > 0 && lvl_n(ctx, l) < ctx->rows_min && lvl_n(ctx, l - 1) < ctx->rows_min;
     const int nl = fused ? ctx->leaf_level_off[l] - ctx->leaf_level_off[l - 1] : 0;
     sm_launch(ctx, k_resid_restrict<T>, lvl_n(ctx, l) + nl, GT, 0, ctx->level_off[l], lvl_n(ctx, l), m.phi, m.rhs,
               m.gh, ctx->nbr6, ctx->parent, ctx->ijk, ctx->bc, (T)ctx->lh.inv_h2[l], m.homog,
