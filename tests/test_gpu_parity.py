@@ -516,12 +516,14 @@ def test_repeatable_bits_full_size_streamer6():
     """Blocks of one launch never read what another block of it writes: the
     same solves on fresh solvers give the same bits, on the captured graphs
     and on the host loop, with and without programmatic dependent launch
-    (FMG, one more V-cycle, a warm-started solve to 1e-11; 2.4e6 leaf
-    cells, where every level is one partial wave of blocks)."""
+    and with the persistent kernel (FMG, one more V-cycle, a warm-started
+    solve to 1e-11; 2.4e6 leaf cells, where every level is one partial wave
+    of blocks)."""
     dom, st = synth.workload("streamer6")
     p = __import__("paper_1708_08434_gb300")
     runs = []
-    for graphs, pdl in ((True, True), (True, True), (False, True), (False, False)):
+    for graphs, pdl, persist in ((True, True, False), (True, True, False), (False, True, False),
+                                 (False, False, False), (True, True, True)):
         g = gpu_mesh(dom, st, max_boxes=8192)
         t = g.tables()
         ne, ni = synth.streamer_densities(dom, st, t["level"], t["ijk"])
@@ -530,6 +532,7 @@ def test_repeatable_bits_full_size_streamer6():
         g.charge_rhs(Q, EPS0)
         g.set_graphs(graphs)
         g.set_pdl(pdl)
+        g.set_persistent(persist)
         out = [g.fmg(1e-30, 1)[2]]
         out.append(g.download(p.PHI).view(np.int64).copy())
         g.vcycles(1)
