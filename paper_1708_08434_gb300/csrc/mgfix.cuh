@@ -433,22 +433,6 @@ __device__ __forceinline__ unsigned long long fx_resid_max_box(const Grp &g, lon
 }
 
 // ---------------------------------------------------------------------------
-// kernels (one box per block of GT threads unless stated)
-// ---------------------------------------------------------------------------
-
-__global__ void __launch_bounds__(GT) k_fcolor(int lo, int color, long long *__restrict__ phx,
-                                               const long long *__restrict__ gx, const long long *__restrict__ ghx,
-                                               const int32_t *__restrict__ nbr6, Bc bc, unsigned long long *sc) {
-  __shared__ long long s[1000];
-  const Grp g = block_grp();
-  const int b = lo + blockIdx.x;
-  const Nb nb = load_nb(g, nbr6, b);
-  pdl_wait();
-  const bool bad = fx_color_box(g, s, b, color, phx, gx, ghx, nb, bc, sc);
-  fx_flag(bad, sc);
-}
-
-// ---------------------------------------------------------------------------
 // red-black Gauss-Seidel by rows: one thread per x row of the colour
 // ---------------------------------------------------------------------------
 //
@@ -908,40 +892,16 @@ struct FxNorm {
   unsigned long long *slot;
 };
 
-// Blocks [0, n) prolong into boxes [lo, lo + n) of level l; blocks beyond
-// add the residual max of the leaf boxes of level l-1 (final once level l
-// is prolonged into) to nm.slot.
-__global__ void __launch_bounds__(GT) k_fprolong(int lo, int n, int mode, long long *__restrict__ phx,
-                                                 const long long *__restrict__ oldx, long long *__restrict__ ghx,
-                                                 const int32_t *__restrict__ nbr6, const int32_t *__restrict__ parent,
-                                                 const int32_t *__restrict__ ijk, Bc bc, unsigned long long *sc,
-                                                 FxNorm nm) {
-  __shared__ long long s[1000];
-  __shared__ unsigned long long red[GT / 32];
-  const Grp g = block_grp();
-  if ((int)blockIdx.x >= n) {
-    const int b = __ldg(nm.leaf + blockIdx.x - n);
-    const Nb nb = load_nb(g, nbr6, b);
-    pdl_wait();
-    const double nq = -fx_q(fx_E(sc)) * nm.inv_h2;
-    const unsigned long long m = fx_resid_max_box(g, s, b, phx, nm.rhs, ghx, nb, bc, sc, nq);
-    group_umax_to(g, nm.slot, m, red);
-    return;
-  }
-  pdl_wait();
-  const bool bad = fx_prolong_box(g, s, lo + blockIdx.x, mode, phx, oldx, ghx, nbr6, parent, ijk, bc, sc,
-                                  sc + SC_ERR);
-  fx_flag(bad, sc);
-}
-
 // Prolongation by rows (large levels): blocks of 128 threads take two boxes
 // of level l, one thread per fine x row of a box.  The 6^3 coarse values
 // (the 4^3 parent cells under the box and their face neighbours, as in
 // fx_prolong_box) are staged per box; each thread forms its row's 8 fine
 // values (c + c_x + c_y + c_z)/4 and adds them to (mode 0) or writes them
 // over (mode 1) its row with 16-byte loads and stores, then the box's Ghat
-// values.  Blocks beyond the prolongation measure leaf residuals as in
-// k_fprolong.  The same integer sums: the bits of k_fprolong.
+// values.  Blocks beyond the prolongation add the residual max of the leaf
+// boxes of level l-1 (final once level l is prolonged into) to nm.slot.
+// The same integer sums as fx_prolong_box (the persistent kernel's): the
+// same bits.
 __global__ void __launch_bounds__(128) k_fprolong_rows(int lo, int n, int mode, long long *__restrict__ phx,
                                                        const long long *__restrict__ oldx,
                                                        long long *__restrict__ ghx,
@@ -1050,7 +1010,8 @@ __global__ void __launch_bounds__(128) k_fprolong_rows(int lo, int n, int mode, 
 // Prolongation with two threads per fine x row (128 per box, small
 // levels): thread (r, h) forms the 4 fine cells i = 4h .. 4h + 3 of row r
 // and updates them with one 16-byte load and store per colour.  Staging,
-// Ghat values and the leaf-residual blocks as in k_fprolong; the same bits.
+// Ghat values and the leaf-residual blocks as in k_fprolong_rows; the same
+// bits.
 __global__ void __launch_bounds__(GT) k_fprolong_half(int lo, int n, int mode, long long *__restrict__ phx,
                                                       const long long *__restrict__ oldx,
                                                       long long *__restrict__ ghx,
