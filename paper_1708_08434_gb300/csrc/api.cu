@@ -58,7 +58,7 @@ struct ArenaPlan {
 
 // layout shared by sm_arena_size and sm_bind_arena
 struct Layout {
-  size_t level, ijk, parent, child, nbr, nbr6, leaf, morton, scan_a, scan_b, count, flags;
+  size_t level, ijk, parent, child, nbr, nbr6, leaf, cf_leaf, morton, scan_a, scan_b, count, flags;
   size_t phi, rhs, res, old, rho, emag, nb[3], ib[3], gh, cflux, basis, tab, dscal, hist, e32, f32, old32, gh32,
       phx, gx, ghx, total;
 };
@@ -74,6 +74,7 @@ static Layout plan(int cap, bool mixed) {
   L.nbr = p.take<int32_t>((size_t)cap * 26);
   L.nbr6 = p.take<int32_t>((size_t)cap * 6);
   L.leaf = p.take<int32_t>(cap);
+  L.cf_leaf = p.take<int32_t>(cap);
   L.morton = p.take<uint64_t>(cap);
   L.scan_a = p.take<int32_t>(cap + 1);
   L.scan_b = p.take<int32_t>(cap + 1);
@@ -199,6 +200,7 @@ extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   ctx->nbr = (int32_t *)(a + L.nbr);
   ctx->nbr6 = (int32_t *)(a + L.nbr6);
   ctx->leaf = (int32_t *)(a + L.leaf);
+  ctx->cf_leaf = (int32_t *)(a + L.cf_leaf);
   ctx->morton = (uint64_t *)(a + L.morton);
   ctx->scan_a = (int32_t *)(a + L.scan_a);
   ctx->scan_b = (int32_t *)(a + L.scan_b);
@@ -231,7 +233,7 @@ extern "C" int sm_bind_arena(sm_ctx *ctx, void *dev_ptr, size_t bytes) {
   }
   SM_CK(cudaMemsetAsync(a, 0, L.total, ctx->stream));
   sm_drop_graphs(ctx);
-  ctx->n_boxes = ctx->n_levels = ctx->n_leaves = 0;
+  ctx->n_boxes = ctx->n_levels = ctx->n_leaves = ctx->n_cf_leaves = 0;
   ctx->basis_ready = false;
   return SM_OK;
 }
@@ -374,6 +376,18 @@ __global__ void k_mark_leaves(int n, const int32_t *__restrict__ child, int32_t 
   if (b < n) is_leaf[b] = child[8 * b] < 0 ? 1 : 0;
 }
 
+// leaf boxes with a refinement face: a face whose same-level neighbour is
+// missing inside the domain (nbr6 == -2)
+__global__ void k_mark_cf_leaves(int n, const int32_t *__restrict__ child, const int32_t *__restrict__ nbr6,
+                                 int32_t *flag) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  int f = 0;
+  if (child[8 * b] < 0)
+    for (int k = 0; k < 6; ++k) f |= nbr6[6 * b + k] == -2;
+  flag[b] = f;
+}
+
 __global__ void k_compact(int n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
                           int32_t *out) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -398,14 +412,26 @@ int sm_rebuild_leaves(sm_ctx *ctx) {
   ++ctx->n_launch;
   SM_CKL("leaf list");
   // leaf count and per-level leaf offsets from the prefix sums at level offsets
-  std::vector<int32_t> h(ctx->n_levels + 1);
+  std::vector<int32_t> h(ctx->n_levels + 2);
   for (int l = 0; l <= ctx->n_levels; ++l) {
     SM_CK(cudaMemcpyAsync(&h[l], ctx->scan_b + ctx->level_off[l], sizeof(int32_t),
                           cudaMemcpyDeviceToHost, ctx->stream));
   }
+  // the leaves with a refinement face (the fluid step's refinement fluxes);
+  // the scan buffers are reused after the copies above in stream order
+  k_mark_cf_leaves<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->child, ctx->nbr6, ctx->scan_a);
+  ++ctx->n_launch;
+  k_scan<<<1, 1024, 0, ctx->stream>>>(ctx->scan_a, ctx->scan_b, n);
+  ++ctx->n_launch;
+  k_compact<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->scan_a, ctx->scan_b, ctx->cf_leaf);
+  ++ctx->n_launch;
+  SM_CKL("refinement-face leaf list");
+  SM_CK(cudaMemcpyAsync(&h[ctx->n_levels + 1], ctx->scan_b + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                        ctx->stream));
   SM_CK(cudaStreamSynchronize(ctx->stream));
   for (int l = 0; l <= ctx->n_levels; ++l) ctx->leaf_level_off[l] = h[l];
   ctx->n_leaves = h[ctx->n_levels];
+  ctx->n_cf_leaves = h[ctx->n_levels + 1];
   ctx->pdl_fence = true;  // level kernels read the new tables before their PDL wait
   return SM_OK;
 }

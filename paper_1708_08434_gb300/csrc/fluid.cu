@@ -284,8 +284,9 @@ __global__ void __launch_bounds__(512) k_dt(const int32_t *__restrict__ leaf, co
 }
 
 // Fine-side fluxes through the refinement faces of leaf boxes (64 threads
-// per leaf box, one per face cell); read by the box itself and averaged by
-// its coarse neighbour, so both sides use the same numbers.
+// per box, one per face cell, over the list of leaves that have such a
+// face); read by the box itself and averaged by its coarse neighbour, so
+// both sides use the same numbers.
 __global__ void __launch_bounds__(64) k_cf_flux(const int32_t *__restrict__ leaf, const int32_t *__restrict__ level,
                                                 const double *__restrict__ n, const double *__restrict__ phi,
                                                 const double *__restrict__ gh, const double *__restrict__ emag,
@@ -559,11 +560,13 @@ static int stage(sm_ctx *ctx, int s, int d, int h0, double dt, double q, double 
   int st;
   Table tb = table_of(ctx);
   if ((st = sm_fill_all_cf(ctx, ctx->phi))) return st;
-  k_cf_flux<<<ctx->n_leaves, 64, 0, ctx->stream>>>(ctx->leaf, ctx->level, ctx->nbuf[s], ctx->phi, ctx->gh,
-                                                   ctx->emag, ctx->nbr6, ctx->parent, ctx->ijk, ctx->lh, tb,
-                                                   ctx->cflux, ctx->dscal + SC_ERR);
-  ++ctx->n_launch;
-  SM_CKL("cf_flux");
+  if (ctx->n_cf_leaves > 0) {
+    k_cf_flux<<<ctx->n_cf_leaves, 64, 0, ctx->stream>>>(ctx->cf_leaf, ctx->level, ctx->nbuf[s], ctx->phi,
+                                                         ctx->gh, ctx->emag, ctx->nbr6, ctx->parent, ctx->ijk,
+                                                         ctx->lh, tb, ctx->cflux, ctx->dscal + SC_ERR);
+    ++ctx->n_launch;
+    SM_CKL("cf_flux");
+  }
   size_t smem = sizeof(UpdSmem);
   k_update<<<ctx->n_leaves, 512, smem, ctx->stream>>>(
       ctx->leaf, ctx->level, ctx->nbuf[s], ctx->ibuf[s], h0 >= 0 ? ctx->nbuf[h0] : nullptr,

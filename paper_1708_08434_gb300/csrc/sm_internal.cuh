@@ -93,6 +93,7 @@ struct sm_ctx {
   // tables (device)
   int32_t *level = nullptr, *ijk = nullptr, *parent = nullptr, *child = nullptr,
           *nbr = nullptr, *nbr6 = nullptr, *leaf = nullptr;
+  int32_t *cf_leaf = nullptr;  // leaf boxes with at least one refinement face (nbr6 == -2)
   uint64_t *morton = nullptr;
   int32_t *scan_a = nullptr, *scan_b = nullptr;  // [max_boxes] build scratch
   int32_t *dev_count = nullptr;                   // small device counters
@@ -124,7 +125,7 @@ struct sm_ctx {
   double tab_emax = 0.0;
 
   // host mirrors
-  int n_boxes = 0, n_levels = 0, n_leaves = 0;
+  int n_boxes = 0, n_levels = 0, n_leaves = 0, n_cf_leaves = 0;
   int level_off[SM_MAX_LEVELS + 1] = {0};
   int leaf_level_off[SM_MAX_LEVELS + 1] = {0};
   double *hscal = nullptr;   // pinned host scalars [SC_N], then a staged copy [SC_N]
