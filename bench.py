@@ -510,6 +510,14 @@ def run_gpu(args):
         fmg_only = {"solves_per_s": round(10 / (fa.elapsed_time(fb) * 1e-3), 2), "vcycles": fcyc,
                     "note": "FMG to 1e-8 from phi = 0 on the same workload, 10 solves timed with CUDA events "
                             "(L2 not flushed)"}
+    # where the step's time goes: CUDA events on the library's stream
+    # between the calls of one step (after an L2 flush, like a timed step;
+    # host gaps such as the time-step read are inside the phase that waits),
+    # and the fixed and per-cycle cost of a solve from warm-started solves
+    # run to tol 0 for 1 and 4 V-cycles
+    step_phases = None
+    if not args.no_profile:
+        step_phases = phase_breakdown(g, ne_d, ni_d, flush, Q, E0)
     # end to end through the C ABI with host buffers (H2D + D2H every step)
     e2e_ms, _, _ = timed(args.steps, host_io=True)
     e2e_ms = max_over_ranks(e2e_ms, dev)
@@ -723,6 +731,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "fmg_only": fmg_only,
+        "step_phases": step_phases,
         "roofline": roof,
         "mixed_precision": mixed,
         "field_and_fluid": fluid,
@@ -742,6 +751,60 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def phase_breakdown(g, ne_d, ni_d, flush, q, eps, reps=10):
+    """Mean microseconds of each call of the benchmark step (CUDA events
+    recorded on the library's stream between the calls, L2 flushed before
+    each step), and the cost of a warm-started FP64 solve as a fixed part
+    plus a part per V-cycle, from solves of 1 and 4 cycles (tol 0)."""
+    import torch
+    import paper_1708_08434_gb300 as pkg
+    s = g.stream
+    names = ("density copy", "charge", "fmg", "field", "dt limit", "heun step")
+    acc = [0.0] * len(names)
+    for _ in range(reps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(s)
+        g.var(pkg.NE).copy_(ne_d)
+        g.var(pkg.NI).copy_(ni_d)
+        ev[1].record(s)
+        g.charge_rhs(q, eps)
+        ev[2].record(s)
+        g.fmg(TOL, MAX_CYCLES)
+        ev[3].record(s)
+        g.compute_field()
+        ev[4].record(s)
+        dt = g.dt_limit(q, eps)
+        ev[5].record(s)
+        g.advance(dt, q, eps, TOL, MAX_CYCLES)
+        ev[6].record(s)
+        torch.cuda.synchronize()
+        for i in range(len(names)):
+            acc[i] += ev[i].elapsed_time(ev[i + 1]) * 1e3
+    out = {n: round(a / reps, 1) for n, a in zip(names, acc)}
+
+    def solve_us(k):
+        g.solve(0.0, k)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(reps):
+            g.solve(0.0, k)
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / reps
+
+    t1, t4 = solve_us(1), solve_us(4)
+    per_cycle = (t4 - t1) / 3.0
+    out["solve_cost"] = {"fixed_us": round(t1 - per_cycle, 1), "per_vcycle_us": round(per_cycle, 1),
+                         "note": "warm-started FP64 solve (CUDA graph with a device-side loop): scale, "
+                                 "conversions and ghost fills before and after the loop, the graph launch "
+                                 "and the read of the cycle count; per V-cycle the cycle and its stopping test"}
+    return out
 
 
 def bench_configs():

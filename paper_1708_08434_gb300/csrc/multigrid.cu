@@ -1730,14 +1730,13 @@ static int fx_epilogue(sm_ctx *ctx) {
   return sm_fill_all_cf(ctx, ctx->phi);
 }
 
-// nu red-black sweeps of level l (two colour passes each, in place).  A
+// nu red-black sweeps of level l (two colour passes each, in place); with
+// skip_first the first colour pass has already run (k_ffas_color0).  A
 // level of at least ctx->rows_min boxes runs the row kernel (4 cells and
 // 16-byte row loads per thread, fewer instructions per cell); a level that
 // is one partial wave of blocks runs the half-row kernel (2 cells per
 // thread, twice the warps to hide its load latency).  Both give the bits
 // of the box kernel (fx_color_box, which the persistent kernel runs).
-// nu red-black sweeps of level l; with skip_first the first colour pass has
-// already run (k_ffas_color0)
 static int fx_smooth(sm_ctx *ctx, int l, int nu, bool skip_first = false) {
   const int n = lvl_n(ctx, l);
   if (!n) return SM_OK;
