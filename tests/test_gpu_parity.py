@@ -217,6 +217,7 @@ def check_advance(name, tol_solve=1e-8):
     assert ro[2:] == rg[2:], (ro, rg)
     assert rg[1] == pytest.approx(ro[1], rel=TOL)
     leaf = t["child"][:, 0] < 0
+    p = pkg()
     for vo, vg in ((oracle.NE, p.NE), (oracle.NI, p.NI), (oracle.PHI, p.PHI), (oracle.EMAG, p.EMAG)):
         e = rel_err(g.download(vg)[leaf], o.get(vo)[leaf])
         assert e <= TOL, (vo, e)
