@@ -93,9 +93,20 @@ def load():
     if not os.path.exists(path):
         raise ImportError("CUDA library %s is not built (run __graft_entry__.build())" % path)
     lib = C.CDLL(path)
+    for name, args in signatures().items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name.endswith("last_error") else C.c_int
+    _lib = lib
+    return lib
+
+
+def signatures() -> dict:
+    """ctypes argument types of every C-ABI entry point, by name (the
+    prototypes of include/sm_streamer.h and include/sm_quad.h)."""
     P, I, D = C.c_void_p, C.c_int, C.c_double
     pI, pD = C.POINTER(C.c_int), C.POINTER(C.c_double)
-    sig = {
+    return {
         "sm_create": [C.POINTER(P), P, P, P],
         "sm_destroy": [P],
         "sm_arena_size": [P, C.POINTER(C.c_size_t)],
@@ -188,12 +199,6 @@ def load():
         "sm_quad_launch_count": [P, C.POINTER(C.c_longlong)],
         "sm_quad_last_error": [P],
     }
-    for name, args in sig.items():
-        fn = getattr(lib, name)
-        fn.argtypes = args
-        fn.restype = C.c_char_p if name.endswith("last_error") else C.c_int
-    _lib = lib
-    return lib
 
 
 def _hp(a: np.ndarray):

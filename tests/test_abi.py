@@ -34,6 +34,54 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def prototypes():
+    """{name: [parameter type class, ...]} of every prototype in include/*.h
+    (a pointer of any type is "ptr")."""
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    scalar = {"int": "i32", "double": "f64", "float": "f32", "long long": "i64",
+              "unsigned long long": "u64", "size_t": "u64"}
+    out = {}
+    for name, params in re.findall(r"\b(?:int|const\s+char\s*\*)\s*(sm_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", src):
+        kinds = []
+        for p in params.split(","):
+            p = " ".join(p.split())
+            if not p or p == "void":
+                continue
+            if "*" in p:
+                kinds.append("ptr")
+                continue
+            words = p.replace("const ", "").split()
+            assert " ".join(words[:-1]) in scalar, (name, p)
+            kinds.append(scalar[" ".join(words[:-1])])
+        out[name] = kinds
+    return out
+
+
+def ctypes_kind(t):
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    for kind, types in (("i32", (C.c_int,)), ("f64", (C.c_double,)), ("f32", (C.c_float,)),
+                        ("i64", (C.c_longlong,)), ("u64", (C.c_ulonglong, C.c_size_t))):
+        if t in types:
+            return kind
+    raise AssertionError(t)
+
+
+def test_binding_signatures_match_the_headers():
+    """Every ctypes signature of the binding has the parameter count and
+    the scalar types of its prototype (a mismatch would pass garbage
+    through the C ABI without any error)."""
+    import paper_1708_08434_gb300 as pkg
+    protos = prototypes()
+    sigs = pkg.signatures()
+    assert sorted(protos) == sorted(sigs) == sorted(pkg.EXPORTS)
+    for name, kinds in protos.items():
+        assert [ctypes_kind(t) for t in sigs[name]] == kinds, name
+
+
 def test_library_is_sm103a_only():
     from paper_1708_08434_gb300 import _build
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
