@@ -176,7 +176,8 @@ int sm_set_table(sm_ctx *ctx, int n, double e_max, const double *mu,
 int sm_charge_rhs(sm_ctx *ctx, double q, double eps, int use_rho);
 
 /* Refined boxes of n_e and n_i get the average of their 8 children,
- * finest level first. */
+ * finest level first (the 8-child restriction of the multigrid hierarchy,
+ * Sec. 2.1.2, applied to the densities). */
 int sm_restrict_densities(sm_ctx *ctx);
 
 /* Coarse-to-fine interpolation values at refinement boundaries of `level`
@@ -197,8 +198,8 @@ int sm_get_ghosts(sm_ctx *ctx, int var, double *host, int n_boxes);
 
 /* ---- multigrid (Sec. 2.1.2) ---------------------------------------------- */
 
-/* n_cycles FAS V(nu1,nu2) cycles on the full hierarchy starting from the
- * current potential.  Out: relative residual max_leaf|f - L phi| /
+/* n_cycles FAS V(nu1,nu2) cycles (Sec. 2.1.2) on the full hierarchy
+ * starting from the current potential.  Out: relative residual max_leaf|f - L phi| /
  * max_leaf|f - L 0| after the last cycle (may be NULL). */
 int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res);
 
@@ -207,8 +208,9 @@ int sm_mg_vcycle(sm_ctx *ctx, int n_cycles, double *rel_res);
  * when max_cycles is reached (the potential is still updated). */
 int sm_mg_solve(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res);
 
-/* Full multigrid from scratch (restrict f, exact level-0 solve, prolong
- * and one V-cycle per level), then V-cycles to tol.  *cycles counts the
+/* Full multigrid from scratch (Sec. 2.1.2, the initial potential of a
+ * run: restrict f, exact level-0 solve, prolong and one V-cycle per
+ * level), then V-cycles to tol.  *cycles counts the
  * top-level V-cycles including the last FMG one. */
 int sm_mg_fmg(sm_ctx *ctx, double tol, int max_cycles, int *cycles, double *rel_res);
 
@@ -255,17 +257,18 @@ int sm_refine(sm_ctx *ctx, const int8_t *flags, int *n_boxes);
 
 /* ---- field and fluid step (Sec. 2.3, 2.4) --------------------------------- */
 
-/* |E| on every leaf cell: face fields E = (phi_i - phi_{i+1})/dx, cell
- * components = mean of the two faces, |E| = Euclidean norm. */
+/* |E| on every leaf cell (Sec. 2.3): face fields E = (phi_i - phi_{i+1})/dx,
+ * cell components = mean of the two faces, |E| = Euclidean norm. */
 int sm_compute_field(sm_ctx *ctx);
 
-/* Next time step from the current field and n_e: 0.9 x min of the CFL 0.5
- * limit, the advection+diffusion limit and the dielectric relaxation time
- * eps/(q mu n_e).  Synchronises. */
+/* Next time step (Sec. 2.4) from the current field and n_e: 0.9 x min of
+ * the CFL 0.5 limit, the advection+diffusion limit and the dielectric
+ * relaxation time eps/(q mu n_e).  Synchronises. */
 int sm_dt_limit(sm_ctx *ctx, double q, double eps, double *dt);
 
-/* One forward-Euler stage n <- n + dt F(n) with the current field (for
- * tests); densities of refined boxes are restricted afterwards. */
+/* One forward-Euler stage n <- n + dt F(n) with the current field (Sec.
+ * 2.2-2.3, Eq. 2-3 with the fluxes of Eq. 6-7; for tests); densities of
+ * refined boxes are restricted afterwards. */
 int sm_fluid_stage(sm_ctx *ctx, double dt);
 
 /* One explicit trapezoidal (Heun) step over dt (Sec. 2.4): stage 1, charge
